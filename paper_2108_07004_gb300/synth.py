@@ -1,0 +1,205 @@
+"""Seeded synthetic channel generator (untimed input side).
+
+Produces dual-polarisation received samples shaped like a 28 GBd coherent
+link: i.i.d. uniform bits mapped onto a constellation (PCG64 random numbers,
+as the transmitter in Sec. 3 of the paper uses), root-raised-cosine pulse
+shaping at ``sps`` samples per symbol, chromatic dispersion
+H_CD(f) = exp(j*D*L*lambda^2*omega^2/(4*pi*c)), a fixed Haar-random 2x2
+unitary polarisation rotation, one Wiener laser phase process common to
+both polarisations, and complex AWGN.
+
+This module is shared by the tests, the benchmark and the oracle.  It holds
+none of the receiver's arithmetic: it only makes inputs.  All arithmetic is
+float64; the output samples are cast to complex64.
+
+Conventions
+-----------
+* Es/N0 is per polarisation per symbol; the constellation has unit mean
+  energy per polarisation, so N0 = 10**(-EsN0_dB/10).
+* The transmit filter G(f) = sqrt(sps * r(f)), r the raised-cosine shape,
+  so that sum(g**2) == 1 and the matched-filtered, symbol-spaced samples
+  reproduce the symbols exactly (Nyquist).  AWGN of complex variance N0 per
+  sample therefore gives Es/N0 at the matched-filter output.
+* Spectra use numpy's forward DFT sign (exp(-j 2 pi k n / N)), under which
+  H_CD above delays low frequencies more than high ones for D > 0, as
+  standard single-mode fibre at 1550 nm does.
+"""
+from __future__ import annotations
+
+import json
+import os
+from dataclasses import dataclass
+
+import numpy as np
+import scipy.fft as sfft
+
+C_LIGHT = 299_792_458.0
+LAMBDA_1550 = 1550e-9
+SEED_BASE = 2108070040
+
+_DATA = os.path.join(os.path.dirname(__file__), "data")
+
+
+def stream_seed(cfg: int, point: int = 0) -> int:
+    """Seed convention for workload ``cfg`` and sweep point ``point``."""
+    return SEED_BASE + 10 * cfg + point
+
+
+# ---------------------------------------------------------------------------
+# transmitter constellations (Tx mapping only)
+# ---------------------------------------------------------------------------
+
+@dataclass
+class TxFormat:
+    name: str
+    dims: int            # 2: the same 2D table on each polarisation; 4: joint 4D
+    points: np.ndarray   # dims==2: [M] complex; dims==4: [M, 2] complex; index == label
+    bits_per_4d: int     # bits per 4D symbol (both polarisations)
+
+
+def _gray_pam_levels(nbits: int) -> np.ndarray:
+    """Amplitude for each PAM label, Gray coded, label MSB = sign (0 -> +)."""
+    n = 1 << nbits
+    levels = np.empty(n)
+    # position p (0 = most positive) carries Gray code p ^ (p >> 1)
+    for p in range(n):
+        g = p ^ (p >> 1)
+        levels[g] = (n - 1) - 2 * p
+    return levels
+
+
+def tx_qam_gray(m_pol: int) -> TxFormat:
+    """Square Gray QAM with ``m_pol`` bits per polarisation (2: QPSK, 4: 16QAM)."""
+    h = m_pol // 2
+    lv = _gray_pam_levels(h)
+    pts = np.empty(1 << m_pol, dtype=np.complex128)
+    for lab in range(1 << m_pol):
+        pts[lab] = lv[lab >> h] + 1j * lv[lab & ((1 << h) - 1)]
+    pts /= np.sqrt(np.mean(np.abs(pts) ** 2))
+    name = {2: "dp_qpsk", 4: "dp_16qam"}.get(m_pol, f"dp_{1 << m_pol}qam")
+    return TxFormat(name, 2, pts, 2 * m_pol)
+
+
+def tx_table4d(path: str) -> TxFormat:
+    """Joint 4D table from a JSON file holding ``points`` as [M][4] reals
+    (x_re, x_im, y_re, y_im) and ``labels`` (a permutation of 0..M-1)."""
+    with open(path) as f:
+        d = json.load(f)
+    p = np.asarray(d["points"], dtype=np.float64)
+    lab = np.asarray(d["labels"], dtype=np.int64)
+    pts = np.empty((len(lab), 2), dtype=np.complex128)
+    pts[lab, 0] = p[:, 0] + 1j * p[:, 1]
+    pts[lab, 1] = p[:, 2] + 1j * p[:, 3]
+    return TxFormat(d.get("name", "table4d"), 4, pts, int(np.log2(len(lab))))
+
+
+def tx_format(name: str) -> TxFormat:
+    if name == "dp_qpsk":
+        return tx_qam_gray(2)
+    if name == "dp_16qam":
+        return tx_qam_gray(4)
+    if name == "gs4d64":
+        return tx_table4d(os.path.join(_DATA, "gs4d64_v1.json"))
+    raise ValueError(f"unknown format {name!r}")
+
+
+def bits_to_symbols(fmt: TxFormat, bits: np.ndarray) -> np.ndarray:
+    """bits [N, m] (MSB first; for 2D formats X bits then Y bits) -> [2, N]."""
+    n, m = bits.shape
+    w = (1 << np.arange(m - 1, -1, -1)).astype(np.int64)
+    if fmt.dims == 4:
+        lab = bits.astype(np.int64) @ w
+        return fmt.points[lab].T.copy()
+    h = m // 2
+    wx = (1 << np.arange(h - 1, -1, -1)).astype(np.int64)
+    lx = bits[:, :h].astype(np.int64) @ wx
+    ly = bits[:, h:].astype(np.int64) @ wx
+    return np.stack([fmt.points[lx], fmt.points[ly]])
+
+
+# ---------------------------------------------------------------------------
+# channel
+# ---------------------------------------------------------------------------
+
+def raised_cosine_shape(f: np.ndarray, symbol_rate: float, rolloff: float) -> np.ndarray:
+    """Normalised raised-cosine spectrum r(f) in [0, 1]."""
+    af = np.abs(f)
+    f1 = (1 - rolloff) * symbol_rate / 2
+    f2 = (1 + rolloff) * symbol_rate / 2
+    r = np.zeros_like(af)
+    r[af <= f1] = 1.0
+    band = (af > f1) & (af <= f2)
+    if rolloff > 0:
+        r[band] = 0.5 * (1 + np.cos(np.pi / (rolloff * symbol_rate) * (af[band] - f1)))
+    return r
+
+
+def cd_channel_response(f: np.ndarray, cd_ps_per_nm: float,
+                        wavelength: float = LAMBDA_1550) -> np.ndarray:
+    """Fibre response exp(j*D*L*lambda^2*omega^2/(4*pi*c)), D*L in ps/nm."""
+    dl = cd_ps_per_nm * 1e-3                     # ps/nm -> s/m
+    w = 2 * np.pi * f
+    return np.exp(1j * dl * wavelength ** 2 * w ** 2 / (4 * np.pi * C_LIGHT))
+
+
+def haar_unitary(rng: np.random.Generator) -> np.ndarray:
+    z = (rng.standard_normal((2, 2)) + 1j * rng.standard_normal((2, 2))) / np.sqrt(2)
+    q, r = np.linalg.qr(z)
+    d = np.diag(r)
+    return q * (d / np.abs(d))
+
+
+@dataclass
+class Stream:
+    rx: np.ndarray        # [2, sps*N] complex64, pol-major
+    bits: np.ndarray      # [N, m] uint8
+    sym: np.ndarray       # [2, N] complex128 transmitted symbols
+    J: np.ndarray         # [2, 2] polarisation rotation
+    phase: np.ndarray     # [sps*N] float64 laser phase per sample
+    n0: float
+    fmt: TxFormat
+
+
+def make_stream(fmt: TxFormat | str, n_sym: int, *, seed: int, esn0_db: float,
+                cd_ps_per_nm: float, linewidth_ts: float, sps: int = 2,
+                rolloff: float = 0.1, symbol_rate: float = 28e9,
+                wavelength: float = LAMBDA_1550, rotation: bool = True,
+                noise: bool = True, pad_samples: int = 4096,
+                phase0: float | None = None) -> Stream:
+    """Generate one seeded stream of ``n_sym`` 4D symbols."""
+    if isinstance(fmt, str):
+        fmt = tx_format(fmt)
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m = fmt.bits_per_4d
+    bits = rng.integers(0, 2, size=(n_sym, m), dtype=np.uint8)
+    sym = bits_to_symbols(fmt, bits)
+    J = haar_unitary(rng) if rotation else np.eye(2, dtype=np.complex128)
+
+    ns = sps * n_sym
+    nfft = sfft.next_fast_len(ns + pad_samples)
+    u = np.zeros((2, nfft), dtype=np.complex128)
+    u[:, 0:ns:sps] = sym
+    f = sfft.fftfreq(nfft, d=1.0 / (sps * symbol_rate))
+    g = np.sqrt(sps * raised_cosine_shape(f, symbol_rate, rolloff))
+    h = g * cd_channel_response(f, cd_ps_per_nm, wavelength)
+    tx = sfft.ifft(sfft.fft(u, axis=1) * h, axis=1)[:, :ns]
+    sig = J @ tx
+
+    inc = rng.standard_normal(ns) * np.sqrt(2 * np.pi * linewidth_ts / sps)
+    th0 = rng.uniform(-np.pi, np.pi) if phase0 is None else phase0
+    phase = th0 + np.cumsum(inc) - inc[0]
+    sig = sig * np.exp(1j * phase)[None, :]
+
+    n0 = 10.0 ** (-esn0_db / 10.0)
+    if noise:
+        w = rng.standard_normal((2, 2, ns))
+        sig = sig + np.sqrt(n0 / 2) * (w[0] + 1j * w[1])
+    return Stream(sig.astype(np.complex64), bits, sym, J, phase, n0, fmt)
+
+
+def make_batch(fmt: TxFormat | str, n_sym: int, seeds, esn0_dbs, **kw):
+    """Several independent streams of equal length; returns (rx [S,2,sps*N]
+    complex64, list of Stream)."""
+    streams = [make_stream(fmt, n_sym, seed=s, esn0_db=e, **kw)
+               for s, e in zip(seeds, esn0_dbs)]
+    return np.stack([s.rx for s in streams]), streams

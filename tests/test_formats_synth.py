@@ -1,0 +1,101 @@
+"""Pins of the constellation tables, the GS table and the input generator."""
+import hashlib
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import chain, oracle_format
+from paper_2108_07004_gb300 import gs_design, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.mark.parametrize("name", ["dp_qpsk", "dp_16qam"])
+def test_gray_property_and_unit_energy(name):
+    fmt = oracle_format(name)
+    pts = fmt.points
+    assert abs(np.mean(np.abs(pts) ** 2) - 1) < 1e-12
+    dmin = min(abs(a - b) for i, a in enumerate(pts) for b in pts[i + 1:])
+    for i in range(fmt.M):
+        for j in range(fmt.M):
+            if i != j and abs(abs(pts[i] - pts[j]) - dmin) < 1e-9:
+                assert bin(i ^ j).count("1") == 1      # nearest neighbours differ in 1 bit
+
+
+@pytest.mark.parametrize("name", ["dp_qpsk", "dp_16qam", "gs4d64"])
+def test_oracle_and_generator_tables_agree(name):
+    """Two independent constructions of each table (transmitter mapping and
+    oracle) give the same points for every label."""
+    fo = oracle_format(name)
+    ft = synth.tx_format(name)
+    assert np.max(np.abs(fo.points - ft.points)) < 1e-7
+    rng = np.random.default_rng(0)
+    bits = rng.integers(0, 2, size=(100, fo.m), dtype=np.uint8)
+    assert np.max(np.abs(fo.symbols_from_bits(bits) - synth.bits_to_symbols(ft, bits))) < 1e-7
+
+
+def test_gs_table_invariants():
+    path = os.path.join(ROOT, "paper_2108_07004_gb300", "data", "gs4d64_v1.json")
+    d = json.load(open(path))
+    assert d["sha256"] == hashlib.sha256(json.dumps(d["points"]).encode()).hexdigest()
+    assert sorted(d["labels"]) == list(range(64))
+    fmt = oracle_format("gs4d64")
+    pts = fmt.points
+    # unit energy per polarisation (float32 rounding)
+    assert np.max(np.abs(np.mean(np.abs(pts) ** 2, axis=0) - 1)) < 1e-6
+    # exact joint 90-degree symmetry: rotating label (g(k)<<4)|o gives (g(k+1)<<4)|o
+    gray = [0, 1, 3, 2]
+    for lab in range(64):
+        k = gray.index(lab >> 4)
+        nxt = (gray[(k + 1) % 4] << 4) | (lab & 15)
+        rot = 1j * pts[lab]
+        assert np.array_equal(rot.real, pts[nxt].real) and np.array_equal(rot.imag, pts[nxt].imag)
+    # all points distinct
+    dd = np.sum(np.abs(pts[:, None, :] - pts[None, :, :]) ** 2, axis=-1) + np.eye(64)
+    assert dd.min() > 0.05
+
+
+def test_gs_table_beats_its_conventional_start_in_oracle_gmi():
+    """The designed table's AWGN GMI at the design point (14 dB), computed by
+    the oracle's own LLR/GMI code on fresh noise, exceeds the star-8QAM
+    product it started from."""
+    fmt = oracle_format("gs4d64")
+    start = gs_design.expand(gs_design.normalise(gs_design.initial_orbits()), np.arange(16))
+    n0 = 10 ** (-14 / 10)
+    rng = np.random.default_rng(99)
+    n = 1 << 15
+    bits = rng.integers(0, 2, size=(n, 6), dtype=np.uint8)
+    w = np.sqrt(n0 / 2) * (rng.standard_normal((2, n)) + 1j * rng.standard_normal((2, n)))
+    g = []
+    for pts in (start, fmt.points):
+        f = oracle_format("gs4d64")
+        f.points = pts
+        z = f.symbols_from_bits(bits) + w
+        g.append(chain.count(chain.llr(z, n0, f), bits.astype(float))["gmi"])
+    assert g[1] > g[0]
+
+
+def test_generator_esn0_at_matched_filter_output():
+    """Matched-filter output at the symbol instants has SNR Es/N0 (CD and
+    rotation off)."""
+    n = 1 << 16
+    st = synth.make_stream("dp_16qam", n, seed=3, esn0_db=10.0, cd_ps_per_nm=0.0,
+                           linewidth_ts=0.0, rotation=False, phase0=0.0)
+    p = chain.RxParams(n_fft=1024, n_ov=256)
+    x = chain.cdc(st.rx.astype(np.complex128), p)[:, 0::2]
+    e = x[:, 1000:-1000] - st.sym[:, 1000:-1000]
+    snr_db = 10 * np.log10(1 / np.mean(np.abs(e) ** 2))
+    assert abs(snr_db - 10.0) < 0.05
+
+
+def test_generator_phase_noise_and_rotation():
+    st = synth.make_stream("dp_qpsk", 1 << 16, seed=4, esn0_db=12, cd_ps_per_nm=100.0,
+                           linewidth_ts=1e-4)
+    inc = np.diff(st.phase)
+    assert abs(np.var(inc) / (2 * np.pi * 1e-4 / 2) - 1) < 0.02
+    assert np.max(np.abs(st.J @ st.J.conj().T - np.eye(2))) < 1e-12
+    st3 = synth.make_stream("dp_qpsk", 1 << 16, seed=4, esn0_db=12, cd_ps_per_nm=100.0,
+                            linewidth_ts=1e-4)
+    assert np.array_equal(st3.rx, st.rx)                                     # reproducible
