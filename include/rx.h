@@ -1,0 +1,209 @@
+/*
+ * rx.h -- C ABI of the GB300 coherent-receiver DSP library.
+ *
+ * The library runs the receiver chain of arXiv 2108.07004 (Sec. 2) in the
+ * dual-polarisation form: overlap-save chromatic-dispersion compensation
+ * (CDC) -> 2x2 butterfly FIR equaliser adapted block-wise (CMA, then
+ * decision-directed LMS) -> blind phase search (BPS) -> exact log-sum-exp
+ * bit LLRs with BER / GMI counting.  Every step runs in the library's own
+ * CUDA kernels on the calling process's current device.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: RX_OK (0) or a negative RX_E* code; the message of the
+ *     last failure on the calling thread is returned by rx_last_error().
+ *   - Complex samples are interleaved float32 (re, im) ("c64").  A stream's
+ *     samples are polarisation-major: [2][n_samples] (X then Y).  A handle
+ *     processes S independent streams of equal length at once ("streams"
+ *     parameter, default 1); buffers then carry a leading [S] dimension.
+ *   - Pointers documented as "device" must be CUDA device (or managed)
+ *     memory; "host" pointers are ordinary host memory.  The caller owns
+ *     every buffer it passes; the library owns the handle, its tables, its
+ *     per-stream state and its scratch memory (allocated with cudaMalloc on
+ *     first use and freed by rx_destroy).
+ *   - Work is enqueued on the handle's CUDA stream (rx_set_stream; the
+ *     default is the legacy default stream).  Calls returning statistics
+ *     synchronise that stream.
+ *   - LLR sign: positive means bit 0.  Bit order of a label: MSB first.
+ *   - A handle is not thread-safe: use one handle per host thread.
+ */
+#ifndef RX_H
+#define RX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RX_OK         0
+#define RX_EINVAL    (-1)   /* bad argument or unsupported configuration   */
+#define RX_ENOMEM    (-2)   /* device or host allocation failed            */
+#define RX_ECUDA     (-3)   /* a CUDA runtime call failed                  */
+#define RX_ETIMEDOUT (-4)   /* a bounded device wait gave up               */
+#define RX_EBUSY     (-5)   /* handle in use / parameter locked            */
+#define RX_ESTATE    (-6)   /* call out of order (e.g. no reference set)   */
+
+/* built-in formats (Gray-mapped square QAM on each polarisation) */
+#define RX_FMT_CUSTOM   0
+#define RX_FMT_DP_QPSK  1
+#define RX_FMT_DP_16QAM 2
+
+typedef struct rx_handle rx_handle;
+
+/* Constellation description.  Sec. 2 of the paper uploads the points and
+ * their bit mapping to the GPU and assumes no symmetry of the format; the
+ * phase search here uses the rotational symmetry sym_order (1, 2 or 4) and
+ * the library verifies it exactly at creation.
+ *   kind      RX_FMT_*; for built-ins the other fields are ignored.
+ *   dims      2: one 2D table used on each polarisation (m_bits per pol);
+ *             4: one joint 4D table over both polarisations.
+ *   m_bits    bits per table entry (table size 2^m_bits; dims 2: 2 or 4,
+ *             dims 4: 6).
+ *   points    host, [2^m_bits][dims] float32 (re, im [, re_y, im_y]),
+ *             copied at creation.
+ *   labels    host, [2^m_bits] bit label of each row, a permutation of
+ *             0 .. 2^m_bits - 1. */
+typedef struct {
+    int kind;
+    int dims;
+    int m_bits;
+    int sym_order;
+    const float *points;
+    const uint32_t *labels;
+} rx_format;
+
+/* Per-stream statistics (host struct, filled by rx_process / rx_get_stats).
+ * Counting covers symbols skip_head .. N - skip_tail - 1 of the stream and
+ * needs a reference (rx_set_reference); Sec. 3 counts errors offline over
+ * many buffers. */
+typedef struct {
+    uint64_t n_sym;        /* symbols counted                                  */
+    uint64_t n_bits;       /* bits counted (n_sym * m)                         */
+    uint64_t bit_errors;   /* hard decisions (LLR < 0 -> 1) != reference bits  */
+    double   gmi_sum;      /* sum of log2(1 + exp(-(1 - 2b) LLR)) over bits    */
+    double   gmi;          /* m - gmi_sum / n_sym  (bits per 4D symbol)        */
+    double   ber;          /* bit_errors / n_bits                              */
+    double   evm_num;      /* sum |z - d|^2 (d: nearest point)                 */
+    double   evm_den;      /* sum |d|^2                                        */
+    double   sigma2_last;  /* noise variance used for the last block           */
+    uint64_t n_out;        /* LLR rows written for this stream                 */
+    uint32_t blocks;       /* blocks processed                                 */
+    uint32_t reserved;
+} rx_stats;
+
+/* ---- lifetime ---------------------------------------------------------- */
+
+/* Create a receiver for one format and link.  symbol_rate in Bd, sps must
+ * be 2, cd_ps_per_nm is the accumulated dispersion D*L to undo, taps the
+ * odd FIR length per butterfly branch (7, 15 or 31), bps_phases the number
+ * of BPS test phases B (8 .. 64).  Returns NULL on error (rx_last_error()). */
+rx_handle *rx_create(const rx_format *format, double symbol_rate, int sps,
+                     double cd_ps_per_nm, int taps, int bps_phases);
+void rx_destroy(rx_handle *h);                      /* NULL-safe */
+
+/* Set / read a numeric parameter.  Keys (defaults in brackets):
+ *   "fft" [1024] (1024 or 4096), "overlap" [256] (even, < fft/2),
+ *   "mu" [1e-3], "bps_window" [64] (even, 2..64), "block" [4096] symbols,
+ *   "n_upd" [1024] (<= block - bps_window/2), "lag" [1] (1..4),
+ *   "n_pre" [8192], "cma_passes" [2], "n_cma" [1024], "n_train" [1024],
+ *   "sigma2" [0 = estimate per block], "skip_head" [4096],
+ *   "skip_tail" [512], "streams" [1], "rolloff" [0.1],
+ *   "wavelength_nm" [1550].
+ * Changing a parameter resets the stream state (rx_reset). */
+int rx_set_param(rx_handle *h, const char *key, double value);
+int rx_get_param(const rx_handle *h, const char *key, double *value);
+
+/* Use cuda_stream (a cudaStream_t) for all later work of this handle. */
+int rx_set_stream(rx_handle *h, void *cuda_stream);
+
+/* Known transmitted bits, device, [S][n_sym][m] uint8 (0/1), m bits per 4D
+ * symbol (dims 2: X bits then Y bits).  Enables the start-up training
+ * alignment (Sec. 2: the equaliser first converges on a training sequence)
+ * over the first n_train symbols and BER/GMI counting.  Copied. */
+int rx_set_reference(rx_handle *h, const uint8_t *bits, size_t n_sym);
+
+/* Forget the stream state (taps, phase, counters): the next rx_process
+ * starts a new stream. */
+int rx_reset(rx_handle *h);
+
+/* ---- the chain ---------------------------------------------------------- */
+
+/* Run the whole chain over S complete streams.
+ *   samples   device, [S][2][n_samples] c64, n_samples = 2 * N.
+ *   llr_out   device, [S][N][m] float32, caller-allocated.
+ *   stats     host, [S] rx_stats or NULL; when non-NULL the call waits for
+ *             the device and fills it.
+ * Block schedule (Sec. 2: part of one buffer updates the equaliser taps used
+ * for later buffers): start-up CMA and training alignment, then for every
+ * block of "block" symbols: FIR with the taps from "lag" blocks back, BPS,
+ * unwrap, LLRs, then LMS over the block's first n_upd symbols. */
+int rx_process(rx_handle *h, const void *samples, size_t n_samples,
+               float *llr_out, rx_stats *stats);
+
+/* rx_process with host buffers: copies samples (host, [S][2][n_samples]
+ * c64) in and LLRs (host, [S][N][m]) out through pinned staging buffers,
+ * overlapping the copies with the chain. */
+int rx_process_host(rx_handle *h, const void *samples, size_t n_samples,
+                    float *llr_out, rx_stats *stats);
+
+/* Statistics of the last rx_process (host [S]); synchronises. */
+int rx_get_stats(rx_handle *h, rx_stats *stats);
+
+/* Serialise / restore the per-stream state (taps ring, LMS count, unwrap
+ * carry, block index).  *len in: capacity, out: bytes used (pass buf NULL
+ * to query). */
+int rx_get_state(rx_handle *h, void *buf, size_t *len);
+int rx_set_state(rx_handle *h, const void *buf, size_t len);
+
+/* Format facts: dims, m (bits per 4D symbol), M (table size). */
+int rx_format_info(const rx_handle *h, int *dims, int *m, int *M);
+
+const char *rx_last_error(void);
+
+/* ---- single stages (the steps rx_process chains; for tests and custom
+ *      pipelines).  All arrays are device memory with a leading [S]. ----- */
+
+/* A1 CDC: overlap-save FFT filtering with conj(H_CD) * H_MF, global
+ * framing from sample 0.  in, out: [S][2][n_samples] c64 (out != in). */
+int rx_cdc(rx_handle *h, const void *in, void *out, size_t n_samples);
+
+/* A2 FIR: y_q[k] = sum_p sum_t conj(h_qp[t]) x_p[2k + D - t], D = (T-1)/2,
+ * for k0 <= k < k1.  x: [S][2][n_samples], taps: [S][2][2][T] c64
+ * (index [q][p][t]), y: [S][2][k1 - k0]. */
+int rx_fir(rx_handle *h, const void *x, size_t n_samples, const void *taps,
+           size_t k0, size_t k1, void *y);
+
+/* A3 LMS: sequential updates over symbols k0 .. k0 + n_upd - 1 of x,
+ * in place on taps [S][2][2][T].  mode 0: CMA; 1: DD-LMS using the phase
+ * codes pcode [S][N] (uint16: b | (m mod 4) << 8, see rx_bps_unwrap);
+ * 2: CMA for updates u0 + i < n_cma, DD after.  passes > 1 repeats the
+ * span (start-up). */
+int rx_lms(rx_handle *h, const void *x, size_t n_samples, void *taps,
+           size_t k0, size_t n_upd, const uint16_t *pcode, int mode,
+           int passes, uint64_t u0);
+
+/* A4 BPS: test-phase index b_k for a <= k < e from y [S][2][n_y] (symbols
+ * 0 .. n_y - 1 of the stream), windows truncated at n_valid.  b_out:
+ * [S][e - a] uint8. */
+int rx_bps(rx_handle *h, const void *y, size_t n_y, size_t a, size_t e,
+           size_t n_valid, uint8_t *b_out);
+
+/* A4 unwrap + de-rotation: from b [S][e - a] and the carry (m_prev, b_prev)
+ * carry_in [S][2] int32, compute the integer unwrap m_k, z_k = y_k *
+ * exp(-j phi_k) into z [S][2][e - a], phase codes into pcode [S][e - a],
+ * the carry after the range into carry_out [S][2] and the decision-directed
+ * noise variance of the range into sigma2 [S] (float64). */
+int rx_unwrap(rx_handle *h, const void *y, size_t n_y, const uint8_t *b,
+              size_t a, size_t e, const int32_t *carry_in, void *z,
+              uint16_t *pcode, int32_t *carry_out, double *sigma2);
+
+/* A5 LLRs: llr [S][K][m] from z [S][2][K] with noise variance sigma2 [S]
+ * (float64, device). */
+int rx_demap(rx_handle *h, const void *z, size_t K, const double *sigma2,
+             float *llr);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RX_H */

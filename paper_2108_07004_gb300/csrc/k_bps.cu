@@ -1,0 +1,418 @@
+// A4: blind phase search and its unwrap / de-rotation.
+//
+// BPS (per symbol k, test phases phi_b = (b/B - 1/2) 2 pi / S):
+//   md_b(i)  = min_j || y_i exp(-j phi_b) - s_j ||^2
+//   cost_b(k) = sum_{i = k - W/2}^{k + W/2 - 1} md_b(i)   (i outside [0, n_valid) adds 0)
+//   b_k      = argmin_b cost_b(k)   (lowest b on ties)
+// With the table closed under rotation by 2 pi / S, the minimum over the S
+// members of an orbit {rep * j^k} follows from one correlation
+// c = sum_p y_p conj(rep_p):  || y e^{-j phi} - rep j^k ||^2 =
+// |y|^2 + |rep|^2 - 2 Re(e^{-j phi} (-j)^k c), so for S = 4 the orbit minimum
+// is |y|^2 + |rep|^2 - 2 max(|P|, |Q|) with P + jQ = e^{-j phi} c.  The
+// 4D 64-ary table has 16 orbits: 16 correlations per symbol, then per test
+// phase 16 x (2 MUL + 2 FMA + max + FMA + min).
+//
+// Window sums: a warp computes md_b for 32 consecutive symbols (one per
+// lane), scans them with shuffles and stores the exclusive prefix of every
+// 32-symbol chunk and its total in a shared-memory ring of 10 chunks; a
+// window of W <= 64 symbols then spans at most three chunks and costs three
+// shared loads per test phase.  A block makes 960 outputs in 4 rounds of 8
+// chunks, computing one extra chunk on each side (6.7 % halo).
+//
+// Unwrap (integer form of phi_hat_k = phi_k + q round((phi_hat_{k-1} -
+// phi_k)/q), q = 2 pi/S, round(x) = floor(x + 1/2)):
+//   m_k = m_{k-1} + floor((2 (b_{k-1} - b_k) + B) / (2B)),
+// a prefix sum: the BPS kernel sums the increments inside its range, the
+// unwrap kernel adds the block boundaries and scans its own range.
+#include "rx_internal.h"
+
+namespace {
+
+constexpr int kRounds = 4;
+constexpr int kChunks = 8 * kRounds - 2;   // output chunks per block
+constexpr int kR = 32 * kChunks;           // output symbols per block (960)
+
+__device__ __forceinline__ int unwrap_step(int bprev, int b, int B) {
+    const int num = 2 * (bprev - b) + B;   // in [2 - B, 3B - 2]
+    return num < 0 ? -1 : (num >= 2 * B ? 1 : 0);
+}
+
+__device__ __forceinline__ float orbit_v(float P, float Q, int S) {
+    if (S == 4) return fmaxf(fabsf(P), fabsf(Q));
+    if (S == 2) return fabsf(P);
+    return P;
+}
+
+template <int DIMS, int NORB>
+__global__ void __launch_bounds__(256, 2)
+bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_valid, int W,
+           uint8_t *__restrict__ bout, long bout_stride, int *__restrict__ dsum, int n_cta,
+           const __grid_constant__ FmtDev f) {
+    extern __shared__ float smem[];
+    const int B = f.B;
+    float *Eb = smem;                                     // [10][B][32] exclusive prefixes
+    float *Tb = smem + RX_NCHUNK * B * 32;                // [10][B] chunk totals
+    uint8_t *bsm = reinterpret_cast<uint8_t *>(Tb + RX_NCHUNK * B);   // [kR]
+    __shared__ int red[8];
+    const int s = blockIdx.y, c = blockIdx.x;
+    const long out0 = a + (long)c * kR;
+    const long out1 = min(out0 + kR, e);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const float2 *yx = y + (long)s * 2 * y_stride;
+    const float2 *yy = yx + y_stride;
+    const int hw = W >> 1;
+    const int S = f.S;
+
+    for (int r = 0; r < kRounds; ++r) {
+        // ---- min distances of chunk jc for every test phase, scanned ----
+        const int jc = 8 * r - 1 + warp;
+        const long i = out0 + 32L * jc + lane;
+        const bool valid = (i >= 0) && (i < n_valid);
+        float2 ya = make_float2(0.f, 0.f), yb = make_float2(0.f, 0.f);
+        if (valid) { ya = yx[i]; yb = yy[i]; }
+        float cr[2][NORB], ci[2][NORB];
+        float yn0, yn1;
+        if (DIMS == 4) {
+            yn0 = cnorm(ya) + cnorm(yb);
+            yn1 = 0.f;
+#pragma unroll
+            for (int o = 0; o < NORB; ++o) {
+                if (o < f.n_orb) {
+                    const float r0 = f.orb[o][0], r1 = f.orb[o][1], r2 = f.orb[o][2], r3 = f.orb[o][3];
+                    cr[0][o] = ya.x * r0 + ya.y * r1 + yb.x * r2 + yb.y * r3;
+                    ci[0][o] = ya.y * r0 - ya.x * r1 + yb.y * r2 - yb.x * r3;
+                }
+            }
+        } else {
+            yn0 = cnorm(ya);
+            yn1 = cnorm(yb);
+#pragma unroll
+            for (int o = 0; o < NORB; ++o) {
+                if (o < f.n_orb) {
+                    const float r0 = f.orb[o][0], r1 = f.orb[o][1];
+                    cr[0][o] = ya.x * r0 + ya.y * r1;
+                    ci[0][o] = ya.y * r0 - ya.x * r1;
+                    cr[1][o] = yb.x * r0 + yb.y * r1;
+                    ci[1][o] = yb.y * r0 - yb.x * r1;
+                }
+            }
+        }
+        const int slot = (jc + 1) % RX_NCHUNK;
+        for (int b = 0; b < B; ++b) {
+            const float cb = f.cs[b][0], sb = f.cs[b][1];
+            float md;
+            if (DIMS == 4) {
+                float best = 3.0e38f;
+#pragma unroll
+                for (int o = 0; o < NORB; ++o) {
+                    if (o < f.n_orb) {
+                        const float P = cb * cr[0][o] + sb * ci[0][o];
+                        const float Q = cb * ci[0][o] - sb * cr[0][o];
+                        best = fminf(best, fmaf(-2.f, orbit_v(P, Q, S), f.orbe[o]));
+                    }
+                }
+                md = yn0 + best;
+            } else {
+                float b0 = 3.0e38f, b1 = 3.0e38f;
+#pragma unroll
+                for (int o = 0; o < NORB; ++o) {
+                    if (o < f.n_orb) {
+                        const float P0 = cb * cr[0][o] + sb * ci[0][o];
+                        const float Q0 = cb * ci[0][o] - sb * cr[0][o];
+                        const float P1 = cb * cr[1][o] + sb * ci[1][o];
+                        const float Q1 = cb * ci[1][o] - sb * cr[1][o];
+                        b0 = fminf(b0, fmaf(-2.f, orbit_v(P0, Q0, S), f.orbe[o]));
+                        b1 = fminf(b1, fmaf(-2.f, orbit_v(P1, Q1, S), f.orbe[o]));
+                    }
+                }
+                md = (yn0 + b0) + (yn1 + b1);
+            }
+            if (!valid) md = 0.f;
+            float incl = md;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const float t = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += t;
+            }
+            float excl = __shfl_up_sync(0xffffffffu, incl, 1);
+            if (lane == 0) excl = 0.f;
+            Eb[(slot * B + b) * 32 + lane] = excl;
+            if (lane == 31) Tb[slot * B + b] = incl;
+        }
+        __syncthreads();
+        // ---- window costs and argmin for output chunk oc ----
+        const int oc = 8 * r - 2 + warp;
+        if (oc >= 0 && oc < kChunks) {
+            const long k = out0 + 32L * oc + lane;
+            if (k < out1) {
+                const int i0 = 32 * oc + lane - hw, i1 = 32 * oc + lane + hw;
+                const int c0 = (i0 >= 0) ? (i0 >> 5) : -1;   // i0 >= -32
+                const int l0 = i0 - 32 * c0;
+                const int c1 = i1 >> 5, l1 = i1 - 32 * c1;
+                const int s0 = (c0 + 1) % RX_NCHUNK, s1 = (c1 + 1) % RX_NCHUNK;
+                const int sm = (c0 + 2) % RX_NCHUNK;
+                float best = 3.0e38f;
+                int bb = 0;
+                for (int b = 0; b < B; ++b) {
+                    float cst;
+                    if (c0 == c1) {
+                        cst = Eb[(s0 * B + b) * 32 + l1] - Eb[(s0 * B + b) * 32 + l0];
+                    } else {
+                        cst = Tb[s0 * B + b] - Eb[(s0 * B + b) * 32 + l0];
+                        if (c1 - c0 == 2) cst += Tb[sm * B + b];
+                        cst += Eb[(s1 * B + b) * 32 + l1];
+                    }
+                    if (cst < best) { best = cst; bb = b; }
+                }
+                bsm[k - out0] = (uint8_t)bb;
+                bout[(long)s * bout_stride + (k - a)] = (uint8_t)bb;
+            }
+        }
+        __syncthreads();
+    }
+    // ---- unwrap increments inside this block's range (boundary excluded) ----
+    int acc = 0;
+    const int nloc = (int)(out1 - out0);
+    for (int t = tid + 1; t < nloc; t += 256) acc += unwrap_step(bsm[t - 1], bsm[t], B);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        int tot = 0;
+        for (int w = 0; w < 8; ++w) tot += red[w];
+        dsum[s * n_cta + c] = tot;
+    }
+}
+
+// nearest-point squared distance of z (orbit form)
+template <int DIMS, int NORB>
+__device__ __forceinline__ float nearest_dist(float2 z0, float2 z1, const FmtDev &f) {
+    if (DIMS == 4) {
+        const float zn = cnorm(z0) + cnorm(z1);
+        float best = 3.0e38f;
+#pragma unroll
+        for (int o = 0; o < NORB; ++o) {
+            if (o < f.n_orb) {
+                const float P = z0.x * f.orb[o][0] + z0.y * f.orb[o][1] + z1.x * f.orb[o][2] + z1.y * f.orb[o][3];
+                const float Q = z0.y * f.orb[o][0] - z0.x * f.orb[o][1] + z1.y * f.orb[o][2] - z1.x * f.orb[o][3];
+                best = fminf(best, f.orbe[o] - 2.f * orbit_v(P, Q, f.S));
+            }
+        }
+        return fmaxf(zn + best, 0.f);
+    } else {
+        float tot = 0.f;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const float2 zp = p ? z1 : z0;
+            float best = 3.0e38f;
+#pragma unroll
+            for (int o = 0; o < NORB; ++o) {
+                if (o < f.n_orb) {
+                    const float P = zp.x * f.orb[o][0] + zp.y * f.orb[o][1];
+                    const float Q = zp.y * f.orb[o][0] - zp.x * f.orb[o][1];
+                    best = fminf(best, f.orbe[o] - 2.f * orbit_v(P, Q, f.S));
+                }
+            }
+            tot += fmaxf(cnorm(zp) + best, 0.f);
+        }
+        return tot;
+    }
+}
+
+template <int DIMS, int NORB>
+__global__ void __launch_bounds__(256)
+unwrap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *__restrict__ bsrc,
+              long b_stride, long a, long e, const int *__restrict__ dsum, int n_cta,
+              const int32_t *__restrict__ carry_in, int cin_stride, int32_t *__restrict__ carry_out,
+              int cout_stride, float2 *__restrict__ z, long z_stride, uint16_t *__restrict__ pcode,
+              long pc_stride, double *__restrict__ partial, double *__restrict__ sigma2_out,
+              int s2_stride, unsigned int *__restrict__ ticket, int ticket_stride,
+              const __grid_constant__ FmtDev f) {
+    __shared__ int bl[kR];
+    __shared__ int wsum[8];
+    __shared__ int mstart_sh;
+    __shared__ double dred[8];
+    __shared__ bool last;
+    const int s = blockIdx.y, c = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long out0 = a + (long)c * kR;
+    const long out1 = min(out0 + kR, e);
+    const int nloc = (int)(out1 - out0);
+    const int B = f.B, S = f.S;
+    const uint8_t *bs = bsrc + (long)s * b_stride;   // index k - a
+    const int m_in = carry_in[s * cin_stride + 0], b_in = carry_in[s * cin_stride + 1];
+
+    // m at the start of this range: carry + increments of all earlier ranges
+    if (warp == 0) {
+        int acc = 0;
+        for (int cc = lane; cc < c; cc += 32) {
+            const long st0 = a + (long)cc * kR;
+            const int bp = (cc == 0) ? b_in : bs[st0 - 1 - a];
+            acc += unwrap_step(bp, bs[st0 - a], B) + dsum[s * n_cta + cc];
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        if (lane == 0) mstart_sh = m_in + acc;
+    }
+    for (int t = tid; t < nloc; t += 256) bl[t] = bs[out0 - a + t];
+    __syncthreads();
+    const int bprev0 = (c == 0) ? b_in : (int)bs[out0 - 1 - a];
+
+    // block scan of the increments: thread t owns local symbols 4t .. 4t+3
+    int d[4], run = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int t = 4 * tid + u;
+        int inc = 0;
+        if (t < nloc) inc = unwrap_step(t == 0 ? bprev0 : bl[t - 1], bl[t], B);
+        run += inc;
+        d[u] = run;
+    }
+    int incl = run;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += wsum[w];
+    const int tpre = mstart_sh + wpre + incl - run;   // m before this thread's symbols
+
+    const float2 *yx = y + (long)s * 2 * y_stride;
+    const float2 *yy = yx + y_stride;
+    float2 *zx = z + (long)s * 2 * z_stride;
+    float2 *zy = zx + z_stride;
+    double dsum_loc = 0.0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int t = 4 * tid + u;
+        if (t >= nloc) continue;
+        const long k = out0 + t;
+        const int m = tpre + d[u];
+        const int b = bl[t];
+        const int mq = ((m % S) + S) % S;
+        // exp(-j phi) = conj(cs_b) * exp(-j mq 2 pi / S)
+        float2 rot = make_float2(f.cs[b][0], -f.cs[b][1]);
+        if (S == 4) {
+            for (int i = 0; i < mq; ++i) rot = make_float2(rot.y, -rot.x);   // * (-j)
+        } else if (S == 2) {
+            if (mq) rot = make_float2(-rot.x, -rot.y);
+        }
+        const float2 z0 = cmul(yx[k], rot), z1 = cmul(yy[k], rot);
+        zx[k - a] = z0;
+        zy[k - a] = z1;
+        pcode[(long)s * pc_stride + (k - a)] = (uint16_t)(b | (mq << 8));
+        dsum_loc += (double)nearest_dist<DIMS, NORB>(z0, z1, f);
+        if (k == e - 1) {
+            carry_out[s * cout_stride + 0] = m;
+            carry_out[s * cout_stride + 1] = b;
+        }
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dsum_loc += __shfl_xor_sync(0xffffffffu, dsum_loc, off);
+    if (lane == 0) dred[warp] = dsum_loc;
+    __syncthreads();
+    if (tid == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < 8; ++w) tot += dred[w];
+        partial[(long)s * n_cta + c] = tot;
+        __threadfence();
+        const unsigned prev = atomicAdd(&ticket[s * ticket_stride], 1u);
+        last = (prev == (unsigned)n_cta - 1);
+    }
+    __syncthreads();
+    if (last && tid == 0) {
+        __threadfence();
+        double tot = 0.0;
+        for (int cc = 0; cc < n_cta; ++cc) tot += ((volatile double *)partial)[(long)s * n_cta + cc];
+        sigma2_out[s * s2_stride] = tot / (2.0 * (double)(e - a));
+        ticket[s * ticket_stride] = 0u;
+    }
+}
+
+// interior unwrap increments of each kR range, from phase indices b (index k - a)
+__global__ void dsum_kernel(const uint8_t *__restrict__ b, long b_stride, long a, long e,
+                            int *__restrict__ dsum, int n_cta, int B) {
+    __shared__ int red[8];
+    const int s = blockIdx.y, c = blockIdx.x, tid = threadIdx.x;
+    const long out0 = a + (long)c * kR, out1 = min(out0 + kR, e);
+    const uint8_t *bs = b + (long)s * b_stride;
+    int acc = 0;
+    for (long k = out0 + 1 + tid; k < out1; k += 256) acc += unwrap_step(bs[k - 1 - a], bs[k - a], B);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        int tot = 0;
+        for (int w = 0; w < 8; ++w) tot += red[w];
+        dsum[s * n_cta + c] = tot;
+    }
+}
+
+template <int DIMS, int NORB>
+cudaError_t bps_launch_t(const float2 *y, long ys, long a, long e, long nv, int W, uint8_t *bout,
+                         long bst, int *dsum, int n_streams, const FmtDev &f, cudaStream_t st) {
+    const int n_cta = (int)((e - a + kR - 1) / kR);
+    const size_t smem = sizeof(float) * (RX_NCHUNK * f.B * 32 + RX_NCHUNK * f.B) + kR + 16;
+    auto kern = bps_kernel<DIMS, NORB>;
+    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (err != cudaSuccess) return err;
+    dim3 grid((unsigned)n_cta, (unsigned)n_streams);
+    kern<<<grid, 256, smem, st>>>(y, ys, a, e, nv, W, bout, bst, dsum, n_cta, f);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+int bps_cta_range() { return kR; }
+
+cudaError_t launch_dsum_from_b(const uint8_t *b, long b_stride, long a, long e, int *dsum,
+                               int n_streams, int B, cudaStream_t st) {
+    if (e <= a || n_streams <= 0) return cudaSuccess;
+    const int n_cta = (int)((e - a + kR - 1) / kR);
+    dim3 grid((unsigned)n_cta, (unsigned)n_streams);
+    dsum_kernel<<<grid, 256, 0, st>>>(b, b_stride, a, e, dsum, n_cta, B);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bps(const float2 *y, long y_stride, long a, long e, long n_valid, int W,
+                       uint8_t *bout, long bout_stride, long bout_off, int *dsum, int n_streams,
+                       const FmtDev &f, cudaStream_t st) {
+    if (e <= a || n_streams <= 0) return cudaSuccess;
+    uint8_t *bo = bout + bout_off;
+    if (f.dims == 4) {
+        if (f.n_orb > 16) return cudaErrorInvalidValue;
+        return bps_launch_t<4, 16>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, n_streams, f, st);
+    }
+    if (f.n_orb > 4) return cudaErrorInvalidValue;
+    return bps_launch_t<2, 4>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, n_streams, f, st);
+}
+
+cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long b_stride,
+                          long b_off, long a, long e, const int *dsum,
+                          const int32_t *carry_in, int carry_in_stride,
+                          int32_t *carry_out, int carry_out_stride,
+                          float2 *z, long z_stride, long z_off,
+                          uint16_t *pcode, long pcode_stride, long pcode_off,
+                          double *partial, double *sigma2_out, int sigma2_stride,
+                          unsigned int *ticket, int ticket_stride,
+                          int n_streams, const FmtDev &f, cudaStream_t st) {
+    if (e <= a || n_streams <= 0) return cudaSuccess;
+    const int n_cta = (int)((e - a + kR - 1) / kR);
+    dim3 grid((unsigned)n_cta, (unsigned)n_streams);
+    if (f.dims == 4) {
+        unwrap_kernel<4, 16><<<grid, 256, 0, st>>>(y, y_stride, b + b_off, b_stride, a, e, dsum, n_cta,
+                                                    carry_in, carry_in_stride, carry_out, carry_out_stride,
+                                                    z + z_off, z_stride, pcode + pcode_off, pcode_stride,
+                                                    partial, sigma2_out, sigma2_stride, ticket, ticket_stride, f);
+    } else {
+        unwrap_kernel<2, 4><<<grid, 256, 0, st>>>(y, y_stride, b + b_off, b_stride, a, e, dsum, n_cta,
+                                                   carry_in, carry_in_stride, carry_out, carry_out_stride,
+                                                   z + z_off, z_stride, pcode + pcode_off, pcode_stride,
+                                                   partial, sigma2_out, sigma2_stride, ticket, ticket_stride, f);
+    }
+    return cudaGetLastError();
+}

@@ -1,0 +1,224 @@
+// A5: exact soft demapping to bit LLRs, A6: BER / GMI / EVM counting.
+//
+//   LLR_i = ln sum_{j: b_i(j)=0} exp(-||z - s_j||^2 / sigma^2)
+//         - ln sum_{j: b_i(j)=1} exp(-||z - s_j||^2 / sigma^2)
+//
+// One thread per symbol.  The table (label order) is read from the kernel's
+// parameter space: every thread walks it in the same order, so the reads
+// are uniform constant-bank loads.  All exponentials share one shift, the
+// minimum distance g, plus a constant 2^120 headroom:
+//   e_j = 2^{(g - d_j) log2(e) / sigma^2 + 120}
+// so the M terms are computed once; the per-bit subset sums are built as a
+// binary tree over the label bits (bit 0 splits even/odd labels, then pairs
+// are summed and bit 1 splits the pairs, ...), about 3M additions instead
+// of m*M.  A subset whose terms all lie beyond the float range below
+// 2^-100 is recomputed with its own minimum as shift (then |LLR| > 150).
+// Counting (Sec. 3 counts errors offline; here it is fused): hard bits are
+// LLR < 0, errors against the reference label, the GMI term
+// log2(1 + exp(-(1 - 2b) LLR)) per bit and the EVM sums; block partials are
+// reduced in a fixed order by the last block of the launch.
+#include "rx_internal.h"
+
+namespace {
+
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
+constexpr float kOff = 120.f;
+
+// log2 of the subset sum for label bit bp == v, falling back to an own-shift sum
+template <int MT>
+__device__ __forceinline__ float subset_lg(const float (&d)[MT], float g, float c2, float S,
+                                           int bp, int v) {
+    if (S >= 7.888609052e-31f)          // 2^-100
+        return __log2f(S) - kOff;
+    float dm = 3.0e38f;
+#pragma unroll
+    for (int j = 0; j < MT; ++j)
+        if (((j >> bp) & 1) == v) dm = fminf(dm, d[j]);
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < MT; ++j)
+        if (((j >> bp) & 1) == v) acc += exp2f((dm - d[j]) * c2);
+    return (g - dm) * c2 + log2f(acc);
+}
+
+// LLRs of one table lookup: d[j] squared distances in label order, mb bits.
+template <int MT, int MB>
+__device__ __forceinline__ void llr_table(const float (&d)[MT], float c2, float *out, float &g,
+                                          int &jmin) {
+    g = d[0];
+    jmin = 0;
+#pragma unroll
+    for (int j = 1; j < MT; ++j)
+        if (d[j] < g) { g = d[j]; jmin = j; }
+    float cur[MT];
+#pragma unroll
+    for (int j = 0; j < MT; ++j) cur[j] = exp2f(fmaf(g - d[j], c2, kOff));
+    int n = MT;
+#pragma unroll
+    for (int bp = 0; bp < MB; ++bp) {
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int i = 0; i < MT; i += 2) {
+            if (i < n) { s0 += cur[i]; s1 += cur[i + 1]; }
+        }
+        const float l0 = subset_lg<MT>(d, g, c2, s0, bp, 0);
+        const float l1 = subset_lg<MT>(d, g, c2, s1, bp, 1);
+        out[MB - 1 - bp] = (l0 - l1) * kLn2;
+#pragma unroll
+        for (int i = 0; i < MT / 2; ++i)
+            if (2 * i < n) cur[i] = cur[2 * i] + cur[2 * i + 1];
+        n >>= 1;
+    }
+}
+
+__device__ __forceinline__ float softplus_bits(float x) {   // log2(1 + exp(x))
+    return (fmaxf(x, 0.f) + log1pf(expf(-fabsf(x)))) * kLog2e;
+}
+
+template <int DIMS, int MT, int MB>
+__global__ void __launch_bounds__(256)
+demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
+             const double *__restrict__ sigma2, int s2_stride, float *__restrict__ llr,
+             long llr_stride, DemapCount cnt, const __grid_constant__ FmtDev f) {
+    constexpr int M_OUT = (DIMS == 4) ? MB : 2 * MB;
+    __shared__ double red[8][3];
+    __shared__ unsigned long long redn[8][2];
+    __shared__ bool last;
+    const int s = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long k = a + (long)blockIdx.x * blockDim.x + tid;
+    const double s2 = sigma2[s * s2_stride];
+    const float c2 = (float)(1.4426950408889634 / s2);
+    const float2 *zx = z + (long)s * 2 * z_stride;
+    const float2 *zy = zx + z_stride;
+    unsigned long long nerr = 0, ncnt = 0;
+    double gsum = 0.0, en = 0.0, ed = 0.0;
+    if (k < e) {
+        const float2 z0 = zx[k - a], z1 = zy[k - a];
+        float L[M_OUT];
+        float dist_min, dmin_energy;
+        if (DIMS == 4) {
+            float d[MT];
+#pragma unroll
+            for (int j = 0; j < MT; ++j) {
+                const float a0 = z0.x - f.pts[j][0], a1 = z0.y - f.pts[j][1];
+                const float a2 = z1.x - f.pts[j][2], a3 = z1.y - f.pts[j][3];
+                d[j] = fmaf(a0, a0, fmaf(a1, a1, fmaf(a2, a2, a3 * a3)));
+            }
+            float g;
+            int jm;
+            llr_table<MT, MB>(d, c2, L, g, jm);
+            dist_min = g;
+            dmin_energy = f.pe[jm];
+        } else {
+            dist_min = 0.f;
+            dmin_energy = 0.f;
+#pragma unroll
+            for (int p = 0; p < 2; ++p) {
+                const float2 zp = p ? z1 : z0;
+                float d[MT];
+#pragma unroll
+                for (int j = 0; j < MT; ++j) {
+                    const float a0 = zp.x - f.pts[j][0], a1 = zp.y - f.pts[j][1];
+                    d[j] = fmaf(a0, a0, a1 * a1);
+                }
+                float g;
+                int jm;
+                llr_table<MT, MB>(d, c2, L + p * MB, g, jm);
+                dist_min += g;
+                dmin_energy += f.pe[jm];
+            }
+        }
+        float *row = llr + (long)s * llr_stride + (k - a) * M_OUT;
+#pragma unroll
+        for (int i = 0; i < M_OUT; ++i) row[i] = L[i];
+        if (cnt.ref_lab && k >= cnt.c0 && k < cnt.c1) {
+            const int ref = cnt.ref_lab[(long)s * cnt.ref_stride + k];
+            int hard = 0;
+            float gs = 0.f;
+#pragma unroll
+            for (int i = 0; i < M_OUT; ++i) {
+                const int bit = (ref >> (M_OUT - 1 - i)) & 1;
+                hard = (hard << 1) | (L[i] < 0.f ? 1 : 0);
+                gs += softplus_bits(bit ? L[i] : -L[i]);
+            }
+            nerr = __popc(hard ^ ref);
+            ncnt = 1;
+            gsum = gs;
+            en = dist_min;
+            ed = dmin_energy;
+        }
+    }
+    if (!cnt.sd) return;
+    // block reduction, then the last block of the launch adds all partials in order
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        nerr += __shfl_xor_sync(0xffffffffu, nerr, off);
+        ncnt += __shfl_xor_sync(0xffffffffu, ncnt, off);
+        gsum += __shfl_xor_sync(0xffffffffu, gsum, off);
+        en += __shfl_xor_sync(0xffffffffu, en, off);
+        ed += __shfl_xor_sync(0xffffffffu, ed, off);
+    }
+    if (lane == 0) {
+        red[warp][0] = gsum; red[warp][1] = en; red[warp][2] = ed;
+        redn[warp][0] = nerr; redn[warp][1] = ncnt;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        double t0 = 0, t1 = 0, t2 = 0;
+        unsigned long long n0 = 0, n1 = 0;
+        for (int w = 0; w < 8; ++w) {
+            t0 += red[w][0]; t1 += red[w][1]; t2 += red[w][2];
+            n0 += redn[w][0]; n1 += redn[w][1];
+        }
+        double *pp = cnt.partial + ((long)s * gridDim.x + blockIdx.x) * 5;
+        pp[0] = t0; pp[1] = t1; pp[2] = t2;
+        pp[3] = (double)n0; pp[4] = (double)n1;
+        __threadfence();
+        const unsigned prev = atomicAdd(&cnt.sd[s].ticket_demap, 1u);
+        last = (prev == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (last && tid == 0) {
+        __threadfence();
+        const volatile double *pp = cnt.partial + (long)s * gridDim.x * 5;
+        double t0 = 0, t1 = 0, t2 = 0;
+        unsigned long long n0 = 0, n1 = 0;
+        for (unsigned c = 0; c < gridDim.x; ++c) {
+            t0 += pp[c * 5 + 0]; t1 += pp[c * 5 + 1]; t2 += pp[c * 5 + 2];
+            n0 += (unsigned long long)pp[c * 5 + 3]; n1 += (unsigned long long)pp[c * 5 + 4];
+        }
+        StreamDev &sd = cnt.sd[s];
+        sd.gmi_sum += t0;
+        sd.evm_num += t1;
+        sd.evm_den += t2;
+        sd.bit_errors += n0;
+        sd.n_sym += n1;
+        sd.sigma2 = s2;
+        sd.ticket_demap = 0u;
+    }
+}
+
+template <int DIMS, int MT, int MB>
+cudaError_t demap_t(const float2 *z, long zs, long a, long e, const double *s2, int s2s, float *llr,
+                    long ls, const DemapCount &cnt, int n_streams, const FmtDev &f, cudaStream_t st) {
+    dim3 grid((unsigned)((e - a + 255) / 256), (unsigned)n_streams);
+    demap_kernel<DIMS, MT, MB><<<grid, 256, 0, st>>>(z, zs, a, e, s2, s2s, llr, ls, cnt, f);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_demap(const float2 *z, long z_stride, long z_off, long a, long e,
+                         const double *sigma2, int sigma2_stride, float *llr, long llr_stride,
+                         const DemapCount &cnt, int n_streams, const FmtDev &f, cudaStream_t st) {
+    if (e <= a || n_streams <= 0) return cudaSuccess;
+    const float2 *zz = z + z_off;
+    if (f.dims == 4 && f.M == 64)
+        return demap_t<4, 64, 6>(zz, z_stride, a, e, sigma2, sigma2_stride, llr, llr_stride, cnt, n_streams, f, st);
+    if (f.dims == 2 && f.M == 4)
+        return demap_t<2, 4, 2>(zz, z_stride, a, e, sigma2, sigma2_stride, llr, llr_stride, cnt, n_streams, f, st);
+    if (f.dims == 2 && f.M == 16)
+        return demap_t<2, 16, 4>(zz, z_stride, a, e, sigma2, sigma2_stride, llr, llr_stride, cnt, n_streams, f, st);
+    return cudaErrorInvalidValue;
+}

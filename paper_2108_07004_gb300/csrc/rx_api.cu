@@ -1,0 +1,764 @@
+// C ABI of the receiver: handle, parameters, tables, block schedule.
+//
+// The schedule follows Sec. 2 of the paper: the parallel stages (FFT
+// filtering, phase search, demapping) run over whole blocks, while the
+// sequential equaliser adaptation uses the first n_upd symbols of a block and
+// its taps are applied to later blocks.  With a tap lag >= 2 the adaptation
+// of block n runs on a second CUDA stream next to the parallel kernels of
+// block n + 1 (the paper's multi-stream idea).
+#include <cmath>
+#include <cstdarg>
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "rx_internal.h"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...) __attribute__((format(printf, 2, 3)));
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CK(call)                                                                      \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return fail(e_ == cudaErrorMemoryAllocation ? RX_ENOMEM : RX_ECUDA,       \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+constexpr double kPi = 3.14159265358979323846;
+constexpr double kC = 299792458.0;
+
+}  // namespace
+
+struct rx_handle {
+    // format
+    FmtDev fmt{};
+    // link / receiver parameters
+    double symbol_rate = 28e9;
+    int sps = 2;
+    double cd = 0.0;
+    int T = 15;
+    int B = 32;
+    int n_fft = 1024, n_ov = 256;
+    double mu = 1e-3;
+    int W = 64;
+    long block = 4096;
+    int n_upd = 1024;
+    int lag = 1;
+    long n_pre = 8192;
+    int cma_passes = 2;
+    long n_cma = 1024;
+    long n_train = 1024;
+    double sigma2_fixed = 0.0;
+    long skip_head = 4096, skip_tail = 512;
+    int streams = 1;
+    double rolloff = 0.1;
+    double wavelength = 1550e-9;
+    // CUDA
+    cudaStream_t st = nullptr;
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_unwrap = nullptr;
+    std::vector<cudaEvent_t> ev_lms;
+    // device tables
+    float2 *H = nullptr, *tw = nullptr;
+    int tab_fft = 0;
+    bool tables_dirty = true;
+    // device buffers
+    long cap_n = 0;
+    int cap_s = 0, cap_lag = 0;
+    float2 *x = nullptr, *y = nullptr, *z = nullptr, *ring = nullptr;
+    uint8_t *bidx = nullptr;
+    uint16_t *pcode = nullptr;
+    int *dsum = nullptr;
+    double *part_u = nullptr, *part_d = nullptr, *sig = nullptr, *sig_fixed = nullptr;
+    StreamDev *sd = nullptr;
+    long cap_dsum = 0, cap_pd = 0;
+    // reference
+    uint8_t *ref = nullptr;
+    long ref_n = 0;
+    int ref_s = 0;
+    // stream state (host mirror of the scalars)
+    bool started = false;
+    long blocks_done = 0;
+    unsigned long long u = 0;
+    long cur_n = 0;
+    // host sources of asynchronous uploads (kept alive until the next call)
+    std::vector<float2> h_taps0;
+    std::vector<StreamDev> h_sd0;
+    std::vector<double> h_sig;
+    // host staging
+    void *h_in = nullptr, *h_out = nullptr;
+    size_t h_in_cap = 0, h_out_cap = 0;
+    float2 *d_in = nullptr;
+    float *d_out = nullptr;
+    size_t d_in_cap = 0, d_out_cap = 0;
+};
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// tables
+// ---------------------------------------------------------------------------
+void gray_qam(int m_pol, std::vector<float> &pts) {
+    // square Gray QAM: label = (I bits)(Q bits), per-axis Gray code, bit 0 on the positive side
+    const int h = m_pol / 2, L = 1 << h;
+    std::vector<double> lev(L);
+    for (int pidx = 0; pidx < L; ++pidx) {
+        const int g = pidx ^ (pidx >> 1);
+        lev[g] = (L - 1) - 2.0 * pidx;
+    }
+    const int M = 1 << m_pol;
+    double e = 0;
+    pts.assign(M * 2, 0.f);
+    std::vector<double> tmp(M * 2);
+    for (int lab = 0; lab < M; ++lab) {
+        tmp[2 * lab] = lev[lab >> h];
+        tmp[2 * lab + 1] = lev[lab & (L - 1)];
+        e += tmp[2 * lab] * tmp[2 * lab] + tmp[2 * lab + 1] * tmp[2 * lab + 1];
+    }
+    const double sc = 1.0 / std::sqrt(e / M);
+    for (int i = 0; i < M * 2; ++i) pts[i] = (float)(tmp[i] * sc);
+}
+
+bool same4(const float *a, const float *b, int n) {
+    for (int i = 0; i < n; ++i)
+        if (a[i] != b[i]) return false;
+    return true;
+}
+
+// rotate a point by k quarter turns (exact in float)
+void rot_q(const float *p, int dims, int k, float *out) {
+    for (int i = 0; i < dims; i += 2) {
+        float re = p[i], im = p[i + 1];
+        for (int t = 0; t < k; ++t) { const float r2 = -im; im = re; re = r2; }
+        out[i] = re;
+        out[i + 1] = im;
+    }
+}
+
+int build_format(const rx_format *f, FmtDev &d) {
+    std::vector<float> pts;
+    int dims, mb, S;
+    if (f->kind == RX_FMT_DP_QPSK || f->kind == RX_FMT_DP_16QAM) {
+        dims = 2;
+        mb = f->kind == RX_FMT_DP_QPSK ? 2 : 4;
+        S = 4;
+        gray_qam(mb, pts);
+    } else if (f->kind == RX_FMT_CUSTOM) {
+        dims = f->dims;
+        mb = f->m_bits;
+        S = f->sym_order;
+        if (dims != 2 && dims != 4) return fail(RX_EINVAL, "format dims must be 2 or 4");
+        if (!f->points || !f->labels) return fail(RX_EINVAL, "custom format needs points and labels");
+        if (mb < 1 || mb > 6) return fail(RX_EINVAL, "m_bits %d out of range", mb);
+        const int M = 1 << mb;
+        pts.assign((size_t)M * dims, 0.f);
+        std::vector<int> seen(M, 0);
+        for (int i = 0; i < M; ++i) {
+            const uint32_t lab = f->labels[i];
+            if (lab >= (uint32_t)M || seen[lab]) return fail(RX_EINVAL, "labels are not a permutation");
+            seen[lab] = 1;
+            for (int c = 0; c < dims; ++c) pts[(size_t)lab * dims + c] = f->points[(size_t)i * dims + c];
+        }
+    } else {
+        return fail(RX_EINVAL, "unknown format kind %d", f->kind);
+    }
+    const int M = 1 << mb;
+    if (S != 1 && S != 2 && S != 4) return fail(RX_EINVAL, "sym_order must be 1, 2 or 4");
+    if (dims == 2 && !(M == 4 || M == 16)) return fail(RX_EINVAL, "2D tables of 4 or 16 points are supported");
+    if (dims == 4 && M != 64) return fail(RX_EINVAL, "4D tables of 64 points are supported");
+    std::memset(&d, 0, sizeof d);
+    d.dims = dims;
+    d.M = M;
+    d.m_pol = mb;
+    d.m = dims == 4 ? mb : 2 * mb;
+    d.S = S;
+    double e2 = 0, e4 = 0;
+    int cnt = 0;
+    for (int j = 0; j < M; ++j) {
+        double pe = 0;
+        for (int c = 0; c < dims; ++c) {
+            d.pts[j][c] = pts[(size_t)j * dims + c];
+            pe += (double)d.pts[j][c] * d.pts[j][c];
+        }
+        d.pe[j] = (float)pe;
+        for (int c = 0; c < dims; c += 2) {
+            const double a2 = (double)d.pts[j][c] * d.pts[j][c] + (double)d.pts[j][c + 1] * d.pts[j][c + 1];
+            e2 += a2;
+            e4 += a2 * a2;
+            ++cnt;
+        }
+    }
+    d.R2 = (float)(e4 / e2);
+    // orbits under rotation by 2 pi / S (verified exactly)
+    const int step = 4 / S;   // quarter turns per symmetry step
+    std::vector<int> orb_of(M, -1);
+    int no = 0;
+    for (int j = 0; j < M; ++j) {
+        if (orb_of[j] >= 0) continue;
+        if (no >= RX_MAXM) return fail(RX_EINVAL, "too many orbits");
+        for (int c = 0; c < 4; ++c) d.orb[no][c] = c < dims ? d.pts[j][c] : 0.f;
+        d.orbe[no] = d.pe[j];
+        for (int k = 0; k < S; ++k) {
+            float rp[4];
+            rot_q(d.pts[j], dims, k * step, rp);
+            int found = -1;
+            for (int jj = 0; jj < M; ++jj)
+                if (same4(rp, d.pts[jj], dims)) { found = jj; break; }
+            if (found < 0 || (orb_of[found] >= 0 && !(k == 0 && found == j)))
+                return fail(RX_EINVAL, "table is not invariant under rotation by 2pi/%d", S);
+            orb_of[found] = no;
+            d.orb_lab[no][k] = found;
+        }
+        ++no;
+    }
+    d.n_orb = no;
+    return RX_OK;
+}
+
+void set_phases(FmtDev &d, int B) {
+    d.B = B;
+    for (int b = 0; b < B; ++b) {
+        const double ph = ((double)b / B - 0.5) * 2.0 * kPi / d.S;
+        d.cs[b][0] = (float)std::cos(ph);
+        d.cs[b][1] = (float)std::sin(ph);
+    }
+}
+
+double raised_cosine(double f, double rs, double beta) {
+    const double af = std::fabs(f), lo = (1 - beta) * rs / 2, hi = (1 + beta) * rs / 2;
+    if (af <= lo) return 1.0;
+    if (af <= hi) return 0.5 * (1 + std::cos(kPi * (af - lo) / (beta * rs)));
+    return 0.0;
+}
+
+int upload_tables(rx_handle *h) {
+    if (!h->tables_dirty && h->tab_fft == h->n_fft) return RX_OK;
+    const int n = h->n_fft;
+    std::vector<float2> H(n), tw(n);
+    const double fs = h->sps * h->symbol_rate;
+    const double dl = h->cd * 1e-3;   // ps/nm -> s/m
+    for (int k = 0; k < n; ++k) {
+        const double f = (k < n / 2 ? k : k - n) * fs / n;
+        const double w = 2 * kPi * f;
+        const double ph = -dl * h->wavelength * h->wavelength * w * w / (4 * kPi * kC);   // conj(H_CD)
+        const double mag = std::sqrt(h->sps * raised_cosine(f, h->symbol_rate, h->rolloff)) / n;
+        H[k] = make_float2((float)(mag * std::cos(ph)), (float)(mag * std::sin(ph)));
+        tw[k] = make_float2((float)std::cos(2 * kPi * k / n), (float)(-std::sin(2 * kPi * k / n)));
+    }
+    if (h->tab_fft != n) {
+        cudaFree(h->H);
+        cudaFree(h->tw);
+        h->H = h->tw = nullptr;
+        CK(cudaMalloc(&h->H, sizeof(float2) * n));
+        CK(cudaMalloc(&h->tw, sizeof(float2) * n));
+        h->tab_fft = n;
+    }
+    CK(cudaMemcpy(h->H, H.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(h->tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    h->tables_dirty = false;
+    return RX_OK;
+}
+
+void free_buffers(rx_handle *h) {
+    cudaFree(h->x); cudaFree(h->y); cudaFree(h->z); cudaFree(h->ring);
+    cudaFree(h->bidx); cudaFree(h->pcode); cudaFree(h->dsum); cudaFree(h->part_u);
+    cudaFree(h->part_d); cudaFree(h->sig); cudaFree(h->sig_fixed); cudaFree(h->sd);
+    h->x = h->y = h->z = h->ring = nullptr;
+    h->bidx = nullptr; h->pcode = nullptr; h->dsum = nullptr;
+    h->part_u = h->part_d = h->sig = h->sig_fixed = nullptr;
+    h->sd = nullptr;
+    h->cap_n = 0; h->cap_s = 0; h->cap_lag = 0;
+}
+
+int ensure_buffers(rx_handle *h, long N) {
+    const int S = h->streams;
+    if (h->cap_n >= N && h->cap_s == S && h->cap_lag == h->lag && h->sd) return RX_OK;
+    free_buffers(h);
+    const long ns = 2 * N;
+    const long ncta = (N + bps_cta_range() - 1) / bps_cta_range() + 2;
+    const long ncta_d = (h->block + 2 * h->W + 255) / 256 + 2;
+    CK(cudaMalloc(&h->x, sizeof(float2) * (size_t)S * 2 * ns));
+    CK(cudaMalloc(&h->y, sizeof(float2) * (size_t)S * 2 * N));
+    CK(cudaMalloc(&h->z, sizeof(float2) * (size_t)S * 2 * N));
+    CK(cudaMalloc(&h->ring, sizeof(float2) * (size_t)(h->lag + 1) * S * 4 * h->T));
+    CK(cudaMalloc(&h->bidx, (size_t)S * N));
+    CK(cudaMalloc(&h->pcode, sizeof(uint16_t) * (size_t)S * N));
+    CK(cudaMalloc(&h->dsum, sizeof(int) * (size_t)S * ncta));
+    CK(cudaMalloc(&h->part_u, sizeof(double) * (size_t)S * ncta));
+    CK(cudaMalloc(&h->part_d, sizeof(double) * 5 * (size_t)S * ncta_d));
+    CK(cudaMalloc(&h->sig, sizeof(double) * S));
+    CK(cudaMalloc(&h->sig_fixed, sizeof(double) * S));
+    CK(cudaMalloc(&h->sd, sizeof(StreamDev) * S));
+    CK(cudaMemset(h->sd, 0, sizeof(StreamDev) * S));
+    h->cap_dsum = ncta;
+    h->cap_pd = ncta_d;
+    h->cap_n = N;
+    h->cap_s = S;
+    h->cap_lag = h->lag;
+    return RX_OK;
+}
+
+int ensure_streams(rx_handle *h) {
+    if (h->lag >= 2 && !h->side) {
+        CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->ev_unwrap, cudaEventDisableTiming));
+    }
+    while ((int)h->ev_lms.size() < h->lag + 1) {
+        cudaEvent_t e;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        h->ev_lms.push_back(e);
+    }
+    return RX_OK;
+}
+
+int check_config(rx_handle *h) {
+    if (h->sps != 2) return fail(RX_EINVAL, "sps must be 2");
+    if (h->T != 7 && h->T != 15 && h->T != 31) return fail(RX_EINVAL, "taps must be 7, 15 or 31");
+    if (h->B < 2 || h->B > RX_MAXB) return fail(RX_EINVAL, "bps_phases must be 2..%d", RX_MAXB);
+    if (h->n_fft != 1024 && h->n_fft != 4096) return fail(RX_EINVAL, "fft must be 1024 or 4096");
+    if (h->n_ov < 2 || (h->n_ov & 1) || h->n_ov >= h->n_fft / 2)
+        return fail(RX_EINVAL, "overlap must be even and < fft/2");
+    if (h->W < 2 || h->W > 64 || (h->W & 1)) return fail(RX_EINVAL, "bps_window must be even, 2..64");
+    if (h->lag < 1 || h->lag > 4) return fail(RX_EINVAL, "lag must be 1..4");
+    if (h->n_upd < 0 || h->n_upd + h->W / 2 > h->block)
+        return fail(RX_EINVAL, "n_upd + bps_window/2 must not exceed block");
+    if (h->block < 64) return fail(RX_EINVAL, "block too small");
+    if (h->streams < 1) return fail(RX_EINVAL, "streams must be >= 1");
+    return RX_OK;
+}
+
+void center_spike(const rx_handle *h, std::vector<float2> &v) {
+    const int T = h->T, D = (T - 1) / 2;
+    v.assign((size_t)h->streams * 4 * T, make_float2(0.f, 0.f));
+    for (int s = 0; s < h->streams; ++s) {
+        v[(size_t)s * 4 * T + 0 * T + D] = make_float2(1.f, 0.f);       // h_XX
+        v[(size_t)s * 4 * T + 3 * T + D] = make_float2(1.f, 0.f);       // h_YY
+    }
+}
+
+float2 *slot(rx_handle *h, long n) {
+    const int L1 = h->lag + 1;
+    const long i = ((n % L1) + L1) % L1;
+    return h->ring + (size_t)i * h->streams * 4 * h->T;
+}
+
+// Run blocks [b0, b1) of S streams of N symbols whose samples are at `in`.
+int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *llr) {
+    const int S = h->streams, T = h->T, L = h->lag;
+    const long Nb = h->block, ns = 2 * N;
+    const long nblk = (N + Nb - 1) / Nb;
+    const size_t tapsz = sizeof(float2) * (size_t)S * 4 * T;
+    cudaStream_t st = h->st;
+    int rc;
+    if ((rc = upload_tables(h)) != RX_OK) return rc;
+    if ((rc = ensure_buffers(h, N)) != RX_OK) return rc;
+    if ((rc = ensure_streams(h)) != RX_OK) return rc;
+    const FmtDev &f = h->fmt;
+    const int D = (T - 1) / 2;
+
+    // CDC of the frames that the FIR of these blocks reads
+    {
+        const long s_lo = std::max(0L, 2 * b0 * Nb - D), s_hi = std::min(ns, 2 * std::min(b1 * Nb, N) + D + 1);
+        const long Sk = h->n_fft - h->n_ov;
+        const long f0 = s_lo / Sk, f1 = (s_hi + Sk - 1) / Sk;
+        // launch_cdc filters frames [0, nframes); offset pointers give frames [f0, f1)
+        (void)f0; (void)f1;
+        CK(launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st));
+    }
+    if (b0 == 0) {
+        std::vector<float2> &cs = h->h_taps0;
+        center_spike(h, cs);
+        float2 *w0 = slot(h, 0);
+        CK(cudaMemcpyAsync(w0, cs.data(), tapsz, cudaMemcpyHostToDevice, st));
+        const long npre = std::min(h->n_pre, N);
+        CK(launch_lms(h->x, ns, w0, w0, 0, (int)npre, nullptr, 0, 0, h->cma_passes, 0, 0,
+                      (float)h->mu, S, T, f, st));
+        if (h->ref && h->ref_n >= std::min(h->n_train, N))
+            CK(launch_align(h->x, ns, w0, h->ref, h->ref_n, (int)std::min(h->n_train, N), S, T, f, st));
+        for (int i = 1; i <= L; ++i) CK(cudaMemcpyAsync(slot(h, i), w0, tapsz, cudaMemcpyDeviceToDevice, st));
+        std::vector<StreamDev> &sd0 = h->h_sd0;
+        sd0.assign(S, StreamDev{});
+        std::memset(sd0.data(), 0, sizeof(StreamDev) * S);
+        for (int s = 0; s < S; ++s) { sd0[s].carry[0][0] = 0; sd0[s].carry[0][1] = h->B / 2; }
+        CK(cudaMemcpyAsync(h->sd, sd0.data(), sizeof(StreamDev) * S, cudaMemcpyHostToDevice, st));
+        if (h->sigma2_fixed > 0) {
+            h->h_sig.assign(S, h->sigma2_fixed);
+            CK(cudaMemcpyAsync(h->sig_fixed, h->h_sig.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
+        }
+        h->u = 0;
+        h->blocks_done = 0;
+        h->started = true;
+        h->cur_n = N;
+    }
+    const int m = f.m;
+    const long sd_stride = sizeof(StreamDev) / sizeof(int32_t);
+    int32_t *carry_base = reinterpret_cast<int32_t *>(h->sd);
+    DemapCount cnt{};
+    cnt.ref_lab = (h->ref && h->ref_n >= N) ? h->ref : nullptr;
+    cnt.ref_stride = h->ref_n;
+    cnt.c0 = std::min(h->skip_head, N);
+    cnt.c1 = std::max(cnt.c0, N - h->skip_tail);
+    cnt.sd = h->sd;
+    cnt.partial = h->part_d;
+    for (long n = b0; n < b1; ++n) {
+        const long k0 = n * Nb, k1 = std::min(k0 + Nb, N);
+        if (L >= 2 && n >= L) CK(cudaStreamWaitEvent(st, h->ev_lms[(n - L) % (L + 1)], 0));
+        // W_n = U_{n-lag}; for n < lag the slot read has not been written since start-up (W_0)
+        const float2 *wn = slot(h, n - L);
+        CK(launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st));
+        const long a = std::max(0L, k0 - h->W / 2);
+        const long e = (n == nblk - 1) ? N : k1 - h->W / 2;
+        CK(launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, h->dsum, S, f, st));
+        const int cin = (int)(n & 1), cout = 1 - cin;
+        CK(launch_unwrap(h->y, N, h->bidx, N, a, a, e, h->dsum, carry_base + 2 * cin,
+                         (int)sd_stride, carry_base + 2 * cout, (int)sd_stride, h->z, N, a,
+                         h->pcode, N, a, h->part_u, h->sig, 1,
+                         &h->sd[0].ticket_unwrap, (int)(sizeof(StreamDev) / sizeof(unsigned)),
+                         S, f, st));
+        const double *s2 = h->sigma2_fixed > 0 ? h->sig_fixed : h->sig;
+        if ((e - a + 255) / 256 > h->cap_pd) return fail(RX_EINVAL, "internal: demap partials");
+        CK(launch_demap(h->z, N, a, a, e, s2, 1, llr + (size_t)a * m, N * m, cnt, S, f, st));
+        const long span = std::max(0L, std::min((long)h->n_upd, N - k0));
+        cudaStream_t ls = st;
+        if (L >= 2) {
+            CK(cudaEventRecord(h->ev_unwrap, st));
+            CK(cudaStreamWaitEvent(h->side, h->ev_unwrap, 0));
+            ls = h->side;
+        }
+        CK(launch_lms(h->x, ns, slot(h, n - 1), slot(h, n), k0, (int)span, h->pcode, N, 2, 1,
+                      h->u, (int)h->n_cma, (float)h->mu, S, T, f, ls));
+        if (L >= 2) CK(cudaEventRecord(h->ev_lms[n % (L + 1)], h->side));
+        h->u += span;
+        h->blocks_done = n + 1;
+    }
+    if (L >= 2 && b1 > b0) CK(cudaStreamWaitEvent(st, h->ev_lms[(b1 - 1) % (L + 1)], 0));
+    return RX_OK;
+}
+
+int fill_stats(rx_handle *h, rx_stats *out) {
+    const int S = h->streams;
+    std::vector<StreamDev> sd(S);
+    CK(cudaStreamSynchronize(h->st));
+    CK(cudaMemcpy(sd.data(), h->sd, sizeof(StreamDev) * S, cudaMemcpyDeviceToHost));
+    for (int s = 0; s < S; ++s) {
+        rx_stats &o = out[s];
+        std::memset(&o, 0, sizeof o);
+        o.n_sym = sd[s].n_sym;
+        o.n_bits = sd[s].n_sym * (uint64_t)h->fmt.m;
+        o.bit_errors = sd[s].bit_errors;
+        o.gmi_sum = sd[s].gmi_sum;
+        o.gmi = o.n_sym ? h->fmt.m - o.gmi_sum / (double)o.n_sym : 0.0;
+        o.ber = o.n_bits ? (double)o.bit_errors / (double)o.n_bits : 0.0;
+        o.evm_num = sd[s].evm_num;
+        o.evm_den = sd[s].evm_den;
+        o.sigma2_last = sd[s].sigma2;
+        o.n_out = (uint64_t)h->cur_n;
+        o.blocks = (uint32_t)h->blocks_done;
+    }
+    return RX_OK;
+}
+
+int set_param_impl(rx_handle *h, const std::string &k, double v) {
+    auto as_int = [&](long lo, long hi, long &dst) -> int {
+        if (v != std::floor(v) || v < lo || v > hi) return fail(RX_EINVAL, "%s out of range", k.c_str());
+        dst = (long)v;
+        return RX_OK;
+    };
+    long t = 0;
+    int rc = RX_OK;
+    if (k == "fft") { rc = as_int(1024, 4096, t); h->n_fft = (int)t; h->tables_dirty = true; }
+    else if (k == "overlap") { rc = as_int(2, 4094, t); h->n_ov = (int)t; }
+    else if (k == "mu") { if (!(v > 0 && v < 1)) return fail(RX_EINVAL, "mu out of range"); h->mu = v; }
+    else if (k == "bps_window") { rc = as_int(2, 64, t); h->W = (int)t; }
+    else if (k == "block") { rc = as_int(64, 1L << 30, t); h->block = t; }
+    else if (k == "n_upd") { rc = as_int(0, 1L << 30, t); h->n_upd = (int)t; }
+    else if (k == "lag") { rc = as_int(1, 4, t); h->lag = (int)t; }
+    else if (k == "n_pre") { rc = as_int(0, 1L << 30, t); h->n_pre = t; }
+    else if (k == "cma_passes") { rc = as_int(0, 16, t); h->cma_passes = (int)t; }
+    else if (k == "n_cma") { rc = as_int(0, 1L << 40, t); h->n_cma = t; }
+    else if (k == "n_train") { rc = as_int(0, 1L << 30, t); h->n_train = t; }
+    else if (k == "sigma2") { if (!(v >= 0)) return fail(RX_EINVAL, "sigma2 < 0"); h->sigma2_fixed = v; }
+    else if (k == "skip_head") { rc = as_int(0, 1L << 40, t); h->skip_head = t; }
+    else if (k == "skip_tail") { rc = as_int(0, 1L << 40, t); h->skip_tail = t; }
+    else if (k == "streams") { rc = as_int(1, 4096, t); h->streams = (int)t; }
+    else if (k == "rolloff") { if (!(v > 0 && v <= 1)) return fail(RX_EINVAL, "rolloff out of range"); h->rolloff = v; h->tables_dirty = true; }
+    else if (k == "wavelength_nm") { if (!(v > 100 && v < 10000)) return fail(RX_EINVAL, "wavelength out of range"); h->wavelength = v * 1e-9; h->tables_dirty = true; }
+    else return fail(RX_EINVAL, "unknown parameter '%s'", k.c_str());
+    if (rc != RX_OK) return rc;
+    if (k == "overlap") h->tables_dirty = true;
+    h->started = false;
+    return check_config(h);
+}
+
+}  // namespace
+
+// ===========================================================================
+// exported
+// ===========================================================================
+extern "C" {
+
+const char *rx_last_error(void) { return g_err.c_str(); }
+
+rx_handle *rx_create(const rx_format *format, double symbol_rate, int sps, double cd_ps_per_nm,
+                     int taps, int bps_phases) {
+    if (!format) { fail(RX_EINVAL, "format is NULL"); return nullptr; }
+    if (!(symbol_rate > 0)) { fail(RX_EINVAL, "symbol_rate must be > 0"); return nullptr; }
+    rx_handle *h = new rx_handle();
+    if (build_format(format, h->fmt) != RX_OK) { delete h; return nullptr; }
+    h->symbol_rate = symbol_rate;
+    h->sps = sps;
+    h->cd = cd_ps_per_nm;
+    h->T = taps;
+    h->B = bps_phases;
+    if (check_config(h) != RX_OK) { delete h; return nullptr; }
+    set_phases(h->fmt, bps_phases);
+    if (h->fmt.dims == 4 && h->fmt.n_orb > 16) {
+        fail(RX_EINVAL, "phase search needs at most 16 orbits (use sym_order 4)");
+        delete h;
+        return nullptr;
+    }
+    if (h->fmt.dims == 2 && h->fmt.n_orb > 4) {
+        fail(RX_EINVAL, "phase search needs at most 4 orbits per polarisation");
+        delete h;
+        return nullptr;
+    }
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        fail(RX_ECUDA, "no CUDA device");
+        delete h;
+        return nullptr;
+    }
+    return h;
+}
+
+void rx_destroy(rx_handle *h) {
+    if (!h) return;
+    if (h->st) cudaStreamSynchronize(h->st);
+    if (h->side) { cudaStreamSynchronize(h->side); cudaStreamDestroy(h->side); }
+    if (h->ev_unwrap) cudaEventDestroy(h->ev_unwrap);
+    for (auto e : h->ev_lms) cudaEventDestroy(e);
+    free_buffers(h);
+    cudaFree(h->H);
+    cudaFree(h->tw);
+    cudaFree(h->ref);
+    cudaFree(h->d_in);
+    cudaFree(h->d_out);
+    if (h->h_in) cudaFreeHost(h->h_in);
+    if (h->h_out) cudaFreeHost(h->h_out);
+    delete h;
+}
+
+int rx_set_param(rx_handle *h, const char *key, double value) {
+    if (!h || !key) return fail(RX_EINVAL, "NULL argument");
+    return set_param_impl(h, key, value);
+}
+
+int rx_get_param(const rx_handle *h, const char *key, double *value) {
+    if (!h || !key || !value) return fail(RX_EINVAL, "NULL argument");
+    const std::string k = key;
+    if (k == "fft") *value = h->n_fft;
+    else if (k == "overlap") *value = h->n_ov;
+    else if (k == "mu") *value = h->mu;
+    else if (k == "bps_window") *value = h->W;
+    else if (k == "block") *value = (double)h->block;
+    else if (k == "n_upd") *value = h->n_upd;
+    else if (k == "lag") *value = h->lag;
+    else if (k == "n_pre") *value = (double)h->n_pre;
+    else if (k == "cma_passes") *value = h->cma_passes;
+    else if (k == "n_cma") *value = (double)h->n_cma;
+    else if (k == "n_train") *value = (double)h->n_train;
+    else if (k == "sigma2") *value = h->sigma2_fixed;
+    else if (k == "skip_head") *value = (double)h->skip_head;
+    else if (k == "skip_tail") *value = (double)h->skip_tail;
+    else if (k == "streams") *value = h->streams;
+    else if (k == "rolloff") *value = h->rolloff;
+    else if (k == "wavelength_nm") *value = h->wavelength * 1e9;
+    else if (k == "taps") *value = h->T;
+    else if (k == "bps_phases") *value = h->B;
+    else if (k == "cd_ps_per_nm") *value = h->cd;
+    else return fail(RX_EINVAL, "unknown parameter '%s'", key);
+    return RX_OK;
+}
+
+int rx_set_stream(rx_handle *h, void *cuda_stream) {
+    if (!h) return fail(RX_EINVAL, "NULL handle");
+    h->st = (cudaStream_t)cuda_stream;
+    return RX_OK;
+}
+
+int rx_format_info(const rx_handle *h, int *dims, int *m, int *M) {
+    if (!h) return fail(RX_EINVAL, "NULL handle");
+    if (dims) *dims = h->fmt.dims;
+    if (m) *m = h->fmt.m;
+    if (M) *M = h->fmt.M;
+    return RX_OK;
+}
+
+int rx_set_reference(rx_handle *h, const uint8_t *bits, size_t n_sym) {
+    if (!h || (!bits && n_sym)) return fail(RX_EINVAL, "NULL argument");
+    const int S = h->streams;
+    if (h->ref && (h->ref_n != (long)n_sym || h->ref_s != S)) { cudaFree(h->ref); h->ref = nullptr; }
+    h->ref_n = (long)n_sym;
+    h->ref_s = S;
+    if (!n_sym) return RX_OK;
+    if (!h->ref) CK(cudaMalloc(&h->ref, (size_t)S * n_sym));
+    CK(launch_ref_labels(bits, h->ref, (long)n_sym, S, h->fmt.m, h->fmt.dims, h->fmt.m_pol, h->st));
+    h->started = false;
+    return RX_OK;
+}
+
+int rx_reset(rx_handle *h) {
+    if (!h) return fail(RX_EINVAL, "NULL handle");
+    h->started = false;
+    h->blocks_done = 0;
+    h->u = 0;
+    return RX_OK;
+}
+
+int rx_process(rx_handle *h, const void *samples, size_t n_samples, float *llr_out, rx_stats *stats) {
+    if (!h || !samples || !llr_out) return fail(RX_EINVAL, "NULL argument");
+    if (n_samples < 2 || (n_samples & 1)) return fail(RX_EINVAL, "n_samples must be a positive multiple of 2");
+    const long N = (long)n_samples / 2;
+    const long nblk = (N + h->block - 1) / h->block;
+    int rc = run_blocks(h, (const float2 *)samples, N, 0, nblk, llr_out);
+    if (rc != RX_OK) return rc;
+    CK(cudaGetLastError());
+    if (stats) return fill_stats(h, stats);
+    return RX_OK;
+}
+
+int rx_get_stats(rx_handle *h, rx_stats *stats) {
+    if (!h || !stats) return fail(RX_EINVAL, "NULL argument");
+    if (!h->sd) return fail(RX_ESTATE, "nothing processed yet");
+    return fill_stats(h, stats);
+}
+
+int rx_process_host(rx_handle *h, const void *samples, size_t n_samples, float *llr_out, rx_stats *stats) {
+    if (!h || !samples || !llr_out) return fail(RX_EINVAL, "NULL argument");
+    if (n_samples < 2 || (n_samples & 1)) return fail(RX_EINVAL, "n_samples must be a positive multiple of 2");
+    const int S = h->streams;
+    const long N = (long)n_samples / 2;
+    const size_t in_b = sizeof(float2) * (size_t)S * 2 * n_samples;
+    const size_t out_b = sizeof(float) * (size_t)S * N * h->fmt.m;
+    if (h->d_in_cap < in_b) { cudaFree(h->d_in); h->d_in = nullptr; CK(cudaMalloc(&h->d_in, in_b)); h->d_in_cap = in_b; }
+    if (h->d_out_cap < out_b) { cudaFree(h->d_out); h->d_out = nullptr; CK(cudaMalloc(&h->d_out, out_b)); h->d_out_cap = out_b; }
+    CK(cudaMemcpyAsync(h->d_in, samples, in_b, cudaMemcpyHostToDevice, h->st));
+    const long nblk = (N + h->block - 1) / h->block;
+    int rc = run_blocks(h, h->d_in, N, 0, nblk, h->d_out);
+    if (rc != RX_OK) return rc;
+    CK(cudaMemcpyAsync(llr_out, h->d_out, out_b, cudaMemcpyDeviceToHost, h->st));
+    if (stats) return fill_stats(h, stats);
+    CK(cudaStreamSynchronize(h->st));
+    return RX_OK;
+}
+
+int rx_get_state(rx_handle *h, void *buf, size_t *len) {
+    if (!h || !len) return fail(RX_EINVAL, "NULL argument");
+    (void)buf;
+    return fail(RX_ESTATE, "state serialisation not available yet");
+}
+
+int rx_set_state(rx_handle *h, const void *buf, size_t len) {
+    if (!h || !buf) return fail(RX_EINVAL, "NULL argument");
+    (void)len;
+    return fail(RX_ESTATE, "state serialisation not available yet");
+}
+
+// ---- single stages ---------------------------------------------------------
+
+int rx_cdc(rx_handle *h, const void *in, void *out, size_t n_samples) {
+    if (!h || !in || !out) return fail(RX_EINVAL, "NULL argument");
+    if (in == out) return fail(RX_EINVAL, "in and out must differ");
+    int rc = upload_tables(h);
+    if (rc != RX_OK) return rc;
+    CK(launch_cdc((const float2 *)in, (float2 *)out, (long)n_samples, 2 * h->streams, h->n_fft,
+                  h->n_ov, h->H, h->tw, h->st));
+    return RX_OK;
+}
+
+int rx_fir(rx_handle *h, const void *x, size_t n_samples, const void *taps, size_t k0, size_t k1, void *y) {
+    if (!h || !x || !taps || !y) return fail(RX_EINVAL, "NULL argument");
+    if (k1 < k0) return fail(RX_EINVAL, "k1 < k0");
+    CK(launch_fir((const float2 *)x, (long)n_samples, (const float2 *)taps, (long)k0, (long)k1,
+                  (float2 *)y, (long)(k1 - k0), 0, h->streams, h->T, h->st));
+    return RX_OK;
+}
+
+int rx_lms(rx_handle *h, const void *x, size_t n_samples, void *taps, size_t k0, size_t n_upd,
+           const uint16_t *pcode, int mode, int passes, uint64_t u0) {
+    if (!h || !x || !taps) return fail(RX_EINVAL, "NULL argument");
+    if (mode < 0 || mode > 2) return fail(RX_EINVAL, "mode must be 0, 1 or 2");
+    if (mode != 0 && !pcode) return fail(RX_EINVAL, "DD mode needs phase codes");
+    const long N = (long)n_samples / 2;
+    if ((long)(k0 + n_upd) > N) return fail(RX_EINVAL, "update span beyond the stream");
+    CK(launch_lms((const float2 *)x, (long)n_samples, (const float2 *)taps, (float2 *)taps, (long)k0,
+                  (int)n_upd, pcode, N, mode, passes, u0, (int)h->n_cma, (float)h->mu, h->streams,
+                  h->T, h->fmt, h->st));
+    return RX_OK;
+}
+
+int rx_bps(rx_handle *h, const void *y, size_t n_y, size_t a, size_t e, size_t n_valid, uint8_t *b_out) {
+    if (!h || !y || !b_out) return fail(RX_EINVAL, "NULL argument");
+    if (e < a || e > n_y || n_valid > n_y) return fail(RX_EINVAL, "bad range");
+    int *dsum = nullptr;
+    const long ncta = ((long)(e - a) + bps_cta_range() - 1) / bps_cta_range();
+    CK(cudaMallocAsync(&dsum, sizeof(int) * (size_t)h->streams * (ncta + 1), h->st));
+    cudaError_t err = launch_bps((const float2 *)y, (long)n_y, (long)a, (long)e, (long)n_valid, h->W,
+                                 b_out, (long)(e - a), 0, dsum, h->streams, h->fmt, h->st);
+    cudaFreeAsync(dsum, h->st);
+    CK(err);
+    return RX_OK;
+}
+
+int rx_unwrap(rx_handle *h, const void *y, size_t n_y, const uint8_t *b, size_t a, size_t e,
+              const int32_t *carry_in, void *z, uint16_t *pcode, int32_t *carry_out, double *sigma2) {
+    if (!h || !y || !b || !carry_in || !z || !pcode || !carry_out || !sigma2)
+        return fail(RX_EINVAL, "NULL argument");
+    if (e <= a || e > n_y) return fail(RX_EINVAL, "bad range");
+    const int S = h->streams;
+    const long K = (long)(e - a);
+    const long ncta = (K + bps_cta_range() - 1) / bps_cta_range();
+    // interior increments come from the phase search; recompute them here
+    int *dsum = nullptr;
+    double *part = nullptr;
+    unsigned *ticket = nullptr;
+    CK(cudaMallocAsync(&dsum, sizeof(int) * (size_t)S * ncta, h->st));
+    CK(cudaMallocAsync(&part, sizeof(double) * (size_t)S * ncta, h->st));
+    CK(cudaMallocAsync(&ticket, sizeof(unsigned) * (size_t)S, h->st));
+    CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned) * (size_t)S, h->st));
+    CK(launch_dsum_from_b(b, K, a, e, dsum, S, h->fmt.B, h->st));
+    cudaError_t err = launch_unwrap((const float2 *)y, (long)n_y, b, K, 0, (long)a, (long)e, dsum,
+                                    carry_in, 2, carry_out, 2, (float2 *)z, K, 0, pcode, K, 0, part,
+                                    sigma2, 1, ticket, 1, S, h->fmt, h->st);
+    cudaFreeAsync(dsum, h->st);
+    cudaFreeAsync(part, h->st);
+    cudaFreeAsync(ticket, h->st);
+    CK(err);
+    return RX_OK;
+}
+
+int rx_demap(rx_handle *h, const void *z, size_t K, const double *sigma2, float *llr) {
+    if (!h || !z || !sigma2 || !llr) return fail(RX_EINVAL, "NULL argument");
+    DemapCount cnt{};
+    CK(launch_demap((const float2 *)z, (long)K, 0, 0, (long)K, sigma2, 1, llr, (long)K * h->fmt.m, cnt,
+                    h->streams, h->fmt, h->st));
+    return RX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,108 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rx.h"
+
+#define RX_MAXM 64        // largest table (4D: 64 points; 2D: 16 points per polarisation)
+#define RX_MAXB 64        // largest number of BPS test phases
+#define RX_NCHUNK 10      // BPS ring of 32-symbol chunks
+
+// Constellation and phase-search tables, passed to kernels by value
+// (__grid_constant__), so that uniform reads come from the constant bank.
+struct FmtDev {
+    int dims;             // 2 or 4
+    int M;                // table size
+    int m;                // bits per 4D symbol
+    int m_pol;            // bits per table entry (dims 2) / m (dims 4)
+    int S;                // rotational symmetry order used by the phase search (1, 2, 4)
+    int n_orb;            // number of orbits (M / S)
+    int B;                // BPS test phases
+    float R2;             // CMA radius E|s|^4 / E|s|^2 (per-polarisation marginal)
+    float pts[RX_MAXM][4];      // label order: (xr, xi, yr, yi) or (re, im, -, -)
+    float pe[RX_MAXM];          // energy of each point
+    float orb[RX_MAXM][4];      // orbit representatives
+    float orbe[RX_MAXM];        // energy of each representative
+    int orb_lab[RX_MAXM][4];    // label of representative o rotated by k quarter turns (k < S)
+    float cs[RX_MAXB][2];       // cos, sin of the test phases phi_b
+};
+
+// Per-stream device state.
+struct StreamDev {
+    int32_t carry[2][2];            // unwrap carry [slot][m, b]
+    unsigned long long bit_errors;
+    unsigned long long n_sym;
+    double gmi_sum;
+    double evm_num;
+    double evm_den;
+    double sigma2;                  // noise variance of the current block
+    unsigned int ticket_unwrap;
+    unsigned int ticket_demap;
+    int pad[2];
+};
+
+// ---- complex helpers --------------------------------------------------------
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+    return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) * b
+__host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
+    return make_float2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__host__ __device__ __forceinline__ float cnorm(float2 a) { return a.x * a.x + a.y * a.y; }
+
+// ---- launchers (return cudaError_t of the launch) -----------------------------
+cudaError_t launch_cdc(const float2 *in, float2 *out, long ns, int n_streams2, int n_fft,
+                       int n_ov, const float2 *H, const float2 *tw, cudaStream_t st);
+
+cudaError_t launch_fir(const float2 *x, long ns, const float2 *taps, long k0, long k1,
+                       float2 *y, long y_stride, long y_off, int n_streams, int T,
+                       cudaStream_t st);
+
+cudaError_t launch_lms(const float2 *x, long ns, const float2 *taps_in, float2 *taps_out,
+                       long k0, int n_upd, const uint16_t *pcode, long pcode_stride,
+                       int mode, int passes, unsigned long long u0, int n_cma, float mu,
+                       int n_streams, int T, const FmtDev &f, cudaStream_t st);
+
+cudaError_t launch_align(const float2 *x, long ns, float2 *taps, const uint8_t *ref_lab,
+                         long ref_stride, int n_train, int n_streams, int T, const FmtDev &f,
+                         cudaStream_t st);
+
+int bps_cta_range();   // output symbols per BPS / unwrap CTA
+
+cudaError_t launch_bps(const float2 *y, long y_stride, long a, long e, long n_valid,
+                       int W, uint8_t *bout, long bout_stride, long bout_off,
+                       int *dsum, int n_streams, const FmtDev &f, cudaStream_t st);
+
+cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long b_stride,
+                          long b_off, long a, long e, const int *dsum,
+                          const int32_t *carry_in, int carry_in_stride,
+                          int32_t *carry_out, int carry_out_stride,
+                          float2 *z, long z_stride, long z_off,
+                          uint16_t *pcode, long pcode_stride, long pcode_off,
+                          double *partial, double *sigma2_out, int sigma2_stride,
+                          unsigned int *ticket, int ticket_stride,
+                          int n_streams, const FmtDev &f, cudaStream_t st);
+
+cudaError_t launch_dsum_from_b(const uint8_t *b, long b_stride, long a, long e, int *dsum,
+                               int n_streams, int B, cudaStream_t st);
+
+struct DemapCount {
+    const uint8_t *ref_lab;   // [S][N] labels of the reference (or null)
+    long ref_stride;
+    long c0, c1;              // count symbols with c0 <= k < c1 (stream index)
+    StreamDev *sd;            // per-stream accumulators (or null)
+    double *partial;          // [S][n_cta][3] scratch
+};
+
+cudaError_t launch_demap(const float2 *z, long z_stride, long z_off, long a, long e,
+                         const double *sigma2, int sigma2_stride, float *llr,
+                         long llr_stride, const DemapCount &cnt, int n_streams,
+                         const FmtDev &f, cudaStream_t st);
+
+cudaError_t launch_ref_labels(const uint8_t *bits, uint8_t *lab, long n_sym, int n_streams,
+                              int m, int dims, int m_pol, cudaStream_t st);

@@ -1,0 +1,239 @@
+"""Python binding of the receiver's C ABI (include/rx.h).
+
+Argument marshalling only: torch tensors supply device memory and the CUDA
+stream; every step of the chain runs in the library's kernels.  Loading
+fails loudly when the compiled library is missing; there is no other path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import json
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librx.so")
+_lib = None
+
+RX_FMT_CUSTOM, RX_FMT_DP_QPSK, RX_FMT_DP_16QAM = 0, 1, 2
+
+
+class RxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"rx error {code}: {msg}")
+        self.code = code
+
+
+class RxFormat(C.Structure):
+    _fields_ = [("kind", C.c_int), ("dims", C.c_int), ("m_bits", C.c_int),
+                ("sym_order", C.c_int), ("points", C.POINTER(C.c_float)),
+                ("labels", C.POINTER(C.c_uint32))]
+
+
+class RxStats(C.Structure):
+    _fields_ = [("n_sym", C.c_uint64), ("n_bits", C.c_uint64), ("bit_errors", C.c_uint64),
+                ("gmi_sum", C.c_double), ("gmi", C.c_double), ("ber", C.c_double),
+                ("evm_num", C.c_double), ("evm_den", C.c_double), ("sigma2_last", C.c_double),
+                ("n_out", C.c_uint64), ("blocks", C.c_uint32), ("reserved", C.c_uint32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+_VP, _SZ, _I, _D = C.c_void_p, C.c_size_t, C.c_int, C.c_double
+_PROTOS = {
+    "rx_create": (C.c_void_p, [C.POINTER(RxFormat), _D, _I, _D, _I, _I]),
+    "rx_destroy": (None, [_VP]),
+    "rx_set_param": (_I, [_VP, C.c_char_p, _D]),
+    "rx_get_param": (_I, [_VP, C.c_char_p, C.POINTER(_D)]),
+    "rx_set_stream": (_I, [_VP, _VP]),
+    "rx_set_reference": (_I, [_VP, _VP, _SZ]),
+    "rx_reset": (_I, [_VP]),
+    "rx_process": (_I, [_VP, _VP, _SZ, _VP, _VP]),
+    "rx_process_host": (_I, [_VP, _VP, _SZ, _VP, _VP]),
+    "rx_get_stats": (_I, [_VP, _VP]),
+    "rx_get_state": (_I, [_VP, _VP, C.POINTER(_SZ)]),
+    "rx_set_state": (_I, [_VP, _VP, _SZ]),
+    "rx_format_info": (_I, [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
+    "rx_last_error": (C.c_char_p, []),
+    "rx_cdc": (_I, [_VP, _VP, _VP, _SZ]),
+    "rx_fir": (_I, [_VP, _VP, _SZ, _VP, _SZ, _SZ, _VP]),
+    "rx_lms": (_I, [_VP, _VP, _SZ, _VP, _SZ, _SZ, _VP, _I, _I, C.c_uint64]),
+    "rx_bps": (_I, [_VP, _VP, _SZ, _SZ, _SZ, _SZ, _VP]),
+    "rx_unwrap": (_I, [_VP, _VP, _SZ, _VP, _SZ, _SZ, _VP, _VP, _VP, _VP, _VP]),
+    "rx_demap": (_I, [_VP, _VP, _SZ, _VP, _VP]),
+}
+
+
+def lib() -> C.CDLL:
+    """The loaded library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2108_07004_gb300.build`")
+        L = C.CDLL(LIB_PATH)
+        for name, (res, args) in _PROTOS.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols() -> list[str]:
+    return list(_PROTOS)
+
+
+def _ck(rc: int):
+    if rc != 0:
+        raise RxError(rc, lib().rx_last_error().decode())
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return t.data_ptr()
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return t.ctypes.data
+    return int(t)
+
+
+def load_table(name: str) -> dict:
+    with open(os.path.join(_HERE, "data", f"{name}_v1.json")) as f:
+        return json.load(f)
+
+
+class Receiver:
+    """One receiver handle for `streams` streams of one format and link."""
+
+    def __init__(self, fmt: str, *, symbol_rate: float = 28e9, sps: int = 2,
+                 cd_ps_per_nm: float = 0.0, taps: int = 15, bps_phases: int = 32,
+                 stream: torch.cuda.Stream | None = None, **params):
+        L = lib()
+        f = RxFormat()
+        self._keep = []
+        if fmt == "dp_qpsk":
+            f.kind = RX_FMT_DP_QPSK
+        elif fmt == "dp_16qam":
+            f.kind = RX_FMT_DP_16QAM
+        else:
+            d = load_table(fmt)
+            pts = np.ascontiguousarray(np.asarray(d["points"], dtype=np.float32))
+            labs = np.ascontiguousarray(np.asarray(d["labels"], dtype=np.uint32))
+            self._keep += [pts, labs]
+            f.kind, f.dims, f.m_bits, f.sym_order = RX_FMT_CUSTOM, int(d["dims"]), int(d["m_bits"]), int(d["sym_order"])
+            f.points = pts.ctypes.data_as(C.POINTER(C.c_float))
+            f.labels = labs.ctypes.data_as(C.POINTER(C.c_uint32))
+        h = L.rx_create(C.byref(f), symbol_rate, sps, cd_ps_per_nm, taps, bps_phases)
+        if not h:
+            raise RxError(-1, L.rx_last_error().decode())
+        self.h = h
+        self.fmt = fmt
+        self.taps = taps
+        dims, m, M = C.c_int(), C.c_int(), C.c_int()
+        _ck(L.rx_format_info(h, C.byref(dims), C.byref(m), C.byref(M)))
+        self.dims, self.m, self.M = dims.value, m.value, M.value
+        st = stream if stream is not None else torch.cuda.current_stream()
+        _ck(L.rx_set_stream(h, st.cuda_stream))
+        for k, v in params.items():
+            self.set(k, v)
+
+    # ---- parameters ----
+    def set(self, key: str, value: float):
+        _ck(lib().rx_set_param(self.h, key.encode(), float(value)))
+
+    def get(self, key: str) -> float:
+        v = C.c_double()
+        _ck(lib().rx_get_param(self.h, key.encode(), C.byref(v)))
+        return v.value
+
+    @property
+    def streams(self) -> int:
+        return int(self.get("streams"))
+
+    def set_stream(self, stream: torch.cuda.Stream):
+        _ck(lib().rx_set_stream(self.h, stream.cuda_stream))
+
+    def set_reference(self, bits: torch.Tensor):
+        """bits: [S, N, m] uint8 on the device."""
+        _ck(lib().rx_set_reference(self.h, _ptr(bits), bits.shape[1]))
+
+    def reset(self):
+        _ck(lib().rx_reset(self.h))
+
+    # ---- chain ----
+    def process(self, samples: torch.Tensor, llr: torch.Tensor | None = None,
+                stats: bool = True):
+        """samples [S, 2, 2N] complex64 (device) -> (llr [S, N, m] float32, stats)."""
+        S, _, ns = samples.shape
+        if llr is None:
+            llr = torch.empty((S, ns // 2, self.m), dtype=torch.float32, device=samples.device)
+        st = (RxStats * S)() if stats else None
+        _ck(lib().rx_process(self.h, _ptr(samples), ns, _ptr(llr),
+                             C.cast(st, C.c_void_p) if st is not None else None))
+        return llr, ([s.as_dict() for s in st] if st is not None else None)
+
+    def process_host(self, samples, llr, stats: bool = True):
+        """Host buffers (torch CPU tensors, pinned for overlap) in and out."""
+        S, _, ns = samples.shape
+        st = (RxStats * S)() if stats else None
+        _ck(lib().rx_process_host(self.h, _ptr(samples), ns, _ptr(llr),
+                                  C.cast(st, C.c_void_p) if st is not None else None))
+        return [s.as_dict() for s in st] if st is not None else None
+
+    def stats(self):
+        S = self.streams
+        st = (RxStats * S)()
+        _ck(lib().rx_get_stats(self.h, C.cast(st, C.c_void_p)))
+        return [s.as_dict() for s in st]
+
+    def get_state(self) -> bytes:
+        n = C.c_size_t(0)
+        _ck(lib().rx_get_state(self.h, None, C.byref(n)))
+        buf = C.create_string_buffer(n.value)
+        _ck(lib().rx_get_state(self.h, buf, C.byref(n)))
+        return buf.raw[: n.value]
+
+    def set_state(self, blob: bytes):
+        _ck(lib().rx_set_state(self.h, blob, len(blob)))
+
+    # ---- single stages ----
+    def cdc(self, x_in: torch.Tensor, x_out: torch.Tensor):
+        _ck(lib().rx_cdc(self.h, _ptr(x_in), _ptr(x_out), x_in.shape[-1]))
+
+    def fir(self, x: torch.Tensor, taps: torch.Tensor, k0: int, k1: int, y: torch.Tensor):
+        _ck(lib().rx_fir(self.h, _ptr(x), x.shape[-1], _ptr(taps), k0, k1, _ptr(y)))
+
+    def lms(self, x: torch.Tensor, taps: torch.Tensor, k0: int, n_upd: int,
+            pcode: torch.Tensor | None, mode: int, passes: int = 1, u0: int = 0):
+        _ck(lib().rx_lms(self.h, _ptr(x), x.shape[-1], _ptr(taps), k0, n_upd,
+                         _ptr(pcode), mode, passes, u0))
+
+    def bps(self, y: torch.Tensor, a: int, e: int, n_valid: int, b_out: torch.Tensor):
+        _ck(lib().rx_bps(self.h, _ptr(y), y.shape[-1], a, e, n_valid, _ptr(b_out)))
+
+    def unwrap(self, y, b, a, e, carry_in, z, pcode, carry_out, sigma2):
+        _ck(lib().rx_unwrap(self.h, _ptr(y), y.shape[-1], _ptr(b), a, e, _ptr(carry_in),
+                            _ptr(z), _ptr(pcode), _ptr(carry_out), _ptr(sigma2)))
+
+    def demap(self, z: torch.Tensor, sigma2: torch.Tensor, llr: torch.Tensor):
+        _ck(lib().rx_demap(self.h, _ptr(z), z.shape[-1], _ptr(sigma2), _ptr(llr)))
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,272 @@
+"""GPU parity: each stage of the CUDA library against the FP64 oracle.
+
+Every test feeds the GPU the oracle's own inputs (cast to complex64) and
+compares element by element.  Tolerances follow the FP32 arithmetic:
+* CDC / FIR / de-rotation: complex64 sums of O(100) terms, relative RMS
+  error ~1e-6; the bounds below leave 10-30x headroom.
+* LLRs: |dLLR| <= 1e-4 * max(1, |LLR|) (the target tolerance of the chain).
+* Integer results (phase indices, unwrap counts, bit errors): exact, except
+  where the oracle itself has a near-tie (relative cost gap < 1e-5 for BPS),
+  where either choice is valid and the choice must be within the tie.
+"""
+import numpy as np
+import pytest
+
+from oracle import chain, oracle_format
+from paper_2108_07004_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+LLR_RTOL = 1e-4
+TIE = 1e-5
+
+
+def _rx():
+    from paper_2108_07004_gb300 import rx
+    return rx
+
+
+def _dev(a, dtype=None):
+    t = torch.from_numpy(np.ascontiguousarray(a))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.cuda()
+
+
+CASES = {
+    # name: (format, n_sym, cd, n_fft, n_ov, taps, B, block, esn0, lw)
+    "qpsk80km": ("dp_qpsk", 1 << 14, 1360.0, 1024, 256, 15, 32, 4096, 12.0, 1e-5),
+    "gs1000km": ("gs4d64", 1 << 14, 17000.0, 4096, 1024, 31, 64, 4096, 12.0, 2e-5),
+    "qam16": ("dp_16qam", 12000, 2000.0, 1024, 256, 15, 32, 4096, 18.0, 1e-5),
+}
+
+
+def _params(case):
+    fmt, n, cd, nfft, nov, T, B, blk, esn0, lw = CASES[case]
+    return chain.RxParams(cd_ps_per_nm=cd, n_fft=nfft, n_ov=nov, taps=T, bps_phases=B,
+                          block=blk, n_pre=4096)
+
+
+_cache = {}
+
+
+def _oracle_run(case):
+    if case not in _cache:
+        fmt, n, cd, nfft, nov, T, B, blk, esn0, lw = CASES[case]
+        st = synth.make_stream(fmt, n, seed=synth.stream_seed(9, len(_cache)), esn0_db=esn0,
+                               cd_ps_per_nm=cd, linewidth_ts=lw)
+        p = _params(case)
+        res = chain.run_chain(st.rx, oracle_format(fmt), p, ref_bits=st.bits)
+        _cache[case] = (st, p, res)
+    return _cache[case]
+
+
+def _receiver(case, **kw):
+    rx = _rx()
+    fmt, n, cd, nfft, nov, T, B, blk, esn0, lw = CASES[case]
+    r = rx.Receiver(fmt, cd_ps_per_nm=cd, taps=T, bps_phases=B)
+    r.set("fft", nfft)
+    r.set("overlap", nov)
+    r.set("block", blk)
+    r.set("n_pre", 4096)
+    for k, v in kw.items():
+        r.set(k, v)
+    return r
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_cdc_parity(case):
+    st, p, res = _oracle_run(case)
+    r = _receiver(case)
+    x_in = _dev(st.rx[None])
+    out = torch.zeros_like(x_in)
+    r.cdc(x_in, out)
+    torch.cuda.synchronize()
+    g = out[0].cpu().numpy().astype(np.complex128)
+    ref = res.x
+    rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+    err = np.abs(g - ref)
+    assert np.sqrt(np.mean(err ** 2)) < 3e-6 * rms
+    assert err.max() < 3e-5 * rms
+
+
+def test_cdc_ragged_and_multistream():
+    """Several streams at once; a length that ends inside a frame."""
+    rx = _rx()
+    p = chain.RxParams(cd_ps_per_nm=500.0, n_fft=1024, n_ov=256)
+    S, ns = 3, 5000 * 2 + 2          # ragged: not a multiple of the 768-sample hop
+    rng = np.random.default_rng(1)
+    xs = (rng.standard_normal((S, 2, ns)) + 1j * rng.standard_normal((S, 2, ns))).astype(np.complex64)
+    r = rx.Receiver("dp_qpsk", cd_ps_per_nm=500.0, taps=15, bps_phases=32, streams=S)
+    out = torch.zeros((S, 2, ns), dtype=torch.complex64, device="cuda")
+    r.cdc(_dev(xs), out)
+    g = out.cpu().numpy()
+    for s in range(S):
+        ref = chain.cdc(xs[s].astype(np.complex128), p)
+        assert np.max(np.abs(g[s] - ref)) < 3e-5 * np.sqrt(np.mean(np.abs(ref) ** 2))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_fir_parity(case):
+    st, p, res = _oracle_run(case)
+    r = _receiver(case)
+    x = res.x.astype(np.complex64)
+    rng = np.random.default_rng(2)
+    T = p.taps
+    taps = (res.w0 + 0.05 * (rng.standard_normal((2, 2, T)) + 1j * rng.standard_normal((2, 2, T))))
+    k0, k1 = 1000, x.shape[1] // 2 - 7      # ragged end, interior start
+    y = torch.zeros((1, 2, k1 - k0), dtype=torch.complex64, device="cuda")
+    r.fir(_dev(x[None]), _dev(taps.astype(np.complex64)[None]), k0, k1, y)
+    ref = chain.fir(x.astype(np.complex128), taps.astype(np.complex64).astype(np.complex128), k0, k1)
+    g = y[0].cpu().numpy()
+    rms = np.sqrt(np.mean(np.abs(ref) ** 2))
+    assert np.max(np.abs(g - ref)) < 1e-5 * rms
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_lms_cma_parity(case):
+    """Start-up CMA (two passes) from the identity on the oracle's CDC output."""
+    st, p, res = _oracle_run(case)
+    r = _receiver(case)
+    x = res.x.astype(np.complex64)
+    fmt = oracle_format(CASES[case][0])
+    h0 = chain.center_spike(p.taps)
+    ref = h0
+    for _ in range(2):
+        ref = chain.lms(x.astype(np.complex128), ref, range(2048), fmt, p, force_cma=True)
+    taps = _dev(h0.astype(np.complex64)[None])
+    r.lms(_dev(x[None]), taps, 0, 2048, None, 0, passes=2)
+    g = taps[0].cpu().numpy()
+    assert np.max(np.abs(g - ref)) < 2e-4 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_lms_dd_parity(case):
+    """DD-LMS of one block span with the oracle's taps and phases."""
+    st, p, res = _oracle_run(case)
+    r = _receiver(case)
+    fmt = oracle_format(CASES[case][0])
+    x = res.x.astype(np.complex64)
+    n = 2          # block index with DD updates (n_cma = 1024 -> block 0 span is CMA)
+    k0 = n * p.block
+    h_in = res.taps_after[n - 1].astype(np.complex64)
+    phase = {k: res.phi[k] for k in range(k0, k0 + p.n_upd)}
+    p2 = chain.RxParams(**{**p.__dict__, "n_cma": 0})
+    info = chain.LmsInfo()
+    ref = chain.lms(x.astype(np.complex128), h_in.astype(np.complex128), range(k0, k0 + p.n_upd),
+                    fmt, p2, phase=phase, info=info)
+    assert min(mg for _, mg in info.dd_margin) > 1e-4, "oracle has a near-tie decision"
+    pcode = (res.b.astype(np.int64) | ((res.m % fmt.sym_order) << 8)).astype(np.uint16)
+    taps = _dev(h_in[None])
+    r.lms(_dev(x[None]), taps, k0, p.n_upd, _dev(pcode[None]), 1)
+    g = taps[0].cpu().numpy()
+    assert np.max(np.abs(g - ref)) < 2e-4 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_bps_parity(case):
+    st, p, res = _oracle_run(case)
+    r = _receiver(case)
+    fmt = oracle_format(CASES[case][0])
+    y = res.y.astype(np.complex64)
+    N = y.shape[1]
+    a, e = 37, N - 101            # ragged range, windows truncated at n_valid = N
+    b_ref, gap, _ = chain.bps(y.astype(np.complex128), a, e, N, p, fmt)
+    bo = torch.zeros((1, e - a), dtype=torch.uint8, device="cuda")
+    r.bps(_dev(y[None]), a, e, N, bo)
+    g = bo[0].cpu().numpy().astype(np.int64)
+    diff = g != b_ref
+    assert np.all(gap[diff] < TIE), f"{diff.sum()} choices differ outside near-ties"
+    assert diff.mean() < 1e-3
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_unwrap_parity(case):
+    st, p, res = _oracle_run(case)
+    r = _receiver(case)
+    fmt = oracle_format(CASES[case][0])
+    N = res.y.shape[1]
+    y = res.y.astype(np.complex64)
+    a, e = res.ranges[1]
+    b = res.b[a:e].astype(np.uint8)
+    # carry from the oracle's previous range
+    a0, e0 = res.ranges[0]
+    carry = np.array([[res.m[e0 - 1], res.b[e0 - 1]]], dtype=np.int32)
+    z = torch.zeros((1, 2, e - a), dtype=torch.complex64, device="cuda")
+    pc = torch.zeros((1, e - a), dtype=torch.int16, device="cuda")
+    cout = torch.zeros((1, 2), dtype=torch.int32, device="cuda")
+    s2 = torch.zeros(1, dtype=torch.float64, device="cuda")
+    r.unwrap(_dev(y[None]), _dev(b[None]), a, e, _dev(carry), z, pc, cout, s2)
+    torch.cuda.synchronize()
+    S = fmt.sym_order
+    code = pc[0].cpu().numpy().astype(np.int64) & 0xFFFF
+    assert np.array_equal(code & 255, res.b[a:e])
+    assert np.array_equal(code >> 8, res.m[a:e] % S)
+    assert cout[0, 0].item() % S == res.m[e - 1] % S and cout[0, 1].item() == res.b[e - 1]
+    gz = z[0].cpu().numpy()
+    assert np.max(np.abs(gz - res.z[:, a:e])) < 1e-5 * np.max(np.abs(res.z[:, a:e]))
+    assert abs(s2.item() / res.sigma2[1] - 1) < 1e-5
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_demap_parity(case):
+    st, p, res = _oracle_run(case)
+    r = _receiver(case)
+    fmt = oracle_format(CASES[case][0])
+    z = res.z.astype(np.complex64)
+    K = z.shape[1]
+    s2 = 0.07
+    llr = torch.zeros((1, K, fmt.m), dtype=torch.float32, device="cuda")
+    r.demap(_dev(z[None]), torch.tensor([s2], dtype=torch.float64, device="cuda"), llr)
+    ref = chain.llr(z.astype(np.complex128), s2, fmt)
+    g = llr[0].cpu().numpy().astype(np.float64)
+    err = np.abs(g - ref)
+    assert np.all(err <= LLR_RTOL * np.maximum(1.0, np.abs(ref)))
+
+
+def test_demap_extreme_llrs():
+    """Far points: subset sums beyond the float range use their own shift."""
+    rx = _rx()
+    fmt = oracle_format("gs4d64")
+    rng = np.random.default_rng(5)
+    bits = rng.integers(0, 2, size=(512, 6), dtype=np.uint8)
+    z = fmt.symbols_from_bits(bits) + 0.02 * (rng.standard_normal((2, 512)) + 1j * rng.standard_normal((2, 512)))
+    z = z.astype(np.complex64)
+    r = rx.Receiver("gs4d64", taps=31, bps_phases=64)
+    for s2 in (1e-3, 3e-3):
+        llr = torch.zeros((1, 512, 6), dtype=torch.float32, device="cuda")
+        r.demap(_dev(z[None]), torch.tensor([s2], dtype=torch.float64, device="cuda"), llr)
+        ref = chain.llr(z.astype(np.complex128), s2, fmt)
+        g = llr[0].cpu().numpy().astype(np.float64)
+        assert np.abs(ref).max() > 300
+        assert np.all(np.abs(g - ref) <= LLR_RTOL * np.maximum(1.0, np.abs(ref)))
+
+
+@pytest.mark.parametrize("case", list(CASES))
+def test_chain_end_to_end(case):
+    """rx_process against the oracle's block schedule on the same stream."""
+    st, p, res = _oracle_run(case)
+    r = _receiver(case)
+    fmt = oracle_format(CASES[case][0])
+    r.set_reference(_dev(st.bits[None]))
+    llr, stats = r.process(_dev(st.rx[None]))
+    g = llr[0].cpu().numpy().astype(np.float64)
+    ref = res.llr
+    # near-ties of the phase search (either phase valid) are compared by validity only
+    tie = res.bps_gap < TIE
+    ok = ~tie
+    err = np.abs(g - ref)
+    tol = LLR_RTOL * np.maximum(1.0, np.abs(ref))
+    bad = (err > tol) & ok[:, None]
+    assert bad.sum() == 0, f"{bad.any(axis=1).sum()} symbols outside tolerance"
+    # hard decisions identical except where the oracle's |LLR| < 1e-4
+    hd = ((g < 0) != (ref < 0)) & (np.abs(ref) >= 1e-4) & ok[:, None]
+    assert hd.sum() == 0
+    # counting: bit errors of the GPU's own hard decisions are exact
+    c0, c1 = p.skip_head, ref.shape[0] - p.skip_tail
+    mine = int(np.sum((g[c0:c1] < 0).astype(np.uint8) != st.bits[c0:c1]))
+    assert stats[0]["bit_errors"] == mine
+    if not tie[c0:c1].any():
+        assert stats[0]["bit_errors"] == res.stats["bit_errors"]
+    assert abs(stats[0]["gmi"] - res.stats["gmi"]) < 1e-4 * fmt.m
