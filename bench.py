@@ -1,0 +1,333 @@
+#!/usr/bin/env python3
+"""Receiver throughput benchmark: Rx line rate in Gbit/s of LLRs out.
+
+Workload (one step): the 4D 64-ary GS format over 1000 km of SSMF
+(D*L = 17000 ps/nm), 28 GBd, 2 samples per symbol, a random 2x2
+polarisation rotation, laser phase noise linewidth*Ts = 2e-5, and the Es/N0
+sweep 8..16 dB in 1 dB steps: 9 independent streams of 2^20 4D symbols,
+processed by one handle (FFT 4096 / overlap 1024, 31 taps, BPS with 64
+test phases and window 64, blocks of 2^16 symbols with 1024 LMS updates,
+tap lag 2).  Inputs (9 x 32 MiB) are larger than L2, so no flush is used.
+
+value: 9 * 2^20 * 6 LLR bits per step / device time per step.
+e2e:   the same metric through rx_process_host (samples and reference bits
+       copied in from pinned host memory, LLRs copied out, every step).
+--impl reference times the FP64 CPU oracle on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2108_07004_gb300 import synth  # noqa: E402
+
+METRIC = "Rx line rate Gbit/s (LLRs out) per GB300 at oracle-matched BER; p99 block latency"
+WL = dict(workload="gs4d64_1000km_esn0_8to16dB", fmt="gs4d64", n_sym=1 << 20,
+          esn0_db=list(range(8, 17)), cd_ps_per_nm=17000.0, linewidth_ts=2e-5,
+          symbol_rate=28e9, sps=2, fft=4096, overlap=1024, taps=31, bps_phases=64,
+          bps_window=64, block=1 << 16, n_upd=1024, lag=2, mu=1e-3, n_pre=8192,
+          cma_passes=2, n_cma=1024, n_train=1024, skip_head=16384, skip_tail=512)
+FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+
+
+def make_inputs(rank: int, n_sym: int, n_streams: int):
+    rxs, bits = [], []
+    for p in range(n_streams):
+        st = synth.make_stream(WL["fmt"], n_sym, seed=synth.stream_seed(2, p) + 1000 * rank,
+                               esn0_db=WL["esn0_db"][p % len(WL["esn0_db"])],
+                               cd_ps_per_nm=WL["cd_ps_per_nm"], linewidth_ts=WL["linewidth_ts"])
+        rxs.append(st.rx)
+        bits.append(st.bits)
+    return np.stack(rxs), np.stack(bits)
+
+
+def rx_params():
+    keys = ["fft", "overlap", "bps_window", "block", "n_upd", "lag", "mu", "n_pre",
+            "cma_passes", "n_cma", "n_train", "skip_head", "skip_tail"]
+    return {k: WL[k] for k in keys}
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu, self.proc, self.f = gpu, None, None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.flush()
+        self.f.seek(0)
+        sm, mx, reasons, n = [], [], set(), 0
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.f.read().splitlines():
+            c = [x.strip() for x in line.split(",")]
+            if len(c) < 9:
+                continue
+            try:
+                sm.append(float(c[1]))
+                mx.append(float(c[2]))
+            except ValueError:
+                continue
+            n += 1
+            for nm, v in zip(names, c[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": n}
+
+
+def parity_sample(rx_mod, torch):
+    """GPU chain vs oracle on one truncated stream (first 2^14 symbols of the
+    12 dB stream): the bench's own check that its path matches the oracle."""
+    from oracle import chain, oracle_format
+    n = 1 << 14
+    st = synth.make_stream(WL["fmt"], n, seed=synth.stream_seed(2, 4), esn0_db=12.0,
+                           cd_ps_per_nm=WL["cd_ps_per_nm"], linewidth_ts=WL["linewidth_ts"])
+    p = chain.RxParams(cd_ps_per_nm=WL["cd_ps_per_nm"], n_fft=WL["fft"], n_ov=WL["overlap"],
+                       taps=WL["taps"], bps_phases=WL["bps_phases"], block=WL["block"],
+                       n_upd=WL["n_upd"], lag=WL["lag"], n_pre=WL["n_pre"],
+                       skip_head=2048, skip_tail=512)
+    res = chain.run_chain(st.rx, oracle_format(WL["fmt"]), p, ref_bits=st.bits)
+    r = rx_mod.Receiver(WL["fmt"], cd_ps_per_nm=WL["cd_ps_per_nm"], taps=WL["taps"],
+                        bps_phases=WL["bps_phases"], **{**rx_params(), "skip_head": 2048})
+    r.set_reference(torch.from_numpy(st.bits[None]).cuda())
+    llr, stats = r.process(torch.from_numpy(st.rx[None]).cuda())
+    g = llr[0].cpu().numpy().astype(np.float64)
+    ok = res.bps_gap >= 1e-5
+    rel = (np.abs(g - res.llr) / np.maximum(1.0, np.abs(res.llr)))[ok]
+    r.close()
+    return {"sample": "first 2^14 symbols of the 12 dB stream, one stream",
+            "max_rel_llr_err": float(rel.max()), "tol": 1e-4, "ok": bool(rel.max() <= 1e-4),
+            "near_tie_symbols": int((~ok).sum()),
+            "bit_errors_gpu": int(stats[0]["bit_errors"]),
+            "bit_errors_oracle": int(res.stats["bit_errors"])}
+
+
+def cpu_baseline(n_sym: int):
+    """The FP64 oracle as it stands, single process, on one stream."""
+    from oracle import chain, oracle_format
+    st = synth.make_stream(WL["fmt"], n_sym, seed=synth.stream_seed(2, 4), esn0_db=12.0,
+                           cd_ps_per_nm=WL["cd_ps_per_nm"], linewidth_ts=WL["linewidth_ts"])
+    p = chain.RxParams(cd_ps_per_nm=WL["cd_ps_per_nm"], n_fft=WL["fft"], n_ov=WL["overlap"],
+                       taps=WL["taps"], bps_phases=WL["bps_phases"], block=WL["block"],
+                       n_upd=WL["n_upd"], lag=WL["lag"], n_pre=WL["n_pre"])
+    t0 = time.perf_counter()
+    chain.run_chain(st.rx, oracle_format(WL["fmt"]), p, ref_bits=st.bits)
+    dt = time.perf_counter() - t0
+    return n_sym * 6 / dt / 1e9, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    n = args.ref_sym
+    for _ in range(args.warmup):
+        cpu_baseline(n)
+    times = []
+    for _ in range(args.steps):
+        v, dt = cpu_baseline(n)
+        times.append(dt)
+    tot = sum(times)
+    val = args.steps * n * 6 / tot / 1e9
+    line = {"metric": METRIC, "value": val, "unit": "Gbit/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": WL["workload"], "sample_symbols": n, "streams": 1},
+            "cpu_baseline": {"value": val, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
+                             "sample": f"one stream of {n} 4D symbols (12 dB) per step"},
+            "e2e": {"value": val, "unit": "Gbit/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    from paper_2108_07004_gb300 import rx as rx_mod
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    n_sym, S = args.n_sym, args.streams
+    rx_h, bits_h = make_inputs(rank, n_sym, S)
+    samples = torch.from_numpy(rx_h).cuda()
+    bits = torch.from_numpy(bits_h).cuda()
+    r = rx_mod.Receiver(WL["fmt"], cd_ps_per_nm=WL["cd_ps_per_nm"], taps=WL["taps"],
+                        bps_phases=WL["bps_phases"], streams=S, **rx_params())
+    r.set_reference(bits)
+    llr = torch.empty((S, n_sym, 6), dtype=torch.float32, device="cuda")
+    r.set("profile", 1)
+    for _ in range(args.warmup):
+        r.process(samples, llr, stats=False)
+    torch.cuda.synchronize()
+    clk = Clocks(local)
+    clk.start()
+    time.sleep(0.3)
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.steps):
+        r.process(samples, llr, stats=False)
+    ev1.record()
+    torch.cuda.synchronize()
+    barrier()
+    clocks = clk.stop()
+    ms = ev0.elapsed_time(ev1) / args.steps
+    stats = r.stats()
+    stage = {s: r.profile(s) for s in ("cdc", "fir", "bps", "unwrap", "demap", "lms", "startup")}
+    launches_per_step = r.launches()
+    lat = sorted(r.block_latency())
+    if world > 1:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+    bits_per_step = S * n_sym * 6 * world
+    value = bits_per_step / (ms * 1e-3) / 1e9
+
+    # ---- end to end through the host-buffer entry point ----
+    e2e = None
+    if not args.no_e2e:
+        s_h = torch.from_numpy(rx_h).pin_memory()
+        b_h = torch.from_numpy(bits_h).pin_memory()
+        l_h = torch.empty((S, n_sym, 6), dtype=torch.float32).pin_memory()
+        r.set("profile", 0)
+        bd = torch.empty_like(bits)
+        for _ in range(2):
+            bd.copy_(b_h, non_blocking=True)
+            r.set_reference(bd)
+            r.process_host(s_h, l_h, stats=False)
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        ke = max(3, args.steps // 4)
+        for _ in range(ke):
+            bd.copy_(b_h, non_blocking=True)
+            r.set_reference(bd)
+            r.process_host(s_h, l_h, stats=False)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / ke
+        if world > 1:
+            t = torch.tensor([dt], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            dt = t.item()
+        e2e = {"value": bits_per_step / dt / 1e9, "unit": "Gbit/s",
+               "h2d_bytes_per_step": int(rx_h.nbytes + bits_h.nbytes),
+               "d2h_bytes_per_step": int(l_h.numel() * 4), "ms_per_step": dt * 1e3}
+
+    if rank != 0:
+        return
+    pk, pk_kind = peaks()
+    bps_ms, bps_n = stage["bps"]
+    ops = S * n_sym * WL["bps_phases"] * 64            # candidate (phase, point) distances
+    peak_ops = FP32_LANES_PER_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = ops / (bps_ms * 1e-3) / 1e12 if bps_ms > 0 else None
+    cdc_ms = stage["cdc"][0]
+    cdc_bytes = S * 2 * 2 * n_sym * 8 * (WL["fft"] / (WL["fft"] - WL["overlap"]) + 1)
+    line = {
+        "metric": METRIC, "value": value, "unit": "Gbit/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WL["workload"], "streams": S, "symbols_per_stream": n_sym,
+                   "format": WL["fmt"], "fft": WL["fft"], "overlap": WL["overlap"],
+                   "taps": WL["taps"], "bps_phases": WL["bps_phases"], "block": WL["block"],
+                   "lag": WL["lag"], "l2": "inputs 9 x 32 MiB > L2, no flush"},
+        "latency": {"block_p50_ms": lat[len(lat) // 2] if lat else None,
+                    "block_p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
+                    "blocks_per_step": len(lat)},
+        "roofline": {"bound": "alu", "kernel": "bps", "achieved": achieved, "peak": peak_ops,
+                     "unit": "Top/s", "frac": (achieved / peak_ops) if achieved else None,
+                     "traffic": None,
+                     "op": "one (test phase, constellation point) candidate distance",
+                     "peak_from": "128 FP32 lanes x 152 SMs x 2070 MHz"},
+        "stages_ms": {k: v[0] for k, v in stage.items()},
+        "stage_hbm": {"cdc": {"achieved_gbs": cdc_bytes / (cdc_ms * 1e-3) / 1e9 if cdc_ms else None,
+                              "peak_gbs": pk.get("hbm_gbs"), "peak_kind": pk_kind}},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "clocks": clocks,
+        "stats": [{"esn0_db": WL["esn0_db"][i % 9], "ber": s["ber"], "gmi": s["gmi"],
+                   "sigma2": s["sigma2_last"]} for i, s in enumerate(stats)],
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_parity and world == 1:
+        line["parity"] = parity_sample(rx_mod, torch)
+    if not args.no_cpu_baseline and world == 1:
+        v, dt = cpu_baseline(args.cpu_sym)
+        line["cpu_baseline"] = {"value": v, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one stream of {args.cpu_sym} 4D symbols (12 dB), "
+                                          f"{dt:.1f} s"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n-sym", type=int, default=WL["n_sym"])
+    ap.add_argument("--streams", type=int, default=len(WL["esn0_db"]))
+    ap.add_argument("--cpu-sym", type=int, default=1 << 17)
+    ap.add_argument("--ref-sym", type=int, default=1 << 14)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-parity", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -109,7 +109,7 @@ void rx_destroy(rx_handle *h);                      /* NULL-safe */
  *   "n_pre" [8192], "cma_passes" [2], "n_cma" [1024], "n_train" [1024],
  *   "sigma2" [0 = estimate per block], "skip_head" [4096],
  *   "skip_tail" [512], "streams" [1], "rolloff" [0.1],
- *   "wavelength_nm" [1550].
+ *   "wavelength_nm" [1550], "profile" [0] (1: time every launch).
  * Changing a parameter resets the stream state (rx_reset). */
 int rx_set_param(rx_handle *h, const char *key, double value);
 int rx_get_param(const rx_handle *h, const char *key, double *value);
@@ -149,6 +149,18 @@ int rx_process_host(rx_handle *h, const void *samples, size_t n_samples,
 
 /* Statistics of the last rx_process (host [S]); synchronises. */
 int rx_get_stats(rx_handle *h, rx_stats *stats);
+
+/* Device time of the last rx_process per stage, from CUDA events recorded
+ * around every launch on its own stream when the parameter "profile" is 1
+ * (launch counts are kept always).  stage: "cdc", "fir", "bps", "unwrap",
+ * "demap", "lms", "startup" or "all".  ms_total may be NULL; synchronises
+ * the device when it is not. */
+int rx_get_profile(rx_handle *h, const char *stage, double *ms_total, uint64_t *launches);
+
+/* Per-block latency of the last rx_process (profile = 1): device time from
+ * the start of a block's FIR to the end of its demapping, in ms, for up to
+ * cap blocks; *n receives the number of blocks.  ms may be NULL to query. */
+int rx_get_block_latency(rx_handle *h, double *ms, size_t cap, size_t *n);
 
 /* Serialise / restore the per-stream state (taps ring, LMS count, unwrap
  * carry, block index).  *len in: capacity, out: bytes used (pass buf NULL

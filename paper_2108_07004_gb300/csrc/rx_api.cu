@@ -97,6 +97,14 @@ struct rx_handle {
     long blocks_done = 0;
     unsigned long long u = 0;
     long cur_n = 0;
+    // profiling: CUDA events around every launch (parameter "profile")
+    bool profile = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct Rec { int stage; cudaEvent_t a, b; };
+    std::vector<Rec> recs;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> blk;
+    unsigned long long nlaunch[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // host sources of asynchronous uploads (kept alive until the next call)
     std::vector<float2> h_taps0;
     std::vector<StreamDev> h_sd0;
@@ -358,6 +366,42 @@ float2 *slot(rx_handle *h, long n) {
     return h->ring + (size_t)i * h->streams * 4 * h->T;
 }
 
+enum { ST_CDC = 0, ST_FIR, ST_BPS, ST_UNWRAP, ST_DEMAP, ST_LMS, ST_STARTUP, ST_N };
+const char *kStageNames[ST_N] = {"cdc", "fir", "bps", "unwrap", "demap", "lms", "startup"};
+
+cudaEvent_t prof_event(rx_handle *h) {
+    if (h->ev_used == h->ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        h->ev_pool.push_back(e);
+    }
+    return h->ev_pool[h->ev_used++];
+}
+
+// record the start of a launch group of `stage` on stream `s`; returns a token
+cudaEvent_t prof_begin(rx_handle *h, cudaStream_t s) {
+    if (!h->profile) return nullptr;
+    cudaEvent_t e = prof_event(h);
+    if (e) cudaEventRecord(e, s);
+    return e;
+}
+
+void prof_end(rx_handle *h, int stage, cudaEvent_t a, cudaStream_t s, int launches) {
+    h->nlaunch[stage] += launches;
+    if (!h->profile || !a) return;
+    cudaEvent_t b = prof_event(h);
+    if (!b) return;
+    cudaEventRecord(b, s);
+    h->recs.push_back({stage, a, b});
+}
+
+#define STAGE(stage, stream, nl, call)                  \
+    do {                                               \
+        cudaEvent_t ev_a_ = prof_begin(h, stream);     \
+        CK(call);                                      \
+        prof_end(h, stage, ev_a_, stream, nl);         \
+    } while (0)
+
 // Run blocks [b0, b1) of S streams of N symbols whose samples are at `in`.
 int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *llr) {
     const int S = h->streams, T = h->T, L = h->lag;
@@ -379,7 +423,11 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         const long f0 = s_lo / Sk, f1 = (s_hi + Sk - 1) / Sk;
         // launch_cdc filters frames [0, nframes); offset pointers give frames [f0, f1)
         (void)f0; (void)f1;
-        CK(launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st));
+        h->ev_used = 0;
+        h->recs.clear();
+        h->blk.clear();
+        for (auto &c : h->nlaunch) c = 0;
+        STAGE(ST_CDC, st, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st));
     }
     if (b0 == 0) {
         std::vector<float2> &cs = h->h_taps0;
@@ -387,10 +435,11 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         float2 *w0 = slot(h, 0);
         CK(cudaMemcpyAsync(w0, cs.data(), tapsz, cudaMemcpyHostToDevice, st));
         const long npre = std::min(h->n_pre, N);
-        CK(launch_lms(h->x, ns, w0, w0, 0, (int)npre, nullptr, 0, 0, h->cma_passes, 0, 0,
-                      (float)h->mu, S, T, f, st));
+        STAGE(ST_STARTUP, st, 1, launch_lms(h->x, ns, w0, w0, 0, (int)npre, nullptr, 0, 0, h->cma_passes,
+                                            0, 0, (float)h->mu, S, T, f, st));
         if (h->ref && h->ref_n >= std::min(h->n_train, N))
-            CK(launch_align(h->x, ns, w0, h->ref, h->ref_n, (int)std::min(h->n_train, N), S, T, f, st));
+            STAGE(ST_STARTUP, st, 1, launch_align(h->x, ns, w0, h->ref, h->ref_n,
+                                                  (int)std::min(h->n_train, N), S, T, f, st));
         for (int i = 1; i <= L; ++i) CK(cudaMemcpyAsync(slot(h, i), w0, tapsz, cudaMemcpyDeviceToDevice, st));
         std::vector<StreamDev> &sd0 = h->h_sd0;
         sd0.assign(S, StreamDev{});
@@ -421,19 +470,26 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         if (L >= 2 && n >= L) CK(cudaStreamWaitEvent(st, h->ev_lms[(n - L) % (L + 1)], 0));
         // W_n = U_{n-lag}; for n < lag the slot read has not been written since start-up (W_0)
         const float2 *wn = slot(h, n - L);
-        CK(launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st));
+        cudaEvent_t blk0 = nullptr;
+        if (h->profile && (blk0 = prof_event(h))) CK(cudaEventRecord(blk0, st));
+        STAGE(ST_FIR, st, 1, launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st));
         const long a = std::max(0L, k0 - h->W / 2);
         const long e = (n == nblk - 1) ? N : k1 - h->W / 2;
-        CK(launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, h->dsum, S, f, st));
+        STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, h->dsum, S, f, st));
         const int cin = (int)(n & 1), cout = 1 - cin;
-        CK(launch_unwrap(h->y, N, h->bidx, N, a, a, e, h->dsum, carry_base + 2 * cin,
-                         (int)sd_stride, carry_base + 2 * cout, (int)sd_stride, h->z, N, a,
-                         h->pcode, N, a, h->part_u, h->sig, 1,
-                         &h->sd[0].ticket_unwrap, (int)(sizeof(StreamDev) / sizeof(unsigned)),
-                         S, f, st));
+        STAGE(ST_UNWRAP, st, 1,
+              launch_unwrap(h->y, N, h->bidx, N, a, a, e, h->dsum, carry_base + 2 * cin,
+                            (int)sd_stride, carry_base + 2 * cout, (int)sd_stride, h->z, N, a,
+                            h->pcode, N, a, h->part_u, h->sig, 1,
+                            &h->sd[0].ticket_unwrap, (int)(sizeof(StreamDev) / sizeof(unsigned)),
+                            S, f, st));
         const double *s2 = h->sigma2_fixed > 0 ? h->sig_fixed : h->sig;
         if ((e - a + 255) / 256 > h->cap_pd) return fail(RX_EINVAL, "internal: demap partials");
-        CK(launch_demap(h->z, N, a, a, e, s2, 1, llr + (size_t)a * m, N * m, cnt, S, f, st));
+        STAGE(ST_DEMAP, st, 1, launch_demap(h->z, N, a, a, e, s2, 1, llr + (size_t)a * m, N * m, cnt, S, f, st));
+        if (blk0) {
+            cudaEvent_t blk1 = prof_event(h);
+            if (blk1) { CK(cudaEventRecord(blk1, st)); h->blk.push_back({blk0, blk1}); }
+        }
         const long span = std::max(0L, std::min((long)h->n_upd, N - k0));
         cudaStream_t ls = st;
         if (L >= 2) {
@@ -441,8 +497,9 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
             CK(cudaStreamWaitEvent(h->side, h->ev_unwrap, 0));
             ls = h->side;
         }
-        CK(launch_lms(h->x, ns, slot(h, n - 1), slot(h, n), k0, (int)span, h->pcode, N, 2, 1,
-                      h->u, (int)h->n_cma, (float)h->mu, S, T, f, ls));
+        STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
+              launch_lms(h->x, ns, slot(h, n - 1), slot(h, n), k0, (int)span, h->pcode, N, 2, 1,
+                         h->u, (int)h->n_cma, (float)h->mu, S, T, f, ls));
         if (L >= 2) CK(cudaEventRecord(h->ev_lms[n % (L + 1)], h->side));
         h->u += span;
         h->blocks_done = n + 1;
@@ -499,6 +556,7 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     else if (k == "streams") { rc = as_int(1, 4096, t); h->streams = (int)t; }
     else if (k == "rolloff") { if (!(v > 0 && v <= 1)) return fail(RX_EINVAL, "rolloff out of range"); h->rolloff = v; h->tables_dirty = true; }
     else if (k == "wavelength_nm") { if (!(v > 100 && v < 10000)) return fail(RX_EINVAL, "wavelength out of range"); h->wavelength = v * 1e-9; h->tables_dirty = true; }
+    else if (k == "profile") { h->profile = v != 0; return RX_OK; }
     else return fail(RX_EINVAL, "unknown parameter '%s'", k.c_str());
     if (rc != RX_OK) return rc;
     if (k == "overlap") h->tables_dirty = true;
@@ -553,6 +611,7 @@ void rx_destroy(rx_handle *h) {
     if (h->side) { cudaStreamSynchronize(h->side); cudaStreamDestroy(h->side); }
     if (h->ev_unwrap) cudaEventDestroy(h->ev_unwrap);
     for (auto e : h->ev_lms) cudaEventDestroy(e);
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
     free_buffers(h);
     cudaFree(h->H);
     cudaFree(h->tw);
@@ -592,6 +651,7 @@ int rx_get_param(const rx_handle *h, const char *key, double *value) {
     else if (k == "taps") *value = h->T;
     else if (k == "bps_phases") *value = h->B;
     else if (k == "cd_ps_per_nm") *value = h->cd;
+    else if (k == "profile") *value = h->profile ? 1 : 0;
     else return fail(RX_EINVAL, "unknown parameter '%s'", key);
     return RX_OK;
 }
@@ -665,6 +725,47 @@ int rx_process_host(rx_handle *h, const void *samples, size_t n_samples, float *
     CK(cudaMemcpyAsync(llr_out, h->d_out, out_b, cudaMemcpyDeviceToHost, h->st));
     if (stats) return fill_stats(h, stats);
     CK(cudaStreamSynchronize(h->st));
+    return RX_OK;
+}
+
+int rx_get_profile(rx_handle *h, const char *stage, double *ms_total, uint64_t *launches) {
+    if (!h || !stage) return fail(RX_EINVAL, "NULL argument");
+    int id = -1;
+    const std::string k = stage;
+    if (k != "all") {
+        for (int i = 0; i < ST_N; ++i)
+            if (k == kStageNames[i]) id = i;
+        if (id < 0) return fail(RX_EINVAL, "unknown stage '%s'", stage);
+    }
+    uint64_t nl = 0;
+    for (int i = 0; i < ST_N; ++i)
+        if (id < 0 || id == i) nl += h->nlaunch[i];
+    if (launches) *launches = nl;
+    if (ms_total) {
+        *ms_total = 0.0;
+        if (!h->recs.empty()) {
+            CK(cudaDeviceSynchronize());
+            for (const auto &r : h->recs) {
+                if (id >= 0 && r.stage != id) continue;
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, r.a, r.b));
+                *ms_total += ms;
+            }
+        }
+    }
+    return RX_OK;
+}
+
+int rx_get_block_latency(rx_handle *h, double *ms, size_t cap, size_t *n) {
+    if (!h || !n) return fail(RX_EINVAL, "NULL argument");
+    *n = h->blk.size();
+    if (!ms) return RX_OK;
+    if (!h->blk.empty()) CK(cudaDeviceSynchronize());
+    for (size_t i = 0; i < h->blk.size() && i < cap; ++i) {
+        float v = 0.f;
+        CK(cudaEventElapsedTime(&v, h->blk[i].first, h->blk[i].second));
+        ms[i] = v;
+    }
     return RX_OK;
 }
 

@@ -54,6 +54,8 @@ _PROTOS = {
     "rx_process": (_I, [_VP, _VP, _SZ, _VP, _VP]),
     "rx_process_host": (_I, [_VP, _VP, _SZ, _VP, _VP]),
     "rx_get_stats": (_I, [_VP, _VP]),
+    "rx_get_profile": (_I, [_VP, C.c_char_p, C.POINTER(_D), C.POINTER(C.c_uint64)]),
+    "rx_get_block_latency": (_I, [_VP, C.POINTER(_D), _SZ, C.POINTER(_SZ)]),
     "rx_get_state": (_I, [_VP, _VP, C.POINTER(_SZ)]),
     "rx_set_state": (_I, [_VP, _VP, _SZ]),
     "rx_format_info": (_I, [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
@@ -194,6 +196,24 @@ class Receiver:
         st = (RxStats * S)()
         _ck(lib().rx_get_stats(self.h, C.cast(st, C.c_void_p)))
         return [s.as_dict() for s in st]
+
+    def profile(self, stage: str = "all") -> tuple[float, int]:
+        """(device ms, launches) of the last process() for one stage."""
+        ms, n = C.c_double(), C.c_uint64()
+        _ck(lib().rx_get_profile(self.h, stage.encode(), C.byref(ms), C.byref(n)))
+        return ms.value, n.value
+
+    def launches(self) -> int:
+        n = C.c_uint64()
+        _ck(lib().rx_get_profile(self.h, b"all", None, C.byref(n)))
+        return n.value
+
+    def block_latency(self) -> list[float]:
+        n = C.c_size_t()
+        _ck(lib().rx_get_block_latency(self.h, None, 0, C.byref(n)))
+        buf = (C.c_double * max(1, n.value))()
+        _ck(lib().rx_get_block_latency(self.h, buf, n.value, C.byref(n)))
+        return list(buf[: n.value])
 
     def get_state(self) -> bytes:
         n = C.c_size_t(0)
