@@ -37,7 +37,7 @@ WL = dict(workload="gs4d64_1000km_esn0_8to16dB", fmt="gs4d64", n_sym=1 << 20,
           esn0_db=list(range(8, 17)), cd_ps_per_nm=17000.0, linewidth_ts=2e-5,
           symbol_rate=28e9, sps=2, fft=4096, overlap=1024, taps=31, bps_phases=64,
           bps_window=64, block=1 << 16, n_upd=1024, lag=2, mu=1e-3, n_pre=8192,
-          cma_passes=2, n_cma=1024, n_train=1024, skip_head=16384, skip_tail=512)
+          cma_passes=2, n_cma=0, n_train=1024, train_passes=2, skip_head=16384, skip_tail=512)
 FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070.0
 
 
@@ -62,7 +62,7 @@ def make_inputs(rank: int, n_sym: int, n_streams: int):
 
 def rx_params():
     keys = ["fft", "overlap", "bps_window", "block", "n_upd", "lag", "mu", "n_pre",
-            "cma_passes", "n_cma", "n_train", "skip_head", "skip_tail"]
+            "cma_passes", "n_cma", "n_train", "train_passes", "skip_head", "skip_tail"]
     return {k: WL[k] for k in keys}
 
 

@@ -106,7 +106,8 @@ void rx_destroy(rx_handle *h);                      /* NULL-safe */
  *   "fft" [1024] (1024 or 4096), "overlap" [256] (even, < fft/2),
  *   "mu" [1e-3], "bps_window" [64] (even, 2..64), "block" [4096] symbols,
  *   "n_upd" [1024] (<= block - bps_window/2), "lag" [1] (1..4),
- *   "n_pre" [8192], "cma_passes" [2], "n_cma" [1024], "n_train" [1024],
+ *   "n_pre" [8192], "cma_passes" [2], "n_cma" [0], "n_train" [1024]
+ *   (<= 20000), "train_passes" [2],
  *   "sigma2" [0 = estimate per block], "skip_head" [4096],
  *   "skip_tail" [512], "streams" [1], "rolloff" [0.1],
  *   "wavelength_nm" [1550], "profile" [0] (1: time every launch).
@@ -188,12 +189,20 @@ int rx_fir(rx_handle *h, const void *x, size_t n_samples, const void *taps,
 
 /* A3 LMS: sequential updates over symbols k0 .. k0 + n_upd - 1 of x,
  * in place on taps [S][2][2][T].  mode 0: CMA; 1: DD-LMS using the phase
- * codes pcode [S][N] (uint16: b | (m mod 4) << 8, see rx_bps_unwrap);
- * 2: CMA for updates u0 + i < n_cma, DD after.  passes > 1 repeats the
- * span (start-up). */
+ * codes pcode [S][N] (uint16: b | (m mod S) << 8, see rx_unwrap);
+ * 2: CMA for updates u0 + i < n_cma, DD after; 3: data-aided LMS with the
+ * reference symbols (rx_set_reference) in place of the decisions.
+ * passes > 1 repeats the span (start-up). */
 int rx_lms(rx_handle *h, const void *x, size_t n_samples, void *taps,
            size_t k0, size_t n_upd, const uint16_t *pcode, int mode,
            int passes, uint64_t u0);
+
+/* A3 training stage on taps [S][2][2][T] (in place), the start-up step of
+ * rx_process after CMA: output order and phases from the correlation of the
+ * equalised first n_train symbols with the reference, data-aided phase codes
+ * (written to pcode, [S][n_train] uint16) and train_passes passes of
+ * data-aided LMS.  Needs rx_set_reference. */
+int rx_train(rx_handle *h, const void *x, size_t n_samples, void *taps, uint16_t *pcode);
 
 /* A4 BPS: test-phase index b_k for a <= k < e from y [S][2][n_y] (symbols
  * 0 .. n_y - 1 of the stream), windows truncated at n_valid.  b_out:

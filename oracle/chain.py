@@ -46,8 +46,9 @@ class RxParams:
     lag: int = 1               # taps from block n's update apply from block n+lag
     n_pre: int = 8192          # start-up CMA span (symbols)
     cma_passes: int = 2
-    n_cma: int = 1024          # block-wise updates run as CMA before DD
-    n_train: int = 1024        # known symbols used to fix permutation/phase
+    n_cma: int = 0             # block-wise updates run as CMA before DD
+    n_train: int = 1024        # known training symbols at the stream start
+    train_passes: int = 2      # data-aided LMS passes over the training span
     sigma2: float | None = None  # fixed noise variance, else per-block estimate
     skip_head: int = 4096      # symbols excluded from counting at stream start
     skip_tail: int = 512       # ... and at the stream end
@@ -253,6 +254,45 @@ def align_training(x: np.ndarray, h: np.ndarray, ref_sym: np.ndarray) -> np.ndar
     return out
 
 
+def train_phase(y: np.ndarray, ref_sym: np.ndarray, W: int, B: int, S: int):
+    """Data-aided phase over the training span, on the phase-search grid.
+
+    R_k = sum over i in [k - W/2, k + W/2) (within the span) of
+    sum_p y_p[i] conj(s_p[i]); phi_k = arg R_k, rounded to the nearest
+    multiple n_k of q/B (q = 2 pi/S; round(x) = floor(x + 1/2)), written as
+    phi_k = phi_b + m q with b = n_k + B/2 - m B, m = floor((n_k + B/2)/B).
+    Reading: the paper trains the equaliser on a known sequence before it
+    runs blind (Sec. 2); the known symbols give the phase without the
+    rotational ambiguity."""
+    n = y.shape[1]
+    r = np.sum(y * np.conj(ref_sym), axis=0)
+    b = np.empty(n, dtype=np.int64)
+    m = np.empty(n, dtype=np.int64)
+    step = 2 * np.pi / S / B
+    for k in range(n):
+        R = np.sum(r[max(0, k - W // 2): min(n, k + W // 2)])
+        nk = int(np.floor(np.angle(R) / step + 0.5))
+        m[k] = (nk + B // 2) // B
+        b[k] = nk + B // 2 - m[k] * B
+    return b, m
+
+
+def lms_trained(x: np.ndarray, h: np.ndarray, ks, ref_sym: np.ndarray, phase: np.ndarray,
+                p: RxParams) -> np.ndarray:
+    """Data-aided LMS over symbols ks: e_q = s_q[k] exp(j phi_k) - y_q,
+    h_qp[t] += mu conj(e_q) x_p[2k + D - t] (the DD update with the known
+    symbol in place of the decision)."""
+    h = h.copy()
+    T = h.shape[2]
+    for k in ks:
+        xw = x_window(x, k, T)
+        y = np.array([np.sum(np.conj(h[q]) * xw) for q in range(2)])
+        e = ref_sym[:, k] * np.exp(1j * phase[k]) - y
+        for q in range(2):
+            h[q] += p.mu * np.conj(e[q]) * xw
+    return h
+
+
 # ---------------------------------------------------------------------------
 # A4: blind phase search
 # ---------------------------------------------------------------------------
@@ -397,6 +437,9 @@ class ChainResult:
     bps_gap: np.ndarray
     dd_margin: list
     stats: dict
+    train_b: np.ndarray | None = None
+    train_m: np.ndarray | None = None
+    w_cma: np.ndarray | None = None
 
 
 def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
@@ -404,8 +447,10 @@ def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
     """Whole receiver on one stream r [2, sps*N] with the block schedule:
 
     start-up: CMA over the first n_pre symbols (cma_passes passes) from the
-    identity butterfly, then (if known bits are given) the training
-    alignment over the first n_train symbols -> W_0.  Block n (symbols
+    identity butterfly; then, if known bits are given, the training stage
+    over the first n_train symbols: output order and phases from the
+    correlation with the known symbols, a data-aided phase estimate, and
+    train_passes passes of data-aided LMS -> W_0.  Block n (symbols
     n*block .. n*block+block-1):
       1. FIR with W_n = U_{n-lag} (W_0 while n < lag);
       2. BPS, unwrap, de-rotation and LLRs over the range
@@ -423,9 +468,16 @@ def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
     npre = min(p.n_pre, N)
     for _ in range(p.cma_passes):
         h = lms(x, h, range(npre), fmt, p, force_cma=True)
-    if ref_bits is not None:
+    w_cma = h.copy()
+    train_b = train_m = None
+    if ref_bits is not None and p.n_train > 0:
         ntr = min(p.n_train, N)
-        h = align_training(x, h, fmt.symbols_from_bits(ref_bits[:ntr]))
+        ref = fmt.symbols_from_bits(ref_bits[:ntr])
+        h = align_training(x, h, ref)
+        train_b, train_m = train_phase(fir(x, h, 0, ntr), ref, p.bps_window, p.bps_phases, S)
+        tphi = phase_of(train_b, train_m, p.bps_phases, S)
+        for _ in range(p.train_passes):
+            h = lms_trained(x, h, range(ntr), ref, tphi, p)
     w0 = h.copy()
     ring = [w0.copy() for _ in range(L + 1)]
     y = np.zeros((2, N), complex)
@@ -469,4 +521,4 @@ def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
         stats["evm_num"] = float(np.sum(np.abs(z[:, c0:c1] - d) ** 2))
         stats["evm_den"] = float(np.sum(np.abs(d) ** 2))
     return ChainResult(x, w0, used, after, y, bb, mm, phi_all, z, s2s, ranges, out,
-                       gap, info.dd_margin, stats)
+                       gap, info.dd_margin, stats, train_b, train_m, w_cma)

@@ -11,8 +11,8 @@
 // so the M terms are computed once; the per-bit subset sums are built as a
 // binary tree over the label bits (bit 0 splits even/odd labels, then pairs
 // are summed and bit 1 splits the pairs, ...), about 3M additions instead
-// of m*M.  A subset whose terms all lie beyond the float range below
-// 2^-100 is recomputed with its own minimum as shift (then |LLR| > 150).
+// of m*M.  A subset whose terms all lie below 2^-100 of the shift is
+// recomputed from z with its own minimum as shift (then |LLR| > 150).
 // Counting (Sec. 3 counts errors offline; here it is fused): hard bits are
 // LLR < 0, errors against the reference label, the GMI term
 // log2(1 + exp(-(1 - 2b) LLR)) per bit and the EVM sums; block partials are
@@ -25,59 +25,98 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kOff = 120.f;
 
-// log2 of the subset sum for label bit bp == v, falling back to an own-shift sum
-template <int MT>
-__device__ __forceinline__ float subset_lg(const float (&d)[MT], float g, float c2, float S,
-                                           int bp, int v) {
-    if (S >= 7.888609052e-31f)          // 2^-100
-        return __log2f(S) - kOff;
-    float dm = 3.0e38f;
-#pragma unroll
-    for (int j = 0; j < MT; ++j)
-        if (((j >> bp) & 1) == v) dm = fminf(dm, d[j]);
-    float acc = 0.f;
-#pragma unroll
-    for (int j = 0; j < MT; ++j)
-        if (((j >> bp) & 1) == v) acc += exp2f((dm - d[j]) * c2);
-    return (g - dm) * c2 + log2f(acc);
-}
-
-// LLRs of one table lookup: d[j] squared distances in label order, mb bits.
-template <int MT, int MB>
-__device__ __forceinline__ void llr_table(const float (&d)[MT], float c2, float *out, float &g,
-                                          int &jmin) {
-    g = d[0];
-    jmin = 0;
-#pragma unroll
-    for (int j = 1; j < MT; ++j)
-        if (d[j] < g) { g = d[j]; jmin = j; }
-    float cur[MT];
-#pragma unroll
-    for (int j = 0; j < MT; ++j) cur[j] = exp2f(fmaf(g - d[j], c2, kOff));
-    int n = MT;
-#pragma unroll
-    for (int bp = 0; bp < MB; ++bp) {
-        float s0 = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int i = 0; i < MT; i += 2) {
-            if (i < n) { s0 += cur[i]; s1 += cur[i + 1]; }
-        }
-        const float l0 = subset_lg<MT>(d, g, c2, s0, bp, 0);
-        const float l1 = subset_lg<MT>(d, g, c2, s1, bp, 1);
-        out[MB - 1 - bp] = (l0 - l1) * kLn2;
-#pragma unroll
-        for (int i = 0; i < MT / 2; ++i)
-            if (2 * i < n) cur[i] = cur[2 * i] + cur[2 * i + 1];
-        n >>= 1;
-    }
-}
-
 __device__ __forceinline__ float softplus_bits(float x) {   // log2(1 + exp(x))
     return (fmaxf(x, 0.f) + log1pf(expf(-fabsf(x)))) * kLog2e;
 }
 
+template <int DIMS>
+__device__ __forceinline__ float dist_to(float2 z0, float2 z1, const FmtDev &f, int j) {
+    const float a0 = z0.x - f.pts[j][0], a1 = z0.y - f.pts[j][1];
+    float d = fmaf(a0, a0, a1 * a1);
+    if (DIMS == 4) {
+        const float a2 = z1.x - f.pts[j][2], a3 = z1.y - f.pts[j][3];
+        d = fmaf(a2, a2, fmaf(a3, a3, d));
+    }
+    return d;
+}
+
+// Rare path, for a lookup where some bit's subset sum fell below 2^-100 of
+// the common shift: every subset gets its own minimum as shift.  Rewrites
+// out[] and the counting terms of this lookup.
 template <int DIMS, int MT, int MB>
-__global__ void __launch_bounds__(256)
+__device__ __noinline__ void llr_table_slow(float2 z0, float2 z1, const FmtDev &f, float c2,
+                                            float *out, int ref, int *nerr, float *gs) {
+    int ne = 0;
+    float g2 = 0.f;
+    for (int bp = 0; bp < MB; ++bp) {
+        float lg[2];
+        for (int v = 0; v < 2; ++v) {
+            float dm = 3.0e38f;
+            for (int j = 0; j < MT; ++j)
+                if (((j >> bp) & 1) == v) dm = fminf(dm, dist_to<DIMS>(z0, z1, f, j));
+            float acc = 0.f;
+            for (int j = 0; j < MT; ++j)
+                if (((j >> bp) & 1) == v) acc += exp2f((dm - dist_to<DIMS>(z0, z1, f, j)) * c2);
+            lg[v] = -dm * c2 + log2f(acc);
+        }
+        const float L = (lg[0] - lg[1]) * kLn2;
+        out[MB - 1 - bp] = L;
+        if (ref >= 0) {
+            const int bit = (ref >> bp) & 1;
+            ne += (int)((L < 0.f) != (bit != 0));
+            g2 += softplus_bits(bit ? L : -L);
+        }
+    }
+    *nerr = ne;
+    *gs = g2;
+}
+
+// LLRs of one table lookup of z (DIMS 4: joint; DIMS 2: z0 alone), MB bits,
+// written to out[0..MB-1] (MSB first).  When ref >= 0 (the reference label of
+// this lookup) the hard-decision errors and the GMI terms are accumulated.
+template <int DIMS, int MT, int MB>
+__device__ __forceinline__ void llr_table(float2 z0, float2 z1, const FmtDev &f, float c2,
+                                          float *out, float &g, int &jmin, int ref, int &nerr,
+                                          float &gs) {
+    float cur[MT];
+#pragma unroll
+    for (int j = 0; j < MT; ++j) cur[j] = dist_to<DIMS>(z0, z1, f, j);
+    g = cur[0];
+    jmin = 0;
+#pragma unroll
+    for (int j = 1; j < MT; ++j)
+        if (cur[j] < g) { g = cur[j]; jmin = j; }
+#pragma unroll
+    for (int j = 0; j < MT; ++j) cur[j] = exp2f(fmaf(g - cur[j], c2, kOff));
+    bool low = false;
+    int ne = 0;
+    float g2 = 0.f;
+#pragma unroll
+    for (int bp = 0; bp < MB; ++bp) {
+        const int n = MT >> bp;
+        float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+        for (int i = 0; i < MT; i += 2)
+            if (i < n) { s0 += cur[i]; s1 += cur[i + 1]; }
+        low |= (s0 < 7.888609052e-31f) | (s1 < 7.888609052e-31f);   // 2^-100
+        const float L = (__log2f(s0) - __log2f(s1)) * kLn2;
+        out[MB - 1 - bp] = L;
+        if (ref >= 0) {
+            const int bit = (ref >> bp) & 1;
+            ne += (int)((L < 0.f) != (bit != 0));
+            g2 += softplus_bits(bit ? L : -L);
+        }
+#pragma unroll
+        for (int i = 0; i < MT / 2; ++i)
+            if (2 * i < n) cur[i] = cur[2 * i] + cur[2 * i + 1];
+    }
+    if (low) llr_table_slow<DIMS, MT, MB>(z0, z1, f, c2, out, ref, &ne, &g2);
+    nerr += ne;
+    gs += g2;
+}
+
+template <int DIMS, int MT, int MB>
+__global__ void __launch_bounds__(256, 2)
 demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
              const double *__restrict__ sigma2, int s2_stride, float *__restrict__ llr,
              long llr_stride, DemapCount cnt, const __grid_constant__ FmtDev f) {
@@ -95,19 +134,15 @@ demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
     double gsum = 0.0, en = 0.0, ed = 0.0;
     if (k < e) {
         const float2 z0 = zx[k - a], z1 = zy[k - a];
-        float L[M_OUT];
-        float dist_min, dmin_energy;
+        const bool counted = cnt.ref_lab && k >= cnt.c0 && k < cnt.c1;
+        const int ref = counted ? (int)cnt.ref_lab[(long)s * cnt.ref_stride + k] : -1;
+        float *row = llr + (long)s * llr_stride + (k - a) * M_OUT;
+        int ne = 0;
+        float gs = 0.f, dist_min, dmin_energy;
         if (DIMS == 4) {
-            float d[MT];
-#pragma unroll
-            for (int j = 0; j < MT; ++j) {
-                const float a0 = z0.x - f.pts[j][0], a1 = z0.y - f.pts[j][1];
-                const float a2 = z1.x - f.pts[j][2], a3 = z1.y - f.pts[j][3];
-                d[j] = fmaf(a0, a0, fmaf(a1, a1, fmaf(a2, a2, a3 * a3)));
-            }
             float g;
             int jm;
-            llr_table<MT, MB>(d, c2, L, g, jm);
+            llr_table<4, MT, MB>(z0, z1, f, c2, row, g, jm, ref, ne, gs);
             dist_min = g;
             dmin_energy = f.pe[jm];
         } else {
@@ -116,33 +151,16 @@ demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
                 const float2 zp = p ? z1 : z0;
-                float d[MT];
-#pragma unroll
-                for (int j = 0; j < MT; ++j) {
-                    const float a0 = zp.x - f.pts[j][0], a1 = zp.y - f.pts[j][1];
-                    d[j] = fmaf(a0, a0, a1 * a1);
-                }
+                const int rp = ref < 0 ? -1 : (p ? (ref & ((1 << MB) - 1)) : (ref >> MB));
                 float g;
                 int jm;
-                llr_table<MT, MB>(d, c2, L + p * MB, g, jm);
+                llr_table<2, MT, MB>(zp, zp, f, c2, row + p * MB, g, jm, rp, ne, gs);
                 dist_min += g;
                 dmin_energy += f.pe[jm];
             }
         }
-        float *row = llr + (long)s * llr_stride + (k - a) * M_OUT;
-#pragma unroll
-        for (int i = 0; i < M_OUT; ++i) row[i] = L[i];
-        if (cnt.ref_lab && k >= cnt.c0 && k < cnt.c1) {
-            const int ref = cnt.ref_lab[(long)s * cnt.ref_stride + k];
-            int hard = 0;
-            float gs = 0.f;
-#pragma unroll
-            for (int i = 0; i < M_OUT; ++i) {
-                const int bit = (ref >> (M_OUT - 1 - i)) & 1;
-                hard = (hard << 1) | (L[i] < 0.f ? 1 : 0);
-                gs += softplus_bits(bit ? L[i] : -L[i]);
-            }
-            nerr = __popc(hard ^ ref);
+        if (counted) {
+            nerr = ne;
             ncnt = 1;
             gsum = gs;
             en = dist_min;

@@ -99,12 +99,13 @@ __global__ void __launch_bounds__(256)
 lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ taps_in,
            float2 *__restrict__ taps_out, long k0, int n_upd, const uint16_t *__restrict__ pcode,
            long pcode_stride, int mode, int passes, unsigned long long u0, int n_cma, float mu,
-           const __grid_constant__ FmtDev f) {
+           const uint8_t *__restrict__ ref_lab, long ref_stride, const __grid_constant__ FmtDev f) {
     constexpr int D = (T - 1) / 2;
     constexpr int NSX = 2 * kCH + 2 * D;
     constexpr int NT = (T + 7) / 8;
     __shared__ float2 xs[2][NSX];
     __shared__ uint16_t pc[kCH];
+    __shared__ uint8_t rl[kCH];
     __shared__ Tables tb;
     const int s = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -133,6 +134,9 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
             if (mode != 0)
                 for (int i = threadIdx.x; i < n; i += blockDim.x)
                     pc[i] = pcode[(long)s * pcode_stride + kb + i];
+            if (mode == 3)
+                for (int i = threadIdx.x; i < n; i += blockDim.x)
+                    rl[i] = ref_lab[(long)s * ref_stride + kb + i];
             __syncthreads();
             if (warp != 0) continue;
 
@@ -179,8 +183,14 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
                     yo.x = __shfl_xor_sync(0xffffffffu, yq.x, 16);
                     yo.y = __shfl_xor_sync(0xffffffffu, yq.y, 16);
                     const float2 y0 = q ? yo : yq, y1 = q ? yq : yo;
-                    const float2 z0 = cmulc(r, y0), z1 = cmulc(r, y1), zq = cmulc(r, yq);
-                    const int lab = decide_warp<DIMS>(z0, z1, zq, tb, f, lane);
+                    int lab;
+                    if (mode == 3) {          // data-aided: the known symbol
+                        lab = rl[kk];
+                        if (DIMS == 2) lab = q ? (lab & ((1 << f.m_pol) - 1)) : (lab >> f.m_pol);
+                    } else {
+                        const float2 z0 = cmulc(r, y0), z1 = cmulc(r, y1), zq = cmulc(r, yq);
+                        lab = decide_warp<DIMS>(z0, z1, zq, tb, f, lane);
+                    }
                     const float4 pt = tb.pts[lab];
                     float2 d;
                     if (DIMS == 4) d = q ? make_float2(pt.z, pt.w) : make_float2(pt.x, pt.y);
@@ -282,6 +292,58 @@ align_kernel(const float2 *__restrict__ x, long ns, float2 *__restrict__ taps,
     }
 }
 
+// Data-aided phase codes over the training span [0, n):
+//   R_k = sum_{i in [k - W/2, k + W/2) within the span} sum_p y_p[i] conj(s_p[i]),
+//   n_k = floor(arg(R_k) / (2 pi / (S B)) + 1/2), code = b | (m mod S) << 8 with
+//   b = n_k + B/2 - m B, m = floor((n_k + B/2) / B).
+template <int T, int DIMS>
+__global__ void __launch_bounds__(256)
+train_phase_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ taps,
+                   const uint8_t *__restrict__ ref_lab, long ref_stride, int n, int W,
+                   uint16_t *__restrict__ pcode, long pcode_stride, const __grid_constant__ FmtDev f) {
+    constexpr int D = (T - 1) / 2;
+    extern __shared__ float2 rs[];      // [n] per-symbol correlations
+    __shared__ float2 hs[4 * T];
+    const int s = blockIdx.x, tid = threadIdx.x;
+    for (int i = tid; i < 4 * T; i += 256) hs[i] = taps[(long)s * 4 * T + i];
+    __syncthreads();
+    const float2 *xs = x + (long)s * 2 * ns;
+    for (int k = tid; k < n; k += 256) {
+        float2 y[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        for (int qq = 0; qq < 2; ++qq)
+            for (int pp = 0; pp < 2; ++pp)
+                for (int t = 0; t < T; ++t) {
+                    const long g = 2L * k + D - t;
+                    if (g < 0 || g >= ns) continue;
+                    y[qq] = cadd(y[qq], cmulc(hs[(qq * 2 + pp) * T + t], xs[(long)pp * ns + g]));
+                }
+        const int lab = ref_lab[(long)s * ref_stride + k];
+        float2 s0, s1;
+        if (DIMS == 4) {
+            s0 = make_float2(f.pts[lab][0], f.pts[lab][1]);
+            s1 = make_float2(f.pts[lab][2], f.pts[lab][3]);
+        } else {
+            const int lx = lab >> f.m_pol, ly = lab & ((1 << f.m_pol) - 1);
+            s0 = make_float2(f.pts[lx][0], f.pts[lx][1]);
+            s1 = make_float2(f.pts[ly][0], f.pts[ly][1]);
+        }
+        rs[k] = cadd(cmulc(s0, y[0]), cmulc(s1, y[1]));   // sum_p y_p conj(s_p)
+    }
+    __syncthreads();
+    const int B = f.B, S = f.S;
+    const double step = 2.0 * 3.14159265358979323846 / ((double)S * B);
+    for (int k = tid; k < n; k += 256) {
+        float2 R = make_float2(0.f, 0.f);
+        const int i0 = max(0, k - W / 2), i1 = min(n, k + W / 2);
+        for (int i = i0; i < i1; ++i) R = cadd(R, rs[i]);
+        const int nk = (int)floor((double)atan2f(R.y, R.x) / step + 0.5);
+        const int m = (int)floor((double)(nk + B / 2) / B);
+        const int b = nk + B / 2 - m * B;
+        const int mq = ((m % S) + S) % S;
+        pcode[(long)s * pcode_stride + k] = (uint16_t)(b | (mq << 8));
+    }
+}
+
 __global__ void ref_labels_kernel(const uint8_t *__restrict__ bits, uint8_t *__restrict__ lab,
                                   long n, int m) {
     const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -296,14 +358,15 @@ __global__ void ref_labels_kernel(const uint8_t *__restrict__ bits, uint8_t *__r
 template <int T>
 cudaError_t lms_dispatch_dims(const float2 *x, long ns, const float2 *ti, float2 *to, long k0,
                               int n_upd, const uint16_t *pcode, long pstride, int mode,
-                              int passes, unsigned long long u0, int n_cma, float mu, int S,
-                              const FmtDev &f, cudaStream_t st) {
+                              int passes, unsigned long long u0, int n_cma, float mu,
+                              const uint8_t *ref, long rstride, int S, const FmtDev &f,
+                              cudaStream_t st) {
     if (f.dims == 4)
         lms_kernel<T, 4><<<S, 256, 0, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, mode, passes,
-                                            u0, n_cma, mu, f);
+                                            u0, n_cma, mu, ref, rstride, f);
     else
         lms_kernel<T, 2><<<S, 256, 0, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, mode, passes,
-                                            u0, n_cma, mu, f);
+                                            u0, n_cma, mu, ref, rstride, f);
     return cudaGetLastError();
 }
 
@@ -321,8 +384,8 @@ cudaError_t align_dispatch(const float2 *x, long ns, float2 *taps, const uint8_t
 
 cudaError_t launch_lms(const float2 *x, long ns, const float2 *taps_in, float2 *taps_out, long k0,
                        int n_upd, const uint16_t *pcode, long pcode_stride, int mode, int passes,
-                       unsigned long long u0, int n_cma, float mu, int n_streams, int T,
-                       const FmtDev &f, cudaStream_t st) {
+                       unsigned long long u0, int n_cma, float mu, const uint8_t *ref_lab,
+                       long ref_stride, int n_streams, int T, const FmtDev &f, cudaStream_t st) {
     if (n_upd <= 0 || n_streams <= 0) {
         if (taps_in != taps_out)
             return cudaMemcpyAsync(taps_out, taps_in, sizeof(float2) * 4 * T * (size_t)n_streams,
@@ -330,9 +393,9 @@ cudaError_t launch_lms(const float2 *x, long ns, const float2 *taps_in, float2 *
         return cudaSuccess;
     }
     switch (T) {
-        case 7: return lms_dispatch_dims<7>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, n_streams, f, st);
-        case 15: return lms_dispatch_dims<15>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, n_streams, f, st);
-        case 31: return lms_dispatch_dims<31>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, n_streams, f, st);
+        case 7: return lms_dispatch_dims<7>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st);
+        case 15: return lms_dispatch_dims<15>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st);
+        case 31: return lms_dispatch_dims<31>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -347,6 +410,32 @@ cudaError_t launch_align(const float2 *x, long ns, float2 *taps, const uint8_t *
         case 31: return align_dispatch<31>(x, ns, taps, ref_lab, ref_stride, n_train, n_streams, f, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_train_phase(const float2 *x, long ns, const float2 *taps, const uint8_t *ref_lab,
+                               long ref_stride, int n, int W, uint16_t *pcode, long pcode_stride,
+                               int n_streams, int T, const FmtDev &f, cudaStream_t st) {
+    if (n <= 0 || n_streams <= 0) return cudaSuccess;
+    const size_t smem = sizeof(float2) * (size_t)n;
+    if (smem > 160 * 1024) return cudaErrorInvalidValue;
+#define RX_TP(TT, DD)                                                                          \
+    do {                                                                                       \
+        auto k_ = train_phase_kernel<TT, DD>;                                                  \
+        cudaError_t e_ = cudaFuncSetAttribute(k_, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                              (int)smem);                                     \
+        if (e_ != cudaSuccess) return e_;                                                      \
+        k_<<<n_streams, 256, smem, st>>>(x, ns, taps, ref_lab, ref_stride, n, W, pcode,        \
+                                         pcode_stride, f);                                     \
+    } while (0)
+    const bool d4 = f.dims == 4;
+    switch (T) {
+        case 7: if (d4) RX_TP(7, 4); else RX_TP(7, 2); break;
+        case 15: if (d4) RX_TP(15, 4); else RX_TP(15, 2); break;
+        case 31: if (d4) RX_TP(31, 4); else RX_TP(31, 2); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef RX_TP
+    return cudaGetLastError();
 }
 
 cudaError_t launch_ref_labels(const uint8_t *bits, uint8_t *lab, long n_sym, int n_streams, int m,

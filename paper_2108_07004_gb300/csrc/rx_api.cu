@@ -62,8 +62,9 @@ struct rx_handle {
     int lag = 1;
     long n_pre = 8192;
     int cma_passes = 2;
-    long n_cma = 1024;
+    long n_cma = 0;
     long n_train = 1024;
+    int train_passes = 2;
     double sigma2_fixed = 0.0;
     long skip_head = 4096, skip_tail = 512;
     int streams = 1;
@@ -402,6 +403,23 @@ void prof_end(rx_handle *h, int stage, cudaEvent_t a, cudaStream_t s, int launch
         prof_end(h, stage, ev_a_, stream, nl);         \
     } while (0)
 
+// Training stage (Sec. 2: the equaliser converges on a known sequence before
+// it runs blind): output order and phases from the correlation with the
+// known symbols, data-aided phase codes over the span, then train_passes
+// passes of data-aided LMS.  Taps are updated in place.
+int train_stage(rx_handle *h, const float2 *x, long ns, float2 *taps, long ntr, uint16_t *pcode,
+                long pcode_stride, cudaStream_t st) {
+    const int S = h->streams, T = h->T;
+    STAGE(ST_STARTUP, st, 1, launch_align(x, ns, taps, h->ref, h->ref_n, (int)ntr, S, T, h->fmt, st));
+    STAGE(ST_STARTUP, st, 1, launch_train_phase(x, ns, taps, h->ref, h->ref_n, (int)ntr, h->W, pcode,
+                                                pcode_stride, S, T, h->fmt, st));
+    if (h->train_passes > 0)
+        STAGE(ST_STARTUP, st, 1, launch_lms(x, ns, taps, taps, 0, (int)ntr, pcode, pcode_stride, 3,
+                                            h->train_passes, 0, 0, (float)h->mu, h->ref, h->ref_n,
+                                            S, T, h->fmt, st));
+    return RX_OK;
+}
+
 // Run blocks [b0, b1) of S streams of N symbols whose samples are at `in`.
 int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *llr) {
     const int S = h->streams, T = h->T, L = h->lag;
@@ -436,10 +454,12 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         CK(cudaMemcpyAsync(w0, cs.data(), tapsz, cudaMemcpyHostToDevice, st));
         const long npre = std::min(h->n_pre, N);
         STAGE(ST_STARTUP, st, 1, launch_lms(h->x, ns, w0, w0, 0, (int)npre, nullptr, 0, 0, h->cma_passes,
-                                            0, 0, (float)h->mu, S, T, f, st));
-        if (h->ref && h->ref_n >= std::min(h->n_train, N))
-            STAGE(ST_STARTUP, st, 1, launch_align(h->x, ns, w0, h->ref, h->ref_n,
-                                                  (int)std::min(h->n_train, N), S, T, f, st));
+                                            0, 0, (float)h->mu, nullptr, 0, S, T, f, st));
+        const long ntr = std::min(h->n_train, N);
+        if (h->ref && ntr > 0 && h->ref_n >= ntr) {
+            int rc2 = train_stage(h, h->x, ns, w0, ntr, h->pcode, N, st);
+            if (rc2 != RX_OK) return rc2;
+        }
         for (int i = 1; i <= L; ++i) CK(cudaMemcpyAsync(slot(h, i), w0, tapsz, cudaMemcpyDeviceToDevice, st));
         std::vector<StreamDev> &sd0 = h->h_sd0;
         sd0.assign(S, StreamDev{});
@@ -499,7 +519,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         }
         STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
               launch_lms(h->x, ns, slot(h, n - 1), slot(h, n), k0, (int)span, h->pcode, N, 2, 1,
-                         h->u, (int)h->n_cma, (float)h->mu, S, T, f, ls));
+                         h->u, (int)h->n_cma, (float)h->mu, nullptr, 0, S, T, f, ls));
         if (L >= 2) CK(cudaEventRecord(h->ev_lms[n % (L + 1)], h->side));
         h->u += span;
         h->blocks_done = n + 1;
@@ -549,7 +569,8 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     else if (k == "n_pre") { rc = as_int(0, 1L << 30, t); h->n_pre = t; }
     else if (k == "cma_passes") { rc = as_int(0, 16, t); h->cma_passes = (int)t; }
     else if (k == "n_cma") { rc = as_int(0, 1L << 40, t); h->n_cma = t; }
-    else if (k == "n_train") { rc = as_int(0, 1L << 30, t); h->n_train = t; }
+    else if (k == "n_train") { rc = as_int(0, 20000, t); h->n_train = t; }
+    else if (k == "train_passes") { rc = as_int(0, 64, t); h->train_passes = (int)t; }
     else if (k == "sigma2") { if (!(v >= 0)) return fail(RX_EINVAL, "sigma2 < 0"); h->sigma2_fixed = v; }
     else if (k == "skip_head") { rc = as_int(0, 1L << 40, t); h->skip_head = t; }
     else if (k == "skip_tail") { rc = as_int(0, 1L << 40, t); h->skip_tail = t; }
@@ -642,6 +663,7 @@ int rx_get_param(const rx_handle *h, const char *key, double *value) {
     else if (k == "cma_passes") *value = h->cma_passes;
     else if (k == "n_cma") *value = (double)h->n_cma;
     else if (k == "n_train") *value = (double)h->n_train;
+    else if (k == "train_passes") *value = h->train_passes;
     else if (k == "sigma2") *value = h->sigma2_fixed;
     else if (k == "skip_head") *value = (double)h->skip_head;
     else if (k == "skip_tail") *value = (double)h->skip_tail;
@@ -804,14 +826,24 @@ int rx_fir(rx_handle *h, const void *x, size_t n_samples, const void *taps, size
 int rx_lms(rx_handle *h, const void *x, size_t n_samples, void *taps, size_t k0, size_t n_upd,
            const uint16_t *pcode, int mode, int passes, uint64_t u0) {
     if (!h || !x || !taps) return fail(RX_EINVAL, "NULL argument");
-    if (mode < 0 || mode > 2) return fail(RX_EINVAL, "mode must be 0, 1 or 2");
+    if (mode < 0 || mode > 3) return fail(RX_EINVAL, "mode must be 0, 1, 2 or 3");
     if (mode != 0 && !pcode) return fail(RX_EINVAL, "DD mode needs phase codes");
+    if (mode == 3 && (!h->ref || h->ref_n < (long)(k0 + n_upd)))
+        return fail(RX_ESTATE, "data-aided mode needs a reference covering the span");
     const long N = (long)n_samples / 2;
     if ((long)(k0 + n_upd) > N) return fail(RX_EINVAL, "update span beyond the stream");
     CK(launch_lms((const float2 *)x, (long)n_samples, (const float2 *)taps, (float2 *)taps, (long)k0,
-                  (int)n_upd, pcode, N, mode, passes, u0, (int)h->n_cma, (float)h->mu, h->streams,
-                  h->T, h->fmt, h->st));
+                  (int)n_upd, pcode, N, mode, passes, u0, (int)h->n_cma, (float)h->mu, h->ref,
+                  h->ref_n, h->streams, h->T, h->fmt, h->st));
     return RX_OK;
+}
+
+int rx_train(rx_handle *h, const void *x, size_t n_samples, void *taps, uint16_t *pcode) {
+    if (!h || !x || !taps || !pcode) return fail(RX_EINVAL, "NULL argument");
+    const long N = (long)n_samples / 2;
+    const long ntr = std::min(h->n_train, N);
+    if (!h->ref || h->ref_n < ntr) return fail(RX_ESTATE, "training needs a reference (rx_set_reference)");
+    return train_stage(h, (const float2 *)x, (long)n_samples, (float2 *)taps, ntr, pcode, ntr, h->st);
 }
 
 int rx_bps(rx_handle *h, const void *y, size_t n_y, size_t a, size_t e, size_t n_valid, uint8_t *b_out) {

@@ -66,7 +66,12 @@ cudaError_t launch_fir(const float2 *x, long ns, const float2 *taps, long k0, lo
 cudaError_t launch_lms(const float2 *x, long ns, const float2 *taps_in, float2 *taps_out,
                        long k0, int n_upd, const uint16_t *pcode, long pcode_stride,
                        int mode, int passes, unsigned long long u0, int n_cma, float mu,
+                       const uint8_t *ref_lab, long ref_stride,
                        int n_streams, int T, const FmtDev &f, cudaStream_t st);
+
+cudaError_t launch_train_phase(const float2 *x, long ns, const float2 *taps, const uint8_t *ref_lab,
+                               long ref_stride, int n, int W, uint16_t *pcode, long pcode_stride,
+                               int n_streams, int T, const FmtDev &f, cudaStream_t st);
 
 cudaError_t launch_align(const float2 *x, long ns, float2 *taps, const uint8_t *ref_lab,
                          long ref_stride, int n_train, int n_streams, int T, const FmtDev &f,

@@ -63,6 +63,7 @@ _PROTOS = {
     "rx_cdc": (_I, [_VP, _VP, _VP, _SZ]),
     "rx_fir": (_I, [_VP, _VP, _SZ, _VP, _SZ, _SZ, _VP]),
     "rx_lms": (_I, [_VP, _VP, _SZ, _VP, _SZ, _SZ, _VP, _I, _I, C.c_uint64]),
+    "rx_train": (_I, [_VP, _VP, _SZ, _VP, _VP]),
     "rx_bps": (_I, [_VP, _VP, _SZ, _SZ, _SZ, _SZ, _VP]),
     "rx_unwrap": (_I, [_VP, _VP, _SZ, _VP, _SZ, _SZ, _VP, _VP, _VP, _VP, _VP]),
     "rx_demap": (_I, [_VP, _VP, _SZ, _VP, _VP]),
@@ -236,6 +237,9 @@ class Receiver:
             pcode: torch.Tensor | None, mode: int, passes: int = 1, u0: int = 0):
         _ck(lib().rx_lms(self.h, _ptr(x), x.shape[-1], _ptr(taps), k0, n_upd,
                          _ptr(pcode), mode, passes, u0))
+
+    def train(self, x: torch.Tensor, taps: torch.Tensor, pcode: torch.Tensor):
+        _ck(lib().rx_train(self.h, _ptr(x), x.shape[-1], _ptr(taps), _ptr(pcode)))
 
     def bps(self, y: torch.Tensor, a: int, e: int, n_valid: int, b_out: torch.Tensor):
         _ck(lib().rx_bps(self.h, _ptr(y), y.shape[-1], a, e, n_valid, _ptr(b_out)))

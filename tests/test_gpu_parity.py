@@ -165,6 +165,29 @@ def test_lms_dd_parity(case):
 
 
 @pytest.mark.parametrize("case", list(CASES))
+def test_training_stage_parity(case):
+    """Order/phase alignment, data-aided phase codes and data-aided LMS from
+    the oracle's start-up CMA taps."""
+    st, p, res = _oracle_run(case)
+    r = _receiver(case)
+    fmt = oracle_format(CASES[case][0])
+    r.set_reference(_dev(st.bits[None]))
+    x = res.x.astype(np.complex64)
+    taps = _dev(res.w_cma.astype(np.complex64)[None])
+    ntr = p.n_train
+    pc = torch.zeros((1, ntr), dtype=torch.int16, device="cuda")
+    r.train(_dev(x[None]), taps, pc)
+    torch.cuda.synchronize()
+    code = pc[0].cpu().numpy().astype(np.int64) & 0xFFFF
+    S = fmt.sym_order
+    same = (code & 255) == res.train_b
+    same &= (code >> 8) == (res.train_m % S)
+    assert same.mean() > 0.995          # codes that differ sit on a rounding boundary
+    g = taps[0].cpu().numpy()
+    assert np.max(np.abs(g - res.w0)) < 1e-3 * np.max(np.abs(res.w0))
+
+
+@pytest.mark.parametrize("case", list(CASES))
 def test_bps_parity(case):
     st, p, res = _oracle_run(case)
     r = _receiver(case)

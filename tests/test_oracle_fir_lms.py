@@ -129,3 +129,39 @@ def test_cma_radius():
     assert abs(oracle_format("dp_qpsk").cma_radius2() - 1.0) < 1e-12
     # 16QAM: E|s|^4 = 1.32 for unit energy
     assert abs(oracle_format("dp_16qam").cma_radius2() - 1.32) < 1e-12
+
+
+def test_training_stage_recovers_a_singular_cma_solution():
+    """CMA can let both outputs capture the same polarisation.  The training
+    stage (order/phase from the known symbols, data-aided phase, data-aided
+    LMS) recovers both polarisations."""
+    fmt = oracle_format("gs4d64")
+    st, p, x = _equalised_link("gs4d64", 3000)
+    T, D = p.taps, (p.taps - 1) // 2
+    Jinv = np.linalg.inv(st.J)
+    h = np.zeros((2, 2, T), complex)
+    h[0, :, D] = np.conj(Jinv[1])          # both outputs see polarisation Y
+    h[1, :, D] = np.conj(Jinv[1]) * np.exp(0.4j)
+    ref = fmt.symbols_from_bits(st.bits[:2048])
+    y0 = chain.fir(x, h, 0, 2048)
+    assert np.mean(np.abs(y0[0] - ref[0]) ** 2) > 0.5
+    h = chain.align_training(x, h, ref)
+    b, m = chain.train_phase(chain.fir(x, h, 0, 2048), ref, 64, 64, 4)
+    phi = chain.phase_of(b, m, 64, 4)
+    p.mu = 2e-3
+    for _ in range(3):
+        h = chain.lms_trained(x, h, range(2048), ref, phi, p)
+    y = chain.fir(x, h, 100, 2048)
+    err = np.mean(np.abs(y * np.exp(-1j * phi[100:2048]) - ref[:, 100:2048]) ** 2)
+    assert err < 2e-2
+
+
+def test_train_phase_is_exact_on_grid_phases():
+    fmt = oracle_format("gs4d64")
+    rng = np.random.default_rng(3)
+    bits = rng.integers(0, 2, size=(500, 6), dtype=np.uint8)
+    s = fmt.symbols_from_bits(bits)
+    step = 2 * np.pi / 4 / 64
+    for nk in (-100, -5, 0, 37, 120):       # beyond +-pi/4: no rotational ambiguity
+        b, m = chain.train_phase(s * np.exp(1j * nk * step), s, 64, 64, 4)
+        assert np.all(b + 64 * m - 32 == nk)
