@@ -456,6 +456,7 @@ def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
       2. BPS, unwrap, de-rotation and LLRs over the range
          [n*block - W/2, (n+1)*block - W/2) (clipped to the stream; the last
          block runs to the stream end), which needs FIR output of block n only;
+         the unwrap starts from the training phase of symbol 0;
       3. LMS over the first n_upd symbols of block n starting from U_{n-1}
          (U_{-1} = W_0) -> U_n  (Sec. 2: part of a buffer updates the taps
          used for subsequent buffers)."""
@@ -486,7 +487,9 @@ def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
     mm = np.zeros(N, np.int64)
     gap = np.zeros(N)
     out = np.zeros((N, fmt.m))
-    m_prev, b_prev = 0, B // 2
+    # the unwrap starts from the training phase of symbol 0 (the known symbols
+    # fix the rotational ambiguity); without training, from phi_hat = 0
+    m_prev, b_prev = (int(train_m[0]), int(train_b[0])) if train_b is not None else (0, B // 2)
     u = 0
     nblk = -(-N // p.block)
     used, after, s2s, ranges, info = [], [], [], [], LmsInfo()

@@ -300,7 +300,8 @@ template <int T, int DIMS>
 __global__ void __launch_bounds__(256)
 train_phase_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ taps,
                    const uint8_t *__restrict__ ref_lab, long ref_stride, int n, int W,
-                   uint16_t *__restrict__ pcode, long pcode_stride, const __grid_constant__ FmtDev f) {
+                   uint16_t *__restrict__ pcode, long pcode_stride, int32_t *__restrict__ carry,
+                   int carry_stride, const __grid_constant__ FmtDev f) {
     constexpr int D = (T - 1) / 2;
     extern __shared__ float2 rs[];      // [n] per-symbol correlations
     __shared__ float2 hs[4 * T];
@@ -341,6 +342,10 @@ train_phase_kernel(const float2 *__restrict__ x, long ns, const float2 *__restri
         const int b = nk + B / 2 - m * B;
         const int mq = ((m % S) + S) % S;
         pcode[(long)s * pcode_stride + k] = (uint16_t)(b | (mq << 8));
+        if (k == 0 && carry) {                 // the unwrap starts from this phase
+            carry[s * carry_stride + 0] = mq;
+            carry[s * carry_stride + 1] = b;
+        }
     }
 }
 
@@ -414,7 +419,8 @@ cudaError_t launch_align(const float2 *x, long ns, float2 *taps, const uint8_t *
 
 cudaError_t launch_train_phase(const float2 *x, long ns, const float2 *taps, const uint8_t *ref_lab,
                                long ref_stride, int n, int W, uint16_t *pcode, long pcode_stride,
-                               int n_streams, int T, const FmtDev &f, cudaStream_t st) {
+                               int32_t *carry, int carry_stride, int n_streams, int T,
+                               const FmtDev &f, cudaStream_t st) {
     if (n <= 0 || n_streams <= 0) return cudaSuccess;
     const size_t smem = sizeof(float2) * (size_t)n;
     if (smem > 160 * 1024) return cudaErrorInvalidValue;
@@ -425,7 +431,7 @@ cudaError_t launch_train_phase(const float2 *x, long ns, const float2 *taps, con
                                               (int)smem);                                     \
         if (e_ != cudaSuccess) return e_;                                                      \
         k_<<<n_streams, 256, smem, st>>>(x, ns, taps, ref_lab, ref_stride, n, W, pcode,        \
-                                         pcode_stride, f);                                     \
+                                         pcode_stride, carry, carry_stride, f);                \
     } while (0)
     const bool d4 = f.dims == 4;
     switch (T) {

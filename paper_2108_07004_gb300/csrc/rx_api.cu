@@ -408,11 +408,11 @@ void prof_end(rx_handle *h, int stage, cudaEvent_t a, cudaStream_t s, int launch
 // known symbols, data-aided phase codes over the span, then train_passes
 // passes of data-aided LMS.  Taps are updated in place.
 int train_stage(rx_handle *h, const float2 *x, long ns, float2 *taps, long ntr, uint16_t *pcode,
-                long pcode_stride, cudaStream_t st) {
+                long pcode_stride, int32_t *carry, int carry_stride, cudaStream_t st) {
     const int S = h->streams, T = h->T;
     STAGE(ST_STARTUP, st, 1, launch_align(x, ns, taps, h->ref, h->ref_n, (int)ntr, S, T, h->fmt, st));
     STAGE(ST_STARTUP, st, 1, launch_train_phase(x, ns, taps, h->ref, h->ref_n, (int)ntr, h->W, pcode,
-                                                pcode_stride, S, T, h->fmt, st));
+                                                pcode_stride, carry, carry_stride, S, T, h->fmt, st));
     if (h->train_passes > 0)
         STAGE(ST_STARTUP, st, 1, launch_lms(x, ns, taps, taps, 0, (int)ntr, pcode, pcode_stride, 3,
                                             h->train_passes, 0, 0, (float)h->mu, h->ref, h->ref_n,
@@ -455,17 +455,20 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         const long npre = std::min(h->n_pre, N);
         STAGE(ST_STARTUP, st, 1, launch_lms(h->x, ns, w0, w0, 0, (int)npre, nullptr, 0, 0, h->cma_passes,
                                             0, 0, (float)h->mu, nullptr, 0, S, T, f, st));
-        const long ntr = std::min(h->n_train, N);
-        if (h->ref && ntr > 0 && h->ref_n >= ntr) {
-            int rc2 = train_stage(h, h->x, ns, w0, ntr, h->pcode, N, st);
-            if (rc2 != RX_OK) return rc2;
-        }
-        for (int i = 1; i <= L; ++i) CK(cudaMemcpyAsync(slot(h, i), w0, tapsz, cudaMemcpyDeviceToDevice, st));
+        // stream state: counters zero, unwrap carry phi_hat = 0 (the training
+        // stage overwrites the carry with the phase of symbol 0)
         std::vector<StreamDev> &sd0 = h->h_sd0;
         sd0.assign(S, StreamDev{});
         std::memset(sd0.data(), 0, sizeof(StreamDev) * S);
         for (int s = 0; s < S; ++s) { sd0[s].carry[0][0] = 0; sd0[s].carry[0][1] = h->B / 2; }
         CK(cudaMemcpyAsync(h->sd, sd0.data(), sizeof(StreamDev) * S, cudaMemcpyHostToDevice, st));
+        const long ntr = std::min(h->n_train, N);
+        if (h->ref && ntr > 0 && h->ref_n >= ntr) {
+            int rc2 = train_stage(h, h->x, ns, w0, ntr, h->pcode, N, reinterpret_cast<int32_t *>(h->sd),
+                                  (int)(sizeof(StreamDev) / sizeof(int32_t)), st);
+            if (rc2 != RX_OK) return rc2;
+        }
+        for (int i = 1; i <= L; ++i) CK(cudaMemcpyAsync(slot(h, i), w0, tapsz, cudaMemcpyDeviceToDevice, st));
         if (h->sigma2_fixed > 0) {
             h->h_sig.assign(S, h->sigma2_fixed);
             CK(cudaMemcpyAsync(h->sig_fixed, h->h_sig.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
@@ -843,7 +846,8 @@ int rx_train(rx_handle *h, const void *x, size_t n_samples, void *taps, uint16_t
     const long N = (long)n_samples / 2;
     const long ntr = std::min(h->n_train, N);
     if (!h->ref || h->ref_n < ntr) return fail(RX_ESTATE, "training needs a reference (rx_set_reference)");
-    return train_stage(h, (const float2 *)x, (long)n_samples, (float2 *)taps, ntr, pcode, ntr, h->st);
+    return train_stage(h, (const float2 *)x, (long)n_samples, (float2 *)taps, ntr, pcode, ntr, nullptr, 0,
+                       h->st);
 }
 
 int rx_bps(rx_handle *h, const void *y, size_t n_y, size_t a, size_t e, size_t n_valid, uint8_t *b_out) {

@@ -71,7 +71,8 @@ cudaError_t launch_lms(const float2 *x, long ns, const float2 *taps_in, float2 *
 
 cudaError_t launch_train_phase(const float2 *x, long ns, const float2 *taps, const uint8_t *ref_lab,
                                long ref_stride, int n, int W, uint16_t *pcode, long pcode_stride,
-                               int n_streams, int T, const FmtDev &f, cudaStream_t st);
+                               int32_t *carry, int carry_stride, int n_streams, int T,
+                               const FmtDev &f, cudaStream_t st);
 
 cudaError_t launch_align(const float2 *x, long ns, float2 *taps, const uint8_t *ref_lab,
                          long ref_stride, int n_train, int n_streams, int T, const FmtDev &f,
