@@ -360,6 +360,23 @@ def unwrap(b: np.ndarray, m_prev: int, b_prev: int, B: int):
     return m, m_prev, b_prev
 
 
+def quadrant_anchor(b: np.ndarray, train_b: np.ndarray, train_m: np.ndarray, B: int,
+                    S: int) -> int:
+    """Resolve the rotational ambiguity of the blind phase against the
+    training phases (reading: the known start of the stream fixes it once).
+
+    Unwrap the first phase indices from phi_hat = 0, and over the training
+    span compare with the training phase in grid units (n = b - B/2 + m B):
+    q_k = floor((n_train_k - n_blind_k) / B + 1/2) mod S.  The most common
+    q (lowest on ties) is the quadrant count the unwrap starts from."""
+    n = min(len(b), len(train_b))
+    m0, _, _ = unwrap(b[:n], 0, B // 2, B)
+    d = (train_b[:n] - B // 2 + train_m[:n] * B) - (b[:n] - B // 2 + m0 * B)
+    q = np.floor_divide(2 * d + B, 2 * B) % S
+    votes = np.bincount(q, minlength=S)
+    return int(np.argmax(votes))
+
+
 def phase_of(b: np.ndarray, m: np.ndarray, B: int, S: int) -> np.ndarray:
     q = 2 * np.pi / S
     return (b / B - 0.5) * q + m * q
@@ -456,7 +473,7 @@ def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
       2. BPS, unwrap, de-rotation and LLRs over the range
          [n*block - W/2, (n+1)*block - W/2) (clipped to the stream; the last
          block runs to the stream end), which needs FIR output of block n only;
-         the unwrap starts from the training phase of symbol 0;
+         in block 0 the unwrap's start quadrant comes from the training phases;
       3. LMS over the first n_upd symbols of block n starting from U_{n-1}
          (U_{-1} = W_0) -> U_n  (Sec. 2: part of a buffer updates the taps
          used for subsequent buffers)."""
@@ -487,9 +504,7 @@ def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
     mm = np.zeros(N, np.int64)
     gap = np.zeros(N)
     out = np.zeros((N, fmt.m))
-    # the unwrap starts from the training phase of symbol 0 (the known symbols
-    # fix the rotational ambiguity); without training, from phi_hat = 0
-    m_prev, b_prev = (int(train_m[0]), int(train_b[0])) if train_b is not None else (0, B // 2)
+    m_prev, b_prev = 0, B // 2          # phi_hat = 0 before the first symbol
     u = 0
     nblk = -(-N // p.block)
     used, after, s2s, ranges, info = [], [], [], [], LmsInfo()
@@ -501,6 +516,8 @@ def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
         a = max(0, k0 - W // 2)
         e = N if n == nblk - 1 else k1 - W // 2
         b, g, _ = bps(y, a, e, k1, p, fmt)
+        if n == 0 and train_b is not None:
+            m_prev = quadrant_anchor(b, train_b, train_m, B, S)
         m, m_prev, b_prev = unwrap(b, m_prev, b_prev, B)
         bb[a:e], mm[a:e], gap[a:e] = b, m, g
         phi = phase_of(b, m, B, S)

@@ -369,6 +369,58 @@ cudaError_t bps_launch_t(const float2 *y, long ys, long a, long e, long nv, int 
 
 int bps_cta_range() { return kR; }
 
+// Start quadrant of the unwrap from the training phases (one block per
+// stream): unwrap b[0..n) from phi_hat = 0 (m0), compare with the training
+// phase codes in grid units, q_k = floor((2 d_k + B) / (2B)) mod S with
+// d_k = (b_train - b_k) + B ((m_train - m0_k) mod S), and write the most
+// common q (lowest on ties) with b = B/2 as the unwrap carry.
+__global__ void __launch_bounds__(256)
+anchor_kernel(const uint8_t *__restrict__ b, long b_stride, const uint16_t *__restrict__ tcode,
+              long t_stride, int n, int32_t *__restrict__ carry, int carry_stride, int B, int S) {
+    __shared__ int tot[256];
+    __shared__ int votes[4];
+    const int s = blockIdx.x, tid = threadIdx.x;
+    const uint8_t *bs = b + (long)s * b_stride;
+    const uint16_t *ts = tcode + (long)s * t_stride;
+    if (tid < 4) votes[tid] = 0;
+    const int L = (n + 255) / 256, i0 = min(n, tid * L), i1 = min(n, i0 + L);
+    int run = 0;
+    for (int i = i0; i < i1; ++i) run += unwrap_step(i == 0 ? B / 2 : bs[i - 1], bs[i], B);
+    tot[tid] = run;
+    __syncthreads();
+    if (tid == 0) {                      // exclusive scan of the 256 segment totals
+        int acc = 0;
+        for (int t = 0; t < 256; ++t) { const int v = tot[t]; tot[t] = acc; acc += v; }
+    }
+    __syncthreads();
+    int m0 = tot[tid];
+    for (int i = i0; i < i1; ++i) {
+        m0 += unwrap_step(i == 0 ? B / 2 : bs[i - 1], bs[i], B);
+        const int bt = ts[i] & 255, mt = (ts[i] >> 8) & 3;
+        const int dm = (((mt - m0) % S) + S) % S;
+        const int d = (bt - (int)bs[i]) + B * dm;
+        const int num = 2 * d + B;
+        const int q = ((num >= 0 ? num / (2 * B) : -((-num + 2 * B - 1) / (2 * B))) % S + S) % S;
+        atomicAdd(&votes[q], 1);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int best = 0;
+        for (int q = 1; q < S; ++q)
+            if (votes[q] > votes[best]) best = q;
+        carry[s * carry_stride + 0] = best;
+        carry[s * carry_stride + 1] = B / 2;
+    }
+}
+
+cudaError_t launch_anchor(const uint8_t *b, long b_stride, const uint16_t *tcode, long t_stride,
+                          int n, int32_t *carry, int carry_stride, int n_streams, int B, int S,
+                          cudaStream_t st) {
+    if (n <= 0 || n_streams <= 0) return cudaSuccess;
+    anchor_kernel<<<n_streams, 256, 0, st>>>(b, b_stride, tcode, t_stride, n, carry, carry_stride, B, S);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_dsum_from_b(const uint8_t *b, long b_stride, long a, long e, int *dsum,
                                int n_streams, int B, cudaStream_t st) {
     if (e <= a || n_streams <= 0) return cudaSuccess;

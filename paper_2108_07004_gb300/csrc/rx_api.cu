@@ -95,6 +95,7 @@ struct rx_handle {
     int ref_s = 0;
     // stream state (host mirror of the scalars)
     bool started = false;
+    bool trained = false;
     long blocks_done = 0;
     unsigned long long u = 0;
     long cur_n = 0;
@@ -455,17 +456,17 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         const long npre = std::min(h->n_pre, N);
         STAGE(ST_STARTUP, st, 1, launch_lms(h->x, ns, w0, w0, 0, (int)npre, nullptr, 0, 0, h->cma_passes,
                                             0, 0, (float)h->mu, nullptr, 0, S, T, f, st));
-        // stream state: counters zero, unwrap carry phi_hat = 0 (the training
-        // stage overwrites the carry with the phase of symbol 0)
+        // stream state: counters zero, unwrap carry phi_hat = 0
         std::vector<StreamDev> &sd0 = h->h_sd0;
         sd0.assign(S, StreamDev{});
         std::memset(sd0.data(), 0, sizeof(StreamDev) * S);
         for (int s = 0; s < S; ++s) { sd0[s].carry[0][0] = 0; sd0[s].carry[0][1] = h->B / 2; }
         CK(cudaMemcpyAsync(h->sd, sd0.data(), sizeof(StreamDev) * S, cudaMemcpyHostToDevice, st));
         const long ntr = std::min(h->n_train, N);
+        h->trained = false;
         if (h->ref && ntr > 0 && h->ref_n >= ntr) {
-            int rc2 = train_stage(h, h->x, ns, w0, ntr, h->pcode, N, reinterpret_cast<int32_t *>(h->sd),
-                                  (int)(sizeof(StreamDev) / sizeof(int32_t)), st);
+            h->trained = true;
+            int rc2 = train_stage(h, h->x, ns, w0, ntr, h->pcode, N, nullptr, 0, st);
             if (rc2 != RX_OK) return rc2;
         }
         for (int i = 1; i <= L; ++i) CK(cudaMemcpyAsync(slot(h, i), w0, tapsz, cudaMemcpyDeviceToDevice, st));
@@ -500,6 +501,11 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         const long e = (n == nblk - 1) ? N : k1 - h->W / 2;
         STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, h->dsum, S, f, st));
         const int cin = (int)(n & 1), cout = 1 - cin;
+        if (n == 0 && h->trained) {
+            // the training phases fix the start quadrant of the unwrap
+            STAGE(ST_UNWRAP, st, 1, launch_anchor(h->bidx, N, h->pcode, N, (int)std::min(h->n_train, e),
+                                                  carry_base, (int)sd_stride, S, h->B, f.S, st));
+        }
         STAGE(ST_UNWRAP, st, 1,
               launch_unwrap(h->y, N, h->bidx, N, a, a, e, h->dsum, carry_base + 2 * cin,
                             (int)sd_stride, carry_base + 2 * cout, (int)sd_stride, h->z, N, a,

@@ -94,6 +94,10 @@ cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long
                           unsigned int *ticket, int ticket_stride,
                           int n_streams, const FmtDev &f, cudaStream_t st);
 
+cudaError_t launch_anchor(const uint8_t *b, long b_stride, const uint16_t *tcode, long t_stride,
+                          int n, int32_t *carry, int carry_stride, int n_streams, int B, int S,
+                          cudaStream_t st);
+
 cudaError_t launch_dsum_from_b(const uint8_t *b, long b_stride, long a, long e, int *dsum,
                                int n_streams, int B, cudaStream_t st);
 

@@ -189,3 +189,24 @@ def test_sigma2_estimate_close_to_true_noise_at_high_snr():
     _, s = _symbols(fmt, 20000, 10)
     z = s + np.sqrt(n0 / 2) * (rng.standard_normal(s.shape) + 1j * rng.standard_normal(s.shape))
     assert abs(chain.estimate_sigma2(z, fmt) / n0 - 1) < 0.03
+
+
+def test_quadrant_anchor_recovers_training_quadrant():
+    """Blind phase indices that agree with the training phase up to a whole
+    number of quadrants (plus a garbled start) are anchored to the training
+    quadrant: the anchored unwrap equals the training phase modulo 2 pi."""
+    B, S = 64, 4
+    rng = np.random.default_rng(11)
+    n = 1024
+    true_n = np.cumsum(rng.integers(-1, 2, size=n)) + 40          # grid units, drifting
+    mt = np.floor_divide(true_n + B // 2, B)
+    bt = true_n + B // 2 - mt * B
+    for shift in range(4):
+        blind = (true_n + shift * B + B // 2) % B                 # b is blind to quadrants
+        b = blind.copy()
+        b[:60] = rng.integers(0, B, size=60)                       # garbled stream start
+        q = chain.quadrant_anchor(b, bt, mt, B, S)
+        m, _, _ = chain.unwrap(b, q, B // 2, B)
+        nb = b - B // 2 + m * B
+        agree = ((nb - true_n) % (S * B)) == 0
+        assert agree[100:].mean() > 0.99
