@@ -24,13 +24,17 @@
 //   m_k = m_{k-1} + floor((2 (b_{k-1} - b_k) + B) / (2B)),
 // a prefix sum: the BPS kernel sums the increments inside its range, the
 // unwrap kernel adds the block boundaries and scans its own range.
+#include <algorithm>
+
 #include "rx_internal.h"
 
 namespace {
 
-constexpr int kRounds = 4;
-constexpr int kChunks = 8 * kRounds - 2;   // output chunks per block
-constexpr int kR = 32 * kChunks;           // output symbols per block (960)
+constexpr int kMaxRounds = 16;
+constexpr int kMaxR = 32 * (8 * kMaxRounds - 2);   // largest output range per block (4032)
+
+// Output symbols per block for `rounds` rounds of 8 chunks (one halo chunk on each side).
+__host__ __device__ __forceinline__ int range_of(int rounds) { return 32 * (8 * rounds - 2); }
 
 __device__ __forceinline__ int unwrap_step(int bprev, int b, int B) {
     const int num = 2 * (bprev - b) + B;   // in [2 - B, 3B - 2]
@@ -47,9 +51,10 @@ template <int DIMS, int NORB>
 __global__ void __launch_bounds__(256, 2)
 bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_valid, int W,
            uint8_t *__restrict__ bout, long bout_stride, int *__restrict__ dsum, int n_cta,
-           const __grid_constant__ FmtDev f) {
+           int rounds, const __grid_constant__ FmtDev f) {
     extern __shared__ float smem[];
     const int B = f.B;
+    const int kChunks = 8 * rounds - 2, kR = range_of(rounds);
     float *Eb = smem;                                     // [10][B][32] exclusive prefixes
     float *Tb = smem + RX_NCHUNK * B * 32;                // [10][B] chunk totals
     uint8_t *bsm = reinterpret_cast<uint8_t *>(Tb + RX_NCHUNK * B);   // [kR]
@@ -63,7 +68,7 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
     const int hw = W >> 1;
     const int S = f.S;
 
-    for (int r = 0; r < kRounds; ++r) {
+    for (int r = 0; r < rounds; ++r) {
         // ---- min distances of chunk jc for every test phase, scanned ----
         const int jc = 8 * r - 1 + warp;
         const long i = out0 + 32L * jc + lane;
@@ -98,22 +103,31 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
             }
         }
         const int slot = (jc + 1) % RX_NCHUNK;
-        for (int b = 0; b < B; ++b) {
+        const int hb = B >> 1;
+        // test phases b and b + B/2 together: four independent minimum chains
+        for (int b = 0; b < hb; ++b) {
             const float cb = f.cs[b][0], sb = f.cs[b][1];
-            float md;
+            const float cb2 = f.cs[b + hb][0], sb2 = f.cs[b + hb][1];
+            float md, md2;
             if (DIMS == 4) {
-                float best = 3.0e38f;
+                float a0 = 3.0e38f, a1 = 3.0e38f, c0m = 3.0e38f, c1m = 3.0e38f;
 #pragma unroll
                 for (int o = 0; o < NORB; ++o) {
                     if (o < f.n_orb) {
                         const float P = cb * cr[0][o] + sb * ci[0][o];
                         const float Q = cb * ci[0][o] - sb * cr[0][o];
-                        best = fminf(best, fmaf(-2.f, orbit_v(P, Q, S), f.orbe[o]));
+                        const float P2 = cb2 * cr[0][o] + sb2 * ci[0][o];
+                        const float Q2 = cb2 * ci[0][o] - sb2 * cr[0][o];
+                        const float v1 = fmaf(-2.f, orbit_v(P, Q, S), f.orbe[o]);
+                        const float v2 = fmaf(-2.f, orbit_v(P2, Q2, S), f.orbe[o]);
+                        if (o & 1) { a1 = fminf(a1, v1); c1m = fminf(c1m, v2); }
+                        else       { a0 = fminf(a0, v1); c0m = fminf(c0m, v2); }
                     }
                 }
-                md = yn0 + best;
+                md = yn0 + fminf(a0, a1);
+                md2 = yn0 + fminf(c0m, c1m);
             } else {
-                float b0 = 3.0e38f, b1 = 3.0e38f;
+                float x0 = 3.0e38f, x1 = 3.0e38f, w0 = 3.0e38f, w1 = 3.0e38f;
 #pragma unroll
                 for (int o = 0; o < NORB; ++o) {
                     if (o < f.n_orb) {
@@ -121,23 +135,33 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
                         const float Q0 = cb * ci[0][o] - sb * cr[0][o];
                         const float P1 = cb * cr[1][o] + sb * ci[1][o];
                         const float Q1 = cb * ci[1][o] - sb * cr[1][o];
-                        b0 = fminf(b0, fmaf(-2.f, orbit_v(P0, Q0, S), f.orbe[o]));
-                        b1 = fminf(b1, fmaf(-2.f, orbit_v(P1, Q1, S), f.orbe[o]));
+                        const float R0 = cb2 * cr[0][o] + sb2 * ci[0][o];
+                        const float U0 = cb2 * ci[0][o] - sb2 * cr[0][o];
+                        const float R1 = cb2 * cr[1][o] + sb2 * ci[1][o];
+                        const float U1 = cb2 * ci[1][o] - sb2 * cr[1][o];
+                        x0 = fminf(x0, fmaf(-2.f, orbit_v(P0, Q0, S), f.orbe[o]));
+                        x1 = fminf(x1, fmaf(-2.f, orbit_v(P1, Q1, S), f.orbe[o]));
+                        w0 = fminf(w0, fmaf(-2.f, orbit_v(R0, U0, S), f.orbe[o]));
+                        w1 = fminf(w1, fmaf(-2.f, orbit_v(R1, U1, S), f.orbe[o]));
                     }
                 }
-                md = (yn0 + b0) + (yn1 + b1);
+                md = (yn0 + x0) + (yn1 + x1);
+                md2 = (yn0 + w0) + (yn1 + w1);
             }
-            if (!valid) md = 0.f;
-            float incl = md;
+            if (!valid) { md = 0.f; md2 = 0.f; }
+            float incl = md, incl2 = md2;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
                 const float t = __shfl_up_sync(0xffffffffu, incl, off);
-                if (lane >= off) incl += t;
+                const float t2 = __shfl_up_sync(0xffffffffu, incl2, off);
+                if (lane >= off) { incl += t; incl2 += t2; }
             }
             float excl = __shfl_up_sync(0xffffffffu, incl, 1);
-            if (lane == 0) excl = 0.f;
+            float excl2 = __shfl_up_sync(0xffffffffu, incl2, 1);
+            if (lane == 0) { excl = 0.f; excl2 = 0.f; }
             Eb[(slot * B + b) * 32 + lane] = excl;
-            if (lane == 31) Tb[slot * B + b] = incl;
+            Eb[(slot * B + b + hb) * 32 + lane] = excl2;
+            if (lane == 31) { Tb[slot * B + b] = incl; Tb[slot * B + b + hb] = incl2; }
         }
         __syncthreads();
         // ---- window costs and argmin for output chunk oc ----
@@ -227,9 +251,9 @@ unwrap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *__rest
               const int32_t *__restrict__ carry_in, int cin_stride, int32_t *__restrict__ carry_out,
               int cout_stride, float2 *__restrict__ z, long z_stride, uint16_t *__restrict__ pcode,
               long pc_stride, double *__restrict__ partial, double *__restrict__ sigma2_out,
-              int s2_stride, unsigned int *__restrict__ ticket, int ticket_stride,
+              int s2_stride, unsigned int *__restrict__ ticket, int ticket_stride, int kR,
               const __grid_constant__ FmtDev f) {
-    __shared__ int bl[kR];
+    __shared__ uint8_t bl[kMaxR];
     __shared__ int wsum[8];
     __shared__ int mstart_sh;
     __shared__ double dred[8];
@@ -258,11 +282,12 @@ unwrap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *__rest
     __syncthreads();
     const int bprev0 = (c == 0) ? b_in : (int)bs[out0 - 1 - a];
 
-    // block scan of the increments: thread t owns local symbols 4t .. 4t+3
-    int d[4], run = 0;
+    // block scan of the increments: thread t owns local symbols PT t .. PT t + PT - 1
+    constexpr int PT = (kMaxR + 255) / 256;
+    int d[PT], run = 0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int t = 4 * tid + u;
+    for (int u = 0; u < PT; ++u) {
+        const int t = PT * tid + u;
         int inc = 0;
         if (t < nloc) inc = unwrap_step(t == 0 ? bprev0 : bl[t - 1], bl[t], B);
         run += inc;
@@ -286,8 +311,8 @@ unwrap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *__rest
     float2 *zy = zx + z_stride;
     double dsum_loc = 0.0;
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-        const int t = 4 * tid + u;
+    for (int u = 0; u < PT; ++u) {
+        const int t = PT * tid + u;
         if (t >= nloc) continue;
         const long k = out0 + t;
         const int m = tpre + d[u];
@@ -334,7 +359,7 @@ unwrap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *__rest
 
 // interior unwrap increments of each kR range, from phase indices b (index k - a)
 __global__ void dsum_kernel(const uint8_t *__restrict__ b, long b_stride, long a, long e,
-                            int *__restrict__ dsum, int n_cta, int B) {
+                            int *__restrict__ dsum, int n_cta, int B, int kR) {
     __shared__ int red[8];
     const int s = blockIdx.y, c = blockIdx.x, tid = threadIdx.x;
     const long out0 = a + (long)c * kR, out1 = min(out0 + kR, e);
@@ -354,20 +379,38 @@ __global__ void dsum_kernel(const uint8_t *__restrict__ b, long b_stride, long a
 
 template <int DIMS, int NORB>
 cudaError_t bps_launch_t(const float2 *y, long ys, long a, long e, long nv, int W, uint8_t *bout,
-                         long bst, int *dsum, int n_streams, const FmtDev &f, cudaStream_t st) {
+                         long bst, int *dsum, int rounds, int n_streams, const FmtDev &f,
+                         cudaStream_t st) {
+    const int kR = range_of(rounds);
     const int n_cta = (int)((e - a + kR - 1) / kR);
     const size_t smem = sizeof(float) * (RX_NCHUNK * f.B * 32 + RX_NCHUNK * f.B) + kR + 16;
     auto kern = bps_kernel<DIMS, NORB>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     dim3 grid((unsigned)n_cta, (unsigned)n_streams);
-    kern<<<grid, 256, smem, st>>>(y, ys, a, e, nv, W, bout, bst, dsum, n_cta, f);
+    kern<<<grid, 256, smem, st>>>(y, ys, a, e, nv, W, bout, bst, dsum, n_cta, rounds, f);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-int bps_cta_range() { return kR; }
+int bps_cta_range(int rounds) { return range_of(rounds); }
+
+// Rounds per block so that one launch of S streams x (e - a) outputs fills
+// about one wave of 2 blocks per SM (the ring of 10 chunks takes ~85 KB).
+int bps_rounds(long len, int n_streams) {
+    static int n_sm = 0;
+    if (!n_sm) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0)
+            n_sm = 152;
+    }
+    const long per_stream = std::max(1L, (long)(2 * n_sm) / std::max(1, n_streams));
+    const long want = (len + per_stream - 1) / per_stream;         // outputs per block
+    int rounds = (int)((want / 32 + 2 + 7) / 8);
+    return std::max(1, std::min(kMaxRounds, rounds));
+}
 
 // Start quadrant of the unwrap from the training phases (one block per
 // stream): unwrap b[0..n) from phi_hat = 0 (m0), compare with the training
@@ -422,25 +465,27 @@ cudaError_t launch_anchor(const uint8_t *b, long b_stride, const uint16_t *tcode
 }
 
 cudaError_t launch_dsum_from_b(const uint8_t *b, long b_stride, long a, long e, int *dsum,
-                               int n_streams, int B, cudaStream_t st) {
+                               int rounds, int n_streams, int B, cudaStream_t st) {
     if (e <= a || n_streams <= 0) return cudaSuccess;
+    const int kR = range_of(rounds);
     const int n_cta = (int)((e - a + kR - 1) / kR);
     dim3 grid((unsigned)n_cta, (unsigned)n_streams);
-    dsum_kernel<<<grid, 256, 0, st>>>(b, b_stride, a, e, dsum, n_cta, B);
+    dsum_kernel<<<grid, 256, 0, st>>>(b, b_stride, a, e, dsum, n_cta, B, kR);
     return cudaGetLastError();
 }
 
 cudaError_t launch_bps(const float2 *y, long y_stride, long a, long e, long n_valid, int W,
-                       uint8_t *bout, long bout_stride, long bout_off, int *dsum, int n_streams,
-                       const FmtDev &f, cudaStream_t st) {
+                       uint8_t *bout, long bout_stride, long bout_off, int *dsum, int rounds,
+                       int n_streams, const FmtDev &f, cudaStream_t st) {
     if (e <= a || n_streams <= 0) return cudaSuccess;
+    if (rounds < 1 || rounds > kMaxRounds || (f.B & 1)) return cudaErrorInvalidValue;
     uint8_t *bo = bout + bout_off;
     if (f.dims == 4) {
         if (f.n_orb > 16) return cudaErrorInvalidValue;
-        return bps_launch_t<4, 16>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, n_streams, f, st);
+        return bps_launch_t<4, 16>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, rounds, n_streams, f, st);
     }
     if (f.n_orb > 4) return cudaErrorInvalidValue;
-    return bps_launch_t<2, 4>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, n_streams, f, st);
+    return bps_launch_t<2, 4>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, rounds, n_streams, f, st);
 }
 
 cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long b_stride,
@@ -450,21 +495,23 @@ cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long
                           float2 *z, long z_stride, long z_off,
                           uint16_t *pcode, long pcode_stride, long pcode_off,
                           double *partial, double *sigma2_out, int sigma2_stride,
-                          unsigned int *ticket, int ticket_stride,
+                          unsigned int *ticket, int ticket_stride, int rounds,
                           int n_streams, const FmtDev &f, cudaStream_t st) {
     if (e <= a || n_streams <= 0) return cudaSuccess;
+    if (rounds < 1 || rounds > kMaxRounds) return cudaErrorInvalidValue;
+    const int kR = range_of(rounds);
     const int n_cta = (int)((e - a + kR - 1) / kR);
     dim3 grid((unsigned)n_cta, (unsigned)n_streams);
     if (f.dims == 4) {
         unwrap_kernel<4, 16><<<grid, 256, 0, st>>>(y, y_stride, b + b_off, b_stride, a, e, dsum, n_cta,
                                                     carry_in, carry_in_stride, carry_out, carry_out_stride,
                                                     z + z_off, z_stride, pcode + pcode_off, pcode_stride,
-                                                    partial, sigma2_out, sigma2_stride, ticket, ticket_stride, f);
+                                                    partial, sigma2_out, sigma2_stride, ticket, ticket_stride, kR, f);
     } else {
         unwrap_kernel<2, 4><<<grid, 256, 0, st>>>(y, y_stride, b + b_off, b_stride, a, e, dsum, n_cta,
                                                    carry_in, carry_in_stride, carry_out, carry_out_stride,
                                                    z + z_off, z_stride, pcode + pcode_off, pcode_stride,
-                                                   partial, sigma2_out, sigma2_stride, ticket, ticket_stride, f);
+                                                   partial, sigma2_out, sigma2_stride, ticket, ticket_stride, kR, f);
     }
     return cudaGetLastError();
 }

@@ -17,6 +17,8 @@
 // The start-up training alignment (Sec. 2: the equaliser first converges on
 // a known sequence) is align_kernel: it correlates the equalised training
 // span with the known symbols and fixes the output order and phases.
+#include <algorithm>
+
 #include "rx_internal.h"
 
 namespace {
@@ -40,12 +42,6 @@ __device__ __forceinline__ void load_tables(Tables &tb, const FmtDev &f) {
         tb.pts[i] = make_float4(f.pts[i][0], f.pts[i][1], f.pts[i][2], f.pts[i][3]);
 }
 
-__device__ __forceinline__ unsigned long long shfl_xor_u64(unsigned long long v, int m) {
-    unsigned lo = __shfl_xor_sync(0xffffffffu, (unsigned)v, m);
-    unsigned hi = __shfl_xor_sync(0xffffffffu, (unsigned)(v >> 32), m);
-    return ((unsigned long long)hi << 32) | lo;
-}
-
 // best rotation of an orbit given P + jQ = sum_p z_p conj(rep_p):
 // Re of the correlation with rep * j^k is P, Q, -P, -Q for k = 0..3.
 __device__ __forceinline__ void best_rot(float P, float Q, int S, float &v, int &k) {
@@ -60,158 +56,219 @@ __device__ __forceinline__ void best_rot(float P, float Q, int S, float &v, int 
     }
 }
 
-// Nearest-point label, distributed over the 16 lanes of each half warp.
-// DIMS 4: both halves decide the joint point of (z0, z1).
-// DIMS 2: half q decides the point of its own polarisation zq.
-template <int DIMS>
-__device__ __forceinline__ int decide_warp(float2 z0, float2 z1, float2 zq, const Tables &tb,
-                                           const FmtDev &f, int lane) {
-    const int o = lane & 15;
-    unsigned long long key = ~0ull;
-    if (o < f.n_orb) {
-        const float4 r = tb.orb[o];
-        float P, Q, zn;
-        if (DIMS == 4) {
-            P = z0.x * r.x + z0.y * r.y + z1.x * r.z + z1.y * r.w;
-            Q = z0.y * r.x - z0.x * r.y + z1.y * r.z - z1.x * r.w;
-            zn = cnorm(z0) + cnorm(z1);
-        } else {
-            P = zq.x * r.x + zq.y * r.y;
-            Q = zq.y * r.x - zq.x * r.y;
-            zn = cnorm(zq);
-        }
-        float v;
-        int k;
-        best_rot(P, Q, f.S, v, k);
-        const float dist = fmaxf(zn + tb.orbe[o] - 2.f * v, 0.f);
-        key = ((unsigned long long)__float_as_uint(dist) << 32) | (unsigned)tb.orblab[o][k];
-    }
-#pragma unroll
-    for (int m = 1; m < 16; m <<= 1) {
-        unsigned long long other = shfl_xor_u64(key, m);
-        key = other < key ? other : key;
-    }
-    return (int)(key & 0xffffffffu);
+// Point of representative o turned by k quarter turns (both polarisations).
+__device__ __forceinline__ float4 turn(float4 r, int k) {
+    for (int i = 0; i < k; ++i) r = make_float4(-r.y, r.x, -r.w, r.z);
+    return r;
 }
 
-template <int T, int DIMS>
+// Nearest table point of the candidates held by the lanes: lane o (o < 16)
+// holds orbit o's best rotation with squared distance dist and its point;
+// the minimum distance over lanes 0..15 wins, exact ties go to the lowest
+// label.  Returns the winning lane.
+__device__ __forceinline__ int argmin_lane(float dist, bool valid, int label, int lane) {
+    const unsigned bits = valid ? __float_as_uint(fmaxf(dist, 0.f)) : 0xffffffffu;
+    const unsigned mn = __reduce_min_sync(0xffffffffu, bits);
+    const unsigned tie = __ballot_sync(0xffffffffu, bits == mn && lane < 16);
+    if (__popc(tie) == 1) return __ffs(tie) - 1;
+    const unsigned key = (bits == mn && lane < 16) ? (unsigned)label : 0xffffffffu;
+    const unsigned ml = __reduce_min_sync(0xffffffffu, key);
+    return __ffs(__ballot_sync(0xffffffffu, key == ml && lane < 16)) - 1;
+}
+
+// (y0, y1) from per-lane partials of both outputs: xor-16 halving step, four
+// xor steps within the half warp, then exchange of the halves.
+__device__ __forceinline__ void reduce_pair(float2 a, float2 b, int p, float2 &y0, float2 &y1) {
+    float2 send = p ? a : b, keep = p ? b : a;
+    keep.x += __shfl_xor_sync(0xffffffffu, send.x, 16);
+    keep.y += __shfl_xor_sync(0xffffffffu, send.y, 16);
+#pragma unroll
+    for (int m = 8; m > 0; m >>= 1) {
+        keep.x += __shfl_xor_sync(0xffffffffu, keep.x, m);
+        keep.y += __shfl_xor_sync(0xffffffffu, keep.y, m);
+    }
+    float2 other;
+    other.x = __shfl_xor_sync(0xffffffffu, keep.x, 16);
+    other.y = __shfl_xor_sync(0xffffffffu, keep.y, 16);
+    y0 = p ? other : keep;
+    y1 = p ? keep : other;
+}
+
+// Sequential CMA (MODE 0), DD-LMS (MODE 1) or data-aided LMS (MODE 3).
+//
+// Lane (p, j) = (lane >> 4, lane & 15) holds h_qp[j + 16 i] of both outputs
+// q.  The recursion is written in look-ahead form: with X_k the stacked
+// input window of symbol k and h_k the taps after update k,
+//   y_k = h_{k-1}^H X_k = h_{k-2}^H X_k + mu e_{k-1} X_{k-1}^H X_k,
+// so the 32-lane reduction of base_k = h_{k-2}^H X_k is issued two updates
+// ahead and overlaps with the decision of the update in between; only the
+// scalar correction with r1_k = X_{k-1}^H X_k (precomputed by the whole block
+// for the staged span) is on the sequential path.
+template <int T, int DIMS, int MODE>
 __global__ void __launch_bounds__(256)
 lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ taps_in,
            float2 *__restrict__ taps_out, long k0, int n_upd, const uint16_t *__restrict__ pcode,
-           long pcode_stride, int mode, int passes, unsigned long long u0, int n_cma, float mu,
-           const uint8_t *__restrict__ ref_lab, long ref_stride, const __grid_constant__ FmtDev f) {
+           long pcode_stride, int passes, float mu, const uint8_t *__restrict__ ref_lab,
+           long ref_stride, const __grid_constant__ FmtDev f) {
     constexpr int D = (T - 1) / 2;
-    constexpr int NSX = 2 * kCH + 2 * D;
-    constexpr int NT = (T + 7) / 8;
+    constexpr int NSX = 2 * kCH + 2 * D + 2;
+    constexpr int NT = (T + 15) / 16;
     __shared__ float2 xs[2][NSX];
+    __shared__ float2 r1s[kCH];
     __shared__ uint16_t pc[kCH];
     __shared__ uint8_t rl[kCH];
     __shared__ Tables tb;
     const int s = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int q = lane >> 4, p = (lane >> 3) & 1, j = lane & 7;
+    const int p = lane >> 4, j = lane & 15;
     load_tables(tb, f);
 
-    float2 h[NT];
+    float2 h[2][NT];
 #pragma unroll
-    for (int i = 0; i < NT; ++i) {
-        const int t = j + 8 * i;
-        h[i] = (t < T) ? taps_in[(((long)s * 2 + q) * 2 + p) * T + t] : make_float2(0.f, 0.f);
-    }
+    for (int q = 0; q < 2; ++q)
+#pragma unroll
+        for (int i = 0; i < NT; ++i) {
+            const int t = j + 16 * i;
+            h[q][i] = (t < T) ? taps_in[(((long)s * 2 + q) * 2 + p) * T + t] : make_float2(0.f, 0.f);
+        }
     const float2 *xsrc = x + (long)s * 2 * ns;
-    unsigned long long u = u0;
+    const int qt_step = 4 / f.S;
     for (int pass = 0; pass < passes; ++pass) {
         for (int c0 = 0; c0 < n_upd; c0 += kCH) {
             const int n = min(kCH, n_upd - c0);
             const long kb = k0 + c0;
-            const int nsx = 2 * n + 2 * D;
+            const int nsx = 2 * n + 2 * D + 2;
             __syncthreads();
+            // local sample index of symbol kb + kk, tap t: 2 kk + 2 + 2D - t
             for (int i = threadIdx.x; i < 2 * nsx; i += blockDim.x) {
                 const int pp = i / nsx, jj = i - pp * nsx;
-                const long g = 2 * kb - D + jj;
+                const long g = 2 * (kb - 1) - D + jj;
                 xs[pp][jj] = (g >= 0 && g < ns) ? xsrc[(long)pp * ns + g] : make_float2(0.f, 0.f);
             }
-            if (mode != 0)
-                for (int i = threadIdx.x; i < n; i += blockDim.x)
-                    pc[i] = pcode[(long)s * pcode_stride + kb + i];
-            if (mode == 3)
-                for (int i = threadIdx.x; i < n; i += blockDim.x)
-                    rl[i] = ref_lab[(long)s * ref_stride + kb + i];
+            if (MODE != 0)
+                for (int i = threadIdx.x; i < n; i += blockDim.x) pc[i] = pcode[(long)s * pcode_stride + kb + i];
+            if (MODE == 3)
+                for (int i = threadIdx.x; i < n; i += blockDim.x) rl[i] = ref_lab[(long)s * ref_stride + kb + i];
+            __syncthreads();
+            for (int kk = threadIdx.x; kk < n; kk += blockDim.x) {   // r1_k = X_{k-1}^H X_k
+                float2 acc = make_float2(0.f, 0.f);
+                for (int pp = 0; pp < 2; ++pp)
+#pragma unroll 8
+                    for (int t = 0; t < T; ++t)
+                        acc = cadd(acc, cmulc(xs[pp][2 * kk + 2 * D - t], xs[pp][2 * kk + 2 + 2 * D - t]));
+                r1s[kk] = acc;
+            }
             __syncthreads();
             if (warp != 0) continue;
 
-            float2 xv[NT], xn[NT];
-#pragma unroll
-            for (int i = 0; i < NT; ++i) {
-                const int t = j + 8 * i;
-                xn[i] = (t < T) ? xs[p][2 * D - t] : make_float2(0.f, 0.f);
-            }
-            for (int kk = 0; kk < n; ++kk, ++u) {
-#pragma unroll
-                for (int i = 0; i < NT; ++i) xv[i] = xn[i];
-                if (kk + 1 < n) {
-#pragma unroll
-                    for (int i = 0; i < NT; ++i) {
-                        const int t = j + 8 * i;
-                        if (t < T) xn[i] = xs[p][2 * (kk + 1) + 2 * D - t];
-                    }
-                }
-                float2 part = make_float2(0.f, 0.f);
+            auto xval = [&](int kk, int i) -> float2 {
+                const int t = j + 16 * i;
+                return (t < T) ? xs[p][2 * kk + 2 + 2 * D - t] : make_float2(0.f, 0.f);
+            };
+            auto base = [&](int kk, float2 &b0, float2 &b1) {
+                float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int i = 0; i < NT; ++i) {
-                    part.x += h[i].x * xv[i].x + h[i].y * xv[i].y;
-                    part.y += h[i].x * xv[i].y - h[i].y * xv[i].x;
+                    const float2 xv = xval(kk, i);
+                    a = cadd(a, cmulc(h[0][i], xv));
+                    c = cadd(c, cmulc(h[1][i], xv));
                 }
-#pragma unroll
-                for (int m = 1; m < 16; m <<= 1) {
-                    part.x += __shfl_xor_sync(0xffffffffu, part.x, m);
-                    part.y += __shfl_xor_sync(0xffffffffu, part.y, m);
-                }
-                const float2 yq = part;
-                const bool cma = (mode == 0) || (mode == 2 && u < (unsigned long long)n_cma);
-                float2 e;
-                if (cma) {
-                    const float g = f.R2 - cnorm(yq);
-                    e = make_float2(g * yq.x, g * yq.y);
+                reduce_pair(a, c, p, b0, b1);
+            };
+            float2 bc0, bc1, bn0 = make_float2(0.f, 0.f), bn1 = make_float2(0.f, 0.f);
+            base(0, bc0, bc1);
+            if (n > 1) base(1, bn0, bn1);
+            float2 ep0 = make_float2(0.f, 0.f), ep1 = make_float2(0.f, 0.f);
+            for (int kk = 0; kk < n; ++kk) {
+                const float2 r1 = r1s[kk];
+                const float2 y0 = cadd(bc0, cmul(make_float2(mu * ep0.x, mu * ep0.y), r1));
+                const float2 y1 = cadd(bc1, cmul(make_float2(mu * ep1.x, mu * ep1.y), r1));
+                float2 e0, e1;
+                if (MODE == 0) {
+                    const float g0 = f.R2 - cnorm(y0), g1 = f.R2 - cnorm(y1);
+                    e0 = make_float2(g0 * y0.x, g0 * y0.y);
+                    e1 = make_float2(g1 * y1.x, g1 * y1.y);
                 } else {
                     const unsigned code = pc[kk];
-                    const int b = min((int)(code & 255), f.B - 1), mq = (code >> 8) & 3;
-                    float2 r = make_float2(f.cs[b][0], f.cs[b][1]);   // exp(j phi_b)
-                    const int qt = mq * (4 / f.S);   // quarter turns of exp(j mq 2pi/S)
-                    for (int i = 0; i < qt; ++i) r = make_float2(-r.y, r.x);
-                    float2 yo;
-                    yo.x = __shfl_xor_sync(0xffffffffu, yq.x, 16);
-                    yo.y = __shfl_xor_sync(0xffffffffu, yq.y, 16);
-                    const float2 y0 = q ? yo : yq, y1 = q ? yq : yo;
-                    int lab;
-                    if (mode == 3) {          // data-aided: the known symbol
-                        lab = rl[kk];
-                        if (DIMS == 2) lab = q ? (lab & ((1 << f.m_pol) - 1)) : (lab >> f.m_pol);
+                    const int b = min((int)(code & 255), f.B - 1);
+                    const int qt = (int)((code >> 8) & 3) * qt_step;
+                    float2 rot = make_float2(f.cs[b][0], f.cs[b][1]);   // exp(j phi)
+                    for (int i = 0; i < qt; ++i) rot = make_float2(-rot.y, rot.x);
+                    float2 d0, d1;
+                    if (MODE == 3) {
+                        const int lab = rl[kk];
+                        if (DIMS == 4) {
+                            const float4 pt = tb.pts[lab];
+                            d0 = make_float2(pt.x, pt.y);
+                            d1 = make_float2(pt.z, pt.w);
+                        } else {
+                            const float4 px = tb.pts[lab >> f.m_pol];
+                            const float4 py = tb.pts[lab & ((1 << f.m_pol) - 1)];
+                            d0 = make_float2(px.x, px.y);
+                            d1 = make_float2(py.x, py.y);
+                        }
                     } else {
-                        const float2 z0 = cmulc(r, y0), z1 = cmulc(r, y1), zq = cmulc(r, yq);
-                        lab = decide_warp<DIMS>(z0, z1, zq, tb, f, lane);
+                        const float2 z0 = cmulc(rot, y0), z1 = cmulc(rot, y1);   // y exp(-j phi)
+                        const int o = lane & 15;
+                        const bool valid = o < f.n_orb;
+                        const float4 r = tb.orb[valid ? o : 0];
+                        if (DIMS == 4) {
+                            const float P = z0.x * r.x + z0.y * r.y + z1.x * r.z + z1.y * r.w;
+                            const float Q = z0.y * r.x - z0.x * r.y + z1.y * r.z - z1.x * r.w;
+                            float v;
+                            int k;
+                            best_rot(P, Q, f.S, v, k);
+                            const float dist = cnorm(z0) + cnorm(z1) + tb.orbe[valid ? o : 0] - 2.f * v;
+                            const int w = argmin_lane(dist, valid, tb.orblab[valid ? o : 0][k], lane);
+                            const float4 pt = turn(r, k * qt_step);
+                            d0.x = __shfl_sync(0xffffffffu, pt.x, w);
+                            d0.y = __shfl_sync(0xffffffffu, pt.y, w);
+                            d1.x = __shfl_sync(0xffffffffu, pt.z, w);
+                            d1.y = __shfl_sync(0xffffffffu, pt.w, w);
+                        } else {
+                            float v0, v1;
+                            int k0r, k1r;
+                            best_rot(z0.x * r.x + z0.y * r.y, z0.y * r.x - z0.x * r.y, f.S, v0, k0r);
+                            best_rot(z1.x * r.x + z1.y * r.y, z1.y * r.x - z1.x * r.y, f.S, v1, k1r);
+                            const float eo = tb.orbe[valid ? o : 0];
+                            const int w0 = argmin_lane(cnorm(z0) + eo - 2.f * v0, valid,
+                                                       tb.orblab[valid ? o : 0][k0r], lane);
+                            const int w1 = argmin_lane(cnorm(z1) + eo - 2.f * v1, valid,
+                                                       tb.orblab[valid ? o : 0][k1r], lane);
+                            const float4 p0 = turn(r, k0r * qt_step), p1 = turn(r, k1r * qt_step);
+                            d0.x = __shfl_sync(0xffffffffu, p0.x, w0);
+                            d0.y = __shfl_sync(0xffffffffu, p0.y, w0);
+                            d1.x = __shfl_sync(0xffffffffu, p1.x, w1);
+                            d1.y = __shfl_sync(0xffffffffu, p1.y, w1);
+                        }
                     }
-                    const float4 pt = tb.pts[lab];
-                    float2 d;
-                    if (DIMS == 4) d = q ? make_float2(pt.z, pt.w) : make_float2(pt.x, pt.y);
-                    else d = make_float2(pt.x, pt.y);
-                    e = csub(cmul(d, r), yq);
+                    e0 = csub(cmul(d0, rot), y0);
+                    e1 = csub(cmul(d1, rot), y1);
                 }
-                const float2 ce = make_float2(mu * e.x, -mu * e.y);   // mu conj(e)
+                // h_q += mu conj(e_q) X_k
+                const float2 c0v = make_float2(mu * e0.x, -mu * e0.y), c1v = make_float2(mu * e1.x, -mu * e1.y);
 #pragma unroll
                 for (int i = 0; i < NT; ++i) {
-                    h[i].x += ce.x * xv[i].x - ce.y * xv[i].y;
-                    h[i].y += ce.x * xv[i].y + ce.y * xv[i].x;
+                    const float2 xv = xval(kk, i);
+                    h[0][i] = cadd(h[0][i], cmul(c0v, xv));
+                    h[1][i] = cadd(h[1][i], cmul(c1v, xv));
                 }
+                float2 bnn0 = make_float2(0.f, 0.f), bnn1 = make_float2(0.f, 0.f);
+                if (kk + 2 < n) base(kk + 2, bnn0, bnn1);
+                bc0 = bn0; bc1 = bn1;
+                bn0 = bnn0; bn1 = bnn1;
+                ep0 = e0; ep1 = e1;
             }
         }
     }
     if (warp == 0) {
 #pragma unroll
-        for (int i = 0; i < NT; ++i) {
-            const int t = j + 8 * i;
-            if (t < T) taps_out[(((long)s * 2 + q) * 2 + p) * T + t] = h[i];
-        }
+        for (int q = 0; q < 2; ++q)
+#pragma unroll
+            for (int i = 0; i < NT; ++i) {
+                const int t = j + 16 * i;
+                if (t < T) taps_out[(((long)s * 2 + q) * 2 + p) * T + t] = h[q][i];
+            }
     }
 }
 
@@ -360,19 +417,47 @@ __global__ void ref_labels_kernel(const uint8_t *__restrict__ bits, uint8_t *__r
     lab[(long)s * n + i] = (uint8_t)v;
 }
 
+template <int T, int MODE>
+cudaError_t lms_launch_mode(const float2 *x, long ns, const float2 *ti, float2 *to, long k0,
+                            int n_upd, const uint16_t *pcode, long pstride, int passes, float mu,
+                            const uint8_t *ref, long rstride, int S, const FmtDev &f,
+                            cudaStream_t st) {
+    if (f.dims == 4)
+        lms_kernel<T, 4, MODE><<<S, 256, 0, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes,
+                                                  mu, ref, rstride, f);
+    else
+        lms_kernel<T, 2, MODE><<<S, 256, 0, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes,
+                                                  mu, ref, rstride, f);
+    return cudaGetLastError();
+}
+
 template <int T>
 cudaError_t lms_dispatch_dims(const float2 *x, long ns, const float2 *ti, float2 *to, long k0,
                               int n_upd, const uint16_t *pcode, long pstride, int mode,
                               int passes, unsigned long long u0, int n_cma, float mu,
                               const uint8_t *ref, long rstride, int S, const FmtDev &f,
                               cudaStream_t st) {
-    if (f.dims == 4)
-        lms_kernel<T, 4><<<S, 256, 0, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, mode, passes,
-                                            u0, n_cma, mu, ref, rstride, f);
-    else
-        lms_kernel<T, 2><<<S, 256, 0, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, mode, passes,
-                                            u0, n_cma, mu, ref, rstride, f);
-    return cudaGetLastError();
+    switch (mode) {
+        case 0: return lms_launch_mode<T, 0>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st);
+        case 1: return lms_launch_mode<T, 1>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st);
+        case 3: return lms_launch_mode<T, 3>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st);
+        case 2: {
+            // CMA while the update count is below n_cma, DD after (one pass)
+            const long ncma = (u0 >= (unsigned long long)n_cma) ? 0 : std::min<long>(n_upd, (long)(n_cma - u0));
+            cudaError_t e = cudaSuccess;
+            const float2 *src = ti;
+            if (ncma > 0) {
+                e = lms_launch_mode<T, 0>(x, ns, src, to, k0, (int)ncma, pcode, pstride, 1, mu, ref, rstride, S, f, st);
+                if (e != cudaSuccess) return e;
+                src = to;
+            }
+            if (n_upd - ncma > 0)
+                e = lms_launch_mode<T, 1>(x, ns, src, to, k0 + ncma, (int)(n_upd - ncma), pcode, pstride, 1, mu,
+                                          ref, rstride, S, f, st);
+            return e;
+        }
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 template <int T>

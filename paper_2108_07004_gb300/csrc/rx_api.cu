@@ -301,7 +301,7 @@ int ensure_buffers(rx_handle *h, long N) {
     if (h->cap_n >= N && h->cap_s == S && h->cap_lag == h->lag && h->sd) return RX_OK;
     free_buffers(h);
     const long ns = 2 * N;
-    const long ncta = (N + bps_cta_range() - 1) / bps_cta_range() + 2;
+    const long ncta = (N + bps_cta_range(1) - 1) / bps_cta_range(1) + 2;
     const long ncta_d = (h->block + 2 * h->W + 255) / 256 + 2;
     CK(cudaMalloc(&h->x, sizeof(float2) * (size_t)S * 2 * ns));
     CK(cudaMalloc(&h->y, sizeof(float2) * (size_t)S * 2 * N));
@@ -340,7 +340,7 @@ int ensure_streams(rx_handle *h) {
 int check_config(rx_handle *h) {
     if (h->sps != 2) return fail(RX_EINVAL, "sps must be 2");
     if (h->T != 7 && h->T != 15 && h->T != 31) return fail(RX_EINVAL, "taps must be 7, 15 or 31");
-    if (h->B < 2 || h->B > RX_MAXB) return fail(RX_EINVAL, "bps_phases must be 2..%d", RX_MAXB);
+    if (h->B < 2 || h->B > RX_MAXB || (h->B & 1)) return fail(RX_EINVAL, "bps_phases must be even, 2..%d", RX_MAXB);
     if (h->n_fft != 1024 && h->n_fft != 4096) return fail(RX_EINVAL, "fft must be 1024 or 4096");
     if (h->n_ov < 2 || (h->n_ov & 1) || h->n_ov >= h->n_fft / 2)
         return fail(RX_EINVAL, "overlap must be even and < fft/2");
@@ -499,7 +499,8 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         STAGE(ST_FIR, st, 1, launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st));
         const long a = std::max(0L, k0 - h->W / 2);
         const long e = (n == nblk - 1) ? N : k1 - h->W / 2;
-        STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, h->dsum, S, f, st));
+        const int rounds = bps_rounds(e - a, S);
+        STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, h->dsum, rounds, S, f, st));
         const int cin = (int)(n & 1), cout = 1 - cin;
         if (n == 0 && h->trained) {
             // the training phases fix the start quadrant of the unwrap
@@ -511,7 +512,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
                             (int)sd_stride, carry_base + 2 * cout, (int)sd_stride, h->z, N, a,
                             h->pcode, N, a, h->part_u, h->sig, 1,
                             &h->sd[0].ticket_unwrap, (int)(sizeof(StreamDev) / sizeof(unsigned)),
-                            S, f, st));
+                            rounds, S, f, st));
         const double *s2 = h->sigma2_fixed > 0 ? h->sig_fixed : h->sig;
         if ((e - a + 255) / 256 > h->cap_pd) return fail(RX_EINVAL, "internal: demap partials");
         STAGE(ST_DEMAP, st, 1, launch_demap(h->z, N, a, a, e, s2, 1, llr + (size_t)a * m, N * m, cnt, S, f, st));
@@ -860,10 +861,11 @@ int rx_bps(rx_handle *h, const void *y, size_t n_y, size_t a, size_t e, size_t n
     if (!h || !y || !b_out) return fail(RX_EINVAL, "NULL argument");
     if (e < a || e > n_y || n_valid > n_y) return fail(RX_EINVAL, "bad range");
     int *dsum = nullptr;
-    const long ncta = ((long)(e - a) + bps_cta_range() - 1) / bps_cta_range();
+    const int rounds = bps_rounds((long)(e - a), h->streams);
+    const long ncta = ((long)(e - a) + bps_cta_range(rounds) - 1) / bps_cta_range(rounds);
     CK(cudaMallocAsync(&dsum, sizeof(int) * (size_t)h->streams * (ncta + 1), h->st));
     cudaError_t err = launch_bps((const float2 *)y, (long)n_y, (long)a, (long)e, (long)n_valid, h->W,
-                                 b_out, (long)(e - a), 0, dsum, h->streams, h->fmt, h->st);
+                                 b_out, (long)(e - a), 0, dsum, rounds, h->streams, h->fmt, h->st);
     cudaFreeAsync(dsum, h->st);
     CK(err);
     return RX_OK;
@@ -876,7 +878,8 @@ int rx_unwrap(rx_handle *h, const void *y, size_t n_y, const uint8_t *b, size_t 
     if (e <= a || e > n_y) return fail(RX_EINVAL, "bad range");
     const int S = h->streams;
     const long K = (long)(e - a);
-    const long ncta = (K + bps_cta_range() - 1) / bps_cta_range();
+    const int rounds = bps_rounds(K, S);
+    const long ncta = (K + bps_cta_range(rounds) - 1) / bps_cta_range(rounds);
     // interior increments come from the phase search; recompute them here
     int *dsum = nullptr;
     double *part = nullptr;
@@ -885,10 +888,10 @@ int rx_unwrap(rx_handle *h, const void *y, size_t n_y, const uint8_t *b, size_t 
     CK(cudaMallocAsync(&part, sizeof(double) * (size_t)S * ncta, h->st));
     CK(cudaMallocAsync(&ticket, sizeof(unsigned) * (size_t)S, h->st));
     CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned) * (size_t)S, h->st));
-    CK(launch_dsum_from_b(b, K, a, e, dsum, S, h->fmt.B, h->st));
+    CK(launch_dsum_from_b(b, K, a, e, dsum, rounds, S, h->fmt.B, h->st));
     cudaError_t err = launch_unwrap((const float2 *)y, (long)n_y, b, K, 0, (long)a, (long)e, dsum,
                                     carry_in, 2, carry_out, 2, (float2 *)z, K, 0, pcode, K, 0, part,
-                                    sigma2, 1, ticket, 1, S, h->fmt, h->st);
+                                    sigma2, 1, ticket, 1, rounds, S, h->fmt, h->st);
     cudaFreeAsync(dsum, h->st);
     cudaFreeAsync(part, h->st);
     cudaFreeAsync(ticket, h->st);

@@ -78,11 +78,12 @@ cudaError_t launch_align(const float2 *x, long ns, float2 *taps, const uint8_t *
                          long ref_stride, int n_train, int n_streams, int T, const FmtDev &f,
                          cudaStream_t st);
 
-int bps_cta_range();   // output symbols per BPS / unwrap CTA
+int bps_cta_range(int rounds);              // output symbols per BPS / unwrap block
+int bps_rounds(long len, int n_streams);    // rounds that fill about one wave
 
 cudaError_t launch_bps(const float2 *y, long y_stride, long a, long e, long n_valid,
                        int W, uint8_t *bout, long bout_stride, long bout_off,
-                       int *dsum, int n_streams, const FmtDev &f, cudaStream_t st);
+                       int *dsum, int rounds, int n_streams, const FmtDev &f, cudaStream_t st);
 
 cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long b_stride,
                           long b_off, long a, long e, const int *dsum,
@@ -91,7 +92,7 @@ cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long
                           float2 *z, long z_stride, long z_off,
                           uint16_t *pcode, long pcode_stride, long pcode_off,
                           double *partial, double *sigma2_out, int sigma2_stride,
-                          unsigned int *ticket, int ticket_stride,
+                          unsigned int *ticket, int ticket_stride, int rounds,
                           int n_streams, const FmtDev &f, cudaStream_t st);
 
 cudaError_t launch_anchor(const uint8_t *b, long b_stride, const uint16_t *tcode, long t_stride,
@@ -99,7 +100,7 @@ cudaError_t launch_anchor(const uint8_t *b, long b_stride, const uint16_t *tcode
                           cudaStream_t st);
 
 cudaError_t launch_dsum_from_b(const uint8_t *b, long b_stride, long a, long e, int *dsum,
-                               int n_streams, int B, cudaStream_t st);
+                               int rounds, int n_streams, int B, cudaStream_t st);
 
 struct DemapCount {
     const uint8_t *ref_lab;   // [S][N] labels of the reference (or null)
