@@ -348,32 +348,21 @@ unwrap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *__rest
         last = (prev == (unsigned)n_cta - 1);
     }
     __syncthreads();
-    if (last && tid == 0) {
-        __threadfence();
-        double tot = 0.0;
-        for (int cc = 0; cc < n_cta; ++cc) tot += ((volatile double *)partial)[(long)s * n_cta + cc];
-        sigma2_out[s * s2_stride] = tot / (2.0 * (double)(e - a));
-        ticket[s * ticket_stride] = 0u;
-    }
-}
-
-// interior unwrap increments of each kR range, from phase indices b (index k - a)
-__global__ void dsum_kernel(const uint8_t *__restrict__ b, long b_stride, long a, long e,
-                            int *__restrict__ dsum, int n_cta, int B, int kR) {
-    __shared__ int red[8];
-    const int s = blockIdx.y, c = blockIdx.x, tid = threadIdx.x;
-    const long out0 = a + (long)c * kR, out1 = min(out0 + kR, e);
-    const uint8_t *bs = b + (long)s * b_stride;
-    int acc = 0;
-    for (long k = out0 + 1 + tid; k < out1; k += 256) acc += unwrap_step(bs[k - 1 - a], bs[k - a], B);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    if (!last) return;
+    __threadfence();
+    const volatile double *pp = partial + (long)s * n_cta;
+    double v = 0.0;
+    for (int cc = tid; cc < n_cta; cc += 256) v += pp[cc];
+    __shared__ double tr[256];
+    tr[tid] = v;
     __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w) tr[tid] += tr[tid + w];
+        __syncthreads();
+    }
     if (tid == 0) {
-        int tot = 0;
-        for (int w = 0; w < 8; ++w) tot += red[w];
-        dsum[s * n_cta + c] = tot;
+        sigma2_out[s * s2_stride] = tr[0] / (2.0 * (double)(e - a));
+        ticket[s * ticket_stride] = 0u;
     }
 }
 

@@ -121,17 +121,18 @@ demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
              const double *__restrict__ sigma2, int s2_stride, float *__restrict__ llr,
              long llr_stride, DemapCount cnt, const __grid_constant__ FmtDev f) {
     constexpr int M_OUT = (DIMS == 4) ? MB : 2 * MB;
-    __shared__ double red[8][3];
-    __shared__ unsigned long long redn[8][2];
+    __shared__ float red[8][3];
+    __shared__ int redn[8][2];
     __shared__ bool last;
     const int s = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long k = a + (long)blockIdx.x * blockDim.x + tid;
-    const double s2 = sigma2[s * s2_stride];
-    const float c2 = (float)(1.4426950408889634 / s2);
+    const float c2 = 1.4426950408889634f / (float)sigma2[s * s2_stride];
     const float2 *zx = z + (long)s * 2 * z_stride;
     const float2 *zy = zx + z_stride;
-    unsigned long long nerr = 0, ncnt = 0;
-    double gsum = 0.0, en = 0.0, ed = 0.0;
+    // per-thread counts in 32-bit / float (one symbol each); warp sums are
+    // widened to float64 before the block and grid reductions
+    int nerr = 0, ncnt = 0;
+    float gsum = 0.f, en = 0.f, ed = 0.f;
     if (k < e) {
         const float2 z0 = zx[k - a], z1 = zy[k - a];
         const bool counted = cnt.ref_lab && k >= cnt.c0 && k < cnt.c1;
@@ -168,7 +169,6 @@ demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
         }
     }
     if (!cnt.sd) return;
-    // block reduction, then the last block of the launch adds all partials in order
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         nerr += __shfl_xor_sync(0xffffffffu, nerr, off);
@@ -197,22 +197,30 @@ demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
         last = (prev == gridDim.x - 1);
     }
     __syncthreads();
-    if (last && tid == 0) {
-        __threadfence();
-        const volatile double *pp = cnt.partial + (long)s * gridDim.x * 5;
-        double t0 = 0, t1 = 0, t2 = 0;
-        unsigned long long n0 = 0, n1 = 0;
-        for (unsigned c = 0; c < gridDim.x; ++c) {
-            t0 += pp[c * 5 + 0]; t1 += pp[c * 5 + 1]; t2 += pp[c * 5 + 2];
-            n0 += (unsigned long long)pp[c * 5 + 3]; n1 += (unsigned long long)pp[c * 5 + 4];
-        }
+    if (!last) return;
+    // the last block of this stream adds the partials: strided per thread, then
+    // a fixed-order tree, so the sum does not depend on block timing
+    __threadfence();
+    const volatile double *pp = cnt.partial + (long)s * gridDim.x * 5;
+    __shared__ double tr[5][256];
+    double v[5] = {0, 0, 0, 0, 0};
+    for (unsigned c = tid; c < gridDim.x; c += blockDim.x)
+        for (int i = 0; i < 5; ++i) v[i] += pp[c * 5 + i];
+    for (int i = 0; i < 5; ++i) tr[i][tid] = v[i];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (tid < w)
+            for (int i = 0; i < 5; ++i) tr[i][tid] += tr[i][tid + w];
+        __syncthreads();
+    }
+    if (tid == 0) {
         StreamDev &sd = cnt.sd[s];
-        sd.gmi_sum += t0;
-        sd.evm_num += t1;
-        sd.evm_den += t2;
-        sd.bit_errors += n0;
-        sd.n_sym += n1;
-        sd.sigma2 = s2;
+        sd.gmi_sum += tr[0][0];
+        sd.evm_num += tr[1][0];
+        sd.evm_den += tr[2][0];
+        sd.bit_errors += (unsigned long long)tr[3][0];
+        sd.n_sym += (unsigned long long)tr[4][0];
+        sd.sigma2 = sigma2[s * s2_stride];
         sd.ticket_demap = 0u;
     }
 }

@@ -69,8 +69,7 @@ __device__ __forceinline__ float4 turn(float4 r, int k) {
 __device__ __forceinline__ int argmin_lane(float dist, bool valid, int label, int lane) {
     const unsigned bits = valid ? __float_as_uint(fmaxf(dist, 0.f)) : 0xffffffffu;
     const unsigned mn = __reduce_min_sync(0xffffffffu, bits);
-    const unsigned tie = __ballot_sync(0xffffffffu, bits == mn && lane < 16);
-    if (__popc(tie) == 1) return __ffs(tie) - 1;
+    // among the lanes at the minimum, the lowest label (branch-free)
     const unsigned key = (bits == mn && lane < 16) ? (unsigned)label : 0xffffffffu;
     const unsigned ml = __reduce_min_sync(0xffffffffu, key);
     return __ffs(__ballot_sync(0xffffffffu, key == ml && lane < 16)) - 1;
@@ -111,7 +110,7 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
            long pcode_stride, int passes, float mu, const uint8_t *__restrict__ ref_lab,
            long ref_stride, const __grid_constant__ FmtDev f) {
     constexpr int D = (T - 1) / 2;
-    constexpr int NSX = 2 * kCH + 2 * D + 2;
+    constexpr int NSX = 2 * kCH + 2 * D + 8;   // + slack read by the look-ahead past the span
     constexpr int NT = (T + 15) / 16;
     __shared__ float2 xs[2][NSX];
     __shared__ float2 r1s[kCH];
@@ -137,7 +136,7 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
         for (int c0 = 0; c0 < n_upd; c0 += kCH) {
             const int n = min(kCH, n_upd - c0);
             const long kb = k0 + c0;
-            const int nsx = 2 * n + 2 * D + 2;
+            const int nsx = 2 * n + 2 * D + 8;
             __syncthreads();
             // local sample index of symbol kb + kk, tap t: 2 kk + 2 + 2D - t
             for (int i = threadIdx.x; i < 2 * nsx; i += blockDim.x) {
@@ -179,6 +178,7 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
             base(0, bc0, bc1);
             if (n > 1) base(1, bn0, bn1);
             float2 ep0 = make_float2(0.f, 0.f), ep1 = make_float2(0.f, 0.f);
+#pragma unroll 2
             for (int kk = 0; kk < n; ++kk) {
                 const float2 r1 = r1s[kk];
                 const float2 y0 = cadd(bc0, cmul(make_float2(mu * ep0.x, mu * ep0.y), r1));
@@ -253,8 +253,8 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
                     h[0][i] = cadd(h[0][i], cmul(c0v, xv));
                     h[1][i] = cadd(h[1][i], cmul(c1v, xv));
                 }
-                float2 bnn0 = make_float2(0.f, 0.f), bnn1 = make_float2(0.f, 0.f);
-                if (kk + 2 < n) base(kk + 2, bnn0, bnn1);
+                float2 bnn0, bnn1;
+                base(kk + 2, bnn0, bnn1);      // past the span: reads the zeroed slack, unused
                 bc0 = bn0; bc1 = bn1;
                 bn0 = bnn0; bn1 = bnn1;
                 ep0 = e0; ep1 = e1;
@@ -417,18 +417,38 @@ __global__ void ref_labels_kernel(const uint8_t *__restrict__ bits, uint8_t *__r
     lab[(long)s * n + i] = (uint8_t)v;
 }
 
+// The recursion is latency-bound: a block asks for (nearly) all of an SM's
+// shared memory so that no other kernel's blocks share its SM and its warp
+// issues whenever it is ready.
+template <int T, int DIMS, int MODE>
+cudaError_t lms_launch_one(const float2 *x, long ns, const float2 *ti, float2 *to, long k0, int n_upd,
+                           const uint16_t *pcode, long pstride, int passes, float mu,
+                           const uint8_t *ref, long rstride, int S, const FmtDev &f, cudaStream_t st) {
+    auto kern = lms_kernel<T, DIMS, MODE>;
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    if (e != cudaSuccess) return e;
+    int dev = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    int dyn = optin - (int)fa.sharedSizeBytes;
+    if (dyn < 0) dyn = 0;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
+    if (e != cudaSuccess) return e;
+    kern<<<S, 256, dyn, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, f);
+    return cudaGetLastError();
+}
+
 template <int T, int MODE>
 cudaError_t lms_launch_mode(const float2 *x, long ns, const float2 *ti, float2 *to, long k0,
                             int n_upd, const uint16_t *pcode, long pstride, int passes, float mu,
                             const uint8_t *ref, long rstride, int S, const FmtDev &f,
                             cudaStream_t st) {
     if (f.dims == 4)
-        lms_kernel<T, 4, MODE><<<S, 256, 0, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes,
-                                                  mu, ref, rstride, f);
-    else
-        lms_kernel<T, 2, MODE><<<S, 256, 0, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes,
-                                                  mu, ref, rstride, f);
-    return cudaGetLastError();
+        return lms_launch_one<T, 4, MODE>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref,
+                                          rstride, S, f, st);
+    return lms_launch_one<T, 2, MODE>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref,
+                                      rstride, S, f, st);
 }
 
 template <int T>

@@ -326,7 +326,10 @@ int ensure_buffers(rx_handle *h, long N) {
 
 int ensure_streams(rx_handle *h) {
     if (h->lag >= 2 && !h->side) {
-        CK(cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking));
+        // the sequential adaptation runs on a high-priority stream
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        CK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest));
         CK(cudaEventCreateWithFlags(&h->ev_unwrap, cudaEventDisableTiming));
     }
     while ((int)h->ev_lms.size() < h->lag + 1) {
