@@ -366,6 +366,26 @@ unwrap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *__rest
     }
 }
 
+// interior unwrap increments of each kR range, from phase indices b (index k - a)
+__global__ void dsum_kernel(const uint8_t *__restrict__ b, long b_stride, long a, long e,
+                            int *__restrict__ dsum, int n_cta, int B, int kR) {
+    __shared__ int red[8];
+    const int s = blockIdx.y, c = blockIdx.x, tid = threadIdx.x;
+    const long out0 = a + (long)c * kR, out1 = min(out0 + kR, e);
+    const uint8_t *bs = b + (long)s * b_stride;
+    int acc = 0;
+    for (long k = out0 + 1 + tid; k < out1; k += 256) acc += unwrap_step(bs[k - 1 - a], bs[k - a], B);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+    if ((tid & 31) == 0) red[tid >> 5] = acc;
+    __syncthreads();
+    if (tid == 0) {
+        int tot = 0;
+        for (int w = 0; w < 8; ++w) tot += red[w];
+        dsum[s * n_cta + c] = tot;
+    }
+}
+
 template <int DIMS, int NORB>
 cudaError_t bps_launch_t(const float2 *y, long ys, long a, long e, long nv, int W, uint8_t *bout,
                          long bst, int *dsum, int rounds, int n_streams, const FmtDev &f,
