@@ -219,6 +219,29 @@ int rx_unwrap(rx_handle *h, const void *y, size_t n_y, const uint8_t *b,
               size_t a, size_t e, const int32_t *carry_in, void *z,
               uint16_t *pcode, int32_t *carry_out, double *sigma2);
 
+/* rx_unwrap without any device allocation.  The paper has no counterpart:
+ * this entry point exists for callers that must not allocate device memory
+ * while they process -- a real-time thread on which cudaMalloc / cudaFree
+ * (which can synchronise the whole device and take unbounded time) is not
+ * allowed, or an application whose device memory is owned by another
+ * allocator or a fixed budget.  Arguments, layouts and results are those of
+ * rx_unwrap; the caller still passes every input and output buffer.
+ * Scratch (per-block unwrap increments, noise partial sums, completion
+ * tickets) lives in one static device array of 64 KiB compiled into the
+ * library; every GPU that loads the library keeps it until the process
+ * exits.  S streams x n_blocks blocks need about 12 bytes per (stream,
+ * block) plus 4 bytes per stream; a call that would need more than the
+ * 64 KiB returns RX_EINVAL without launching anything.  The first call on
+ * a device looks up the array's device address with that device current
+ * (once per device; make that first call before any stream capture).  All
+ * calls share the array and it keeps the last call's contents: the tickets
+ * are cleared at the start of every call, so calls that are ordered on the
+ * GPU are independent, but calls that overlap on the GPU (different streams,
+ * different handles, different host threads) race on the scratch. */
+int rx_unwrap_static(rx_handle *h, const void *y, size_t n_y, const uint8_t *b, size_t a,
+                     size_t e, const int32_t *carry_in, void *z, uint16_t *pcode,
+                     int32_t *carry_out, double *sigma2);
+
 /* A5 LLRs: llr [S][K][m] from z [S][2][K] with noise variance sigma2 [S]
  * (float64, device). */
 int rx_demap(rx_handle *h, const void *z, size_t K, const double *sigma2,

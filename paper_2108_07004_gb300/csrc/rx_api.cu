@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -598,6 +599,40 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     return check_config(h);
 }
 
+// ---------------------------------------------------------------------------
+// Scratch of rx_unwrap_static, which allocates no device memory: one static
+// device array shared by every call in the process (per device).  Layout per
+// call: S tickets (uint32), then S x n_blocks unwrap increments (int32), then
+// S x n_blocks noise partial sums (float64), each region 256-byte aligned.
+// ---------------------------------------------------------------------------
+constexpr size_t kStaticScratchBytes = 64 * 1024;
+static __device__ __align__(256) unsigned char g_unwrap_scratch[kStaticScratchBytes];
+
+constexpr int kMaxDevices = 64;
+void *g_scratch_addr[kMaxDevices] = {};   // device address of g_unwrap_scratch per device
+std::mutex g_scratch_mu;
+
+// Device address of the scratch array on the current device.  The first call
+// on a device looks it up with that device current (host code cannot use the
+// array's name as a device address).
+int static_scratch(void **out) {
+    int dev = -1;
+    CK(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(RX_EINVAL, "device %d beyond the %d supported", dev, kMaxDevices);
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_unwrap_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(RX_ECUDA, "cudaGetSymbolAddress of the static scratch: %s", cudaGetErrorString(e));
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return RX_OK;
+}
+
+size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
 }  // namespace
 
 // ===========================================================================
@@ -899,6 +934,40 @@ int rx_unwrap(rx_handle *h, const void *y, size_t n_y, const uint8_t *b, size_t 
     cudaFreeAsync(part, h->st);
     cudaFreeAsync(ticket, h->st);
     CK(err);
+    return RX_OK;
+}
+
+int rx_unwrap_static(rx_handle *h, const void *y, size_t n_y, const uint8_t *b, size_t a, size_t e,
+                     const int32_t *carry_in, void *z, uint16_t *pcode, int32_t *carry_out,
+                     double *sigma2) {
+    if (!h || !y || !b || !carry_in || !z || !pcode || !carry_out || !sigma2)
+        return fail(RX_EINVAL, "NULL argument");
+    if (e <= a || e > n_y) return fail(RX_EINVAL, "bad range");
+    const int S = h->streams;
+    const long K = (long)(e - a);
+    const int rounds = bps_rounds(K, S);
+    const long ncta = (K + bps_cta_range(rounds) - 1) / bps_cta_range(rounds);
+    const size_t off_dsum = align256(sizeof(unsigned) * (size_t)S);
+    const size_t off_part = off_dsum + align256(sizeof(int) * (size_t)S * ncta);
+    const size_t need = off_part + sizeof(double) * (size_t)S * ncta;
+    if (need > kStaticScratchBytes)
+        return fail(RX_EINVAL,
+                    "rx_unwrap_static: %d stream(s) x %ld block(s) need %zu bytes of scratch, "
+                    "more than the static %zu bytes; use fewer streams or a shorter range",
+                    S, ncta, need, kStaticScratchBytes);
+    void *base = nullptr;
+    int rc = static_scratch(&base);
+    if (rc != RX_OK) return rc;
+    unsigned char *sc = static_cast<unsigned char *>(base);
+    unsigned *ticket = reinterpret_cast<unsigned *>(sc);
+    int *dsum = reinterpret_cast<int *>(sc + off_dsum);
+    double *part = reinterpret_cast<double *>(sc + off_part);
+    // the tickets must start at zero; the other regions are written before read
+    CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned) * (size_t)S, h->st));
+    CK(launch_dsum_from_b(b, K, a, e, dsum, rounds, S, h->fmt.B, h->st));
+    CK(launch_unwrap((const float2 *)y, (long)n_y, b, K, 0, (long)a, (long)e, dsum, carry_in, 2,
+                     carry_out, 2, (float2 *)z, K, 0, pcode, K, 0, part, sigma2, 1, ticket, 1,
+                     rounds, S, h->fmt, h->st));
     return RX_OK;
 }
 

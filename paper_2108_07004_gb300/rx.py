@@ -66,6 +66,7 @@ _PROTOS = {
     "rx_train": (_I, [_VP, _VP, _SZ, _VP, _VP]),
     "rx_bps": (_I, [_VP, _VP, _SZ, _SZ, _SZ, _SZ, _VP]),
     "rx_unwrap": (_I, [_VP, _VP, _SZ, _VP, _SZ, _SZ, _VP, _VP, _VP, _VP, _VP]),
+    "rx_unwrap_static": (_I, [_VP, _VP, _SZ, _VP, _SZ, _SZ, _VP, _VP, _VP, _VP, _VP]),
     "rx_demap": (_I, [_VP, _VP, _SZ, _VP, _VP]),
 }
 
@@ -247,6 +248,12 @@ class Receiver:
     def unwrap(self, y, b, a, e, carry_in, z, pcode, carry_out, sigma2):
         _ck(lib().rx_unwrap(self.h, _ptr(y), y.shape[-1], _ptr(b), a, e, _ptr(carry_in),
                             _ptr(z), _ptr(pcode), _ptr(carry_out), _ptr(sigma2)))
+
+    def unwrap_static(self, y, b, a, e, carry_in, z, pcode, carry_out, sigma2):
+        """unwrap() without device allocation (static 64 KiB scratch; for
+        callers that may not allocate while they process)."""
+        _ck(lib().rx_unwrap_static(self.h, _ptr(y), y.shape[-1], _ptr(b), a, e, _ptr(carry_in),
+                                   _ptr(z), _ptr(pcode), _ptr(carry_out), _ptr(sigma2)))
 
     def demap(self, z: torch.Tensor, sigma2: torch.Tensor, llr: torch.Tensor):
         _ck(lib().rx_demap(self.h, _ptr(z), z.shape[-1], _ptr(sigma2), _ptr(llr)))
