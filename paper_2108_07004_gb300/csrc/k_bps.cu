@@ -75,7 +75,10 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
         const bool valid = (i >= 0) && (i < n_valid);
         float2 ya = make_float2(0.f, 0.f), yb = make_float2(0.f, 0.f);
         if (valid) { ya = yx[i]; yb = yy[i]; }
-        float cr[2][NORB], ci[2][NORB];
+        // per orbit o (and polarisation for 2D tables): CR = (Re c, Im c) and
+        // CI = (Im c, -Re c), c = sum_p y_p conj(rep_p); then for a test phase,
+        // (P, Q) = cos(phi) CR + sin(phi) CI is one packed multiply and one packed FMA
+        f32x2 CR[2][NORB], CI[2][NORB];
         float yn0, yn1;
         if (DIMS == 4) {
             yn0 = cnorm(ya) + cnorm(yb);
@@ -84,8 +87,10 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
             for (int o = 0; o < NORB; ++o) {
                 if (o < f.n_orb) {
                     const float r0 = f.orb[o][0], r1 = f.orb[o][1], r2 = f.orb[o][2], r3 = f.orb[o][3];
-                    cr[0][o] = ya.x * r0 + ya.y * r1 + yb.x * r2 + yb.y * r3;
-                    ci[0][o] = ya.y * r0 - ya.x * r1 + yb.y * r2 - yb.x * r3;
+                    const float cr = ya.x * r0 + ya.y * r1 + yb.x * r2 + yb.y * r3;
+                    const float ci = ya.y * r0 - ya.x * r1 + yb.y * r2 - yb.x * r3;
+                    CR[0][o] = pk2(cr, ci);
+                    CI[0][o] = pk2(ci, -cr);
                 }
             }
         } else {
@@ -95,50 +100,56 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
             for (int o = 0; o < NORB; ++o) {
                 if (o < f.n_orb) {
                     const float r0 = f.orb[o][0], r1 = f.orb[o][1];
-                    cr[0][o] = ya.x * r0 + ya.y * r1;
-                    ci[0][o] = ya.y * r0 - ya.x * r1;
-                    cr[1][o] = yb.x * r0 + yb.y * r1;
-                    ci[1][o] = yb.y * r0 - yb.x * r1;
+                    const float cr0 = ya.x * r0 + ya.y * r1, ci0 = ya.y * r0 - ya.x * r1;
+                    const float cr1 = yb.x * r0 + yb.y * r1, ci1 = yb.y * r0 - yb.x * r1;
+                    CR[0][o] = pk2(cr0, ci0);
+                    CI[0][o] = pk2(ci0, -cr0);
+                    CR[1][o] = pk2(cr1, ci1);
+                    CI[1][o] = pk2(ci1, -cr1);
                 }
             }
         }
         const int slot = (jc + 1) % RX_NCHUNK;
         const int hb = B >> 1;
-        // test phases b and b + B/2 together: four independent minimum chains
+        // test phases b and b + B/2 together: independent minimum chains
         for (int b = 0; b < hb; ++b) {
-            const float cb = f.cs[b][0], sb = f.cs[b][1];
-            const float cb2 = f.cs[b + hb][0], sb2 = f.cs[b + hb][1];
+            const f32x2 C1 = pk2(f.cs[b][0], f.cs[b][0]), S1 = pk2(f.cs[b][1], f.cs[b][1]);
+            const f32x2 C2 = pk2(f.cs[b + hb][0], f.cs[b + hb][0]);
+            const f32x2 S2 = pk2(f.cs[b + hb][1], f.cs[b + hb][1]);
             float md, md2;
             if (DIMS == 4) {
-                float a0 = 3.0e38f, a1 = 3.0e38f, c0m = 3.0e38f, c1m = 3.0e38f;
+                float a0 = 3.0e38f, a1 = 3.0e38f;
 #pragma unroll
-                for (int o = 0; o < NORB; ++o) {
+                for (int o = 0; o < NORB; o += 2) {
                     if (o < f.n_orb) {
-                        const float P = cb * cr[0][o] + sb * ci[0][o];
-                        const float Q = cb * ci[0][o] - sb * cr[0][o];
-                        const float P2 = cb2 * cr[0][o] + sb2 * ci[0][o];
-                        const float Q2 = cb2 * ci[0][o] - sb2 * cr[0][o];
+                        float P, Q, P2, Q2, R, U, R2, U2;
+                        upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P, Q);
+                        upk2(fma2(S2, CI[0][o], mul2(C2, CR[0][o])), P2, Q2);
                         const float v1 = fmaf(-2.f, orbit_v(P, Q, S), f.orbe[o]);
                         const float v2 = fmaf(-2.f, orbit_v(P2, Q2, S), f.orbe[o]);
-                        if (o & 1) { a1 = fminf(a1, v1); c1m = fminf(c1m, v2); }
-                        else       { a0 = fminf(a0, v1); c0m = fminf(c0m, v2); }
+                        if (o + 1 < f.n_orb) {
+                            upk2(fma2(S1, CI[0][o + 1], mul2(C1, CR[0][o + 1])), R, U);
+                            upk2(fma2(S2, CI[0][o + 1], mul2(C2, CR[0][o + 1])), R2, U2);
+                            a0 = fmin3(a0, v1, fmaf(-2.f, orbit_v(R, U, S), f.orbe[o + 1]));
+                            a1 = fmin3(a1, v2, fmaf(-2.f, orbit_v(R2, U2, S), f.orbe[o + 1]));
+                        } else {
+                            a0 = fminf(a0, v1);
+                            a1 = fminf(a1, v2);
+                        }
                     }
                 }
-                md = yn0 + fminf(a0, a1);
-                md2 = yn0 + fminf(c0m, c1m);
+                md = yn0 + a0;
+                md2 = yn0 + a1;
             } else {
                 float x0 = 3.0e38f, x1 = 3.0e38f, w0 = 3.0e38f, w1 = 3.0e38f;
 #pragma unroll
                 for (int o = 0; o < NORB; ++o) {
                     if (o < f.n_orb) {
-                        const float P0 = cb * cr[0][o] + sb * ci[0][o];
-                        const float Q0 = cb * ci[0][o] - sb * cr[0][o];
-                        const float P1 = cb * cr[1][o] + sb * ci[1][o];
-                        const float Q1 = cb * ci[1][o] - sb * cr[1][o];
-                        const float R0 = cb2 * cr[0][o] + sb2 * ci[0][o];
-                        const float U0 = cb2 * ci[0][o] - sb2 * cr[0][o];
-                        const float R1 = cb2 * cr[1][o] + sb2 * ci[1][o];
-                        const float U1 = cb2 * ci[1][o] - sb2 * cr[1][o];
+                        float P0, Q0, P1, Q1, R0, U0, R1, U1;
+                        upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P0, Q0);
+                        upk2(fma2(S1, CI[1][o], mul2(C1, CR[1][o])), P1, Q1);
+                        upk2(fma2(S2, CI[0][o], mul2(C2, CR[0][o])), R0, U0);
+                        upk2(fma2(S2, CI[1][o], mul2(C2, CR[1][o])), R1, U1);
                         x0 = fminf(x0, fmaf(-2.f, orbit_v(P0, Q0, S), f.orbe[o]));
                         x1 = fminf(x1, fmaf(-2.f, orbit_v(P1, Q1, S), f.orbe[o]));
                         w0 = fminf(w0, fmaf(-2.f, orbit_v(R0, U0, S), f.orbe[o]));

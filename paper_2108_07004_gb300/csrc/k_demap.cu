@@ -115,8 +115,80 @@ __device__ __forceinline__ void llr_table(float2 z0, float2 z1, const FmtDev &f,
     gs += g2;
 }
 
+// 4D table of MT points with MB label bits, streaming form: the shift is the
+// minimum distance from the orbit form (|z|^2 + |rep|^2 - 2 max(|P|,|Q|), no
+// per-point state), then every point's exact distance and exponential is
+// added to the two running subset sums of each label bit (the bit pattern of
+// point j is known at compile time).  Twelve accumulators instead of 64
+// stored terms keep the registers low; the result is the same sum.
+template <int MT, int MB>
+__device__ __forceinline__ void llr_4d_stream(float2 z0, float2 z1, const FmtDev &f, float c2,
+                                              float *out, float &gmin, int &jmin, int ref,
+                                              int &nerr, float &gs) {
+    float g = 3.0e38f;
+    const float zn = cnorm(z0) + cnorm(z1);
+#pragma unroll
+    for (int o = 0; o < 16; ++o) {
+        if (o < f.n_orb) {
+            const float P = z0.x * f.orb[o][0] + z0.y * f.orb[o][1] + z1.x * f.orb[o][2] + z1.y * f.orb[o][3];
+            const float Q = z0.y * f.orb[o][0] - z0.x * f.orb[o][1] + z1.y * f.orb[o][2] - z1.x * f.orb[o][3];
+            const float v = (f.S == 4) ? fmaxf(fabsf(P), fabsf(Q)) : (f.S == 2 ? fabsf(P) : P);
+            g = fminf(g, zn + f.orbe[o] - 2.f * v);
+        }
+    }
+    const float sh = fmaf(g, c2, kOff);      // exponent of point j: sh - d_j c2
+    float s0[MB], s1[MB];
+#pragma unroll
+    for (int i = 0; i < MB; ++i) { s0[i] = 0.f; s1[i] = 0.f; }
+    float dmin = 3.0e38f;
+    int jm = 0;
+    // groups of 8 points: the low 3 label bits are fixed per point, the high
+    // bits per group (the group total is added to their subset sums)
+#pragma unroll 1
+    for (int g8 = 0; g8 < MT; g8 += 8) {
+        float tot = 0.f;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int j = g8 + u;
+            const float d = dist_to<4>(z0, z1, f, j);
+            if (d < dmin) { dmin = d; jm = j; }
+            const float ej = exp2f(fmaf(-d, c2, sh));
+            tot += ej;
+#pragma unroll
+            for (int i = 0; i < 3 && i < MB; ++i) {
+                if ((u >> i) & 1) s1[i] += ej;
+                else s0[i] += ej;
+            }
+        }
+#pragma unroll
+        for (int i = 3; i < MB; ++i) {
+            if ((g8 >> i) & 1) s1[i] += tot;
+            else s0[i] += tot;
+        }
+    }
+    gmin = dmin;
+    jmin = jm;
+    bool low = false;
+    int ne = 0;
+    float g2 = 0.f;
+#pragma unroll
+    for (int bp = 0; bp < MB; ++bp) {
+        low |= (s0[bp] < 7.888609052e-31f) | (s1[bp] < 7.888609052e-31f);   // 2^-100
+        const float L = (__log2f(s0[bp]) - __log2f(s1[bp])) * kLn2;
+        out[MB - 1 - bp] = L;
+        if (ref >= 0) {
+            const int bit = (ref >> bp) & 1;
+            ne += (int)((L < 0.f) != (bit != 0));
+            g2 += softplus_bits(bit ? L : -L);
+        }
+    }
+    if (low) llr_table_slow<4, MT, MB>(z0, z1, f, c2, out, ref, &ne, &g2);
+    nerr += ne;
+    gs += g2;
+}
+
 template <int DIMS, int MT, int MB>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, (DIMS == 4 ? 4 : 2))
 demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
              const double *__restrict__ sigma2, int s2_stride, float *__restrict__ llr,
              long llr_stride, DemapCount cnt, const __grid_constant__ FmtDev f) {
@@ -143,7 +215,7 @@ demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
         if (DIMS == 4) {
             float g;
             int jm;
-            llr_table<4, MT, MB>(z0, z1, f, c2, row, g, jm, ref, ne, gs);
+            llr_4d_stream<MT, MB>(z0, z1, f, c2, row, g, jm, ref, ne, gs);
             dist_min = g;
             dmin_energy = f.pe[jm];
         } else {

@@ -55,6 +55,32 @@ __host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 }
 __host__ __device__ __forceinline__ float cnorm(float2 a) { return a.x * a.x + a.y * a.y; }
 
+// ---- packed float pairs (sm_100+ f32x2 arithmetic) ---------------------------
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float a, float b) {
+    f32x2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ void upk2(f32x2 v, float &a, float &b) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {   // a * b + c, per lane
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ float fmin3(float a, float b, float c) {
+    float d;
+    asm("min.f32 %0, %1, %2, %3;" : "=f"(d) : "f"(a), "f"(b), "f"(c));
+    return d;
+}
+
 // ---- launchers (return cudaError_t of the launch) -----------------------------
 cudaError_t launch_cdc(const float2 *in, float2 *out, long ns, int n_streams2, int n_fft,
                        int n_ov, const float2 *H, const float2 *tw, cudaStream_t st);
