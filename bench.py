@@ -36,8 +36,8 @@ METRIC = "Rx line rate Gbit/s (LLRs out) per GB300 at oracle-matched BER; p99 bl
 WL = dict(workload="gs4d64_1000km_esn0_8to16dB", fmt="gs4d64", n_sym=1 << 20,
           esn0_db=list(range(8, 17)), cd_ps_per_nm=17000.0, linewidth_ts=2e-5,
           symbol_rate=28e9, sps=2, fft=4096, overlap=1024, taps=31, bps_phases=64,
-          bps_window=64, block=1 << 16, n_upd=1024, lag=2, mu=1e-3, n_pre=8192,
-          cma_passes=2, n_cma=0, n_train=1024, train_passes=2, skip_head=16384, skip_tail=512)
+          bps_window=64, block=1 << 16, n_upd=1024, lag=2, mu=1e-3, n_pre=2048,
+          cma_passes=1, n_cma=0, n_train=1024, train_passes=3, skip_head=16384, skip_tail=512)
 FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070.0
 
 
@@ -125,7 +125,8 @@ def parity_sample(rx_mod, torch):
     p = chain.RxParams(cd_ps_per_nm=WL["cd_ps_per_nm"], n_fft=WL["fft"], n_ov=WL["overlap"],
                        taps=WL["taps"], bps_phases=WL["bps_phases"], block=WL["block"],
                        n_upd=WL["n_upd"], lag=WL["lag"], n_pre=WL["n_pre"],
-                       skip_head=2048, skip_tail=512)
+                       cma_passes=WL["cma_passes"], n_cma=WL["n_cma"], n_train=WL["n_train"],
+                       train_passes=WL["train_passes"], skip_head=2048, skip_tail=512)
     res = chain.run_chain(st.rx, oracle_format(WL["fmt"]), p, ref_bits=st.bits)
     r = rx_mod.Receiver(WL["fmt"], cd_ps_per_nm=WL["cd_ps_per_nm"], taps=WL["taps"],
                         bps_phases=WL["bps_phases"], **{**rx_params(), "skip_head": 2048})
@@ -149,7 +150,9 @@ def cpu_baseline(n_sym: int):
                            cd_ps_per_nm=WL["cd_ps_per_nm"], linewidth_ts=WL["linewidth_ts"])
     p = chain.RxParams(cd_ps_per_nm=WL["cd_ps_per_nm"], n_fft=WL["fft"], n_ov=WL["overlap"],
                        taps=WL["taps"], bps_phases=WL["bps_phases"], block=WL["block"],
-                       n_upd=WL["n_upd"], lag=WL["lag"], n_pre=WL["n_pre"])
+                       n_upd=WL["n_upd"], lag=WL["lag"], n_pre=WL["n_pre"],
+                       cma_passes=WL["cma_passes"], n_cma=WL["n_cma"], n_train=WL["n_train"],
+                       train_passes=WL["train_passes"])
     t0 = time.perf_counter()
     chain.run_chain(st.rx, oracle_format(WL["fmt"]), p, ref_bits=st.bits)
     dt = time.perf_counter() - t0

@@ -106,8 +106,8 @@ void rx_destroy(rx_handle *h);                      /* NULL-safe */
  *   "fft" [1024] (1024 or 4096), "overlap" [256] (even, < fft/2),
  *   "mu" [1e-3], "bps_window" [64] (even, 2..64), "block" [4096] symbols,
  *   "n_upd" [1024] (<= block - bps_window/2), "lag" [1] (1..4),
- *   "n_pre" [8192], "cma_passes" [2], "n_cma" [0], "n_train" [1024]
- *   (<= 20000), "train_passes" [2],
+ *   "n_pre" [2048], "cma_passes" [1], "n_cma" [0], "n_train" [1024]
+ *   (<= 20000), "train_passes" [3],
  *   "sigma2" [0 = estimate per block], "skip_head" [4096],
  *   "skip_tail" [512], "streams" [1], "rolloff" [0.1],
  *   "wavelength_nm" [1550], "profile" [0] (1: time every launch).

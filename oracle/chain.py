@@ -44,11 +44,11 @@ class RxParams:
     block: int = 4096          # symbols per processing block
     n_upd: int = 1024          # LMS updates per block (first symbols of it)
     lag: int = 1               # taps from block n's update apply from block n+lag
-    n_pre: int = 8192          # start-up CMA span (symbols)
-    cma_passes: int = 2
+    n_pre: int = 2048          # start-up CMA span (symbols)
+    cma_passes: int = 1
     n_cma: int = 0             # block-wise updates run as CMA before DD
     n_train: int = 1024        # known training symbols at the stream start
-    train_passes: int = 2      # data-aided LMS passes over the training span
+    train_passes: int = 3      # data-aided LMS passes over the training span
     sigma2: float | None = None  # fixed noise variance, else per-block estimate
     skip_head: int = 4096      # symbols excluded from counting at stream start
     skip_tail: int = 512       # ... and at the stream end

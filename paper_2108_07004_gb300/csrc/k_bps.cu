@@ -113,30 +113,30 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
         const int hb = B >> 1;
         // test phases b and b + B/2 together: independent minimum chains
         for (int b = 0; b < hb; ++b) {
-            const f32x2 C1 = pk2(f.cs[b][0], f.cs[b][0]), S1 = pk2(f.cs[b][1], f.cs[b][1]);
-            const f32x2 C2 = pk2(f.cs[b + hb][0], f.cs[b + hb][0]);
-            const f32x2 S2 = pk2(f.cs[b + hb][1], f.cs[b + hb][1]);
+            const f32x2 *cp1 = reinterpret_cast<const f32x2 *>(f.csp[b]);
+            const f32x2 *cp2 = reinterpret_cast<const f32x2 *>(f.csp[b + hb]);
+            const f32x2 C1 = cp1[0], S1 = cp1[1], C2 = cp2[0], S2 = cp2[1];
             float md, md2;
             if (DIMS == 4) {
                 float a0 = 3.0e38f, a1 = 3.0e38f;
 #pragma unroll
-                for (int o = 0; o < NORB; o += 2) {
-                    if (o < f.n_orb) {
-                        float P, Q, P2, Q2, R, U, R2, U2;
-                        upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P, Q);
-                        upk2(fma2(S2, CI[0][o], mul2(C2, CR[0][o])), P2, Q2);
-                        const float v1 = fmaf(-2.f, orbit_v(P, Q, S), f.orbe[o]);
-                        const float v2 = fmaf(-2.f, orbit_v(P2, Q2, S), f.orbe[o]);
-                        if (o + 1 < f.n_orb) {
-                            upk2(fma2(S1, CI[0][o + 1], mul2(C1, CR[0][o + 1])), R, U);
-                            upk2(fma2(S2, CI[0][o + 1], mul2(C2, CR[0][o + 1])), R2, U2);
-                            a0 = fmin3(a0, v1, fmaf(-2.f, orbit_v(R, U, S), f.orbe[o + 1]));
-                            a1 = fmin3(a1, v2, fmaf(-2.f, orbit_v(R2, U2, S), f.orbe[o + 1]));
-                        } else {
-                            a0 = fminf(a0, v1);
-                            a1 = fminf(a1, v2);
-                        }
-                    }
+                for (int o = 0; o + 1 < NORB; o += 2) {
+                    float P, Q, P2, Q2, R, U, R2, U2;
+                    upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P, Q);
+                    upk2(fma2(S2, CI[0][o], mul2(C2, CR[0][o])), P2, Q2);
+                    upk2(fma2(S1, CI[0][o + 1], mul2(C1, CR[0][o + 1])), R, U);
+                    upk2(fma2(S2, CI[0][o + 1], mul2(C2, CR[0][o + 1])), R2, U2);
+                    a0 = fmin3(a0, fmaf(-2.f, orbit_v(P, Q, S), f.orbe[o]),
+                               fmaf(-2.f, orbit_v(R, U, S), f.orbe[o + 1]));
+                    a1 = fmin3(a1, fmaf(-2.f, orbit_v(P2, Q2, S), f.orbe[o]),
+                               fmaf(-2.f, orbit_v(R2, U2, S), f.orbe[o + 1]));
+                }
+                if (NORB & 1) {
+                    float P, Q, P2, Q2;
+                    upk2(fma2(S1, CI[0][NORB - 1], mul2(C1, CR[0][NORB - 1])), P, Q);
+                    upk2(fma2(S2, CI[0][NORB - 1], mul2(C2, CR[0][NORB - 1])), P2, Q2);
+                    a0 = fminf(a0, fmaf(-2.f, orbit_v(P, Q, S), f.orbe[NORB - 1]));
+                    a1 = fminf(a1, fmaf(-2.f, orbit_v(P2, Q2, S), f.orbe[NORB - 1]));
                 }
                 md = yn0 + a0;
                 md2 = yn0 + a1;
@@ -144,7 +144,7 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
                 float x0 = 3.0e38f, x1 = 3.0e38f, w0 = 3.0e38f, w1 = 3.0e38f;
 #pragma unroll
                 for (int o = 0; o < NORB; ++o) {
-                    if (o < f.n_orb) {
+                    {
                         float P0, Q0, P1, Q1, R0, U0, R1, U1;
                         upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P0, Q0);
                         upk2(fma2(S1, CI[1][o], mul2(C1, CR[1][o])), P1, Q1);
@@ -427,9 +427,9 @@ int bps_rounds(long len, int n_streams) {
             n_sm = 152;
     }
     const long per_stream = std::max(1L, (long)(2 * n_sm) / std::max(1, n_streams));
-    const long want = (len + per_stream - 1) / per_stream;         // outputs per block
-    int rounds = (int)((want / 32 + 2 + 7) / 8);
-    return std::max(1, std::min(kMaxRounds, rounds));
+    for (int r = 1; r <= kMaxRounds; ++r)                            // fewest rounds that fit
+        if ((len + range_of(r) - 1) / range_of(r) <= per_stream) return r;
+    return kMaxRounds;
 }
 
 // Start quadrant of the unwrap from the training phases (one block per
@@ -500,12 +500,21 @@ cudaError_t launch_bps(const float2 *y, long y_stride, long a, long e, long n_va
     if (e <= a || n_streams <= 0) return cudaSuccess;
     if (rounds < 1 || rounds > kMaxRounds || (f.B & 1)) return cudaErrorInvalidValue;
     uint8_t *bo = bout + bout_off;
+#define RX_BPS(DD, NO) return bps_launch_t<DD, NO>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, rounds, n_streams, f, st)
     if (f.dims == 4) {
-        if (f.n_orb > 16) return cudaErrorInvalidValue;
-        return bps_launch_t<4, 16>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, rounds, n_streams, f, st);
+        switch (f.n_orb) {
+            case 16: RX_BPS(4, 16);
+            case 8: RX_BPS(4, 8);
+            default: return cudaErrorInvalidValue;
+        }
     }
-    if (f.n_orb > 4) return cudaErrorInvalidValue;
-    return bps_launch_t<2, 4>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, rounds, n_streams, f, st);
+    switch (f.n_orb) {
+        case 1: RX_BPS(2, 1);
+        case 2: RX_BPS(2, 2);
+        case 4: RX_BPS(2, 4);
+        default: return cudaErrorInvalidValue;
+    }
+#undef RX_BPS
 }
 
 cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long b_stride,

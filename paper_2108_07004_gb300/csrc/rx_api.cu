@@ -61,11 +61,11 @@ struct rx_handle {
     long block = 4096;
     int n_upd = 1024;
     int lag = 1;
-    long n_pre = 8192;
-    int cma_passes = 2;
+    long n_pre = 2048;
+    int cma_passes = 1;
     long n_cma = 0;
     long n_train = 1024;
-    int train_passes = 2;
+    int train_passes = 3;
     double sigma2_fixed = 0.0;
     long skip_head = 4096, skip_tail = 512;
     int streams = 1;
@@ -248,6 +248,8 @@ void set_phases(FmtDev &d, int B) {
         const double ph = ((double)b / B - 0.5) * 2.0 * kPi / d.S;
         d.cs[b][0] = (float)std::cos(ph);
         d.cs[b][1] = (float)std::sin(ph);
+        d.csp[b][0] = d.csp[b][1] = d.cs[b][0];
+        d.csp[b][2] = d.csp[b][3] = d.cs[b][1];
     }
 }
 

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "rx.h"
@@ -12,7 +13,8 @@
 
 // Constellation and phase-search tables, passed to kernels by value
 // (__grid_constant__), so that uniform reads come from the constant bank.
-struct FmtDev {
+// 16-byte aligned so that the packed (64-bit) reads of csp are aligned.
+struct __align__(16) FmtDev {
     int dims;             // 2 or 4
     int M;                // table size
     int m;                // bits per 4D symbol
@@ -27,7 +29,10 @@ struct FmtDev {
     float orbe[RX_MAXM];        // energy of each representative
     int orb_lab[RX_MAXM][4];    // label of representative o rotated by k quarter turns (k < S)
     float cs[RX_MAXB][2];       // cos, sin of the test phases phi_b
+    float csp[RX_MAXB][4];      // (cos, cos, sin, sin) of phi_b, for packed pairs
 };
+static_assert(offsetof(FmtDev, csp) % 16 == 0, "packed phase table must be 16-byte aligned");
+static_assert(alignof(FmtDev) == 16, "FmtDev alignment");
 
 // Per-stream device state.
 struct StreamDev {
