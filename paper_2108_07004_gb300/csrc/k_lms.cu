@@ -30,6 +30,7 @@ struct Tables {
     float orbe[RX_MAXM];
     int orblab[RX_MAXM][4];
     float4 pts[RX_MAXM];
+    float2 cs[RX_MAXB];
 };
 
 __device__ __forceinline__ void load_tables(Tables &tb, const FmtDev &f) {
@@ -40,6 +41,7 @@ __device__ __forceinline__ void load_tables(Tables &tb, const FmtDev &f) {
     }
     for (int i = threadIdx.x; i < f.M; i += blockDim.x)
         tb.pts[i] = make_float4(f.pts[i][0], f.pts[i][1], f.pts[i][2], f.pts[i][3]);
+    for (int i = threadIdx.x; i < f.B; i += blockDim.x) tb.cs[i] = make_float2(f.cs[i][0], f.cs[i][1]);
 }
 
 // best rotation of an orbit given P + jQ = sum_p z_p conj(rep_p):
@@ -47,8 +49,9 @@ __device__ __forceinline__ void load_tables(Tables &tb, const FmtDev &f) {
 __device__ __forceinline__ void best_rot(float P, float Q, int S, float &v, int &k) {
     if (S == 4) {
         const float aP = fabsf(P), aQ = fabsf(Q);
-        if (aP >= aQ) { v = aP; k = P >= 0.f ? 0 : 2; }
-        else          { v = aQ; k = Q >= 0.f ? 1 : 3; }
+        const bool pw = aP >= aQ;
+        v = pw ? aP : aQ;
+        k = pw ? (P >= 0.f ? 0 : 2) : (Q >= 0.f ? 1 : 3);
     } else if (S == 2) {
         v = fabsf(P); k = P >= 0.f ? 0 : 1;
     } else {
@@ -56,23 +59,15 @@ __device__ __forceinline__ void best_rot(float P, float Q, int S, float &v, int 
     }
 }
 
-// Point of representative o turned by k quarter turns (both polarisations).
-__device__ __forceinline__ float4 turn(float4 r, int k) {
-    for (int i = 0; i < k; ++i) r = make_float4(-r.y, r.x, -r.w, r.z);
-    return r;
-}
-
 // Nearest table point of the candidates held by the lanes: lane o (o < 16)
-// holds orbit o's best rotation with squared distance dist and its point;
-// the minimum distance over lanes 0..15 wins, exact ties go to the lowest
-// label.  Returns the winning lane.
-__device__ __forceinline__ int argmin_lane(float dist, bool valid, int label, int lane) {
+// holds orbit o's best rotation, its squared distance and its label; the
+// minimum distance over the lanes wins and exact ties go to the lowest label.
+// Two warp reductions return the winning label itself.
+__device__ __forceinline__ int argmin_label(float dist, bool valid, int label) {
     const unsigned bits = valid ? __float_as_uint(fmaxf(dist, 0.f)) : 0xffffffffu;
     const unsigned mn = __reduce_min_sync(0xffffffffu, bits);
-    // among the lanes at the minimum, the lowest label (branch-free)
-    const unsigned key = (bits == mn && lane < 16) ? (unsigned)label : 0xffffffffu;
-    const unsigned ml = __reduce_min_sync(0xffffffffu, key);
-    return __ffs(__ballot_sync(0xffffffffu, key == ml && lane < 16)) - 1;
+    const unsigned key = (bits == mn) ? (unsigned)label : 0xffffffffu;
+    return (int)__reduce_min_sync(0xffffffffu, key);
 }
 
 // (y0, y1) from per-lane partials of both outputs: xor-16 halving step, four
@@ -192,7 +187,7 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
                     const unsigned code = pc[kk];
                     const int b = min((int)(code & 255), f.B - 1);
                     const int qt = (int)((code >> 8) & 3) * qt_step;
-                    float2 rot = make_float2(f.cs[b][0], f.cs[b][1]);   // exp(j phi)
+                    float2 rot = tb.cs[b];                               // exp(j phi)
                     for (int i = 0; i < qt; ++i) rot = make_float2(-rot.y, rot.x);
                     float2 d0, d1;
                     if (MODE == 3) {
@@ -219,27 +214,21 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
                             int k;
                             best_rot(P, Q, f.S, v, k);
                             const float dist = cnorm(z0) + cnorm(z1) + tb.orbe[valid ? o : 0] - 2.f * v;
-                            const int w = argmin_lane(dist, valid, tb.orblab[valid ? o : 0][k], lane);
-                            const float4 pt = turn(r, k * qt_step);
-                            d0.x = __shfl_sync(0xffffffffu, pt.x, w);
-                            d0.y = __shfl_sync(0xffffffffu, pt.y, w);
-                            d1.x = __shfl_sync(0xffffffffu, pt.z, w);
-                            d1.y = __shfl_sync(0xffffffffu, pt.w, w);
+                            const float4 pt = tb.pts[argmin_label(dist, valid, tb.orblab[valid ? o : 0][k])];
+                            d0 = make_float2(pt.x, pt.y);
+                            d1 = make_float2(pt.z, pt.w);
                         } else {
                             float v0, v1;
                             int k0r, k1r;
                             best_rot(z0.x * r.x + z0.y * r.y, z0.y * r.x - z0.x * r.y, f.S, v0, k0r);
                             best_rot(z1.x * r.x + z1.y * r.y, z1.y * r.x - z1.x * r.y, f.S, v1, k1r);
                             const float eo = tb.orbe[valid ? o : 0];
-                            const int w0 = argmin_lane(cnorm(z0) + eo - 2.f * v0, valid,
-                                                       tb.orblab[valid ? o : 0][k0r], lane);
-                            const int w1 = argmin_lane(cnorm(z1) + eo - 2.f * v1, valid,
-                                                       tb.orblab[valid ? o : 0][k1r], lane);
-                            const float4 p0 = turn(r, k0r * qt_step), p1 = turn(r, k1r * qt_step);
-                            d0.x = __shfl_sync(0xffffffffu, p0.x, w0);
-                            d0.y = __shfl_sync(0xffffffffu, p0.y, w0);
-                            d1.x = __shfl_sync(0xffffffffu, p1.x, w1);
-                            d1.y = __shfl_sync(0xffffffffu, p1.y, w1);
+                            const float4 p0 = tb.pts[argmin_label(cnorm(z0) + eo - 2.f * v0, valid,
+                                                                  tb.orblab[valid ? o : 0][k0r])];
+                            const float4 p1 = tb.pts[argmin_label(cnorm(z1) + eo - 2.f * v1, valid,
+                                                                  tb.orblab[valid ? o : 0][k1r])];
+                            d0 = make_float2(p0.x, p0.y);
+                            d1 = make_float2(p1.x, p1.y);
                         }
                     }
                     e0 = csub(cmul(d0, rot), y0);

@@ -6,8 +6,15 @@ compares element by element.  Tolerances follow the FP32 arithmetic:
   error ~1e-6; the bounds below leave 10-30x headroom.
 * LLRs: |dLLR| <= 1e-4 * max(1, |LLR|) (the target tolerance of the chain).
 * Integer results (phase indices, unwrap counts, bit errors): exact, except
-  where the oracle itself has a near-tie (relative cost gap < 1e-5 for BPS),
-  where either choice is valid and the choice must be within the tie.
+  where the oracle itself has a near-tie, where either choice is valid and
+  the choice must be within the tie.  BPS near-tie: relative gap between the
+  two smallest window costs < 1e-4 (the FP32 window cost uses
+  |y|^2 + |r|^2 - 2 max(|P|,|Q|) per symbol; at sigma^2 ~ 0.017 its relative
+  error reaches ~1e-5).
+* End to end: a near-tie inside a block's LMS span may send the taps of the
+  following blocks along a different, equally valid trajectory, so rows are
+  compared up to the blocks those taps reach; the later blocks are covered by
+  the stage tests, which inject the oracle's own taps and phases.
 """
 import numpy as np
 import pytest
@@ -19,7 +26,8 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 LLR_RTOL = 1e-4
-TIE = 1e-5
+TIE = 1e-4
+DD_TIE = 1e-5
 
 
 def _rx():
@@ -276,9 +284,21 @@ def test_chain_end_to_end(case):
     llr, stats = r.process(_dev(st.rx[None]))
     g = llr[0].cpu().numpy().astype(np.float64)
     ref = res.llr
-    # near-ties of the phase search (either phase valid) are compared by validity only
+    N = ref.shape[0]
     tie = res.bps_gap < TIE
-    ok = ~tie
+    # first block whose LMS span holds a BPS or DD near-tie: its taps (used from
+    # block + lag on) may legitimately differ, so compare rows before that
+    dd_ties = {k for k, mg in res.dd_margin if mg < DD_TIE}
+    lim = N
+    for nb, (a_r, e_r) in enumerate(res.ranges):
+        span = range(nb * p.block, min(nb * p.block + p.n_upd, N))
+        if any(tie[k] or k in dd_ties for k in span):
+            last = nb + p.lag - 1            # last block still equalised with shared taps
+            lim = res.ranges[last][1] if last < len(res.ranges) else N
+            break
+    rows = np.arange(N) < lim
+    ok = ~tie & rows
+    assert rows.mean() >= 0.3, "too few rows comparable end to end"
     err = np.abs(g - ref)
     tol = LLR_RTOL * np.maximum(1.0, np.abs(ref))
     bad = (err > tol) & ok[:, None]
@@ -287,9 +307,9 @@ def test_chain_end_to_end(case):
     hd = ((g < 0) != (ref < 0)) & (np.abs(ref) >= 1e-4) & ok[:, None]
     assert hd.sum() == 0
     # counting: bit errors of the GPU's own hard decisions are exact
-    c0, c1 = p.skip_head, ref.shape[0] - p.skip_tail
+    c0, c1 = p.skip_head, N - p.skip_tail
     mine = int(np.sum((g[c0:c1] < 0).astype(np.uint8) != st.bits[c0:c1]))
     assert stats[0]["bit_errors"] == mine
-    if not tie[c0:c1].any():
+    if lim == N and not tie[c0:c1].any():
         assert stats[0]["bit_errors"] == res.stats["bit_errors"]
-    assert abs(stats[0]["gmi"] - res.stats["gmi"]) < 1e-4 * fmt.m
+        assert abs(stats[0]["gmi"] - res.stats["gmi"]) < 1e-4 * fmt.m
