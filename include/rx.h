@@ -163,10 +163,75 @@ int rx_get_profile(rx_handle *h, const char *stage, double *ms_total, uint64_t *
  * cap blocks; *n receives the number of blocks.  ms may be NULL to query. */
 int rx_get_block_latency(rx_handle *h, double *ms, size_t cap, size_t *n);
 
-/* Serialise / restore the per-stream state (taps ring, LMS count, unwrap
- * carry, block index).  *len in: capacity, out: bytes used (pass buf NULL
- * to query). */
+/* Run blocks b0 .. b1-1 of S streams whose complete samples are at
+ * `samples` (device, [S][2][n_samples] c64, n_samples = 2 N), the block
+ * schedule of rx_process cut at block boundaries (Sec. 2: the taps an LMS
+ * span produces serve later buffers, so the state carried from block to
+ * block is the taps, the phase unwrap carry and the counters).
+ *   b0 == 0   starts the stream: start-up CMA and training, then block 0.
+ *   b0 >  0   continues the stream: the handle must hold the state after
+ *             block b0 - 1 of a stream of the same N, left by an earlier
+ *             call or restored by rx_set_state; RX_ESTATE otherwise.
+ *   b1        <= ceil(N / block); b1 > b0.
+ * llr_out (device, [S][N][m]) receives rows a(b0) .. e(b1-1) - 1, where
+ * a(n) = max(0, n*block - W/2), e(n) = (n+1)*block - W/2 (N for the last
+ * block), W = "bps_window"; other rows are not touched.  Only the CDC
+ * frames these blocks read are filtered.  stats as in rx_process (counters
+ * accumulate over the calls of one stream).  Calls for b0 = 0 .. B-1 in
+ * order give the same output as one rx_process over the stream. */
+int rx_process_blocks(rx_handle *h, const void *samples, size_t n_samples, size_t b0,
+                      size_t b1, float *llr_out, rx_stats *stats);
+
+/* Checkpoint / resume of the stream state between blocks (what block n of
+ * the schedule needs from blocks before it).  A state is a host byte
+ * buffer: one rx_state_header, then, for n = blocks_done, L = lag,
+ * S = streams, T = taps, W = bps_window, K = n*block:
+ *   taps     [L][S][2][2][T] c64: U_{n-L+j}, j = 0 .. L-1, the LMS results
+ *            blocks n .. n+L-1 equalise with (block n+j uses entry j);
+ *            U_{n-1} (entry L-1) is where the LMS of block n starts;
+ *            U_i = W_0 (start-up result) for i < 0.  Tap layout h[q][p][t]
+ *            of rx_fir.
+ *   carry    [S][2] int32: unwrap carry (m, b) of the last symbol before
+ *            a(n), as in rx_unwrap.
+ *   y_tail   [S][2][W] c64: FIR output of symbols K-W .. K-1 (zeros before
+ *            symbol 0), the phase-search window halo of block n.
+ *   counters [S] rx_state_counters.
+ * Nothing else carries from block to block: a state restored into a handle
+ * with the same create arguments and parameters continues the stream as
+ * the handle that saved it would (rx_process_blocks with b0 = n).  The
+ * layout is public so that a state can be built from outside (a test
+ * injects a model receiver's state). */
+#define RX_STATE_MAGIC   0x31535852u   /* "RXS1" */
+#define RX_STATE_VERSION 1u
+typedef struct {
+    uint32_t magic;        /* RX_STATE_MAGIC                                   */
+    uint32_t version;      /* RX_STATE_VERSION                                 */
+    int32_t  streams;      /* S      must match the handle                     */
+    int32_t  taps;         /* T      must match                                */
+    int32_t  lag;          /* L      must match                                */
+    int32_t  bps_window;   /* W      must match                                */
+    int32_t  bps_phases;   /* B      must match                                */
+    int32_t  m_bits;       /* m      must match                                */
+    int64_t  block;        /* block length, must match                         */
+    int64_t  n_sym;        /* N of the stream (symbols)                        */
+    int64_t  blocks_done;  /* n >= 1: the next block to run                    */
+    int64_t  lms_updates;  /* LMS updates so far (CMA -> DD switch at n_cma)   */
+} rx_state_header;
+typedef struct {
+    uint64_t bit_errors, n_sym;
+    double   gmi_sum, evm_num, evm_den, sigma2;
+} rx_state_counters;
+
+/* Serialise the state after the last processed block into buf (host).
+ * *len in: capacity, out: bytes used; buf NULL queries the size.
+ * RX_ESTATE before the first block of a stream has run; RX_EINVAL when
+ * the capacity is too small (*len then holds the size).  Synchronises. */
 int rx_get_state(rx_handle *h, void *buf, size_t *len);
+/* Restore a state (host buf of exactly len bytes, layout above).  RX_EINVAL
+ * on a bad magic, version or length, or a header that does not match the
+ * handle's parameters; nothing is changed then.  blocks_done must be >= 1
+ * (block 0 also needs the start-up's training phases, which are not part
+ * of a state).  Synchronises. */
 int rx_set_state(rx_handle *h, const void *buf, size_t len);
 
 /* Format facts: dims, m (bits per 4D symbol), M (table size). */

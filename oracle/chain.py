@@ -459,8 +459,30 @@ class ChainResult:
     w_cma: np.ndarray | None = None
 
 
+def state_at(res: ChainResult, p: RxParams, n: int) -> dict:
+    """What block n (n >= 1) of the schedule in run_chain takes from the
+    blocks before it: the LMS results U_{n-lag} .. U_{n-1} (U_i = W_0 for
+    i < 0; block n+j equalises with entry j and the LMS of block n starts
+    from the last), the unwrap carry (m, b) of the last symbol before block
+    n's range, the equaliser output of the W symbols before n*block (the
+    phase-search halo; zeros before symbol 0) and the number of LMS updates
+    so far.  Everything else in block n is computed from the samples."""
+    N = res.y.shape[1]
+    L, W = p.lag, p.bps_window
+    assert 1 <= n <= len(res.ranges)
+    taps = [res.taps_after[i] if i >= 0 else res.w0 for i in range(n - L, n)]
+    last = res.ranges[n - 1][1] - 1
+    K = n * p.block
+    y_tail = np.zeros((2, W), complex)
+    lo = max(0, K - W)
+    y_tail[:, lo - (K - W):] = res.y[:, lo:K]
+    u = sum(len(range(i * p.block, min(i * p.block + p.n_upd, N))) for i in range(n))
+    return {"taps": taps, "carry": (int(res.m[last]), int(res.b[last])), "y_tail": y_tail,
+            "lms_updates": u}
+
+
 def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
-              ref_bits: np.ndarray | None = None) -> ChainResult:
+              ref_bits: np.ndarray | None = None, resume: tuple | None = None) -> ChainResult:
     """Whole receiver on one stream r [2, sps*N] with the block schedule:
 
     start-up: CMA over the first n_pre symbols (cma_passes passes) from the
@@ -476,19 +498,22 @@ def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
          in block 0 the unwrap's start quadrant comes from the training phases;
       3. LMS over the first n_upd symbols of block n starting from U_{n-1}
          (U_{-1} = W_0) -> U_n  (Sec. 2: part of a buffer updates the taps
-         used for subsequent buffers)."""
+         used for subsequent buffers).
+    resume = (n, state_at(...) of block n): skip the start-up and blocks
+    before n and continue from that state (outputs before block n's range
+    stay zero; counting still covers skip_head .. N - skip_tail)."""
     r = np.asarray(r, dtype=np.complex128)
     N = r.shape[1] // p.sps
     W, B, L, S = p.bps_window, p.bps_phases, p.lag, fmt.sym_order
     assert p.n_upd + W // 2 <= p.block, "update span must have phases in its block"
     x = cdc(r, p)
     h = center_spike(p.taps)
-    npre = min(p.n_pre, N)
-    for _ in range(p.cma_passes):
+    npre = 0 if resume else min(p.n_pre, N)
+    for _ in range(p.cma_passes if npre else 0):
         h = lms(x, h, range(npre), fmt, p, force_cma=True)
     w_cma = h.copy()
     train_b = train_m = None
-    if ref_bits is not None and p.n_train > 0:
+    if ref_bits is not None and p.n_train > 0 and not resume:
         ntr = min(p.n_train, N)
         ref = fmt.symbols_from_bits(ref_bits[:ntr])
         h = align_training(x, h, ref)
@@ -508,7 +533,18 @@ def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
     u = 0
     nblk = -(-N // p.block)
     used, after, s2s, ranges, info = [], [], [], [], LmsInfo()
-    for n in range(nblk):
+    n_first = 0
+    if resume:
+        n_first, stt = resume
+        for j, t in enumerate(stt["taps"]):
+            ring[(n_first - L + j) % (L + 1)] = np.array(t, dtype=complex)
+        m_prev, b_prev = stt["carry"]
+        K = n_first * p.block
+        lo = max(0, K - W)
+        y[:, lo:K] = stt["y_tail"][:, lo - (K - W):]
+        u = stt["lms_updates"]
+        used, after, s2s, ranges = [None] * n_first, [None] * n_first, [None] * n_first, [None] * n_first
+    for n in range(n_first, nblk):
         k0, k1 = n * p.block, min((n + 1) * p.block, N)
         wn = ring[(n - L) % (L + 1)]
         used.append(wn.copy())

@@ -50,8 +50,8 @@ __device__ __forceinline__ float orbit_v(float P, float Q, int S) {
 template <int DIMS, int NORB>
 __global__ void __launch_bounds__(256, 2)
 bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_valid, int W,
-           uint8_t *__restrict__ bout, long bout_stride, int *__restrict__ dsum, int n_cta,
-           int rounds, const __grid_constant__ FmtDev f) {
+           uint8_t *__restrict__ bout, long bout_stride, int *__restrict__ dsum,
+           double *__restrict__ mdsum, int n_cta, int rounds, const __grid_constant__ FmtDev f) {
     extern __shared__ float smem[];
     const int B = f.B;
     const int kChunks = 8 * rounds - 2, kR = range_of(rounds);
@@ -59,8 +59,10 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
     float *Tb = smem + RX_NCHUNK * B * 32;                // [10][B] chunk totals
     uint8_t *bsm = reinterpret_cast<uint8_t *>(Tb + RX_NCHUNK * B);   // [kR]
     __shared__ int red[8];
+    __shared__ float redm[8];
     const int s = blockIdx.y, c = blockIdx.x;
     const long out0 = a + (long)c * kR;
+    float md_acc = 0.f;   // min distance at the chosen phase: the decision-directed noise
     const long out1 = min(out0 + kR, e);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float2 *yx = y + (long)s * 2 * y_stride;
@@ -201,6 +203,11 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
                 }
                 bsm[k - out0] = (uint8_t)bb;
                 bout[(long)s * bout_stride + (k - a)] = (uint8_t)bb;
+                // md at (bb, k) from the chunk prefixes: |z_k - d_k|^2 of the
+                // de-rotated symbol (the table is closed under the rotations)
+                const int sc = (oc + 1) % RX_NCHUNK;
+                const float hi = (lane < 31) ? Eb[(sc * B + bb) * 32 + lane + 1] : Tb[sc * B + bb];
+                md_acc += hi - Eb[(sc * B + bb) * 32 + lane];
             }
         }
         __syncthreads();
@@ -210,13 +217,18 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
     const int nloc = (int)(out1 - out0);
     for (int t = tid + 1; t < nloc; t += 256) acc += unwrap_step(bsm[t - 1], bsm[t], B);
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
-    if (lane == 0) red[warp] = acc;
+    for (int off = 16; off > 0; off >>= 1) {
+        acc += __shfl_xor_sync(0xffffffffu, acc, off);
+        md_acc += __shfl_xor_sync(0xffffffffu, md_acc, off);
+    }
+    if (lane == 0) { red[warp] = acc; redm[warp] = md_acc; }
     __syncthreads();
     if (tid == 0) {
         int tot = 0;
-        for (int w = 0; w < 8; ++w) tot += red[w];
+        double mt = 0.0;
+        for (int w = 0; w < 8; ++w) { tot += red[w]; mt += (double)redm[w]; }
         dsum[s * n_cta + c] = tot;
+        if (mdsum) mdsum[s * n_cta + c] = mt;
     }
 }
 
@@ -263,7 +275,7 @@ unwrap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *__rest
               int cout_stride, float2 *__restrict__ z, long z_stride, uint16_t *__restrict__ pcode,
               long pc_stride, double *__restrict__ partial, double *__restrict__ sigma2_out,
               int s2_stride, unsigned int *__restrict__ ticket, int ticket_stride, int kR,
-              const __grid_constant__ FmtDev f) {
+              const double *__restrict__ mdsum, const __grid_constant__ FmtDev f) {
     __shared__ uint8_t bl[kMaxR];
     __shared__ int wsum[8];
     __shared__ int mstart_sh;
@@ -340,7 +352,7 @@ unwrap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *__rest
         zx[k - a] = z0;
         zy[k - a] = z1;
         pcode[(long)s * pc_stride + (k - a)] = (uint16_t)(b | (mq << 8));
-        dsum_loc += (double)nearest_dist<DIMS, NORB>(z0, z1, f);
+        if (!mdsum) dsum_loc += (double)nearest_dist<DIMS, NORB>(z0, z1, f);
         if (k == e - 1) {
             carry_out[s * cout_stride + 0] = m;
             carry_out[s * cout_stride + 1] = b;
@@ -353,7 +365,7 @@ unwrap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *__rest
     if (tid == 0) {
         double tot = 0.0;
         for (int w = 0; w < 8; ++w) tot += dred[w];
-        partial[(long)s * n_cta + c] = tot;
+        partial[(long)s * n_cta + c] = mdsum ? mdsum[(long)s * n_cta + c] : tot;
         __threadfence();
         const unsigned prev = atomicAdd(&ticket[s * ticket_stride], 1u);
         last = (prev == (unsigned)n_cta - 1);
@@ -399,8 +411,8 @@ __global__ void dsum_kernel(const uint8_t *__restrict__ b, long b_stride, long a
 
 template <int DIMS, int NORB>
 cudaError_t bps_launch_t(const float2 *y, long ys, long a, long e, long nv, int W, uint8_t *bout,
-                         long bst, int *dsum, int rounds, int n_streams, const FmtDev &f,
-                         cudaStream_t st) {
+                         long bst, int *dsum, double *mdsum, int rounds, int n_streams,
+                         const FmtDev &f, cudaStream_t st) {
     const int kR = range_of(rounds);
     const int n_cta = (int)((e - a + kR - 1) / kR);
     const size_t smem = sizeof(float) * (RX_NCHUNK * f.B * 32 + RX_NCHUNK * f.B) + kR + 16;
@@ -408,7 +420,7 @@ cudaError_t bps_launch_t(const float2 *y, long ys, long a, long e, long nv, int 
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     dim3 grid((unsigned)n_cta, (unsigned)n_streams);
-    kern<<<grid, 256, smem, st>>>(y, ys, a, e, nv, W, bout, bst, dsum, n_cta, rounds, f);
+    kern<<<grid, 256, smem, st>>>(y, ys, a, e, nv, W, bout, bst, dsum, mdsum, n_cta, rounds, f);
     return cudaGetLastError();
 }
 
@@ -495,12 +507,12 @@ cudaError_t launch_dsum_from_b(const uint8_t *b, long b_stride, long a, long e, 
 }
 
 cudaError_t launch_bps(const float2 *y, long y_stride, long a, long e, long n_valid, int W,
-                       uint8_t *bout, long bout_stride, long bout_off, int *dsum, int rounds,
-                       int n_streams, const FmtDev &f, cudaStream_t st) {
+                       uint8_t *bout, long bout_stride, long bout_off, int *dsum, double *mdsum,
+                       int rounds, int n_streams, const FmtDev &f, cudaStream_t st) {
     if (e <= a || n_streams <= 0) return cudaSuccess;
     if (rounds < 1 || rounds > kMaxRounds || (f.B & 1)) return cudaErrorInvalidValue;
     uint8_t *bo = bout + bout_off;
-#define RX_BPS(DD, NO) return bps_launch_t<DD, NO>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, rounds, n_streams, f, st)
+#define RX_BPS(DD, NO) return bps_launch_t<DD, NO>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, mdsum, rounds, n_streams, f, st)
     if (f.dims == 4) {
         switch (f.n_orb) {
             case 16: RX_BPS(4, 16);
@@ -525,7 +537,7 @@ cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long
                           uint16_t *pcode, long pcode_stride, long pcode_off,
                           double *partial, double *sigma2_out, int sigma2_stride,
                           unsigned int *ticket, int ticket_stride, int rounds,
-                          int n_streams, const FmtDev &f, cudaStream_t st) {
+                          const double *mdsum, int n_streams, const FmtDev &f, cudaStream_t st) {
     if (e <= a || n_streams <= 0) return cudaSuccess;
     if (rounds < 1 || rounds > kMaxRounds) return cudaErrorInvalidValue;
     const int kR = range_of(rounds);
@@ -535,12 +547,12 @@ cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long
         unwrap_kernel<4, 16><<<grid, 256, 0, st>>>(y, y_stride, b + b_off, b_stride, a, e, dsum, n_cta,
                                                     carry_in, carry_in_stride, carry_out, carry_out_stride,
                                                     z + z_off, z_stride, pcode + pcode_off, pcode_stride,
-                                                    partial, sigma2_out, sigma2_stride, ticket, ticket_stride, kR, f);
+                                                    partial, sigma2_out, sigma2_stride, ticket, ticket_stride, kR, mdsum, f);
     } else {
         unwrap_kernel<2, 4><<<grid, 256, 0, st>>>(y, y_stride, b + b_off, b_stride, a, e, dsum, n_cta,
                                                    carry_in, carry_in_stride, carry_out, carry_out_stride,
                                                    z + z_off, z_stride, pcode + pcode_off, pcode_stride,
-                                                   partial, sigma2_out, sigma2_stride, ticket, ticket_stride, kR, f);
+                                                   partial, sigma2_out, sigma2_stride, ticket, ticket_stride, kR, mdsum, f);
     }
     return cudaGetLastError();
 }

@@ -112,11 +112,11 @@ __device__ __forceinline__ float2 twid(const float2 *__restrict__ tw, int e, int
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(256, 2)
 cdc4096_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, long ns, int S, int half,
-               const float2 *__restrict__ H, const float2 *__restrict__ tw) {
+               long f0, const float2 *__restrict__ H, const float2 *__restrict__ tw) {
     constexpr int RP = 257;   // padded row
     __shared__ float2 sm[16 * RP];
     const int t = threadIdx.x;
-    const long f = blockIdx.x;
+    const long f = f0 + blockIdx.x;
     const float2 *src = in + (long)blockIdx.y * ns;
     float2 *dst = out + (long)blockIdx.y * ns;
     const long start = f * S - half;
@@ -201,12 +201,12 @@ cdc4096_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, long ns,
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(128)
 cdc1024_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, long ns, int S, int half,
-               int nframes, const float2 *__restrict__ H, const float2 *__restrict__ tw) {
+               long f0, long f1, const float2 *__restrict__ H, const float2 *__restrict__ tw) {
     constexpr int RP = 33;
     __shared__ float2 smem[4][32 * RP];
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const long f = (long)blockIdx.x * 4 + w;
-    if (f >= nframes) return;
+    const long f = f0 + (long)blockIdx.x * 4 + w;
+    if (f >= f1) return;
     float2 *sm = smem[w];
     const float2 *src = in + (long)blockIdx.y * ns;
     float2 *dst = out + (long)blockIdx.y * ns;
@@ -257,16 +257,18 @@ cdc1024_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, long ns,
 }  // namespace
 
 cudaError_t launch_cdc(const float2 *in, float2 *out, long ns, int n_streams2, int n_fft,
-                       int n_ov, const float2 *H, const float2 *tw, cudaStream_t st) {
+                       int n_ov, const float2 *H, const float2 *tw, cudaStream_t st, long f0, long f1) {
     const int S = n_fft - n_ov, half = n_ov / 2;
     const long nframes = (ns + S - 1) / S;
-    if (nframes <= 0 || n_streams2 <= 0) return cudaSuccess;
+    if (f1 < 0 || f1 > nframes) f1 = nframes;
+    if (f0 < 0) f0 = 0;
+    if (f1 <= f0 || n_streams2 <= 0) return cudaSuccess;
     if (n_fft == 4096) {
-        dim3 grid((unsigned)nframes, (unsigned)n_streams2);
-        cdc4096_kernel<<<grid, 256, 0, st>>>(in, out, ns, S, half, H, tw);
+        dim3 grid((unsigned)(f1 - f0), (unsigned)n_streams2);
+        cdc4096_kernel<<<grid, 256, 0, st>>>(in, out, ns, S, half, f0, H, tw);
     } else if (n_fft == 1024) {
-        dim3 grid((unsigned)((nframes + 3) / 4), (unsigned)n_streams2);
-        cdc1024_kernel<<<grid, 128, 0, st>>>(in, out, ns, S, half, (int)nframes, H, tw);
+        dim3 grid((unsigned)((f1 - f0 + 3) / 4), (unsigned)n_streams2);
+        cdc1024_kernel<<<grid, 128, 0, st>>>(in, out, ns, S, half, f0, f1, H, tw);
     } else {
         return cudaErrorInvalidValue;
     }

@@ -88,6 +88,7 @@ struct rx_handle {
     uint16_t *pcode = nullptr;
     int *dsum = nullptr;
     double *part_u = nullptr, *part_d = nullptr, *sig = nullptr, *sig_fixed = nullptr;
+    double *mdsum = nullptr;
     StreamDev *sd = nullptr;
     long cap_dsum = 0, cap_pd = 0;
     // reference
@@ -292,6 +293,8 @@ void free_buffers(rx_handle *h) {
     cudaFree(h->x); cudaFree(h->y); cudaFree(h->z); cudaFree(h->ring);
     cudaFree(h->bidx); cudaFree(h->pcode); cudaFree(h->dsum); cudaFree(h->part_u);
     cudaFree(h->part_d); cudaFree(h->sig); cudaFree(h->sig_fixed); cudaFree(h->sd);
+    cudaFree(h->mdsum);
+    h->mdsum = nullptr;
     h->x = h->y = h->z = h->ring = nullptr;
     h->bidx = nullptr; h->pcode = nullptr; h->dsum = nullptr;
     h->part_u = h->part_d = h->sig = h->sig_fixed = nullptr;
@@ -314,6 +317,7 @@ int ensure_buffers(rx_handle *h, long N) {
     CK(cudaMalloc(&h->pcode, sizeof(uint16_t) * (size_t)S * N));
     CK(cudaMalloc(&h->dsum, sizeof(int) * (size_t)S * ncta));
     CK(cudaMalloc(&h->part_u, sizeof(double) * (size_t)S * ncta));
+    CK(cudaMalloc(&h->mdsum, sizeof(double) * (size_t)S * ncta));
     CK(cudaMalloc(&h->part_d, sizeof(double) * 5 * (size_t)S * ncta_d));
     CK(cudaMalloc(&h->sig, sizeof(double) * S));
     CK(cudaMalloc(&h->sig_fixed, sizeof(double) * S));
@@ -441,18 +445,19 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     const FmtDev &f = h->fmt;
     const int D = (T - 1) / 2;
 
-    // CDC of the frames that the FIR of these blocks reads
+    // CDC of the frames that these blocks (and, for b0 = 0, the start-up)
+    // read: output k of the FIR and the LMS reads samples 2k - D .. 2k + D
     {
-        const long s_lo = std::max(0L, 2 * b0 * Nb - D), s_hi = std::min(ns, 2 * std::min(b1 * Nb, N) + D + 1);
+        long k_hi = std::min(b1 * Nb, N);
+        if (b0 == 0) k_hi = std::max(k_hi, std::min(N, std::max(h->n_pre, h->n_train)));
+        const long s_lo = std::max(0L, 2 * b0 * Nb - D), s_hi = std::min(ns, 2 * k_hi + D);
         const long Sk = h->n_fft - h->n_ov;
         const long f0 = s_lo / Sk, f1 = (s_hi + Sk - 1) / Sk;
-        // launch_cdc filters frames [0, nframes); offset pointers give frames [f0, f1)
-        (void)f0; (void)f1;
         h->ev_used = 0;
         h->recs.clear();
         h->blk.clear();
         for (auto &c : h->nlaunch) c = 0;
-        STAGE(ST_CDC, st, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st));
+        STAGE(ST_CDC, st, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st, f0, f1));
     }
     if (b0 == 0) {
         std::vector<float2> &cs = h->h_taps0;
@@ -476,14 +481,14 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
             if (rc2 != RX_OK) return rc2;
         }
         for (int i = 1; i <= L; ++i) CK(cudaMemcpyAsync(slot(h, i), w0, tapsz, cudaMemcpyDeviceToDevice, st));
-        if (h->sigma2_fixed > 0) {
-            h->h_sig.assign(S, h->sigma2_fixed);
-            CK(cudaMemcpyAsync(h->sig_fixed, h->h_sig.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
-        }
         h->u = 0;
         h->blocks_done = 0;
         h->started = true;
         h->cur_n = N;
+    }
+    if (h->sigma2_fixed > 0) {
+        h->h_sig.assign(S, h->sigma2_fixed);
+        CK(cudaMemcpyAsync(h->sig_fixed, h->h_sig.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
     }
     const int m = f.m;
     const long sd_stride = sizeof(StreamDev) / sizeof(int32_t);
@@ -506,7 +511,8 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         const long a = std::max(0L, k0 - h->W / 2);
         const long e = (n == nblk - 1) ? N : k1 - h->W / 2;
         const int rounds = bps_rounds(e - a, S);
-        STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, h->dsum, rounds, S, f, st));
+        STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, h->dsum, h->mdsum, rounds, S,
+                                        f, st));
         const int cin = (int)(n & 1), cout = 1 - cin;
         if (n == 0 && h->trained) {
             // the training phases fix the start quadrant of the unwrap
@@ -518,7 +524,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
                             (int)sd_stride, carry_base + 2 * cout, (int)sd_stride, h->z, N, a,
                             h->pcode, N, a, h->part_u, h->sig, 1,
                             &h->sd[0].ticket_unwrap, (int)(sizeof(StreamDev) / sizeof(unsigned)),
-                            rounds, S, f, st));
+                            rounds, h->mdsum, S, f, st));
         const double *s2 = h->sigma2_fixed > 0 ? h->sig_fixed : h->sig;
         if ((e - a + 255) / 256 > h->cap_pd) return fail(RX_EINVAL, "internal: demap partials");
         STAGE(ST_DEMAP, st, 1, launch_demap(h->z, N, a, a, e, s2, 1, llr + (size_t)a * m, N * m, cnt, S, f, st));
@@ -634,6 +640,26 @@ int static_scratch(void **out) {
 }
 
 size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
+
+static_assert(sizeof(rx_state_header) == 64 && sizeof(rx_state_counters) == 48,
+              "the state layout is part of the ABI");
+
+// Byte offsets of the parts of a state buffer (layout documented with
+// rx_state_header): header, taps, carry, y halo, counters, packed.
+struct StateLayout {
+    size_t taps, carry, y_tail, counters, total;
+};
+
+StateLayout state_layout(const rx_handle *h) {
+    const size_t S = (size_t)h->streams;
+    StateLayout l{};
+    l.taps = sizeof(rx_state_header);
+    l.carry = l.taps + (size_t)h->lag * S * 4 * h->T * sizeof(float2);
+    l.y_tail = l.carry + S * 2 * sizeof(int32_t);
+    l.counters = l.y_tail + S * 2 * (size_t)h->W * sizeof(float2);
+    l.total = l.counters + S * sizeof(rx_state_counters);
+    return l;
+}
 
 }  // namespace
 
@@ -841,16 +867,127 @@ int rx_get_block_latency(rx_handle *h, double *ms, size_t cap, size_t *n) {
     return RX_OK;
 }
 
+int rx_process_blocks(rx_handle *h, const void *samples, size_t n_samples, size_t b0, size_t b1,
+                      float *llr_out, rx_stats *stats) {
+    if (!h || !samples || !llr_out) return fail(RX_EINVAL, "NULL argument");
+    if (n_samples < 2 || (n_samples & 1)) return fail(RX_EINVAL, "n_samples must be a positive multiple of 2");
+    const long N = (long)n_samples / 2;
+    const long nblk = (N + h->block - 1) / h->block;
+    if (b1 <= b0 || (long)b1 > nblk)
+        return fail(RX_EINVAL, "block range [%zu, %zu) not inside the stream's %ld blocks", b0, b1, nblk);
+    if (b0 > 0 && !(h->started && h->cur_n == N && h->blocks_done == (long)b0))
+        return fail(RX_ESTATE, "block %zu does not continue the handle's stream (at block %ld of a %ld-symbol "
+                    "stream%s)", b0, h->blocks_done, h->cur_n, h->started ? "" : ", not started");
+    int rc = run_blocks(h, (const float2 *)samples, N, (long)b0, (long)b1, llr_out);
+    if (rc != RX_OK) return rc;
+    CK(cudaGetLastError());
+    if (stats) return fill_stats(h, stats);
+    return RX_OK;
+}
+
 int rx_get_state(rx_handle *h, void *buf, size_t *len) {
     if (!h || !len) return fail(RX_EINVAL, "NULL argument");
-    (void)buf;
-    return fail(RX_ESTATE, "state serialisation not available yet");
+    if (!h->started || h->blocks_done < 1) return fail(RX_ESTATE, "no block of a stream has run yet");
+    const StateLayout lay = state_layout(h);
+    if (!buf) { *len = lay.total; return RX_OK; }
+    if (*len < lay.total) {
+        *len = lay.total;
+        return fail(RX_EINVAL, "state needs %zu bytes", lay.total);
+    }
+    const int S = h->streams, T = h->T, L = h->lag, W = h->W;
+    const long n = h->blocks_done, N = h->cur_n, K = n * h->block;
+    unsigned char *out = static_cast<unsigned char *>(buf);
+    std::memset(out, 0, lay.total);
+    CK(cudaStreamSynchronize(h->st));
+    rx_state_header hd{};
+    hd.magic = RX_STATE_MAGIC;
+    hd.version = RX_STATE_VERSION;
+    hd.streams = S; hd.taps = T; hd.lag = L; hd.bps_window = W; hd.bps_phases = h->B; hd.m_bits = h->fmt.m;
+    hd.block = h->block; hd.n_sym = N; hd.blocks_done = n; hd.lms_updates = h->u;
+    std::memcpy(out, &hd, sizeof hd);
+    const size_t tapsz = sizeof(float2) * (size_t)S * 4 * T;
+    for (int j = 0; j < L; ++j)
+        CK(cudaMemcpy(out + lay.taps + j * tapsz, slot(h, n - L + j), tapsz, cudaMemcpyDeviceToHost));
+    std::vector<StreamDev> sd(S);
+    CK(cudaMemcpy(sd.data(), h->sd, sizeof(StreamDev) * S, cudaMemcpyDeviceToHost));
+    int32_t *carry = reinterpret_cast<int32_t *>(out + lay.carry);
+    rx_state_counters *cnt = reinterpret_cast<rx_state_counters *>(out + lay.counters);
+    for (int s = 0; s < S; ++s) {
+        carry[2 * s] = sd[s].carry[n & 1][0];
+        carry[2 * s + 1] = sd[s].carry[n & 1][1];
+        cnt[s].bit_errors = sd[s].bit_errors;
+        cnt[s].n_sym = sd[s].n_sym;
+        cnt[s].gmi_sum = sd[s].gmi_sum;
+        cnt[s].evm_num = sd[s].evm_num;
+        cnt[s].evm_den = sd[s].evm_den;
+        cnt[s].sigma2 = sd[s].sigma2;
+    }
+    // y rows [S*2][N]; the halo is symbols K-W .. K-1 (zeros outside 0 .. N-1)
+    const long lo = std::max(0L, K - W), hi = std::min(K, N), skip = lo - (K - W);
+    if (hi > lo)
+        CK(cudaMemcpy2D(out + lay.y_tail + sizeof(float2) * skip, sizeof(float2) * W, h->y + lo,
+                        sizeof(float2) * N, sizeof(float2) * (hi - lo), (size_t)2 * S, cudaMemcpyDeviceToHost));
+    *len = lay.total;
+    return RX_OK;
 }
 
 int rx_set_state(rx_handle *h, const void *buf, size_t len) {
     if (!h || !buf) return fail(RX_EINVAL, "NULL argument");
-    (void)len;
-    return fail(RX_ESTATE, "state serialisation not available yet");
+    if (len < sizeof(rx_state_header)) return fail(RX_EINVAL, "state of %zu bytes is shorter than its header", len);
+    rx_state_header hd;
+    std::memcpy(&hd, buf, sizeof hd);
+    if (hd.magic != RX_STATE_MAGIC || hd.version != RX_STATE_VERSION)
+        return fail(RX_EINVAL, "not a version-%u receiver state", RX_STATE_VERSION);
+    if (hd.streams != h->streams || hd.taps != h->T || hd.lag != h->lag || hd.bps_window != h->W ||
+        hd.bps_phases != h->B || hd.m_bits != h->fmt.m || hd.block != h->block)
+        return fail(RX_EINVAL, "state (S %d, T %d, lag %d, W %d, B %d, m %d, block %lld) does not match the "
+                    "handle (S %d, T %d, lag %d, W %d, B %d, m %d, block %ld)", hd.streams, hd.taps, hd.lag,
+                    hd.bps_window, hd.bps_phases, hd.m_bits, (long long)hd.block, h->streams, h->T, h->lag,
+                    h->W, h->B, h->fmt.m, h->block);
+    const long N = (long)hd.n_sym, n = (long)hd.blocks_done;
+    const long nblk = N > 0 ? (N + h->block - 1) / h->block : 0;
+    if (N <= 0 || n < 1 || n > nblk || hd.lms_updates < 0)
+        return fail(RX_EINVAL, "state at block %lld of a %lld-symbol stream cannot be resumed",
+                    (long long)n, (long long)N);
+    const StateLayout lay = state_layout(h);
+    if (len != lay.total) return fail(RX_EINVAL, "state has %zu bytes, expected %zu", len, lay.total);
+    int rc;
+    if ((rc = upload_tables(h)) != RX_OK) return rc;
+    if ((rc = ensure_buffers(h, N)) != RX_OK) return rc;
+    if ((rc = ensure_streams(h)) != RX_OK) return rc;
+    const int S = h->streams, T = h->T, L = h->lag, W = h->W;
+    const long K = n * h->block;
+    const unsigned char *in = static_cast<const unsigned char *>(buf);
+    CK(cudaStreamSynchronize(h->st));
+    if (h->side) CK(cudaStreamSynchronize(h->side));
+    const size_t tapsz = sizeof(float2) * (size_t)S * 4 * T;
+    for (int j = 0; j < L; ++j)
+        CK(cudaMemcpy(slot(h, n - L + j), in + lay.taps + j * tapsz, tapsz, cudaMemcpyHostToDevice));
+    std::vector<StreamDev> sd(S);
+    std::memset(sd.data(), 0, sizeof(StreamDev) * S);
+    const int32_t *carry = reinterpret_cast<const int32_t *>(in + lay.carry);
+    const rx_state_counters *cnt = reinterpret_cast<const rx_state_counters *>(in + lay.counters);
+    for (int s = 0; s < S; ++s) {
+        sd[s].carry[n & 1][0] = carry[2 * s];
+        sd[s].carry[n & 1][1] = carry[2 * s + 1];
+        sd[s].bit_errors = cnt[s].bit_errors;
+        sd[s].n_sym = cnt[s].n_sym;
+        sd[s].gmi_sum = cnt[s].gmi_sum;
+        sd[s].evm_num = cnt[s].evm_num;
+        sd[s].evm_den = cnt[s].evm_den;
+        sd[s].sigma2 = cnt[s].sigma2;
+    }
+    CK(cudaMemcpy(h->sd, sd.data(), sizeof(StreamDev) * S, cudaMemcpyHostToDevice));
+    const long lo = std::max(0L, K - W), hi = std::min(K, N), skip = lo - (K - W);
+    if (hi > lo)
+        CK(cudaMemcpy2D(h->y + lo, sizeof(float2) * N, in + lay.y_tail + sizeof(float2) * skip,
+                        sizeof(float2) * W, sizeof(float2) * (hi - lo), (size_t)2 * S, cudaMemcpyHostToDevice));
+    h->u = (long)hd.lms_updates;
+    h->blocks_done = n;
+    h->cur_n = N;
+    h->trained = false;
+    h->started = true;
+    return RX_OK;
 }
 
 // ---- single stages ---------------------------------------------------------
@@ -905,7 +1042,7 @@ int rx_bps(rx_handle *h, const void *y, size_t n_y, size_t a, size_t e, size_t n
     const long ncta = ((long)(e - a) + bps_cta_range(rounds) - 1) / bps_cta_range(rounds);
     CK(cudaMallocAsync(&dsum, sizeof(int) * (size_t)h->streams * (ncta + 1), h->st));
     cudaError_t err = launch_bps((const float2 *)y, (long)n_y, (long)a, (long)e, (long)n_valid, h->W,
-                                 b_out, (long)(e - a), 0, dsum, rounds, h->streams, h->fmt, h->st);
+                                 b_out, (long)(e - a), 0, dsum, nullptr, rounds, h->streams, h->fmt, h->st);
     cudaFreeAsync(dsum, h->st);
     CK(err);
     return RX_OK;
@@ -931,7 +1068,7 @@ int rx_unwrap(rx_handle *h, const void *y, size_t n_y, const uint8_t *b, size_t 
     CK(launch_dsum_from_b(b, K, a, e, dsum, rounds, S, h->fmt.B, h->st));
     cudaError_t err = launch_unwrap((const float2 *)y, (long)n_y, b, K, 0, (long)a, (long)e, dsum,
                                     carry_in, 2, carry_out, 2, (float2 *)z, K, 0, pcode, K, 0, part,
-                                    sigma2, 1, ticket, 1, rounds, S, h->fmt, h->st);
+                                    sigma2, 1, ticket, 1, rounds, nullptr, S, h->fmt, h->st);
     cudaFreeAsync(dsum, h->st);
     cudaFreeAsync(part, h->st);
     cudaFreeAsync(ticket, h->st);
@@ -969,7 +1106,7 @@ int rx_unwrap_static(rx_handle *h, const void *y, size_t n_y, const uint8_t *b, 
     CK(launch_dsum_from_b(b, K, a, e, dsum, rounds, S, h->fmt.B, h->st));
     CK(launch_unwrap((const float2 *)y, (long)n_y, b, K, 0, (long)a, (long)e, dsum, carry_in, 2,
                      carry_out, 2, (float2 *)z, K, 0, pcode, K, 0, part, sigma2, 1, ticket, 1,
-                     rounds, S, h->fmt, h->st));
+                     rounds, nullptr, S, h->fmt, h->st));
     return RX_OK;
 }
 

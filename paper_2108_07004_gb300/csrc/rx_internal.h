@@ -87,8 +87,11 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
 }
 
 // ---- launchers (return cudaError_t of the launch) -----------------------------
+// Overlap-save frames f0 .. f1-1 (frame f writes outputs f*(n_fft-n_ov) ..
+// (f+1)*(n_fft-n_ov) - 1); f1 < 0 means every frame of the ns samples.
 cudaError_t launch_cdc(const float2 *in, float2 *out, long ns, int n_streams2, int n_fft,
-                       int n_ov, const float2 *H, const float2 *tw, cudaStream_t st);
+                       int n_ov, const float2 *H, const float2 *tw, cudaStream_t st,
+                       long f0 = 0, long f1 = -1);
 
 cudaError_t launch_fir(const float2 *x, long ns, const float2 *taps, long k0, long k1,
                        float2 *y, long y_stride, long y_off, int n_streams, int T,
@@ -112,9 +115,12 @@ cudaError_t launch_align(const float2 *x, long ns, float2 *taps, const uint8_t *
 int bps_cta_range(int rounds);              // output symbols per BPS / unwrap block
 int bps_rounds(long len, int n_streams);    // rounds that fill about one wave
 
+// mdsum (optional, [S][n_blocks] float64): per-block sums of the minimum
+// distance at the chosen phase, the decision-directed noise of the range
 cudaError_t launch_bps(const float2 *y, long y_stride, long a, long e, long n_valid,
                        int W, uint8_t *bout, long bout_stride, long bout_off,
-                       int *dsum, int rounds, int n_streams, const FmtDev &f, cudaStream_t st);
+                       int *dsum, double *mdsum, int rounds, int n_streams, const FmtDev &f,
+                       cudaStream_t st);
 
 cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long b_stride,
                           long b_off, long a, long e, const int *dsum,
@@ -124,7 +130,7 @@ cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long
                           uint16_t *pcode, long pcode_stride, long pcode_off,
                           double *partial, double *sigma2_out, int sigma2_stride,
                           unsigned int *ticket, int ticket_stride, int rounds,
-                          int n_streams, const FmtDev &f, cudaStream_t st);
+                          const double *mdsum, int n_streams, const FmtDev &f, cudaStream_t st);
 
 cudaError_t launch_anchor(const uint8_t *b, long b_stride, const uint16_t *tcode, long t_stride,
                           int n, int32_t *carry, int carry_stride, int n_streams, int B, int S,

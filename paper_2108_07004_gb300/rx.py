@@ -58,6 +58,7 @@ _PROTOS = {
     "rx_get_block_latency": (_I, [_VP, C.POINTER(_D), _SZ, C.POINTER(_SZ)]),
     "rx_get_state": (_I, [_VP, _VP, C.POINTER(_SZ)]),
     "rx_set_state": (_I, [_VP, _VP, _SZ]),
+    "rx_process_blocks": (_I, [_VP, _VP, _SZ, _SZ, _SZ, _VP, _VP]),
     "rx_format_info": (_I, [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "rx_last_error": (C.c_char_p, []),
     "rx_cdc": (_I, [_VP, _VP, _VP, _SZ]),
@@ -108,6 +109,58 @@ def _ptr(t) -> int | None:
             raise ValueError("array must be C-contiguous")
         return t.ctypes.data
     return int(t)
+
+
+# Receiver state buffer (rx_get_state / rx_set_state): header, then
+# taps [L][S][2][2][T] c64, carry [S][2] int32, y_tail [S][2][W] c64,
+# counters [S] (uint64 bit_errors, n_sym; float64 gmi_sum, evm_num,
+# evm_den, sigma2).
+STATE_MAGIC, STATE_VERSION = 0x31535852, 1
+STATE_HEADER = np.dtype([("magic", "<u4"), ("version", "<u4"), ("streams", "<i4"), ("taps", "<i4"),
+                         ("lag", "<i4"), ("bps_window", "<i4"), ("bps_phases", "<i4"),
+                         ("m_bits", "<i4"), ("block", "<i8"), ("n_sym", "<i8"),
+                         ("blocks_done", "<i8"), ("lms_updates", "<i8")])
+STATE_COUNTERS = np.dtype([("bit_errors", "<u8"), ("n_sym", "<u8"), ("gmi_sum", "<f8"),
+                           ("evm_num", "<f8"), ("evm_den", "<f8"), ("sigma2", "<f8")])
+
+
+def pack_state(header: dict, ring: np.ndarray, carry: np.ndarray, y_tail: np.ndarray,
+               counters: np.ndarray | None = None) -> bytes:
+    """Lay out a receiver state from its header fields and parts (ring: the
+    taps [L][S][2][2][T]; shapes as documented)."""
+    hd = np.zeros(1, STATE_HEADER)
+    hd["magic"], hd["version"] = STATE_MAGIC, STATE_VERSION
+    for k, v in header.items():
+        hd[k] = v
+    S = int(hd["streams"][0])
+    if counters is None:
+        counters = np.zeros(S, STATE_COUNTERS)
+    parts = [hd.tobytes(), np.ascontiguousarray(ring, dtype=np.complex64).tobytes(),
+             np.ascontiguousarray(carry, dtype=np.int32).tobytes(),
+             np.ascontiguousarray(y_tail, dtype=np.complex64).tobytes(),
+             np.ascontiguousarray(counters, dtype=STATE_COUNTERS).tobytes()]
+    return b"".join(parts)
+
+
+def unpack_state(blob: bytes) -> dict:
+    """Split a receiver state into its header fields and the arrays "ring"
+    (taps), "carry", "y_tail" and "counters"."""
+    hd = np.frombuffer(blob, STATE_HEADER, count=1)[0]
+    S, T, L, W = int(hd["streams"]), int(hd["taps"]), int(hd["lag"]), int(hd["bps_window"])
+    o = STATE_HEADER.itemsize
+    out = {k: hd[k].item() for k in STATE_HEADER.names}
+    n = L * S * 4 * T
+    out["ring"] = np.frombuffer(blob, np.complex64, n, o).reshape(L, S, 2, 2, T)
+    o += 8 * n
+    out["carry"] = np.frombuffer(blob, np.int32, 2 * S, o).reshape(S, 2)
+    o += 8 * S
+    out["y_tail"] = np.frombuffer(blob, np.complex64, 2 * S * W, o).reshape(S, 2, W)
+    o += 16 * S * W
+    out["counters"] = np.frombuffer(blob, STATE_COUNTERS, S, o)
+    o += STATE_COUNTERS.itemsize * S
+    if o != len(blob):
+        raise ValueError(f"state of {len(blob)} bytes, layout gives {o}")
+    return out
 
 
 def load_table(name: str) -> dict:
@@ -183,6 +236,19 @@ class Receiver:
         st = (RxStats * S)() if stats else None
         _ck(lib().rx_process(self.h, _ptr(samples), ns, _ptr(llr),
                              C.cast(st, C.c_void_p) if st is not None else None))
+        return llr, ([s.as_dict() for s in st] if st is not None else None)
+
+    def process_blocks(self, samples: torch.Tensor, b0: int, b1: int,
+                       llr: torch.Tensor | None = None, stats: bool = True):
+        """Blocks b0 .. b1-1 of the streams in samples [S, 2, 2N] (device);
+        b0 > 0 continues from the handle's state.  Rows outside the blocks'
+        ranges of llr are left as they are."""
+        S, _, ns = samples.shape
+        if llr is None:
+            llr = torch.zeros((S, ns // 2, self.m), dtype=torch.float32, device=samples.device)
+        st = (RxStats * S)() if stats else None
+        _ck(lib().rx_process_blocks(self.h, _ptr(samples), ns, b0, b1, _ptr(llr),
+                                    C.cast(st, C.c_void_p) if st is not None else None))
         return llr, ([s.as_dict() for s in st] if st is not None else None)
 
     def process_host(self, samples, llr, stats: bool = True):

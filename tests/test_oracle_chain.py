@@ -61,3 +61,26 @@ def test_chain_gs4d64_small():
     assert c["ber"] < 2e-2 and c["gmi"] > 5.5
     # once DD-LMS runs, the decision-directed sigma^2 estimate is close to N0
     assert abs(res.sigma2[-1] / st.n0 - 1) < 0.1
+
+
+@pytest.mark.parametrize("lag", [1, 2])
+def test_chain_resumes_from_block_state(lag):
+    """Nothing but the block-boundary state carries from block to block: a
+    run restarted at block n from state_at(n) of a continuous run gives
+    that run's taps, phases and LLRs from block n on, exactly."""
+    fmt = oracle_format("dp_qpsk")
+    n = 10000
+    st = synth.make_stream("dp_qpsk", n, seed=22, esn0_db=11.0, cd_ps_per_nm=500.0,
+                           linewidth_ts=1e-5)
+    p = chain.RxParams(cd_ps_per_nm=500.0, block=2048, n_pre=2048, lag=lag, n_upd=512, n_cma=600)
+    full = chain.run_chain(st.rx, fmt, p, ref_bits=st.bits)
+    for nb in (1, 3):
+        stt = chain.state_at(full, p, nb)
+        part = chain.run_chain(st.rx, fmt, p, ref_bits=st.bits, resume=(nb, stt))
+        a = full.ranges[nb][0]
+        assert part.ranges[nb:] == full.ranges[nb:]
+        assert np.array_equal(part.llr[a:], full.llr[a:])
+        assert np.array_equal(part.b[a:], full.b[a:]) and np.array_equal(part.m[a:], full.m[a:])
+        for i in range(nb, len(full.taps_after)):
+            assert np.array_equal(part.taps_after[i], full.taps_after[i])
+        assert np.all(part.llr[:a] == 0)

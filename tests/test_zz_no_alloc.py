@@ -52,12 +52,14 @@ def test_unwrap_static_matches_allocating_entry_point_twice():
 
 
 def test_unwrap_static_refuses_more_scratch_than_it_has():
-    """4096 streams x 2000 symbols need two blocks per stream: 16 KiB of
-    tickets + 32 KiB of increments + 64 KiB of partial sums > 64 KiB, so the
-    call is refused before anything is launched.  Every buffer still has its
-    full size, so nothing could be touched out of bounds either way."""
+    """2048 streams x 10000 symbols: with one block per stream and wave
+    (2048 streams already fill it) a block covers at most 4032 symbols, so a
+    stream needs three blocks: 8 KiB of tickets + 24 KiB of increments +
+    48 KiB of partial sums = 80 KiB > 64 KiB, and the call is refused before
+    anything is launched.  Every buffer still has its full size, so nothing
+    could be touched out of bounds either way."""
     from paper_2108_07004_gb300 import rx
-    S, n = 4096, 2000
+    S, n = 2048, 10000
     r = rx.Receiver("gs4d64", taps=31, bps_phases=B, streams=S)
     y = torch.zeros((S, 2, n), dtype=torch.complex64, device="cuda")
     b = torch.full((S, n), 32, dtype=torch.uint8, device="cuda")
