@@ -47,6 +47,16 @@ __device__ __forceinline__ float orbit_v(float P, float Q, int S) {
     return P;
 }
 
+// |rep|^2 - 2 (orbit value at the test phase shifted by half the phase span,
+// 2 pi / (2S)) from (P, Q) at the unshifted phase: the shift rotates P + jQ
+// by -pi/4, -pi/2 or -pi, so max(|P'|, |Q'|) = (|P| + |Q|) / sqrt 2 (S = 4),
+// |P'| = |Q| (S = 2), P' = -P (S = 1).
+__device__ __forceinline__ float half_turn_d(float P, float Q, int S, float e) {
+    if (S == 4) return fmaf(-1.41421356237309515f, fabsf(P) + fabsf(Q), e);
+    if (S == 2) return fmaf(-2.f, fabsf(Q), e);
+    return fmaf(2.f, P, e);
+}
+
 template <int DIMS, int NORB>
 __global__ void __launch_bounds__(256, 2)
 bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_valid, int W,
@@ -113,32 +123,28 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
         }
         const int slot = (jc + 1) % RX_NCHUNK;
         const int hb = B >> 1;
-        // test phases b and b + B/2 together: independent minimum chains
+        // test phases b and b + B/2 together: phi_{b+B/2} = phi_b + pi/S, a
+        // rotation of P + jQ that half_turn_d applies without another multiply
         for (int b = 0; b < hb; ++b) {
             const f32x2 *cp1 = reinterpret_cast<const f32x2 *>(f.csp[b]);
-            const f32x2 *cp2 = reinterpret_cast<const f32x2 *>(f.csp[b + hb]);
-            const f32x2 C1 = cp1[0], S1 = cp1[1], C2 = cp2[0], S2 = cp2[1];
+            const f32x2 C1 = cp1[0], S1 = cp1[1];
             float md, md2;
             if (DIMS == 4) {
                 float a0 = 3.0e38f, a1 = 3.0e38f;
 #pragma unroll
                 for (int o = 0; o + 1 < NORB; o += 2) {
-                    float P, Q, P2, Q2, R, U, R2, U2;
+                    float P, Q, R, U;
                     upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P, Q);
-                    upk2(fma2(S2, CI[0][o], mul2(C2, CR[0][o])), P2, Q2);
                     upk2(fma2(S1, CI[0][o + 1], mul2(C1, CR[0][o + 1])), R, U);
-                    upk2(fma2(S2, CI[0][o + 1], mul2(C2, CR[0][o + 1])), R2, U2);
                     a0 = fmin3(a0, fmaf(-2.f, orbit_v(P, Q, S), f.orbe[o]),
                                fmaf(-2.f, orbit_v(R, U, S), f.orbe[o + 1]));
-                    a1 = fmin3(a1, fmaf(-2.f, orbit_v(P2, Q2, S), f.orbe[o]),
-                               fmaf(-2.f, orbit_v(R2, U2, S), f.orbe[o + 1]));
+                    a1 = fmin3(a1, half_turn_d(P, Q, S, f.orbe[o]), half_turn_d(R, U, S, f.orbe[o + 1]));
                 }
                 if (NORB & 1) {
-                    float P, Q, P2, Q2;
+                    float P, Q;
                     upk2(fma2(S1, CI[0][NORB - 1], mul2(C1, CR[0][NORB - 1])), P, Q);
-                    upk2(fma2(S2, CI[0][NORB - 1], mul2(C2, CR[0][NORB - 1])), P2, Q2);
                     a0 = fminf(a0, fmaf(-2.f, orbit_v(P, Q, S), f.orbe[NORB - 1]));
-                    a1 = fminf(a1, fmaf(-2.f, orbit_v(P2, Q2, S), f.orbe[NORB - 1]));
+                    a1 = fminf(a1, half_turn_d(P, Q, S, f.orbe[NORB - 1]));
                 }
                 md = yn0 + a0;
                 md2 = yn0 + a1;
@@ -146,17 +152,13 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
                 float x0 = 3.0e38f, x1 = 3.0e38f, w0 = 3.0e38f, w1 = 3.0e38f;
 #pragma unroll
                 for (int o = 0; o < NORB; ++o) {
-                    {
-                        float P0, Q0, P1, Q1, R0, U0, R1, U1;
-                        upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P0, Q0);
-                        upk2(fma2(S1, CI[1][o], mul2(C1, CR[1][o])), P1, Q1);
-                        upk2(fma2(S2, CI[0][o], mul2(C2, CR[0][o])), R0, U0);
-                        upk2(fma2(S2, CI[1][o], mul2(C2, CR[1][o])), R1, U1);
-                        x0 = fminf(x0, fmaf(-2.f, orbit_v(P0, Q0, S), f.orbe[o]));
-                        x1 = fminf(x1, fmaf(-2.f, orbit_v(P1, Q1, S), f.orbe[o]));
-                        w0 = fminf(w0, fmaf(-2.f, orbit_v(R0, U0, S), f.orbe[o]));
-                        w1 = fminf(w1, fmaf(-2.f, orbit_v(R1, U1, S), f.orbe[o]));
-                    }
+                    float P0, Q0, P1, Q1;
+                    upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P0, Q0);
+                    upk2(fma2(S1, CI[1][o], mul2(C1, CR[1][o])), P1, Q1);
+                    x0 = fminf(x0, fmaf(-2.f, orbit_v(P0, Q0, S), f.orbe[o]));
+                    x1 = fminf(x1, fmaf(-2.f, orbit_v(P1, Q1, S), f.orbe[o]));
+                    w0 = fminf(w0, half_turn_d(P0, Q0, S, f.orbe[o]));
+                    w1 = fminf(w1, half_turn_d(P1, Q1, S, f.orbe[o]));
                 }
                 md = (yn0 + x0) + (yn1 + x1);
                 md2 = (yn0 + w0) + (yn1 + w1);
@@ -277,6 +279,7 @@ unwrap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *__rest
               int s2_stride, unsigned int *__restrict__ ticket, int ticket_stride, int kR,
               const double *__restrict__ mdsum, const __grid_constant__ FmtDev f) {
     __shared__ uint8_t bl[kMaxR];
+    __shared__ uint8_t mql[kMaxR];
     __shared__ int wsum[8];
     __shared__ int mstart_sh;
     __shared__ double dred[8];
@@ -328,35 +331,43 @@ unwrap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *__rest
     for (int w = 0; w < warp; ++w) wpre += wsum[w];
     const int tpre = mstart_sh + wpre + incl - run;   // m before this thread's symbols
 
-    const float2 *yx = y + (long)s * 2 * y_stride;
-    const float2 *yy = yx + y_stride;
-    float2 *zx = z + (long)s * 2 * z_stride;
-    float2 *zy = zx + z_stride;
-    double dsum_loc = 0.0;
+    // quadrant count m mod S of every local symbol into shared memory; the
+    // de-rotation below then walks the symbols in coalesced order
 #pragma unroll
     for (int u = 0; u < PT; ++u) {
         const int t = PT * tid + u;
         if (t >= nloc) continue;
-        const long k = out0 + t;
         const int m = tpre + d[u];
-        const int b = bl[t];
-        const int mq = ((m % S) + S) % S;
-        // exp(-j phi) = conj(cs_b) * exp(-j mq 2 pi / S)
+        mql[t] = (uint8_t)(((m % S) + S) % S);
+        if (out0 + t == e - 1) {
+            carry_out[s * cout_stride + 0] = m;
+            carry_out[s * cout_stride + 1] = bl[t];
+        }
+    }
+    __syncthreads();
+    const float2 *yx = y + (long)s * 2 * y_stride;
+    const float2 *yy = yx + y_stride;
+    float2 *zx = z + (long)s * 2 * z_stride;
+    float2 *zy = zx + z_stride;
+    uint16_t *pc = pcode + (long)s * pc_stride;
+    double dsum_loc = 0.0;
+#pragma unroll 4
+    for (int t = tid; t < nloc; t += 256) {
+        const long k = out0 + t;
+        const int b = bl[t], mq = mql[t];
+        // exp(-j phi) = conj(cs_b) (-j)^mq
         float2 rot = make_float2(f.cs[b][0], -f.cs[b][1]);
         if (S == 4) {
-            for (int i = 0; i < mq; ++i) rot = make_float2(rot.y, -rot.x);   // * (-j)
+            if (mq & 2) rot = make_float2(-rot.x, -rot.y);
+            if (mq & 1) rot = make_float2(rot.y, -rot.x);
         } else if (S == 2) {
             if (mq) rot = make_float2(-rot.x, -rot.y);
         }
         const float2 z0 = cmul(yx[k], rot), z1 = cmul(yy[k], rot);
         zx[k - a] = z0;
         zy[k - a] = z1;
-        pcode[(long)s * pc_stride + (k - a)] = (uint16_t)(b | (mq << 8));
+        pc[k - a] = (uint16_t)(b | (mq << 8));
         if (!mdsum) dsum_loc += (double)nearest_dist<DIMS, NORB>(z0, z1, f);
-        if (k == e - 1) {
-            carry_out[s * cout_stride + 0] = m;
-            carry_out[s * cout_stride + 1] = b;
-        }
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) dsum_loc += __shfl_xor_sync(0xffffffffu, dsum_loc, off);

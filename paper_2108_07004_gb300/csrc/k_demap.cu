@@ -25,8 +25,15 @@ constexpr float kLog2e = 1.4426950408889634f;
 constexpr float kLn2 = 0.6931471805599453f;
 constexpr float kOff = 120.f;
 
+__device__ __forceinline__ float ex2_ftz(float x) {        // 2^x, subnormal results flushed to 0
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 __device__ __forceinline__ float softplus_bits(float x) {   // log2(1 + exp(x))
-    return (fmaxf(x, 0.f) + log1pf(expf(-fabsf(x)))) * kLog2e;
+    const float t = x * kLog2e;
+    return fmaxf(t, 0.f) + __log2f(1.f + ex2_ftz(-fabsf(t)));
 }
 
 template <int DIMS>
@@ -40,44 +47,74 @@ __device__ __forceinline__ float dist_to(float2 z0, float2 z1, const FmtDev &f, 
     return d;
 }
 
-// Rare path, for a lookup where some bit's subset sum fell below 2^-100 of
-// the common shift: every subset gets its own minimum as shift.  Rewrites
-// out[] and the counting terms of this lookup.
+// Rare path, for lookups where some bit's subset sum fell below 2^-100 of
+// the common shift (|LLR| beyond ~150): every subset gets its own minimum
+// as shift.  The whole warp serves the flagged lanes one after another:
+// the lanes split the table (points lane, lane + 32), and the subset minima
+// and sums are warp reductions in a fixed order.  Rewrites the flagged
+// lanes' LLRs L[0..MB-1] and their counting terms (ne, g2) of this lookup.
 template <int DIMS, int MT, int MB>
-__device__ __noinline__ void llr_table_slow(float2 z0, float2 z1, const FmtDev &f, float c2,
-                                            float *out, int ref, int *nerr, float *gs) {
-    int ne = 0;
-    float g2 = 0.f;
-    for (int bp = 0; bp < MB; ++bp) {
-        float lg[2];
-        for (int v = 0; v < 2; ++v) {
-            float dm = 3.0e38f;
-            for (int j = 0; j < MT; ++j)
-                if (((j >> bp) & 1) == v) dm = fminf(dm, dist_to<DIMS>(z0, z1, f, j));
-            float acc = 0.f;
-            for (int j = 0; j < MT; ++j)
-                if (((j >> bp) & 1) == v) acc += exp2f((dm - dist_to<DIMS>(z0, z1, f, j)) * c2);
-            lg[v] = -dm * c2 + log2f(acc);
+__device__ __forceinline__ void llr_fixup_warp(unsigned need, float2 z0, float2 z1, const FmtDev &f, float c2,
+                                            float *L, int ref, int &ne, float &g2) {
+    const int lane = threadIdx.x & 31;
+    constexpr int NPL = (MT + 31) / 32;   // points per lane
+    while (need) {
+        const int src = __ffs(need) - 1;
+        need &= need - 1;
+        const float2 a0 = make_float2(__shfl_sync(0xffffffffu, z0.x, src), __shfl_sync(0xffffffffu, z0.y, src));
+        const float2 a1 = make_float2(__shfl_sync(0xffffffffu, z1.x, src), __shfl_sync(0xffffffffu, z1.y, src));
+        const float cc = __shfl_sync(0xffffffffu, c2, src);
+        float d[NPL];
+#pragma unroll
+        for (int i = 0; i < NPL; ++i) {
+            const int j = lane + 32 * i;
+            d[i] = j < MT ? dist_to<DIMS>(a0, a1, f, j) : 3.0e38f;
         }
-        const float L = (lg[0] - lg[1]) * kLn2;
-        out[MB - 1 - bp] = L;
-        if (ref >= 0) {
-            const int bit = (ref >> bp) & 1;
-            ne += (int)((L < 0.f) != (bit != 0));
-            g2 += softplus_bits(bit ? L : -L);
+        int ne_s = 0;
+        float g2_s = 0.f;
+        const int rs = __shfl_sync(0xffffffffu, ref, src);
+#pragma unroll
+        for (int bp = 0; bp < MB; ++bp) {
+            float lg[2];
+#pragma unroll
+            for (int v = 0; v < 2; ++v) {
+                float dm = 3.0e38f;
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    const int j = lane + 32 * i;
+                    if (j < MT && ((j >> bp) & 1) == v) dm = fminf(dm, d[i]);
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) dm = fminf(dm, __shfl_xor_sync(0xffffffffu, dm, off));
+                float acc = 0.f;
+#pragma unroll
+                for (int i = 0; i < NPL; ++i) {
+                    const int j = lane + 32 * i;
+                    if (j < MT && ((j >> bp) & 1) == v) acc += exp2f((dm - d[i]) * cc);
+                }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, off);
+                lg[v] = -dm * cc + log2f(acc);
+            }
+            const float Lb = (lg[0] - lg[1]) * kLn2;
+            if (lane == src) L[MB - 1 - bp] = Lb;
+            if (rs >= 0) {
+                const int bit = (rs >> bp) & 1;
+                ne_s += (int)((Lb < 0.f) != (bit != 0));
+                g2_s += softplus_bits(bit ? Lb : -Lb);
+            }
         }
+        if (lane == src) { ne = ne_s; g2 = g2_s; }
     }
-    *nerr = ne;
-    *gs = g2;
 }
 
 // LLRs of one table lookup of z (DIMS 4: joint; DIMS 2: z0 alone), MB bits,
 // written to out[0..MB-1] (MSB first).  When ref >= 0 (the reference label of
 // this lookup) the hard-decision errors and the GMI terms are accumulated.
 template <int DIMS, int MT, int MB>
-__device__ __forceinline__ void llr_table(float2 z0, float2 z1, const FmtDev &f, float c2,
-                                          float *out, float &g, int &jmin, int ref, int &nerr,
-                                          float &gs) {
+__device__ __forceinline__ bool llr_table(float2 z0, float2 z1, const FmtDev &f, float c2,
+                                          float *out, float &g, int &jmin, int ref, int &ne,
+                                          float &g2) {
     float cur[MT];
 #pragma unroll
     for (int j = 0; j < MT; ++j) cur[j] = dist_to<DIMS>(z0, z1, f, j);
@@ -87,10 +124,10 @@ __device__ __forceinline__ void llr_table(float2 z0, float2 z1, const FmtDev &f,
     for (int j = 1; j < MT; ++j)
         if (cur[j] < g) { g = cur[j]; jmin = j; }
 #pragma unroll
-    for (int j = 0; j < MT; ++j) cur[j] = exp2f(fmaf(g - cur[j], c2, kOff));
+    for (int j = 0; j < MT; ++j) cur[j] = ex2_ftz(fmaf(g - cur[j], c2, kOff));
     bool low = false;
-    int ne = 0;
-    float g2 = 0.f;
+    ne = 0;
+    g2 = 0.f;
 #pragma unroll
     for (int bp = 0; bp < MB; ++bp) {
         const int n = MT >> bp;
@@ -110,22 +147,50 @@ __device__ __forceinline__ void llr_table(float2 z0, float2 z1, const FmtDev &f,
         for (int i = 0; i < MT / 2; ++i)
             if (2 * i < n) cur[i] = cur[2 * i] + cur[2 * i + 1];
     }
-    if (low) llr_table_slow<DIMS, MT, MB>(z0, z1, f, c2, out, ref, &ne, &g2);
-    nerr += ne;
-    gs += g2;
+    return low;
+}
+
+// Eight consecutive labels g8 .. g8+7 as packed pairs E[v] = (e_{2v}, e_{2v+1})
+// (the low three label bits vary, the high ones are those of g8): subset
+// sums of the low three bits by a small tree, the group total for the high
+// bits.
+template <int MB>
+__device__ __forceinline__ void add_group8(const f32x2 (&E)[4], int g8, f32x2 &s01, float (&s0)[MB],
+                                           float (&s1)[MB]) {
+    const f32x2 H = add2(E[0], E[1]), I = add2(E[2], E[3]);   // (e0+e2, e1+e3), (e4+e6, e5+e7)
+    const f32x2 F = add2(E[0], E[2]), G = add2(E[1], E[3]);   // (e0+e4, e1+e5), (e2+e6, e3+e7)
+    s01 = add2(s01, add2(H, I));                              // bit 0: (evens, odds)
+    float hx, hy, ix, iy, fx, fy, gx, gy;
+    upk2(H, hx, hy);
+    upk2(I, ix, iy);
+    upk2(F, fx, fy);
+    upk2(G, gx, gy);
+    s0[1] += fx + fy;
+    s1[1] += gx + gy;
+    const float q0 = hx + hy, q1 = ix + iy;
+    s0[2] += q0;
+    s1[2] += q1;
+    const float tot = q0 + q1;
+#pragma unroll
+    for (int i = 3; i < MB; ++i) {
+        if ((g8 >> i) & 1) s1[i] += tot;
+        else s0[i] += tot;
+    }
 }
 
 // 4D table of MT points with MB label bits, streaming form: the shift is the
-// minimum distance from the orbit form (|z|^2 + |rep|^2 - 2 max(|P|,|Q|), no
-// per-point state), then every point's exact distance and exponential is
-// added to the two running subset sums of each label bit (the bit pattern of
-// point j is known at compile time).  Twelve accumulators instead of 64
-// stored terms keep the registers low; the result is the same sum.
+// minimum distance from the orbit form (|z|^2 + |rep|^2 - 2 max(|P|,|Q|)),
+// which also gives the nearest point's energy; then every point's exact
+// distance |z - s_j|^2 (differences, no cancellation) and exponential is
+// added to the subset sums of its label bits, eight labels at a time.  The
+// loop is fully unrolled, so every table entry is a constant-bank operand
+// and every label bit is known at compile time; twelve accumulators instead
+// of 64 stored terms keep the registers low.
 template <int MT, int MB>
-__device__ __forceinline__ void llr_4d_stream(float2 z0, float2 z1, const FmtDev &f, float c2,
-                                              float *out, float &gmin, int &jmin, int ref,
-                                              int &nerr, float &gs) {
-    float g = 3.0e38f;
+__device__ __forceinline__ bool llr_4d_stream(float2 z0, float2 z1, const FmtDev &f, float c2,
+                                              float *out, float &gmin, float &emin, int ref,
+                                              int &ne, float &g2) {
+    float g = 3.0e38f, eg = 0.f;
     const float zn = cnorm(z0) + cnorm(z1);
 #pragma unroll
     for (int o = 0; o < 16; ++o) {
@@ -133,44 +198,46 @@ __device__ __forceinline__ void llr_4d_stream(float2 z0, float2 z1, const FmtDev
             const float P = z0.x * f.orb[o][0] + z0.y * f.orb[o][1] + z1.x * f.orb[o][2] + z1.y * f.orb[o][3];
             const float Q = z0.y * f.orb[o][0] - z0.x * f.orb[o][1] + z1.y * f.orb[o][2] - z1.x * f.orb[o][3];
             const float v = (f.S == 4) ? fmaxf(fabsf(P), fabsf(Q)) : (f.S == 2 ? fabsf(P) : P);
-            g = fminf(g, zn + f.orbe[o] - 2.f * v);
+            const float d = zn + f.orbe[o] - 2.f * v;
+            if (d < g) { g = d; eg = f.orbe[o]; }
         }
     }
     const float sh = fmaf(g, c2, kOff);      // exponent of point j: sh - d_j c2
     float s0[MB], s1[MB];
 #pragma unroll
     for (int i = 0; i < MB; ++i) { s0[i] = 0.f; s1[i] = 0.f; }
-    float dmin = 3.0e38f;
-    int jm = 0;
-    // groups of 8 points: the low 3 label bits are fixed per point, the high
-    // bits per group (the group total is added to their subset sums)
-#pragma unroll 1
+    f32x2 s01 = pk2(0.f, 0.f);
+    // labels j, j+1 as packed pairs: d = sum_c (z_c - s_c)^2 per lane
+    const f32x2 Z0 = pk2(z0.x, z0.x), Z1 = pk2(z0.y, z0.y), Z2 = pk2(z1.x, z1.x), Z3 = pk2(z1.y, z1.y);
+    const f32x2 NC = pk2(-c2, -c2), SH = pk2(sh, sh);
+    const f32x2 *T0 = reinterpret_cast<const f32x2 *>(f.ptsT[0]);
+    const f32x2 *T1 = reinterpret_cast<const f32x2 *>(f.ptsT[1]);
+    const f32x2 *T2 = reinterpret_cast<const f32x2 *>(f.ptsT[2]);
+    const f32x2 *T3 = reinterpret_cast<const f32x2 *>(f.ptsT[3]);
+#pragma unroll
     for (int g8 = 0; g8 < MT; g8 += 8) {
-        float tot = 0.f;
+        f32x2 E[4];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-            const int j = g8 + u;
-            const float d = dist_to<4>(z0, z1, f, j);
-            if (d < dmin) { dmin = d; jm = j; }
-            const float ej = exp2f(fmaf(-d, c2, sh));
-            tot += ej;
-#pragma unroll
-            for (int i = 0; i < 3 && i < MB; ++i) {
-                if ((u >> i) & 1) s1[i] += ej;
-                else s0[i] += ej;
-            }
+        for (int v = 0; v < 4; ++v) {
+            const int jp = g8 / 2 + v;
+            const f32x2 u0 = sub2(Z0, T0[jp]), u1 = sub2(Z1, T1[jp]);
+            const f32x2 u2 = sub2(Z2, T2[jp]), u3 = sub2(Z3, T3[jp]);
+            f32x2 d = mul2(u0, u0);
+            d = fma2(u1, u1, d);
+            d = fma2(u2, u2, d);
+            d = fma2(u3, u3, d);
+            float a0, a1;
+            upk2(fma2(d, NC, SH), a0, a1);
+            E[v] = pk2(ex2_ftz(a0), ex2_ftz(a1));
         }
-#pragma unroll
-        for (int i = 3; i < MB; ++i) {
-            if ((g8 >> i) & 1) s1[i] += tot;
-            else s0[i] += tot;
-        }
+        add_group8<MB>(E, g8, s01, s0, s1);
     }
-    gmin = dmin;
-    jmin = jm;
+    upk2(s01, s0[0], s1[0]);
+    gmin = fmaxf(g, 0.f);
+    emin = eg;
     bool low = false;
-    int ne = 0;
-    float g2 = 0.f;
+    ne = 0;
+    g2 = 0.f;
 #pragma unroll
     for (int bp = 0; bp < MB; ++bp) {
         low |= (s0[bp] < 7.888609052e-31f) | (s1[bp] < 7.888609052e-31f);   // 2^-100
@@ -182,9 +249,7 @@ __device__ __forceinline__ void llr_4d_stream(float2 z0, float2 z1, const FmtDev
             g2 += softplus_bits(bit ? L : -L);
         }
     }
-    if (low) llr_table_slow<4, MT, MB>(z0, z1, f, c2, out, ref, &ne, &g2);
-    nerr += ne;
-    gs += g2;
+    return low;
 }
 
 template <int DIMS, int MT, int MB>
@@ -205,19 +270,23 @@ demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
     // widened to float64 before the block and grid reductions
     int nerr = 0, ncnt = 0;
     float gsum = 0.f, en = 0.f, ed = 0.f;
-    if (k < e) {
-        const float2 z0 = zx[k - a], z1 = zy[k - a];
-        const bool counted = cnt.ref_lab && k >= cnt.c0 && k < cnt.c1;
+    // every lane runs the lookup (lanes past the range on the last symbol)
+    // so that the warp-wide rare path sees the whole warp
+    const bool active = k < e;
+    const long kk = active ? k : e - 1;
+    {
+        const float2 z0 = zx[kk - a], z1 = zy[kk - a];
+        const bool counted = active && cnt.ref_lab && k >= cnt.c0 && k < cnt.c1;
         const int ref = counted ? (int)cnt.ref_lab[(long)s * cnt.ref_stride + k] : -1;
-        float *row = llr + (long)s * llr_stride + (k - a) * M_OUT;
+        float L[M_OUT];
         int ne = 0;
         float gs = 0.f, dist_min, dmin_energy;
         if (DIMS == 4) {
-            float g;
-            int jm;
-            llr_4d_stream<MT, MB>(z0, z1, f, c2, row, g, jm, ref, ne, gs);
-            dist_min = g;
-            dmin_energy = f.pe[jm];
+            float g2;
+            const bool low = llr_4d_stream<MT, MB>(z0, z1, f, c2, L, dist_min, dmin_energy, ref, ne, g2);
+            const unsigned need = __ballot_sync(0xffffffffu, low && active);
+            if (need) llr_fixup_warp<4, MT, MB>(need, z0, z1, f, c2, L, ref, ne, g2);
+            gs = g2;
         } else {
             dist_min = 0.f;
             dmin_energy = 0.f;
@@ -225,12 +294,21 @@ demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
             for (int p = 0; p < 2; ++p) {
                 const float2 zp = p ? z1 : z0;
                 const int rp = ref < 0 ? -1 : (p ? (ref & ((1 << MB) - 1)) : (ref >> MB));
-                float g;
-                int jm;
-                llr_table<2, MT, MB>(zp, zp, f, c2, row + p * MB, g, jm, rp, ne, gs);
+                float g, g2;
+                int jm, nep;
+                const bool low = llr_table<2, MT, MB>(zp, zp, f, c2, L + p * MB, g, jm, rp, nep, g2);
+                const unsigned need = __ballot_sync(0xffffffffu, low && active);
+                if (need) llr_fixup_warp<2, MT, MB>(need, zp, zp, f, c2, L + p * MB, rp, nep, g2);
+                ne += nep;
+                gs += g2;
                 dist_min += g;
                 dmin_energy += f.pe[jm];
             }
+        }
+        if (active) {
+            float *row = llr + (long)s * llr_stride + (k - a) * M_OUT;
+#pragma unroll
+            for (int i = 0; i < M_OUT; ++i) row[i] = L[i];
         }
         if (counted) {
             nerr = ne;

@@ -1,13 +1,15 @@
 // A2: 2x2 butterfly FIR, T/2-spaced input, one output per symbol:
 //   y_q[k] = sum_{p in X,Y} sum_{t<T} conj(h_qp[t]) x_p[2k + D - t],  D = (T-1)/2.
 //
-// One block of 128 threads makes 512 consecutive outputs of one stream.  The
-// 1024 + 2D input samples of each polarisation are staged in shared memory
-// (one pad slot every 8 samples, so that threads 8 samples apart hit
-// different banks) and the conjugated taps sit in shared memory, read as
-// broadcasts.  Each thread makes 4 consecutive outputs for both q: per tap
-// it needs one new sample per even/odd tap chain (the other three slide
-// through registers), so the loop is 32 FMAs per shared-memory sample load.
+// A tile is 512 consecutive outputs of one stream; blocks of 128 threads
+// loop over tiles (persistent grid, a few blocks per SM) and stage the next
+// tile's 1024 + 2D input samples per polarisation with cp.async while they
+// filter the current one (double buffer; one pad slot every 8 samples, so
+// that threads 8 samples apart hit different banks).  Each thread makes 4
+// consecutive outputs for both q: per tap it needs one new sample per
+// even/odd tap chain (the other three slide through registers).  The
+// complex multiply-accumulate conj(h) x is two packed f32x2 FMAs:
+//   acc += (a, a) * (xr, xi) + (-b, b) * (xi, xr),   conj(h) = a + jb.
 #include "rx_internal.h"
 
 namespace {
@@ -17,85 +19,148 @@ constexpr int kThreads = 128;
 
 __device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
 
+__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
+
+template <int T>
+struct FirSmem {
+    static constexpr int D = (T - 1) / 2;
+    static constexpr int NS = 2 * kOut + 2 * D;
+    static constexpr int NSP = NS + NS / 8 + 1;
+    float2 xs[2][2][NSP];    // [buffer][p]
+    float2 hraw[2][4 * T];   // [buffer] taps h[q][p][t] of the tile's stream
+    f32x2 hA[2][2][T];       // [q][p][t] (a, a)
+    f32x2 hB[2][2][T];       // [q][p][t] (-b, b), conj(h) = a + jb
+};
+
+// stage tile `tile` (stream s = tile / tps) into buffer `buf`
+template <int T>
+__device__ __forceinline__ void fir_stage(FirSmem<T> &sm, int buf, int tile, int tps, const float2 *x,
+                                          long ns, const float2 *taps, long k0) {
+    constexpr int D = FirSmem<T>::D, NS = FirSmem<T>::NS;
+    const int s = tile / tps, tl = tile - s * tps;
+    const long base = 2 * (k0 + (long)tl * kOut) - D;   // global sample of local index 0
+    const float2 *xs0 = x + (long)s * 2 * ns;
+    for (int i = threadIdx.x; i < 2 * NS; i += kThreads) {
+        const int p = i / NS, j = i - p * NS;
+        const long g = base + j;
+        const bool ok = g >= 0 && g < ns;
+        cp_async8(&sm.xs[buf][p][pad8(j)], xs0 + (long)p * ns + (ok ? g : 0), ok);
+    }
+    for (int i = threadIdx.x; i < 4 * T; i += kThreads)
+        cp_async8(&sm.hraw[buf][i], taps + (long)s * 4 * T + i, true);
+    cp_async_commit();
+}
+
 template <int T>
 __global__ void __launch_bounds__(kThreads)
 fir_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ taps, long k0,
-           long k1, float2 *__restrict__ y, long y_stride, long y_off) {
+           long k1, float2 *__restrict__ y, long y_stride, long y_off, int tps, int n_tiles) {
     constexpr int D = (T - 1) / 2;
-    constexpr int NS = 2 * kOut + 2 * D;
-    constexpr int NSP = NS + NS / 8 + 1;
-    __shared__ float2 xs[2][NSP];
-    __shared__ float2 hs[2][2][T];   // conj(h[q][p][t])
-    const int s = blockIdx.y;
+    __shared__ __align__(16) FirSmem<T> sm;
     const int tid = threadIdx.x;
-    const long kb = k0 + (long)blockIdx.x * kOut;
-    const long base = 2 * kb - D;   // global sample of local index 0
-    const float2 *xs0 = x + (long)s * 2 * ns;
-    for (int i = tid; i < 2 * NS; i += kThreads) {
-        const int p = i / NS, j = i - p * NS;
-        const long g = base + j;
-        xs[p][pad8(j)] = (g >= 0 && g < ns) ? xs0[(long)p * ns + g] : make_float2(0.f, 0.f);
-    }
-    for (int i = tid; i < 4 * T; i += kThreads) {
-        float2 h = taps[(long)s * 4 * T + i];
-        (&hs[0][0][0])[i] = make_float2(h.x, -h.y);
-    }
-    __syncthreads();
-
-    float2 acc[2][4];
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int r = 0; r < 4; ++r) acc[q][r] = make_float2(0.f, 0.f);
-
-    const int lb = 8 * tid + 2 * D;   // local index of (r = 0, t = 0)
-#pragma unroll
-    for (int p = 0; p < 2; ++p) {
-        float2 E[4], O[4];   // even / odd tap chains: E[r] = x[lb + 2r - 2j], O[r] = x[lb + 2r - 2j - 1]
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            E[r] = xs[p][pad8(lb + 2 * r)];
-            O[r] = xs[p][pad8(lb + 2 * r - 1)];
+    int tile = blockIdx.x, buf = 0;
+    if (tile < n_tiles) fir_stage<T>(sm, 0, tile, tps, x, ns, taps, k0);
+    for (; tile < n_tiles; tile += gridDim.x, buf ^= 1) {
+        const int next = tile + gridDim.x;
+        if (next < n_tiles) {
+            fir_stage<T>(sm, buf ^ 1, next, tps, x, ns, taps, k0);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
+        __syncthreads();
+        for (int i = tid; i < 4 * T; i += kThreads) {
+            const float2 h = sm.hraw[buf][i];
+            const int q = i / (2 * T), p = (i / T) & 1, t = i % T;
+            sm.hA[q][p][t] = pk2(h.x, h.x);
+            sm.hB[q][p][t] = pk2(h.y, -h.y);
+        }
+        __syncthreads();
+
+        f32x2 acc[2][4];
 #pragma unroll
-        for (int j = 0; j <= D; ++j) {
-            const int te = 2 * j;
-            {
-                const float2 h0 = hs[0][p][te], h1 = hs[1][p][te];
+        for (int q = 0; q < 2; ++q)
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    acc[0][r].x = fmaf(h0.x, E[r].x, fmaf(-h0.y, E[r].y, acc[0][r].x));
-                    acc[0][r].y = fmaf(h0.x, E[r].y, fmaf(h0.y, E[r].x, acc[0][r].y));
-                    acc[1][r].x = fmaf(h1.x, E[r].x, fmaf(-h1.y, E[r].y, acc[1][r].x));
-                    acc[1][r].y = fmaf(h1.x, E[r].y, fmaf(h1.y, E[r].x, acc[1][r].y));
+            for (int r = 0; r < 4; ++r) acc[q][r] = pk2(0.f, 0.f);
+
+        const int lb = 8 * tid + 2 * D;   // local index of (r = 0, t = 0)
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const float2 *xp = sm.xs[buf][p];
+            // even / odd tap chains: E[r] = x[lb + 2r - 2j], O[r] = x[lb + 2r - 2j - 1],
+            // each kept as (xr, xi) and swapped (xi, xr)
+            f32x2 E[4], Es[4], O[4], Os[4];
+            auto ld = [&](int i, f32x2 &v, f32x2 &vs) {
+                const float2 a = xp[pad8(i)];
+                v = pk2(a.x, a.y);
+                vs = pk2(a.y, a.x);
+            };
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                ld(lb + 2 * r, E[r], Es[r]);
+                ld(lb + 2 * r - 1, O[r], Os[r]);
+            }
+#pragma unroll
+            for (int j = 0; j <= D; ++j) {
+                {
+                    const f32x2 a0 = sm.hA[0][p][2 * j], b0 = sm.hB[0][p][2 * j];
+                    const f32x2 a1 = sm.hA[1][p][2 * j], b1 = sm.hB[1][p][2 * j];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        acc[0][r] = fma2(b0, Es[r], fma2(a0, E[r], acc[0][r]));
+                        acc[1][r] = fma2(b1, Es[r], fma2(a1, E[r], acc[1][r]));
+                    }
+                }
+                if (j < D) {
+                    const f32x2 a0 = sm.hA[0][p][2 * j + 1], b0 = sm.hB[0][p][2 * j + 1];
+                    const f32x2 a1 = sm.hA[1][p][2 * j + 1], b1 = sm.hB[1][p][2 * j + 1];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        acc[0][r] = fma2(b0, Os[r], fma2(a0, O[r], acc[0][r]));
+                        acc[1][r] = fma2(b1, Os[r], fma2(a1, O[r], acc[1][r]));
+                    }
+                    // slide the windows by one output (two samples)
+#pragma unroll
+                    for (int r = 3; r > 0; --r) {
+                        E[r] = E[r - 1]; Es[r] = Es[r - 1];
+                        O[r] = O[r - 1]; Os[r] = Os[r - 1];
+                    }
+                    ld(lb - 2 * (j + 1), E[0], Es[0]);
+                    if (j + 1 < D) ld(lb - 2 * (j + 1) - 1, O[0], Os[0]);
                 }
             }
-            if (j < D) {
-                const int to = 2 * j + 1;
-                const float2 h0 = hs[0][p][to], h1 = hs[1][p][to];
+        }
+        const int s = tile / tps, tl = tile - s * tps;
+        const long kt = k0 + (long)tl * kOut + 4 * tid;
 #pragma unroll
-                for (int r = 0; r < 4; ++r) {
-                    acc[0][r].x = fmaf(h0.x, O[r].x, fmaf(-h0.y, O[r].y, acc[0][r].x));
-                    acc[0][r].y = fmaf(h0.x, O[r].y, fmaf(h0.y, O[r].x, acc[0][r].y));
-                    acc[1][r].x = fmaf(h1.x, O[r].x, fmaf(-h1.y, O[r].y, acc[1][r].x));
-                    acc[1][r].y = fmaf(h1.x, O[r].y, fmaf(h1.y, O[r].x, acc[1][r].y));
-                }
-                // slide the windows by one output (two samples)
+        for (int q = 0; q < 2; ++q) {
+            float2 *yq = y + ((long)s * 2 + q) * y_stride + y_off;
 #pragma unroll
-                for (int r = 3; r > 0; --r) { E[r] = E[r - 1]; O[r] = O[r - 1]; }
-                E[0] = xs[p][pad8(lb - 2 * (j + 1))];
-                if (j + 1 < D) O[0] = xs[p][pad8(lb - 2 * (j + 1) - 1)];
+            for (int r = 0; r < 4; ++r) {
+                float re, im;
+                upk2(acc[q][r], re, im);
+                if (kt + r < k1) yq[kt + r - k0] = make_float2(re, im);
             }
         }
+        __syncthreads();   // buffer `buf` is restaged two tiles later
     }
-    const long kt = kb + 4 * tid;
-#pragma unroll
-    for (int q = 0; q < 2; ++q) {
-        float2 *yq = y + ((long)s * 2 + q) * y_stride + y_off;
-#pragma unroll
-        for (int r = 0; r < 4; ++r)
-            if (kt + r < k1) yq[kt + r - k0] = acc[q][r];
+}
+
+int fir_blocks_per_sm() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
+        n = 4 * sms;
     }
+    return n;
 }
 
 }  // namespace
@@ -103,11 +168,14 @@ fir_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
 cudaError_t launch_fir(const float2 *x, long ns, const float2 *taps, long k0, long k1, float2 *y,
                        long y_stride, long y_off, int n_streams, int T, cudaStream_t st) {
     if (k1 <= k0 || n_streams <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((k1 - k0 + kOut - 1) / kOut), (unsigned)n_streams);
+    const long tps = (k1 - k0 + kOut - 1) / kOut;
+    const long n_tiles = tps * n_streams;
+    if (n_tiles > (1L << 30)) return cudaErrorInvalidValue;
+    const int grid = (int)std::min<long>(n_tiles, fir_blocks_per_sm());
     switch (T) {
-        case 7: fir_kernel<7><<<grid, kThreads, 0, st>>>(x, ns, taps, k0, k1, y, y_stride, y_off); break;
-        case 15: fir_kernel<15><<<grid, kThreads, 0, st>>>(x, ns, taps, k0, k1, y, y_stride, y_off); break;
-        case 31: fir_kernel<31><<<grid, kThreads, 0, st>>>(x, ns, taps, k0, k1, y, y_stride, y_off); break;
+        case 7: fir_kernel<7><<<grid, kThreads, 0, st>>>(x, ns, taps, k0, k1, y, y_stride, y_off, (int)tps, (int)n_tiles); break;
+        case 15: fir_kernel<15><<<grid, kThreads, 0, st>>>(x, ns, taps, k0, k1, y, y_stride, y_off, (int)tps, (int)n_tiles); break;
+        case 31: fir_kernel<31><<<grid, kThreads, 0, st>>>(x, ns, taps, k0, k1, y, y_stride, y_off, (int)tps, (int)n_tiles); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

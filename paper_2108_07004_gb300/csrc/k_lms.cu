@@ -112,6 +112,11 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
     __shared__ uint16_t pc[kCH];
     __shared__ uint8_t rl[kCH];
     __shared__ Tables tb;
+    // dynamic: exp(j phi_k) of the span (MODE 1, 3) and the data-aided
+    // targets d_q exp(j phi_k) (MODE 3), prepared by the whole block
+    extern __shared__ float2 dyn_sm[];
+    float2 *rots = dyn_sm;
+    float2 *tg0 = dyn_sm + kCH, *tg1 = dyn_sm + 2 * kCH;
     const int s = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p = lane >> 4, j = lane & 15;
@@ -151,6 +156,32 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
                     for (int t = 0; t < T; ++t)
                         acc = cadd(acc, cmulc(xs[pp][2 * kk + 2 * D - t], xs[pp][2 * kk + 2 + 2 * D - t]));
                 r1s[kk] = acc;
+                if (MODE != 0) {
+                    // exp(j phi_k) = cs_b j^qt
+                    const unsigned code = pc[kk];
+                    const int b = min((int)(code & 255), f.B - 1);
+                    const int qt = ((int)((code >> 8) & 3) * qt_step) & 3;
+                    float2 rot = tb.cs[b];
+                    if (qt & 2) rot = make_float2(-rot.x, -rot.y);
+                    if (qt & 1) rot = make_float2(-rot.y, rot.x);
+                    rots[kk] = rot;
+                    if (MODE == 3) {
+                        const int lab = rl[kk];
+                        float2 d0, d1;
+                        if (DIMS == 4) {
+                            const float4 pt = tb.pts[lab];
+                            d0 = make_float2(pt.x, pt.y);
+                            d1 = make_float2(pt.z, pt.w);
+                        } else {
+                            const float4 px = tb.pts[lab >> f.m_pol];
+                            const float4 py = tb.pts[lab & ((1 << f.m_pol) - 1)];
+                            d0 = make_float2(px.x, px.y);
+                            d1 = make_float2(py.x, py.y);
+                        }
+                        tg0[kk] = cmul(d0, rot);
+                        tg1[kk] = cmul(d1, rot);
+                    }
+                }
             }
             __syncthreads();
             if (warp != 0) continue;
@@ -169,6 +200,16 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
                 }
                 reduce_pair(a, c, p, b0, b1);
             };
+            // this lane's orbit (DD decisions): representative, energy, and
+            // the labels of its S rotations packed one per byte
+            const int o = lane & 15;
+            const bool valid = o < f.n_orb;
+            const float4 r = tb.orb[valid ? o : 0];
+            const float eo = tb.orbe[valid ? o : 0];
+            unsigned lab4 = 0;
+#pragma unroll
+            for (int k = 0; k < 4; ++k) lab4 |= (unsigned)(tb.orblab[valid ? o : 0][k] & 255) << (8 * k);
+            auto label_of = [&](int k) { return (int)((lab4 >> (8 * k)) & 255u); };
             float2 bc0, bc1, bn0 = make_float2(0.f, 0.f), bn1 = make_float2(0.f, 0.f);
             base(0, bc0, bc1);
             if (n > 1) base(1, bn0, bn1);
@@ -183,53 +224,32 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
                     const float g0 = f.R2 - cnorm(y0), g1 = f.R2 - cnorm(y1);
                     e0 = make_float2(g0 * y0.x, g0 * y0.y);
                     e1 = make_float2(g1 * y1.x, g1 * y1.y);
+                } else if (MODE == 3) {
+                    e0 = csub(tg0[kk], y0);
+                    e1 = csub(tg1[kk], y1);
                 } else {
-                    const unsigned code = pc[kk];
-                    const int b = min((int)(code & 255), f.B - 1);
-                    const int qt = (int)((code >> 8) & 3) * qt_step;
-                    float2 rot = tb.cs[b];                               // exp(j phi)
-                    for (int i = 0; i < qt; ++i) rot = make_float2(-rot.y, rot.x);
+                    const float2 rot = rots[kk];                               // exp(j phi)
                     float2 d0, d1;
-                    if (MODE == 3) {
-                        const int lab = rl[kk];
-                        if (DIMS == 4) {
-                            const float4 pt = tb.pts[lab];
-                            d0 = make_float2(pt.x, pt.y);
-                            d1 = make_float2(pt.z, pt.w);
-                        } else {
-                            const float4 px = tb.pts[lab >> f.m_pol];
-                            const float4 py = tb.pts[lab & ((1 << f.m_pol) - 1)];
-                            d0 = make_float2(px.x, px.y);
-                            d1 = make_float2(py.x, py.y);
-                        }
+                    const float2 z0 = cmulc(rot, y0), z1 = cmulc(rot, y1);   // y exp(-j phi)
+                    if (DIMS == 4) {
+                        const float P = (z0.x * r.x + z0.y * r.y) + (z1.x * r.z + z1.y * r.w);
+                        const float Q = (z0.y * r.x - z0.x * r.y) + (z1.y * r.z - z1.x * r.w);
+                        float v;
+                        int k;
+                        best_rot(P, Q, f.S, v, k);
+                        const float dist = (cnorm(z0) + cnorm(z1)) + (eo - 2.f * v);
+                        const float4 pt = tb.pts[argmin_label(dist, valid, label_of(k))];
+                        d0 = make_float2(pt.x, pt.y);
+                        d1 = make_float2(pt.z, pt.w);
                     } else {
-                        const float2 z0 = cmulc(rot, y0), z1 = cmulc(rot, y1);   // y exp(-j phi)
-                        const int o = lane & 15;
-                        const bool valid = o < f.n_orb;
-                        const float4 r = tb.orb[valid ? o : 0];
-                        if (DIMS == 4) {
-                            const float P = z0.x * r.x + z0.y * r.y + z1.x * r.z + z1.y * r.w;
-                            const float Q = z0.y * r.x - z0.x * r.y + z1.y * r.z - z1.x * r.w;
-                            float v;
-                            int k;
-                            best_rot(P, Q, f.S, v, k);
-                            const float dist = cnorm(z0) + cnorm(z1) + tb.orbe[valid ? o : 0] - 2.f * v;
-                            const float4 pt = tb.pts[argmin_label(dist, valid, tb.orblab[valid ? o : 0][k])];
-                            d0 = make_float2(pt.x, pt.y);
-                            d1 = make_float2(pt.z, pt.w);
-                        } else {
-                            float v0, v1;
-                            int k0r, k1r;
-                            best_rot(z0.x * r.x + z0.y * r.y, z0.y * r.x - z0.x * r.y, f.S, v0, k0r);
-                            best_rot(z1.x * r.x + z1.y * r.y, z1.y * r.x - z1.x * r.y, f.S, v1, k1r);
-                            const float eo = tb.orbe[valid ? o : 0];
-                            const float4 p0 = tb.pts[argmin_label(cnorm(z0) + eo - 2.f * v0, valid,
-                                                                  tb.orblab[valid ? o : 0][k0r])];
-                            const float4 p1 = tb.pts[argmin_label(cnorm(z1) + eo - 2.f * v1, valid,
-                                                                  tb.orblab[valid ? o : 0][k1r])];
-                            d0 = make_float2(p0.x, p0.y);
-                            d1 = make_float2(p1.x, p1.y);
-                        }
+                        float v0, v1;
+                        int k0r, k1r;
+                        best_rot(z0.x * r.x + z0.y * r.y, z0.y * r.x - z0.x * r.y, f.S, v0, k0r);
+                        best_rot(z1.x * r.x + z1.y * r.y, z1.y * r.x - z1.x * r.y, f.S, v1, k1r);
+                        const float4 p0 = tb.pts[argmin_label(cnorm(z0) + eo - 2.f * v0, valid, label_of(k0r))];
+                        const float4 p1 = tb.pts[argmin_label(cnorm(z1) + eo - 2.f * v1, valid, label_of(k1r))];
+                        d0 = make_float2(p0.x, p0.y);
+                        d1 = make_float2(p1.x, p1.y);
                     }
                     e0 = csub(cmul(d0, rot), y0);
                     e1 = csub(cmul(d1, rot), y1);

@@ -75,6 +75,7 @@ struct rx_handle {
     cudaStream_t st = nullptr;
     cudaStream_t side = nullptr;
     cudaEvent_t ev_unwrap = nullptr;
+    cudaEvent_t ev_cdc0 = nullptr, ev_start = nullptr;   // start-up overlap with the CDC
     std::vector<cudaEvent_t> ev_lms;
     // device tables
     float2 *H = nullptr, *tw = nullptr;
@@ -206,6 +207,7 @@ int build_format(const rx_format *f, FmtDev &d) {
         double pe = 0;
         for (int c = 0; c < dims; ++c) {
             d.pts[j][c] = pts[(size_t)j * dims + c];
+            d.ptsT[c][j] = d.pts[j][c];
             pe += (double)d.pts[j][c] * d.pts[j][c];
         }
         d.pe[j] = (float)pe;
@@ -332,12 +334,15 @@ int ensure_buffers(rx_handle *h, long N) {
 }
 
 int ensure_streams(rx_handle *h) {
-    if (h->lag >= 2 && !h->side) {
-        // the sequential adaptation runs on a high-priority stream
+    if (!h->side) {
+        // the sequential adaptation (start-up, and block updates for lag >= 2)
+        // runs on a high-priority stream
         int least = 0, greatest = 0;
         CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
         CK(cudaStreamCreateWithPriority(&h->side, cudaStreamNonBlocking, greatest));
         CK(cudaEventCreateWithFlags(&h->ev_unwrap, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_cdc0, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming));
     }
     while ((int)h->ev_lms.size() < h->lag + 1) {
         cudaEvent_t e;
@@ -446,27 +451,38 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     const int D = (T - 1) / 2;
 
     // CDC of the frames that these blocks (and, for b0 = 0, the start-up)
-    // read: output k of the FIR and the LMS reads samples 2k - D .. 2k + D
+    // read: output k of the FIR and the LMS reads samples 2k - D .. 2k + D.
+    // For b0 = 0 the start-up's frames go first; the start-up then runs on
+    // the side stream while the main stream filters the rest.
     {
-        long k_hi = std::min(b1 * Nb, N);
-        if (b0 == 0) k_hi = std::max(k_hi, std::min(N, std::max(h->n_pre, h->n_train)));
-        const long s_lo = std::max(0L, 2 * b0 * Nb - D), s_hi = std::min(ns, 2 * k_hi + D);
+        const long k_hi = std::min(b1 * Nb, N);
+        const long k_st = b0 == 0 ? std::min(N, std::max(h->n_pre, h->n_train)) : 0;
         const long Sk = h->n_fft - h->n_ov;
-        const long f0 = s_lo / Sk, f1 = (s_hi + Sk - 1) / Sk;
+        const long s_lo = std::max(0L, 2 * b0 * Nb - D);
+        const long f0 = s_lo / Sk;
+        const long f1 = (std::min(ns, 2 * std::max(k_hi, k_st) + D) + Sk - 1) / Sk;
+        const long fs = b0 == 0 ? std::min(f1, (std::min(ns, 2 * k_st + D) + Sk - 1) / Sk) : f0;
         h->ev_used = 0;
         h->recs.clear();
         h->blk.clear();
         for (auto &c : h->nlaunch) c = 0;
-        STAGE(ST_CDC, st, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st, f0, f1));
+        if (fs > f0) {
+            STAGE(ST_CDC, st, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st, f0, fs));
+            CK(cudaEventRecord(h->ev_cdc0, st));
+            CK(cudaStreamWaitEvent(h->side, h->ev_cdc0, 0));
+        }
+        if (f1 > fs)
+            STAGE(ST_CDC, st, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st, fs, f1));
     }
     if (b0 == 0) {
+        const cudaStream_t ss = h->side;     // start-up stream
         std::vector<float2> &cs = h->h_taps0;
         center_spike(h, cs);
         float2 *w0 = slot(h, 0);
-        CK(cudaMemcpyAsync(w0, cs.data(), tapsz, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(w0, cs.data(), tapsz, cudaMemcpyHostToDevice, ss));
         const long npre = std::min(h->n_pre, N);
-        STAGE(ST_STARTUP, st, 1, launch_lms(h->x, ns, w0, w0, 0, (int)npre, nullptr, 0, 0, h->cma_passes,
-                                            0, 0, (float)h->mu, nullptr, 0, S, T, f, st));
+        STAGE(ST_STARTUP, ss, 1, launch_lms(h->x, ns, w0, w0, 0, (int)npre, nullptr, 0, 0, h->cma_passes,
+                                            0, 0, (float)h->mu, nullptr, 0, S, T, f, ss));
         // stream state: counters zero, unwrap carry phi_hat = 0
         std::vector<StreamDev> &sd0 = h->h_sd0;
         sd0.assign(S, StreamDev{});
@@ -477,10 +493,12 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         h->trained = false;
         if (h->ref && ntr > 0 && h->ref_n >= ntr) {
             h->trained = true;
-            int rc2 = train_stage(h, h->x, ns, w0, ntr, h->pcode, N, nullptr, 0, st);
+            int rc2 = train_stage(h, h->x, ns, w0, ntr, h->pcode, N, nullptr, 0, ss);
             if (rc2 != RX_OK) return rc2;
         }
-        for (int i = 1; i <= L; ++i) CK(cudaMemcpyAsync(slot(h, i), w0, tapsz, cudaMemcpyDeviceToDevice, st));
+        for (int i = 1; i <= L; ++i) CK(cudaMemcpyAsync(slot(h, i), w0, tapsz, cudaMemcpyDeviceToDevice, ss));
+        CK(cudaEventRecord(h->ev_start, ss));
+        CK(cudaStreamWaitEvent(st, h->ev_start, 0));
         h->u = 0;
         h->blocks_done = 0;
         h->started = true;
@@ -707,6 +725,8 @@ void rx_destroy(rx_handle *h) {
     if (h->st) cudaStreamSynchronize(h->st);
     if (h->side) { cudaStreamSynchronize(h->side); cudaStreamDestroy(h->side); }
     if (h->ev_unwrap) cudaEventDestroy(h->ev_unwrap);
+    if (h->ev_cdc0) cudaEventDestroy(h->ev_cdc0);
+    if (h->ev_start) cudaEventDestroy(h->ev_start);
     for (auto e : h->ev_lms) cudaEventDestroy(e);
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     free_buffers(h);

@@ -24,6 +24,7 @@ struct __align__(16) FmtDev {
     int B;                // BPS test phases
     float R2;             // CMA radius E|s|^4 / E|s|^2 (per-polarisation marginal)
     float pts[RX_MAXM][4];      // label order: (xr, xi, yr, yi) or (re, im, -, -)
+    float ptsT[4][RX_MAXM];     // the same, component-major (labels j, j+1 adjacent: packed pairs)
     float pe[RX_MAXM];          // energy of each point
     float orb[RX_MAXM][4];      // orbit representatives
     float orbe[RX_MAXM];        // energy of each representative
@@ -32,6 +33,7 @@ struct __align__(16) FmtDev {
     float csp[RX_MAXB][4];      // (cos, cos, sin, sin) of phi_b, for packed pairs
 };
 static_assert(offsetof(FmtDev, csp) % 16 == 0, "packed phase table must be 16-byte aligned");
+static_assert(offsetof(FmtDev, ptsT) % 8 == 0, "packed point pairs must be 8-byte aligned");
 static_assert(alignof(FmtDev) == 16, "FmtDev alignment");
 
 // Per-stream device state.
@@ -73,6 +75,16 @@ __device__ __forceinline__ void upk2(f32x2 v, float &a, float &b) {
 __device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {   // a * b + c, per lane
     f32x2 d;
     asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 add2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
     return d;
 }
 __device__ __forceinline__ f32x2 mul2(f32x2 a, f32x2 b) {

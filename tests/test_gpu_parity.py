@@ -256,22 +256,31 @@ def test_demap_parity(case):
     assert np.all(err <= LLR_RTOL * np.maximum(1.0, np.abs(ref)))
 
 
-def test_demap_extreme_llrs():
-    """Far points: subset sums beyond the float range use their own shift."""
+@pytest.mark.parametrize("name", ["gs4d64", "dp_16qam", "dp_qpsk"])
+def test_demap_extreme_llrs(name):
+    """Subset sums beyond the float range of the common shift use their own
+    shift: every symbol extreme (small sigma^2), and a ragged length with
+    every 7th symbol at twice its amplitude, so that every warp mixes
+    extreme and ordinary lanes (and the last warp has lanes past the end)."""
     rx = _rx()
-    fmt = oracle_format("gs4d64")
+    fmt = oracle_format(name)
     rng = np.random.default_rng(5)
-    bits = rng.integers(0, 2, size=(512, 6), dtype=np.uint8)
-    z = fmt.symbols_from_bits(bits) + 0.02 * (rng.standard_normal((2, 512)) + 1j * rng.standard_normal((2, 512)))
-    z = z.astype(np.complex64)
-    r = rx.Receiver("gs4d64", taps=31, bps_phases=64)
-    for s2 in (1e-3, 3e-3):
-        llr = torch.zeros((1, 512, 6), dtype=torch.float32, device="cuda")
-        r.demap(_dev(z[None]), torch.tensor([s2], dtype=torch.float64, device="cuda"), llr)
-        ref = chain.llr(z.astype(np.complex128), s2, fmt)
+    n = 509
+    bits = rng.integers(0, 2, size=(n, fmt.m), dtype=np.uint8)
+    z = fmt.symbols_from_bits(bits) + 0.02 * (rng.standard_normal((2, n)) + 1j * rng.standard_normal((2, n)))
+    zf = z.copy()
+    zf[:, ::7] *= 2.0
+    kw = dict(taps=31, bps_phases=64) if fmt.dims == 4 else dict(taps=15, bps_phases=32)
+    r = rx.Receiver(name, **kw)
+    for zz, s2 in ((z, 1e-3), (z, 3e-3), (zf, 0.02)):
+        zz = zz.astype(np.complex64)
+        llr = torch.zeros((1, n, fmt.m), dtype=torch.float32, device="cuda")
+        r.demap(_dev(zz[None]), torch.tensor([s2], dtype=torch.float64, device="cuda"), llr)
+        ref = chain.llr(zz.astype(np.complex128), s2, fmt)
         g = llr[0].cpu().numpy().astype(np.float64)
-        assert np.abs(ref).max() > 300
-        assert np.all(np.abs(g - ref) <= LLR_RTOL * np.maximum(1.0, np.abs(ref)))
+        assert np.abs(ref).max() > 200          # past the common shift's range
+        bad = np.abs(g - ref) > LLR_RTOL * np.maximum(1.0, np.abs(ref))
+        assert not bad.any(), (s2, np.flatnonzero(bad.any(axis=1))[:10])
 
 
 def _segments(res, p, N):
