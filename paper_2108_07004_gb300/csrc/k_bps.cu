@@ -36,11 +36,6 @@ constexpr int kMaxR = 32 * (8 * kMaxRounds - 2);   // largest output range per b
 // Output symbols per block for `rounds` rounds of 8 chunks (one halo chunk on each side).
 __host__ __device__ __forceinline__ int range_of(int rounds) { return 32 * (8 * rounds - 2); }
 
-__device__ __forceinline__ int unwrap_step(int bprev, int b, int B) {
-    const int num = 2 * (bprev - b) + B;   // in [2 - B, 3B - 2]
-    return num < 0 ? -1 : (num >= 2 * B ? 1 : 0);
-}
-
 __device__ __forceinline__ float orbit_v(float P, float Q, int S) {
     if (S == 4) return fmaxf(fabsf(P), fabsf(Q));
     if (S == 2) return fabsf(P);

@@ -252,84 +252,79 @@ __device__ __forceinline__ bool llr_4d_stream(float2 z0, float2 z1, const FmtDev
     return low;
 }
 
+// Per-thread counting terms of the symbols one thread demapped.
+struct CountAcc {
+    int nerr = 0, ncnt = 0;
+    float gsum = 0.f, en = 0.f, ed = 0.f;
+};
+
+// LLRs of one symbol (z0, z1) into L[M_OUT] and its counting terms.  Every
+// lane of the warp calls it (inactive lanes on a valid symbol, writing
+// nothing), so the warp-wide rare path sees the whole warp.
 template <int DIMS, int MT, int MB>
-__global__ void __launch_bounds__(256, (DIMS == 4 ? 4 : 2))
-demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
-             const double *__restrict__ sigma2, int s2_stride, float *__restrict__ llr,
-             long llr_stride, DemapCount cnt, const __grid_constant__ FmtDev f) {
+__device__ __forceinline__ void demap_symbol(float2 z0, float2 z1, float c2, const FmtDev &f, bool active,
+                                             int ref, bool counted, float *row, CountAcc &acc) {
     constexpr int M_OUT = (DIMS == 4) ? MB : 2 * MB;
+    float L[M_OUT];
+    int ne = 0;
+    float gs = 0.f, dist_min, dmin_energy;
+    if (DIMS == 4) {
+        float g2;
+        const bool low = llr_4d_stream<MT, MB>(z0, z1, f, c2, L, dist_min, dmin_energy, ref, ne, g2);
+        const unsigned need = __ballot_sync(0xffffffffu, low && active);
+        if (need) llr_fixup_warp<4, MT, MB>(need, z0, z1, f, c2, L, ref, ne, g2);
+        gs = g2;
+    } else {
+        dist_min = 0.f;
+        dmin_energy = 0.f;
+#pragma unroll
+        for (int p = 0; p < 2; ++p) {
+            const float2 zp = p ? z1 : z0;
+            const int rp = ref < 0 ? -1 : (p ? (ref & ((1 << MB) - 1)) : (ref >> MB));
+            float g, g2;
+            int jm, nep;
+            const bool low = llr_table<2, MT, MB>(zp, zp, f, c2, L + p * MB, g, jm, rp, nep, g2);
+            const unsigned need = __ballot_sync(0xffffffffu, low && active);
+            if (need) llr_fixup_warp<2, MT, MB>(need, zp, zp, f, c2, L + p * MB, rp, nep, g2);
+            ne += nep;
+            gs += g2;
+            dist_min += g;
+            dmin_energy += f.pe[jm];
+        }
+    }
+    if (active) {
+#pragma unroll
+        for (int i = 0; i < M_OUT; ++i) row[i] = L[i];
+    }
+    if (counted) {
+        acc.nerr += ne;
+        acc.ncnt += 1;
+        acc.gsum += gs;
+        acc.en += dist_min;
+        acc.ed += dmin_energy;
+    }
+}
+
+// Block sums of the counting terms into this block's partial row, then the
+// last block of the stream (ticket) adds the rows in a fixed order (so the
+// totals do not depend on block timing) into the stream's accumulators.
+__device__ __forceinline__ void count_reduce(CountAcc acc, const DemapCount &cnt, int s, int cta, int n_cta,
+                                             double sigma2) {
     __shared__ float red[8][3];
     __shared__ int redn[8][2];
     __shared__ bool last;
-    const int s = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const long k = a + (long)blockIdx.x * blockDim.x + tid;
-    const float c2 = 1.4426950408889634f / (float)sigma2[s * s2_stride];
-    const float2 *zx = z + (long)s * 2 * z_stride;
-    const float2 *zy = zx + z_stride;
-    // per-thread counts in 32-bit / float (one symbol each); warp sums are
-    // widened to float64 before the block and grid reductions
-    int nerr = 0, ncnt = 0;
-    float gsum = 0.f, en = 0.f, ed = 0.f;
-    // every lane runs the lookup (lanes past the range on the last symbol)
-    // so that the warp-wide rare path sees the whole warp
-    const bool active = k < e;
-    const long kk = active ? k : e - 1;
-    {
-        const float2 z0 = zx[kk - a], z1 = zy[kk - a];
-        const bool counted = active && cnt.ref_lab && k >= cnt.c0 && k < cnt.c1;
-        const int ref = counted ? (int)cnt.ref_lab[(long)s * cnt.ref_stride + k] : -1;
-        float L[M_OUT];
-        int ne = 0;
-        float gs = 0.f, dist_min, dmin_energy;
-        if (DIMS == 4) {
-            float g2;
-            const bool low = llr_4d_stream<MT, MB>(z0, z1, f, c2, L, dist_min, dmin_energy, ref, ne, g2);
-            const unsigned need = __ballot_sync(0xffffffffu, low && active);
-            if (need) llr_fixup_warp<4, MT, MB>(need, z0, z1, f, c2, L, ref, ne, g2);
-            gs = g2;
-        } else {
-            dist_min = 0.f;
-            dmin_energy = 0.f;
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                const float2 zp = p ? z1 : z0;
-                const int rp = ref < 0 ? -1 : (p ? (ref & ((1 << MB) - 1)) : (ref >> MB));
-                float g, g2;
-                int jm, nep;
-                const bool low = llr_table<2, MT, MB>(zp, zp, f, c2, L + p * MB, g, jm, rp, nep, g2);
-                const unsigned need = __ballot_sync(0xffffffffu, low && active);
-                if (need) llr_fixup_warp<2, MT, MB>(need, zp, zp, f, c2, L + p * MB, rp, nep, g2);
-                ne += nep;
-                gs += g2;
-                dist_min += g;
-                dmin_energy += f.pe[jm];
-            }
-        }
-        if (active) {
-            float *row = llr + (long)s * llr_stride + (k - a) * M_OUT;
-#pragma unroll
-            for (int i = 0; i < M_OUT; ++i) row[i] = L[i];
-        }
-        if (counted) {
-            nerr = ne;
-            ncnt = 1;
-            gsum = gs;
-            en = dist_min;
-            ed = dmin_energy;
-        }
-    }
-    if (!cnt.sd) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-        nerr += __shfl_xor_sync(0xffffffffu, nerr, off);
-        ncnt += __shfl_xor_sync(0xffffffffu, ncnt, off);
-        gsum += __shfl_xor_sync(0xffffffffu, gsum, off);
-        en += __shfl_xor_sync(0xffffffffu, en, off);
-        ed += __shfl_xor_sync(0xffffffffu, ed, off);
+        acc.nerr += __shfl_xor_sync(0xffffffffu, acc.nerr, off);
+        acc.ncnt += __shfl_xor_sync(0xffffffffu, acc.ncnt, off);
+        acc.gsum += __shfl_xor_sync(0xffffffffu, acc.gsum, off);
+        acc.en += __shfl_xor_sync(0xffffffffu, acc.en, off);
+        acc.ed += __shfl_xor_sync(0xffffffffu, acc.ed, off);
     }
     if (lane == 0) {
-        red[warp][0] = gsum; red[warp][1] = en; red[warp][2] = ed;
-        redn[warp][0] = nerr; redn[warp][1] = ncnt;
+        red[warp][0] = acc.gsum; red[warp][1] = acc.en; red[warp][2] = acc.ed;
+        redn[warp][0] = acc.nerr; redn[warp][1] = acc.ncnt;
     }
     __syncthreads();
     if (tid == 0) {
@@ -339,22 +334,21 @@ demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
             t0 += red[w][0]; t1 += red[w][1]; t2 += red[w][2];
             n0 += redn[w][0]; n1 += redn[w][1];
         }
-        double *pp = cnt.partial + ((long)s * gridDim.x + blockIdx.x) * 5;
+        double *pp = cnt.partial + ((long)s * n_cta + cta) * 5;
         pp[0] = t0; pp[1] = t1; pp[2] = t2;
         pp[3] = (double)n0; pp[4] = (double)n1;
         __threadfence();
         const unsigned prev = atomicAdd(&cnt.sd[s].ticket_demap, 1u);
-        last = (prev == gridDim.x - 1);
+        last = (prev == (unsigned)n_cta - 1);
     }
     __syncthreads();
     if (!last) return;
-    // the last block of this stream adds the partials: strided per thread, then
-    // a fixed-order tree, so the sum does not depend on block timing
+    // strided per thread, then a fixed-order tree
     __threadfence();
-    const volatile double *pp = cnt.partial + (long)s * gridDim.x * 5;
+    const volatile double *pp = cnt.partial + (long)s * n_cta * 5;
     __shared__ double tr[5][256];
     double v[5] = {0, 0, 0, 0, 0};
-    for (unsigned c = tid; c < gridDim.x; c += blockDim.x)
+    for (int c = tid; c < n_cta; c += blockDim.x)
         for (int i = 0; i < 5; ++i) v[i] += pp[c * 5 + i];
     for (int i = 0; i < 5; ++i) tr[i][tid] = v[i];
     __syncthreads();
@@ -370,9 +364,169 @@ demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
         sd.evm_den += tr[2][0];
         sd.bit_errors += (unsigned long long)tr[3][0];
         sd.n_sym += (unsigned long long)tr[4][0];
-        sd.sigma2 = sigma2[s * s2_stride];
+        sd.sigma2 = sigma2;
         sd.ticket_demap = 0u;
     }
+}
+
+template <int DIMS, int MT, int MB>
+__global__ void __launch_bounds__(256, (DIMS == 4 ? 3 : 2))
+demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
+             const double *__restrict__ sigma2, int s2_stride, float *__restrict__ llr,
+             long llr_stride, DemapCount cnt, const __grid_constant__ FmtDev f) {
+    constexpr int M_OUT = (DIMS == 4) ? MB : 2 * MB;
+    const int s = blockIdx.y, tid = threadIdx.x;
+    const long k = a + (long)blockIdx.x * blockDim.x + tid;
+    const float c2 = 1.4426950408889634f / (float)sigma2[s * s2_stride];
+    const float2 *zx = z + (long)s * 2 * z_stride;
+    const float2 *zy = zx + z_stride;
+    const bool active = k < e;
+    const long kk = active ? k : e - 1;
+    const bool counted = active && cnt.ref_lab && k >= cnt.c0 && k < cnt.c1;
+    const int ref = counted ? (int)cnt.ref_lab[(long)s * cnt.ref_stride + k] : -1;
+    CountAcc acc;
+    demap_symbol<DIMS, MT, MB>(zx[kk - a], zy[kk - a], c2, f, active, ref, counted,
+                               llr + (long)s * llr_stride + (kk - a) * M_OUT, acc);
+    if (!cnt.sd) return;
+    count_reduce(acc, cnt, s, blockIdx.x, gridDim.x, sigma2[s * s2_stride]);
+}
+
+// ---------------------------------------------------------------------------
+// De-rotation fused with demapping (the chain's path).  A block takes a tile
+// of kTile consecutive symbols: the unwrap count m before the tile is the
+// stream carry plus the increments of the BPS ranges before it (dsum, and
+// the boundary increments) plus those of its own range up to the tile;
+// inside the tile a block scan gives m per symbol; then each symbol is
+// de-rotated by exp(-j (phi_b + m 2 pi / S)) and demapped in place.
+// ---------------------------------------------------------------------------
+constexpr int kTile = 1024;
+
+template <int DIMS, int MT, int MB>
+__global__ void __launch_bounds__(256, (DIMS == 4 ? 4 : 2))
+derot_demap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *__restrict__ bsrc,
+                   long b_stride, long a, long e, const int *__restrict__ dsum,
+                   const double *__restrict__ mdsum, int n_rng, int kR,
+                   const int32_t *__restrict__ carry_in, int cin_stride, int32_t *__restrict__ carry_out,
+                   int cout_stride, uint16_t *__restrict__ pcode, long pc_stride,
+                   const double *__restrict__ sigma2_fixed, double *__restrict__ sigma2_out, int s2_stride,
+                   float *__restrict__ llr, long llr_stride, DemapCount cnt, const __grid_constant__ FmtDev f) {
+    constexpr int M_OUT = (DIMS == 4) ? MB : 2 * MB;
+    constexpr int PT = kTile / 256;
+    __shared__ uint8_t bl[kTile];
+    __shared__ uint8_t mql[kTile];
+    __shared__ int wsum[8];
+    __shared__ int mstart_sh;
+    __shared__ float c2_sh;
+    __shared__ double s2_sh;
+    const int s = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int B = f.B, S = f.S;
+    const uint8_t *bs = bsrc + (long)s * b_stride;   // index k - a
+    const long t0 = a + (long)blockIdx.x * kTile;
+    const long t1 = min(t0 + kTile, e);
+    const int nloc = (int)(t1 - t0);
+    const int m_in = carry_in[s * cin_stride + 0], b_in = carry_in[s * cin_stride + 1];
+    const int r0 = (int)((t0 - a) / kR);              // BPS range holding the tile start
+    const long a_r0 = a + (long)r0 * kR;
+
+    // m before the tile: whole ranges before r0 (warp 0), then the part of
+    // range r0 before the tile (all threads)
+    int part = 0;
+    if (warp == 0) {
+        for (int r = lane; r < r0; r += 32) {
+            const long st0 = a + (long)r * kR;
+            const int bp = (r == 0) ? b_in : bs[st0 - 1 - a];
+            part += unwrap_step(bp, bs[st0 - a], B) + dsum[s * n_rng + r];
+        }
+    }
+    for (long k = a_r0 + tid; k < t0; k += 256)
+        part += unwrap_step(k == a ? b_in : bs[k - 1 - a], bs[k - a], B);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    if (lane == 0) wsum[warp] = part;
+    for (int t = tid; t < nloc; t += 256) bl[t] = bs[t0 - a + t];
+    if (tid == 32) {
+        double s2;
+        if (sigma2_fixed) {
+            s2 = sigma2_fixed[s * s2_stride];
+        } else {
+            double tot = 0.0;
+            for (int r = 0; r < n_rng; ++r) tot += mdsum[s * n_rng + r];   // fixed order
+            s2 = tot / (2.0 * (double)(e - a));
+        }
+        s2_sh = s2;
+        c2_sh = 1.4426950408889634f / (float)s2;
+        if (blockIdx.x == 0) sigma2_out[s * s2_stride] = s2;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int tot = 0;
+        for (int w = 0; w < 8; ++w) tot += wsum[w];
+        mstart_sh = m_in + tot;
+    }
+    const int bprev0 = (t0 == a) ? b_in : (int)bs[t0 - 1 - a];
+    // block scan of the tile's increments: thread t owns symbols PT t .. PT t + PT - 1
+    int d[PT], run = 0;
+    __syncthreads();
+#pragma unroll
+    for (int u = 0; u < PT; ++u) {
+        const int t = PT * tid + u;
+        int inc = 0;
+        if (t < nloc) inc = unwrap_step(t == 0 ? bprev0 : bl[t - 1], bl[t], B);
+        run += inc;
+        d[u] = run;
+    }
+    int incl = run;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += v;
+    }
+    __syncthreads();
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    int wpre = 0;
+    for (int w = 0; w < warp; ++w) wpre += wsum[w];
+    const int tpre = mstart_sh + wpre + incl - run;
+#pragma unroll
+    for (int u = 0; u < PT; ++u) {
+        const int t = PT * tid + u;
+        if (t >= nloc) continue;
+        const int m = tpre + d[u];
+        mql[t] = (uint8_t)(((m % S) + S) % S);
+        if (t0 + t == e - 1) {
+            carry_out[s * cout_stride + 0] = m;
+            carry_out[s * cout_stride + 1] = bl[t];
+        }
+    }
+    __syncthreads();
+    const float c2 = c2_sh;
+    const float2 *yx = y + (long)s * 2 * y_stride;
+    const float2 *yy = yx + y_stride;
+    uint16_t *pc = pcode + (long)s * pc_stride;
+    CountAcc acc;
+    for (int u = 0; u < PT; ++u) {
+        const int t = u * 256 + tid;
+        const bool active = t < nloc;
+        const int tt = active ? t : nloc - 1;
+        const long k = t0 + tt;
+        const int b = bl[tt], mq = mql[tt];
+        // exp(-j phi) = conj(cs_b) (-j)^mq
+        float2 rot = make_float2(f.cs[b][0], -f.cs[b][1]);
+        if (S == 4) {
+            if (mq & 2) rot = make_float2(-rot.x, -rot.y);
+            if (mq & 1) rot = make_float2(rot.y, -rot.x);
+        } else if (S == 2) {
+            if (mq) rot = make_float2(-rot.x, -rot.y);
+        }
+        const float2 z0 = cmul(yx[k], rot), z1 = cmul(yy[k], rot);
+        if (active) pc[k - a] = (uint16_t)(b | (mq << 8));
+        const bool counted = active && cnt.ref_lab && k >= cnt.c0 && k < cnt.c1;
+        const int ref = counted ? (int)cnt.ref_lab[(long)s * cnt.ref_stride + k] : -1;
+        demap_symbol<DIMS, MT, MB>(z0, z1, c2, f, active, ref, counted,
+                                   llr + (long)s * llr_stride + (k - a) * M_OUT, acc);
+    }
+    if (!cnt.sd) return;
+    count_reduce(acc, cnt, s, blockIdx.x, gridDim.x, s2_sh);
 }
 
 template <int DIMS, int MT, int MB>
@@ -383,7 +537,42 @@ cudaError_t demap_t(const float2 *z, long zs, long a, long e, const double *s2, 
     return cudaGetLastError();
 }
 
+template <int DIMS, int MT, int MB>
+cudaError_t derot_demap_t(const float2 *y, long ys, const uint8_t *b, long bst, long a, long e,
+                          const int *dsum, const double *mdsum, int kR, const int32_t *cin, int cis,
+                          int32_t *cout, int cos, uint16_t *pc, long pcs, const double *s2f, double *s2o,
+                          int s2s, float *llr, long ls, const DemapCount &cnt, int n_streams, const FmtDev &f,
+                          cudaStream_t st) {
+    const int n_rng = (int)((e - a + kR - 1) / kR);
+    dim3 grid((unsigned)((e - a + kTile - 1) / kTile), (unsigned)n_streams);
+    derot_demap_kernel<DIMS, MT, MB><<<grid, 256, 0, st>>>(y, ys, b, bst, a, e, dsum, mdsum, n_rng, kR, cin, cis,
+                                                           cout, cos, pc, pcs, s2f, s2o, s2s, llr, ls, cnt, f);
+    return cudaGetLastError();
+}
+
 }  // namespace
+
+long derot_demap_ctas(long len) { return (len + kTile - 1) / kTile; }
+
+cudaError_t launch_derot_demap(const float2 *y, long y_stride, const uint8_t *b, long b_stride,
+                               long a, long e, const int *dsum, const double *mdsum, int kR,
+                               const int32_t *carry_in, int cin_stride, int32_t *carry_out,
+                               int cout_stride, uint16_t *pcode, long pc_stride,
+                               const double *sigma2_fixed, double *sigma2_out, int s2_stride,
+                               float *llr, long llr_stride, const DemapCount &cnt, int n_streams,
+                               const FmtDev &f, cudaStream_t st) {
+    if (e <= a || n_streams <= 0) return cudaSuccess;
+    if (!cnt.sd || !cnt.partial || !mdsum) return cudaErrorInvalidValue;
+#define RX_DD(D_, M_, B_)                                                                                  \
+    return derot_demap_t<D_, M_, B_>(y, y_stride, b, b_stride, a, e, dsum, mdsum, kR, carry_in, cin_stride, \
+                                     carry_out, cout_stride, pcode, pc_stride, sigma2_fixed, sigma2_out,    \
+                                     s2_stride, llr, llr_stride, cnt, n_streams, f, st)
+    if (f.dims == 4 && f.M == 64) RX_DD(4, 64, 6);
+    if (f.dims == 2 && f.M == 4) RX_DD(2, 4, 2);
+    if (f.dims == 2 && f.M == 16) RX_DD(2, 16, 4);
+#undef RX_DD
+    return cudaErrorInvalidValue;
+}
 
 cudaError_t launch_demap(const float2 *z, long z_stride, long z_off, long a, long e,
                          const double *sigma2, int sigma2_stride, float *llr, long llr_stride,

@@ -99,7 +99,7 @@ __device__ __forceinline__ void reduce_pair(float2 a, float2 b, int p, float2 &y
 // scalar correction with r1_k = X_{k-1}^H X_k (precomputed by the whole block
 // for the staged span) is on the sequential path.
 template <int T, int DIMS, int MODE>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
 lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ taps_in,
            float2 *__restrict__ taps_out, long k0, int n_upd, const uint16_t *__restrict__ pcode,
            long pcode_stride, int passes, float mu, const uint8_t *__restrict__ ref_lab,
@@ -441,7 +441,7 @@ cudaError_t lms_launch_one(const float2 *x, long ns, const float2 *ti, float2 *t
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int dyn = optin - (int)fa.sharedSizeBytes;
-    if (dyn < 0) dyn = 0;
+    if (dyn < (int)(3 * kCH * sizeof(float2))) return cudaErrorInvalidValue;   // rotations, targets
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
     kern<<<S, 256, dyn, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, f);

@@ -84,7 +84,7 @@ struct rx_handle {
     // device buffers
     long cap_n = 0;
     int cap_s = 0, cap_lag = 0;
-    float2 *x = nullptr, *y = nullptr, *z = nullptr, *ring = nullptr;
+    float2 *x = nullptr, *y = nullptr, *ring = nullptr;
     uint8_t *bidx = nullptr;
     uint16_t *pcode = nullptr;
     int *dsum = nullptr;
@@ -292,12 +292,12 @@ int upload_tables(rx_handle *h) {
 }
 
 void free_buffers(rx_handle *h) {
-    cudaFree(h->x); cudaFree(h->y); cudaFree(h->z); cudaFree(h->ring);
+    cudaFree(h->x); cudaFree(h->y); cudaFree(h->ring);
     cudaFree(h->bidx); cudaFree(h->pcode); cudaFree(h->dsum); cudaFree(h->part_u);
     cudaFree(h->part_d); cudaFree(h->sig); cudaFree(h->sig_fixed); cudaFree(h->sd);
     cudaFree(h->mdsum);
     h->mdsum = nullptr;
-    h->x = h->y = h->z = h->ring = nullptr;
+    h->x = h->y = h->ring = nullptr;
     h->bidx = nullptr; h->pcode = nullptr; h->dsum = nullptr;
     h->part_u = h->part_d = h->sig = h->sig_fixed = nullptr;
     h->sd = nullptr;
@@ -313,7 +313,6 @@ int ensure_buffers(rx_handle *h, long N) {
     const long ncta_d = (h->block + 2 * h->W + 255) / 256 + 2;
     CK(cudaMalloc(&h->x, sizeof(float2) * (size_t)S * 2 * ns));
     CK(cudaMalloc(&h->y, sizeof(float2) * (size_t)S * 2 * N));
-    CK(cudaMalloc(&h->z, sizeof(float2) * (size_t)S * 2 * N));
     CK(cudaMalloc(&h->ring, sizeof(float2) * (size_t)(h->lag + 1) * S * 4 * h->T));
     CK(cudaMalloc(&h->bidx, (size_t)S * N));
     CK(cudaMalloc(&h->pcode, sizeof(uint16_t) * (size_t)S * N));
@@ -537,15 +536,13 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
             STAGE(ST_UNWRAP, st, 1, launch_anchor(h->bidx, N, h->pcode, N, (int)std::min(h->n_train, e),
                                                   carry_base, (int)sd_stride, S, h->B, f.S, st));
         }
-        STAGE(ST_UNWRAP, st, 1,
-              launch_unwrap(h->y, N, h->bidx, N, a, a, e, h->dsum, carry_base + 2 * cin,
-                            (int)sd_stride, carry_base + 2 * cout, (int)sd_stride, h->z, N, a,
-                            h->pcode, N, a, h->part_u, h->sig, 1,
-                            &h->sd[0].ticket_unwrap, (int)(sizeof(StreamDev) / sizeof(unsigned)),
-                            rounds, h->mdsum, S, f, st));
-        const double *s2 = h->sigma2_fixed > 0 ? h->sig_fixed : h->sig;
-        if ((e - a + 255) / 256 > h->cap_pd) return fail(RX_EINVAL, "internal: demap partials");
-        STAGE(ST_DEMAP, st, 1, launch_demap(h->z, N, a, a, e, s2, 1, llr + (size_t)a * m, N * m, cnt, S, f, st));
+        // unwrap, de-rotation, LLRs and counting in one pass over y (no z)
+        if (derot_demap_ctas(e - a) > h->cap_pd) return fail(RX_EINVAL, "internal: demap partials");
+        STAGE(ST_DEMAP, st, 1,
+              launch_derot_demap(h->y, N, h->bidx + a, N, a, e, h->dsum, h->mdsum, bps_cta_range(rounds),
+                                 carry_base + 2 * cin, (int)sd_stride, carry_base + 2 * cout, (int)sd_stride,
+                                 h->pcode + a, N, h->sigma2_fixed > 0 ? h->sig_fixed : nullptr, h->sig, 1,
+                                 llr + (size_t)a * m, N * m, cnt, S, f, st));
         if (blk0) {
             cudaEvent_t blk1 = prof_event(h);
             if (blk1) { CK(cudaEventRecord(blk1, st)); h->blk.push_back({blk0, blk1}); }

@@ -62,6 +62,14 @@ __host__ __device__ __forceinline__ float2 cmulc(float2 a, float2 b) {
 }
 __host__ __device__ __forceinline__ float cnorm(float2 a) { return a.x * a.x + a.y * a.y; }
 
+// Unwrap increment between consecutive phase indices (integer form of
+// phi_hat_k = phi_k + q round((phi_hat_{k-1} - phi_k) / q), round(x) = floor(x + 1/2)):
+// floor((2 (b_{k-1} - b_k) + B) / (2B)).
+__device__ __forceinline__ int unwrap_step(int bprev, int b, int B) {
+    const int num = 2 * (bprev - b) + B;   // in [2 - B, 3B - 2]
+    return num < 0 ? -1 : (num >= 2 * B ? 1 : 0);
+}
+
 // ---- packed float pairs (sm_100+ f32x2 arithmetic) ---------------------------
 typedef unsigned long long f32x2;
 __device__ __forceinline__ f32x2 pk2(float a, float b) {
@@ -158,6 +166,22 @@ struct DemapCount {
     StreamDev *sd;            // per-stream accumulators (or null)
     double *partial;          // [S][n_cta][3] scratch
 };
+
+// De-rotation by the unwrapped phase fused with the LLRs and counting, for
+// the chain: reads the equaliser output y and the BPS indices b (index k - a)
+// with BPS's per-range increment sums dsum and minimum-distance sums mdsum
+// ([S][n_cta], ranges of kR symbols), writes the phase codes and the LLRs;
+// sigma^2 = sum(mdsum) / (2 (e - a)) unless sigma2_fixed is given.  The
+// block's sigma^2 goes to sigma2_out[s * s2_stride].  No z is written.
+cudaError_t launch_derot_demap(const float2 *y, long y_stride, const uint8_t *b, long b_stride,
+                               long a, long e, const int *dsum, const double *mdsum, int kR,
+                               const int32_t *carry_in, int cin_stride, int32_t *carry_out,
+                               int cout_stride, uint16_t *pcode, long pc_stride,
+                               const double *sigma2_fixed, double *sigma2_out, int s2_stride,
+                               float *llr, long llr_stride, const DemapCount &cnt, int n_streams,
+                               const FmtDev &f, cudaStream_t st);
+// number of partial-sum rows launch_derot_demap needs per stream
+long derot_demap_ctas(long len);
 
 cudaError_t launch_demap(const float2 *z, long z_stride, long z_off, long a, long e,
                          const double *sigma2, int sigma2_stride, float *llr,
