@@ -39,6 +39,25 @@ WL = dict(workload="gs4d64_1000km_esn0_8to16dB", fmt="gs4d64", n_sym=1 << 20,
           bps_window=64, block=1 << 16, n_upd=1024, lag=2, mu=1e-3, n_pre=2048,
           cma_passes=1, n_cma=0, n_train=1024, train_passes=3, skip_head=16384, skip_tail=512)
 FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070.0
+# DRAM bytes (read + write) of one bps_kernel launch at this workload's launch
+# size (9 streams x one 2^16-symbol block), from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum); reported only while the
+# kernel's sources hash to the captured ones.
+BPS_TRAFFIC = {"bytes": 9458944, "sources": {
+    "paper_2108_07004_gb300/csrc/k_bps.cu": "51ab10792169d4658929fc0bd772569fc128f5de360d1c59a50dbe4a6c4ca03b",
+    "paper_2108_07004_gb300/csrc/rx_internal.h": "7fb9c4bff840179a2618566e2b65b21fe96654107dacbb9f17937a27000482e7"}}
+
+
+def bps_traffic():
+    import hashlib
+    for rel, want in BPS_TRAFFIC["sources"].items():
+        try:
+            with open(os.path.join(ROOT, rel), "rb") as f:
+                if hashlib.sha256(f.read()).hexdigest() != want:
+                    return None
+        except OSError:
+            return None
+    return BPS_TRAFFIC["bytes"]
 
 
 def peaks():
@@ -289,7 +308,7 @@ def run_ours(args):
                     "blocks_per_step": len(lat)},
         "roofline": {"bound": "alu", "kernel": "bps", "achieved": achieved, "peak": peak_ops,
                      "unit": "Top/s", "frac": (achieved / peak_ops) if achieved else None,
-                     "traffic": None,
+                     "traffic": bps_traffic() if n_sym == WL["n_sym"] and S == 9 else None,
                      "op": "one (test phase, constellation point) candidate distance",
                      "peak_from": "128 FP32 lanes x 152 SMs x 2070 MHz"},
         "stages_ms": {k: v[0] for k, v in stage.items()},

@@ -438,24 +438,27 @@ derot_demap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *_
             part += unwrap_step(bp, bs[st0 - a], B) + dsum[s * n_rng + r];
         }
     }
+#pragma unroll 4
     for (long k = a_r0 + tid; k < t0; k += 256)
         part += unwrap_step(k == a ? b_in : bs[k - 1 - a], bs[k - a], B);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
     if (lane == 0) wsum[warp] = part;
     for (int t = tid; t < nloc; t += 256) bl[t] = bs[t0 - a + t];
-    if (tid == 32) {
-        double s2;
-        if (sigma2_fixed) {
-            s2 = sigma2_fixed[s * s2_stride];
-        } else {
-            double tot = 0.0;
-            for (int r = 0; r < n_rng; ++r) tot += mdsum[s * n_rng + r];   // fixed order
-            s2 = tot / (2.0 * (double)(e - a));
+    if (warp == 1) {
+        // the block's sigma^2: warp sum of the ranges' minimum-distance sums
+        // (lane-strided, then a butterfly: the same order in every block)
+        double tot = 0.0;
+        if (!sigma2_fixed)
+            for (int r = lane; r < n_rng; r += 32) tot += mdsum[s * n_rng + r];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) tot += __shfl_xor_sync(0xffffffffu, tot, off);
+        if (lane == 0) {
+            const double s2 = sigma2_fixed ? sigma2_fixed[s * s2_stride] : tot / (2.0 * (double)(e - a));
+            s2_sh = s2;
+            c2_sh = 1.4426950408889634f / (float)s2;
+            if (blockIdx.x == 0) sigma2_out[s * s2_stride] = s2;
         }
-        s2_sh = s2;
-        c2_sh = 1.4426950408889634f / (float)s2;
-        if (blockIdx.x == 0) sigma2_out[s * s2_stride] = s2;
     }
     __syncthreads();
     if (tid == 0) {
