@@ -14,7 +14,10 @@ is silent, the reading taken is stated in the docstring.
 Parity status: every function here is pinned by a ``-m "not gpu"`` test in
 ``tests/test_oracle_*.py`` against a closed form, an invariant, a physics
 fact or brute force, except ``gs4d64`` table design (the authors' own
-constellation is not printed: parity with it is unpinned).
+constellation is not printed: parity with it is unpinned).  ``mlp`` is the
+learned demapper (forward, BCE, backward, Adam), pinned by identities,
+finite differences and closed forms.
 """
 from .formats import OracleFormat, oracle_format  # noqa: F401
 from . import chain  # noqa: F401
+from . import mlp  # noqa: F401
