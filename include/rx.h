@@ -234,6 +234,42 @@ int rx_get_state(rx_handle *h, void *buf, size_t *len);
  * of a state).  Synchronises. */
 int rx_set_state(rx_handle *h, const void *buf, size_t len);
 
+/* ---- learned demapper -------------------------------------------------- */
+
+/* An MLP 4 -> 128 -> 128 -> 6 (GELU) as a learned alternative to the exact
+ * log-sum-exp demapper (the paper designs its constellations with the GMI of
+ * exact bitwise demapping, Sec. 5; the learned form is judged by its GMI gap
+ * to it).  Input x = (Re z_X, Im z_X, Re z_Y, Im z_Y) of a de-rotated 4D
+ * symbol; output o = sigma^2 * LLR (LLR > 0 means bit 0, MSB first), so
+ * LLR = o / sigma^2 with the block's noise variance.  Layers compute with
+ * bfloat16-rounded weights (round to nearest even) of float32 master
+ * weights, float32 activations and accumulation; training minimises the mean
+ * binary cross-entropy over the bits with Adam (beta 0.9 / 0.999, eps 1e-8).
+ * Parameters, float32, in this order: W1 [128][4], b1 [128], W2 [128][128],
+ * b2 [128], W3 [6][128], b3 [6].  Device buffers below: x [n][4] float32,
+ * sigma2 [n] float32, bits [n][6] uint8 (0/1), llr [n][6] float32.  Work
+ * goes on the MLP's stream (rx_mlp_set_stream).  Batch reductions are in a
+ * fixed order: results do not depend on timing. */
+#define RX_MLP_PARAMS 17926
+typedef struct rx_mlp rx_mlp;
+/* params: host [RX_MLP_PARAMS] float32, copied; NULL gives zeros.  NULL on error. */
+rx_mlp *rx_mlp_create(const float *params);
+void rx_mlp_destroy(rx_mlp *m);                     /* NULL-safe */
+int rx_mlp_set_stream(rx_mlp *m, void *cuda_stream);
+/* float32 master parameters to / from host memory; setting resets Adam. */
+int rx_mlp_get_params(rx_mlp *m, float *params);
+int rx_mlp_set_params(rx_mlp *m, const float *params);
+/* Gradient of the mean BCE over a batch of n samples into grad (device
+ * [RX_MLP_PARAMS]) and the loss into loss (device [1], may be NULL). */
+int rx_mlp_grad(rx_mlp *m, const float *x, const float *sigma2, const uint8_t *bits, size_t n,
+                float *grad, float *loss);
+/* One Adam step on a batch of n samples with learning rate lr; the batch's
+ * loss (before the step) into loss (device [1], may be NULL). */
+int rx_mlp_train_step(rx_mlp *m, const float *x, const float *sigma2, const uint8_t *bits,
+                      size_t n, float lr, float *loss);
+/* LLRs of n samples. */
+int rx_mlp_infer(rx_mlp *m, const float *x, const float *sigma2, size_t n, float *llr);
+
 /* Format facts: dims, m (bits per 4D symbol), M (table size). */
 int rx_format_info(const rx_handle *h, int *dims, int *m, int *M);
 

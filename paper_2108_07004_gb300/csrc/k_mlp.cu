@@ -1,0 +1,358 @@
+// Learned demapper: MLP 4 -> 128 -> 128 -> 6 with GELU, bfloat16 weights,
+// float32 activations and accumulation.  Input: the de-rotated 4D symbol
+// (Re z_X, Im z_X, Re z_Y, Im z_Y); output o = sigma^2 * LLR (LLR > 0 means
+// bit 0), trained with the mean binary cross-entropy over the bits and Adam.
+//
+// Kernels (batch of n samples):
+//   layer1_kernel      a1 = x W1^T + b1, h1 = gelu(a1)
+//   gemm_kernel        tiled float32 GEMM (64 x 64 tiles, 4 x 4 per thread)
+//                      with bfloat16 weight operands and fused epilogues:
+//                      a2 = h1 W2^T + b2 -> h2 = gelu(a2); dh1 = da2 W2 ->
+//                      da1 = dh1 gelu'(a1); dW2 = da2^T h1 over batch slices
+//   layer3_loss_kernel o = h2 W3^T + b3, LLR = o / sigma^2, BCE terms and
+//                      d loss / d o per sample
+//   back3_kernel       dh2 = do W3, da2 = dh2 gelu'(a2)
+//   colsum kernels     the batch reductions (dW1, dW3, biases, loss) in a
+//                      fixed order: per-block partials, then one pass
+//   adam_kernel        Adam on the float32 master weights, then the
+//                      bfloat16 copies the layers use
+// Every reduction over the batch is in a fixed order, so a step gives the
+// same bits on every run.
+#include <cmath>
+
+#include "rx_internal.h"
+
+namespace {
+
+constexpr int H = 128;
+constexpr int NOUT = 6;
+
+__device__ __forceinline__ float bf16_to_f(uint16_t b) { return __uint_as_float((unsigned)b << 16); }
+
+__device__ __forceinline__ uint16_t f_to_bf16(float f) {   // round to nearest, ties to even
+    const unsigned u = __float_as_uint(f);
+    return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+
+__device__ __forceinline__ float gelu(float a) { return 0.5f * a * (1.f + erff(a * 0.70710678118654752f)); }
+
+__device__ __forceinline__ float gelu_grad(float a) {
+    return 0.5f * (1.f + erff(a * 0.70710678118654752f)) + a * expf(-0.5f * a * a) * 0.39894228040143268f;
+}
+
+__device__ __forceinline__ float softplus(float t) { return fmaxf(t, 0.f) + log1pf(expf(-fabsf(t))); }
+__device__ __forceinline__ float sigmoid(float t) { return 1.f / (1.f + expf(-t)); }
+
+// a1, h1 [n][H]
+__global__ void layer1_kernel(const float *__restrict__ x, long n, const uint16_t *__restrict__ W1,
+                              const float *__restrict__ b1, float *__restrict__ a1, float *__restrict__ h1) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * H) return;
+    const long s = i / H;
+    const int j = (int)(i - s * H);
+    float a = b1[j];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) a = fmaf(x[s * 4 + c], bf16_to_f(W1[j * 4 + c]), a);
+    a1[i] = a;
+    h1[i] = gelu(a);
+}
+
+// C[M][N] (+)= op(A) op(B): A float32 (row-major [M][K], or [K][M] when TA),
+// B bfloat16 or float32 ([N][K] when TB, else [K][N]).  Epilogues:
+//   EPI_BIAS_GELU: pre = C + bias[n] -> out0 = pre, out1 = gelu(pre)
+//   EPI_GELU_GRAD: out0 = C * gelu'(aux[m][n])
+//   EPI_STORE:     out0 = C
+enum { EPI_BIAS_GELU = 0, EPI_GELU_GRAD = 1, EPI_STORE = 2 };
+constexpr int TM = 64, TN = 64, TK = 16;
+
+template <bool TA, bool TB, bool BBF, int EPI>
+__global__ void __launch_bounds__(256)
+gemm_kernel(int M, int N, int K, const float *__restrict__ A, int lda, const void *__restrict__ Bv, int ldb,
+            const float *__restrict__ bias, const float *__restrict__ aux, int ldaux, float *__restrict__ out0,
+            float *__restrict__ out1, int ldo, long k_slice, long out_slice_stride) {
+    __shared__ float As[TK][TM + 4];
+    __shared__ float Bs[TK][TN + 4];
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int m0 = blockIdx.y * TM, n0 = blockIdx.x * TN;
+    // batch slice (split K) of this block
+    const long kb = (long)blockIdx.z * k_slice, ke = min((long)K, kb + k_slice);
+    float acc[4][4] = {};
+    for (long k0 = kb; k0 < ke; k0 += TK) {
+        for (int i = tid; i < TK * TM; i += 256) {
+            const int kk = i / TM, mm = i - kk * TM;
+            const long k = k0 + kk;
+            const int m = m0 + mm;
+            float v = 0.f;
+            if (k < ke && m < M) v = TA ? A[k * lda + m] : A[(long)m * lda + k];
+            As[kk][mm] = v;
+        }
+        for (int i = tid; i < TK * TN; i += 256) {
+            const int kk = i / TN, nn = i - kk * TN;
+            const long k = k0 + kk;
+            const int nidx = n0 + nn;
+            float v = 0.f;
+            if (k < ke && nidx < N) {
+                const long off = TB ? (long)nidx * ldb + k : k * ldb + nidx;
+                v = BBF ? bf16_to_f(static_cast<const uint16_t *>(Bv)[off]) : static_cast<const float *>(Bv)[off];
+            }
+            Bs[kk][nn] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < TK; ++kk) {
+            float a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[kk][ty * 4 + r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[kk][tx * 4 + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+    float *o0 = out0 + (long)blockIdx.z * out_slice_stride;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int m = m0 + ty * 4 + r;
+        if (m >= M) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int nidx = n0 + tx * 4 + c;
+            if (nidx >= N) continue;
+            const long o = (long)m * ldo + nidx;
+            if (EPI == EPI_BIAS_GELU) {
+                const float pre = acc[r][c] + bias[nidx];
+                o0[o] = pre;
+                out1[o] = gelu(pre);
+            } else if (EPI == EPI_GELU_GRAD) {
+                o0[o] = acc[r][c] * gelu_grad(aux[(long)m * ldaux + nidx]);
+            } else {
+                o0[o] = acc[r][c];
+            }
+        }
+    }
+}
+
+// o = h2 W3^T + b3; LLR = o / sigma^2; per sample: sum of BCE terms and
+// d loss / d o (mean over n x 6 bits), and (inference) the LLRs
+__global__ void __launch_bounds__(128)
+layer3_kernel(const float *__restrict__ h2, long n, const uint16_t *__restrict__ W3, const float *__restrict__ b3,
+              const float *__restrict__ sigma2, const uint8_t *__restrict__ bits, float *__restrict__ dO,
+              float *__restrict__ loss_s, float *__restrict__ llr) {
+    __shared__ float w[NOUT][H];
+    for (int i = threadIdx.x; i < NOUT * H; i += blockDim.x) w[i / H][i % H] = bf16_to_f(W3[i]);
+    __syncthreads();
+    const long s = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= n) return;
+    float o[NOUT];
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) o[k] = b3[k];
+    const float *hs = h2 + s * H;
+    for (int j = 0; j < H; ++j) {
+        const float v = hs[j];
+#pragma unroll
+        for (int k = 0; k < NOUT; ++k) o[k] = fmaf(v, w[k][j], o[k]);
+    }
+    const float inv = 1.f / sigma2[s];
+    const float scale = 1.f / (float)(n * NOUT);
+    float ls = 0.f;
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) {
+        const float L = o[k] * inv;
+        if (llr) llr[s * NOUT + k] = L;
+        if (bits) {
+            const float sg = bits[s * NOUT + k] ? -1.f : 1.f;     // +1 for bit 0
+            ls += softplus(-sg * L);
+            dO[s * NOUT + k] = -sg * sigmoid(-sg * L) * scale * inv;
+        }
+    }
+    if (bits) loss_s[s] = ls * scale;
+}
+
+// da2[s][j] = (sum_k dO[s][k] W3[k][j]) * gelu'(a2[s][j])
+__global__ void back3_kernel(const float *__restrict__ dO, long n, const uint16_t *__restrict__ W3,
+                             const float *__restrict__ a2, float *__restrict__ da2) {
+    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n * H) return;
+    const long s = i / H;
+    const int j = (int)(i - s * H);
+    float v = 0.f;
+#pragma unroll
+    for (int k = 0; k < NOUT; ++k) v = fmaf(dO[s * NOUT + k], bf16_to_f(W3[k * H + j]), v);
+    da2[i] = v * gelu_grad(a2[i]);
+}
+
+// column sums over the batch in a fixed order: out[c] = sum_s f(s, c) for
+// C columns, where f is src[s][c] (src2 == null) or src[s][c] * src2[s][c2]
+// (outer product column c = (c1, c2) with c1 < C1 over src, c2 < C2 over src2).
+// Block b sums rows b*rows .. (b+1)*rows - 1 into part[b][c]; a second launch
+// (one block per 256 columns) adds the blocks in order.
+__global__ void colsum_partial_kernel(const float *__restrict__ src, int ld, const float *__restrict__ src2,
+                                      int ld2, int C1, int C2, long n, long rows, float *__restrict__ part) {
+    const int C = src2 ? C1 * C2 : C1;
+    const long s0 = (long)blockIdx.y * rows, s1 = min(n, s0 + rows);
+    for (int c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+        const int c1 = src2 ? c / C2 : c, c2 = src2 ? c - (c / C2) * C2 : 0;
+        float acc = 0.f;
+        for (long s = s0; s < s1; ++s) {
+            float v = src[s * ld + c1];
+            if (src2) v *= src2[s * ld2 + c2];
+            acc += v;
+        }
+        part[(long)blockIdx.y * C + c] = acc;
+    }
+}
+
+__global__ void colsum_final_kernel(const float *__restrict__ part, int nb, int C, float *__restrict__ out) {
+    const int c = blockIdx.x * blockDim.x + threadIdx.x;
+    if (c >= C) return;
+    float acc = 0.f;
+    for (int b = 0; b < nb; ++b) acc += part[(long)b * C + c];
+    out[c] = acc;
+}
+
+// Adam on the float32 masters, then the bfloat16 copies of the weights
+__global__ void adam_kernel(float *__restrict__ theta, float *__restrict__ m, float *__restrict__ v,
+                            const float *__restrict__ g, int np, float lr, float b1, float b2, float eps,
+                            float bc1, float bc2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    theta[i] -= lr * (mi / bc1) / (sqrtf(vi / bc2) + eps);
+}
+
+__global__ void quantize_kernel(const float *__restrict__ theta, int off, int cnt, uint16_t *__restrict__ q) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < cnt) q[i] = f_to_bf16(theta[off + i]);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace {
+constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + H * 4, OFF_W2 = OFF_B1 + H, OFF_B2 = OFF_W2 + H * H;
+constexpr int OFF_W3 = OFF_B2 + H, OFF_B3 = OFF_W3 + NOUT * H, NPAR = OFF_B3 + NOUT;
+static_assert(NPAR == RX_MLP_PARAMS, "parameter count");
+constexpr long kRows = 256;          // batch rows per partial-sum block
+}  // namespace
+
+static cudaError_t mlp_ensure(MlpDev &d, long n) {
+    if (d.cap >= n) return cudaSuccess;
+    float **bufs[] = {&d.a1, &d.h1, &d.a2, &d.h2, &d.da2, &d.da1};
+    for (float **b : bufs) { cudaFree(*b); *b = nullptr; }
+    cudaFree(d.dO); cudaFree(d.loss_s); cudaFree(d.part); cudaFree(d.wpart);
+    d.dO = d.loss_s = d.part = d.wpart = nullptr;
+    cudaError_t e;
+    for (float **b : bufs)
+        if ((e = cudaMalloc(b, sizeof(float) * (size_t)n * H)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&d.dO, sizeof(float) * (size_t)n * NOUT)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&d.loss_s, sizeof(float) * (size_t)n)) != cudaSuccess) return e;
+    const long nb = (n + kRows - 1) / kRows;
+    // column-sum partials: the widest is dW1 (H x 4) / biases (H) / dW3 (6 x H)
+    if ((e = cudaMalloc(&d.part, sizeof(float) * (size_t)nb * H * 8)) != cudaSuccess) return e;
+    // dW2 over batch slices of kRows * 8 samples
+    const long ns = (n + kRows * 8 - 1) / (kRows * 8);
+    if ((e = cudaMalloc(&d.wpart, sizeof(float) * (size_t)ns * H * H)) != cudaSuccess) return e;
+    d.cap = n;
+    return cudaSuccess;
+}
+
+cudaError_t mlp_alloc(MlpDev &d) {
+    cudaError_t e;
+    float **p[] = {&d.theta, &d.m, &d.v, &d.grad};
+    for (float **b : p) {
+        if ((e = cudaMalloc(b, sizeof(float) * NPAR)) != cudaSuccess) return e;
+        if ((e = cudaMemset(*b, 0, sizeof(float) * NPAR)) != cudaSuccess) return e;
+    }
+    if ((e = cudaMalloc(&d.W1q, sizeof(uint16_t) * H * 4)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&d.W2q, sizeof(uint16_t) * H * H)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&d.W3q, sizeof(uint16_t) * NOUT * H)) != cudaSuccess) return e;
+    return cudaSuccess;
+}
+
+void mlp_free(MlpDev &d) {
+    float *bufs[] = {d.theta, d.m, d.v, d.grad, d.a1, d.h1, d.a2, d.h2, d.dO, d.da2, d.da1, d.loss_s, d.part, d.wpart};
+    for (float *b : bufs) cudaFree(b);
+    cudaFree(d.W1q); cudaFree(d.W2q); cudaFree(d.W3q);
+    d = MlpDev{};
+}
+
+cudaError_t mlp_quantize(MlpDev &d, cudaStream_t st) {
+    quantize_kernel<<<(H * 4 + 255) / 256, 256, 0, st>>>(d.theta, OFF_W1, H * 4, d.W1q);
+    quantize_kernel<<<(H * H + 255) / 256, 256, 0, st>>>(d.theta, OFF_W2, H * H, d.W2q);
+    quantize_kernel<<<(NOUT * H + 255) / 256, 256, 0, st>>>(d.theta, OFF_W3, NOUT * H, d.W3q);
+    return cudaGetLastError();
+}
+
+static cudaError_t colsum(MlpDev &d, const float *src, int ld, const float *src2, int ld2, int C1, int C2,
+                          long n, float *out, cudaStream_t st) {
+    const int C = src2 ? C1 * C2 : C1;
+    const long nb = (n + kRows - 1) / kRows;
+    dim3 g((unsigned)((C + 255) / 256), (unsigned)nb);
+    colsum_partial_kernel<<<g, 256, 0, st>>>(src, ld, src2, ld2, C1, C2, n, kRows, d.part);
+    colsum_final_kernel<<<(C + 255) / 256, 256, 0, st>>>(d.part, (int)nb, C, out);
+    return cudaGetLastError();
+}
+
+// forward (and, with bits, the loss terms and d loss / d o)
+static cudaError_t mlp_forward(MlpDev &d, const float *x, const float *s2, const uint8_t *bits, long n,
+                               float *llr, cudaStream_t st) {
+    cudaError_t e = mlp_ensure(d, n);
+    if (e != cudaSuccess) return e;
+    layer1_kernel<<<(unsigned)((n * H + 255) / 256), 256, 0, st>>>(x, n, d.W1q, d.theta + OFF_B1, d.a1, d.h1);
+    dim3 g2(H / TN, (unsigned)((n + TM - 1) / TM), 1);
+    gemm_kernel<false, true, true, EPI_BIAS_GELU><<<g2, 256, 0, st>>>(
+        (int)n, H, H, d.h1, H, d.W2q, H, d.theta + OFF_B2, nullptr, 0, d.a2, d.h2, H, H, 0);
+    layer3_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d.h2, n, d.W3q, d.theta + OFF_B3, s2, bits, d.dO,
+                                                              d.loss_s, llr);
+    return cudaGetLastError();
+}
+
+// gradient of the mean BCE into d.grad (and the loss into loss[0])
+cudaError_t mlp_grad(MlpDev &d, const float *x, const float *s2, const uint8_t *bits, long n, float *loss,
+                     cudaStream_t st) {
+    cudaError_t e = mlp_forward(d, x, s2, bits, n, nullptr, st);
+    if (e != cudaSuccess) return e;
+    float *g = d.grad;
+    // layer 3: dW3[k][j] = sum_s dO[s][k] h2[s][j], db3 = sum dO
+    if ((e = colsum(d, d.dO, NOUT, d.h2, H, NOUT, H, n, g + OFF_W3, st)) != cudaSuccess) return e;
+    if ((e = colsum(d, d.dO, NOUT, nullptr, 0, NOUT, 1, n, g + OFF_B3, st)) != cudaSuccess) return e;
+    back3_kernel<<<(unsigned)((n * H + 255) / 256), 256, 0, st>>>(d.dO, n, d.W3q, d.a2, d.da2);
+    // layer 2: dW2 = da2^T h1 (batch slices, then an ordered sum), db2
+    const long slice = kRows * 8;
+    const long ns = (n + slice - 1) / slice;
+    dim3 gw(H / TN, H / TM, (unsigned)ns);
+    gemm_kernel<true, false, false, EPI_STORE><<<gw, 256, 0, st>>>(
+        H, H, (int)n, d.da2, H, d.h1, H, nullptr, nullptr, 0, d.wpart, nullptr, H, slice, (long)H * H);
+    colsum_final_kernel<<<(H * H + 255) / 256, 256, 0, st>>>(d.wpart, (int)ns, H * H, g + OFF_W2);
+    if ((e = colsum(d, d.da2, H, nullptr, 0, H, 1, n, g + OFF_B2, st)) != cudaSuccess) return e;
+    // layer 1: da1 = (da2 W2) gelu'(a1); dW1 = da1^T x; db1
+    dim3 g1(H / TN, (unsigned)((n + TM - 1) / TM), 1);
+    gemm_kernel<false, false, true, EPI_GELU_GRAD><<<g1, 256, 0, st>>>(
+        (int)n, H, H, d.da2, H, d.W2q, H, nullptr, d.a1, H, d.da1, nullptr, H, H, 0);
+    if ((e = colsum(d, d.da1, H, x, 4, H, 4, n, g + OFF_W1, st)) != cudaSuccess) return e;
+    if ((e = colsum(d, d.da1, H, nullptr, 0, H, 1, n, g + OFF_B1, st)) != cudaSuccess) return e;
+    if (loss) {
+        if ((e = colsum(d, d.loss_s, 1, nullptr, 0, 1, 1, n, loss, st)) != cudaSuccess) return e;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_adam(MlpDev &d, int t, float lr, cudaStream_t st) {
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float bc1 = 1.f - powf(b1, (float)t), bc2 = 1.f - powf(b2, (float)t);
+    adam_kernel<<<(NPAR + 255) / 256, 256, 0, st>>>(d.theta, d.m, d.v, d.grad, NPAR, lr, b1, b2, 1e-8f, bc1, bc2);
+    return mlp_quantize(d, st);
+}
+
+cudaError_t mlp_infer(MlpDev &d, const float *x, const float *s2, long n, float *llr, cudaStream_t st) {
+    return mlp_forward(d, x, s2, nullptr, n, llr, st);
+}

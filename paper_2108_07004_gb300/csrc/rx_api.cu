@@ -678,6 +678,13 @@ StateLayout state_layout(const rx_handle *h) {
 
 }  // namespace
 
+struct rx_mlp {
+    MlpDev d;
+    cudaStream_t st = nullptr;
+    int t = 0;                       // Adam steps taken
+    long scratch_n = 0;
+};
+
 // ===========================================================================
 // exported
 // ===========================================================================
@@ -774,6 +781,89 @@ int rx_get_param(const rx_handle *h, const char *key, double *value) {
 int rx_set_stream(rx_handle *h, void *cuda_stream) {
     if (!h) return fail(RX_EINVAL, "NULL handle");
     h->st = (cudaStream_t)cuda_stream;
+    return RX_OK;
+}
+
+rx_mlp *rx_mlp_create(const float *params) {
+    rx_mlp *m = new rx_mlp();
+    cudaError_t e = mlp_alloc(m->d);
+    if (e != cudaSuccess) {
+        fail(RX_ENOMEM, "rx_mlp_create: %s", cudaGetErrorString(e));
+        mlp_free(m->d);
+        delete m;
+        return nullptr;
+    }
+    if (params && rx_mlp_set_params(m, params) != RX_OK) {
+        mlp_free(m->d);
+        delete m;
+        return nullptr;
+    }
+    if (!params && mlp_quantize(m->d, m->st) != cudaSuccess) {
+        fail(RX_ECUDA, "rx_mlp_create: weight copies");
+        mlp_free(m->d);
+        delete m;
+        return nullptr;
+    }
+    return m;
+}
+
+void rx_mlp_destroy(rx_mlp *m) {
+    if (!m) return;
+    if (m->st) cudaStreamSynchronize(m->st);
+    else cudaDeviceSynchronize();
+    mlp_free(m->d);
+    delete m;
+}
+
+int rx_mlp_set_stream(rx_mlp *m, void *cuda_stream) {
+    if (!m) return fail(RX_EINVAL, "NULL handle");
+    m->st = (cudaStream_t)cuda_stream;
+    return RX_OK;
+}
+
+int rx_mlp_get_params(rx_mlp *m, float *params) {
+    if (!m || !params) return fail(RX_EINVAL, "NULL argument");
+    CK(cudaStreamSynchronize(m->st));
+    CK(cudaMemcpy(params, m->d.theta, sizeof(float) * RX_MLP_PARAMS, cudaMemcpyDeviceToHost));
+    return RX_OK;
+}
+
+int rx_mlp_set_params(rx_mlp *m, const float *params) {
+    if (!m || !params) return fail(RX_EINVAL, "NULL argument");
+    CK(cudaStreamSynchronize(m->st));
+    CK(cudaMemcpy(m->d.theta, params, sizeof(float) * RX_MLP_PARAMS, cudaMemcpyHostToDevice));
+    CK(cudaMemset(m->d.m, 0, sizeof(float) * RX_MLP_PARAMS));
+    CK(cudaMemset(m->d.v, 0, sizeof(float) * RX_MLP_PARAMS));
+    m->t = 0;
+    CK(mlp_quantize(m->d, m->st));
+    CK(cudaStreamSynchronize(m->st));
+    return RX_OK;
+}
+
+int rx_mlp_grad(rx_mlp *m, const float *x, const float *sigma2, const uint8_t *bits, size_t n, float *grad,
+                float *loss) {
+    if (!m || !x || !sigma2 || !bits || !grad) return fail(RX_EINVAL, "NULL argument");
+    if (n == 0 || n > (1u << 26)) return fail(RX_EINVAL, "batch of %zu samples (1 .. 2^26)", n);
+    CK(mlp_grad(m->d, x, sigma2, bits, (long)n, loss, m->st));
+    CK(cudaMemcpyAsync(grad, m->d.grad, sizeof(float) * RX_MLP_PARAMS, cudaMemcpyDeviceToDevice, m->st));
+    return RX_OK;
+}
+
+int rx_mlp_train_step(rx_mlp *m, const float *x, const float *sigma2, const uint8_t *bits, size_t n, float lr,
+                      float *loss) {
+    if (!m || !x || !sigma2 || !bits) return fail(RX_EINVAL, "NULL argument");
+    if (n == 0 || n > (1u << 26)) return fail(RX_EINVAL, "batch of %zu samples (1 .. 2^26)", n);
+    if (!(lr > 0.f)) return fail(RX_EINVAL, "learning rate must be > 0");
+    CK(mlp_grad(m->d, x, sigma2, bits, (long)n, loss, m->st));
+    CK(mlp_adam(m->d, ++m->t, lr, m->st));
+    return RX_OK;
+}
+
+int rx_mlp_infer(rx_mlp *m, const float *x, const float *sigma2, size_t n, float *llr) {
+    if (!m || !x || !sigma2 || !llr) return fail(RX_EINVAL, "NULL argument");
+    if (n == 0) return RX_OK;
+    if (n > (1u << 26)) return fail(RX_EINVAL, "%zu samples (at most 2^26 per call)", n);
+    CK(mlp_infer(m->d, x, sigma2, (long)n, llr, m->st));
     return RX_OK;
 }
 

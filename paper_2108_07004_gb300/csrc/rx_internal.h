@@ -183,6 +183,29 @@ cudaError_t launch_derot_demap(const float2 *y, long y_stride, const uint8_t *b,
 // number of partial-sum rows launch_derot_demap needs per stream
 long derot_demap_ctas(long len);
 
+// ---- learned demapper (k_mlp.cu) ----
+// Device state of one MLP: float32 master parameters (order W1 [128][4],
+// b1 [128], W2 [128][128], b2 [128], W3 [6][128], b3 [6]), Adam moments,
+// the gradient, bfloat16 copies of the weights, and activation scratch.
+struct MlpDev {
+    float *theta = nullptr, *m = nullptr, *v = nullptr, *grad = nullptr;
+    uint16_t *W1q = nullptr, *W2q = nullptr, *W3q = nullptr;
+    // activations and scratch for up to cap samples
+    long cap = 0;
+    float *a1 = nullptr, *h1 = nullptr, *a2 = nullptr, *h2 = nullptr, *dO = nullptr, *da2 = nullptr,
+          *da1 = nullptr, *loss_s = nullptr, *part = nullptr, *wpart = nullptr;
+    long part_cap = 0;
+};
+
+
+cudaError_t mlp_alloc(MlpDev &d);
+void mlp_free(MlpDev &d);
+cudaError_t mlp_quantize(MlpDev &d, cudaStream_t st);
+cudaError_t mlp_grad(MlpDev &d, const float *x, const float *s2, const uint8_t *bits, long n, float *loss,
+                     cudaStream_t st);
+cudaError_t mlp_adam(MlpDev &d, int t, float lr, cudaStream_t st);
+cudaError_t mlp_infer(MlpDev &d, const float *x, const float *s2, long n, float *llr, cudaStream_t st);
+
 cudaError_t launch_demap(const float2 *z, long z_stride, long z_off, long a, long e,
                          const double *sigma2, int sigma2_stride, float *llr,
                          long llr_stride, const DemapCount &cnt, int n_streams,

@@ -59,6 +59,14 @@ _PROTOS = {
     "rx_get_state": (_I, [_VP, _VP, C.POINTER(_SZ)]),
     "rx_set_state": (_I, [_VP, _VP, _SZ]),
     "rx_process_blocks": (_I, [_VP, _VP, _SZ, _SZ, _SZ, _VP, _VP]),
+    "rx_mlp_create": (_VP, [_VP]),
+    "rx_mlp_destroy": (None, [_VP]),
+    "rx_mlp_set_stream": (_I, [_VP, _VP]),
+    "rx_mlp_get_params": (_I, [_VP, _VP]),
+    "rx_mlp_set_params": (_I, [_VP, _VP]),
+    "rx_mlp_grad": (_I, [_VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
+    "rx_mlp_train_step": (_I, [_VP, _VP, _VP, _VP, _SZ, C.c_float, _VP]),
+    "rx_mlp_infer": (_I, [_VP, _VP, _VP, _SZ, _VP]),
     "rx_format_info": (_I, [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "rx_last_error": (C.c_char_p, []),
     "rx_cdc": (_I, [_VP, _VP, _VP, _SZ]),
@@ -327,6 +335,63 @@ class Receiver:
     def close(self):
         if getattr(self, "h", None):
             lib().rx_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+MLP_PARAMS = 17926
+
+
+class Mlp:
+    """Learned demapper handle (MLP 4 -> 128 -> 128 -> 6); buffers are torch
+    device tensors: x [n, 4] float32, sigma2 [n] float32, bits [n, 6] uint8."""
+
+    def __init__(self, params: np.ndarray | None = None, stream: torch.cuda.Stream | None = None):
+        L = lib()
+        buf = None
+        if params is not None:
+            buf = np.ascontiguousarray(params, dtype=np.float32)
+            if buf.size != MLP_PARAMS:
+                raise ValueError(f"expected {MLP_PARAMS} parameters")
+        h = L.rx_mlp_create(buf.ctypes.data if buf is not None else None)
+        if not h:
+            raise RxError(-1, L.rx_last_error().decode())
+        self.h = h
+        st = stream if stream is not None else torch.cuda.current_stream()
+        _ck(L.rx_mlp_set_stream(h, st.cuda_stream))
+
+    def params(self) -> np.ndarray:
+        out = np.empty(MLP_PARAMS, np.float32)
+        _ck(lib().rx_mlp_get_params(self.h, out.ctypes.data))
+        return out
+
+    def set_params(self, params: np.ndarray):
+        buf = np.ascontiguousarray(params, dtype=np.float32)
+        _ck(lib().rx_mlp_set_params(self.h, buf.ctypes.data))
+
+    def grad(self, x, sigma2, bits):
+        g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=x.device)
+        loss = torch.empty(1, dtype=torch.float32, device=x.device)
+        _ck(lib().rx_mlp_grad(self.h, _ptr(x), _ptr(sigma2), _ptr(bits), x.shape[0], _ptr(g), _ptr(loss)))
+        return g, loss
+
+    def train_step(self, x, sigma2, bits, lr: float, loss: torch.Tensor | None = None):
+        _ck(lib().rx_mlp_train_step(self.h, _ptr(x), _ptr(sigma2), _ptr(bits), x.shape[0], lr, _ptr(loss)))
+
+    def infer(self, x, sigma2, llr: torch.Tensor | None = None):
+        if llr is None:
+            llr = torch.empty((x.shape[0], 6), dtype=torch.float32, device=x.device)
+        _ck(lib().rx_mlp_infer(self.h, _ptr(x), _ptr(sigma2), x.shape[0], _ptr(llr)))
+        return llr
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rx_mlp_destroy(self.h)
             self.h = None
 
     def __del__(self):
