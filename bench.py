@@ -331,6 +331,110 @@ def run_ours(args):
     print(json.dumps(line), flush=True)
 
 
+# ---- learned demapper (MLP 4 -> 128 -> 128 -> 6) on the same chain ------------
+LEARN = dict(train_streams=16, train_sym=(1 << 18) + (1 << 14), skip=1 << 14, epochs=20, batch=8192,
+             lr=1e-3, infer_streams=16, infer_sym=1 << 20, esn0=(8.0, 16.0), init_seed=2108070044)
+
+
+def learned_inputs(n_streams: int, n_sym: int, seed_base: int):
+    """Streams of the bench channel with Es/N0 drawn uniformly in 8..16 dB."""
+    rng = np.random.default_rng(seed_base)
+    esn0 = rng.uniform(*LEARN["esn0"], size=n_streams)
+    rxs, bits = [], []
+    for p in range(n_streams):
+        st = synth.make_stream(WL["fmt"], n_sym, seed=seed_base + 1 + p, esn0_db=float(esn0[p]),
+                               cd_ps_per_nm=WL["cd_ps_per_nm"], linewidth_ts=WL["linewidth_ts"])
+        rxs.append(st.rx)
+        bits.append(st.bits)
+    return np.stack(rxs), np.stack(bits), esn0
+
+
+def run_learned(args):
+    """Config 4: train the MLP demapper on symbols the chain itself makes, on
+    the GPU's own kernels, then run the chain with it on 2^24 symbols and
+    compare with the exact demapper on the same streams."""
+    import torch
+    from paper_2108_07004_gb300 import rx as rx_mod
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    # training data: de-rotated symbols and block sigma^2 from the exact chain
+    S, N, skip = LEARN["train_streams"], LEARN["train_sym"], LEARN["skip"]
+    rx_h, bits_h, _ = learned_inputs(S, N, synth.stream_seed(4, 0))
+    r = rx_mod.Receiver(WL["fmt"], cd_ps_per_nm=WL["cd_ps_per_nm"], taps=WL["taps"],
+                        bps_phases=WL["bps_phases"], streams=S, **rx_params())
+    r.set_reference(torch.from_numpy(bits_h).cuda())
+    x4 = torch.empty((S, N, 4), dtype=torch.float32, device="cuda")
+    s2 = torch.empty((S, N), dtype=torch.float32, device="cuda")
+    r.set_symbol_output(x4, s2)
+    r.process(torch.from_numpy(rx_h).cuda(), stats=False)
+    torch.cuda.synchronize()
+    X = x4[:, skip:].reshape(-1, 4).contiguous()
+    S2 = s2[:, skip:].reshape(-1).contiguous()
+    B = torch.from_numpy(bits_h[:, skip:].reshape(-1, 6)).cuda()
+    r.set_symbol_output(None, None)
+    r.close()
+    del rx_h
+    n_train = X.shape[0]
+    m = rx_mod.Mlp(synth.mlp_init_params(LEARN["init_seed"]))
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(LEARN["init_seed"])
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    bs = LEARN["batch"]
+    steps_per_epoch = n_train // bs
+    t0 = time.perf_counter()
+    losses = []
+    for ep in range(LEARN["epochs"]):
+        perm = torch.randperm(n_train, device="cuda", generator=gen)
+        for i in range(steps_per_epoch):
+            idx = perm[i * bs:(i + 1) * bs]
+            m.train_step(X[idx], S2[idx], B[idx], LEARN["lr"], loss)
+        losses.append(loss.item())
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    del X, S2, B
+    # inference: the chain with the exact and with the learned demapper
+    S, N = LEARN["infer_streams"], args.learned_sym
+    rx_h, bits_h, esn0 = learned_inputs(S, N, synth.stream_seed(4, 1))
+    samples = torch.from_numpy(rx_h).cuda()
+    del rx_h
+    r = rx_mod.Receiver(WL["fmt"], cd_ps_per_nm=WL["cd_ps_per_nm"], taps=WL["taps"],
+                        bps_phases=WL["bps_phases"], streams=S, **rx_params())
+    r.set_reference(torch.from_numpy(bits_h).cuda())
+    llr = torch.empty((S, N, 6), dtype=torch.float32, device="cuda")
+    out = {}
+    for name, dm in (("exact", None), ("learned", m)):
+        r.set_demapper(dm)
+        for _ in range(args.warmup):
+            r.process(samples, llr, stats=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            r.process(samples, llr, stats=False)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        st = r.stats()
+        out[name] = {"ms_per_step": ms, "gbps": S * N * 6 / (ms * 1e-3) / 1e9,
+                     "gmi": [x["gmi"] for x in st], "ber": [x["ber"] for x in st]}
+    ge, gl = np.array(out["exact"]["gmi"]), np.array(out["learned"]["gmi"])
+    be, bl = np.array(out["exact"]["ber"]), np.array(out["learned"]["ber"])
+    line = {
+        "metric": METRIC, "value": out["learned"]["gbps"], "unit": "Gbit/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": out["learned"]["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16/f32",
+        "data": "synthetic",
+        "config": {"workload": "learned_demapper_mlp_4x128x128x6_gs4d64", "streams": S,
+                   "symbols_per_stream": N, "esn0_db": [round(float(v), 2) for v in esn0],
+                   "train_symbols": int(n_train), "epochs": LEARN["epochs"], "batch": bs, "lr": LEARN["lr"]},
+        "exact_chain_gbps": out["exact"]["gbps"],
+        "gmi_gap_mean": float(np.mean(ge - gl)), "gmi_gap_max": float(np.max(ge - gl)),
+        "ber_delta_rel_max": float(np.max(np.abs(bl - be) / np.maximum(be, 1e-12))),
+        "gmi_exact": [round(float(v), 5) for v in ge], "gmi_learned": [round(float(v), 5) for v in gl],
+        "train_seconds": train_s, "train_loss_per_epoch": [round(float(v), 6) for v in losses],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -344,9 +448,14 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--variant", default="plain", choices=["plain", "learned"],
+                    help="learned: train the MLP demapper on chain output, compare with the exact one")
+    ap.add_argument("--learned-sym", type=int, default=LEARN["infer_sym"])
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.variant == "learned":
+        run_learned(args)
     else:
         run_ours(args)
 

@@ -270,6 +270,18 @@ int rx_mlp_train_step(rx_mlp *m, const float *x, const float *sigma2, const uint
 /* LLRs of n samples. */
 int rx_mlp_infer(rx_mlp *m, const float *x, const float *sigma2, size_t n, float *llr);
 
+/* The chain's demapper: m (not owned; must outlive its use) replaces the
+ * exact log-sum-exp LLRs of rx_process with the MLP's (counting unchanged);
+ * NULL restores the exact demapper.  RX_EINVAL unless the format is a
+ * 64-point 4D table. */
+int rx_set_demapper(rx_handle *h, rx_mlp *m);
+/* Symbol outputs of later rx_process calls (device, caller-owned, sized for
+ * the streams' N): x4 [S][N][4] float32, the de-rotated 4D symbols as the
+ * learned demapper takes them, and sigma2 [S][N] float32, each symbol's
+ * block noise variance; either may be NULL (not written).  Used to make the
+ * learned demapper's training data from the chain. */
+int rx_set_symbol_output(rx_handle *h, float *x4, float *sigma2);
+
 /* Format facts: dims, m (bits per 4D symbol), M (table size). */
 int rx_format_info(const rx_handle *h, int *dims, int *m, int *M);
 

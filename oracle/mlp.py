@@ -35,6 +35,8 @@ from dataclasses import dataclass
 import numpy as np
 from scipy.special import erf
 
+from paper_2108_07004_gb300 import synth
+
 H = 128
 N_IN, N_OUT = 4, 6
 SHAPES = [("W1", (H, N_IN)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)),
@@ -57,17 +59,11 @@ def pack(p: dict) -> np.ndarray:
 
 
 def init_params(seed: int) -> np.ndarray:
-    """He-style uniform initialisation, float32 master values, biases zero."""
-    rng = np.random.default_rng(seed)
-    p = {}
-    for name, shp in SHAPES:
-        if name.startswith("W"):
-            fan_in = shp[1]
-            lim = math.sqrt(6.0 / fan_in)
-            p[name] = rng.uniform(-lim, lim, size=shp).astype(np.float32)
-        else:
-            p[name] = np.zeros(shp, np.float32)
-    return pack(p).astype(np.float32)
+    """Initial float32 parameters from the shared seeded generator (He
+    uniform weights, zero biases); drawn random numbers are inputs."""
+    th = synth.mlp_init_params(seed)
+    assert th.size == N_PARAMS
+    return th
 
 
 def bf16_round(a: np.ndarray) -> np.ndarray:

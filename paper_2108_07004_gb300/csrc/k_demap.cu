@@ -409,7 +409,8 @@ derot_demap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *_
                    const int32_t *__restrict__ carry_in, int cin_stride, int32_t *__restrict__ carry_out,
                    int cout_stride, uint16_t *__restrict__ pcode, long pc_stride,
                    const double *__restrict__ sigma2_fixed, double *__restrict__ sigma2_out, int s2_stride,
-                   float *__restrict__ llr, long llr_stride, DemapCount cnt, const __grid_constant__ FmtDev f) {
+                   float *__restrict__ llr, long llr_stride, DemapCount cnt, SymOut sym,
+                   const __grid_constant__ FmtDev f) {
     constexpr int M_OUT = (DIMS == 4) ? MB : 2 * MB;
     constexpr int PT = kTile / 256;
     __shared__ uint8_t bl[kTile];
@@ -522,14 +523,76 @@ derot_demap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *_
             if (mq) rot = make_float2(-rot.x, -rot.y);
         }
         const float2 z0 = cmul(yx[k], rot), z1 = cmul(yy[k], rot);
-        if (active) pc[k - a] = (uint16_t)(b | (mq << 8));
+        if (active) {
+            pc[k - a] = (uint16_t)(b | (mq << 8));
+            if (sym.x4)
+                reinterpret_cast<float4 *>(sym.x4)[(long)s * sym.stride + k] = make_float4(z0.x, z0.y, z1.x, z1.y);
+            if (sym.s2) sym.s2[(long)s * sym.stride + k] = (float)s2_sh;
+        }
+        if (!llr) continue;                   // symbols only (another demapper follows)
         const bool counted = active && cnt.ref_lab && k >= cnt.c0 && k < cnt.c1;
         const int ref = counted ? (int)cnt.ref_lab[(long)s * cnt.ref_stride + k] : -1;
         demap_symbol<DIMS, MT, MB>(z0, z1, c2, f, active, ref, counted,
                                    llr + (long)s * llr_stride + (k - a) * M_OUT, acc);
     }
-    if (!cnt.sd) return;
+    if (!cnt.sd || !llr) return;
     count_reduce(acc, cnt, s, blockIdx.x, gridDim.x, s2_sh);
+}
+
+// Counting for LLRs made by another demapper (the learned one): hard-decision
+// errors and GMI terms against the reference labels, EVM from the symbols
+// x4 (nearest point by the orbit form), over symbols a .. e-1 of each
+// stream; the same fixed-order reductions as the exact path.
+template <int DIMS, int MB>
+__global__ void __launch_bounds__(256)
+count_llr_kernel(const float *__restrict__ llr, long llr_stride, const float4 *__restrict__ x4, long x_stride,
+                 long a, long e, const double *__restrict__ sigma2, int s2_stride, DemapCount cnt,
+                 const __grid_constant__ FmtDev f) {
+    constexpr int M_OUT = (DIMS == 4) ? MB : 2 * MB;
+    const int s = blockIdx.y;
+    const long k = a + (long)blockIdx.x * blockDim.x + threadIdx.x;
+    CountAcc acc;
+    if (k < e && cnt.ref_lab && k >= cnt.c0 && k < cnt.c1) {
+        const int ref = cnt.ref_lab[(long)s * cnt.ref_stride + k];
+        const float *row = llr + (long)s * llr_stride + (k - a) * M_OUT;
+        int ne = 0;
+        float g2 = 0.f;
+#pragma unroll
+        for (int i = 0; i < M_OUT; ++i) {
+            const int bit = (ref >> (M_OUT - 1 - i)) & 1;
+            const float L = row[i];
+            ne += (int)((L < 0.f) != (bit != 0));
+            g2 += softplus_bits(bit ? L : -L);
+        }
+        const float4 v = x4[(long)s * x_stride + k];
+        float dist = 0.f, en = 0.f;
+        const int npol = DIMS == 4 ? 1 : 2;
+        for (int pp = 0; pp < npol; ++pp) {
+            const float2 z0 = DIMS == 4 ? make_float2(v.x, v.y) : (pp ? make_float2(v.z, v.w) : make_float2(v.x, v.y));
+            const float2 z1 = make_float2(v.z, v.w);
+            const float zn = DIMS == 4 ? cnorm(z0) + cnorm(z1) : cnorm(z0);
+            float g = 3.0e38f, eg = 0.f;
+            for (int o = 0; o < f.n_orb; ++o) {
+                float P = z0.x * f.orb[o][0] + z0.y * f.orb[o][1];
+                float Q = z0.y * f.orb[o][0] - z0.x * f.orb[o][1];
+                if (DIMS == 4) {
+                    P += z1.x * f.orb[o][2] + z1.y * f.orb[o][3];
+                    Q += z1.y * f.orb[o][2] - z1.x * f.orb[o][3];
+                }
+                const float vv = (f.S == 4) ? fmaxf(fabsf(P), fabsf(Q)) : (f.S == 2 ? fabsf(P) : P);
+                const float dd = zn + f.orbe[o] - 2.f * vv;
+                if (dd < g) { g = dd; eg = f.orbe[o]; }
+            }
+            dist += fmaxf(g, 0.f);
+            en += eg;
+        }
+        acc.nerr = ne;
+        acc.ncnt = 1;
+        acc.gsum = g2;
+        acc.en = dist;
+        acc.ed = en;
+    }
+    count_reduce(acc, cnt, s, blockIdx.x, gridDim.x, sigma2[s * s2_stride]);
 }
 
 template <int DIMS, int MT, int MB>
@@ -544,12 +607,12 @@ template <int DIMS, int MT, int MB>
 cudaError_t derot_demap_t(const float2 *y, long ys, const uint8_t *b, long bst, long a, long e,
                           const int *dsum, const double *mdsum, int kR, const int32_t *cin, int cis,
                           int32_t *cout, int cos, uint16_t *pc, long pcs, const double *s2f, double *s2o,
-                          int s2s, float *llr, long ls, const DemapCount &cnt, int n_streams, const FmtDev &f,
-                          cudaStream_t st) {
+                          int s2s, float *llr, long ls, const DemapCount &cnt, const SymOut &sym, int n_streams,
+                          const FmtDev &f, cudaStream_t st) {
     const int n_rng = (int)((e - a + kR - 1) / kR);
     dim3 grid((unsigned)((e - a + kTile - 1) / kTile), (unsigned)n_streams);
     derot_demap_kernel<DIMS, MT, MB><<<grid, 256, 0, st>>>(y, ys, b, bst, a, e, dsum, mdsum, n_rng, kR, cin, cis,
-                                                           cout, cos, pc, pcs, s2f, s2o, s2s, llr, ls, cnt, f);
+                                                           cout, cos, pc, pcs, s2f, s2o, s2s, llr, ls, cnt, sym, f);
     return cudaGetLastError();
 }
 
@@ -562,19 +625,37 @@ cudaError_t launch_derot_demap(const float2 *y, long y_stride, const uint8_t *b,
                                const int32_t *carry_in, int cin_stride, int32_t *carry_out,
                                int cout_stride, uint16_t *pcode, long pc_stride,
                                const double *sigma2_fixed, double *sigma2_out, int s2_stride,
-                               float *llr, long llr_stride, const DemapCount &cnt, int n_streams,
-                               const FmtDev &f, cudaStream_t st) {
+                               float *llr, long llr_stride, const DemapCount &cnt, const SymOut &sym,
+                               int n_streams, const FmtDev &f, cudaStream_t st) {
     if (e <= a || n_streams <= 0) return cudaSuccess;
     if (!cnt.sd || !cnt.partial || !mdsum) return cudaErrorInvalidValue;
 #define RX_DD(D_, M_, B_)                                                                                  \
     return derot_demap_t<D_, M_, B_>(y, y_stride, b, b_stride, a, e, dsum, mdsum, kR, carry_in, cin_stride, \
                                      carry_out, cout_stride, pcode, pc_stride, sigma2_fixed, sigma2_out,    \
-                                     s2_stride, llr, llr_stride, cnt, n_streams, f, st)
+                                     s2_stride, llr, llr_stride, cnt, sym, n_streams, f, st)
     if (f.dims == 4 && f.M == 64) RX_DD(4, 64, 6);
     if (f.dims == 2 && f.M == 4) RX_DD(2, 4, 2);
     if (f.dims == 2 && f.M == 16) RX_DD(2, 16, 4);
 #undef RX_DD
     return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_count_llr(const float *llr, long llr_stride, const float *x4, long x_stride, long a, long e,
+                             const double *sigma2, int s2_stride, const DemapCount &cnt, int n_streams,
+                             const FmtDev &f, cudaStream_t st) {
+    if (e <= a || n_streams <= 0) return cudaSuccess;
+    if (!cnt.sd || !cnt.partial) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((e - a + 255) / 256), (unsigned)n_streams);
+    const float4 *xv = reinterpret_cast<const float4 *>(x4);
+    if (f.dims == 4 && f.m == 6)
+        count_llr_kernel<4, 6><<<grid, 256, 0, st>>>(llr, llr_stride, xv, x_stride, a, e, sigma2, s2_stride, cnt, f);
+    else if (f.dims == 2 && f.m_pol == 2)
+        count_llr_kernel<2, 2><<<grid, 256, 0, st>>>(llr, llr_stride, xv, x_stride, a, e, sigma2, s2_stride, cnt, f);
+    else if (f.dims == 2 && f.m_pol == 4)
+        count_llr_kernel<2, 4><<<grid, 256, 0, st>>>(llr, llr_stride, xv, x_stride, a, e, sigma2, s2_stride, cnt, f);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
 }
 
 cudaError_t launch_demap(const float2 *z, long z_stride, long z_off, long a, long e,

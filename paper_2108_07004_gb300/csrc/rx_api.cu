@@ -46,6 +46,13 @@ constexpr double kC = 299792458.0;
 
 }  // namespace
 
+struct rx_mlp {
+    MlpDev d;
+    cudaStream_t st = nullptr;
+    int t = 0;                       // Adam steps taken
+    long scratch_n = 0;
+};
+
 struct rx_handle {
     // format
     FmtDev fmt{};
@@ -99,6 +106,11 @@ struct rx_handle {
     // stream state (host mirror of the scalars)
     bool started = false;
     bool trained = false;
+    // learned demapper (null: exact log-sum-exp) and symbol outputs
+    rx_mlp *mlp = nullptr;
+    float *user_x4 = nullptr, *user_s2 = nullptr;   // caller's [S][N][4], [S][N]
+    float *x4 = nullptr, *s2sym = nullptr;          // own, for the learned demapper
+    long cap_x4 = 0;
     long blocks_done = 0;
     unsigned long long u = 0;
     long cur_n = 0;
@@ -302,6 +314,19 @@ void free_buffers(rx_handle *h) {
     h->part_u = h->part_d = h->sig = h->sig_fixed = nullptr;
     h->sd = nullptr;
     h->cap_n = 0; h->cap_s = 0; h->cap_lag = 0;
+}
+
+int ensure_symbol_buffers(rx_handle *h, long N) {
+    const size_t need = (size_t)h->streams * N;
+    if (h->x4 && h->cap_x4 >= (long)need) return RX_OK;
+    cudaFree(h->x4);
+    cudaFree(h->s2sym);
+    h->x4 = h->s2sym = nullptr;
+    h->cap_x4 = 0;
+    CK(cudaMalloc(&h->x4, sizeof(float) * 4 * need));
+    CK(cudaMalloc(&h->s2sym, sizeof(float) * need));
+    h->cap_x4 = (long)need;
+    return RX_OK;
 }
 
 int ensure_buffers(rx_handle *h, long N) {
@@ -509,6 +534,18 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     }
     const int m = f.m;
     const long sd_stride = sizeof(StreamDev) / sizeof(int32_t);
+    SymOut sym;
+    if (h->user_x4 || h->user_s2) {
+        sym.x4 = h->user_x4;
+        sym.s2 = h->user_s2;
+        sym.stride = N;
+    }
+    if (h->mlp && (!sym.x4 || !sym.s2)) {
+        if ((rc = ensure_symbol_buffers(h, N)) != RX_OK) return rc;
+        if (!sym.x4) sym.x4 = h->x4;
+        if (!sym.s2) sym.s2 = h->s2sym;
+        sym.stride = N;
+    }
     int32_t *carry_base = reinterpret_cast<int32_t *>(h->sd);
     DemapCount cnt{};
     cnt.ref_lab = (h->ref && h->ref_n >= N) ? h->ref : nullptr;
@@ -536,13 +573,23 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
             STAGE(ST_UNWRAP, st, 1, launch_anchor(h->bidx, N, h->pcode, N, (int)std::min(h->n_train, e),
                                                   carry_base, (int)sd_stride, S, h->B, f.S, st));
         }
-        // unwrap, de-rotation, LLRs and counting in one pass over y (no z)
-        if (derot_demap_ctas(e - a) > h->cap_pd) return fail(RX_EINVAL, "internal: demap partials");
+        // unwrap, de-rotation, LLRs and counting in one pass over y (no z);
+        // with the learned demapper the pass writes the symbols instead
+        if (derot_demap_ctas(e - a) > h->cap_pd || (e - a + 255) / 256 > h->cap_pd)
+            return fail(RX_EINVAL, "internal: demap partials");
         STAGE(ST_DEMAP, st, 1,
               launch_derot_demap(h->y, N, h->bidx + a, N, a, e, h->dsum, h->mdsum, bps_cta_range(rounds),
                                  carry_base + 2 * cin, (int)sd_stride, carry_base + 2 * cout, (int)sd_stride,
                                  h->pcode + a, N, h->sigma2_fixed > 0 ? h->sig_fixed : nullptr, h->sig, 1,
-                                 llr + (size_t)a * m, N * m, cnt, S, f, st));
+                                 h->mlp ? nullptr : llr + (size_t)a * m, N * m, cnt, sym, S, f, st));
+        if (h->mlp) {
+            for (int s = 0; s < S; ++s)
+                STAGE(ST_DEMAP, st, 3,
+                      mlp_infer(h->mlp->d, sym.x4 + ((size_t)s * N + a) * 4, sym.s2 + (size_t)s * N + a, e - a,
+                                llr + ((size_t)s * N + a) * m, st));
+            STAGE(ST_DEMAP, st, 1,
+                  launch_count_llr(llr + (size_t)a * m, N * m, sym.x4, N, a, e, h->sig, 1, cnt, S, f, st));
+        }
         if (blk0) {
             cudaEvent_t blk1 = prof_event(h);
             if (blk1) { CK(cudaEventRecord(blk1, st)); h->blk.push_back({blk0, blk1}); }
@@ -678,13 +725,6 @@ StateLayout state_layout(const rx_handle *h) {
 
 }  // namespace
 
-struct rx_mlp {
-    MlpDev d;
-    cudaStream_t st = nullptr;
-    int t = 0;                       // Adam steps taken
-    long scratch_n = 0;
-};
-
 // ===========================================================================
 // exported
 // ===========================================================================
@@ -734,6 +774,8 @@ void rx_destroy(rx_handle *h) {
     for (auto e : h->ev_lms) cudaEventDestroy(e);
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     free_buffers(h);
+    cudaFree(h->x4);
+    cudaFree(h->s2sym);
     cudaFree(h->H);
     cudaFree(h->tw);
     cudaFree(h->ref);
@@ -864,6 +906,21 @@ int rx_mlp_infer(rx_mlp *m, const float *x, const float *sigma2, size_t n, float
     if (n == 0) return RX_OK;
     if (n > (1u << 26)) return fail(RX_EINVAL, "%zu samples (at most 2^26 per call)", n);
     CK(mlp_infer(m->d, x, sigma2, (long)n, llr, m->st));
+    return RX_OK;
+}
+
+int rx_set_demapper(rx_handle *h, rx_mlp *m) {
+    if (!h) return fail(RX_EINVAL, "NULL handle");
+    if (m && !(h->fmt.dims == 4 && h->fmt.m == 6))
+        return fail(RX_EINVAL, "the learned demapper maps 4D symbols to 6 bits (a 64-point 4D table)");
+    h->mlp = m;
+    return RX_OK;
+}
+
+int rx_set_symbol_output(rx_handle *h, float *x4, float *sigma2) {
+    if (!h) return fail(RX_EINVAL, "NULL handle");
+    h->user_x4 = x4;
+    h->user_s2 = sigma2;
     return RX_OK;
 }
 

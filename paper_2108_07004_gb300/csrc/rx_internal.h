@@ -167,10 +167,26 @@ struct DemapCount {
     double *partial;          // [S][n_cta][3] scratch
 };
 
+// Optional symbol outputs of the chain: x4 [S][stride][4] float32 (Re, Im of
+// z_X, z_Y) and s2 [S][stride] float32 (the block's sigma^2), at absolute
+// symbol index k; null pointers are skipped.
+struct SymOut {
+    float *x4 = nullptr;
+    float *s2 = nullptr;
+    long stride = 0;
+};
+
+// Counting (errors, GMI, EVM) for LLRs made by the learned demapper, rows
+// a .. e-1 of llr (row k - a, stride llr_stride per stream).
+cudaError_t launch_count_llr(const float *llr, long llr_stride, const float *x4, long x_stride, long a, long e,
+                             const double *sigma2, int s2_stride, const DemapCount &cnt, int n_streams,
+                             const FmtDev &f, cudaStream_t st);
+
 // De-rotation by the unwrapped phase fused with the LLRs and counting, for
 // the chain: reads the equaliser output y and the BPS indices b (index k - a)
 // with BPS's per-range increment sums dsum and minimum-distance sums mdsum
-// ([S][n_cta], ranges of kR symbols), writes the phase codes and the LLRs;
+// ([S][n_cta], ranges of kR symbols), writes the phase codes and the LLRs
+// (llr null: symbols only, into sym);
 // sigma^2 = sum(mdsum) / (2 (e - a)) unless sigma2_fixed is given.  The
 // block's sigma^2 goes to sigma2_out[s * s2_stride].  No z is written.
 cudaError_t launch_derot_demap(const float2 *y, long y_stride, const uint8_t *b, long b_stride,
@@ -178,8 +194,8 @@ cudaError_t launch_derot_demap(const float2 *y, long y_stride, const uint8_t *b,
                                const int32_t *carry_in, int cin_stride, int32_t *carry_out,
                                int cout_stride, uint16_t *pcode, long pc_stride,
                                const double *sigma2_fixed, double *sigma2_out, int s2_stride,
-                               float *llr, long llr_stride, const DemapCount &cnt, int n_streams,
-                               const FmtDev &f, cudaStream_t st);
+                               float *llr, long llr_stride, const DemapCount &cnt, const SymOut &sym,
+                               int n_streams, const FmtDev &f, cudaStream_t st);
 // number of partial-sum rows launch_derot_demap needs per stream
 long derot_demap_ctas(long len);
 

@@ -59,6 +59,8 @@ _PROTOS = {
     "rx_get_state": (_I, [_VP, _VP, C.POINTER(_SZ)]),
     "rx_set_state": (_I, [_VP, _VP, _SZ]),
     "rx_process_blocks": (_I, [_VP, _VP, _SZ, _SZ, _SZ, _VP, _VP]),
+    "rx_set_demapper": (_I, [_VP, _VP]),
+    "rx_set_symbol_output": (_I, [_VP, _VP, _VP]),
     "rx_mlp_create": (_VP, [_VP]),
     "rx_mlp_destroy": (None, [_VP]),
     "rx_mlp_set_stream": (_I, [_VP, _VP]),
@@ -258,6 +260,16 @@ class Receiver:
         _ck(lib().rx_process_blocks(self.h, _ptr(samples), ns, b0, b1, _ptr(llr),
                                     C.cast(st, C.c_void_p) if st is not None else None))
         return llr, ([s.as_dict() for s in st] if st is not None else None)
+
+    def set_demapper(self, mlp: "Mlp | None"):
+        """Use the learned demapper (None: the exact one)."""
+        _ck(lib().rx_set_demapper(self.h, mlp.h if mlp is not None else None))
+        self._mlp = mlp
+
+    def set_symbol_output(self, x4: torch.Tensor | None, sigma2: torch.Tensor | None):
+        """x4 [S, N, 4] float32, sigma2 [S, N] float32 (device), or None."""
+        _ck(lib().rx_set_symbol_output(self.h, _ptr(x4), _ptr(sigma2)))
+        self._symout = (x4, sigma2)
 
     def process_host(self, samples, llr, stats: bool = True):
         """Host buffers (torch CPU tensors, pinned for overlap) in and out."""

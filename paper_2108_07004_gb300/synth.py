@@ -203,3 +203,20 @@ def make_batch(fmt: TxFormat | str, n_sym: int, seeds, esn0_dbs, **kw):
     streams = [make_stream(fmt, n_sym, seed=s, esn0_db=e, **kw)
                for s, e in zip(seeds, esn0_dbs)]
     return np.stack([s.rx for s in streams]), streams
+
+
+# ---- learned demapper: seeded initial weights ------------------------------
+MLP_LAYERS = ((128, 4), (128, 128), (6, 128))   # (outputs, inputs) of each layer
+
+
+def mlp_init_params(seed: int) -> np.ndarray:
+    """Initial parameters of the learned demapper's MLP 4 -> 128 -> 128 -> 6,
+    float32 in the library's order (W1, b1, W2, b2, W3, b3): weights drawn
+    uniformly in +-sqrt(6 / fan_in) (He), biases zero."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for n_out, n_in in MLP_LAYERS:
+        lim = np.sqrt(6.0 / n_in)
+        parts.append(rng.uniform(-lim, lim, size=(n_out, n_in)).astype(np.float32).ravel())
+        parts.append(np.zeros(n_out, np.float32))
+    return np.concatenate(parts)

@@ -125,3 +125,41 @@ def test_training_on_the_gpu_gains_over_the_untrained_network():
     assert np.array_equal(p0, p1) and l0 == l1                 # deterministic
     assert l0[-1] < l0[0] / 20
     assert b0 < 0.0 and exact - 0.3 < a0 < exact + 0.01
+
+
+def test_chain_with_learned_demapper_and_symbol_output():
+    """The chain's symbol output does not change its LLRs; with the learned
+    demapper the chain's LLRs are the MLP's on those symbols and its bit
+    counts are those of its own hard decisions."""
+    rx = _rx()
+    from paper_2108_07004_gb300 import synth
+    n = 20000
+    st = synth.make_stream("gs4d64", n, seed=synth.stream_seed(4, 1), esn0_db=13.0,
+                           cd_ps_per_nm=17000.0, linewidth_ts=2e-5)
+    samples = _dev(st.rx[None], np.complex64)
+    bits = _dev(st.bits[None], np.uint8)
+
+    def receiver():
+        r = rx.Receiver("gs4d64", cd_ps_per_nm=17000.0, taps=31, bps_phases=64)
+        for k, v in (("fft", 4096), ("overlap", 1024), ("block", 4096), ("n_pre", 4096)):
+            r.set(k, v)
+        r.set_reference(bits)
+        return r
+
+    ref, st_ref = receiver().process(samples)
+    r = receiver()
+    x4 = torch.zeros((1, n, 4), dtype=torch.float32, device="cuda")
+    s2 = torch.zeros((1, n), dtype=torch.float32, device="cuda")
+    r.set_symbol_output(x4, s2)
+    got, st_got = r.process(samples)
+    assert torch.equal(got, ref) and st_got[0]["bit_errors"] == st_ref[0]["bit_errors"]
+    assert torch.all(s2 > 0) and torch.all(torch.isfinite(x4))
+    m = rx.Mlp(_params(13))
+    r2 = receiver()
+    r2.set_demapper(m)
+    learned, st_l = r2.process(samples)
+    want = m.infer(x4[0].contiguous(), s2[0].contiguous())
+    assert torch.equal(learned[0], want)
+    c0, c1 = 4096, n - 512
+    hard = (learned[0, c0:c1].cpu().numpy() < 0).astype(np.uint8)
+    assert st_l[0]["bit_errors"] == int(np.sum(hard != st.bits[c0:c1]))
