@@ -110,7 +110,10 @@ void rx_destroy(rx_handle *h);                      /* NULL-safe */
  *   (<= 20000), "train_passes" [3],
  *   "sigma2" [0 = estimate per block], "skip_head" [4096],
  *   "skip_tail" [512], "streams" [1], "rolloff" [0.1],
- *   "wavelength_nm" [1550], "profile" [0] (1: time every launch).
+ *   "wavelength_nm" [1550], "profile" [0] (1: time every launch),
+ *   "precision" [0]: storage of the chain's CDC and FIR outputs, 0 float32,
+ *   1 half (FP16), 2 bfloat16; arithmetic, LMS taps and the phase unwrap
+ *   stay float32 (the precision variant; rx_get_state / rx_set_state need 0).
  * Changing a parameter resets the stream state (rx_reset). */
 int rx_set_param(rx_handle *h, const char *key, double value);
 int rx_get_param(const rx_handle *h, const char *key, double *value);

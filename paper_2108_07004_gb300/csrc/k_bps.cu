@@ -54,9 +54,9 @@ __device__ __forceinline__ float half_turn_d(float P, float Q, int S, float e) {
 
 template <int DIMS, int NORB>
 __global__ void __launch_bounds__(256, 2)
-bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_valid, int W,
+bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_valid, int W,
            uint8_t *__restrict__ bout, long bout_stride, int *__restrict__ dsum,
-           double *__restrict__ mdsum, int n_cta, int rounds, const __grid_constant__ FmtDev f) {
+           double *__restrict__ mdsum, int n_cta, int rounds, int sk, const __grid_constant__ FmtDev f) {
     extern __shared__ float smem[];
     const int B = f.B;
     const int kChunks = 8 * rounds - 2, kR = range_of(rounds);
@@ -70,8 +70,7 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
     float md_acc = 0.f;   // min distance at the chosen phase: the decision-directed noise
     const long out1 = min(out0 + kR, e);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float2 *yx = y + (long)s * 2 * y_stride;
-    const float2 *yy = yx + y_stride;
+    const long yoff = (long)s * 2 * y_stride;      // y of stream s: [2][y_stride], storage kind sk
     const int hw = W >> 1;
     const int S = f.S;
 
@@ -81,7 +80,7 @@ bps_kernel(const float2 *__restrict__ y, long y_stride, long a, long e, long n_v
         const long i = out0 + 32L * jc + lane;
         const bool valid = (i >= 0) && (i < n_valid);
         float2 ya = make_float2(0.f, 0.f), yb = make_float2(0.f, 0.f);
-        if (valid) { ya = yx[i]; yb = yy[i]; }
+        if (valid) { ya = ld_sample(y, yoff + i, sk); yb = ld_sample(y, yoff + y_stride + i, sk); }
         // per orbit o (and polarisation for 2D tables): CR = (Re c, Im c) and
         // CI = (Im c, -Re c), c = sum_p y_p conj(rep_p); then for a test phase,
         // (P, Q) = cos(phi) CR + sin(phi) CI is one packed multiply and one packed FMA
@@ -416,9 +415,9 @@ __global__ void dsum_kernel(const uint8_t *__restrict__ b, long b_stride, long a
 }
 
 template <int DIMS, int NORB>
-cudaError_t bps_launch_t(const float2 *y, long ys, long a, long e, long nv, int W, uint8_t *bout,
+cudaError_t bps_launch_t(const void *y, long ys, long a, long e, long nv, int W, uint8_t *bout,
                          long bst, int *dsum, double *mdsum, int rounds, int n_streams,
-                         const FmtDev &f, cudaStream_t st) {
+                         const FmtDev &f, cudaStream_t st, int sk) {
     const int kR = range_of(rounds);
     const int n_cta = (int)((e - a + kR - 1) / kR);
     const size_t smem = sizeof(float) * (RX_NCHUNK * f.B * 32 + RX_NCHUNK * f.B) + kR + 16;
@@ -426,7 +425,7 @@ cudaError_t bps_launch_t(const float2 *y, long ys, long a, long e, long nv, int 
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     dim3 grid((unsigned)n_cta, (unsigned)n_streams);
-    kern<<<grid, 256, smem, st>>>(y, ys, a, e, nv, W, bout, bst, dsum, mdsum, n_cta, rounds, f);
+    kern<<<grid, 256, smem, st>>>(y, ys, a, e, nv, W, bout, bst, dsum, mdsum, n_cta, rounds, sk, f);
     return cudaGetLastError();
 }
 
@@ -512,13 +511,13 @@ cudaError_t launch_dsum_from_b(const uint8_t *b, long b_stride, long a, long e, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_bps(const float2 *y, long y_stride, long a, long e, long n_valid, int W,
+cudaError_t launch_bps(const void *y, long y_stride, long a, long e, long n_valid, int W,
                        uint8_t *bout, long bout_stride, long bout_off, int *dsum, double *mdsum,
-                       int rounds, int n_streams, const FmtDev &f, cudaStream_t st) {
+                       int rounds, int n_streams, const FmtDev &f, cudaStream_t st, int sk) {
     if (e <= a || n_streams <= 0) return cudaSuccess;
     if (rounds < 1 || rounds > kMaxRounds || (f.B & 1)) return cudaErrorInvalidValue;
     uint8_t *bo = bout + bout_off;
-#define RX_BPS(DD, NO) return bps_launch_t<DD, NO>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, mdsum, rounds, n_streams, f, st)
+#define RX_BPS(DD, NO) return bps_launch_t<DD, NO>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, mdsum, rounds, n_streams, f, st, sk)
     if (f.dims == 4) {
         switch (f.n_orb) {
             case 16: RX_BPS(4, 16);

@@ -110,15 +110,16 @@ __device__ __forceinline__ float2 twid(const float2 *__restrict__ tw, int e, int
 // ---------------------------------------------------------------------------
 // 4096 points, 256 threads
 // ---------------------------------------------------------------------------
+template <int SK>
 __global__ void __launch_bounds__(256, 2)
-cdc4096_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, long ns, int S, int half,
+cdc4096_kernel(const float2 *__restrict__ in, typename Store<SK>::T *__restrict__ out, long ns, int S, int half,
                long f0, const float2 *__restrict__ H, const float2 *__restrict__ tw) {
     constexpr int RP = 257;   // padded row
     __shared__ float2 sm[16 * RP];
     const int t = threadIdx.x;
     const long f = f0 + blockIdx.x;
     const float2 *src = in + (long)blockIdx.y * ns;
-    float2 *dst = out + (long)blockIdx.y * ns;
+    typename Store<SK>::T *dst = out + (long)blockIdx.y * ns;
     const long start = f * S - half;
     float2 v[16];
 
@@ -191,7 +192,7 @@ cdc4096_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, long ns,
         const int pos = t + 256 * n1;
         if (pos >= half && pos < half + S) {
             long o = f * S + (pos - half);
-            if (o < ns) dst[o] = v[n1];
+            if (o < ns) Store<SK>::st(dst, o, v[n1]);
         }
     }
 }
@@ -199,8 +200,9 @@ cdc4096_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, long ns,
 // ---------------------------------------------------------------------------
 // 1024 points, one warp per frame
 // ---------------------------------------------------------------------------
+template <int SK>
 __global__ void __launch_bounds__(128)
-cdc1024_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, long ns, int S, int half,
+cdc1024_kernel(const float2 *__restrict__ in, typename Store<SK>::T *__restrict__ out, long ns, int S, int half,
                long f0, long f1, const float2 *__restrict__ H, const float2 *__restrict__ tw) {
     constexpr int RP = 33;
     __shared__ float2 smem[4][32 * RP];
@@ -209,7 +211,7 @@ cdc1024_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, long ns,
     if (f >= f1) return;
     float2 *sm = smem[w];
     const float2 *src = in + (long)blockIdx.y * ns;
-    float2 *dst = out + (long)blockIdx.y * ns;
+    typename Store<SK>::T *dst = out + (long)blockIdx.y * ns;
     const long start = f * S - half;
     float2 v[32];
 #pragma unroll
@@ -249,28 +251,42 @@ cdc1024_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, long ns,
         const int pos = l + 32 * n1;
         if (pos >= half && pos < half + S) {
             long o = f * S + (pos - half);
-            if (o < ns) dst[o] = v[n1];
+            if (o < ns) Store<SK>::st(dst, o, v[n1]);
         }
     }
 }
 
+
+
+template <int SK>
+cudaError_t cdc_t(const float2 *in, void *out, long ns, int n_streams2, int n_fft, int S, int half, long f0,
+                  long f1, const float2 *H, const float2 *tw, cudaStream_t st) {
+    auto *o = static_cast<typename Store<SK>::T *>(out);
+    if (n_fft == 4096) {
+        dim3 grid((unsigned)(f1 - f0), (unsigned)n_streams2);
+        cdc4096_kernel<SK><<<grid, 256, 0, st>>>(in, o, ns, S, half, f0, H, tw);
+    } else if (n_fft == 1024) {
+        dim3 grid((unsigned)((f1 - f0 + 3) / 4), (unsigned)n_streams2);
+        cdc1024_kernel<SK><<<grid, 128, 0, st>>>(in, o, ns, S, half, f0, f1, H, tw);
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-cudaError_t launch_cdc(const float2 *in, float2 *out, long ns, int n_streams2, int n_fft,
-                       int n_ov, const float2 *H, const float2 *tw, cudaStream_t st, long f0, long f1) {
+cudaError_t launch_cdc(const float2 *in, void *out, long ns, int n_streams2, int n_fft,
+                       int n_ov, const float2 *H, const float2 *tw, cudaStream_t st, long f0, long f1, int sk) {
     const int S = n_fft - n_ov, half = n_ov / 2;
     const long nframes = (ns + S - 1) / S;
     if (f1 < 0 || f1 > nframes) f1 = nframes;
     if (f0 < 0) f0 = 0;
     if (f1 <= f0 || n_streams2 <= 0) return cudaSuccess;
-    if (n_fft == 4096) {
-        dim3 grid((unsigned)(f1 - f0), (unsigned)n_streams2);
-        cdc4096_kernel<<<grid, 256, 0, st>>>(in, out, ns, S, half, f0, H, tw);
-    } else if (n_fft == 1024) {
-        dim3 grid((unsigned)((f1 - f0 + 3) / 4), (unsigned)n_streams2);
-        cdc1024_kernel<<<grid, 128, 0, st>>>(in, out, ns, S, half, f0, f1, H, tw);
-    } else {
-        return cudaErrorInvalidValue;
+    switch (sk) {
+        case SK_F32: return cdc_t<SK_F32>(in, out, ns, n_streams2, n_fft, S, half, f0, f1, H, tw, st);
+        case SK_F16: return cdc_t<SK_F16>(in, out, ns, n_streams2, n_fft, S, half, f0, f1, H, tw, st);
+        case SK_BF16: return cdc_t<SK_BF16>(in, out, ns, n_streams2, n_fft, S, half, f0, f1, H, tw, st);
+        default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }

@@ -403,13 +403,13 @@ constexpr int kTile = 1024;
 
 template <int DIMS, int MT, int MB>
 __global__ void __launch_bounds__(256, (DIMS == 4 ? 4 : 2))
-derot_demap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *__restrict__ bsrc,
+derot_demap_kernel(const void *__restrict__ y, long y_stride, const uint8_t *__restrict__ bsrc,
                    long b_stride, long a, long e, const int *__restrict__ dsum,
                    const double *__restrict__ mdsum, int n_rng, int kR,
                    const int32_t *__restrict__ carry_in, int cin_stride, int32_t *__restrict__ carry_out,
                    int cout_stride, uint16_t *__restrict__ pcode, long pc_stride,
                    const double *__restrict__ sigma2_fixed, double *__restrict__ sigma2_out, int s2_stride,
-                   float *__restrict__ llr, long llr_stride, DemapCount cnt, SymOut sym,
+                   float *__restrict__ llr, long llr_stride, DemapCount cnt, SymOut sym, int sk,
                    const __grid_constant__ FmtDev f) {
     constexpr int M_OUT = (DIMS == 4) ? MB : 2 * MB;
     constexpr int PT = kTile / 256;
@@ -504,8 +504,7 @@ derot_demap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *_
     }
     __syncthreads();
     const float c2 = c2_sh;
-    const float2 *yx = y + (long)s * 2 * y_stride;
-    const float2 *yy = yx + y_stride;
+    const long yoff = (long)s * 2 * y_stride;      // y of stream s: [2][y_stride], storage kind sk
     uint16_t *pc = pcode + (long)s * pc_stride;
     CountAcc acc;
     for (int u = 0; u < PT; ++u) {
@@ -522,7 +521,7 @@ derot_demap_kernel(const float2 *__restrict__ y, long y_stride, const uint8_t *_
         } else if (S == 2) {
             if (mq) rot = make_float2(-rot.x, -rot.y);
         }
-        const float2 z0 = cmul(yx[k], rot), z1 = cmul(yy[k], rot);
+        const float2 z0 = cmul(ld_sample(y, yoff + k, sk), rot), z1 = cmul(ld_sample(y, yoff + y_stride + k, sk), rot);
         if (active) {
             pc[k - a] = (uint16_t)(b | (mq << 8));
             if (sym.x4)
@@ -604,15 +603,15 @@ cudaError_t demap_t(const float2 *z, long zs, long a, long e, const double *s2, 
 }
 
 template <int DIMS, int MT, int MB>
-cudaError_t derot_demap_t(const float2 *y, long ys, const uint8_t *b, long bst, long a, long e,
+cudaError_t derot_demap_t(const void *y, long ys, const uint8_t *b, long bst, long a, long e,
                           const int *dsum, const double *mdsum, int kR, const int32_t *cin, int cis,
                           int32_t *cout, int cos, uint16_t *pc, long pcs, const double *s2f, double *s2o,
                           int s2s, float *llr, long ls, const DemapCount &cnt, const SymOut &sym, int n_streams,
-                          const FmtDev &f, cudaStream_t st) {
+                          const FmtDev &f, cudaStream_t st, int sk) {
     const int n_rng = (int)((e - a + kR - 1) / kR);
     dim3 grid((unsigned)((e - a + kTile - 1) / kTile), (unsigned)n_streams);
     derot_demap_kernel<DIMS, MT, MB><<<grid, 256, 0, st>>>(y, ys, b, bst, a, e, dsum, mdsum, n_rng, kR, cin, cis,
-                                                           cout, cos, pc, pcs, s2f, s2o, s2s, llr, ls, cnt, sym, f);
+                                                           cout, cos, pc, pcs, s2f, s2o, s2s, llr, ls, cnt, sym, sk, f);
     return cudaGetLastError();
 }
 
@@ -620,19 +619,19 @@ cudaError_t derot_demap_t(const float2 *y, long ys, const uint8_t *b, long bst, 
 
 long derot_demap_ctas(long len) { return (len + kTile - 1) / kTile; }
 
-cudaError_t launch_derot_demap(const float2 *y, long y_stride, const uint8_t *b, long b_stride,
+cudaError_t launch_derot_demap(const void *y, long y_stride, const uint8_t *b, long b_stride,
                                long a, long e, const int *dsum, const double *mdsum, int kR,
                                const int32_t *carry_in, int cin_stride, int32_t *carry_out,
                                int cout_stride, uint16_t *pcode, long pc_stride,
                                const double *sigma2_fixed, double *sigma2_out, int s2_stride,
                                float *llr, long llr_stride, const DemapCount &cnt, const SymOut &sym,
-                               int n_streams, const FmtDev &f, cudaStream_t st) {
+                               int n_streams, const FmtDev &f, cudaStream_t st, int sk) {
     if (e <= a || n_streams <= 0) return cudaSuccess;
     if (!cnt.sd || !cnt.partial || !mdsum) return cudaErrorInvalidValue;
 #define RX_DD(D_, M_, B_)                                                                                  \
     return derot_demap_t<D_, M_, B_>(y, y_stride, b, b_stride, a, e, dsum, mdsum, kR, carry_in, cin_stride, \
                                      carry_out, cout_stride, pcode, pc_stride, sigma2_fixed, sigma2_out,    \
-                                     s2_stride, llr, llr_stride, cnt, sym, n_streams, f, st)
+                                     s2_stride, llr, llr_stride, cnt, sym, n_streams, f, st, sk)
     if (f.dims == 4 && f.M == 64) RX_DD(4, 64, 6);
     if (f.dims == 2 && f.M == 4) RX_DD(2, 4, 2);
     if (f.dims == 2 && f.M == 16) RX_DD(2, 16, 4);

@@ -19,57 +19,61 @@ constexpr int kThreads = 128;
 
 __device__ __forceinline__ int pad8(int i) { return i + (i >> 3); }
 
-__device__ __forceinline__ void cp_async8(void *dst, const void *src, bool valid) {
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *dst, const void *src, bool valid) {
     const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;" ::"r"(d), "l"(src), "r"(valid ? 8 : 0));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;" ::"r"(d), "l"(src), "n"(BYTES),
+                 "r"(valid ? BYTES : 0));
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N)); }
 
-template <int T>
+template <int T, int SK>
 struct FirSmem {
+    using X = typename Store<SK>::T;
     static constexpr int D = (T - 1) / 2;
     static constexpr int NS = 2 * kOut + 2 * D;
     static constexpr int NSP = NS + NS / 8 + 1;
-    float2 xs[2][2][NSP];    // [buffer][p]
+    X xs[2][2][NSP];         // [buffer][p], the storage type of x
     float2 hraw[2][4 * T];   // [buffer] taps h[q][p][t] of the tile's stream
     f32x2 hA[2][2][T];       // [q][p][t] (a, a)
     f32x2 hB[2][2][T];       // [q][p][t] (-b, b), conj(h) = a + jb
 };
 
 // stage tile `tile` (stream s = tile / tps) into buffer `buf`
-template <int T>
-__device__ __forceinline__ void fir_stage(FirSmem<T> &sm, int buf, int tile, int tps, const float2 *x,
-                                          long ns, const float2 *taps, long k0) {
-    constexpr int D = FirSmem<T>::D, NS = FirSmem<T>::NS;
+template <int T, int SK>
+__device__ __forceinline__ void fir_stage(FirSmem<T, SK> &sm, int buf, int tile, int tps,
+                                          const typename Store<SK>::T *x, long ns, const float2 *taps, long k0) {
+    constexpr int D = FirSmem<T, SK>::D, NS = FirSmem<T, SK>::NS;
+    constexpr int XB = sizeof(typename Store<SK>::T);
     const int s = tile / tps, tl = tile - s * tps;
     const long base = 2 * (k0 + (long)tl * kOut) - D;   // global sample of local index 0
-    const float2 *xs0 = x + (long)s * 2 * ns;
+    const typename Store<SK>::T *xs0 = x + (long)s * 2 * ns;
     for (int i = threadIdx.x; i < 2 * NS; i += kThreads) {
         const int p = i / NS, j = i - p * NS;
         const long g = base + j;
         const bool ok = g >= 0 && g < ns;
-        cp_async8(&sm.xs[buf][p][pad8(j)], xs0 + (long)p * ns + (ok ? g : 0), ok);
+        cp_async<XB>(&sm.xs[buf][p][pad8(j)], xs0 + (long)p * ns + (ok ? g : 0), ok);
     }
     for (int i = threadIdx.x; i < 4 * T; i += kThreads)
-        cp_async8(&sm.hraw[buf][i], taps + (long)s * 4 * T + i, true);
+        cp_async<8>(&sm.hraw[buf][i], taps + (long)s * 4 * T + i, true);
     cp_async_commit();
 }
 
-template <int T>
+template <int T, int SK>
 __global__ void __launch_bounds__(kThreads)
-fir_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ taps, long k0,
-           long k1, float2 *__restrict__ y, long y_stride, long y_off, int tps, int n_tiles) {
+fir_kernel(const typename Store<SK>::T *__restrict__ x, long ns, const float2 *__restrict__ taps, long k0,
+           long k1, typename Store<SK>::T *__restrict__ y, long y_stride, long y_off, int tps, int n_tiles) {
     constexpr int D = (T - 1) / 2;
-    __shared__ __align__(16) FirSmem<T> sm;
+    __shared__ __align__(16) FirSmem<T, SK> sm;
     const int tid = threadIdx.x;
     int tile = blockIdx.x, buf = 0;
-    if (tile < n_tiles) fir_stage<T>(sm, 0, tile, tps, x, ns, taps, k0);
+    if (tile < n_tiles) fir_stage<T, SK>(sm, 0, tile, tps, x, ns, taps, k0);
     for (; tile < n_tiles; tile += gridDim.x, buf ^= 1) {
         const int next = tile + gridDim.x;
         if (next < n_tiles) {
-            fir_stage<T>(sm, buf ^ 1, next, tps, x, ns, taps, k0);
+            fir_stage<T, SK>(sm, buf ^ 1, next, tps, x, ns, taps, k0);
             cp_async_wait<1>();
         } else {
             cp_async_wait<0>();
@@ -92,12 +96,12 @@ fir_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
         const int lb = 8 * tid + 2 * D;   // local index of (r = 0, t = 0)
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
-            const float2 *xp = sm.xs[buf][p];
+            const typename Store<SK>::T *xp = sm.xs[buf][p];
             // even / odd tap chains: E[r] = x[lb + 2r - 2j], O[r] = x[lb + 2r - 2j - 1],
             // each kept as (xr, xi) and swapped (xi, xr)
             f32x2 E[4], Es[4], O[4], Os[4];
             auto ld = [&](int i, f32x2 &v, f32x2 &vs) {
-                const float2 a = xp[pad8(i)];
+                const float2 a = Store<SK>::ld(xp, pad8(i));
                 v = pk2(a.x, a.y);
                 vs = pk2(a.y, a.x);
             };
@@ -140,12 +144,12 @@ fir_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
         const long kt = k0 + (long)tl * kOut + 4 * tid;
 #pragma unroll
         for (int q = 0; q < 2; ++q) {
-            float2 *yq = y + ((long)s * 2 + q) * y_stride + y_off;
+            typename Store<SK>::T *yq = y + ((long)s * 2 + q) * y_stride + y_off;
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 float re, im;
                 upk2(acc[q][r], re, im);
-                if (kt + r < k1) yq[kt + r - k0] = make_float2(re, im);
+                if (kt + r < k1) Store<SK>::st(yq, kt + r - k0, make_float2(re, im));
             }
         }
         __syncthreads();   // buffer `buf` is restaged two tiles later
@@ -163,20 +167,36 @@ int fir_blocks_per_sm() {
     return n;
 }
 
+
+
+template <int SK>
+cudaError_t fir_t(const void *x, long ns, const float2 *taps, long k0, long k1, void *y, long y_stride,
+                  long y_off, int T, int grid, long tps, long n_tiles, cudaStream_t st) {
+    using X = typename Store<SK>::T;
+    const X *xx = static_cast<const X *>(x);
+    X *yy = static_cast<X *>(y);
+    switch (T) {
+        case 7: fir_kernel<7, SK><<<grid, kThreads, 0, st>>>(xx, ns, taps, k0, k1, yy, y_stride, y_off, (int)tps, (int)n_tiles); break;
+        case 15: fir_kernel<15, SK><<<grid, kThreads, 0, st>>>(xx, ns, taps, k0, k1, yy, y_stride, y_off, (int)tps, (int)n_tiles); break;
+        case 31: fir_kernel<31, SK><<<grid, kThreads, 0, st>>>(xx, ns, taps, k0, k1, yy, y_stride, y_off, (int)tps, (int)n_tiles); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-cudaError_t launch_fir(const float2 *x, long ns, const float2 *taps, long k0, long k1, float2 *y,
-                       long y_stride, long y_off, int n_streams, int T, cudaStream_t st) {
+cudaError_t launch_fir(const void *x, long ns, const float2 *taps, long k0, long k1, void *y,
+                       long y_stride, long y_off, int n_streams, int T, cudaStream_t st, int sk) {
     if (k1 <= k0 || n_streams <= 0) return cudaSuccess;
     const long tps = (k1 - k0 + kOut - 1) / kOut;
     const long n_tiles = tps * n_streams;
     if (n_tiles > (1L << 30)) return cudaErrorInvalidValue;
     const int grid = (int)std::min<long>(n_tiles, fir_blocks_per_sm());
-    switch (T) {
-        case 7: fir_kernel<7><<<grid, kThreads, 0, st>>>(x, ns, taps, k0, k1, y, y_stride, y_off, (int)tps, (int)n_tiles); break;
-        case 15: fir_kernel<15><<<grid, kThreads, 0, st>>>(x, ns, taps, k0, k1, y, y_stride, y_off, (int)tps, (int)n_tiles); break;
-        case 31: fir_kernel<31><<<grid, kThreads, 0, st>>>(x, ns, taps, k0, k1, y, y_stride, y_off, (int)tps, (int)n_tiles); break;
+    switch (sk) {
+        case SK_F32: return fir_t<SK_F32>(x, ns, taps, k0, k1, y, y_stride, y_off, T, grid, tps, n_tiles, st);
+        case SK_F16: return fir_t<SK_F16>(x, ns, taps, k0, k1, y, y_stride, y_off, T, grid, tps, n_tiles, st);
+        case SK_BF16: return fir_t<SK_BF16>(x, ns, taps, k0, k1, y, y_stride, y_off, T, grid, tps, n_tiles, st);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }

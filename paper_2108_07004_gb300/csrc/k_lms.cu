@@ -100,10 +100,10 @@ __device__ __forceinline__ void reduce_pair(float2 a, float2 b, int p, float2 &y
 // for the staged span) is on the sequential path.
 template <int T, int DIMS, int MODE>
 __global__ void __launch_bounds__(256, 1)
-lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ taps_in,
+lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_in,
            float2 *__restrict__ taps_out, long k0, int n_upd, const uint16_t *__restrict__ pcode,
            long pcode_stride, int passes, float mu, const uint8_t *__restrict__ ref_lab,
-           long ref_stride, const __grid_constant__ FmtDev f) {
+           long ref_stride, int sk, const __grid_constant__ FmtDev f) {
     constexpr int D = (T - 1) / 2;
     constexpr int NSX = 2 * kCH + 2 * D + 8;   // + slack read by the look-ahead past the span
     constexpr int NT = (T + 15) / 16;
@@ -130,7 +130,7 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
             const int t = j + 16 * i;
             h[q][i] = (t < T) ? taps_in[(((long)s * 2 + q) * 2 + p) * T + t] : make_float2(0.f, 0.f);
         }
-    const float2 *xsrc = x + (long)s * 2 * ns;
+    const long xoff = (long)s * 2 * ns;
     const int qt_step = 4 / f.S;
     for (int pass = 0; pass < passes; ++pass) {
         for (int c0 = 0; c0 < n_upd; c0 += kCH) {
@@ -142,7 +142,7 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
             for (int i = threadIdx.x; i < 2 * nsx; i += blockDim.x) {
                 const int pp = i / nsx, jj = i - pp * nsx;
                 const long g = 2 * (kb - 1) - D + jj;
-                xs[pp][jj] = (g >= 0 && g < ns) ? xsrc[(long)pp * ns + g] : make_float2(0.f, 0.f);
+                xs[pp][jj] = (g >= 0 && g < ns) ? ld_sample(x, xoff + (long)pp * ns + g, sk) : make_float2(0.f, 0.f);
             }
             if (MODE != 0)
                 for (int i = threadIdx.x; i < n; i += blockDim.x) pc[i] = pcode[(long)s * pcode_stride + kb + i];
@@ -286,8 +286,8 @@ lms_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ tap
 // ---------------------------------------------------------------------------
 template <int T, int DIMS>
 __global__ void __launch_bounds__(256)
-align_kernel(const float2 *__restrict__ x, long ns, float2 *__restrict__ taps,
-             const uint8_t *__restrict__ ref_lab, long ref_stride, int n_train,
+align_kernel(const void *__restrict__ x, long ns, float2 *__restrict__ taps,
+             const uint8_t *__restrict__ ref_lab, long ref_stride, int n_train, int sk,
              const __grid_constant__ FmtDev f) {
     constexpr int D = (T - 1) / 2;
     __shared__ float2 hs[4 * T];
@@ -297,7 +297,7 @@ align_kernel(const float2 *__restrict__ x, long ns, float2 *__restrict__ taps,
     const int s = blockIdx.x, tid = threadIdx.x;
     for (int i = tid; i < 4 * T; i += 256) hs[i] = taps[(long)s * 4 * T + i];
     __syncthreads();
-    const float2 *xs = x + (long)s * 2 * ns;
+    const long xoff = (long)s * 2 * ns;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // C[q][p] re, im
     for (int k = tid; k < n_train; k += 256) {
         float2 y[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
@@ -307,7 +307,7 @@ align_kernel(const float2 *__restrict__ x, long ns, float2 *__restrict__ taps,
                     const long g = 2L * k + D - t;
                     if (g < 0 || g >= ns) continue;
                     const float2 hv = hs[(qq * 2 + pp) * T + t];
-                    const float2 xv = xs[(long)pp * ns + g];
+                    const float2 xv = ld_sample(x, xoff + (long)pp * ns + g, sk);
                     y[qq] = cadd(y[qq], cmulc(hv, xv));
                 }
         const int lab = ref_lab[(long)s * ref_stride + k];
@@ -364,17 +364,17 @@ align_kernel(const float2 *__restrict__ x, long ns, float2 *__restrict__ taps,
 //   b = n_k + B/2 - m B, m = floor((n_k + B/2) / B).
 template <int T, int DIMS>
 __global__ void __launch_bounds__(256)
-train_phase_kernel(const float2 *__restrict__ x, long ns, const float2 *__restrict__ taps,
+train_phase_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps,
                    const uint8_t *__restrict__ ref_lab, long ref_stride, int n, int W,
                    uint16_t *__restrict__ pcode, long pcode_stride, int32_t *__restrict__ carry,
-                   int carry_stride, const __grid_constant__ FmtDev f) {
+                   int carry_stride, int sk, const __grid_constant__ FmtDev f) {
     constexpr int D = (T - 1) / 2;
     extern __shared__ float2 rs[];      // [n] per-symbol correlations
     __shared__ float2 hs[4 * T];
     const int s = blockIdx.x, tid = threadIdx.x;
     for (int i = tid; i < 4 * T; i += 256) hs[i] = taps[(long)s * 4 * T + i];
     __syncthreads();
-    const float2 *xs = x + (long)s * 2 * ns;
+    const long xoff = (long)s * 2 * ns;
     for (int k = tid; k < n; k += 256) {
         float2 y[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         for (int qq = 0; qq < 2; ++qq)
@@ -382,7 +382,7 @@ train_phase_kernel(const float2 *__restrict__ x, long ns, const float2 *__restri
                 for (int t = 0; t < T; ++t) {
                     const long g = 2L * k + D - t;
                     if (g < 0 || g >= ns) continue;
-                    y[qq] = cadd(y[qq], cmulc(hs[(qq * 2 + pp) * T + t], xs[(long)pp * ns + g]));
+                    y[qq] = cadd(y[qq], cmulc(hs[(qq * 2 + pp) * T + t], ld_sample(x, xoff + (long)pp * ns + g, sk)));
                 }
         const int lab = ref_lab[(long)s * ref_stride + k];
         float2 s0, s1;
@@ -430,9 +430,9 @@ __global__ void ref_labels_kernel(const uint8_t *__restrict__ bits, uint8_t *__r
 // shared memory so that no other kernel's blocks share its SM and its warp
 // issues whenever it is ready.
 template <int T, int DIMS, int MODE>
-cudaError_t lms_launch_one(const float2 *x, long ns, const float2 *ti, float2 *to, long k0, int n_upd,
+cudaError_t lms_launch_one(const void *x, long ns, const float2 *ti, float2 *to, long k0, int n_upd,
                            const uint16_t *pcode, long pstride, int passes, float mu,
-                           const uint8_t *ref, long rstride, int S, const FmtDev &f, cudaStream_t st) {
+                           const uint8_t *ref, long rstride, int S, const FmtDev &f, cudaStream_t st, int sk) {
     auto kern = lms_kernel<T, DIMS, MODE>;
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, kern);
@@ -444,45 +444,45 @@ cudaError_t lms_launch_one(const float2 *x, long ns, const float2 *ti, float2 *t
     if (dyn < (int)(3 * kCH * sizeof(float2))) return cudaErrorInvalidValue;   // rotations, targets
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
-    kern<<<S, 256, dyn, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, f);
+    kern<<<S, 256, dyn, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, sk, f);
     return cudaGetLastError();
 }
 
 template <int T, int MODE>
-cudaError_t lms_launch_mode(const float2 *x, long ns, const float2 *ti, float2 *to, long k0,
+cudaError_t lms_launch_mode(const void *x, long ns, const float2 *ti, float2 *to, long k0,
                             int n_upd, const uint16_t *pcode, long pstride, int passes, float mu,
                             const uint8_t *ref, long rstride, int S, const FmtDev &f,
-                            cudaStream_t st) {
+                            cudaStream_t st, int sk) {
     if (f.dims == 4)
         return lms_launch_one<T, 4, MODE>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref,
-                                          rstride, S, f, st);
+                                          rstride, S, f, st, sk);
     return lms_launch_one<T, 2, MODE>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref,
-                                      rstride, S, f, st);
+                                      rstride, S, f, st, sk);
 }
 
 template <int T>
-cudaError_t lms_dispatch_dims(const float2 *x, long ns, const float2 *ti, float2 *to, long k0,
+cudaError_t lms_dispatch_dims(const void *x, long ns, const float2 *ti, float2 *to, long k0,
                               int n_upd, const uint16_t *pcode, long pstride, int mode,
                               int passes, unsigned long long u0, int n_cma, float mu,
                               const uint8_t *ref, long rstride, int S, const FmtDev &f,
-                              cudaStream_t st) {
+                              cudaStream_t st, int sk) {
     switch (mode) {
-        case 0: return lms_launch_mode<T, 0>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st);
-        case 1: return lms_launch_mode<T, 1>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st);
-        case 3: return lms_launch_mode<T, 3>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st);
+        case 0: return lms_launch_mode<T, 0>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk);
+        case 1: return lms_launch_mode<T, 1>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk);
+        case 3: return lms_launch_mode<T, 3>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk);
         case 2: {
             // CMA while the update count is below n_cma, DD after (one pass)
             const long ncma = (u0 >= (unsigned long long)n_cma) ? 0 : std::min<long>(n_upd, (long)(n_cma - u0));
             cudaError_t e = cudaSuccess;
             const float2 *src = ti;
             if (ncma > 0) {
-                e = lms_launch_mode<T, 0>(x, ns, src, to, k0, (int)ncma, pcode, pstride, 1, mu, ref, rstride, S, f, st);
+                e = lms_launch_mode<T, 0>(x, ns, src, to, k0, (int)ncma, pcode, pstride, 1, mu, ref, rstride, S, f, st, sk);
                 if (e != cudaSuccess) return e;
                 src = to;
             }
             if (n_upd - ncma > 0)
                 e = lms_launch_mode<T, 1>(x, ns, src, to, k0 + ncma, (int)(n_upd - ncma), pcode, pstride, 1, mu,
-                                          ref, rstride, S, f, st);
+                                          ref, rstride, S, f, st, sk);
             return e;
         }
         default: return cudaErrorInvalidValue;
@@ -490,21 +490,21 @@ cudaError_t lms_dispatch_dims(const float2 *x, long ns, const float2 *ti, float2
 }
 
 template <int T>
-cudaError_t align_dispatch(const float2 *x, long ns, float2 *taps, const uint8_t *ref,
-                           long rstride, int n_train, int S, const FmtDev &f, cudaStream_t st) {
+cudaError_t align_dispatch(const void *x, long ns, float2 *taps, const uint8_t *ref,
+                           long rstride, int n_train, int S, const FmtDev &f, cudaStream_t st, int sk) {
     if (f.dims == 4)
-        align_kernel<T, 4><<<S, 256, 0, st>>>(x, ns, taps, ref, rstride, n_train, f);
+        align_kernel<T, 4><<<S, 256, 0, st>>>(x, ns, taps, ref, rstride, n_train, sk, f);
     else
-        align_kernel<T, 2><<<S, 256, 0, st>>>(x, ns, taps, ref, rstride, n_train, f);
+        align_kernel<T, 2><<<S, 256, 0, st>>>(x, ns, taps, ref, rstride, n_train, sk, f);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-cudaError_t launch_lms(const float2 *x, long ns, const float2 *taps_in, float2 *taps_out, long k0,
+cudaError_t launch_lms(const void *x, long ns, const float2 *taps_in, float2 *taps_out, long k0,
                        int n_upd, const uint16_t *pcode, long pcode_stride, int mode, int passes,
                        unsigned long long u0, int n_cma, float mu, const uint8_t *ref_lab,
-                       long ref_stride, int n_streams, int T, const FmtDev &f, cudaStream_t st) {
+                       long ref_stride, int n_streams, int T, const FmtDev &f, cudaStream_t st, int sk) {
     if (n_upd <= 0 || n_streams <= 0) {
         if (taps_in != taps_out)
             return cudaMemcpyAsync(taps_out, taps_in, sizeof(float2) * 4 * T * (size_t)n_streams,
@@ -512,29 +512,29 @@ cudaError_t launch_lms(const float2 *x, long ns, const float2 *taps_in, float2 *
         return cudaSuccess;
     }
     switch (T) {
-        case 7: return lms_dispatch_dims<7>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st);
-        case 15: return lms_dispatch_dims<15>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st);
-        case 31: return lms_dispatch_dims<31>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st);
+        case 7: return lms_dispatch_dims<7>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk);
+        case 15: return lms_dispatch_dims<15>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk);
+        case 31: return lms_dispatch_dims<31>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_align(const float2 *x, long ns, float2 *taps, const uint8_t *ref_lab,
+cudaError_t launch_align(const void *x, long ns, float2 *taps, const uint8_t *ref_lab,
                          long ref_stride, int n_train, int n_streams, int T, const FmtDev &f,
-                         cudaStream_t st) {
+                         cudaStream_t st, int sk) {
     if (n_train <= 0 || n_streams <= 0) return cudaSuccess;
     switch (T) {
-        case 7: return align_dispatch<7>(x, ns, taps, ref_lab, ref_stride, n_train, n_streams, f, st);
-        case 15: return align_dispatch<15>(x, ns, taps, ref_lab, ref_stride, n_train, n_streams, f, st);
-        case 31: return align_dispatch<31>(x, ns, taps, ref_lab, ref_stride, n_train, n_streams, f, st);
+        case 7: return align_dispatch<7>(x, ns, taps, ref_lab, ref_stride, n_train, n_streams, f, st, sk);
+        case 15: return align_dispatch<15>(x, ns, taps, ref_lab, ref_stride, n_train, n_streams, f, st, sk);
+        case 31: return align_dispatch<31>(x, ns, taps, ref_lab, ref_stride, n_train, n_streams, f, st, sk);
         default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_train_phase(const float2 *x, long ns, const float2 *taps, const uint8_t *ref_lab,
+cudaError_t launch_train_phase(const void *x, long ns, const float2 *taps, const uint8_t *ref_lab,
                                long ref_stride, int n, int W, uint16_t *pcode, long pcode_stride,
                                int32_t *carry, int carry_stride, int n_streams, int T,
-                               const FmtDev &f, cudaStream_t st) {
+                               const FmtDev &f, cudaStream_t st, int sk) {
     if (n <= 0 || n_streams <= 0) return cudaSuccess;
     const size_t smem = sizeof(float2) * (size_t)n;
     if (smem > 160 * 1024) return cudaErrorInvalidValue;
@@ -545,7 +545,7 @@ cudaError_t launch_train_phase(const float2 *x, long ns, const float2 *taps, con
                                               (int)smem);                                     \
         if (e_ != cudaSuccess) return e_;                                                      \
         k_<<<n_streams, 256, smem, st>>>(x, ns, taps, ref_lab, ref_stride, n, W, pcode,        \
-                                         pcode_stride, carry, carry_stride, f);                \
+                                         pcode_stride, carry, carry_stride, sk, f);            \
     } while (0)
     const bool d4 = f.dims == 4;
     switch (T) {

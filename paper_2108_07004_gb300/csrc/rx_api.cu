@@ -91,7 +91,8 @@ struct rx_handle {
     // device buffers
     long cap_n = 0;
     int cap_s = 0, cap_lag = 0;
-    float2 *x = nullptr, *y = nullptr, *ring = nullptr;
+    void *x = nullptr, *y = nullptr;                  // CDC and FIR outputs, storage kind prec
+    float2 *ring = nullptr;
     uint8_t *bidx = nullptr;
     uint16_t *pcode = nullptr;
     int *dsum = nullptr;
@@ -106,6 +107,8 @@ struct rx_handle {
     // stream state (host mirror of the scalars)
     bool started = false;
     bool trained = false;
+    int prec = SK_F32;                                // storage of x and y (precision variant)
+    int cap_prec = -1;
     // learned demapper (null: exact log-sum-exp) and symbol outputs
     rx_mlp *mlp = nullptr;
     float *user_x4 = nullptr, *user_s2 = nullptr;   // caller's [S][N][4], [S][N]
@@ -331,13 +334,13 @@ int ensure_symbol_buffers(rx_handle *h, long N) {
 
 int ensure_buffers(rx_handle *h, long N) {
     const int S = h->streams;
-    if (h->cap_n >= N && h->cap_s == S && h->cap_lag == h->lag && h->sd) return RX_OK;
+    if (h->cap_n >= N && h->cap_s == S && h->cap_lag == h->lag && h->cap_prec == h->prec && h->sd) return RX_OK;
     free_buffers(h);
     const long ns = 2 * N;
     const long ncta = (N + bps_cta_range(1) - 1) / bps_cta_range(1) + 2;
     const long ncta_d = (h->block + 2 * h->W + 255) / 256 + 2;
-    CK(cudaMalloc(&h->x, sizeof(float2) * (size_t)S * 2 * ns));
-    CK(cudaMalloc(&h->y, sizeof(float2) * (size_t)S * 2 * N));
+    CK(cudaMalloc(&h->x, store_bytes(h->prec) * (size_t)S * 2 * ns));
+    CK(cudaMalloc(&h->y, store_bytes(h->prec) * (size_t)S * 2 * N));
     CK(cudaMalloc(&h->ring, sizeof(float2) * (size_t)(h->lag + 1) * S * 4 * h->T));
     CK(cudaMalloc(&h->bidx, (size_t)S * N));
     CK(cudaMalloc(&h->pcode, sizeof(uint16_t) * (size_t)S * N));
@@ -354,6 +357,7 @@ int ensure_buffers(rx_handle *h, long N) {
     h->cap_n = N;
     h->cap_s = S;
     h->cap_lag = h->lag;
+    h->cap_prec = h->prec;
     return RX_OK;
 }
 
@@ -447,16 +451,16 @@ void prof_end(rx_handle *h, int stage, cudaEvent_t a, cudaStream_t s, int launch
 // it runs blind): output order and phases from the correlation with the
 // known symbols, data-aided phase codes over the span, then train_passes
 // passes of data-aided LMS.  Taps are updated in place.
-int train_stage(rx_handle *h, const float2 *x, long ns, float2 *taps, long ntr, uint16_t *pcode,
-                long pcode_stride, int32_t *carry, int carry_stride, cudaStream_t st) {
+int train_stage(rx_handle *h, const void *x, long ns, float2 *taps, long ntr, uint16_t *pcode,
+                long pcode_stride, int32_t *carry, int carry_stride, cudaStream_t st, int sk) {
     const int S = h->streams, T = h->T;
-    STAGE(ST_STARTUP, st, 1, launch_align(x, ns, taps, h->ref, h->ref_n, (int)ntr, S, T, h->fmt, st));
+    STAGE(ST_STARTUP, st, 1, launch_align(x, ns, taps, h->ref, h->ref_n, (int)ntr, S, T, h->fmt, st, sk));
     STAGE(ST_STARTUP, st, 1, launch_train_phase(x, ns, taps, h->ref, h->ref_n, (int)ntr, h->W, pcode,
-                                                pcode_stride, carry, carry_stride, S, T, h->fmt, st));
+                                                pcode_stride, carry, carry_stride, S, T, h->fmt, st, sk));
     if (h->train_passes > 0)
         STAGE(ST_STARTUP, st, 1, launch_lms(x, ns, taps, taps, 0, (int)ntr, pcode, pcode_stride, 3,
                                             h->train_passes, 0, 0, (float)h->mu, h->ref, h->ref_n,
-                                            S, T, h->fmt, st));
+                                            S, T, h->fmt, st, sk));
     return RX_OK;
 }
 
@@ -491,12 +495,14 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         h->blk.clear();
         for (auto &c : h->nlaunch) c = 0;
         if (fs > f0) {
-            STAGE(ST_CDC, st, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st, f0, fs));
+            STAGE(ST_CDC, st, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st, f0, fs,
+                                            h->prec));
             CK(cudaEventRecord(h->ev_cdc0, st));
             CK(cudaStreamWaitEvent(h->side, h->ev_cdc0, 0));
         }
         if (f1 > fs)
-            STAGE(ST_CDC, st, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st, fs, f1));
+            STAGE(ST_CDC, st, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st, fs, f1,
+                                            h->prec));
     }
     if (b0 == 0) {
         const cudaStream_t ss = h->side;     // start-up stream
@@ -506,7 +512,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         CK(cudaMemcpyAsync(w0, cs.data(), tapsz, cudaMemcpyHostToDevice, ss));
         const long npre = std::min(h->n_pre, N);
         STAGE(ST_STARTUP, ss, 1, launch_lms(h->x, ns, w0, w0, 0, (int)npre, nullptr, 0, 0, h->cma_passes,
-                                            0, 0, (float)h->mu, nullptr, 0, S, T, f, ss));
+                                            0, 0, (float)h->mu, nullptr, 0, S, T, f, ss, h->prec));
         // stream state: counters zero, unwrap carry phi_hat = 0
         std::vector<StreamDev> &sd0 = h->h_sd0;
         sd0.assign(S, StreamDev{});
@@ -517,7 +523,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         h->trained = false;
         if (h->ref && ntr > 0 && h->ref_n >= ntr) {
             h->trained = true;
-            int rc2 = train_stage(h, h->x, ns, w0, ntr, h->pcode, N, nullptr, 0, ss);
+            int rc2 = train_stage(h, h->x, ns, w0, ntr, h->pcode, N, nullptr, 0, ss, h->prec);
             if (rc2 != RX_OK) return rc2;
         }
         for (int i = 1; i <= L; ++i) CK(cudaMemcpyAsync(slot(h, i), w0, tapsz, cudaMemcpyDeviceToDevice, ss));
@@ -561,12 +567,12 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         const float2 *wn = slot(h, n - L);
         cudaEvent_t blk0 = nullptr;
         if (h->profile && (blk0 = prof_event(h))) CK(cudaEventRecord(blk0, st));
-        STAGE(ST_FIR, st, 1, launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st));
+        STAGE(ST_FIR, st, 1, launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st, h->prec));
         const long a = std::max(0L, k0 - h->W / 2);
         const long e = (n == nblk - 1) ? N : k1 - h->W / 2;
         const int rounds = bps_rounds(e - a, S);
         STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, h->dsum, h->mdsum, rounds, S,
-                                        f, st));
+                                        f, st, h->prec));
         const int cin = (int)(n & 1), cout = 1 - cin;
         if (n == 0 && h->trained) {
             // the training phases fix the start quadrant of the unwrap
@@ -581,7 +587,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
               launch_derot_demap(h->y, N, h->bidx + a, N, a, e, h->dsum, h->mdsum, bps_cta_range(rounds),
                                  carry_base + 2 * cin, (int)sd_stride, carry_base + 2 * cout, (int)sd_stride,
                                  h->pcode + a, N, h->sigma2_fixed > 0 ? h->sig_fixed : nullptr, h->sig, 1,
-                                 h->mlp ? nullptr : llr + (size_t)a * m, N * m, cnt, sym, S, f, st));
+                                 h->mlp ? nullptr : llr + (size_t)a * m, N * m, cnt, sym, S, f, st, h->prec));
         if (h->mlp) {
             for (int s = 0; s < S; ++s)
                 STAGE(ST_DEMAP, st, 3,
@@ -603,7 +609,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         }
         STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
               launch_lms(h->x, ns, slot(h, n - 1), slot(h, n), k0, (int)span, h->pcode, N, 2, 1,
-                         h->u, (int)h->n_cma, (float)h->mu, nullptr, 0, S, T, f, ls));
+                         h->u, (int)h->n_cma, (float)h->mu, nullptr, 0, S, T, f, ls, h->prec));
         if (L >= 2) CK(cudaEventRecord(h->ev_lms[n % (L + 1)], h->side));
         h->u += span;
         h->blocks_done = n + 1;
@@ -662,6 +668,7 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     else if (k == "rolloff") { if (!(v > 0 && v <= 1)) return fail(RX_EINVAL, "rolloff out of range"); h->rolloff = v; h->tables_dirty = true; }
     else if (k == "wavelength_nm") { if (!(v > 100 && v < 10000)) return fail(RX_EINVAL, "wavelength out of range"); h->wavelength = v * 1e-9; h->tables_dirty = true; }
     else if (k == "profile") { h->profile = v != 0; return RX_OK; }
+    else if (k == "precision") { rc = as_int(0, 2, t); h->prec = (int)t; }
     else return fail(RX_EINVAL, "unknown parameter '%s'", k.c_str());
     if (rc != RX_OK) return rc;
     if (k == "overlap") h->tables_dirty = true;
@@ -816,6 +823,7 @@ int rx_get_param(const rx_handle *h, const char *key, double *value) {
     else if (k == "bps_phases") *value = h->B;
     else if (k == "cd_ps_per_nm") *value = h->cd;
     else if (k == "profile") *value = h->profile ? 1 : 0;
+    else if (k == "precision") *value = h->prec;
     else return fail(RX_EINVAL, "unknown parameter '%s'", key);
     return RX_OK;
 }
@@ -1051,6 +1059,7 @@ int rx_process_blocks(rx_handle *h, const void *samples, size_t n_samples, size_
 
 int rx_get_state(rx_handle *h, void *buf, size_t *len) {
     if (!h || !len) return fail(RX_EINVAL, "NULL argument");
+    if (h->prec != SK_F32) return fail(RX_EINVAL, "stream state is kept for float32 storage only (precision 0)");
     if (!h->started || h->blocks_done < 1) return fail(RX_ESTATE, "no block of a stream has run yet");
     const StateLayout lay = state_layout(h);
     if (!buf) { *len = lay.total; return RX_OK; }
@@ -1089,7 +1098,7 @@ int rx_get_state(rx_handle *h, void *buf, size_t *len) {
     // y rows [S*2][N]; the halo is symbols K-W .. K-1 (zeros outside 0 .. N-1)
     const long lo = std::max(0L, K - W), hi = std::min(K, N), skip = lo - (K - W);
     if (hi > lo)
-        CK(cudaMemcpy2D(out + lay.y_tail + sizeof(float2) * skip, sizeof(float2) * W, h->y + lo,
+        CK(cudaMemcpy2D(out + lay.y_tail + sizeof(float2) * skip, sizeof(float2) * W, static_cast<float2 *>(h->y) + lo,
                         sizeof(float2) * N, sizeof(float2) * (hi - lo), (size_t)2 * S, cudaMemcpyDeviceToHost));
     *len = lay.total;
     return RX_OK;
@@ -1097,6 +1106,7 @@ int rx_get_state(rx_handle *h, void *buf, size_t *len) {
 
 int rx_set_state(rx_handle *h, const void *buf, size_t len) {
     if (!h || !buf) return fail(RX_EINVAL, "NULL argument");
+    if (h->prec != SK_F32) return fail(RX_EINVAL, "stream state is kept for float32 storage only (precision 0)");
     if (len < sizeof(rx_state_header)) return fail(RX_EINVAL, "state of %zu bytes is shorter than its header", len);
     rx_state_header hd;
     std::memcpy(&hd, buf, sizeof hd);
@@ -1144,7 +1154,7 @@ int rx_set_state(rx_handle *h, const void *buf, size_t len) {
     CK(cudaMemcpy(h->sd, sd.data(), sizeof(StreamDev) * S, cudaMemcpyHostToDevice));
     const long lo = std::max(0L, K - W), hi = std::min(K, N), skip = lo - (K - W);
     if (hi > lo)
-        CK(cudaMemcpy2D(h->y + lo, sizeof(float2) * N, in + lay.y_tail + sizeof(float2) * skip,
+        CK(cudaMemcpy2D(static_cast<float2 *>(h->y) + lo, sizeof(float2) * N, in + lay.y_tail + sizeof(float2) * skip,
                         sizeof(float2) * W, sizeof(float2) * (hi - lo), (size_t)2 * S, cudaMemcpyHostToDevice));
     h->u = (long)hd.lms_updates;
     h->blocks_done = n;
@@ -1194,8 +1204,7 @@ int rx_train(rx_handle *h, const void *x, size_t n_samples, void *taps, uint16_t
     const long N = (long)n_samples / 2;
     const long ntr = std::min(h->n_train, N);
     if (!h->ref || h->ref_n < ntr) return fail(RX_ESTATE, "training needs a reference (rx_set_reference)");
-    return train_stage(h, (const float2 *)x, (long)n_samples, (float2 *)taps, ntr, pcode, ntr, nullptr, 0,
-                       h->st);
+    return train_stage(h, x, (long)n_samples, (float2 *)taps, ntr, pcode, ntr, nullptr, 0, h->st, SK_F32);
 }
 
 int rx_bps(rx_handle *h, const void *y, size_t n_y, size_t a, size_t e, size_t n_valid, uint8_t *b_out) {

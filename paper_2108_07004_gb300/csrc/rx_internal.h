@@ -6,6 +6,8 @@
 #include <stdint.h>
 
 #include "rx.h"
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
 
 #define RX_MAXM 64        // largest table (4D: 64 points; 2D: 16 points per polarisation)
 #define RX_MAXB 64        // largest number of BPS test phases
@@ -49,6 +51,34 @@ struct StreamDev {
     unsigned int ticket_demap;
     int pad[2];
 };
+
+// ---- storage of the chain's intermediate samples -------------------------------
+// The CDC output x and the FIR output y are stored as float32 pairs, or (the
+// precision variant) as half or bfloat16 pairs; all arithmetic is float32.
+enum { SK_F32 = 0, SK_F16 = 1, SK_BF16 = 2 };
+template <int SK> struct Store;
+template <> struct Store<SK_F32> {
+    using T = float2;
+    static __device__ __forceinline__ float2 ld(const T *p, long i) { return p[i]; }
+    static __device__ __forceinline__ void st(T *p, long i, float2 v) { p[i] = v; }
+};
+template <> struct Store<SK_F16> {
+    using T = __half2;
+    static __device__ __forceinline__ float2 ld(const T *p, long i) { return __half22float2(p[i]); }
+    static __device__ __forceinline__ void st(T *p, long i, float2 v) { p[i] = __float22half2_rn(v); }
+};
+template <> struct Store<SK_BF16> {
+    using T = __nv_bfloat162;
+    static __device__ __forceinline__ float2 ld(const T *p, long i) { return __bfloat1622float2(p[i]); }
+    static __device__ __forceinline__ void st(T *p, long i, float2 v) { p[i] = __float22bfloat162_rn(v); }
+};
+inline size_t store_bytes(int sk) { return sk == SK_F32 ? sizeof(float2) : sizeof(__half2); }
+// element i of a sample array of storage kind sk (a uniform branch)
+__device__ __forceinline__ float2 ld_sample(const void *p, long i, int sk) {
+    if (sk == SK_F16) return Store<SK_F16>::ld(static_cast<const __half2 *>(p), i);
+    if (sk == SK_BF16) return Store<SK_BF16>::ld(static_cast<const __nv_bfloat162 *>(p), i);
+    return static_cast<const float2 *>(p)[i];
+}
 
 // ---- complex helpers --------------------------------------------------------
 __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
@@ -109,38 +139,38 @@ __device__ __forceinline__ float fmin3(float a, float b, float c) {
 // ---- launchers (return cudaError_t of the launch) -----------------------------
 // Overlap-save frames f0 .. f1-1 (frame f writes outputs f*(n_fft-n_ov) ..
 // (f+1)*(n_fft-n_ov) - 1); f1 < 0 means every frame of the ns samples.
-cudaError_t launch_cdc(const float2 *in, float2 *out, long ns, int n_streams2, int n_fft,
+cudaError_t launch_cdc(const float2 *in, void *out, long ns, int n_streams2, int n_fft,
                        int n_ov, const float2 *H, const float2 *tw, cudaStream_t st,
-                       long f0 = 0, long f1 = -1);
+                       long f0 = 0, long f1 = -1, int sk = SK_F32);
 
-cudaError_t launch_fir(const float2 *x, long ns, const float2 *taps, long k0, long k1,
-                       float2 *y, long y_stride, long y_off, int n_streams, int T,
-                       cudaStream_t st);
+cudaError_t launch_fir(const void *x, long ns, const float2 *taps, long k0, long k1,
+                       void *y, long y_stride, long y_off, int n_streams, int T,
+                       cudaStream_t st, int sk = SK_F32);
 
-cudaError_t launch_lms(const float2 *x, long ns, const float2 *taps_in, float2 *taps_out,
+cudaError_t launch_lms(const void *x, long ns, const float2 *taps_in, float2 *taps_out,
                        long k0, int n_upd, const uint16_t *pcode, long pcode_stride,
                        int mode, int passes, unsigned long long u0, int n_cma, float mu,
                        const uint8_t *ref_lab, long ref_stride,
-                       int n_streams, int T, const FmtDev &f, cudaStream_t st);
+                       int n_streams, int T, const FmtDev &f, cudaStream_t st, int sk = SK_F32);
 
-cudaError_t launch_train_phase(const float2 *x, long ns, const float2 *taps, const uint8_t *ref_lab,
+cudaError_t launch_train_phase(const void *x, long ns, const float2 *taps, const uint8_t *ref_lab,
                                long ref_stride, int n, int W, uint16_t *pcode, long pcode_stride,
                                int32_t *carry, int carry_stride, int n_streams, int T,
-                               const FmtDev &f, cudaStream_t st);
+                               const FmtDev &f, cudaStream_t st, int sk = SK_F32);
 
-cudaError_t launch_align(const float2 *x, long ns, float2 *taps, const uint8_t *ref_lab,
+cudaError_t launch_align(const void *x, long ns, float2 *taps, const uint8_t *ref_lab,
                          long ref_stride, int n_train, int n_streams, int T, const FmtDev &f,
-                         cudaStream_t st);
+                         cudaStream_t st, int sk = SK_F32);
 
 int bps_cta_range(int rounds);              // output symbols per BPS / unwrap block
 int bps_rounds(long len, int n_streams);    // rounds that fill about one wave
 
 // mdsum (optional, [S][n_blocks] float64): per-block sums of the minimum
 // distance at the chosen phase, the decision-directed noise of the range
-cudaError_t launch_bps(const float2 *y, long y_stride, long a, long e, long n_valid,
+cudaError_t launch_bps(const void *y, long y_stride, long a, long e, long n_valid,
                        int W, uint8_t *bout, long bout_stride, long bout_off,
                        int *dsum, double *mdsum, int rounds, int n_streams, const FmtDev &f,
-                       cudaStream_t st);
+                       cudaStream_t st, int sk = SK_F32);
 
 cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long b_stride,
                           long b_off, long a, long e, const int *dsum,
@@ -189,13 +219,13 @@ cudaError_t launch_count_llr(const float *llr, long llr_stride, const float *x4,
 // (llr null: symbols only, into sym);
 // sigma^2 = sum(mdsum) / (2 (e - a)) unless sigma2_fixed is given.  The
 // block's sigma^2 goes to sigma2_out[s * s2_stride].  No z is written.
-cudaError_t launch_derot_demap(const float2 *y, long y_stride, const uint8_t *b, long b_stride,
+cudaError_t launch_derot_demap(const void *y, long y_stride, const uint8_t *b, long b_stride,
                                long a, long e, const int *dsum, const double *mdsum, int kR,
                                const int32_t *carry_in, int cin_stride, int32_t *carry_out,
                                int cout_stride, uint16_t *pcode, long pc_stride,
                                const double *sigma2_fixed, double *sigma2_out, int s2_stride,
                                float *llr, long llr_stride, const DemapCount &cnt, const SymOut &sym,
-                               int n_streams, const FmtDev &f, cudaStream_t st);
+                               int n_streams, const FmtDev &f, cudaStream_t st, int sk = SK_F32);
 // number of partial-sum rows launch_derot_demap needs per stream
 long derot_demap_ctas(long len);
 
