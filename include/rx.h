@@ -285,6 +285,57 @@ int rx_set_demapper(rx_handle *h, rx_mlp *m);
  * learned demapper's training data from the chain. */
 int rx_set_symbol_output(rx_handle *h, float *x4, float *sigma2);
 
+/* ---- serving: continuous batching over streams ---------------------------- */
+
+/* One request = one stream with its own format, link and receiver settings.
+ * Device buffers are caller-owned and must stay valid until the request is
+ * done: samples [2][n_samples] c64, llr_out [N][m] float32, ref_bits
+ * [N][m] uint8 (may be NULL: no training stage, no counting).  fft,
+ * overlap, block, n_pre: 0 keeps the handle default.  Custom tables are
+ * copied at submission. */
+typedef struct {
+    rx_format format;
+    double symbol_rate;
+    int sps;
+    double cd_ps_per_nm;
+    int taps;
+    int bps_phases;
+    int fft, overlap, block, n_pre;
+    const void *samples;
+    size_t n_samples;
+    float *llr_out;
+    const uint8_t *ref_bits;
+} rx_request;
+
+/* A server admits queued requests in arrival order while fewer than
+ * max_slots run and the running ones' device-memory estimates (about 52 B
+ * per symbol plus 1 MiB) leave room in mem_budget_bytes; each admitted
+ * request gets its own handle and CUDA stream, and every step issues one
+ * block of every running request, so requests that arrived at different
+ * times overlap on the device (the paper's multiple processing streams,
+ * Sec. 2).  A finished request frees its slot and memory at the next step.
+ * Results of a request equal those of a handle processing it alone.  Not
+ * thread-safe; errors: rx_server_last_error(). */
+typedef struct rx_server rx_server;
+#define RX_REQ_QUEUED  0
+#define RX_REQ_RUNNING 1
+#define RX_REQ_DONE    2
+#define RX_REQ_FAILED  3
+rx_server *rx_server_create(size_t mem_budget_bytes, int max_slots);
+void rx_server_destroy(rx_server *s);               /* NULL-safe; waits for running work */
+/* Queue a request (RX_EINVAL if it alone exceeds the budget); *id names it. */
+int rx_server_submit(rx_server *s, const rx_request *r, uint64_t *id);
+/* Retire finished requests, admit what fits, issue one block of each running
+ * request; *n_left (may be NULL) = running + queued.  Does not wait. */
+int rx_server_step(rx_server *s, int *n_left);
+/* Step until every submitted request is done. */
+int rx_server_run(rx_server *s);
+/* State (RX_REQ_*) of a request and, once done, its statistics. */
+int rx_server_poll(rx_server *s, uint64_t id, int *state, rx_stats *stats);
+/* Memory in use, the most requests ever running at once, steps taken. */
+int rx_server_info(rx_server *s, size_t *mem_used, int *max_active, long *steps);
+const char *rx_server_last_error(void);
+
 /* Format facts: dims, m (bits per 4D symbol), M (table size). */
 int rx_format_info(const rx_handle *h, int *dims, int *m, int *M);
 

@@ -32,6 +32,14 @@ class RxFormat(C.Structure):
                 ("labels", C.POINTER(C.c_uint32))]
 
 
+class RxRequest(C.Structure):
+    _fields_ = [("format", RxFormat), ("symbol_rate", C.c_double), ("sps", C.c_int),
+                ("cd_ps_per_nm", C.c_double), ("taps", C.c_int), ("bps_phases", C.c_int),
+                ("fft", C.c_int), ("overlap", C.c_int), ("block", C.c_int), ("n_pre", C.c_int),
+                ("samples", C.c_void_p), ("n_samples", C.c_size_t), ("llr_out", C.c_void_p),
+                ("ref_bits", C.c_void_p)]
+
+
 class RxStats(C.Structure):
     _fields_ = [("n_sym", C.c_uint64), ("n_bits", C.c_uint64), ("bit_errors", C.c_uint64),
                 ("gmi_sum", C.c_double), ("gmi", C.c_double), ("ber", C.c_double),
@@ -59,6 +67,14 @@ _PROTOS = {
     "rx_get_state": (_I, [_VP, _VP, C.POINTER(_SZ)]),
     "rx_set_state": (_I, [_VP, _VP, _SZ]),
     "rx_process_blocks": (_I, [_VP, _VP, _SZ, _SZ, _SZ, _VP, _VP]),
+    "rx_server_create": (_VP, [_SZ, _I]),
+    "rx_server_destroy": (None, [_VP]),
+    "rx_server_submit": (_I, [_VP, _VP, C.POINTER(C.c_uint64)]),
+    "rx_server_step": (_I, [_VP, C.POINTER(_I)]),
+    "rx_server_run": (_I, [_VP]),
+    "rx_server_poll": (_I, [_VP, C.c_uint64, C.POINTER(_I), _VP]),
+    "rx_server_info": (_I, [_VP, C.POINTER(_SZ), C.POINTER(_I), C.POINTER(C.c_long)]),
+    "rx_server_last_error": (C.c_char_p, []),
     "rx_set_demapper": (_I, [_VP, _VP]),
     "rx_set_symbol_output": (_I, [_VP, _VP, _VP]),
     "rx_mlp_create": (_VP, [_VP]),
@@ -178,6 +194,26 @@ def load_table(name: str) -> dict:
         return json.load(f)
 
 
+def make_format(fmt: str):
+    """rx_format for a built-in name or a table file; returns (format, arrays
+    that must stay alive while it is used)."""
+    f = RxFormat()
+    keep = []
+    if fmt == "dp_qpsk":
+        f.kind = RX_FMT_DP_QPSK
+    elif fmt == "dp_16qam":
+        f.kind = RX_FMT_DP_16QAM
+    else:
+        d = load_table(fmt)
+        pts = np.ascontiguousarray(np.asarray(d["points"], dtype=np.float32))
+        labs = np.ascontiguousarray(np.asarray(d["labels"], dtype=np.uint32))
+        keep += [pts, labs]
+        f.kind, f.dims, f.m_bits, f.sym_order = RX_FMT_CUSTOM, int(d["dims"]), int(d["m_bits"]), int(d["sym_order"])
+        f.points = pts.ctypes.data_as(C.POINTER(C.c_float))
+        f.labels = labs.ctypes.data_as(C.POINTER(C.c_uint32))
+    return f, keep
+
+
 class Receiver:
     """One receiver handle for `streams` streams of one format and link."""
 
@@ -185,20 +221,7 @@ class Receiver:
                  cd_ps_per_nm: float = 0.0, taps: int = 15, bps_phases: int = 32,
                  stream: torch.cuda.Stream | None = None, **params):
         L = lib()
-        f = RxFormat()
-        self._keep = []
-        if fmt == "dp_qpsk":
-            f.kind = RX_FMT_DP_QPSK
-        elif fmt == "dp_16qam":
-            f.kind = RX_FMT_DP_16QAM
-        else:
-            d = load_table(fmt)
-            pts = np.ascontiguousarray(np.asarray(d["points"], dtype=np.float32))
-            labs = np.ascontiguousarray(np.asarray(d["labels"], dtype=np.uint32))
-            self._keep += [pts, labs]
-            f.kind, f.dims, f.m_bits, f.sym_order = RX_FMT_CUSTOM, int(d["dims"]), int(d["m_bits"]), int(d["sym_order"])
-            f.points = pts.ctypes.data_as(C.POINTER(C.c_float))
-            f.labels = labs.ctypes.data_as(C.POINTER(C.c_uint32))
+        f, self._keep = make_format(fmt)
         h = L.rx_create(C.byref(f), symbol_rate, sps, cd_ps_per_nm, taps, bps_phases)
         if not h:
             raise RxError(-1, L.rx_last_error().decode())
@@ -404,6 +427,70 @@ class Mlp:
     def close(self):
         if getattr(self, "h", None):
             lib().rx_mlp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+
+
+class Server:
+    """Continuous batching over streams (rx_server_*): requests are admitted
+    in arrival order as slots and the device-memory budget allow, and every
+    step issues one block of each running request."""
+
+    def __init__(self, mem_budget: int, max_slots: int):
+        h = lib().rx_server_create(int(mem_budget), int(max_slots))
+        if not h:
+            raise RxError(-1, lib().rx_server_last_error().decode())
+        self.h = h
+        self._keep = {}
+
+    def _ck(self, rc):
+        if rc != 0:
+            raise RxError(rc, lib().rx_server_last_error().decode())
+
+    def submit(self, fmt: str, samples: torch.Tensor, llr: torch.Tensor, bits: torch.Tensor | None = None,
+               *, cd_ps_per_nm: float, taps: int, bps_phases: int, symbol_rate: float = 28e9, sps: int = 2,
+               fft: int = 0, overlap: int = 0, block: int = 0, n_pre: int = 0) -> int:
+        """samples [2, 2N] complex64, llr [N, m] float32, bits [N, m] uint8 (device)."""
+        f, keep = make_format(fmt)
+        r = RxRequest(format=f, symbol_rate=symbol_rate, sps=sps, cd_ps_per_nm=cd_ps_per_nm, taps=taps,
+                      bps_phases=bps_phases, fft=fft, overlap=overlap, block=block, n_pre=n_pre,
+                      samples=_ptr(samples), n_samples=samples.shape[-1], llr_out=_ptr(llr),
+                      ref_bits=_ptr(bits))
+        rid = C.c_uint64()
+        self._ck(lib().rx_server_submit(self.h, C.byref(r), C.byref(rid)))
+        self._keep[rid.value] = (samples, llr, bits, keep)
+        return rid.value
+
+    def step(self) -> int:
+        n = C.c_int()
+        self._ck(lib().rx_server_step(self.h, C.byref(n)))
+        return n.value
+
+    def run(self):
+        self._ck(lib().rx_server_run(self.h))
+
+    def poll(self, rid: int):
+        st = C.c_int()
+        stats = RxStats()
+        self._ck(lib().rx_server_poll(self.h, rid, C.byref(st), C.byref(stats)))
+        return st.value, (stats.as_dict() if st.value == REQ_DONE else None)
+
+    def info(self) -> dict:
+        used, mx, steps = C.c_size_t(), C.c_int(), C.c_long()
+        self._ck(lib().rx_server_info(self.h, C.byref(used), C.byref(mx), C.byref(steps)))
+        return {"mem_used": used.value, "max_active": mx.value, "steps": steps.value}
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rx_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,0 +1,96 @@
+"""Serving with continuous batching (rx_server_*): every request's LLRs and
+counts are the same alone and in a mix of requests of different formats,
+lengths and links, and a small device-memory budget makes requests queue
+without changing any result."""
+import numpy as np
+import pytest
+
+from paper_2108_07004_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+# (format, symbols, km, Es/N0 dB, taps, B)
+REQS = [("dp_qpsk", 20000, 80, 12.0, 15, 32), ("gs4d64", 50000, 1000, 14.0, 31, 64),
+        ("dp_16qam", 33000, 300, 18.0, 15, 32), ("gs4d64", 70001, 2000, 14.0, 31, 64),
+        ("dp_qpsk", 45000, 1500, 12.0, 31, 32), ("dp_16qam", 18000, 80, 18.0, 15, 32)]
+M = {"dp_qpsk": 4, "dp_16qam": 8, "gs4d64": 6}
+
+
+@pytest.fixture(scope="module")
+def streams():
+    out = []
+    for i, (fmt, n, km, esn0, T, B) in enumerate(REQS):
+        st = synth.make_stream(fmt, n, seed=synth.stream_seed(5, i), esn0_db=esn0,
+                               cd_ps_per_nm=17.0 * km, linewidth_ts=1e-5)
+        out.append((torch.from_numpy(st.rx.astype(np.complex64)).cuda(),
+                    torch.from_numpy(st.bits).cuda()))
+    return out
+
+
+def _submit(srv, i, samples, bits):
+    fmt, n, km, esn0, T, B = REQS[i]
+    llr = torch.full((n, M[fmt]), float("nan"), dtype=torch.float32, device="cuda")
+    rid = srv.submit(fmt, samples, llr, bits, cd_ps_per_nm=17.0 * km, taps=T, bps_phases=B,
+                     fft=4096, overlap=1024, block=16384, n_pre=2048)
+    return rid, llr
+
+
+def _serve(idx, streams, budget=1 << 33, slots=16):
+    from paper_2108_07004_gb300 import rx
+    srv = rx.Server(budget, slots)
+    got = {i: _submit(srv, i, *streams[i]) for i in idx}
+    srv.run()
+    torch.cuda.synchronize()
+    res = {}
+    for i, (rid, llr) in got.items():
+        state, stats = srv.poll(rid)
+        assert state == rx.REQ_DONE
+        res[i] = (llr.cpu().numpy(), stats)
+    info = srv.info()
+    srv.close()
+    return res, info
+
+
+def test_each_result_is_the_same_alone_and_in_the_mix(streams):
+    alone = {i: _serve([i], streams)[0][i] for i in range(len(REQS))}
+    mix, info = _serve(range(len(REQS)), streams)
+    assert info["max_active"] == len(REQS)
+    for i in range(len(REQS)):
+        assert np.array_equal(alone[i][0], mix[i][0]), i
+        assert not np.isnan(mix[i][0]).any()
+        for k in ("bit_errors", "n_sym", "gmi_sum"):
+            assert alone[i][1][k] == mix[i][1][k], (i, k)
+
+
+def test_served_request_equals_a_handle(streams):
+    from paper_2108_07004_gb300 import rx
+    i = 1
+    fmt, n, km, esn0, T, B = REQS[i]
+    samples, bits = streams[i]
+    r = rx.Receiver(fmt, cd_ps_per_nm=17.0 * km, taps=T, bps_phases=B, fft=4096, overlap=1024,
+                    block=16384, n_pre=2048)
+    r.set_reference(bits[None].contiguous())
+    ref, st = r.process(samples[None].contiguous())
+    served, _ = _serve([i], streams)
+    assert np.array_equal(served[i][0], ref[0].cpu().numpy())
+    assert served[i][1]["bit_errors"] == st[0]["bit_errors"]
+
+
+def test_small_budget_queues_without_changing_results(streams):
+    alone = {i: _serve([i], streams)[0][i] for i in range(len(REQS))}
+    # room for about two of the requests at a time
+    budget = 52 * 2 * 70001 + 3 * (1 << 20)
+    mix, info = _serve(range(len(REQS)), streams, budget=budget)
+    assert 1 <= info["max_active"] <= 3
+    assert info["mem_used"] == 0
+    for i in range(len(REQS)):
+        assert np.array_equal(alone[i][0], mix[i][0]), i
+
+
+def test_request_larger_than_the_budget_is_refused(streams):
+    from paper_2108_07004_gb300 import rx
+    srv = rx.Server(1 << 20, 4)
+    with pytest.raises(rx.RxError):
+        _submit(srv, 1, *streams[1])
+    srv.close()
