@@ -424,6 +424,94 @@ def run_precision(args):
     print(json.dumps(line), flush=True)
 
 
+# ---- serving (config 5): 64 streams, Poisson arrivals, mixed formats and lengths ----
+SERVE = dict(n_req=64, len_log2=(14, 20), km=(80.0, 2000.0), budget=8 << 30, slots=64, load=0.8,
+             esn0={"dp_qpsk": 12.0, "dp_16qam": 18.0, "gs4d64": 14.0},
+             bps={"dp_qpsk": 32, "dp_16qam": 32, "gs4d64": 64}, m={"dp_qpsk": 4, "dp_16qam": 8, "gs4d64": 6})
+
+
+def serving_requests(seed: int):
+    rng = np.random.default_rng(seed)
+    fmts = ["dp_qpsk", "dp_16qam", "gs4d64"]
+    reqs = []
+    for i in range(SERVE["n_req"]):
+        fmt = fmts[int(rng.integers(0, 3))]
+        n = int(2 ** rng.uniform(*SERVE["len_log2"]))
+        km = float(rng.uniform(*SERVE["km"]))
+        st = synth.make_stream(fmt, n, seed=seed + 1 + i, esn0_db=SERVE["esn0"][fmt],
+                               cd_ps_per_nm=17.0 * km, linewidth_ts=1e-5)
+        reqs.append((fmt, n, km, st))
+    return reqs
+
+
+def run_serving(args):
+    import torch
+    from paper_2108_07004_gb300 import rx as rx_mod
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    reqs = serving_requests(synth.stream_seed(5, 0))
+    dev = [(torch.from_numpy(st.rx.astype(np.complex64)).cuda(), torch.from_numpy(st.bits).cuda())
+           for _, _, _, st in reqs]
+    total_bits = sum(n * SERVE["m"][fmt] for fmt, n, _, _ in reqs)
+
+    def serve(arrivals):
+        srv = rx_mod.Server(SERVE["budget"], SERVE["slots"])
+        llrs, ids, t_arr, t_done = {}, {}, {}, {}
+        order = np.argsort(arrivals)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        k = 0
+        while len(t_done) < len(reqs):
+            now = time.perf_counter() - t0
+            while k < len(order) and arrivals[order[k]] <= now:
+                i = int(order[k])
+                fmt, n, km, _ = reqs[i]
+                llrs[i] = torch.empty((n, SERVE["m"][fmt]), dtype=torch.float32, device="cuda")
+                ids[i] = srv.submit(fmt, dev[i][0], llrs[i], dev[i][1], cd_ps_per_nm=17.0 * km, taps=31,
+                                    bps_phases=SERVE["bps"][fmt], fft=4096, overlap=1024, block=1 << 16)
+                t_arr[i] = now
+                k += 1
+            srv.step()
+            for i, rid in ids.items():
+                if i not in t_done and srv.poll(rid)[0] in (rx_mod.REQ_DONE, rx_mod.REQ_FAILED):
+                    t_done[i] = time.perf_counter() - t0
+            if k < len(order) and not srv.info()["mem_used"]:
+                time.sleep(max(0.0, min(0.001, arrivals[order[k]] - (time.perf_counter() - t0))))
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        states = [srv.poll(ids[i]) for i in range(len(reqs))]
+        info = srv.info()
+        srv.close()
+        lat = sorted(t_done[i] - t_arr[i] for i in range(len(reqs)))
+        return wall, lat, states, info
+
+    # capacity: every request present at once
+    for _ in range(max(1, args.warmup)):
+        serve(np.zeros(len(reqs)))
+    wall0, lat0, states0, info0 = serve(np.zeros(len(reqs)))
+    cap_bits = total_bits / wall0
+    # Poisson arrivals at SERVE["load"] of that capacity
+    rng = np.random.default_rng(7)
+    rate = SERVE["load"] * cap_bits / (total_bits / len(reqs))      # requests per second
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(reqs)))
+    wall, lat, states, info = serve(arrivals)
+    ok = all(s == rx_mod.REQ_DONE for s, _ in states)
+    line = {
+        "metric": METRIC, "value": total_bits / wall / 1e9, "unit": "Gbit/s", "n_gpus": 1,
+        "steps": 1, "warmup": args.warmup, "ms_per_step": wall * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "serving_64_streams_poisson_mixed_formats", "requests": len(reqs),
+                   "symbols": int(sum(n for _, n, _, _ in reqs)), "budget_bytes": SERVE["budget"],
+                   "slots": SERVE["slots"], "load": SERVE["load"], "block": 1 << 16, "fft": 4096, "taps": 31},
+        "capacity_gbps_all_at_once": cap_bits / 1e9,
+        "request_latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
+        "request_latency_ms_all_at_once": {"p50": 1e3 * lat0[len(lat0) // 2], "p99": 1e3 * lat0[-1]},
+        "max_running": info["max_active"], "all_done": ok,
+        "ber_by_format": {f: float(np.mean([st["ber"] for (s_, st), (fm, _, _, _) in zip(states, reqs) if fm == f and st]))
+                          for f in ("dp_qpsk", "dp_16qam", "gs4d64")},
+    }
+    print(json.dumps(line), flush=True)
+
+
 # ---- learned demapper (MLP 4 -> 128 -> 128 -> 6) on the same chain ------------
 LEARN = dict(train_streams=16, train_sym=(1 << 18) + (1 << 14), skip=1 << 14, epochs=20, batch=8192,
              lr=1e-3, infer_streams=16, infer_sym=1 << 20, esn0=(8.0, 16.0), init_seed=2108070044)
@@ -541,9 +629,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision"],
+    ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision", "serving"],
                     help="learned: train the MLP demapper on chain output, compare with the exact one; "
-                         "precision: DP-QPSK chain with CDC/FIR data in float32, half and bfloat16")
+                         "precision: DP-QPSK chain with CDC/FIR data in float32, half and bfloat16; "
+                         "serving: 64 mixed streams with Poisson arrivals through the continuous-batching server")
     ap.add_argument("--learned-sym", type=int, default=LEARN["infer_sym"])
     args = ap.parse_args()
     if args.impl == "reference":
@@ -552,6 +641,8 @@ def main():
         run_learned(args)
     elif args.variant == "precision":
         run_precision(args)
+    elif args.variant == "serving":
+        run_serving(args)
     else:
         run_ours(args)
 
