@@ -7,7 +7,8 @@ polarisation rotation, laser phase noise linewidth*Ts = 2e-5, and the Es/N0
 sweep 8..16 dB in 1 dB steps: 9 independent streams of 2^20 4D symbols,
 processed by one handle (FFT 4096 / overlap 1024, 31 taps, BPS with 64
 test phases and window 64, blocks of 2^16 symbols with 1024 LMS updates,
-tap lag 2).  Inputs (9 x 32 MiB) are larger than L2, so no flush is used.
+tap lag 3: block n is equalised with the taps the LMS made on block n - 3).
+Inputs (9 x 32 MiB) are larger than L2, so no flush is used.
 
 value: 9 * 2^20 * 6 LLR bits per step / device time per step.
 e2e:   the same metric through rx_process_host (samples and reference bits
@@ -36,7 +37,7 @@ METRIC = "Rx line rate Gbit/s (LLRs out) per GB300 at oracle-matched BER; p99 bl
 WL = dict(workload="gs4d64_1000km_esn0_8to16dB", fmt="gs4d64", n_sym=1 << 20,
           esn0_db=list(range(8, 17)), cd_ps_per_nm=17000.0, linewidth_ts=2e-5,
           symbol_rate=28e9, sps=2, fft=4096, overlap=1024, taps=31, bps_phases=64,
-          bps_window=64, block=1 << 16, n_upd=1024, lag=2, mu=1e-3, n_pre=2048,
+          bps_window=64, block=1 << 16, n_upd=1024, lag=3, mu=1e-3, n_pre=2048,
           cma_passes=1, n_cma=0, n_train=1024, train_passes=3, skip_head=16384, skip_tail=512)
 FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070.0
 # DRAM bytes (read + write) of one bps_kernel launch at this workload's launch

@@ -60,8 +60,9 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
     extern __shared__ float smem[];
     const int B = f.B;
     const int kChunks = 8 * rounds - 2, kR = range_of(rounds);
-    float *Eb = smem;                                     // [10][B][32] exclusive prefixes
-    float *Tb = smem + RX_NCHUNK * B * 32;                // [10][B] chunk totals
+    constexpr int kRow = 33;                              // padded row of 32 prefixes
+    float *Eb = smem;                                     // [10][B][kRow] exclusive prefixes
+    float *Tb = smem + RX_NCHUNK * B * kRow;              // [10][B] chunk totals
     uint8_t *bsm = reinterpret_cast<uint8_t *>(Tb + RX_NCHUNK * B);   // [kR]
     __shared__ int red[8];
     __shared__ float redm[8];
@@ -158,19 +159,23 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
                 md2 = (yn0 + w0) + (yn1 + w1);
             }
             if (!valid) { md = 0.f; md2 = 0.f; }
-            float incl = md, incl2 = md2;
+            Eb[(slot * B + b) * kRow + lane] = md;
+            Eb[(slot * B + b + hb) * kRow + lane] = md2;
+        }
+        __syncwarp();
+        // exclusive prefix of every test phase's row over the chunk's 32
+        // symbols, in place: lane l takes phases l and l + 32 (rows padded to
+        // 33 floats, so the lanes' serial walks hit 32 different banks)
+        for (int b = lane; b < B; b += 32) {
+            float *row = Eb + (slot * B + b) * kRow;
+            float run = 0.f;
 #pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const float t = __shfl_up_sync(0xffffffffu, incl, off);
-                const float t2 = __shfl_up_sync(0xffffffffu, incl2, off);
-                if (lane >= off) { incl += t; incl2 += t2; }
+            for (int j = 0; j < 32; ++j) {
+                const float v = row[j];
+                row[j] = run;
+                run += v;
             }
-            float excl = __shfl_up_sync(0xffffffffu, incl, 1);
-            float excl2 = __shfl_up_sync(0xffffffffu, incl2, 1);
-            if (lane == 0) { excl = 0.f; excl2 = 0.f; }
-            Eb[(slot * B + b) * 32 + lane] = excl;
-            Eb[(slot * B + b + hb) * 32 + lane] = excl2;
-            if (lane == 31) { Tb[slot * B + b] = incl; Tb[slot * B + b + hb] = incl2; }
+            Tb[slot * B + b] = run;
         }
         __syncthreads();
         // ---- window costs and argmin for output chunk oc ----
@@ -189,11 +194,11 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
                 for (int b = 0; b < B; ++b) {
                     float cst;
                     if (c0 == c1) {
-                        cst = Eb[(s0 * B + b) * 32 + l1] - Eb[(s0 * B + b) * 32 + l0];
+                        cst = Eb[(s0 * B + b) * kRow + l1] - Eb[(s0 * B + b) * kRow + l0];
                     } else {
-                        cst = Tb[s0 * B + b] - Eb[(s0 * B + b) * 32 + l0];
+                        cst = Tb[s0 * B + b] - Eb[(s0 * B + b) * kRow + l0];
                         if (c1 - c0 == 2) cst += Tb[sm * B + b];
-                        cst += Eb[(s1 * B + b) * 32 + l1];
+                        cst += Eb[(s1 * B + b) * kRow + l1];
                     }
                     if (cst < best) { best = cst; bb = b; }
                 }
@@ -202,8 +207,8 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
                 // md at (bb, k) from the chunk prefixes: |z_k - d_k|^2 of the
                 // de-rotated symbol (the table is closed under the rotations)
                 const int sc = (oc + 1) % RX_NCHUNK;
-                const float hi = (lane < 31) ? Eb[(sc * B + bb) * 32 + lane + 1] : Tb[sc * B + bb];
-                md_acc += hi - Eb[(sc * B + bb) * 32 + lane];
+                const float hi = (lane < 31) ? Eb[(sc * B + bb) * kRow + lane + 1] : Tb[sc * B + bb];
+                md_acc += hi - Eb[(sc * B + bb) * kRow + lane];
             }
         }
         __syncthreads();
@@ -420,7 +425,7 @@ cudaError_t bps_launch_t(const void *y, long ys, long a, long e, long nv, int W,
                          const FmtDev &f, cudaStream_t st, int sk) {
     const int kR = range_of(rounds);
     const int n_cta = (int)((e - a + kR - 1) / kR);
-    const size_t smem = sizeof(float) * (RX_NCHUNK * f.B * 32 + RX_NCHUNK * f.B) + kR + 16;
+    const size_t smem = sizeof(float) * (RX_NCHUNK * f.B * 33 + RX_NCHUNK * f.B) + kR + 16;
     auto kern = bps_kernel<DIMS, NORB>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
@@ -433,17 +438,21 @@ cudaError_t bps_launch_t(const void *y, long ys, long a, long e, long nv, int W,
 
 int bps_cta_range(int rounds) { return range_of(rounds); }
 
-// Rounds per block so that one launch of S streams x (e - a) outputs fills
-// about one wave of 2 blocks per SM (the ring of 10 chunks takes ~85 KB).
-int bps_rounds(long len, int n_streams) {
-    static int n_sm = 0;
-    if (!n_sm) {
+int sm_count() {
+    static int n = 0;
+    if (!n) {
         int dev = 0;
         cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n_sm <= 0)
-            n_sm = 152;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
     }
-    const long per_stream = std::max(1L, (long)(2 * n_sm) / std::max(1, n_streams));
+    return n;
+}
+
+// Rounds per block so that one launch of S streams x (e - a) outputs fills
+// about one wave of 2 blocks per SM (the ring of 10 chunks takes ~85 KB).
+int bps_rounds(long len, int n_streams, int sm_avail) {
+    if (sm_avail <= 0) sm_avail = sm_count();
+    const long per_stream = std::max(1L, (long)(2 * sm_avail) / std::max(1, n_streams));
     for (int r = 1; r <= kMaxRounds; ++r)                            // fewest rounds that fit
         if ((len + range_of(r) - 1) / range_of(r) <= per_stream) return r;
     return kMaxRounds;

@@ -617,7 +617,11 @@ cudaError_t derot_demap_t(const void *y, long ys, const uint8_t *b, long bst, lo
 
 }  // namespace
 
-long derot_demap_ctas(long len) { return (len + kTile - 1) / kTile; }
+long derot_demap_ctas(long len, int n_streams, int sm_avail) {
+    (void)n_streams;
+    (void)sm_avail;
+    return (len + kTile - 1) / kTile;
+}
 
 cudaError_t launch_derot_demap(const void *y, long y_stride, const uint8_t *b, long b_stride,
                                long a, long e, const int *dsum, const double *mdsum, int kR,
@@ -625,7 +629,8 @@ cudaError_t launch_derot_demap(const void *y, long y_stride, const uint8_t *b, l
                                int cout_stride, uint16_t *pcode, long pc_stride,
                                const double *sigma2_fixed, double *sigma2_out, int s2_stride,
                                float *llr, long llr_stride, const DemapCount &cnt, const SymOut &sym,
-                               int n_streams, const FmtDev &f, cudaStream_t st, int sk) {
+                               int n_streams, const FmtDev &f, cudaStream_t st, int sk, int sm_avail) {
+    (void)sm_avail;   // 1024-symbol tiles measured best whatever the SMs left by the LMS
     if (e <= a || n_streams <= 0) return cudaSuccess;
     if (!cnt.sd || !cnt.partial || !mdsum) return cudaErrorInvalidValue;
 #define RX_DD(D_, M_, B_)                                                                                  \

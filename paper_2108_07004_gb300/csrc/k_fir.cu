@@ -156,16 +156,6 @@ fir_kernel(const typename Store<SK>::T *__restrict__ x, long ns, const float2 *_
     }
 }
 
-int fir_blocks_per_sm() {
-    static int n = 0;
-    if (!n) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0) sms = 152;
-        n = 4 * sms;
-    }
-    return n;
-}
 
 
 
@@ -187,12 +177,12 @@ cudaError_t fir_t(const void *x, long ns, const float2 *taps, long k0, long k1, 
 }  // namespace
 
 cudaError_t launch_fir(const void *x, long ns, const float2 *taps, long k0, long k1, void *y,
-                       long y_stride, long y_off, int n_streams, int T, cudaStream_t st, int sk) {
+                       long y_stride, long y_off, int n_streams, int T, cudaStream_t st, int sk, int sm_avail) {
     if (k1 <= k0 || n_streams <= 0) return cudaSuccess;
     const long tps = (k1 - k0 + kOut - 1) / kOut;
     const long n_tiles = tps * n_streams;
     if (n_tiles > (1L << 30)) return cudaErrorInvalidValue;
-    const int grid = (int)std::min<long>(n_tiles, fir_blocks_per_sm());
+    const int grid = (int)std::min<long>(n_tiles, 4L * (sm_avail > 0 ? sm_avail : sm_count()));
     switch (sk) {
         case SK_F32: return fir_t<SK_F32>(x, ns, taps, k0, k1, y, y_stride, y_off, T, grid, tps, n_tiles, st);
         case SK_F16: return fir_t<SK_F16>(x, ns, taps, k0, k1, y, y_stride, y_off, T, grid, tps, n_tiles, st);

@@ -24,6 +24,19 @@
 namespace {
 
 constexpr int kCH = 1024;
+// dynamic shared memory: rotations, two target rows, e_k and base_k rows
+constexpr int kDynBytes = 3 * kCH * sizeof(float2) + 2 * kCH * sizeof(float4);
+// named barriers between the decision warp (0) and the tap warp (1), one
+// pair each way; consecutive updates alternate, so a barrier never receives
+// a second arrival before its waiter has passed (barrier 0 is __syncthreads)
+constexpr int kBarErr0 = 1, kBarBase0 = 3;
+
+__device__ __forceinline__ void bar_sync(int id, int n) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_arrive(int id, int n) {
+    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
+}
 
 struct Tables {
     float4 orb[RX_MAXM];
@@ -114,9 +127,13 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
     __shared__ Tables tb;
     // dynamic: exp(j phi_k) of the span (MODE 1, 3) and the data-aided
     // targets d_q exp(j phi_k) (MODE 3), prepared by the whole block
+    // and the exchange between the decision and tap warps: e_k and base_k
+    // of both outputs as (re0, im0, re1, im1)
     extern __shared__ float2 dyn_sm[];
     float2 *rots = dyn_sm;
     float2 *tg0 = dyn_sm + kCH, *tg1 = dyn_sm + 2 * kCH;
+    float4 *es = reinterpret_cast<float4 *>(dyn_sm + 3 * kCH);
+    float4 *bs = es + kCH;
     const int s = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int p = lane >> 4, j = lane & 15;
@@ -184,8 +201,6 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
                 }
             }
             __syncthreads();
-            if (warp != 0) continue;
-
             auto xval = [&](int kk, int i) -> float2 {
                 const int t = j + 16 * i;
                 return (t < T) ? xs[p][2 * kk + 2 + 2 * D - t] : make_float2(0.f, 0.f);
@@ -200,6 +215,42 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
                 }
                 reduce_pair(a, c, p, b0, b1);
             };
+            if (warp == 1) {
+                // tap warp: h_k = h_{k-1} + mu conj(e_k) X_k, then publishes
+                // base_{k+2} = h_k^H X_{k+2} (base_0, base_1 from the
+                // chunk's initial taps); only bases inside the span are
+                // published, so every barrier phase is matched
+                float2 b0, b1;
+                base(0, b0, b1);
+                bs[0] = make_float4(b0.x, b0.y, b1.x, b1.y);
+                bar_arrive(kBarBase0, 64);
+                if (n > 1) {
+                    base(1, b0, b1);
+                    bs[1] = make_float4(b0.x, b0.y, b1.x, b1.y);
+                    bar_arrive(kBarBase0 + 1, 64);
+                }
+#pragma unroll 2
+                for (int kk = 0; kk < n; ++kk) {
+                    bar_sync(kBarErr0 + (kk & 1), 64);
+                    const float4 e = es[kk];
+                    const float2 c0v = make_float2(mu * e.x, -mu * e.y), c1v = make_float2(mu * e.z, -mu * e.w);
+#pragma unroll
+                    for (int i = 0; i < NT; ++i) {
+                        const float2 xv = xval(kk, i);
+                        h[0][i] = cadd(h[0][i], cmul(c0v, xv));
+                        h[1][i] = cadd(h[1][i], cmul(c1v, xv));
+                    }
+                    if (kk + 2 < n) {
+                        base(kk + 2, b0, b1);
+                        bs[kk + 2] = make_float4(b0.x, b0.y, b1.x, b1.y);
+                        bar_arrive(kBarBase0 + (kk & 1), 64);
+                    }
+                }
+                continue;
+            }
+            if (warp != 0) continue;
+            // decision warp: y_k = base_k + mu e_{k-1} r1_k, e_k, published
+            // for the tap warp
             // this lane's orbit (DD decisions): representative, energy, and
             // the labels of its S rotations packed one per byte
             const int o = lane & 15;
@@ -210,15 +261,14 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
 #pragma unroll
             for (int k = 0; k < 4; ++k) lab4 |= (unsigned)(tb.orblab[valid ? o : 0][k] & 255) << (8 * k);
             auto label_of = [&](int k) { return (int)((lab4 >> (8 * k)) & 255u); };
-            float2 bc0, bc1, bn0 = make_float2(0.f, 0.f), bn1 = make_float2(0.f, 0.f);
-            base(0, bc0, bc1);
-            if (n > 1) base(1, bn0, bn1);
             float2 ep0 = make_float2(0.f, 0.f), ep1 = make_float2(0.f, 0.f);
 #pragma unroll 2
             for (int kk = 0; kk < n; ++kk) {
                 const float2 r1 = r1s[kk];
-                const float2 y0 = cadd(bc0, cmul(make_float2(mu * ep0.x, mu * ep0.y), r1));
-                const float2 y1 = cadd(bc1, cmul(make_float2(mu * ep1.x, mu * ep1.y), r1));
+                bar_sync(kBarBase0 + (kk & 1), 64);
+                const float4 bb = bs[kk];
+                const float2 y0 = cadd(make_float2(bb.x, bb.y), cmul(make_float2(mu * ep0.x, mu * ep0.y), r1));
+                const float2 y1 = cadd(make_float2(bb.z, bb.w), cmul(make_float2(mu * ep1.x, mu * ep1.y), r1));
                 float2 e0, e1;
                 if (MODE == 0) {
                     const float g0 = f.R2 - cnorm(y0), g1 = f.R2 - cnorm(y1);
@@ -254,23 +304,13 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
                     e0 = csub(cmul(d0, rot), y0);
                     e1 = csub(cmul(d1, rot), y1);
                 }
-                // h_q += mu conj(e_q) X_k
-                const float2 c0v = make_float2(mu * e0.x, -mu * e0.y), c1v = make_float2(mu * e1.x, -mu * e1.y);
-#pragma unroll
-                for (int i = 0; i < NT; ++i) {
-                    const float2 xv = xval(kk, i);
-                    h[0][i] = cadd(h[0][i], cmul(c0v, xv));
-                    h[1][i] = cadd(h[1][i], cmul(c1v, xv));
-                }
-                float2 bnn0, bnn1;
-                base(kk + 2, bnn0, bnn1);      // past the span: reads the zeroed slack, unused
-                bc0 = bn0; bc1 = bn1;
-                bn0 = bnn0; bn1 = bnn1;
+                es[kk] = make_float4(e0.x, e0.y, e1.x, e1.y);   // every lane: the same value
+                bar_arrive(kBarErr0 + (kk & 1), 64);
                 ep0 = e0; ep1 = e1;
             }
         }
     }
-    if (warp == 0) {
+    if (warp == 1) {
 #pragma unroll
         for (int q = 0; q < 2; ++q)
 #pragma unroll
@@ -441,7 +481,7 @@ cudaError_t lms_launch_one(const void *x, long ns, const float2 *ti, float2 *to,
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
     int dyn = optin - (int)fa.sharedSizeBytes;
-    if (dyn < (int)(3 * kCH * sizeof(float2))) return cudaErrorInvalidValue;   // rotations, targets
+    if (dyn < (int)(kDynBytes)) return cudaErrorInvalidValue;   // rotations, targets, exchange
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
     kern<<<S, 256, dyn, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, sk, f);

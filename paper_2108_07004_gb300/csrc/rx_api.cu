@@ -534,6 +534,9 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         h->started = true;
         h->cur_n = N;
     }
+    // grids of the main stream leave room for the side-stream LMS (one SM
+    // per stream) when it runs beside them
+    const int avail = L >= 2 ? std::max(sm_count() / 2, sm_count() - S) : sm_count();
     if (h->sigma2_fixed > 0) {
         h->h_sig.assign(S, h->sigma2_fixed);
         CK(cudaMemcpyAsync(h->sig_fixed, h->h_sig.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
@@ -567,10 +570,10 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         const float2 *wn = slot(h, n - L);
         cudaEvent_t blk0 = nullptr;
         if (h->profile && (blk0 = prof_event(h))) CK(cudaEventRecord(blk0, st));
-        STAGE(ST_FIR, st, 1, launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st, h->prec));
+        STAGE(ST_FIR, st, 1, launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st, h->prec, avail));
         const long a = std::max(0L, k0 - h->W / 2);
         const long e = (n == nblk - 1) ? N : k1 - h->W / 2;
-        const int rounds = bps_rounds(e - a, S);
+        const int rounds = bps_rounds(e - a, S, avail);
         STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, h->dsum, h->mdsum, rounds, S,
                                         f, st, h->prec));
         const int cin = (int)(n & 1), cout = 1 - cin;
@@ -581,13 +584,14 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         }
         // unwrap, de-rotation, LLRs and counting in one pass over y (no z);
         // with the learned demapper the pass writes the symbols instead
-        if (derot_demap_ctas(e - a) > h->cap_pd || (e - a + 255) / 256 > h->cap_pd)
+        if (derot_demap_ctas(e - a, S, avail) > h->cap_pd || (e - a + 255) / 256 > h->cap_pd)
             return fail(RX_EINVAL, "internal: demap partials");
         STAGE(ST_DEMAP, st, 1,
               launch_derot_demap(h->y, N, h->bidx + a, N, a, e, h->dsum, h->mdsum, bps_cta_range(rounds),
                                  carry_base + 2 * cin, (int)sd_stride, carry_base + 2 * cout, (int)sd_stride,
                                  h->pcode + a, N, h->sigma2_fixed > 0 ? h->sig_fixed : nullptr, h->sig, 1,
-                                 h->mlp ? nullptr : llr + (size_t)a * m, N * m, cnt, sym, S, f, st, h->prec));
+                                 h->mlp ? nullptr : llr + (size_t)a * m, N * m, cnt, sym, S, f, st, h->prec,
+                                 avail));
         if (h->mlp) {
             for (int s = 0; s < S; ++s)
                 STAGE(ST_DEMAP, st, 3,

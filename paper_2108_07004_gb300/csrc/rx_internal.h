@@ -145,7 +145,7 @@ cudaError_t launch_cdc(const float2 *in, void *out, long ns, int n_streams2, int
 
 cudaError_t launch_fir(const void *x, long ns, const float2 *taps, long k0, long k1,
                        void *y, long y_stride, long y_off, int n_streams, int T,
-                       cudaStream_t st, int sk = SK_F32);
+                       cudaStream_t st, int sk = SK_F32, int sm_avail = 0);
 
 cudaError_t launch_lms(const void *x, long ns, const float2 *taps_in, float2 *taps_out,
                        long k0, int n_upd, const uint16_t *pcode, long pcode_stride,
@@ -163,7 +163,7 @@ cudaError_t launch_align(const void *x, long ns, float2 *taps, const uint8_t *re
                          cudaStream_t st, int sk = SK_F32);
 
 int bps_cta_range(int rounds);              // output symbols per BPS / unwrap block
-int bps_rounds(long len, int n_streams);    // rounds that fill about one wave
+int bps_rounds(long len, int n_streams, int sm_avail = 0);    // rounds that fill about one wave
 
 // mdsum (optional, [S][n_blocks] float64): per-block sums of the minimum
 // distance at the chosen phase, the decision-directed noise of the range
@@ -225,9 +225,15 @@ cudaError_t launch_derot_demap(const void *y, long y_stride, const uint8_t *b, l
                                int cout_stride, uint16_t *pcode, long pc_stride,
                                const double *sigma2_fixed, double *sigma2_out, int s2_stride,
                                float *llr, long llr_stride, const DemapCount &cnt, const SymOut &sym,
-                               int n_streams, const FmtDev &f, cudaStream_t st, int sk = SK_F32);
+                               int n_streams, const FmtDev &f, cudaStream_t st, int sk = SK_F32,
+                               int sm_avail = 0);
 // number of partial-sum rows launch_derot_demap needs per stream
-long derot_demap_ctas(long len);
+long derot_demap_ctas(long len, int n_streams, int sm_avail);
+
+// SMs of the device (cached).  Launchers that size a grid to one wave take
+// the number of SMs to plan for: the chain passes all of them less those the
+// side-stream LMS holds (one per stream) while it runs beside them.
+int sm_count();
 
 // ---- learned demapper (k_mlp.cu) ----
 // Device state of one MLP: float32 master parameters (order W1 [128][4],
