@@ -1,18 +1,18 @@
 // A3: block-wise adaptation of the 2x2 butterfly (CMA, then DD-LMS).
 //
-// The recursion is sequential, so one warp runs it per stream (Sec. 2: the
-// adaptive equaliser is the hard-to-parallelise step; the paper runs it on
-// its own processing stream next to the parallel kernels, as the library
-// does when the tap lag is >= 2).  Lane (q, p, j) holds the taps
-// h_qp[j + 8 i]; an update is
-//   y_q   = sum conj(h_qp[t]) x_p[2k + D - t]       (lane MACs + 4 xor-shuffles)
+// The recursion is sequential (Sec. 2: the adaptive equaliser is the
+// hard-to-parallelise step; the paper runs it on its own processing stream
+// next to the parallel kernels, as the library does when the tap lag is
+// >= 2).  An update is
+//   y_q   = sum conj(h_qp[t]) x_p[2k + D - t]
 //   CMA:  e_q = (R^2 - |y_q|^2) y_q
 //   DD:   z = y exp(-j phi_k); d = nearest table point (orbit per lane,
 //         (distance, label) min over 16 lanes, ties -> lowest label);
 //         e_q = d_q exp(j phi_k) - y_q
 //   h_qp[t] += mu conj(e_q) x_p[2k + D - t]
-// The samples of up to 1024 updates are staged in shared memory by the whole
-// block before the warp runs through them.
+// Per stream one block: a decision warp and a tap warp run it together (see
+// lms_kernel); the samples of up to 1024 updates are staged in shared memory
+// by the whole block before the two warps run through them.
 //
 // The start-up training alignment (Sec. 2: the equaliser first converges on
 // a known sequence) is align_kernel: it correlates the equalised training
@@ -23,19 +23,28 @@
 
 namespace {
 
-constexpr int kCH = 1024;
-// dynamic shared memory: rotations, two target rows, e_k and base_k rows
-constexpr int kDynBytes = 3 * kCH * sizeof(float2) + 2 * kCH * sizeof(float4);
-// named barriers between the decision warp (0) and the tap warp (1), one
-// pair each way; consecutive updates alternate, so a barrier never receives
-// a second arrival before its waiter has passed (barrier 0 is __syncthreads)
-constexpr int kBarErr0 = 1, kBarBase0 = 3;
+constexpr int kCH = 1024;      // updates staged per chunk
+constexpr int kSB = 16;        // updates per sub-block
+constexpr int kLag = 2 * kSB;  // correlation lags kept per row: 0 .. 31 (lag 0 is zero)
+// warp 0 decides; warps 4 and 8 share its scheduler and do no phase work;
+// helper warps 1, 2, 3, 5 form the tap group, 6, 7, 9, 10 the correlation
+// group, 11 stages only
+constexpr int kWarps = 12;
+constexpr int kThreads = 32 * kWarps;
+constexpr int kBarTap = 1;     // named barrier of the tap group (128 threads)
+
+// shared-memory layout of lms_kernel<T> (float2 units)
+__host__ __device__ constexpr int lms_nsx(int T) { return 2 * kCH + (T - 1) + 2 * (kSB + kLag) + 4; }
+__host__ __device__ constexpr int lms_off_h(int T) { return 2 * lms_nsx(T); }
+__host__ __device__ constexpr int lms_off_r(int T) { return lms_off_h(T) + 4 * T; }
+__host__ __device__ constexpr int lms_off_b(int T) { return lms_off_r(T) + 2 * kSB * kLag; }
+__host__ __device__ constexpr int lms_off_e(int T) { return lms_off_b(T) + 2 * kSB * 2; }
+__host__ __device__ constexpr int lms_off_rot(int T) { return lms_off_e(T) + 2 * kSB * 2; }
+__host__ __device__ constexpr int lms_off_pc(int T) { return lms_off_rot(T) + 3 * kCH; }
+__host__ __device__ constexpr int lms_smem_f2(int T) { return lms_off_pc(T) + kCH / 4 + kCH / 8; }
 
 __device__ __forceinline__ void bar_sync(int id, int n) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
-}
-__device__ __forceinline__ void bar_arrive(int id, int n) {
-    asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"(n) : "memory");
 }
 
 struct Tables {
@@ -83,97 +92,172 @@ __device__ __forceinline__ int argmin_label(float dist, bool valid, int label) {
     return (int)__reduce_min_sync(0xffffffffu, key);
 }
 
-// (y0, y1) from per-lane partials of both outputs: xor-16 halving step, four
-// xor steps within the half warp, then exchange of the halves.
-__device__ __forceinline__ void reduce_pair(float2 a, float2 b, int p, float2 &y0, float2 &y1) {
-    float2 send = p ? a : b, keep = p ? b : a;
-    keep.x += __shfl_xor_sync(0xffffffffu, send.x, 16);
-    keep.y += __shfl_xor_sync(0xffffffffu, send.y, 16);
-#pragma unroll
-    for (int m = 8; m > 0; m >>= 1) {
-        keep.x += __shfl_xor_sync(0xffffffffu, keep.x, m);
-        keep.y += __shfl_xor_sync(0xffffffffu, keep.y, m);
-    }
-    float2 other;
-    other.x = __shfl_xor_sync(0xffffffffu, keep.x, 16);
-    other.y = __shfl_xor_sync(0xffffffffu, keep.y, 16);
-    y0 = p ? other : keep;
-    y1 = p ? keep : other;
-}
-
 // Sequential CMA (MODE 0), DD-LMS (MODE 1) or data-aided LMS (MODE 3).
 //
-// Lane (p, j) = (lane >> 4, lane & 15) holds h_qp[j + 16 i] of both outputs
-// q.  The recursion is written in look-ahead form: with X_k the stacked
-// input window of symbol k and h_k the taps after update k,
-//   y_k = h_{k-1}^H X_k = h_{k-2}^H X_k + mu e_{k-1} X_{k-1}^H X_k,
-// so the 32-lane reduction of base_k = h_{k-2}^H X_k is issued two updates
-// ahead and overlaps with the decision of the update in between; only the
-// scalar correction with r1_k = X_{k-1}^H X_k (precomputed by the whole block
-// for the staged span) is on the sequential path.
+// With X_k the stacked input window of symbol k, h_k the taps after update
+// k and r(j, k) = X_j^H X_k, the output of update k is
+//   y_k = h_{k-1}^H X_k = H^H X_k + sum_{j = j0}^{k-1} mu e_j r(j, k)
+// for any earlier taps H = h_{j0-1}.  Updates run in sub-blocks of kSB = 16;
+// for update k of sub-block s the library takes H = the taps before
+// sub-block s - 1, so the sum has at most 2 kSB - 1 terms and everything but
+// the scalar corrections is computed a sub-block ahead by helper warps:
+// * decision warp: lane l holds the partial y of update 16 s + l (l < 16:
+//   this sub-block, l >= 16: the next); per update it takes the decision on
+//   y_k, every lane adds mu e_k r(k, 16 s + l) to its own partial (one
+//   complex FMA per output), and y_{k+1} is lane k+1's partial, fetched by a
+//   shuffle while the decision ran, plus mu e_k r(k, k + 1);
+// * tap group: applies the previous sub-block's 16 updates to the taps,
+//   h += sum_j mu conj(e_j) X_j, then forms H^H X_k for the next sub-block;
+// * correlation group: r(j, j + d) for the next sub-block's rows j and lags
+//   d < 32, by a window sliding along j (two products in, two out per row).
+// One __syncthreads per sub-block hands the products over.
 template <int T, int DIMS, int MODE>
-__global__ void __launch_bounds__(256, 1)
+__global__ void __launch_bounds__(kThreads, 1)
 lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_in,
            float2 *__restrict__ taps_out, long k0, int n_upd, const uint16_t *__restrict__ pcode,
            long pcode_stride, int passes, float mu, const uint8_t *__restrict__ ref_lab,
            long ref_stride, int sk, const __grid_constant__ FmtDev f) {
     constexpr int D = (T - 1) / 2;
-    constexpr int NSX = 2 * kCH + 2 * D + 8;   // + slack read by the look-ahead past the span
-    constexpr int NT = (T + 15) / 16;
-    __shared__ float2 xs[2][NSX];
-    __shared__ float2 r1s[kCH];
-    __shared__ uint16_t pc[kCH];
-    __shared__ uint8_t rl[kCH];
+    constexpr int NSX = lms_nsx(T);
     __shared__ Tables tb;
-    // dynamic: exp(j phi_k) of the span (MODE 1, 3) and the data-aided
-    // targets d_q exp(j phi_k) (MODE 3), prepared by the whole block
-    // and the exchange between the decision and tap warps: e_k and base_k
-    // of both outputs as (re0, im0, re1, im1)
     extern __shared__ float2 dyn_sm[];
-    float2 *rots = dyn_sm;
-    float2 *tg0 = dyn_sm + kCH, *tg1 = dyn_sm + 2 * kCH;
-    float4 *es = reinterpret_cast<float4 *>(dyn_sm + 3 * kCH);
-    float4 *bs = es + kCH;
-    const int s = blockIdx.x;
+    // local sample index of x_p[2 (kb + k) + D - t] is 2 k + 2 D - t
+    float2 *xs0 = dyn_sm, *xs1 = dyn_sm + NSX;
+    float2 *Hs = dyn_sm + lms_off_h(T);               // taps [q][p][t]
+    float2 *Rt = dyn_sm + lms_off_r(T);               // [2][kSB][kLag]: r(j, j + d)
+    float2 *bsb = dyn_sm + lms_off_b(T);              // [2][kSB][q]: H^H X_k
+    float4 *es = reinterpret_cast<float4 *>(dyn_sm + lms_off_e(T));   // [2][kSB]: mu e_k
+    float2 *rots = dyn_sm + lms_off_rot(T);           // exp(j phi_k) (MODE 1, 3)
+    float2 *tg0 = rots + kCH, *tg1 = rots + 2 * kCH;  // d_q exp(j phi_k) (MODE 3)
+    uint16_t *pc = reinterpret_cast<uint16_t *>(dyn_sm + lms_off_pc(T));
+    uint8_t *rl = reinterpret_cast<uint8_t *>(pc + kCH);
+    const int s_id = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int p = lane >> 4, j = lane & 15;
+    const int hw = (warp & 3) ? warp - 1 - (warp >> 2) : -1;   // helper index 0 .. 8
+    const bool tap_grp = hw >= 0 && hw < 4, cor_grp = hw >= 4 && hw < 8;
+    const int gt = (hw & 3) * 32 + lane;                       // index within a group
+    auto xsp = [&](int pp) { return pp ? xs1 : xs0; };
     load_tables(tb, f);
-
-    float2 h[2][NT];
-#pragma unroll
-    for (int q = 0; q < 2; ++q)
-#pragma unroll
-        for (int i = 0; i < NT; ++i) {
-            const int t = j + 16 * i;
-            h[q][i] = (t < T) ? taps_in[(((long)s * 2 + q) * 2 + p) * T + t] : make_float2(0.f, 0.f);
-        }
-    const long xoff = (long)s * 2 * ns;
+    for (int i = threadIdx.x; i < 4 * T; i += blockDim.x) Hs[i] = taps_in[(long)s_id * 4 * T + i];
+    const long xoff = (long)s_id * 2 * ns;
     const int qt_step = 4 / f.S;
+
+    // tap group: h += sum_{i < m} mu conj(e_{jb + i}) X_{jb + i}; thread
+    // (q, p, t) owns one tap
+    auto tap_update = [&](int jb, int m, const float4 *E) {
+        if (gt < 4 * T) {
+            const int q = gt / (2 * T), rem = gt - q * 2 * T, pp = rem / T, t = rem - pp * T;
+            const float2 *xp = xsp(pp) + 2 * jb + 2 * D - t;
+            float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+            if (m == kSB) {
+#pragma unroll
+                for (int i = 0; i < kSB; i += 2) {
+                    const float4 e = E[i], f1 = E[i + 1];
+                    a0 = cadd(a0, cmulc(q ? make_float2(e.z, e.w) : make_float2(e.x, e.y), xp[2 * i]));
+                    a1 = cadd(a1, cmulc(q ? make_float2(f1.z, f1.w) : make_float2(f1.x, f1.y), xp[2 * i + 2]));
+                }
+            } else {
+                for (int i = 0; i < m; ++i) {
+                    const float4 e = E[i];
+                    a0 = cadd(a0, cmulc(q ? make_float2(e.z, e.w) : make_float2(e.x, e.y), xp[2 * i]));
+                }
+            }
+            Hs[gt] = cadd(Hs[gt], cadd(a0, a1));
+        }
+    };
+    // tap group: H^H X_k for the kSB updates from kb0 into bsb row set `buf`;
+    // thread (kk, q, p, half) sums half of one polarisation's taps
+    auto bases = [&](int kb0, int buf) {
+        const int kk = gt >> 3, q = (gt >> 2) & 1, pp = (gt >> 1) & 1, half = gt & 1;
+        const int k = kb0 + kk;
+        const float2 *xp = xsp(pp);
+        const float2 *hq = Hs + (q * 2 + pp) * T;
+        float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int tt = 0; tt < 16; tt += 2) {
+            const int t = 16 * half + tt;
+            if (t < T) a0 = cadd(a0, cmulc(hq[t], xp[2 * k + 2 * D - t]));
+            if (t + 1 < T) a1 = cadd(a1, cmulc(hq[t + 1], xp[2 * k + 2 * D - t - 1]));
+        }
+        float2 acc = cadd(a0, a1);
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+        acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+        acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+        if ((gt & 3) == 0) bsb[(buf * kSB + kk) * 2 + q] = acc;
+    };
+    // correlation group: r(j, j + d) = sum_{u = 2j}^{2j + 2D} c[u] with
+    // c[u] = sum_p conj(x_p[u]) x_p[u + 2d] (local sample index u); thread
+    // (d, p) slides one row per step (two products in, two out) and keeps the
+    // products of the last 32 samples in a register ring (slot u mod 32, so
+    // a sub-block of 16 rows turns the ring exactly once); the
+    // polarisations are summed by a shuffle
+    const int cd = gt >> 1, cp = gt & 1;
+    float2 ring[32];
+    float2 Rc = make_float2(0.f, 0.f);
+    auto corr_first = [&](int buf) {          // rows 0 .. kSB - 1 of the chunk
+        const float2 *xp = xsp(cp);
+#pragma unroll
+        for (int u = 0; u < 32; ++u) ring[u] = make_float2(0.f, 0.f);
+        Rc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = 0; u <= 2 * D; ++u) {
+            ring[u] = cmulc(xp[u], xp[u + 2 * cd]);
+            Rc = cadd(Rc, ring[u]);
+        }
+#pragma unroll
+        for (int jj = 0; jj < kSB; ++jj) {
+            if (jj > 0) {
+                const int j = jj, u1 = 2 * j + 2 * D - 1, u2 = 2 * j + 2 * D;
+                const float2 old = cadd(ring[(2 * j - 2) & 31], ring[(2 * j - 1) & 31]);
+                ring[u1 & 31] = cmulc(xp[u1], xp[u1 + 2 * cd]);
+                ring[u2 & 31] = cmulc(xp[u2], xp[u2 + 2 * cd]);
+                Rc = cadd(Rc, csub(cadd(ring[u1 & 31], ring[u2 & 31]), old));
+            }
+            float2 Rs;
+            Rs.x = Rc.x + __shfl_xor_sync(0xffffffffu, Rc.x, 1);
+            Rs.y = Rc.y + __shfl_xor_sync(0xffffffffu, Rc.y, 1);
+            if (cp == 0) Rt[(buf * kSB + jj) * kLag + cd] = cd ? Rs : make_float2(0.f, 0.f);
+        }
+    };
+    auto corr_next = [&](int jr0, int buf) {   // rows jr0 .. jr0 + kSB - 1, jr0 = 16 s'
+        const float2 *xp = xsp(cp);
+#pragma unroll
+        for (int jj = 0; jj < kSB; ++jj) {
+            const int j = jr0 + jj, u1 = 2 * j + 2 * D - 1, u2 = 2 * j + 2 * D;
+            // 2 jr0 is a multiple of 32: the slots depend on jj only
+            const int s_old0 = (2 * jj - 2) & 31, s_old1 = (2 * jj - 1) & 31;
+            const int s1 = (2 * jj + 2 * D - 1) & 31, s2 = (2 * jj + 2 * D) & 31;
+            const float2 old = cadd(ring[s_old0], ring[s_old1]);
+            ring[s1] = cmulc(xp[u1], xp[u1 + 2 * cd]);
+            ring[s2] = cmulc(xp[u2], xp[u2 + 2 * cd]);
+            Rc = cadd(Rc, csub(cadd(ring[s1], ring[s2]), old));
+            float2 Rs;
+            Rs.x = Rc.x + __shfl_xor_sync(0xffffffffu, Rc.x, 1);
+            Rs.y = Rc.y + __shfl_xor_sync(0xffffffffu, Rc.y, 1);
+            if (cp == 0) Rt[(buf * kSB + jj) * kLag + cd] = cd ? Rs : make_float2(0.f, 0.f);
+        }
+    };
+
     for (int pass = 0; pass < passes; ++pass) {
         for (int c0 = 0; c0 < n_upd; c0 += kCH) {
             const int n = min(kCH, n_upd - c0);
             const long kb = k0 + c0;
-            const int nsx = 2 * n + 2 * D + 8;
+            const int nsb = (n + kSB - 1) / kSB;
+            const int nsx = 2 * n + 2 * D + 2 * (kSB + kLag) + 4;
             __syncthreads();
-            // local sample index of symbol kb + kk, tap t: 2 kk + 2 + 2D - t
             for (int i = threadIdx.x; i < 2 * nsx; i += blockDim.x) {
                 const int pp = i / nsx, jj = i - pp * nsx;
-                const long g = 2 * (kb - 1) - D + jj;
-                xs[pp][jj] = (g >= 0 && g < ns) ? ld_sample(x, xoff + (long)pp * ns + g, sk) : make_float2(0.f, 0.f);
+                const long g = 2 * kb - D + jj;
+                xsp(pp)[jj] = (g >= 0 && g < ns) ? ld_sample(x, xoff + (long)pp * ns + g, sk) : make_float2(0.f, 0.f);
             }
             if (MODE != 0)
-                for (int i = threadIdx.x; i < n; i += blockDim.x) pc[i] = pcode[(long)s * pcode_stride + kb + i];
+                for (int i = threadIdx.x; i < n; i += blockDim.x) pc[i] = pcode[(long)s_id * pcode_stride + kb + i];
             if (MODE == 3)
-                for (int i = threadIdx.x; i < n; i += blockDim.x) rl[i] = ref_lab[(long)s * ref_stride + kb + i];
+                for (int i = threadIdx.x; i < n; i += blockDim.x) rl[i] = ref_lab[(long)s_id * ref_stride + kb + i];
             __syncthreads();
-            for (int kk = threadIdx.x; kk < n; kk += blockDim.x) {   // r1_k = X_{k-1}^H X_k
-                float2 acc = make_float2(0.f, 0.f);
-                for (int pp = 0; pp < 2; ++pp)
-#pragma unroll 8
-                    for (int t = 0; t < T; ++t)
-                        acc = cadd(acc, cmulc(xs[pp][2 * kk + 2 * D - t], xs[pp][2 * kk + 2 + 2 * D - t]));
-                r1s[kk] = acc;
-                if (MODE != 0) {
+            if (MODE != 0)
+                for (int kk = threadIdx.x; kk < n; kk += blockDim.x) {
                     // exp(j phi_k) = cs_b j^qt
                     const unsigned code = pc[kk];
                     const int b = min((int)(code & 255), f.B - 1);
@@ -199,60 +283,12 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
                         tg1[kk] = cmul(d1, rot);
                     }
                 }
-            }
+            if (tap_grp) bases(0, 0);
+            if (cor_grp && hw < 6) corr_first(0);
             __syncthreads();
-            auto xval = [&](int kk, int i) -> float2 {
-                const int t = j + 16 * i;
-                return (t < T) ? xs[p][2 * kk + 2 + 2 * D - t] : make_float2(0.f, 0.f);
-            };
-            auto base = [&](int kk, float2 &b0, float2 &b1) {
-                float2 a = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int i = 0; i < NT; ++i) {
-                    const float2 xv = xval(kk, i);
-                    a = cadd(a, cmulc(h[0][i], xv));
-                    c = cadd(c, cmulc(h[1][i], xv));
-                }
-                reduce_pair(a, c, p, b0, b1);
-            };
-            if (warp == 1) {
-                // tap warp: h_k = h_{k-1} + mu conj(e_k) X_k, then publishes
-                // base_{k+2} = h_k^H X_{k+2} (base_0, base_1 from the
-                // chunk's initial taps); only bases inside the span are
-                // published, so every barrier phase is matched
-                float2 b0, b1;
-                base(0, b0, b1);
-                bs[0] = make_float4(b0.x, b0.y, b1.x, b1.y);
-                bar_arrive(kBarBase0, 64);
-                if (n > 1) {
-                    base(1, b0, b1);
-                    bs[1] = make_float4(b0.x, b0.y, b1.x, b1.y);
-                    bar_arrive(kBarBase0 + 1, 64);
-                }
-#pragma unroll 2
-                for (int kk = 0; kk < n; ++kk) {
-                    bar_sync(kBarErr0 + (kk & 1), 64);
-                    const float4 e = es[kk];
-                    const float2 c0v = make_float2(mu * e.x, -mu * e.y), c1v = make_float2(mu * e.z, -mu * e.w);
-#pragma unroll
-                    for (int i = 0; i < NT; ++i) {
-                        const float2 xv = xval(kk, i);
-                        h[0][i] = cadd(h[0][i], cmul(c0v, xv));
-                        h[1][i] = cadd(h[1][i], cmul(c1v, xv));
-                    }
-                    if (kk + 2 < n) {
-                        base(kk + 2, b0, b1);
-                        bs[kk + 2] = make_float4(b0.x, b0.y, b1.x, b1.y);
-                        bar_arrive(kBarBase0 + (kk & 1), 64);
-                    }
-                }
-                continue;
-            }
-            if (warp != 0) continue;
-            // decision warp: y_k = base_k + mu e_{k-1} r1_k, e_k, published
-            // for the tap warp
-            // this lane's orbit (DD decisions): representative, energy, and
-            // the labels of its S rotations packed one per byte
+
+            // decision warp state: partial y of update 16 s + lane, both outputs
+            float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
             const int o = lane & 15;
             const bool valid = o < f.n_orb;
             const float4 r = tb.orb[valid ? o : 0];
@@ -261,64 +297,99 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
 #pragma unroll
             for (int k = 0; k < 4; ++k) lab4 |= (unsigned)(tb.orblab[valid ? o : 0][k] & 255) << (8 * k);
             auto label_of = [&](int k) { return (int)((lab4 >> (8 * k)) & 255u); };
-            float2 ep0 = make_float2(0.f, 0.f), ep1 = make_float2(0.f, 0.f);
-#pragma unroll 2
-            for (int kk = 0; kk < n; ++kk) {
-                const float2 r1 = r1s[kk];
-                bar_sync(kBarBase0 + (kk & 1), 64);
-                const float4 bb = bs[kk];
-                const float2 y0 = cadd(make_float2(bb.x, bb.y), cmul(make_float2(mu * ep0.x, mu * ep0.y), r1));
-                const float2 y1 = cadd(make_float2(bb.z, bb.w), cmul(make_float2(mu * ep1.x, mu * ep1.y), r1));
-                float2 e0, e1;
-                if (MODE == 0) {
-                    const float g0 = f.R2 - cnorm(y0), g1 = f.R2 - cnorm(y1);
-                    e0 = make_float2(g0 * y0.x, g0 * y0.y);
-                    e1 = make_float2(g1 * y1.x, g1 * y1.y);
-                } else if (MODE == 3) {
-                    e0 = csub(tg0[kk], y0);
-                    e1 = csub(tg1[kk], y1);
-                } else {
-                    const float2 rot = rots[kk];                               // exp(j phi)
-                    float2 d0, d1;
-                    const float2 z0 = cmulc(rot, y0), z1 = cmulc(rot, y1);   // y exp(-j phi)
-                    if (DIMS == 4) {
-                        const float P = (z0.x * r.x + z0.y * r.y) + (z1.x * r.z + z1.y * r.w);
-                        const float Q = (z0.y * r.x - z0.x * r.y) + (z1.y * r.z - z1.x * r.w);
-                        float v;
-                        int k;
-                        best_rot(P, Q, f.S, v, k);
-                        const float dist = (cnorm(z0) + cnorm(z1)) + (eo - 2.f * v);
-                        const float4 pt = tb.pts[argmin_label(dist, valid, label_of(k))];
-                        d0 = make_float2(pt.x, pt.y);
-                        d1 = make_float2(pt.z, pt.w);
+            for (int s = 0; s < nsb; ++s) {
+                const int buf = s & 1;
+                if (warp == 0) {
+                    // lanes < 16 take this sub-block's bases plus what the
+                    // previous sub-block left in lanes >= 16
+                    float2 c0, c1;
+                    c0.x = __shfl_down_sync(0xffffffffu, v0.x, 16);
+                    c0.y = __shfl_down_sync(0xffffffffu, v0.y, 16);
+                    c1.x = __shfl_down_sync(0xffffffffu, v1.x, 16);
+                    c1.y = __shfl_down_sync(0xffffffffu, v1.y, 16);
+                    if (lane < kSB) {
+                        v0 = cadd(c0, bsb[(buf * kSB + lane) * 2]);
+                        v1 = cadd(c1, bsb[(buf * kSB + lane) * 2 + 1]);
                     } else {
-                        float v0, v1;
-                        int k0r, k1r;
-                        best_rot(z0.x * r.x + z0.y * r.y, z0.y * r.x - z0.x * r.y, f.S, v0, k0r);
-                        best_rot(z1.x * r.x + z1.y * r.y, z1.y * r.x - z1.x * r.y, f.S, v1, k1r);
-                        const float4 p0 = tb.pts[argmin_label(cnorm(z0) + eo - 2.f * v0, valid, label_of(k0r))];
-                        const float4 p1 = tb.pts[argmin_label(cnorm(z1) + eo - 2.f * v1, valid, label_of(k1r))];
-                        d0 = make_float2(p0.x, p0.y);
-                        d1 = make_float2(p1.x, p1.y);
+                        v0 = v1 = make_float2(0.f, 0.f);
                     }
-                    e0 = csub(cmul(d0, rot), y0);
-                    e1 = csub(cmul(d1, rot), y1);
+                    const float2 *Rr = Rt + buf * kSB * kLag;
+                    const int ms = min(kSB, n - kSB * s);
+                    float2 y0, y1;
+                    y0.x = __shfl_sync(0xffffffffu, v0.x, 0);
+                    y0.y = __shfl_sync(0xffffffffu, v0.y, 0);
+                    y1.x = __shfl_sync(0xffffffffu, v1.x, 0);
+                    y1.y = __shfl_sync(0xffffffffu, v1.y, 0);
+                    for (int i = 0; i < ms; ++i) {
+                        const int k = kSB * s + i;
+                        const float2 rc = Rr[i * kLag + (lane > i ? lane - i : 0)];   // r(k, 16 s + lane)
+                        const float2 r1 = Rr[i * kLag + 1];                             // r(k, k + 1)
+                        // the next update's partial before this update's term:
+                        // fetched while the decision runs
+                        float2 w0, w1;
+                        w0.x = __shfl_sync(0xffffffffu, v0.x, i + 1);
+                        w0.y = __shfl_sync(0xffffffffu, v0.y, i + 1);
+                        w1.x = __shfl_sync(0xffffffffu, v1.x, i + 1);
+                        w1.y = __shfl_sync(0xffffffffu, v1.y, i + 1);
+                        float2 e0, e1;
+                        if (MODE == 0) {
+                            const float g0 = f.R2 - cnorm(y0), g1 = f.R2 - cnorm(y1);
+                            e0 = make_float2(g0 * y0.x, g0 * y0.y);
+                            e1 = make_float2(g1 * y1.x, g1 * y1.y);
+                        } else if (MODE == 3) {
+                            e0 = csub(tg0[k], y0);
+                            e1 = csub(tg1[k], y1);
+                        } else {
+                            const float2 rot = rots[k];                               // exp(j phi)
+                            float2 d0, d1;
+                            const float2 z0 = cmulc(rot, y0), z1 = cmulc(rot, y1);   // y exp(-j phi)
+                            if (DIMS == 4) {
+                                const float P = (z0.x * r.x + z0.y * r.y) + (z1.x * r.z + z1.y * r.w);
+                                const float Q = (z0.y * r.x - z0.x * r.y) + (z1.y * r.z - z1.x * r.w);
+                                float v;
+                                int kr;
+                                best_rot(P, Q, f.S, v, kr);
+                                const float dist = (cnorm(z0) + cnorm(z1)) + (eo - 2.f * v);
+                                const float4 pt = tb.pts[argmin_label(dist, valid, label_of(kr))];
+                                d0 = make_float2(pt.x, pt.y);
+                                d1 = make_float2(pt.z, pt.w);
+                            } else {
+                                float va, vb;
+                                int ka, kc;
+                                best_rot(z0.x * r.x + z0.y * r.y, z0.y * r.x - z0.x * r.y, f.S, va, ka);
+                                best_rot(z1.x * r.x + z1.y * r.y, z1.y * r.x - z1.x * r.y, f.S, vb, kc);
+                                const float4 p0 = tb.pts[argmin_label(cnorm(z0) + eo - 2.f * va, valid, label_of(ka))];
+                                const float4 p1 = tb.pts[argmin_label(cnorm(z1) + eo - 2.f * vb, valid, label_of(kc))];
+                                d0 = make_float2(p0.x, p0.y);
+                                d1 = make_float2(p1.x, p1.y);
+                            }
+                            e0 = csub(cmul(d0, rot), y0);
+                            e1 = csub(cmul(d1, rot), y1);
+                        }
+                        const float2 me0 = make_float2(mu * e0.x, mu * e0.y), me1 = make_float2(mu * e1.x, mu * e1.y);
+                        v0 = cadd(v0, cmul(me0, rc));
+                        v1 = cadd(v1, cmul(me1, rc));
+                        // lane i + 1's new partial, formed the same way in every lane
+                        y0 = cadd(w0, cmul(me0, r1));
+                        y1 = cadd(w1, cmul(me1, r1));
+                        es[buf * kSB + i] = make_float4(me0.x, me0.y, me1.x, me1.y);   // every lane: the same value
+                    }
+                } else if (tap_grp) {
+                    if (s >= 1) tap_update(kSB * (s - 1), kSB, es + (buf ^ 1) * kSB);
+                    bar_sync(kBarTap, 128);
+                    if (s + 1 < nsb) bases(kSB * (s + 1), buf ^ 1);
+                } else if (cor_grp && hw < 6) {
+                    if (s + 1 < nsb) corr_next(kSB * (s + 1), buf ^ 1);
                 }
-                es[kk] = make_float4(e0.x, e0.y, e1.x, e1.y);   // every lane: the same value
-                bar_arrive(kBarErr0 + (kk & 1), 64);
-                ep0 = e0; ep1 = e1;
+                __syncthreads();
             }
+            // the last sub-block's updates (the next chunk, the next pass or
+            // the output read the taps after the next barrier)
+            if (tap_grp) tap_update(kSB * (nsb - 1), n - kSB * (nsb - 1), es + ((nsb - 1) & 1) * kSB);
         }
     }
-    if (warp == 1) {
-#pragma unroll
-        for (int q = 0; q < 2; ++q)
-#pragma unroll
-            for (int i = 0; i < NT; ++i) {
-                const int t = j + 16 * i;
-                if (t < T) taps_out[(((long)s * 2 + q) * 2 + p) * T + t] = h[q][i];
-            }
-    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < 4 * T; i += blockDim.x) taps_out[(long)s_id * 4 * T + i] = Hs[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -480,11 +551,11 @@ cudaError_t lms_launch_one(const void *x, long ns, const float2 *ti, float2 *to,
     int dev = 0, optin = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    int dyn = optin - (int)fa.sharedSizeBytes;
-    if (dyn < (int)(kDynBytes)) return cudaErrorInvalidValue;   // rotations, targets, exchange
+    const int dyn = optin - (int)fa.sharedSizeBytes;
+    if (dyn < (int)(lms_smem_f2(T) * sizeof(float2))) return cudaErrorInvalidValue;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
-    kern<<<S, 256, dyn, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, sk, f);
+    kern<<<S, kThreads, dyn, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, sk, f);
     return cudaGetLastError();
 }
 
