@@ -18,6 +18,7 @@
 // a known sequence) is align_kernel: it correlates the equalised training
 // span with the known symbols and fixes the output order and phases.
 #include <algorithm>
+#include <type_traits>
 
 #include "rx_internal.h"
 
@@ -32,12 +33,14 @@ constexpr int kLag = 2 * kSB;  // correlation lags kept per row: 0 .. 31 (lag 0 
 constexpr int kWarps = 12;
 constexpr int kThreads = 32 * kWarps;
 constexpr int kBarTap = 1;     // named barrier of the tap group (128 threads)
+constexpr int kBarCor = 2;     // named barrier of the correlation group (128 threads)
 
 // shared-memory layout of lms_kernel<T> (float2 units)
 __host__ __device__ constexpr int lms_nsx(int T) { return 2 * kCH + (T - 1) + 2 * (kSB + kLag) + 4; }
 __host__ __device__ constexpr int lms_off_h(int T) { return 2 * lms_nsx(T); }
 __host__ __device__ constexpr int lms_off_r(int T) { return lms_off_h(T) + 4 * T; }
-__host__ __device__ constexpr int lms_off_b(int T) { return lms_off_r(T) + 2 * kSB * kLag; }
+__host__ __device__ constexpr int lms_off_rp(int T) { return lms_off_r(T) + 2 * kSB * kLag; }
+__host__ __device__ constexpr int lms_off_b(int T) { return lms_off_rp(T) + kSB * kLag * 4; }
 __host__ __device__ constexpr int lms_off_e(int T) { return lms_off_b(T) + 2 * kSB * 2; }
 __host__ __device__ constexpr int lms_off_rot(int T) { return lms_off_e(T) + 2 * kSB * 2; }
 __host__ __device__ constexpr int lms_off_pc(int T) { return lms_off_rot(T) + 3 * kCH; }
@@ -66,27 +69,30 @@ __device__ __forceinline__ void load_tables(Tables &tb, const FmtDev &f) {
     for (int i = threadIdx.x; i < f.B; i += blockDim.x) tb.cs[i] = make_float2(f.cs[i][0], f.cs[i][1]);
 }
 
-// best rotation of an orbit given P + jQ = sum_p z_p conj(rep_p):
-// Re of the correlation with rep * j^k is P, Q, -P, -Q for k = 0..3.
-__device__ __forceinline__ void best_rot(float P, float Q, int S, float &v, int &k) {
+// Best rotation of an orbit given P + jQ = sum_p y_p conj(rep_p exp(j phi))
+// (Re of the correlation with rep * j^k is P, Q, -P, -Q for k = 0..3): its
+// value v and the label of that rotation (lab[k] = label of rep * j^k).
+__device__ __forceinline__ void best_rot_label(float P, float Q, int S, const int (&lab)[4], float &v, int &label) {
     if (S == 4) {
         const float aP = fabsf(P), aQ = fabsf(Q);
         const bool pw = aP >= aQ;
         v = pw ? aP : aQ;
-        k = pw ? (P >= 0.f ? 0 : 2) : (Q >= 0.f ? 1 : 3);
+        label = pw ? (P >= 0.f ? lab[0] : lab[2]) : (Q >= 0.f ? lab[1] : lab[3]);
     } else if (S == 2) {
-        v = fabsf(P); k = P >= 0.f ? 0 : 1;
+        v = fabsf(P);
+        label = P >= 0.f ? lab[0] : lab[1];
     } else {
-        v = P; k = 0;
+        v = P;
+        label = lab[0];
     }
 }
 
-// Nearest table point of the candidates held by the lanes: lane o (o < 16)
-// holds orbit o's best rotation, its squared distance and its label; the
-// minimum distance over the lanes wins and exact ties go to the lowest label.
-// Two warp reductions return the winning label itself.
-__device__ __forceinline__ int argmin_label(float dist, bool valid, int label) {
-    const unsigned bits = valid ? __float_as_uint(fmaxf(dist, 0.f)) : 0xffffffffu;
+// Nearest table point of the candidates held by the lanes: each lane holds
+// its orbit's best rotation, the squared distance and the label (lanes
+// without an orbit hold +inf); the minimum distance wins and exact ties go
+// to the lowest label.  Two warp reductions return the winning label.
+__device__ __forceinline__ int argmin_label(float dist, int label) {
+    const unsigned bits = __float_as_uint(fmaxf(dist, 0.f));
     const unsigned mn = __reduce_min_sync(0xffffffffu, bits);
     const unsigned key = (bits == mn) ? (unsigned)label : 0xffffffffu;
     return (int)__reduce_min_sync(0xffffffffu, key);
@@ -124,9 +130,10 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
     // local sample index of x_p[2 (kb + k) + D - t] is 2 k + 2 D - t
     float2 *xs0 = dyn_sm, *xs1 = dyn_sm + NSX;
     float2 *Hs = dyn_sm + lms_off_h(T);               // taps [q][p][t]
-    float2 *Rt = dyn_sm + lms_off_r(T);               // [2][kSB][kLag]: r(j, j + d)
+    float2 *Rt = dyn_sm + lms_off_r(T);               // [2][kSB][kLag]: mu r(j, j + d)
+    float2 *Rp = dyn_sm + lms_off_rp(T);              // [kSB][kLag][4]: per (p, parity) partial sums
     float2 *bsb = dyn_sm + lms_off_b(T);              // [2][kSB][q]: H^H X_k
-    float4 *es = reinterpret_cast<float4 *>(dyn_sm + lms_off_e(T));   // [2][kSB]: mu e_k
+    float4 *es = reinterpret_cast<float4 *>(dyn_sm + lms_off_e(T));   // [2][kSB]: e_k
     float2 *rots = dyn_sm + lms_off_rot(T);           // exp(j phi_k) (MODE 1, 3)
     float2 *tg0 = rots + kCH, *tg1 = rots + 2 * kCH;  // d_q exp(j phi_k) (MODE 3)
     uint16_t *pc = reinterpret_cast<uint16_t *>(dyn_sm + lms_off_pc(T));
@@ -142,7 +149,7 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
     const long xoff = (long)s_id * 2 * ns;
     const int qt_step = 4 / f.S;
 
-    // tap group: h += sum_{i < m} mu conj(e_{jb + i}) X_{jb + i}; thread
+    // tap group: h += mu sum_{i < m} conj(e_{jb + i}) X_{jb + i}; thread
     // (q, p, t) owns one tap
     auto tap_update = [&](int jb, int m, const float4 *E) {
         if (gt < 4 * T) {
@@ -162,7 +169,8 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
                     a0 = cadd(a0, cmulc(q ? make_float2(e.z, e.w) : make_float2(e.x, e.y), xp[2 * i]));
                 }
             }
-            Hs[gt] = cadd(Hs[gt], cadd(a0, a1));
+            const float2 a = cadd(a0, a1);
+            Hs[gt] = cadd(Hs[gt], make_float2(mu * a.x, mu * a.y));
         }
     };
     // tap group: H^H X_k for the kSB updates from kb0 into bsb row set `buf`;
@@ -187,56 +195,77 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
         if ((gt & 3) == 0) bsb[(buf * kSB + kk) * 2 + q] = acc;
     };
     // correlation group: r(j, j + d) = sum_{u = 2j}^{2j + 2D} c[u] with
-    // c[u] = sum_p conj(x_p[u]) x_p[u + 2d] (local sample index u); thread
-    // (d, p) slides one row per step (two products in, two out) and keeps the
-    // products of the last 32 samples in a register ring (slot u mod 32, so
-    // a sub-block of 16 rows turns the ring exactly once); the
-    // polarisations are summed by a shuffle
-    const int cd = gt >> 1, cp = gt & 1;
-    float2 ring[32];
+    // c[u] = sum_p conj(x_p[u]) x_p[u + 2d] (local sample index u).  Thread
+    // (d, p, parity) slides its share of the window one row per step (one
+    // product in, one out) and keeps its products of the last 32 samples in a
+    // register ring (slot (u >> 1) mod 16, so a sub-block of 16 rows turns it
+    // exactly once); the four partial sums per (row, lag) go through shared
+    // memory and are added, times mu, after a group barrier
+    // warps 6, 7 take the even samples, 9, 10 the odd ones (a warp-uniform
+    // parity keeps the ring indices static); lane pairs are the two
+    // polarisations of one lag
+    const int ce = (hw >> 1) & 1, cd = ((hw & 1) * 32 + lane) >> 1, cp = lane & 1;
+    float2 ring[16];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) ring[i] = make_float2(0.f, 0.f);
     float2 Rc = make_float2(0.f, 0.f);
-    auto corr_first = [&](int buf) {          // rows 0 .. kSB - 1 of the chunk
-        const float2 *xp = xsp(cp);
+    auto corr_sum = [&](int buf) {
+        bar_sync(kBarCor, 128);
 #pragma unroll
-        for (int u = 0; u < 32; ++u) ring[u] = make_float2(0.f, 0.f);
-        Rc = make_float2(0.f, 0.f);
-#pragma unroll
-        for (int u = 0; u <= 2 * D; ++u) {
-            ring[u] = cmulc(xp[u], xp[u + 2 * cd]);
-            Rc = cadd(Rc, ring[u]);
-        }
-#pragma unroll
-        for (int jj = 0; jj < kSB; ++jj) {
-            if (jj > 0) {
-                const int j = jj, u1 = 2 * j + 2 * D - 1, u2 = 2 * j + 2 * D;
-                const float2 old = cadd(ring[(2 * j - 2) & 31], ring[(2 * j - 1) & 31]);
-                ring[u1 & 31] = cmulc(xp[u1], xp[u1 + 2 * cd]);
-                ring[u2 & 31] = cmulc(xp[u2], xp[u2 + 2 * cd]);
-                Rc = cadd(Rc, csub(cadd(ring[u1 & 31], ring[u2 & 31]), old));
-            }
-            float2 Rs;
-            Rs.x = Rc.x + __shfl_xor_sync(0xffffffffu, Rc.x, 1);
-            Rs.y = Rc.y + __shfl_xor_sync(0xffffffffu, Rc.y, 1);
-            if (cp == 0) Rt[(buf * kSB + jj) * kLag + cd] = cd ? Rs : make_float2(0.f, 0.f);
+        for (int r4 = 0; r4 < kSB * kLag / 128; ++r4) {
+            const int idx = r4 * 128 + gt;             // (row, lag)
+            const float4 *pp4 = reinterpret_cast<const float4 *>(Rp + idx * 4);
+            const float4 a = pp4[0], b = pp4[1];
+            const float2 sum = make_float2((a.x + a.z) + (b.x + b.z), (a.y + a.w) + (b.y + b.w));
+            Rt[buf * kSB * kLag + idx] = (idx & (kLag - 1)) ? make_float2(mu * sum.x, mu * sum.y) : make_float2(0.f, 0.f);
         }
     };
-    auto corr_next = [&](int jr0, int buf) {   // rows jr0 .. jr0 + kSB - 1, jr0 = 16 s'
+    // one step of the even (E = 0) or odd (E = 1) share: row j from row j - 1
+    auto corr_step = [&](auto E, int j, int jj, const float2 *xp) {
+        constexpr int e = decltype(E)::value;
+        const int uin = e ? 2 * j + 2 * D - 1 : 2 * j + 2 * D;
+        const int s_out = (jj - 1) & 15;
+        const int s_in = e ? (jj + D - 1) & 15 : (jj + D) & 15;
+        const float2 old = ring[s_out];
+        ring[s_in] = cmulc(xp[uin], xp[uin + 2 * cd]);
+        Rc = cadd(Rc, csub(ring[s_in], old));
+    };
+    auto corr_first_e = [&](auto E, int buf) {   // rows 0 .. kSB - 1 of the chunk
+        constexpr int e = decltype(E)::value;
         const float2 *xp = xsp(cp);
 #pragma unroll
-        for (int jj = 0; jj < kSB; ++jj) {
-            const int j = jr0 + jj, u1 = 2 * j + 2 * D - 1, u2 = 2 * j + 2 * D;
-            // 2 jr0 is a multiple of 32: the slots depend on jj only
-            const int s_old0 = (2 * jj - 2) & 31, s_old1 = (2 * jj - 1) & 31;
-            const int s1 = (2 * jj + 2 * D - 1) & 31, s2 = (2 * jj + 2 * D) & 31;
-            const float2 old = cadd(ring[s_old0], ring[s_old1]);
-            ring[s1] = cmulc(xp[u1], xp[u1 + 2 * cd]);
-            ring[s2] = cmulc(xp[u2], xp[u2 + 2 * cd]);
-            Rc = cadd(Rc, csub(cadd(ring[s1], ring[s2]), old));
-            float2 Rs;
-            Rs.x = Rc.x + __shfl_xor_sync(0xffffffffu, Rc.x, 1);
-            Rs.y = Rc.y + __shfl_xor_sync(0xffffffffu, Rc.y, 1);
-            if (cp == 0) Rt[(buf * kSB + jj) * kLag + cd] = cd ? Rs : make_float2(0.f, 0.f);
+        for (int i = 0; i < 16; ++i) ring[i] = make_float2(0.f, 0.f);
+        Rc = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int u = e; u <= 2 * D; u += 2) {
+            ring[(u >> 1) & 15] = cmulc(xp[u], xp[u + 2 * cd]);
+            Rc = cadd(Rc, ring[(u >> 1) & 15]);
         }
+#pragma unroll
+        for (int jj = 0; jj < kSB; ++jj) {
+            if (jj > 0) corr_step(E, jj, jj, xp);
+            Rp[(jj * kLag + cd) * 4 + cp * 2 + e] = Rc;
+        }
+    };
+    auto corr_first = [&](int buf) {
+        if (ce) corr_first_e(std::integral_constant<int, 1>(), buf);
+        else corr_first_e(std::integral_constant<int, 0>(), buf);
+        corr_sum(buf);
+    };
+    auto corr_next_e = [&](auto E, int jr0) {     // rows jr0 .. jr0 + kSB - 1, jr0 = 16 s'
+        constexpr int e = decltype(E)::value;
+        const float2 *xp = xsp(cp);
+        // jr0 is a multiple of 16: the ring slots depend on jj only
+#pragma unroll
+        for (int jj = 0; jj < kSB; ++jj) {
+            corr_step(E, jr0 + jj, jj, xp);
+            Rp[(jj * kLag + cd) * 4 + cp * 2 + e] = Rc;
+        }
+    };
+    auto corr_next = [&](int jr0, int buf) {
+        if (ce) corr_next_e(std::integral_constant<int, 1>(), jr0);
+        else corr_next_e(std::integral_constant<int, 0>(), jr0);
+        corr_sum(buf);
     };
 
     for (int pass = 0; pass < passes; ++pass) {
@@ -284,7 +313,7 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
                     }
                 }
             if (tap_grp) bases(0, 0);
-            if (cor_grp && hw < 6) corr_first(0);
+            if (cor_grp) corr_first(0);
             __syncthreads();
 
             // decision warp state: partial y of update 16 s + lane, both outputs
@@ -292,11 +321,10 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
             const int o = lane & 15;
             const bool valid = o < f.n_orb;
             const float4 r = tb.orb[valid ? o : 0];
-            const float eo = tb.orbe[valid ? o : 0];
-            unsigned lab4 = 0;
+            const float eo = valid ? tb.orbe[o] : __int_as_float(0x7f800000);   // +inf: never the minimum
+            int lab[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) lab4 |= (unsigned)(tb.orblab[valid ? o : 0][k] & 255) << (8 * k);
-            auto label_of = [&](int k) { return (int)((lab4 >> (8 * k)) & 255u); };
+            for (int k = 0; k < 4; ++k) lab[k] = tb.orblab[valid ? o : 0][k] & 255;
             for (int s = 0; s < nsb; ++s) {
                 const int buf = s & 1;
                 if (warp == 0) {
@@ -320,10 +348,13 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
                     y0.y = __shfl_sync(0xffffffffu, v0.y, 0);
                     y1.x = __shfl_sync(0xffffffffu, v1.x, 0);
                     y1.y = __shfl_sync(0xffffffffu, v1.y, 0);
+                    const float2 *Rl = Rr + lane;
+#pragma unroll 2
                     for (int i = 0; i < ms; ++i) {
                         const int k = kSB * s + i;
-                        const float2 rc = Rr[i * kLag + (lane > i ? lane - i : 0)];   // r(k, 16 s + lane)
-                        const float2 r1 = Rr[i * kLag + 1];                             // r(k, k + 1)
+                        // mu r(k, 16 s + lane) (lanes <= i read values they never use)
+                        const float2 rc = Rl[i * (kLag - 1)];
+                        const float2 r1 = Rr[i * kLag + 1];                             // mu r(k, k + 1)
                         // the next update's partial before this update's term:
                         // fetched while the decision runs
                         float2 w0, w1;
@@ -341,44 +372,47 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
                             e1 = csub(tg1[k], y1);
                         } else {
                             const float2 rot = rots[k];                               // exp(j phi)
+                            // this lane's representative turned by phi: the
+                            // correlation with y equals that of y exp(-j phi)
+                            // with the representative, and |y| = |y exp(-j phi)|
+                            const float2 q0 = cmul(make_float2(r.x, r.y), rot);
                             float2 d0, d1;
-                            const float2 z0 = cmulc(rot, y0), z1 = cmulc(rot, y1);   // y exp(-j phi)
                             if (DIMS == 4) {
-                                const float P = (z0.x * r.x + z0.y * r.y) + (z1.x * r.z + z1.y * r.w);
-                                const float Q = (z0.y * r.x - z0.x * r.y) + (z1.y * r.z - z1.x * r.w);
+                                const float2 q1 = cmul(make_float2(r.z, r.w), rot);
+                                const float P = (y0.x * q0.x + y0.y * q0.y) + (y1.x * q1.x + y1.y * q1.y);
+                                const float Q = (y0.y * q0.x - y0.x * q0.y) + (y1.y * q1.x - y1.x * q1.y);
                                 float v;
-                                int kr;
-                                best_rot(P, Q, f.S, v, kr);
-                                const float dist = (cnorm(z0) + cnorm(z1)) + (eo - 2.f * v);
-                                const float4 pt = tb.pts[argmin_label(dist, valid, label_of(kr))];
+                                int lb;
+                                best_rot_label(P, Q, f.S, lab, v, lb);
+                                const float dist = (cnorm(y0) + cnorm(y1)) + (eo - 2.f * v);
+                                const float4 pt = tb.pts[argmin_label(dist, lb)];
                                 d0 = make_float2(pt.x, pt.y);
                                 d1 = make_float2(pt.z, pt.w);
                             } else {
                                 float va, vb;
-                                int ka, kc;
-                                best_rot(z0.x * r.x + z0.y * r.y, z0.y * r.x - z0.x * r.y, f.S, va, ka);
-                                best_rot(z1.x * r.x + z1.y * r.y, z1.y * r.x - z1.x * r.y, f.S, vb, kc);
-                                const float4 p0 = tb.pts[argmin_label(cnorm(z0) + eo - 2.f * va, valid, label_of(ka))];
-                                const float4 p1 = tb.pts[argmin_label(cnorm(z1) + eo - 2.f * vb, valid, label_of(kc))];
+                                int la, lc;
+                                best_rot_label(y0.x * q0.x + y0.y * q0.y, y0.y * q0.x - y0.x * q0.y, f.S, lab, va, la);
+                                best_rot_label(y1.x * q0.x + y1.y * q0.y, y1.y * q0.x - y1.x * q0.y, f.S, lab, vb, lc);
+                                const float4 p0 = tb.pts[argmin_label(cnorm(y0) + (eo - 2.f * va), la)];
+                                const float4 p1 = tb.pts[argmin_label(cnorm(y1) + (eo - 2.f * vb), lc)];
                                 d0 = make_float2(p0.x, p0.y);
                                 d1 = make_float2(p1.x, p1.y);
                             }
                             e0 = csub(cmul(d0, rot), y0);
                             e1 = csub(cmul(d1, rot), y1);
                         }
-                        const float2 me0 = make_float2(mu * e0.x, mu * e0.y), me1 = make_float2(mu * e1.x, mu * e1.y);
-                        v0 = cadd(v0, cmul(me0, rc));
-                        v1 = cadd(v1, cmul(me1, rc));
+                        v0 = cadd(v0, cmul(e0, rc));
+                        v1 = cadd(v1, cmul(e1, rc));
                         // lane i + 1's new partial, formed the same way in every lane
-                        y0 = cadd(w0, cmul(me0, r1));
-                        y1 = cadd(w1, cmul(me1, r1));
-                        es[buf * kSB + i] = make_float4(me0.x, me0.y, me1.x, me1.y);   // every lane: the same value
+                        y0 = cadd(w0, cmul(e0, r1));
+                        y1 = cadd(w1, cmul(e1, r1));
+                        es[buf * kSB + i] = make_float4(e0.x, e0.y, e1.x, e1.y);   // every lane: the same value
                     }
                 } else if (tap_grp) {
                     if (s >= 1) tap_update(kSB * (s - 1), kSB, es + (buf ^ 1) * kSB);
                     bar_sync(kBarTap, 128);
                     if (s + 1 < nsb) bases(kSB * (s + 1), buf ^ 1);
-                } else if (cor_grp && hw < 6) {
+                } else if (cor_grp) {
                     if (s + 1 < nsb) corr_next(kSB * (s + 1), buf ^ 1);
                 }
                 __syncthreads();
