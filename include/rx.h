@@ -110,7 +110,8 @@ void rx_destroy(rx_handle *h);                      /* NULL-safe */
  *   (<= 20000), "train_passes" [3],
  *   "sigma2" [0 = estimate per block], "skip_head" [4096],
  *   "skip_tail" [512], "streams" [1], "rolloff" [0.1],
- *   "wavelength_nm" [1550], "profile" [0] (1: time every launch),
+ *   "wavelength_nm" [1550], "profile" [0] (1: time every launch group and
+ *   every block, 2: time the BPS launches only),
  *   "precision" [0]: storage of the chain's CDC and FIR outputs, 0 float32,
  *   1 half (FP16), 2 bfloat16; arithmetic, LMS taps and the phase unwrap
  *   stay float32 (the precision variant; rx_get_state / rx_set_state need 0).
@@ -145,9 +146,14 @@ int rx_reset(rx_handle *h);
 int rx_process(rx_handle *h, const void *samples, size_t n_samples,
                float *llr_out, rx_stats *stats);
 
-/* rx_process with host buffers: copies samples (host, [S][2][n_samples]
- * c64) in and LLRs (host, [S][N][m]) out through pinned staging buffers,
- * overlapping the copies with the chain. */
+/* rx_process with host buffers: samples (host, [S][2][n_samples] c64) in,
+ * LLRs (host, [S][N][m]) out; results identical to rx_process.  The blocks
+ * run in groups of two: the input samples a group's CDC frames read are
+ * copied in on one copy stream and its LLR rows copied out on another, so
+ * the copies overlap the chain of the neighbouring groups (asynchronously
+ * when the host buffers are pinned; pageable buffers also work).  Device
+ * copies of the input and output are kept by the handle (allocated on first
+ * use).  Returns when the LLRs are in llr_out. */
 int rx_process_host(rx_handle *h, const void *samples, size_t n_samples,
                     float *llr_out, rx_stats *stats);
 
@@ -156,6 +162,7 @@ int rx_get_stats(rx_handle *h, rx_stats *stats);
 
 /* Device time of the last rx_process per stage, from CUDA events recorded
  * around every launch on its own stream when the parameter "profile" is 1
+ * (2: the "bps" stage only)
  * (launch counts are kept always).  stage: "cdc", "fir", "bps", "unwrap",
  * "demap", "lms", "startup" or "all".  ms_total may be NULL; synchronises
  * the device when it is not. */

@@ -52,7 +52,9 @@ __device__ __forceinline__ float half_turn_d(float P, float Q, int S, float e) {
     return fmaf(2.f, P, e);
 }
 
-template <int DIMS, int NORB>
+// SS: the table's rotation order S as a constant, so that the per-orbit
+// value and the half-turn identity compile to their one case
+template <int DIMS, int NORB, int SS>
 __global__ void __launch_bounds__(256, 2)
 bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_valid, int W,
            uint8_t *__restrict__ bout, long bout_stride, int *__restrict__ dsum,
@@ -73,7 +75,6 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long yoff = (long)s * 2 * y_stride;      // y of stream s: [2][y_stride], storage kind sk
     const int hw = W >> 1;
-    const int S = f.S;
 
     for (int r = 0; r < rounds; ++r) {
         // ---- min distances of chunk jc for every test phase, scanned ----
@@ -131,15 +132,15 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
                     float P, Q, R, U;
                     upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P, Q);
                     upk2(fma2(S1, CI[0][o + 1], mul2(C1, CR[0][o + 1])), R, U);
-                    a0 = fmin3(a0, fmaf(-2.f, orbit_v(P, Q, S), f.orbe[o]),
-                               fmaf(-2.f, orbit_v(R, U, S), f.orbe[o + 1]));
-                    a1 = fmin3(a1, half_turn_d(P, Q, S, f.orbe[o]), half_turn_d(R, U, S, f.orbe[o + 1]));
+                    a0 = fmin3(a0, fmaf(-2.f, orbit_v(P, Q, SS), f.orbe[o]),
+                               fmaf(-2.f, orbit_v(R, U, SS), f.orbe[o + 1]));
+                    a1 = fmin3(a1, half_turn_d(P, Q, SS, f.orbe[o]), half_turn_d(R, U, SS, f.orbe[o + 1]));
                 }
                 if (NORB & 1) {
                     float P, Q;
                     upk2(fma2(S1, CI[0][NORB - 1], mul2(C1, CR[0][NORB - 1])), P, Q);
-                    a0 = fminf(a0, fmaf(-2.f, orbit_v(P, Q, S), f.orbe[NORB - 1]));
-                    a1 = fminf(a1, half_turn_d(P, Q, S, f.orbe[NORB - 1]));
+                    a0 = fminf(a0, fmaf(-2.f, orbit_v(P, Q, SS), f.orbe[NORB - 1]));
+                    a1 = fminf(a1, half_turn_d(P, Q, SS, f.orbe[NORB - 1]));
                 }
                 md = yn0 + a0;
                 md2 = yn0 + a1;
@@ -150,10 +151,10 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
                     float P0, Q0, P1, Q1;
                     upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P0, Q0);
                     upk2(fma2(S1, CI[1][o], mul2(C1, CR[1][o])), P1, Q1);
-                    x0 = fminf(x0, fmaf(-2.f, orbit_v(P0, Q0, S), f.orbe[o]));
-                    x1 = fminf(x1, fmaf(-2.f, orbit_v(P1, Q1, S), f.orbe[o]));
-                    w0 = fminf(w0, half_turn_d(P0, Q0, S, f.orbe[o]));
-                    w1 = fminf(w1, half_turn_d(P1, Q1, S, f.orbe[o]));
+                    x0 = fminf(x0, fmaf(-2.f, orbit_v(P0, Q0, SS), f.orbe[o]));
+                    x1 = fminf(x1, fmaf(-2.f, orbit_v(P1, Q1, SS), f.orbe[o]));
+                    w0 = fminf(w0, half_turn_d(P0, Q0, SS, f.orbe[o]));
+                    w1 = fminf(w1, half_turn_d(P1, Q1, SS, f.orbe[o]));
                 }
                 md = (yn0 + x0) + (yn1 + x1);
                 md2 = (yn0 + w0) + (yn1 + w1);
@@ -419,14 +420,14 @@ __global__ void dsum_kernel(const uint8_t *__restrict__ b, long b_stride, long a
     }
 }
 
-template <int DIMS, int NORB>
+template <int DIMS, int NORB, int SS>
 cudaError_t bps_launch_t(const void *y, long ys, long a, long e, long nv, int W, uint8_t *bout,
                          long bst, int *dsum, double *mdsum, int rounds, int n_streams,
                          const FmtDev &f, cudaStream_t st, int sk) {
     const int kR = range_of(rounds);
     const int n_cta = (int)((e - a + kR - 1) / kR);
     const size_t smem = sizeof(float) * (RX_NCHUNK * f.B * 33 + RX_NCHUNK * f.B) + kR + 16;
-    auto kern = bps_kernel<DIMS, NORB>;
+    auto kern = bps_kernel<DIMS, NORB, SS>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     dim3 grid((unsigned)n_cta, (unsigned)n_streams);
@@ -526,7 +527,16 @@ cudaError_t launch_bps(const void *y, long y_stride, long a, long e, long n_vali
     if (e <= a || n_streams <= 0) return cudaSuccess;
     if (rounds < 1 || rounds > kMaxRounds || (f.B & 1)) return cudaErrorInvalidValue;
     uint8_t *bo = bout + bout_off;
-#define RX_BPS(DD, NO) return bps_launch_t<DD, NO>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, mdsum, rounds, n_streams, f, st, sk)
+#define RX_BPS(DD, NO)                                                                                   \
+    switch (f.S) {                                                                                       \
+        case 4: return bps_launch_t<DD, NO, 4>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, mdsum, \
+                                               rounds, n_streams, f, st, sk);                             \
+        case 2: return bps_launch_t<DD, NO, 2>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, mdsum, \
+                                               rounds, n_streams, f, st, sk);                             \
+        case 1: return bps_launch_t<DD, NO, 1>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, mdsum, \
+                                               rounds, n_streams, f, st, sk);                             \
+        default: return cudaErrorInvalidValue;                                                           \
+    }
     if (f.dims == 4) {
         switch (f.n_orb) {
             case 16: RX_BPS(4, 16);

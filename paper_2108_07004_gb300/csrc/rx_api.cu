@@ -83,6 +83,9 @@ struct rx_handle {
     cudaStream_t side = nullptr;
     cudaEvent_t ev_unwrap = nullptr;
     cudaEvent_t ev_cdc0 = nullptr, ev_start = nullptr;   // start-up overlap with the CDC
+    // host-buffer entry: input and output copies on their own streams
+    cudaStream_t cp_in = nullptr, cp_out = nullptr;
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
     std::vector<cudaEvent_t> ev_lms;
     // device tables
     float2 *H = nullptr, *tw = nullptr;
@@ -117,8 +120,9 @@ struct rx_handle {
     long blocks_done = 0;
     unsigned long long u = 0;
     long cur_n = 0;
-    // profiling: CUDA events around every launch (parameter "profile")
-    bool profile = false;
+    // profiling (parameter "profile"): 1 = CUDA events around every launch
+    // group and every block, 2 = around the BPS launches only
+    int profile = 0;
     std::vector<cudaEvent_t> ev_pool;
     size_t ev_used = 0;
     struct Rec { int stage; cudaEvent_t a, b; };
@@ -424,8 +428,8 @@ cudaEvent_t prof_event(rx_handle *h) {
 }
 
 // record the start of a launch group of `stage` on stream `s`; returns a token
-cudaEvent_t prof_begin(rx_handle *h, cudaStream_t s) {
-    if (!h->profile) return nullptr;
+cudaEvent_t prof_begin(rx_handle *h, cudaStream_t s, int stage) {
+    if (!h->profile || (h->profile == 2 && stage != ST_BPS)) return nullptr;
     cudaEvent_t e = prof_event(h);
     if (e) cudaEventRecord(e, s);
     return e;
@@ -442,7 +446,7 @@ void prof_end(rx_handle *h, int stage, cudaEvent_t a, cudaStream_t s, int launch
 
 #define STAGE(stage, stream, nl, call)                  \
     do {                                               \
-        cudaEvent_t ev_a_ = prof_begin(h, stream);     \
+        cudaEvent_t ev_a_ = prof_begin(h, stream, stage); \
         CK(call);                                      \
         prof_end(h, stage, ev_a_, stream, nl);         \
     } while (0)
@@ -464,8 +468,33 @@ int train_stage(rx_handle *h, const void *x, long ns, float2 *taps, long ntr, ui
     return RX_OK;
 }
 
-// Run blocks [b0, b1) of S streams of N symbols whose samples are at `in`.
-int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *llr) {
+// CDC frames that blocks [b0, b1) (and, for b0 = 0, the start-up) read:
+// output k of the FIR and the LMS reads samples 2k - D .. 2k + D.  [f0, fs)
+// are the start-up's frames (b0 = 0), [fs, f1) the rest.
+struct CdcFrames {
+    long f0, fs, f1;
+};
+CdcFrames cdc_frames(const rx_handle *h, long N, long b0, long b1) {
+    const long Nb = h->block, ns = 2 * N;
+    const int D = (h->T - 1) / 2;
+    const long k_hi = std::min(b1 * Nb, N);
+    const long k_st = b0 == 0 ? std::min(N, std::max(h->n_pre, h->n_train)) : 0;
+    const long Sk = h->n_fft - h->n_ov;
+    const long s_lo = std::max(0L, 2 * b0 * Nb - D);
+    CdcFrames c;
+    c.f0 = s_lo / Sk;
+    c.f1 = (std::min(ns, 2 * std::max(k_hi, k_st) + D) + Sk - 1) / Sk;
+    c.fs = b0 == 0 ? std::min(c.f1, (std::min(ns, 2 * k_st + D) + Sk - 1) / Sk) : c.f0;
+    return c;
+}
+
+// Run blocks [b0, b1) of S streams of N symbols whose samples are at `in`;
+// `fresh` starts new per-call records (stage times, block latencies);
+// `join` makes the main stream wait for the side stream's last LMS, so that
+// the state is complete when the main stream's work is (calls that return
+// to the user; the host entry's groups pass false except for the last).
+int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *llr, bool fresh = true,
+               bool join = true) {
     const int S = h->streams, T = h->T, L = h->lag;
     const long Nb = h->block, ns = 2 * N;
     const long nblk = (N + Nb - 1) / Nb;
@@ -483,17 +512,14 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     // For b0 = 0 the start-up's frames go first; the start-up then runs on
     // the side stream while the main stream filters the rest.
     {
-        const long k_hi = std::min(b1 * Nb, N);
-        const long k_st = b0 == 0 ? std::min(N, std::max(h->n_pre, h->n_train)) : 0;
-        const long Sk = h->n_fft - h->n_ov;
-        const long s_lo = std::max(0L, 2 * b0 * Nb - D);
-        const long f0 = s_lo / Sk;
-        const long f1 = (std::min(ns, 2 * std::max(k_hi, k_st) + D) + Sk - 1) / Sk;
-        const long fs = b0 == 0 ? std::min(f1, (std::min(ns, 2 * k_st + D) + Sk - 1) / Sk) : f0;
-        h->ev_used = 0;
-        h->recs.clear();
-        h->blk.clear();
-        for (auto &c : h->nlaunch) c = 0;
+        const CdcFrames cf = cdc_frames(h, N, b0, b1);
+        const long f0 = cf.f0, fs = cf.fs, f1 = cf.f1;
+        if (fresh) {
+            h->ev_used = 0;
+            h->recs.clear();
+            h->blk.clear();
+            for (auto &c : h->nlaunch) c = 0;
+        }
         if (fs > f0) {
             STAGE(ST_CDC, st, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st, f0, fs,
                                             h->prec));
@@ -569,7 +595,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         // W_n = U_{n-lag}; for n < lag the slot read has not been written since start-up (W_0)
         const float2 *wn = slot(h, n - L);
         cudaEvent_t blk0 = nullptr;
-        if (h->profile && (blk0 = prof_event(h))) CK(cudaEventRecord(blk0, st));
+        if (h->profile == 1 && (blk0 = prof_event(h))) CK(cudaEventRecord(blk0, st));
         STAGE(ST_FIR, st, 1, launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st, h->prec, avail));
         const long a = std::max(0L, k0 - h->W / 2);
         const long e = (n == nblk - 1) ? N : k1 - h->W / 2;
@@ -618,7 +644,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         h->u += span;
         h->blocks_done = n + 1;
     }
-    if (L >= 2 && b1 > b0) CK(cudaStreamWaitEvent(st, h->ev_lms[(b1 - 1) % (L + 1)], 0));
+    if (join && L >= 2 && b1 > b0) CK(cudaStreamWaitEvent(st, h->ev_lms[(b1 - 1) % (L + 1)], 0));
     return RX_OK;
 }
 
@@ -671,7 +697,7 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     else if (k == "streams") { rc = as_int(1, 4096, t); h->streams = (int)t; }
     else if (k == "rolloff") { if (!(v > 0 && v <= 1)) return fail(RX_EINVAL, "rolloff out of range"); h->rolloff = v; h->tables_dirty = true; }
     else if (k == "wavelength_nm") { if (!(v > 100 && v < 10000)) return fail(RX_EINVAL, "wavelength out of range"); h->wavelength = v * 1e-9; h->tables_dirty = true; }
-    else if (k == "profile") { h->profile = v != 0; return RX_OK; }
+    else if (k == "profile") { rc = as_int(0, 2, t); h->profile = (int)t; }
     else if (k == "precision") { rc = as_int(0, 2, t); h->prec = (int)t; }
     else return fail(RX_EINVAL, "unknown parameter '%s'", k.c_str());
     if (rc != RX_OK) return rc;
@@ -779,6 +805,10 @@ void rx_destroy(rx_handle *h) {
     if (!h) return;
     if (h->st) cudaStreamSynchronize(h->st);
     if (h->side) { cudaStreamSynchronize(h->side); cudaStreamDestroy(h->side); }
+    if (h->cp_in) { cudaStreamSynchronize(h->cp_in); cudaStreamDestroy(h->cp_in); }
+    if (h->cp_out) { cudaStreamSynchronize(h->cp_out); cudaStreamDestroy(h->cp_out); }
+    if (h->ev_in) cudaEventDestroy(h->ev_in);
+    if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->ev_unwrap) cudaEventDestroy(h->ev_unwrap);
     if (h->ev_cdc0) cudaEventDestroy(h->ev_cdc0);
     if (h->ev_start) cudaEventDestroy(h->ev_start);
@@ -826,7 +856,7 @@ int rx_get_param(const rx_handle *h, const char *key, double *value) {
     else if (k == "taps") *value = h->T;
     else if (k == "bps_phases") *value = h->B;
     else if (k == "cd_ps_per_nm") *value = h->cd;
-    else if (k == "profile") *value = h->profile ? 1 : 0;
+    else if (k == "profile") *value = h->profile;
     else if (k == "precision") *value = h->prec;
     else return fail(RX_EINVAL, "unknown parameter '%s'", key);
     return RX_OK;
@@ -986,17 +1016,59 @@ int rx_get_stats(rx_handle *h, rx_stats *stats) {
 int rx_process_host(rx_handle *h, const void *samples, size_t n_samples, float *llr_out, rx_stats *stats) {
     if (!h || !samples || !llr_out) return fail(RX_EINVAL, "NULL argument");
     if (n_samples < 2 || (n_samples & 1)) return fail(RX_EINVAL, "n_samples must be a positive multiple of 2");
-    const int S = h->streams;
-    const long N = (long)n_samples / 2;
+    const int S = h->streams, m = h->fmt.m;
+    const long N = (long)n_samples / 2, ns = (long)n_samples;
     const size_t in_b = sizeof(float2) * (size_t)S * 2 * n_samples;
-    const size_t out_b = sizeof(float) * (size_t)S * N * h->fmt.m;
+    const size_t out_b = sizeof(float) * (size_t)S * N * m;
     if (h->d_in_cap < in_b) { cudaFree(h->d_in); h->d_in = nullptr; CK(cudaMalloc(&h->d_in, in_b)); h->d_in_cap = in_b; }
     if (h->d_out_cap < out_b) { cudaFree(h->d_out); h->d_out = nullptr; CK(cudaMalloc(&h->d_out, out_b)); h->d_out_cap = out_b; }
-    CK(cudaMemcpyAsync(h->d_in, samples, in_b, cudaMemcpyHostToDevice, h->st));
-    const long nblk = (N + h->block - 1) / h->block;
-    int rc = run_blocks(h, h->d_in, N, 0, nblk, h->d_out);
-    if (rc != RX_OK) return rc;
-    CK(cudaMemcpyAsync(llr_out, h->d_out, out_b, cudaMemcpyDeviceToHost, h->st));
+    if (!h->cp_in) {
+        CK(cudaStreamCreateWithFlags(&h->cp_in, cudaStreamNonBlocking));
+        CK(cudaStreamCreateWithFlags(&h->cp_out, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+    }
+    // the previous call's output copies and this call's device buffers
+    CK(cudaEventRecord(h->ev_out, h->st));
+    CK(cudaStreamWaitEvent(h->cp_in, h->ev_out, 0));
+    // Groups of blocks: the input samples a group's CDC frames read go in on
+    // one copy stream, its LLR rows come out on another, so both overlap the
+    // chain of the neighbouring groups (with pinned host buffers the copies
+    // are asynchronous).  Samples [S][2][n_samples] and LLRs [S][N][m] are
+    // 2D regions: one row per stream and polarisation (stream).
+    const long Nb = h->block, nblk = (N + Nb - 1) / Nb;
+    const long Sk = h->n_fft - h->n_ov, half = h->n_ov / 2;
+    const long G = 2;                         // blocks per group
+    const size_t pin = sizeof(float2) * (size_t)ns, pout = sizeof(float) * (size_t)N * m;
+    long copied = 0;                          // samples [0, copied) of every row are on the device
+    long out_done = 0;                        // LLR rows [0, out_done) copied out
+    const float2 *src = static_cast<const float2 *>(samples);
+    for (long g0 = 0; g0 < nblk; g0 += G) {
+        const long g1 = std::min(nblk, g0 + G);
+        const CdcFrames cf = cdc_frames(h, N, g0, g1);
+        const long hi = std::min(ns, (cf.f1 - 1) * Sk - half + h->n_fft);
+        if (hi > copied) {
+            CK(cudaMemcpy2DAsync(h->d_in + copied, pin, src + copied, pin, sizeof(float2) * (size_t)(hi - copied),
+                                 (size_t)(2 * S), cudaMemcpyHostToDevice, h->cp_in));
+            copied = hi;
+        }
+        CK(cudaEventRecord(h->ev_in, h->cp_in));
+        CK(cudaStreamWaitEvent(h->st, h->ev_in, 0));
+        const int rc = run_blocks(h, h->d_in, N, g0, g1, h->d_out, g0 == 0, g1 == nblk);
+        if (rc != RX_OK) return rc;
+        // block n writes rows [k0 - W/2, k1 - W/2) (the last block up to N)
+        const long e = (g1 == nblk) ? N : std::min(N, g1 * Nb) - h->W / 2;
+        CK(cudaEventRecord(h->ev_out, h->st));
+        CK(cudaStreamWaitEvent(h->cp_out, h->ev_out, 0));
+        if (e > out_done) {
+            CK(cudaMemcpy2DAsync(llr_out + out_done * m, pout, h->d_out + out_done * m, pout,
+                                 sizeof(float) * (size_t)((e - out_done) * m), (size_t)S,
+                                 cudaMemcpyDeviceToHost, h->cp_out));
+            out_done = e;
+        }
+    }
+    CK(cudaEventRecord(h->ev_out, h->cp_out));
+    CK(cudaStreamWaitEvent(h->st, h->ev_out, 0));
     if (stats) return fill_stats(h, stats);
     CK(cudaStreamSynchronize(h->st));
     return RX_OK;
