@@ -52,6 +52,20 @@ __device__ __forceinline__ float half_turn_d(float P, float Q, int S, float e) {
     return fmaf(2.f, P, e);
 }
 
+// Orbit value v and the half-turn value u of (P, Q) with their distance
+// coefficients: d = e + cv * v at the test phase, d' = e + cu * u at the
+// phase shifted by pi/S (see half_turn_d).
+template <int SS>
+__device__ __forceinline__ void orbit_vu(float P, float Q, float &v, float &u) {
+    if (SS == 4) { v = fmaxf(fabsf(P), fabsf(Q)); u = fabsf(P) + fabsf(Q); }
+    else if (SS == 2) { v = fabsf(P); u = fabsf(Q); }
+    else { v = P; u = P; }
+}
+template <int SS> struct OrbitCoef {
+    static constexpr float cv = -2.f;
+    static constexpr float cu = SS == 4 ? -1.41421356237309515f : (SS == 2 ? -2.f : 2.f);
+};
+
 // SS: the table's rotation order S as a constant, so that the per-orbit
 // value and the half-turn identity compile to their one case
 template <int DIMS, int NORB, int SS>
@@ -65,7 +79,8 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
     constexpr int kRow = 33;                              // padded row of 32 prefixes
     float *Eb = smem;                                     // [10][B][kRow] exclusive prefixes
     float *Tb = smem + RX_NCHUNK * B * kRow;              // [10][B] chunk totals
-    uint8_t *bsm = reinterpret_cast<uint8_t *>(Tb + RX_NCHUNK * B);   // [kR]
+    float *T2 = Tb + RX_NCHUNK * B;                       // [8 warps][B] totals of two chunks
+    uint8_t *bsm = reinterpret_cast<uint8_t *>(T2 + 8 * B);   // [kR]
     __shared__ int red[8];
     __shared__ float redm[8];
     const int s = blockIdx.y, c = blockIdx.x;
@@ -126,15 +141,23 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
             const f32x2 C1 = cp1[0], S1 = cp1[1];
             float md, md2;
             if (DIMS == 4) {
+                // two orbits per step: (e - 2v) and (e + cu u) of both as one
+                // packed FMA each, then a three-input min
                 float a0 = 3.0e38f, a1 = 3.0e38f;
+                const f32x2 CV = pk2(OrbitCoef<SS>::cv, OrbitCoef<SS>::cv);
+                const f32x2 CU = pk2(OrbitCoef<SS>::cu, OrbitCoef<SS>::cu);
 #pragma unroll
                 for (int o = 0; o + 1 < NORB; o += 2) {
-                    float P, Q, R, U;
+                    float P, Q, R, U, v0, u0, v1, u1, d0, d1, h0, h1;
                     upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P, Q);
                     upk2(fma2(S1, CI[0][o + 1], mul2(C1, CR[0][o + 1])), R, U);
-                    a0 = fmin3(a0, fmaf(-2.f, orbit_v(P, Q, SS), f.orbe[o]),
-                               fmaf(-2.f, orbit_v(R, U, SS), f.orbe[o + 1]));
-                    a1 = fmin3(a1, half_turn_d(P, Q, SS, f.orbe[o]), half_turn_d(R, U, SS, f.orbe[o + 1]));
+                    orbit_vu<SS>(P, Q, v0, u0);
+                    orbit_vu<SS>(R, U, v1, u1);
+                    const f32x2 EO = pk2(f.orbe[o], f.orbe[o + 1]);
+                    upk2(fma2(CV, pk2(v0, v1), EO), d0, d1);
+                    upk2(fma2(CU, pk2(u0, u1), EO), h0, h1);
+                    a0 = fmin3(a0, d0, d1);
+                    a1 = fmin3(a1, h0, h1);
                 }
                 if (NORB & 1) {
                     float P, Q;
@@ -181,6 +204,14 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
         __syncthreads();
         // ---- window costs and argmin for output chunk oc ----
         const int oc = 8 * r - 2 + warp;
+        // totals of chunks oc - 1 and oc per test phase (the middle of a
+        // 64-symbol window), once per warp
+        float *t2 = T2 + warp * B;
+        if (oc >= 0 && oc < kChunks) {
+            const int sa = oc % RX_NCHUNK, sb = (oc + 1) % RX_NCHUNK;
+            for (int b = lane; b < B; b += 32) t2[b] = Tb[sa * B + b] + Tb[sb * B + b];
+        }
+        __syncwarp();
         if (oc >= 0 && oc < kChunks) {
             const long k = out0 + 32L * oc + lane;
             if (k < out1) {
@@ -192,16 +223,27 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
                 const int sm = (c0 + 2) % RX_NCHUNK;
                 float best = 3.0e38f;
                 int bb = 0;
-                for (int b = 0; b < B; ++b) {
-                    float cst;
-                    if (c0 == c1) {
-                        cst = Eb[(s0 * B + b) * kRow + l1] - Eb[(s0 * B + b) * kRow + l0];
-                    } else {
-                        cst = Tb[s0 * B + b] - Eb[(s0 * B + b) * kRow + l0];
-                        if (c1 - c0 == 2) cst += Tb[sm * B + b];
-                        cst += Eb[(s1 * B + b) * kRow + l1];
+                const float *e0 = Eb + s0 * B * kRow + l0, *e1 = Eb + s1 * B * kRow + l1;
+                if (c0 == oc - 1 && c1 == oc + 1) {
+                    // window over chunks oc - 1 .. oc + 1: the two-chunk total
+                    // minus the head of chunk oc - 1 plus the head of oc + 1
+#pragma unroll 4
+                    for (int b = 0; b < B; ++b) {
+                        const float cst = (t2[b] - e0[b * kRow]) + e1[b * kRow];
+                        if (cst < best) { best = cst; bb = b; }
                     }
-                    if (cst < best) { best = cst; bb = b; }
+                } else if (c0 == c1) {
+                    for (int b = 0; b < B; ++b) {
+                        const float cst = e1[b * kRow] - e0[b * kRow];
+                        if (cst < best) { best = cst; bb = b; }
+                    }
+                } else {
+                    for (int b = 0; b < B; ++b) {
+                        float cst = Tb[s0 * B + b] - e0[b * kRow];
+                        if (c1 - c0 == 2) cst += Tb[sm * B + b];
+                        cst += e1[b * kRow];
+                        if (cst < best) { best = cst; bb = b; }
+                    }
                 }
                 bsm[k - out0] = (uint8_t)bb;
                 bout[(long)s * bout_stride + (k - a)] = (uint8_t)bb;
@@ -426,7 +468,7 @@ cudaError_t bps_launch_t(const void *y, long ys, long a, long e, long nv, int W,
                          const FmtDev &f, cudaStream_t st, int sk) {
     const int kR = range_of(rounds);
     const int n_cta = (int)((e - a + kR - 1) / kR);
-    const size_t smem = sizeof(float) * (RX_NCHUNK * f.B * 33 + RX_NCHUNK * f.B) + kR + 16;
+    const size_t smem = sizeof(float) * (RX_NCHUNK * f.B * 33 + RX_NCHUNK * f.B + 8 * f.B) + kR + 16;
     auto kern = bps_kernel<DIMS, NORB, SS>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
