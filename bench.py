@@ -83,7 +83,10 @@ def make_inputs(rank: int, n_sym: int, n_streams: int):
 def rx_params(wl: dict = WL):
     keys = ["fft", "overlap", "bps_window", "block", "n_upd", "lag", "mu", "n_pre",
             "cma_passes", "n_cma", "n_train", "train_passes", "skip_head", "skip_tail"]
-    return {k: wl[k] for k in keys}
+    out = {k: wl[k] for k in keys}
+    if wl.get("lms_block", 1) > 1:
+        out["lms_block"] = wl["lms_block"]
+    return out
 
 
 class Clocks:
@@ -141,7 +144,7 @@ def oracle_params(wl: dict, **over):
               bps_phases=wl["bps_phases"], bps_window=wl["bps_window"], block=wl["block"],
               n_upd=wl["n_upd"], lag=wl["lag"], mu=wl["mu"], n_pre=wl["n_pre"], cma_passes=wl["cma_passes"],
               n_cma=wl["n_cma"], n_train=wl["n_train"], train_passes=wl["train_passes"],
-              skip_head=wl["skip_head"], skip_tail=wl["skip_tail"])
+              skip_head=wl["skip_head"], skip_tail=wl["skip_tail"], lms_block=wl.get("lms_block", 1))
     kw.update(over)
     return chain.RxParams(**kw)
 
@@ -364,6 +367,90 @@ def chain_bytes_per_symbol(wl: dict, store: int) -> float:
     return (32 * ovl + 4 * store) + (4 * store + 2 * store) + (2 * store + 1) + (2 * store + 1 + 2 + 4 * m)
 
 
+def timed_steps(r, samples, llr, steps: int, warmup: int):
+    """Device ms per step (CUDA events, library events around the BPS
+    launches only), then the stage breakdown of one profiled step and the
+    statistics."""
+    import torch
+    r.set("profile", 2)
+    for _ in range(warmup):
+        r.process(samples, llr, stats=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(steps):
+        r.process(samples, llr, stats=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    st_ = r.stats()
+    r.set("profile", 1)
+    r.process(samples, llr, stats=False)
+    stg = {k: r.profile(k)[0] for k in ("cdc", "fir", "bps", "demap", "lms", "startup")}
+    r.set("profile", 0)
+    return ms, stg, st_
+
+
+# ---- block LMS (next row F2): groups of P updates share the taps at the group start ----
+BLOCK_LMS = dict(P=(1, 4, 16, 64), lag=(1, 2, 3), cpu_P=16)
+
+
+def run_block_lms(args):
+    """The bench workload with the block-wise tap updates in groups of P
+    (P = 1: the exact recursion) for tap lags 1..3: Gbit/s, the LMS stage's
+    device time per block and the bit errors over the 9 streams."""
+    import torch
+    from paper_2108_07004_gb300 import rx as rx_mod
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n_sym, S = args.n_sym, args.streams
+    rx_h, bits_h = make_inputs(0, n_sym, S)
+    samples = torch.from_numpy(rx_h).cuda()
+    bits = torch.from_numpy(bits_h).cuda()
+    del rx_h
+    m = 6
+    nblk = (n_sym + WL["block"] - 1) // WL["block"]
+    sweep = []
+    for lag in BLOCK_LMS["lag"]:
+        for P in BLOCK_LMS["P"]:
+            wl = dict(WL, lag=lag, lms_block=P)
+            r = rx_mod.Receiver(WL["fmt"], cd_ps_per_nm=WL["cd_ps_per_nm"], taps=WL["taps"],
+                                bps_phases=WL["bps_phases"], streams=S, **rx_params(wl))
+            r.set_reference(bits)
+            llr = torch.empty((S, n_sym, m), dtype=torch.float32, device="cuda")
+            ms, stg, st_ = timed_steps(r, samples, llr, args.steps, args.warmup)
+            sweep.append({"lms_block": P, "lag": lag, "gbps": S * n_sym * m / (ms * 1e-3) / 1e9,
+                          "ms_per_step": ms, "lms_ms_per_block": stg["lms"] / nblk,
+                          "main_ms_per_block": (stg["fir"] + stg["bps"] + stg["demap"]) / nblk,
+                          "bit_errors": int(sum(x["bit_errors"] for x in st_)),
+                          "n_bits": int(sum(x["n_bits"] for x in st_)),
+                          "ber_12db": st_[4]["ber"]})
+            r.close()
+    ex = {(e["lag"], e["lms_block"]): e for e in sweep}
+    for e in sweep:
+        base = ex[(e["lag"], 1)]["bit_errors"]
+        e["ber_delta_rel_vs_exact"] = (e["bit_errors"] - base) / max(base, 1)
+    head = ex[(1, 16)]
+    line = {
+        "metric": METRIC, "value": head["gbps"], "unit": "Gbit/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": WL["workload"] + "_block_lms", "streams": S, "symbols_per_stream": n_sym,
+                   "format": WL["fmt"], "taps": WL["taps"], "bps_phases": WL["bps_phases"],
+                   "block": WL["block"], "lag": 1, "lms_block": 16},
+        "sweep": sweep,
+    }
+    if not args.no_cpu_baseline:
+        wl = dict(WL, lag=1, lms_block=BLOCK_LMS["cpu_P"])
+        v, dt, st_o, res_o = cpu_baseline(args.cpu_sym, wl, 12.0)
+        line["cpu_baseline"] = {"value": v, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one stream of {args.cpu_sym} 4D symbols (12 dB), block LMS P = "
+                                          f"{BLOCK_LMS['cpu_P']}, {dt:.1f} s"}
+        if not args.no_parity:
+            line["parity"] = parity_on(rx_mod, torch, st_o, res_o, wl)
+    print(json.dumps(line), flush=True)
+
+
 def run_precision(args):
     import torch
     from paper_2108_07004_gb300 import rx as rx_mod
@@ -388,19 +475,7 @@ def run_precision(args):
                             bps_phases=wl["bps_phases"], streams=S, **rx_params(wl), precision=prec)
         r.set_reference(bits_d)
         llr = torch.empty((S, n, m), dtype=torch.float32, device="cuda")
-        r.set("profile", 1)
-        for _ in range(args.warmup):
-            r.process(samples, llr, stats=False)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        for _ in range(args.steps):
-            r.process(samples, llr, stats=False)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1) / args.steps
-        stg = {k: r.profile(k)[0] for k in ("cdc", "fir", "bps", "demap", "lms", "startup")}
-        st_ = r.stats()
+        ms, stg, st_ = timed_steps(r, samples, llr, args.steps, args.warmup)
         bps = chain_bytes_per_symbol(wl, store)
         sym_s = S * n / (ms * 1e-3)
         forms[name] = {"gbps": sym_s * m / 1e9, "ms_per_step": ms, "stages_ms": stg,
@@ -637,7 +712,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision", "serving"],
+    ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision", "serving", "block_lms"],
                     help="learned: train the MLP demapper on chain output, compare with the exact one; "
                          "precision: DP-QPSK chain with CDC/FIR data in float32, half and bfloat16; "
                          "serving: 64 mixed streams with Poisson arrivals through the continuous-batching server")
@@ -647,6 +722,8 @@ def main():
         run_reference(args)
     elif args.variant == "learned":
         run_learned(args)
+    elif args.variant == "block_lms":
+        run_block_lms(args)
     elif args.variant == "precision":
         run_precision(args)
     elif args.variant == "serving":

@@ -110,6 +110,10 @@ void rx_destroy(rx_handle *h);                      /* NULL-safe */
  *   (<= 20000), "train_passes" [3],
  *   "sigma2" [0 = estimate per block], "skip_head" [4096],
  *   "skip_tail" [512], "streams" [1], "rolloff" [0.1],
+ *   "lms_block" [1]: the block-wise (blind) tap updates in groups of this
+ *   many (1..64) whose outputs and errors all use the taps at the group's
+ *   start (block LMS, a parallel variant beside the exact recursion; also
+ *   rx_lms modes 0-2; the start-up training stays sequential),
  *   "wavelength_nm" [1550], "profile" [0] (1: time every launch group and
  *   every block, 2: time the BPS launches only),
  *   "precision" [0]: storage of the chain's CDC and FIR outputs, 0 float32,

@@ -47,6 +47,7 @@ class RxParams:
     n_pre: int = 2048          # start-up CMA span (symbols)
     cma_passes: int = 1
     n_cma: int = 0             # block-wise updates run as CMA before DD
+    lms_block: int = 1         # block-wise updates in groups of this many (1: sequential)
     n_train: int = 1024        # known training symbols at the stream start
     train_passes: int = 3      # data-aided LMS passes over the training span
     sigma2: float | None = None  # fixed noise variance, else per-block estimate
@@ -230,6 +231,43 @@ def lms(x: np.ndarray, h: np.ndarray, ks, fmt: OracleFormat, p: RxParams,
         for q in range(2):
             h[q] += p.mu * np.conj(e[q]) * xw
         u += 1
+    return h
+
+
+def lms_block(x: np.ndarray, h: np.ndarray, ks, fmt: OracleFormat, p: RxParams, P: int,
+              u0: int = 0, phase: dict | None = None, info: LmsInfo | None = None) -> np.ndarray:
+    """Block LMS (Clark, Mitra and Parker, 1981) over symbols ``ks``: the
+    updates run in groups of P consecutive symbols; every output y_k and
+    error e_k of a group is computed with the taps at the start of the group
+    (CMA or DD per update count exactly as in ``lms``), then the group's P
+    gradient terms are applied together, h_q += mu * sum_k conj(e_q[k]) x[k].
+    P = 1 is the sequential recursion.  Reading: the paper names the
+    sequential tap update as the part of the chain that is hard to
+    parallelise (Sec. 2) and prints no alternative; this is the textbook
+    parallel form, a variant beside the exact chain."""
+    h = h.copy()
+    T = h.shape[2]
+    R2 = fmt.cma_radius2()
+    ks = list(ks)
+    u = u0
+    for g0 in range(0, len(ks), P):
+        terms = []
+        for k in ks[g0:g0 + P]:
+            xw = x_window(x, k, T)
+            y = np.array([np.sum(np.conj(h[q]) * xw) for q in range(2)])
+            if u < p.n_cma:
+                e = (R2 - np.abs(y) ** 2) * y
+            else:
+                ph = phase[k]
+                d, _, marg = decide((y * np.exp(-1j * ph))[:, None], fmt)
+                e = d[:, 0] * np.exp(1j * ph) - y
+                if info is not None:
+                    info.dd_margin.append((k, float(marg[0])))
+            terms.append((e, xw))
+            u += 1
+        for e, xw in terms:
+            for q in range(2):
+                h[q] += p.mu * np.conj(e[q]) * xw
     return h
 
 
@@ -564,7 +602,10 @@ def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
         out[a:e] = llr(z[:, a:e], s2, fmt)
         span = range(k0, min(k0 + p.n_upd, N))
         phase = {k: phi[k - a] for k in span}
-        hn = lms(x, ring[(n - 1) % (L + 1)], span, fmt, p, u0=u, phase=phase, info=info)
+        if p.lms_block > 1:
+            hn = lms_block(x, ring[(n - 1) % (L + 1)], span, fmt, p, p.lms_block, u0=u, phase=phase, info=info)
+        else:
+            hn = lms(x, ring[(n - 1) % (L + 1)], span, fmt, p, u0=u, phase=phase, info=info)
         u += len(span)
         ring[n % (L + 1)] = hn
         after.append(hn.copy())

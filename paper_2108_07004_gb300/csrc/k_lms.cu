@@ -427,6 +427,155 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
 }
 
 // ---------------------------------------------------------------------------
+// block LMS
+// ---------------------------------------------------------------------------
+
+// Nearest table point of (z0, z1) by one thread: every orbit's best rotation
+// (P + jQ = sum_p z_p conj(rep_p)), the minimum distance, lowest label on
+// exact ties (the rule of the warp-wide search in lms_kernel).
+template <int DIMS>
+__device__ __forceinline__ void decide_serial(float2 z0, float2 z1, const Tables &tb, const FmtDev &f,
+                                              float2 &d0, float2 &d1) {
+    if (DIMS == 4) {
+        const float zn = cnorm(z0) + cnorm(z1);
+        float best = __int_as_float(0x7f800000);
+        int bl = 0x7fffffff;
+        for (int o = 0; o < f.n_orb; ++o) {
+            const float4 r = tb.orb[o];
+            const float P = (z0.x * r.x + z0.y * r.y) + (z1.x * r.z + z1.y * r.w);
+            const float Q = (z0.y * r.x - z0.x * r.y) + (z1.y * r.z - z1.x * r.w);
+            const int lab[4] = {tb.orblab[o][0] & 255, tb.orblab[o][1] & 255, tb.orblab[o][2] & 255,
+                                tb.orblab[o][3] & 255};
+            float v;
+            int lb;
+            best_rot_label(P, Q, f.S, lab, v, lb);
+            const float dist = fmaxf(zn + (tb.orbe[o] - 2.f * v), 0.f);
+            if (dist < best || (dist == best && lb < bl)) { best = dist; bl = lb; }
+        }
+        const float4 pt = tb.pts[bl];
+        d0 = make_float2(pt.x, pt.y);
+        d1 = make_float2(pt.z, pt.w);
+    } else {
+#pragma unroll
+        for (int pol = 0; pol < 2; ++pol) {
+            const float2 z = pol ? z1 : z0;
+            float best = __int_as_float(0x7f800000);
+            int bl = 0x7fffffff;
+            for (int o = 0; o < f.n_orb; ++o) {
+                const float4 r = tb.orb[o];
+                const int lab[4] = {tb.orblab[o][0] & 255, tb.orblab[o][1] & 255, tb.orblab[o][2] & 255,
+                                    tb.orblab[o][3] & 255};
+                float v;
+                int lb;
+                best_rot_label(z.x * r.x + z.y * r.y, z.y * r.x - z.x * r.y, f.S, lab, v, lb);
+                const float dist = fmaxf(cnorm(z) + (tb.orbe[o] - 2.f * v), 0.f);
+                if (dist < best || (dist == best && lb < bl)) { best = dist; bl = lb; }
+            }
+            const float4 pt = tb.pts[bl];
+            (pol ? d1 : d0) = make_float2(pt.x, pt.y);
+        }
+    }
+}
+
+// Block LMS (Clark, Mitra and Parker): the updates run in groups of P; all
+// outputs and errors of a group use the taps at its start, then the group's
+// gradient terms are applied together, h_q += mu sum_k conj(e_q[k]) X_k.
+// Update u0 + i is CMA while below n_cma, DD after (per update, so groups may
+// straddle the switch).  One block of 256 threads per stream; per group:
+// outputs (thread (k, q, p, half of the taps), shuffles over the four), one
+// thread per error, one thread per tap for the update, a barrier after each.
+template <int T, int DIMS>
+__global__ void __launch_bounds__(256)
+lms_block_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_in,
+                 float2 *__restrict__ taps_out, long k0, int n_upd, const uint16_t *__restrict__ pcode,
+                 long pcode_stride, long u0, long n_cma, float mu, int P, int sk,
+                 const __grid_constant__ FmtDev f) {
+    constexpr int D = (T - 1) / 2;
+    constexpr int NSX = 2 * kCH + 2 * D + 2;
+    __shared__ Tables tb;
+    __shared__ float2 xs[2][NSX];         // local index of x_p[2 (kb + k) + D - t]: 2 k + 2 D - t
+    __shared__ float2 Hs[4 * T];
+    __shared__ float2 ys[64][2];
+    __shared__ float2 es[64][2];
+    __shared__ uint16_t pc[kCH];
+    const int s = blockIdx.x, tid = threadIdx.x;
+    load_tables(tb, f);
+    for (int i = tid; i < 4 * T; i += blockDim.x) Hs[i] = taps_in[(long)s * 4 * T + i];
+    const long xoff = (long)s * 2 * ns;
+    const int qt_step = 4 / f.S;
+    for (int c0 = 0; c0 < n_upd; c0 += kCH) {
+        const int n = min(kCH, n_upd - c0);
+        const long kb = k0 + c0;
+        const int nsx = 2 * n + 2 * D + 2;
+        __syncthreads();
+        for (int i = tid; i < 2 * nsx; i += blockDim.x) {
+            const int pp = i / nsx, jj = i - pp * nsx;
+            const long g = 2 * kb - D + jj;
+            xs[pp][jj] = (g >= 0 && g < ns) ? ld_sample(x, xoff + (long)pp * ns + g, sk) : make_float2(0.f, 0.f);
+        }
+        if (pcode)
+            for (int i = tid; i < n; i += blockDim.x) pc[i] = pcode[(long)s * pcode_stride + kb + i];
+        __syncthreads();
+        for (int g0 = 0; g0 < n; g0 += P) {
+            const int m = min(P, n - g0);
+            // outputs of the group with its starting taps
+            for (int base = 0; base < m * 8; base += blockDim.x) {
+                const int it = base + tid;
+                const bool act = it < m * 8;
+                const int kk = it >> 3, q = (it >> 2) & 1, pp = (it >> 1) & 1, half = it & 1;
+                float2 acc = make_float2(0.f, 0.f);
+                if (act) {
+                    const float2 *hq = Hs + (q * 2 + pp) * T;
+                    const float2 *xp = xs[pp] + 2 * (g0 + kk) + 2 * D;
+                    const int t1 = half ? T : (T < 16 ? T : 16);
+                    for (int t = half ? 16 : 0; t < t1; ++t) acc = cadd(acc, cmulc(hq[t], xp[-t]));
+                }
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
+                acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 2);
+                acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 2);
+                if (act && (it & 3) == 0) ys[kk][q] = acc;
+            }
+            __syncthreads();
+            if (tid < m) {
+                const int k = g0 + tid;
+                const float2 y0 = ys[tid][0], y1 = ys[tid][1];
+                float2 e0, e1;
+                if (u0 + c0 + k < n_cma) {
+                    const float g0c = f.R2 - cnorm(y0), g1c = f.R2 - cnorm(y1);
+                    e0 = make_float2(g0c * y0.x, g0c * y0.y);
+                    e1 = make_float2(g1c * y1.x, g1c * y1.y);
+                } else {
+                    // exp(j phi_k) = cs_b j^qt
+                    const unsigned code = pc[k];
+                    const int b = min((int)(code & 255), f.B - 1);
+                    const int qt = ((int)((code >> 8) & 3) * qt_step) & 3;
+                    float2 rot = tb.cs[b];
+                    if (qt & 2) rot = make_float2(-rot.x, -rot.y);
+                    if (qt & 1) rot = make_float2(-rot.y, rot.x);
+                    float2 d0, d1;
+                    decide_serial<DIMS>(cmulc(rot, y0), cmulc(rot, y1), tb, f, d0, d1);
+                    e0 = csub(cmul(d0, rot), y0);
+                    e1 = csub(cmul(d1, rot), y1);
+                }
+                es[tid][0] = e0;
+                es[tid][1] = e1;
+            }
+            __syncthreads();
+            if (tid < 4 * T) {
+                const int q = tid / (2 * T), rem = tid - q * 2 * T, pp = rem / T, t = rem - pp * T;
+                const float2 *xp = xs[pp] + 2 * g0 + 2 * D - t;
+                float2 acc = make_float2(0.f, 0.f);
+                for (int i = 0; i < m; ++i) acc = cadd(acc, cmulc(es[i][q], xp[2 * i]));
+                Hs[tid] = cadd(Hs[tid], make_float2(mu * acc.x, mu * acc.y));
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = tid; i < 4 * T; i += blockDim.x) taps_out[(long)s * 4 * T + i] = Hs[i];
+}
+
+// ---------------------------------------------------------------------------
 // training alignment
 // ---------------------------------------------------------------------------
 template <int T, int DIMS>
@@ -662,6 +811,34 @@ cudaError_t launch_lms(const void *x, long ns, const float2 *taps_in, float2 *ta
         case 31: return lms_dispatch_dims<31>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_lms_block(const void *x, long ns, const float2 *taps_in, float2 *taps_out, long k0,
+                             int n_upd, const uint16_t *pcode, long pcode_stride, int mode,
+                             unsigned long long u0, int n_cma, float mu, int P, int n_streams, int T,
+                             const FmtDev &f, cudaStream_t st, int sk) {
+    if (P < 1 || P > 64) return cudaErrorInvalidValue;
+    if (n_upd <= 0 || n_streams <= 0) {
+        if (taps_in != taps_out)
+            return cudaMemcpyAsync(taps_out, taps_in, sizeof(float2) * 4 * T * (size_t)n_streams,
+                                   cudaMemcpyDeviceToDevice, st);
+        return cudaSuccess;
+    }
+    // mode 0: CMA throughout, 1: DD throughout, 2: CMA below n_cma updates
+    const long ncma = mode == 0 ? (long)(u0 + n_upd) : (mode == 1 ? 0 : (long)n_cma);
+    if (mode != 0 && !pcode) return cudaErrorInvalidValue;
+#define RX_LB(TT, DD)                                                                                      \
+    lms_block_kernel<TT, DD><<<n_streams, 256, 0, st>>>(x, ns, taps_in, taps_out, k0, n_upd, pcode,          \
+                                                       pcode_stride, (long)u0, ncma, mu, P, sk, f)
+    const bool d4 = f.dims == 4;
+    switch (T) {
+        case 7: if (d4) RX_LB(7, 4); else RX_LB(7, 2); break;
+        case 15: if (d4) RX_LB(15, 4); else RX_LB(15, 2); break;
+        case 31: if (d4) RX_LB(31, 4); else RX_LB(31, 2); break;
+        default: return cudaErrorInvalidValue;
+    }
+#undef RX_LB
+    return cudaGetLastError();
 }
 
 cudaError_t launch_align(const void *x, long ns, float2 *taps, const uint8_t *ref_lab,

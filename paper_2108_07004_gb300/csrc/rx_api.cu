@@ -71,6 +71,7 @@ struct rx_handle {
     long n_pre = 2048;
     int cma_passes = 1;
     long n_cma = 0;
+    int lms_block = 1;       // block-wise updates in groups of this many (1: sequential)
     long n_train = 1024;
     int train_passes = 3;
     double sigma2_fixed = 0.0;
@@ -562,7 +563,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     }
     // grids of the main stream leave room for the side-stream LMS (one SM
     // per stream) when it runs beside them
-    const int avail = L >= 2 ? std::max(sm_count() / 2, sm_count() - S) : sm_count();
+    const int avail = (L >= 2 && h->lms_block == 1) ? std::max(sm_count() / 2, sm_count() - S) : sm_count();
     if (h->sigma2_fixed > 0) {
         h->h_sig.assign(S, h->sigma2_fixed);
         CK(cudaMemcpyAsync(h->sig_fixed, h->h_sig.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
@@ -637,9 +638,14 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
             CK(cudaStreamWaitEvent(h->side, h->ev_unwrap, 0));
             ls = h->side;
         }
-        STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
-              launch_lms(h->x, ns, slot(h, n - 1), slot(h, n), k0, (int)span, h->pcode, N, 2, 1,
-                         h->u, (int)h->n_cma, (float)h->mu, nullptr, 0, S, T, f, ls, h->prec));
+        if (h->lms_block > 1)
+            STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
+                  launch_lms_block(h->x, ns, slot(h, n - 1), slot(h, n), k0, (int)span, h->pcode, N, 2, h->u,
+                                   (int)h->n_cma, (float)h->mu, h->lms_block, S, T, f, ls, h->prec));
+        else
+            STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
+                  launch_lms(h->x, ns, slot(h, n - 1), slot(h, n), k0, (int)span, h->pcode, N, 2, 1,
+                             h->u, (int)h->n_cma, (float)h->mu, nullptr, 0, S, T, f, ls, h->prec));
         if (L >= 2) CK(cudaEventRecord(h->ev_lms[n % (L + 1)], h->side));
         h->u += span;
         h->blocks_done = n + 1;
@@ -689,6 +695,7 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     else if (k == "n_pre") { rc = as_int(0, 1L << 30, t); h->n_pre = t; }
     else if (k == "cma_passes") { rc = as_int(0, 16, t); h->cma_passes = (int)t; }
     else if (k == "n_cma") { rc = as_int(0, 1L << 40, t); h->n_cma = t; }
+    else if (k == "lms_block") { rc = as_int(1, 64, t); h->lms_block = (int)t; }
     else if (k == "n_train") { rc = as_int(0, 20000, t); h->n_train = t; }
     else if (k == "train_passes") { rc = as_int(0, 64, t); h->train_passes = (int)t; }
     else if (k == "sigma2") { if (!(v >= 0)) return fail(RX_EINVAL, "sigma2 < 0"); h->sigma2_fixed = v; }
@@ -845,6 +852,7 @@ int rx_get_param(const rx_handle *h, const char *key, double *value) {
     else if (k == "n_pre") *value = (double)h->n_pre;
     else if (k == "cma_passes") *value = h->cma_passes;
     else if (k == "n_cma") *value = (double)h->n_cma;
+    else if (k == "lms_block") *value = h->lms_block;
     else if (k == "n_train") *value = (double)h->n_train;
     else if (k == "train_passes") *value = h->train_passes;
     else if (k == "sigma2") *value = h->sigma2_fixed;
@@ -1269,6 +1277,14 @@ int rx_lms(rx_handle *h, const void *x, size_t n_samples, void *taps, size_t k0,
         return fail(RX_ESTATE, "data-aided mode needs a reference covering the span");
     const long N = (long)n_samples / 2;
     if ((long)(k0 + n_upd) > N) return fail(RX_EINVAL, "update span beyond the stream");
+    if (h->lms_block > 1 && mode != 3) {
+        // block LMS (passes repeat the span)
+        for (int pass = 0; pass < passes; ++pass)
+            CK(launch_lms_block((const float2 *)x, (long)n_samples, (const float2 *)taps, (float2 *)taps,
+                                (long)k0, (int)n_upd, pcode, N, mode, u0, (int)h->n_cma, (float)h->mu,
+                                h->lms_block, h->streams, h->T, h->fmt, h->st));
+        return RX_OK;
+    }
     CK(launch_lms((const float2 *)x, (long)n_samples, (const float2 *)taps, (float2 *)taps, (long)k0,
                   (int)n_upd, pcode, N, mode, passes, u0, (int)h->n_cma, (float)h->mu, h->ref,
                   h->ref_n, h->streams, h->T, h->fmt, h->st));

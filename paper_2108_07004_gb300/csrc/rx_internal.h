@@ -153,6 +153,13 @@ cudaError_t launch_lms(const void *x, long ns, const float2 *taps_in, float2 *ta
                        const uint8_t *ref_lab, long ref_stride,
                        int n_streams, int T, const FmtDev &f, cudaStream_t st, int sk = SK_F32);
 
+// Block LMS: groups of P (1..64) updates share the taps at the group start
+// (mode 0 CMA, 1 DD, 2 CMA below n_cma updates then DD).
+cudaError_t launch_lms_block(const void *x, long ns, const float2 *taps_in, float2 *taps_out, long k0,
+                             int n_upd, const uint16_t *pcode, long pcode_stride, int mode,
+                             unsigned long long u0, int n_cma, float mu, int P, int n_streams, int T,
+                             const FmtDev &f, cudaStream_t st, int sk = SK_F32);
+
 cudaError_t launch_train_phase(const void *x, long ns, const float2 *taps, const uint8_t *ref_lab,
                                long ref_stride, int n, int W, uint16_t *pcode, long pcode_stride,
                                int32_t *carry, int carry_stride, int n_streams, int T,
