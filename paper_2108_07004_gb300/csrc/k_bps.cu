@@ -16,8 +16,9 @@
 // lane), scans them with shuffles and stores the exclusive prefix of every
 // 32-symbol chunk and its total in a shared-memory ring of 10 chunks; a
 // window of W <= 64 symbols then spans at most three chunks and costs three
-// shared loads per test phase.  A block makes 960 outputs in 4 rounds of 8
-// chunks, computing one extra chunk on each side (6.7 % halo).
+// shared loads per test phase.  A block makes the outputs of a whole number
+// of chunks in rounds of 8 chunks (one per warp), computing one extra chunk
+// on each side; the launch splits each stream's range evenly.
 //
 // Unwrap (integer form of phi_hat_k = phi_k + q round((phi_hat_{k-1} -
 // phi_k)/q), q = 2 pi/S, round(x) = floor(x + 1/2)):
@@ -30,11 +31,14 @@
 
 namespace {
 
-constexpr int kMaxRounds = 16;
-constexpr int kMaxR = 32 * (8 * kMaxRounds - 2);   // largest output range per block (4032)
+constexpr int kMaxChunks = 126;
+constexpr int kMaxR = 32 * kMaxChunks;              // largest output range per block (4032)
+constexpr int kMinChunks = 6;                       // halo (two chunks) at most a third
 
-// Output symbols per block for `rounds` rounds of 8 chunks (one halo chunk on each side).
-__host__ __device__ __forceinline__ int range_of(int rounds) { return 32 * (8 * rounds - 2); }
+// Output symbols per block of `chunks` 32-symbol output chunks; the block
+// computes the minimum distances of one halo chunk on each side as well,
+// eight chunks per round (one per warp).
+__host__ __device__ __forceinline__ int range_of(int chunks) { return 32 * chunks; }
 
 __device__ __forceinline__ float orbit_v(float P, float Q, int S) {
     if (S == 4) return fmaxf(fabsf(P), fabsf(Q));
@@ -72,10 +76,11 @@ template <int DIMS, int NORB, int SS>
 __global__ void __launch_bounds__(256, 2)
 bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_valid, int W,
            uint8_t *__restrict__ bout, long bout_stride, int *__restrict__ dsum,
-           double *__restrict__ mdsum, int n_cta, int rounds, int sk, const __grid_constant__ FmtDev f) {
+           double *__restrict__ mdsum, int n_cta, int chunks, int sk, const __grid_constant__ FmtDev f) {
     extern __shared__ float smem[];
     const int B = f.B;
-    const int kChunks = 8 * rounds - 2, kR = range_of(rounds);
+    const int kChunks = chunks, kR = range_of(chunks);
+    const int rounds = (kChunks + 2 + 7) / 8;           // chunks -1 .. kChunks
     constexpr int kRow = 33;                              // padded row of 32 prefixes
     float *Eb = smem;                                     // [10][B][kRow] exclusive prefixes
     float *Tb = smem + RX_NCHUNK * B * kRow;              // [10][B] chunk totals
@@ -94,112 +99,114 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
     for (int r = 0; r < rounds; ++r) {
         // ---- min distances of chunk jc for every test phase, scanned ----
         const int jc = 8 * r - 1 + warp;
-        const long i = out0 + 32L * jc + lane;
-        const bool valid = (i >= 0) && (i < n_valid);
-        float2 ya = make_float2(0.f, 0.f), yb = make_float2(0.f, 0.f);
-        if (valid) { ya = ld_sample(y, yoff + i, sk); yb = ld_sample(y, yoff + y_stride + i, sk); }
-        // per orbit o (and polarisation for 2D tables): CR = (Re c, Im c) and
-        // CI = (Im c, -Re c), c = sum_p y_p conj(rep_p); then for a test phase,
-        // (P, Q) = cos(phi) CR + sin(phi) CI is one packed multiply and one packed FMA
-        f32x2 CR[2][NORB], CI[2][NORB];
-        float yn0, yn1;
-        if (DIMS == 4) {
-            yn0 = cnorm(ya) + cnorm(yb);
-            yn1 = 0.f;
-#pragma unroll
-            for (int o = 0; o < NORB; ++o) {
-                if (o < f.n_orb) {
-                    const float r0 = f.orb[o][0], r1 = f.orb[o][1], r2 = f.orb[o][2], r3 = f.orb[o][3];
-                    const float cr = ya.x * r0 + ya.y * r1 + yb.x * r2 + yb.y * r3;
-                    const float ci = ya.y * r0 - ya.x * r1 + yb.y * r2 - yb.x * r3;
-                    CR[0][o] = pk2(cr, ci);
-                    CI[0][o] = pk2(ci, -cr);
-                }
-            }
-        } else {
-            yn0 = cnorm(ya);
-            yn1 = cnorm(yb);
-#pragma unroll
-            for (int o = 0; o < NORB; ++o) {
-                if (o < f.n_orb) {
-                    const float r0 = f.orb[o][0], r1 = f.orb[o][1];
-                    const float cr0 = ya.x * r0 + ya.y * r1, ci0 = ya.y * r0 - ya.x * r1;
-                    const float cr1 = yb.x * r0 + yb.y * r1, ci1 = yb.y * r0 - yb.x * r1;
-                    CR[0][o] = pk2(cr0, ci0);
-                    CI[0][o] = pk2(ci0, -cr0);
-                    CR[1][o] = pk2(cr1, ci1);
-                    CI[1][o] = pk2(ci1, -cr1);
-                }
-            }
-        }
-        const int slot = (jc + 1) % RX_NCHUNK;
-        const int hb = B >> 1;
-        // test phases b and b + B/2 together: phi_{b+B/2} = phi_b + pi/S, a
-        // rotation of P + jQ that half_turn_d applies without another multiply
-        for (int b = 0; b < hb; ++b) {
-            const f32x2 *cp1 = reinterpret_cast<const f32x2 *>(f.csp[b]);
-            const f32x2 C1 = cp1[0], S1 = cp1[1];
-            float md, md2;
+        if (jc <= kChunks) {
+            const long i = out0 + 32L * jc + lane;
+            const bool valid = (i >= 0) && (i < n_valid);
+            float2 ya = make_float2(0.f, 0.f), yb = make_float2(0.f, 0.f);
+            if (valid) { ya = ld_sample(y, yoff + i, sk); yb = ld_sample(y, yoff + y_stride + i, sk); }
+            // per orbit o (and polarisation for 2D tables): CR = (Re c, Im c) and
+            // CI = (Im c, -Re c), c = sum_p y_p conj(rep_p); then for a test phase,
+            // (P, Q) = cos(phi) CR + sin(phi) CI is one packed multiply and one packed FMA
+            f32x2 CR[2][NORB], CI[2][NORB];
+            float yn0, yn1;
             if (DIMS == 4) {
-                // two orbits per step: (e - 2v) and (e + cu u) of both as one
-                // packed FMA each, then a three-input min
-                float a0 = 3.0e38f, a1 = 3.0e38f;
-                const f32x2 CV = pk2(OrbitCoef<SS>::cv, OrbitCoef<SS>::cv);
-                const f32x2 CU = pk2(OrbitCoef<SS>::cu, OrbitCoef<SS>::cu);
-#pragma unroll
-                for (int o = 0; o + 1 < NORB; o += 2) {
-                    float P, Q, R, U, v0, u0, v1, u1, d0, d1, h0, h1;
-                    upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P, Q);
-                    upk2(fma2(S1, CI[0][o + 1], mul2(C1, CR[0][o + 1])), R, U);
-                    orbit_vu<SS>(P, Q, v0, u0);
-                    orbit_vu<SS>(R, U, v1, u1);
-                    const f32x2 EO = pk2(f.orbe[o], f.orbe[o + 1]);
-                    upk2(fma2(CV, pk2(v0, v1), EO), d0, d1);
-                    upk2(fma2(CU, pk2(u0, u1), EO), h0, h1);
-                    a0 = fmin3(a0, d0, d1);
-                    a1 = fmin3(a1, h0, h1);
-                }
-                if (NORB & 1) {
-                    float P, Q;
-                    upk2(fma2(S1, CI[0][NORB - 1], mul2(C1, CR[0][NORB - 1])), P, Q);
-                    a0 = fminf(a0, fmaf(-2.f, orbit_v(P, Q, SS), f.orbe[NORB - 1]));
-                    a1 = fminf(a1, half_turn_d(P, Q, SS, f.orbe[NORB - 1]));
-                }
-                md = yn0 + a0;
-                md2 = yn0 + a1;
-            } else {
-                float x0 = 3.0e38f, x1 = 3.0e38f, w0 = 3.0e38f, w1 = 3.0e38f;
-#pragma unroll
+                yn0 = cnorm(ya) + cnorm(yb);
+                yn1 = 0.f;
+    #pragma unroll
                 for (int o = 0; o < NORB; ++o) {
-                    float P0, Q0, P1, Q1;
-                    upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P0, Q0);
-                    upk2(fma2(S1, CI[1][o], mul2(C1, CR[1][o])), P1, Q1);
-                    x0 = fminf(x0, fmaf(-2.f, orbit_v(P0, Q0, SS), f.orbe[o]));
-                    x1 = fminf(x1, fmaf(-2.f, orbit_v(P1, Q1, SS), f.orbe[o]));
-                    w0 = fminf(w0, half_turn_d(P0, Q0, SS, f.orbe[o]));
-                    w1 = fminf(w1, half_turn_d(P1, Q1, SS, f.orbe[o]));
+                    if (o < f.n_orb) {
+                        const float r0 = f.orb[o][0], r1 = f.orb[o][1], r2 = f.orb[o][2], r3 = f.orb[o][3];
+                        const float cr = ya.x * r0 + ya.y * r1 + yb.x * r2 + yb.y * r3;
+                        const float ci = ya.y * r0 - ya.x * r1 + yb.y * r2 - yb.x * r3;
+                        CR[0][o] = pk2(cr, ci);
+                        CI[0][o] = pk2(ci, -cr);
+                    }
                 }
-                md = (yn0 + x0) + (yn1 + x1);
-                md2 = (yn0 + w0) + (yn1 + w1);
+            } else {
+                yn0 = cnorm(ya);
+                yn1 = cnorm(yb);
+    #pragma unroll
+                for (int o = 0; o < NORB; ++o) {
+                    if (o < f.n_orb) {
+                        const float r0 = f.orb[o][0], r1 = f.orb[o][1];
+                        const float cr0 = ya.x * r0 + ya.y * r1, ci0 = ya.y * r0 - ya.x * r1;
+                        const float cr1 = yb.x * r0 + yb.y * r1, ci1 = yb.y * r0 - yb.x * r1;
+                        CR[0][o] = pk2(cr0, ci0);
+                        CI[0][o] = pk2(ci0, -cr0);
+                        CR[1][o] = pk2(cr1, ci1);
+                        CI[1][o] = pk2(ci1, -cr1);
+                    }
+                }
             }
-            if (!valid) { md = 0.f; md2 = 0.f; }
-            Eb[(slot * B + b) * kRow + lane] = md;
-            Eb[(slot * B + b + hb) * kRow + lane] = md2;
-        }
-        __syncwarp();
-        // exclusive prefix of every test phase's row over the chunk's 32
-        // symbols, in place: lane l takes phases l and l + 32 (rows padded to
-        // 33 floats, so the lanes' serial walks hit 32 different banks)
-        for (int b = lane; b < B; b += 32) {
-            float *row = Eb + (slot * B + b) * kRow;
-            float run = 0.f;
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float v = row[j];
-                row[j] = run;
-                run += v;
+            const int slot = (jc + 1) % RX_NCHUNK;
+            const int hb = B >> 1;
+            // test phases b and b + B/2 together: phi_{b+B/2} = phi_b + pi/S, a
+            // rotation of P + jQ that half_turn_d applies without another multiply
+            for (int b = 0; b < hb; ++b) {
+                const f32x2 *cp1 = reinterpret_cast<const f32x2 *>(f.csp[b]);
+                const f32x2 C1 = cp1[0], S1 = cp1[1];
+                float md, md2;
+                if (DIMS == 4) {
+                    // two orbits per step: (e - 2v) and (e + cu u) of both as one
+                    // packed FMA each, then a three-input min
+                    float a0 = 3.0e38f, a1 = 3.0e38f;
+                    const f32x2 CV = pk2(OrbitCoef<SS>::cv, OrbitCoef<SS>::cv);
+                    const f32x2 CU = pk2(OrbitCoef<SS>::cu, OrbitCoef<SS>::cu);
+    #pragma unroll
+                    for (int o = 0; o + 1 < NORB; o += 2) {
+                        float P, Q, R, U, v0, u0, v1, u1, d0, d1, h0, h1;
+                        upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P, Q);
+                        upk2(fma2(S1, CI[0][o + 1], mul2(C1, CR[0][o + 1])), R, U);
+                        orbit_vu<SS>(P, Q, v0, u0);
+                        orbit_vu<SS>(R, U, v1, u1);
+                        const f32x2 EO = pk2(f.orbe[o], f.orbe[o + 1]);
+                        upk2(fma2(CV, pk2(v0, v1), EO), d0, d1);
+                        upk2(fma2(CU, pk2(u0, u1), EO), h0, h1);
+                        a0 = fmin3(a0, d0, d1);
+                        a1 = fmin3(a1, h0, h1);
+                    }
+                    if (NORB & 1) {
+                        float P, Q;
+                        upk2(fma2(S1, CI[0][NORB - 1], mul2(C1, CR[0][NORB - 1])), P, Q);
+                        a0 = fminf(a0, fmaf(-2.f, orbit_v(P, Q, SS), f.orbe[NORB - 1]));
+                        a1 = fminf(a1, half_turn_d(P, Q, SS, f.orbe[NORB - 1]));
+                    }
+                    md = yn0 + a0;
+                    md2 = yn0 + a1;
+                } else {
+                    float x0 = 3.0e38f, x1 = 3.0e38f, w0 = 3.0e38f, w1 = 3.0e38f;
+    #pragma unroll
+                    for (int o = 0; o < NORB; ++o) {
+                        float P0, Q0, P1, Q1;
+                        upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P0, Q0);
+                        upk2(fma2(S1, CI[1][o], mul2(C1, CR[1][o])), P1, Q1);
+                        x0 = fminf(x0, fmaf(-2.f, orbit_v(P0, Q0, SS), f.orbe[o]));
+                        x1 = fminf(x1, fmaf(-2.f, orbit_v(P1, Q1, SS), f.orbe[o]));
+                        w0 = fminf(w0, half_turn_d(P0, Q0, SS, f.orbe[o]));
+                        w1 = fminf(w1, half_turn_d(P1, Q1, SS, f.orbe[o]));
+                    }
+                    md = (yn0 + x0) + (yn1 + x1);
+                    md2 = (yn0 + w0) + (yn1 + w1);
+                }
+                if (!valid) { md = 0.f; md2 = 0.f; }
+                Eb[(slot * B + b) * kRow + lane] = md;
+                Eb[(slot * B + b + hb) * kRow + lane] = md2;
             }
-            Tb[slot * B + b] = run;
+            __syncwarp();
+            // exclusive prefix of every test phase's row over the chunk's 32
+            // symbols, in place: lane l takes phases l and l + 32 (rows padded to
+            // 33 floats, so the lanes' serial walks hit 32 different banks)
+            for (int b = lane; b < B; b += 32) {
+                float *row = Eb + (slot * B + b) * kRow;
+                float run = 0.f;
+    #pragma unroll
+                for (int j = 0; j < 32; ++j) {
+                    const float v = row[j];
+                    row[j] = run;
+                    run += v;
+                }
+                Tb[slot * B + b] = run;
+            }
         }
         __syncthreads();
         // ---- window costs and argmin for output chunk oc ----
@@ -464,22 +471,22 @@ __global__ void dsum_kernel(const uint8_t *__restrict__ b, long b_stride, long a
 
 template <int DIMS, int NORB, int SS>
 cudaError_t bps_launch_t(const void *y, long ys, long a, long e, long nv, int W, uint8_t *bout,
-                         long bst, int *dsum, double *mdsum, int rounds, int n_streams,
+                         long bst, int *dsum, double *mdsum, int chunks, int n_streams,
                          const FmtDev &f, cudaStream_t st, int sk) {
-    const int kR = range_of(rounds);
+    const int kR = range_of(chunks);
     const int n_cta = (int)((e - a + kR - 1) / kR);
     const size_t smem = sizeof(float) * (RX_NCHUNK * f.B * 33 + RX_NCHUNK * f.B + 8 * f.B) + kR + 16;
     auto kern = bps_kernel<DIMS, NORB, SS>;
     cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (err != cudaSuccess) return err;
     dim3 grid((unsigned)n_cta, (unsigned)n_streams);
-    kern<<<grid, 256, smem, st>>>(y, ys, a, e, nv, W, bout, bst, dsum, mdsum, n_cta, rounds, sk, f);
+    kern<<<grid, 256, smem, st>>>(y, ys, a, e, nv, W, bout, bst, dsum, mdsum, n_cta, chunks, sk, f);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-int bps_cta_range(int rounds) { return range_of(rounds); }
+int bps_cta_range(int chunks) { return range_of(chunks); }
 
 int sm_count() {
     static int n = 0;
@@ -491,14 +498,18 @@ int sm_count() {
     return n;
 }
 
-// Rounds per block so that one launch of S streams x (e - a) outputs fills
-// about one wave of 2 blocks per SM (the ring of 10 chunks takes ~85 KB).
-int bps_rounds(long len, int n_streams, int sm_avail) {
+// Output chunks per block so that one launch of S streams x len outputs is
+// about one wave of 2 blocks per SM: the fewest blocks per stream that fit
+// in the wave, with the range split evenly among them (whole chunks), so the
+// blocks carry equal work (the ring of 10 chunks takes ~88 KB per block).
+int bps_chunks(long len, int n_streams, int sm_avail) {
     if (sm_avail <= 0) sm_avail = sm_count();
     const long per_stream = std::max(1L, (long)(2 * sm_avail) / std::max(1, n_streams));
-    for (int r = 1; r <= kMaxRounds; ++r)                            // fewest rounds that fit
-        if ((len + range_of(r) - 1) / range_of(r) <= per_stream) return r;
-    return kMaxRounds;
+    const long nch = std::max(1L, (len + 31) / 32);
+    long c = (nch + per_stream - 1) / per_stream;                  // chunks per block
+    c = std::max<long>(c, kMinChunks);
+    c = std::min<long>(c, kMaxChunks);
+    return (int)c;
 }
 
 // Start quadrant of the unwrap from the training phases (one block per
@@ -554,9 +565,9 @@ cudaError_t launch_anchor(const uint8_t *b, long b_stride, const uint16_t *tcode
 }
 
 cudaError_t launch_dsum_from_b(const uint8_t *b, long b_stride, long a, long e, int *dsum,
-                               int rounds, int n_streams, int B, cudaStream_t st) {
+                               int chunks, int n_streams, int B, cudaStream_t st) {
     if (e <= a || n_streams <= 0) return cudaSuccess;
-    const int kR = range_of(rounds);
+    const int kR = range_of(chunks);
     const int n_cta = (int)((e - a + kR - 1) / kR);
     dim3 grid((unsigned)n_cta, (unsigned)n_streams);
     dsum_kernel<<<grid, 256, 0, st>>>(b, b_stride, a, e, dsum, n_cta, B, kR);
@@ -565,18 +576,18 @@ cudaError_t launch_dsum_from_b(const uint8_t *b, long b_stride, long a, long e, 
 
 cudaError_t launch_bps(const void *y, long y_stride, long a, long e, long n_valid, int W,
                        uint8_t *bout, long bout_stride, long bout_off, int *dsum, double *mdsum,
-                       int rounds, int n_streams, const FmtDev &f, cudaStream_t st, int sk) {
+                       int chunks, int n_streams, const FmtDev &f, cudaStream_t st, int sk) {
     if (e <= a || n_streams <= 0) return cudaSuccess;
-    if (rounds < 1 || rounds > kMaxRounds || (f.B & 1)) return cudaErrorInvalidValue;
+    if (chunks < 1 || chunks > kMaxChunks || (f.B & 1)) return cudaErrorInvalidValue;
     uint8_t *bo = bout + bout_off;
 #define RX_BPS(DD, NO)                                                                                   \
     switch (f.S) {                                                                                       \
         case 4: return bps_launch_t<DD, NO, 4>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, mdsum, \
-                                               rounds, n_streams, f, st, sk);                             \
+                                               chunks, n_streams, f, st, sk);                             \
         case 2: return bps_launch_t<DD, NO, 2>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, mdsum, \
-                                               rounds, n_streams, f, st, sk);                             \
+                                               chunks, n_streams, f, st, sk);                             \
         case 1: return bps_launch_t<DD, NO, 1>(y, y_stride, a, e, n_valid, W, bo, bout_stride, dsum, mdsum, \
-                                               rounds, n_streams, f, st, sk);                             \
+                                               chunks, n_streams, f, st, sk);                             \
         default: return cudaErrorInvalidValue;                                                           \
     }
     if (f.dims == 4) {
@@ -602,11 +613,11 @@ cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long
                           float2 *z, long z_stride, long z_off,
                           uint16_t *pcode, long pcode_stride, long pcode_off,
                           double *partial, double *sigma2_out, int sigma2_stride,
-                          unsigned int *ticket, int ticket_stride, int rounds,
+                          unsigned int *ticket, int ticket_stride, int chunks,
                           const double *mdsum, int n_streams, const FmtDev &f, cudaStream_t st) {
     if (e <= a || n_streams <= 0) return cudaSuccess;
-    if (rounds < 1 || rounds > kMaxRounds) return cudaErrorInvalidValue;
-    const int kR = range_of(rounds);
+    if (chunks < 1 || chunks > kMaxChunks) return cudaErrorInvalidValue;
+    const int kR = range_of(chunks);
     const int n_cta = (int)((e - a + kR - 1) / kR);
     dim3 grid((unsigned)n_cta, (unsigned)n_streams);
     if (f.dims == 4) {

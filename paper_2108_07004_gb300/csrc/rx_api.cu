@@ -82,6 +82,11 @@ struct rx_handle {
     // CUDA
     cudaStream_t st = nullptr;
     cudaStream_t side = nullptr;
+    // the de-rotation/demap of block n runs on its own stream beside the
+    // FIR and BPS of block n + 1 (ev_bps: BPS of a block done; ev_dm: its
+    // demap done, by block parity)
+    cudaStream_t dst = nullptr;
+    cudaEvent_t ev_bps[2] = {nullptr, nullptr}, ev_dm[2] = {nullptr, nullptr}, ev_setup = nullptr;
     cudaEvent_t ev_unwrap = nullptr;
     cudaEvent_t ev_cdc0 = nullptr, ev_start = nullptr;   // start-up overlap with the CDC
     // host-buffer entry: input and output copies on their own streams
@@ -349,9 +354,9 @@ int ensure_buffers(rx_handle *h, long N) {
     CK(cudaMalloc(&h->ring, sizeof(float2) * (size_t)(h->lag + 1) * S * 4 * h->T));
     CK(cudaMalloc(&h->bidx, (size_t)S * N));
     CK(cudaMalloc(&h->pcode, sizeof(uint16_t) * (size_t)S * N));
-    CK(cudaMalloc(&h->dsum, sizeof(int) * (size_t)S * ncta));
+    CK(cudaMalloc(&h->dsum, sizeof(int) * 2 * (size_t)S * ncta));        // by block parity
     CK(cudaMalloc(&h->part_u, sizeof(double) * (size_t)S * ncta));
-    CK(cudaMalloc(&h->mdsum, sizeof(double) * (size_t)S * ncta));
+    CK(cudaMalloc(&h->mdsum, sizeof(double) * 2 * (size_t)S * ncta));
     CK(cudaMalloc(&h->part_d, sizeof(double) * 5 * (size_t)S * ncta_d));
     CK(cudaMalloc(&h->sig, sizeof(double) * S));
     CK(cudaMalloc(&h->sig_fixed, sizeof(double) * S));
@@ -376,6 +381,12 @@ int ensure_streams(rx_handle *h) {
         CK(cudaEventCreateWithFlags(&h->ev_unwrap, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&h->ev_cdc0, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming));
+        CK(cudaStreamCreateWithFlags(&h->dst, cudaStreamNonBlocking));
+        for (int i = 0; i < 2; ++i) {
+            CK(cudaEventCreateWithFlags(&h->ev_bps[i], cudaEventDisableTiming));
+            CK(cudaEventCreateWithFlags(&h->ev_dm[i], cudaEventDisableTiming));
+        }
+        CK(cudaEventCreateWithFlags(&h->ev_setup, cudaEventDisableTiming));
     }
     while ((int)h->ev_lms.size() < h->lag + 1) {
         cudaEvent_t e;
@@ -590,6 +601,10 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     cnt.c1 = std::max(cnt.c0, N - h->skip_tail);
     cnt.sd = h->sd;
     cnt.partial = h->part_d;
+    const cudaStream_t ds = h->dst;
+    // the demap stream starts after this call's set-up on the main stream
+    CK(cudaEventRecord(h->ev_setup, st));
+    CK(cudaStreamWaitEvent(ds, h->ev_setup, 0));
     for (long n = b0; n < b1; ++n) {
         const long k0 = n * Nb, k1 = std::min(k0 + Nb, N);
         if (L >= 2 && n >= L) CK(cudaStreamWaitEvent(st, h->ev_lms[(n - L) % (L + 1)], 0));
@@ -600,43 +615,54 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         STAGE(ST_FIR, st, 1, launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st, h->prec, avail));
         const long a = std::max(0L, k0 - h->W / 2);
         const long e = (n == nblk - 1) ? N : k1 - h->W / 2;
-        const int rounds = bps_rounds(e - a, S, avail);
-        STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, h->dsum, h->mdsum, rounds, S,
+        const int chunks = bps_chunks(e - a, S, avail);
+        const int par = (int)(n & 1);
+        int *dsum_n = h->dsum + (size_t)par * S * h->cap_dsum;
+        double *mdsum_n = h->mdsum + (size_t)par * S * h->cap_dsum;
+        // the partial sums of this parity were read by the demap of block n - 2
+        if (n - 2 >= b0) CK(cudaStreamWaitEvent(st, h->ev_dm[par], 0));
+        STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, dsum_n, mdsum_n, chunks, S,
                                         f, st, h->prec));
+        CK(cudaEventRecord(h->ev_bps[par], st));
+        CK(cudaStreamWaitEvent(ds, h->ev_bps[par], 0));
         const int cin = (int)(n & 1), cout = 1 - cin;
         if (n == 0 && h->trained) {
             // the training phases fix the start quadrant of the unwrap
-            STAGE(ST_UNWRAP, st, 1, launch_anchor(h->bidx, N, h->pcode, N, (int)std::min(h->n_train, e),
-                                                  carry_base, (int)sd_stride, S, h->B, f.S, st));
+            STAGE(ST_UNWRAP, ds, 1, launch_anchor(h->bidx, N, h->pcode, N, (int)std::min(h->n_train, e),
+                                                  carry_base, (int)sd_stride, S, h->B, f.S, ds));
         }
         // unwrap, de-rotation, LLRs and counting in one pass over y (no z);
         // with the learned demapper the pass writes the symbols instead
         if (derot_demap_ctas(e - a, S, avail) > h->cap_pd || (e - a + 255) / 256 > h->cap_pd)
             return fail(RX_EINVAL, "internal: demap partials");
-        STAGE(ST_DEMAP, st, 1,
-              launch_derot_demap(h->y, N, h->bidx + a, N, a, e, h->dsum, h->mdsum, bps_cta_range(rounds),
+        STAGE(ST_DEMAP, ds, 1,
+              launch_derot_demap(h->y, N, h->bidx + a, N, a, e, dsum_n, mdsum_n, bps_cta_range(chunks),
                                  carry_base + 2 * cin, (int)sd_stride, carry_base + 2 * cout, (int)sd_stride,
                                  h->pcode + a, N, h->sigma2_fixed > 0 ? h->sig_fixed : nullptr, h->sig, 1,
-                                 h->mlp ? nullptr : llr + (size_t)a * m, N * m, cnt, sym, S, f, st, h->prec,
+                                 h->mlp ? nullptr : llr + (size_t)a * m, N * m, cnt, sym, S, f, ds, h->prec,
                                  avail));
         if (h->mlp) {
             for (int s = 0; s < S; ++s)
-                STAGE(ST_DEMAP, st, 3,
+                STAGE(ST_DEMAP, ds, 3,
                       mlp_infer(h->mlp->d, sym.x4 + ((size_t)s * N + a) * 4, sym.s2 + (size_t)s * N + a, e - a,
-                                llr + ((size_t)s * N + a) * m, st));
-            STAGE(ST_DEMAP, st, 1,
-                  launch_count_llr(llr + (size_t)a * m, N * m, sym.x4, N, a, e, h->sig, 1, cnt, S, f, st));
+                                llr + ((size_t)s * N + a) * m, ds));
+            STAGE(ST_DEMAP, ds, 1,
+                  launch_count_llr(llr + (size_t)a * m, N * m, sym.x4, N, a, e, h->sig, 1, cnt, S, f, ds));
         }
+        CK(cudaEventRecord(h->ev_dm[par], ds));
         if (blk0) {
             cudaEvent_t blk1 = prof_event(h);
-            if (blk1) { CK(cudaEventRecord(blk1, st)); h->blk.push_back({blk0, blk1}); }
+            if (blk1) { CK(cudaEventRecord(blk1, ds)); h->blk.push_back({blk0, blk1}); }
         }
         const long span = std::max(0L, std::min((long)h->n_upd, N - k0));
+        // the LMS of block n reads the phase codes its demap wrote
+        CK(cudaEventRecord(h->ev_unwrap, ds));
         cudaStream_t ls = st;
         if (L >= 2) {
-            CK(cudaEventRecord(h->ev_unwrap, st));
             CK(cudaStreamWaitEvent(h->side, h->ev_unwrap, 0));
             ls = h->side;
+        } else {
+            CK(cudaStreamWaitEvent(st, h->ev_unwrap, 0));
         }
         if (h->lms_block > 1)
             STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
@@ -650,6 +676,8 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         h->u += span;
         h->blocks_done = n + 1;
     }
+    // the caller's stream sees the demaps (LLRs, counters, carries) done
+    if (b1 > b0) CK(cudaStreamWaitEvent(st, h->ev_dm[(int)((b1 - 1) & 1)], 0));
     if (join && L >= 2 && b1 > b0) CK(cudaStreamWaitEvent(st, h->ev_lms[(b1 - 1) % (L + 1)], 0));
     return RX_OK;
 }
@@ -819,6 +847,12 @@ void rx_destroy(rx_handle *h) {
     if (h->ev_unwrap) cudaEventDestroy(h->ev_unwrap);
     if (h->ev_cdc0) cudaEventDestroy(h->ev_cdc0);
     if (h->ev_start) cudaEventDestroy(h->ev_start);
+    if (h->dst) { cudaStreamSynchronize(h->dst); cudaStreamDestroy(h->dst); }
+    for (int i = 0; i < 2; ++i) {
+        if (h->ev_bps[i]) cudaEventDestroy(h->ev_bps[i]);
+        if (h->ev_dm[i]) cudaEventDestroy(h->ev_dm[i]);
+    }
+    if (h->ev_setup) cudaEventDestroy(h->ev_setup);
     for (auto e : h->ev_lms) cudaEventDestroy(e);
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     free_buffers(h);
@@ -1303,11 +1337,11 @@ int rx_bps(rx_handle *h, const void *y, size_t n_y, size_t a, size_t e, size_t n
     if (!h || !y || !b_out) return fail(RX_EINVAL, "NULL argument");
     if (e < a || e > n_y || n_valid > n_y) return fail(RX_EINVAL, "bad range");
     int *dsum = nullptr;
-    const int rounds = bps_rounds((long)(e - a), h->streams);
-    const long ncta = ((long)(e - a) + bps_cta_range(rounds) - 1) / bps_cta_range(rounds);
+    const int chunks = bps_chunks((long)(e - a), h->streams);
+    const long ncta = ((long)(e - a) + bps_cta_range(chunks) - 1) / bps_cta_range(chunks);
     CK(cudaMallocAsync(&dsum, sizeof(int) * (size_t)h->streams * (ncta + 1), h->st));
     cudaError_t err = launch_bps((const float2 *)y, (long)n_y, (long)a, (long)e, (long)n_valid, h->W,
-                                 b_out, (long)(e - a), 0, dsum, nullptr, rounds, h->streams, h->fmt, h->st);
+                                 b_out, (long)(e - a), 0, dsum, nullptr, chunks, h->streams, h->fmt, h->st);
     cudaFreeAsync(dsum, h->st);
     CK(err);
     return RX_OK;
@@ -1320,8 +1354,8 @@ int rx_unwrap(rx_handle *h, const void *y, size_t n_y, const uint8_t *b, size_t 
     if (e <= a || e > n_y) return fail(RX_EINVAL, "bad range");
     const int S = h->streams;
     const long K = (long)(e - a);
-    const int rounds = bps_rounds(K, S);
-    const long ncta = (K + bps_cta_range(rounds) - 1) / bps_cta_range(rounds);
+    const int chunks = bps_chunks(K, S);
+    const long ncta = (K + bps_cta_range(chunks) - 1) / bps_cta_range(chunks);
     // interior increments come from the phase search; recompute them here
     int *dsum = nullptr;
     double *part = nullptr;
@@ -1330,10 +1364,10 @@ int rx_unwrap(rx_handle *h, const void *y, size_t n_y, const uint8_t *b, size_t 
     CK(cudaMallocAsync(&part, sizeof(double) * (size_t)S * ncta, h->st));
     CK(cudaMallocAsync(&ticket, sizeof(unsigned) * (size_t)S, h->st));
     CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned) * (size_t)S, h->st));
-    CK(launch_dsum_from_b(b, K, a, e, dsum, rounds, S, h->fmt.B, h->st));
+    CK(launch_dsum_from_b(b, K, a, e, dsum, chunks, S, h->fmt.B, h->st));
     cudaError_t err = launch_unwrap((const float2 *)y, (long)n_y, b, K, 0, (long)a, (long)e, dsum,
                                     carry_in, 2, carry_out, 2, (float2 *)z, K, 0, pcode, K, 0, part,
-                                    sigma2, 1, ticket, 1, rounds, nullptr, S, h->fmt, h->st);
+                                    sigma2, 1, ticket, 1, chunks, nullptr, S, h->fmt, h->st);
     cudaFreeAsync(dsum, h->st);
     cudaFreeAsync(part, h->st);
     cudaFreeAsync(ticket, h->st);
@@ -1349,8 +1383,8 @@ int rx_unwrap_static(rx_handle *h, const void *y, size_t n_y, const uint8_t *b, 
     if (e <= a || e > n_y) return fail(RX_EINVAL, "bad range");
     const int S = h->streams;
     const long K = (long)(e - a);
-    const int rounds = bps_rounds(K, S);
-    const long ncta = (K + bps_cta_range(rounds) - 1) / bps_cta_range(rounds);
+    const int chunks = bps_chunks(K, S);
+    const long ncta = (K + bps_cta_range(chunks) - 1) / bps_cta_range(chunks);
     const size_t off_dsum = align256(sizeof(unsigned) * (size_t)S);
     const size_t off_part = off_dsum + align256(sizeof(int) * (size_t)S * ncta);
     const size_t need = off_part + sizeof(double) * (size_t)S * ncta;
@@ -1368,10 +1402,10 @@ int rx_unwrap_static(rx_handle *h, const void *y, size_t n_y, const uint8_t *b, 
     double *part = reinterpret_cast<double *>(sc + off_part);
     // the tickets must start at zero; the other regions are written before read
     CK(cudaMemsetAsync(ticket, 0, sizeof(unsigned) * (size_t)S, h->st));
-    CK(launch_dsum_from_b(b, K, a, e, dsum, rounds, S, h->fmt.B, h->st));
+    CK(launch_dsum_from_b(b, K, a, e, dsum, chunks, S, h->fmt.B, h->st));
     CK(launch_unwrap((const float2 *)y, (long)n_y, b, K, 0, (long)a, (long)e, dsum, carry_in, 2,
                      carry_out, 2, (float2 *)z, K, 0, pcode, K, 0, part, sigma2, 1, ticket, 1,
-                     rounds, nullptr, S, h->fmt, h->st));
+                     chunks, nullptr, S, h->fmt, h->st));
     return RX_OK;
 }
 

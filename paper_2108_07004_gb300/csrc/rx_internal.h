@@ -169,14 +169,14 @@ cudaError_t launch_align(const void *x, long ns, float2 *taps, const uint8_t *re
                          long ref_stride, int n_train, int n_streams, int T, const FmtDev &f,
                          cudaStream_t st, int sk = SK_F32);
 
-int bps_cta_range(int rounds);              // output symbols per BPS / unwrap block
-int bps_rounds(long len, int n_streams, int sm_avail = 0);    // rounds that fill about one wave
+int bps_cta_range(int chunks);              // output symbols per BPS / unwrap block
+int bps_chunks(long len, int n_streams, int sm_avail = 0);    // chunks per block for about one wave
 
 // mdsum (optional, [S][n_blocks] float64): per-block sums of the minimum
 // distance at the chosen phase, the decision-directed noise of the range
 cudaError_t launch_bps(const void *y, long y_stride, long a, long e, long n_valid,
                        int W, uint8_t *bout, long bout_stride, long bout_off,
-                       int *dsum, double *mdsum, int rounds, int n_streams, const FmtDev &f,
+                       int *dsum, double *mdsum, int chunks, int n_streams, const FmtDev &f,
                        cudaStream_t st, int sk = SK_F32);
 
 cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long b_stride,
@@ -186,7 +186,7 @@ cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long
                           float2 *z, long z_stride, long z_off,
                           uint16_t *pcode, long pcode_stride, long pcode_off,
                           double *partial, double *sigma2_out, int sigma2_stride,
-                          unsigned int *ticket, int ticket_stride, int rounds,
+                          unsigned int *ticket, int ticket_stride, int chunks,
                           const double *mdsum, int n_streams, const FmtDev &f, cudaStream_t st);
 
 cudaError_t launch_anchor(const uint8_t *b, long b_stride, const uint16_t *tcode, long t_stride,
@@ -194,7 +194,7 @@ cudaError_t launch_anchor(const uint8_t *b, long b_stride, const uint16_t *tcode
                           cudaStream_t st);
 
 cudaError_t launch_dsum_from_b(const uint8_t *b, long b_stride, long a, long e, int *dsum,
-                               int rounds, int n_streams, int B, cudaStream_t st);
+                               int chunks, int n_streams, int B, cudaStream_t st);
 
 struct DemapCount {
     const uint8_t *ref_lab;   // [S][N] labels of the reference (or null)
