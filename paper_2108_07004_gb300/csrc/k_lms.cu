@@ -578,32 +578,24 @@ lms_block_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__
 // ---------------------------------------------------------------------------
 // training alignment
 // ---------------------------------------------------------------------------
-template <int T, int DIMS>
+// Correlation of the equalised training span (y [S][2][ystride], storage sk,
+// the FIR's output with the start-up taps) with the known symbols:
+// C[q][p] = sum_k y_q[k] conj(s_p[k]); keep or swap the outputs, then turn
+// each by the phase of its matched correlation (taps [S][2][2][T] in place).
+template <int DIMS>
 __global__ void __launch_bounds__(256)
-align_kernel(const void *__restrict__ x, long ns, float2 *__restrict__ taps,
+align_kernel(const void *__restrict__ y, long ystride, float2 *__restrict__ taps, int T,
              const uint8_t *__restrict__ ref_lab, long ref_stride, int n_train, int sk,
              const __grid_constant__ FmtDev f) {
-    constexpr int D = (T - 1) / 2;
-    __shared__ float2 hs[4 * T];
     __shared__ double red[8][256];
     __shared__ float2 rot[2];
     __shared__ int src[2];
+    __shared__ float2 hs[4 * 31];
     const int s = blockIdx.x, tid = threadIdx.x;
-    for (int i = tid; i < 4 * T; i += 256) hs[i] = taps[(long)s * 4 * T + i];
-    __syncthreads();
-    const long xoff = (long)s * 2 * ns;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // C[q][p] re, im
     for (int k = tid; k < n_train; k += 256) {
-        float2 y[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        for (int qq = 0; qq < 2; ++qq)
-            for (int pp = 0; pp < 2; ++pp)
-                for (int t = 0; t < T; ++t) {
-                    const long g = 2L * k + D - t;
-                    if (g < 0 || g >= ns) continue;
-                    const float2 hv = hs[(qq * 2 + pp) * T + t];
-                    const float2 xv = ld_sample(x, xoff + (long)pp * ns + g, sk);
-                    y[qq] = cadd(y[qq], cmulc(hv, xv));
-                }
+        const float2 y0 = ld_sample(y, ((long)s * 2 + 0) * ystride + k, sk);
+        const float2 y1 = ld_sample(y, ((long)s * 2 + 1) * ystride + k, sk);
         const int lab = ref_lab[(long)s * ref_stride + k];
         float2 sp[2];
         if (DIMS == 4) {
@@ -614,14 +606,16 @@ align_kernel(const void *__restrict__ x, long ns, float2 *__restrict__ taps,
             sp[0] = make_float2(f.pts[lx][0], f.pts[lx][1]);
             sp[1] = make_float2(f.pts[ly][0], f.pts[ly][1]);
         }
+        const float2 yq[2] = {y0, y1};
         for (int qq = 0; qq < 2; ++qq)
             for (int pp = 0; pp < 2; ++pp) {
-                const float2 c = cmulc(sp[pp], y[qq]);   // y_q conj(s_p)
+                const float2 c = cmulc(sp[pp], yq[qq]);   // y_q conj(s_p)
                 acc[(qq * 2 + pp) * 2] += c.x;
                 acc[(qq * 2 + pp) * 2 + 1] += c.y;
             }
     }
     for (int i = 0; i < 8; ++i) red[i][tid] = acc[i];
+    for (int i = tid; i < 4 * T; i += 256) hs[i] = taps[(long)s * 4 * T + i];
     __syncthreads();
     for (int w = 128; w > 0; w >>= 1) {
         if (tid < w)
@@ -652,32 +646,21 @@ align_kernel(const void *__restrict__ x, long ns, float2 *__restrict__ taps,
     }
 }
 
-// Data-aided phase codes over the training span [0, n):
+// Data-aided phase codes over the training span [0, n) from the equalised
+// span y (the FIR's output with the aligned taps):
 //   R_k = sum_{i in [k - W/2, k + W/2) within the span} sum_p y_p[i] conj(s_p[i]),
 //   n_k = floor(arg(R_k) / (2 pi / (S B)) + 1/2), code = b | (m mod S) << 8 with
 //   b = n_k + B/2 - m B, m = floor((n_k + B/2) / B).
-template <int T, int DIMS>
+template <int DIMS>
 __global__ void __launch_bounds__(256)
-train_phase_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps,
-                   const uint8_t *__restrict__ ref_lab, long ref_stride, int n, int W,
-                   uint16_t *__restrict__ pcode, long pcode_stride, int32_t *__restrict__ carry,
-                   int carry_stride, int sk, const __grid_constant__ FmtDev f) {
-    constexpr int D = (T - 1) / 2;
+train_phase_kernel(const void *__restrict__ y, long ystride, const uint8_t *__restrict__ ref_lab,
+                   long ref_stride, int n, int W, uint16_t *__restrict__ pcode, long pcode_stride,
+                   int32_t *__restrict__ carry, int carry_stride, int sk, const __grid_constant__ FmtDev f) {
     extern __shared__ float2 rs[];      // [n] per-symbol correlations
-    __shared__ float2 hs[4 * T];
     const int s = blockIdx.x, tid = threadIdx.x;
-    for (int i = tid; i < 4 * T; i += 256) hs[i] = taps[(long)s * 4 * T + i];
-    __syncthreads();
-    const long xoff = (long)s * 2 * ns;
     for (int k = tid; k < n; k += 256) {
-        float2 y[2] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
-        for (int qq = 0; qq < 2; ++qq)
-            for (int pp = 0; pp < 2; ++pp)
-                for (int t = 0; t < T; ++t) {
-                    const long g = 2L * k + D - t;
-                    if (g < 0 || g >= ns) continue;
-                    y[qq] = cadd(y[qq], cmulc(hs[(qq * 2 + pp) * T + t], ld_sample(x, xoff + (long)pp * ns + g, sk)));
-                }
+        const float2 y0 = ld_sample(y, ((long)s * 2 + 0) * ystride + k, sk);
+        const float2 y1 = ld_sample(y, ((long)s * 2 + 1) * ystride + k, sk);
         const int lab = ref_lab[(long)s * ref_stride + k];
         float2 s0, s1;
         if (DIMS == 4) {
@@ -688,7 +671,7 @@ train_phase_kernel(const void *__restrict__ x, long ns, const float2 *__restrict
             s0 = make_float2(f.pts[lx][0], f.pts[lx][1]);
             s1 = make_float2(f.pts[ly][0], f.pts[ly][1]);
         }
-        rs[k] = cadd(cmulc(s0, y[0]), cmulc(s1, y[1]));   // sum_p y_p conj(s_p)
+        rs[k] = cadd(cmulc(s0, y0), cmulc(s1, y1));   // sum_p y_p conj(s_p)
     }
     __syncthreads();
     const int B = f.B, S = f.S;
@@ -783,16 +766,6 @@ cudaError_t lms_dispatch_dims(const void *x, long ns, const float2 *ti, float2 *
     }
 }
 
-template <int T>
-cudaError_t align_dispatch(const void *x, long ns, float2 *taps, const uint8_t *ref,
-                           long rstride, int n_train, int S, const FmtDev &f, cudaStream_t st, int sk) {
-    if (f.dims == 4)
-        align_kernel<T, 4><<<S, 256, 0, st>>>(x, ns, taps, ref, rstride, n_train, sk, f);
-    else
-        align_kernel<T, 2><<<S, 256, 0, st>>>(x, ns, taps, ref, rstride, n_train, sk, f);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 cudaError_t launch_lms(const void *x, long ns, const float2 *taps_in, float2 *taps_out, long k0,
@@ -841,42 +814,37 @@ cudaError_t launch_lms_block(const void *x, long ns, const float2 *taps_in, floa
     return cudaGetLastError();
 }
 
-cudaError_t launch_align(const void *x, long ns, float2 *taps, const uint8_t *ref_lab,
+cudaError_t launch_align(const void *y, long ystride, float2 *taps, const uint8_t *ref_lab,
                          long ref_stride, int n_train, int n_streams, int T, const FmtDev &f,
                          cudaStream_t st, int sk) {
     if (n_train <= 0 || n_streams <= 0) return cudaSuccess;
-    switch (T) {
-        case 7: return align_dispatch<7>(x, ns, taps, ref_lab, ref_stride, n_train, n_streams, f, st, sk);
-        case 15: return align_dispatch<15>(x, ns, taps, ref_lab, ref_stride, n_train, n_streams, f, st, sk);
-        case 31: return align_dispatch<31>(x, ns, taps, ref_lab, ref_stride, n_train, n_streams, f, st, sk);
-        default: return cudaErrorInvalidValue;
-    }
+    if (T != 7 && T != 15 && T != 31) return cudaErrorInvalidValue;
+    if (f.dims == 4)
+        align_kernel<4><<<n_streams, 256, 0, st>>>(y, ystride, taps, T, ref_lab, ref_stride, n_train, sk, f);
+    else
+        align_kernel<2><<<n_streams, 256, 0, st>>>(y, ystride, taps, T, ref_lab, ref_stride, n_train, sk, f);
+    return cudaGetLastError();
 }
 
-cudaError_t launch_train_phase(const void *x, long ns, const float2 *taps, const uint8_t *ref_lab,
-                               long ref_stride, int n, int W, uint16_t *pcode, long pcode_stride,
-                               int32_t *carry, int carry_stride, int n_streams, int T,
-                               const FmtDev &f, cudaStream_t st, int sk) {
+cudaError_t launch_train_phase(const void *y, long ystride, const uint8_t *ref_lab, long ref_stride, int n,
+                               int W, uint16_t *pcode, long pcode_stride, int32_t *carry, int carry_stride,
+                               int n_streams, const FmtDev &f, cudaStream_t st, int sk) {
     if (n <= 0 || n_streams <= 0) return cudaSuccess;
     const size_t smem = sizeof(float2) * (size_t)n;
     if (smem > 160 * 1024) return cudaErrorInvalidValue;
-#define RX_TP(TT, DD)                                                                          \
-    do {                                                                                       \
-        auto k_ = train_phase_kernel<TT, DD>;                                                  \
-        cudaError_t e_ = cudaFuncSetAttribute(k_, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                              (int)smem);                                     \
-        if (e_ != cudaSuccess) return e_;                                                      \
-        k_<<<n_streams, 256, smem, st>>>(x, ns, taps, ref_lab, ref_stride, n, W, pcode,        \
-                                         pcode_stride, carry, carry_stride, sk, f);            \
-    } while (0)
-    const bool d4 = f.dims == 4;
-    switch (T) {
-        case 7: if (d4) RX_TP(7, 4); else RX_TP(7, 2); break;
-        case 15: if (d4) RX_TP(15, 4); else RX_TP(15, 2); break;
-        case 31: if (d4) RX_TP(31, 4); else RX_TP(31, 2); break;
-        default: return cudaErrorInvalidValue;
+    if (f.dims == 4) {
+        cudaError_t e = cudaFuncSetAttribute(train_phase_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        train_phase_kernel<4><<<n_streams, 256, smem, st>>>(y, ystride, ref_lab, ref_stride, n, W, pcode,
+                                                             pcode_stride, carry, carry_stride, sk, f);
+    } else {
+        cudaError_t e = cudaFuncSetAttribute(train_phase_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem);
+        if (e != cudaSuccess) return e;
+        train_phase_kernel<2><<<n_streams, 256, smem, st>>>(y, ystride, ref_lab, ref_stride, n, W, pcode,
+                                                             pcode_stride, carry, carry_stride, sk, f);
     }
-#undef RX_TP
     return cudaGetLastError();
 }
 

@@ -86,6 +86,9 @@ struct rx_handle {
     // FIR and BPS of block n + 1 (ev_bps: BPS of a block done; ev_dm: its
     // demap done, by block parity)
     cudaStream_t dst = nullptr;
+    // the equalised training span [S][2][n_train] (start-up scratch)
+    void *ytr = nullptr;
+    size_t ytr_cap = 0;
     cudaEvent_t ev_bps[2] = {nullptr, nullptr}, ev_dm[2] = {nullptr, nullptr}, ev_setup = nullptr;
     cudaEvent_t ev_unwrap = nullptr;
     cudaEvent_t ev_cdc0 = nullptr, ev_start = nullptr;   // start-up overlap with the CDC
@@ -470,9 +473,19 @@ void prof_end(rx_handle *h, int stage, cudaEvent_t a, cudaStream_t s, int launch
 int train_stage(rx_handle *h, const void *x, long ns, float2 *taps, long ntr, uint16_t *pcode,
                 long pcode_stride, int32_t *carry, int carry_stride, cudaStream_t st, int sk) {
     const int S = h->streams, T = h->T;
-    STAGE(ST_STARTUP, st, 1, launch_align(x, ns, taps, h->ref, h->ref_n, (int)ntr, S, T, h->fmt, st, sk));
-    STAGE(ST_STARTUP, st, 1, launch_train_phase(x, ns, taps, h->ref, h->ref_n, (int)ntr, h->W, pcode,
-                                                pcode_stride, carry, carry_stride, S, T, h->fmt, st, sk));
+    // the training span equalised by the FIR kernel, once with the start-up
+    // taps (for the alignment) and once with the aligned taps (for the phases)
+    const size_t need = store_bytes(sk) * (size_t)S * 2 * ntr;
+    if (h->ytr_cap < need) {
+        if (h->ytr) { CK(cudaStreamSynchronize(st)); cudaFree(h->ytr); h->ytr = nullptr; }
+        CK(cudaMalloc(&h->ytr, need));
+        h->ytr_cap = need;
+    }
+    STAGE(ST_STARTUP, st, 1, launch_fir(x, ns, taps, 0, ntr, h->ytr, ntr, 0, S, T, st, sk));
+    STAGE(ST_STARTUP, st, 1, launch_align(h->ytr, ntr, taps, h->ref, h->ref_n, (int)ntr, S, T, h->fmt, st, sk));
+    STAGE(ST_STARTUP, st, 1, launch_fir(x, ns, taps, 0, ntr, h->ytr, ntr, 0, S, T, st, sk));
+    STAGE(ST_STARTUP, st, 1, launch_train_phase(h->ytr, ntr, h->ref, h->ref_n, (int)ntr, h->W, pcode,
+                                                pcode_stride, carry, carry_stride, S, h->fmt, st, sk));
     if (h->train_passes > 0)
         STAGE(ST_STARTUP, st, 1, launch_lms(x, ns, taps, taps, 0, (int)ntr, pcode, pcode_stride, 3,
                                             h->train_passes, 0, 0, (float)h->mu, h->ref, h->ref_n,
@@ -863,6 +876,7 @@ void rx_destroy(rx_handle *h) {
     cudaFree(h->ref);
     cudaFree(h->d_in);
     cudaFree(h->d_out);
+    cudaFree(h->ytr);
     if (h->h_in) cudaFreeHost(h->h_in);
     if (h->h_out) cudaFreeHost(h->h_out);
     delete h;

@@ -160,12 +160,14 @@ cudaError_t launch_lms_block(const void *x, long ns, const float2 *taps_in, floa
                              unsigned long long u0, int n_cma, float mu, int P, int n_streams, int T,
                              const FmtDev &f, cudaStream_t st, int sk = SK_F32);
 
-cudaError_t launch_train_phase(const void *x, long ns, const float2 *taps, const uint8_t *ref_lab,
-                               long ref_stride, int n, int W, uint16_t *pcode, long pcode_stride,
-                               int32_t *carry, int carry_stride, int n_streams, int T,
-                               const FmtDev &f, cudaStream_t st, int sk = SK_F32);
+// Training stage kernels on the equalised training span y [S][2][ystride]
+// (storage kind sk): data-aided phase codes, and the output order / phase
+// alignment of the taps [S][2][2][T] (in place).
+cudaError_t launch_train_phase(const void *y, long ystride, const uint8_t *ref_lab, long ref_stride, int n,
+                               int W, uint16_t *pcode, long pcode_stride, int32_t *carry, int carry_stride,
+                               int n_streams, const FmtDev &f, cudaStream_t st, int sk = SK_F32);
 
-cudaError_t launch_align(const void *x, long ns, float2 *taps, const uint8_t *ref_lab,
+cudaError_t launch_align(const void *y, long ystride, float2 *taps, const uint8_t *ref_lab,
                          long ref_stride, int n_train, int n_streams, int T, const FmtDev &f,
                          cudaStream_t st, int sk = SK_F32);
 
