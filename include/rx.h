@@ -110,6 +110,11 @@ void rx_destroy(rx_handle *h);                      /* NULL-safe */
  *   (<= 20000), "train_passes" [3],
  *   "sigma2" [0 = estimate per block], "skip_head" [4096],
  *   "skip_tail" [512], "streams" [1], "rolloff" [0.1],
+ *   "widely_linear" [0]: 1 makes the butterfly widely linear, y_q =
+ *   sum_p sum_t conj(h_qp[t]) x_p[2k+D-t] + conj(g_qp[t]) conj(x_p[2k+D-t])
+ *   (the paper's equaliser acts on the signal and its conjugate, Sec. 2);
+ *   every tap array of the handle and of the stage entries (rx_fir, rx_lms,
+ *   rx_train) is then [S][2][2][2T] with h_qp[0..T-1] then g_qp[0..T-1],
  *   "lms_block" [1]: the block-wise (blind) tap updates in groups of this
  *   many (1..64) whose outputs and errors all use the taps at the group's
  *   start (block LMS, a parallel variant beside the exact recursion; also
@@ -199,7 +204,9 @@ int rx_process_blocks(rx_handle *h, const void *samples, size_t n_samples, size_
 /* Checkpoint / resume of the stream state between blocks (what block n of
  * the schedule needs from blocks before it).  A state is a host byte
  * buffer: one rx_state_header, then, for n = blocks_done, L = lag,
- * S = streams, T = taps, W = bps_window, K = n*block:
+ * S = streams, T = taps per butterfly branch (the filter length, 2x it when
+ * "widely_linear" is 1; the header's taps field holds this number),
+ * W = bps_window, K = n*block:
  *   taps     [L][S][2][2][T] c64: U_{n-L+j}, j = 0 .. L-1, the LMS results
  *            blocks n .. n+L-1 equalise with (block n+j uses entry j);
  *            U_{n-1} (entry L-1) is where the LMS of block n starts;

@@ -48,6 +48,7 @@ class RxParams:
     cma_passes: int = 1
     n_cma: int = 0             # block-wise updates run as CMA before DD
     lms_block: int = 1         # block-wise updates in groups of this many (1: sequential)
+    widely_linear: bool = False  # butterfly on x and conj(x) (augmented taps, 2T per branch)
     n_train: int = 1024        # known training symbols at the stream start
     train_passes: int = 3      # data-aided LMS passes over the training span
     sigma2: float | None = None  # fixed noise variance, else per-block estimate
@@ -123,13 +124,26 @@ def cdc(r: np.ndarray, p: RxParams, H: np.ndarray | None = None) -> np.ndarray:
 # A2: 2x2 butterfly FIR, T/2-spaced in, one output per symbol
 # ---------------------------------------------------------------------------
 
-def center_spike(T: int) -> np.ndarray:
-    """h[q, p, t]: identity butterfly, h_XX[D] = h_YY[D] = 1, D=(T-1)/2."""
-    h = np.zeros((2, 2, T), dtype=np.complex128)
+def center_spike(T: int, widely_linear: bool = False) -> np.ndarray:
+    """h[q, p, t]: identity butterfly, h_XX[D] = h_YY[D] = 1, D=(T-1)/2.
+    Widely linear: 2T taps per branch, the first T on x (identity), the
+    last T on conj(x) (zero)."""
+    h = np.zeros((2, 2, 2 * T if widely_linear else T), dtype=np.complex128)
     D = (T - 1) // 2
     h[0, 0, D] = 1.0
     h[1, 1, D] = 1.0
     return h
+
+
+def window(x: np.ndarray, k: int, L: int) -> np.ndarray:
+    """The input window of update k for taps of length L per branch: x_window
+    for odd L (= T), and for even L = 2T the widely-linear window
+    [x_window, conj(x_window)] (paper Sec. 2: a widely linear equaliser acts
+    on the signal and its conjugate)."""
+    if L % 2:
+        return x_window(x, k, L)
+    xw = x_window(x, k, L // 2)
+    return np.concatenate([xw, np.conj(xw)], axis=1)
 
 
 def x_window(x: np.ndarray, k: int, T: int) -> np.ndarray:
@@ -145,8 +159,12 @@ def x_window(x: np.ndarray, k: int, T: int) -> np.ndarray:
 
 
 def fir(x: np.ndarray, h: np.ndarray, k0: int, k1: int) -> np.ndarray:
-    """y_q[k] = sum_p sum_t conj(h[q,p,t]) * x_p[2k + D - t] for k0 <= k < k1."""
-    T = h.shape[2]
+    """y_q[k] = sum_p sum_t conj(h[q,p,t]) * x_p[2k + D - t] for k0 <= k < k1;
+    with widely-linear taps (2T per branch) also + conj(h[q,p,T+t]) *
+    conj(x_p[2k + D - t])."""
+    L = h.shape[2]
+    wl = L % 2 == 0
+    T = L // 2 if wl else L
     D = (T - 1) // 2
     ns = x.shape[1]
     k = np.arange(k0, k1)
@@ -159,6 +177,8 @@ def fir(x: np.ndarray, h: np.ndarray, k0: int, k1: int) -> np.ndarray:
                 v = np.zeros(k.shape, dtype=np.complex128)
                 v[ok] = x[pol, i[ok]]
                 y[q] += np.conj(h[q, pol, t]) * v
+                if wl:
+                    y[q] += np.conj(h[q, pol, T + t]) * np.conj(v)
     return y
 
 
@@ -217,7 +237,7 @@ def lms(x: np.ndarray, h: np.ndarray, ks, fmt: OracleFormat, p: RxParams,
     R2 = fmt.cma_radius2()
     u = u0
     for k in ks:
-        xw = x_window(x, k, T)
+        xw = window(x, k, T)
         y = np.array([np.sum(np.conj(h[q]) * xw) for q in range(2)])
         if force_cma or u < p.n_cma:
             e = (R2 - np.abs(y) ** 2) * y           # conj(e) = (R^2-|y|^2) conj(y)
@@ -253,7 +273,7 @@ def lms_block(x: np.ndarray, h: np.ndarray, ks, fmt: OracleFormat, p: RxParams, 
     for g0 in range(0, len(ks), P):
         terms = []
         for k in ks[g0:g0 + P]:
-            xw = x_window(x, k, T)
+            xw = window(x, k, T)
             y = np.array([np.sum(np.conj(h[q]) * xw) for q in range(2)])
             if u < p.n_cma:
                 e = (R2 - np.abs(y) ** 2) * y
@@ -323,7 +343,7 @@ def lms_trained(x: np.ndarray, h: np.ndarray, ks, ref_sym: np.ndarray, phase: np
     h = h.copy()
     T = h.shape[2]
     for k in ks:
-        xw = x_window(x, k, T)
+        xw = window(x, k, T)
         y = np.array([np.sum(np.conj(h[q]) * xw) for q in range(2)])
         e = ref_sym[:, k] * np.exp(1j * phase[k]) - y
         for q in range(2):
@@ -545,7 +565,7 @@ def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
     W, B, L, S = p.bps_window, p.bps_phases, p.lag, fmt.sym_order
     assert p.n_upd + W // 2 <= p.block, "update span must have phases in its block"
     x = cdc(r, p)
-    h = center_spike(p.taps)
+    h = center_spike(p.taps, p.widely_linear)
     npre = 0 if resume else min(p.n_pre, N)
     for _ in range(p.cma_passes if npre else 0):
         h = lms(x, h, range(npre), fmt, p, force_cma=True)

@@ -38,7 +38,7 @@ constexpr int kBarCor = 2;     // named barrier of the correlation group (128 th
 // shared-memory layout of lms_kernel<T> (float2 units)
 __host__ __device__ constexpr int lms_nsx(int T) { return 2 * kCH + (T - 1) + 2 * (kSB + kLag) + 4; }
 __host__ __device__ constexpr int lms_off_h(int T) { return 2 * lms_nsx(T); }
-__host__ __device__ constexpr int lms_off_r(int T) { return lms_off_h(T) + 4 * T; }
+__host__ __device__ constexpr int lms_off_r(int T) { return lms_off_h(T) + 8 * T; }   // taps: room for 2T per branch
 __host__ __device__ constexpr int lms_off_rp(int T) { return lms_off_r(T) + 2 * kSB * kLag; }
 __host__ __device__ constexpr int lms_off_b(int T) { return lms_off_rp(T) + kSB * kLag * 4; }
 __host__ __device__ constexpr int lms_off_e(int T) { return lms_off_b(T) + 2 * kSB * 2; }
@@ -122,14 +122,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_in,
            float2 *__restrict__ taps_out, long k0, int n_upd, const uint16_t *__restrict__ pcode,
            long pcode_stride, int passes, float mu, const uint8_t *__restrict__ ref_lab,
-           long ref_stride, int sk, const __grid_constant__ FmtDev f) {
+           long ref_stride, int sk, int wl, const __grid_constant__ FmtDev f) {
     constexpr int D = (T - 1) / 2;
     constexpr int NSX = lms_nsx(T);
+    const int L = wl ? 2 * T : T;                     // taps per branch (widely linear: [h on x, g on conj x])
     __shared__ Tables tb;
     extern __shared__ float2 dyn_sm[];
     // local sample index of x_p[2 (kb + k) + D - t] is 2 k + 2 D - t
     float2 *xs0 = dyn_sm, *xs1 = dyn_sm + NSX;
-    float2 *Hs = dyn_sm + lms_off_h(T);               // taps [q][p][t]
+    float2 *Hs = dyn_sm + lms_off_h(T);               // taps [q][p][t], t < L
     float2 *Rt = dyn_sm + lms_off_r(T);               // [2][kSB][kLag]: mu r(j, j + d)
     float2 *Rp = dyn_sm + lms_off_rp(T);              // [kSB][kLag][4]: per (p, parity) partial sums
     float2 *bsb = dyn_sm + lms_off_b(T);              // [2][kSB][q]: H^H X_k
@@ -145,32 +146,36 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
     const int gt = (hw & 3) * 32 + lane;                       // index within a group
     auto xsp = [&](int pp) { return pp ? xs1 : xs0; };
     load_tables(tb, f);
-    for (int i = threadIdx.x; i < 4 * T; i += blockDim.x) Hs[i] = taps_in[(long)s_id * 4 * T + i];
+    for (int i = threadIdx.x; i < 4 * L; i += blockDim.x) Hs[i] = taps_in[(long)s_id * 4 * L + i];
     const long xoff = (long)s_id * 2 * ns;
     const int qt_step = 4 / f.S;
 
     // tap group: h += mu sum_{i < m} conj(e_{jb + i}) X_{jb + i}; thread
-    // (q, p, t) owns one tap
+    // (q, p, t) owns one tap (two when widely linear: the taps on conj(x)
+    // take the conjugate samples)
     auto tap_update = [&](int jb, int m, const float4 *E) {
-        if (gt < 4 * T) {
-            const int q = gt / (2 * T), rem = gt - q * 2 * T, pp = rem / T, t = rem - pp * T;
+        for (int te = gt; te < 4 * L; te += 128) {
+            const int q = te / (2 * L), rem = te - q * 2 * L, pp = rem / L, tt = rem - pp * L;
+            const bool cj = tt >= T;
+            const int t = cj ? tt - T : tt;
             const float2 *xp = xsp(pp) + 2 * jb + 2 * D - t;
             float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+            auto xv = [&](int i) { const float2 v = xp[2 * i]; return cj ? make_float2(v.x, -v.y) : v; };
             if (m == kSB) {
 #pragma unroll
                 for (int i = 0; i < kSB; i += 2) {
                     const float4 e = E[i], f1 = E[i + 1];
-                    a0 = cadd(a0, cmulc(q ? make_float2(e.z, e.w) : make_float2(e.x, e.y), xp[2 * i]));
-                    a1 = cadd(a1, cmulc(q ? make_float2(f1.z, f1.w) : make_float2(f1.x, f1.y), xp[2 * i + 2]));
+                    a0 = cadd(a0, cmulc(q ? make_float2(e.z, e.w) : make_float2(e.x, e.y), xv(i)));
+                    a1 = cadd(a1, cmulc(q ? make_float2(f1.z, f1.w) : make_float2(f1.x, f1.y), xv(i + 1)));
                 }
             } else {
                 for (int i = 0; i < m; ++i) {
                     const float4 e = E[i];
-                    a0 = cadd(a0, cmulc(q ? make_float2(e.z, e.w) : make_float2(e.x, e.y), xp[2 * i]));
+                    a0 = cadd(a0, cmulc(q ? make_float2(e.z, e.w) : make_float2(e.x, e.y), xv(i)));
                 }
             }
             const float2 a = cadd(a0, a1);
-            Hs[gt] = cadd(Hs[gt], make_float2(mu * a.x, mu * a.y));
+            Hs[te] = cadd(Hs[te], make_float2(mu * a.x, mu * a.y));
         }
     };
     // tap group: H^H X_k for the kSB updates from kb0 into bsb row set `buf`;
@@ -179,13 +184,25 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
         const int kk = gt >> 3, q = (gt >> 2) & 1, pp = (gt >> 1) & 1, half = gt & 1;
         const int k = kb0 + kk;
         const float2 *xp = xsp(pp);
-        const float2 *hq = Hs + (q * 2 + pp) * T;
+        const float2 *hq = Hs + (q * 2 + pp) * L;
         float2 a0 = make_float2(0.f, 0.f), a1 = make_float2(0.f, 0.f);
+        if (wl) {
+            // half 0: taps on x, half 1: taps on conj(x)
+            const float2 *hh = hq + half * T;
 #pragma unroll
-        for (int tt = 0; tt < 16; tt += 2) {
-            const int t = 16 * half + tt;
-            if (t < T) a0 = cadd(a0, cmulc(hq[t], xp[2 * k + 2 * D - t]));
-            if (t + 1 < T) a1 = cadd(a1, cmulc(hq[t + 1], xp[2 * k + 2 * D - t - 1]));
+            for (int t = 0; t < T; ++t) {
+                const float2 v = xp[2 * k + 2 * D - t];
+                const float2 xv = half ? make_float2(v.x, -v.y) : v;
+                if (t & 1) a1 = cadd(a1, cmulc(hh[t], xv));
+                else a0 = cadd(a0, cmulc(hh[t], xv));
+            }
+        } else {
+#pragma unroll
+            for (int tt = 0; tt < 16; tt += 2) {
+                const int t = 16 * half + tt;
+                if (t < T) a0 = cadd(a0, cmulc(hq[t], xp[2 * k + 2 * D - t]));
+                if (t + 1 < T) a1 = cadd(a1, cmulc(hq[t + 1], xp[2 * k + 2 * D - t - 1]));
+            }
         }
         float2 acc = cadd(a0, a1);
         acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
@@ -217,7 +234,9 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
             const float4 *pp4 = reinterpret_cast<const float4 *>(Rp + idx * 4);
             const float4 a = pp4[0], b = pp4[1];
             const float2 sum = make_float2((a.x + a.z) + (b.x + b.z), (a.y + a.w) + (b.y + b.w));
-            Rt[buf * kSB * kLag + idx] = (idx & (kLag - 1)) ? make_float2(mu * sum.x, mu * sum.y) : make_float2(0.f, 0.f);
+            // widely linear: the augmented windows correlate to r + conj(r)
+            const float2 v = wl ? make_float2(2.f * mu * sum.x, 0.f) : make_float2(mu * sum.x, mu * sum.y);
+            Rt[buf * kSB * kLag + idx] = (idx & (kLag - 1)) ? v : make_float2(0.f, 0.f);
         }
     };
     // one step of the even (E = 0) or odd (E = 1) share: row j from row j - 1
@@ -423,7 +442,7 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < 4 * T; i += blockDim.x) taps_out[(long)s_id * 4 * T + i] = Hs[i];
+    for (int i = threadIdx.x; i < 4 * L; i += blockDim.x) taps_out[(long)s_id * 4 * L + i] = Hs[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -488,19 +507,20 @@ template <int T, int DIMS>
 __global__ void __launch_bounds__(256)
 lms_block_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_in,
                  float2 *__restrict__ taps_out, long k0, int n_upd, const uint16_t *__restrict__ pcode,
-                 long pcode_stride, long u0, long n_cma, float mu, int P, int sk,
+                 long pcode_stride, long u0, long n_cma, float mu, int P, int sk, int wl,
                  const __grid_constant__ FmtDev f) {
     constexpr int D = (T - 1) / 2;
     constexpr int NSX = 2 * kCH + 2 * D + 2;
+    const int L = wl ? 2 * T : T;         // taps per branch
     __shared__ Tables tb;
     __shared__ float2 xs[2][NSX];         // local index of x_p[2 (kb + k) + D - t]: 2 k + 2 D - t
-    __shared__ float2 Hs[4 * T];
+    __shared__ float2 Hs[4 * 2 * T];
     __shared__ float2 ys[64][2];
     __shared__ float2 es[64][2];
     __shared__ uint16_t pc[kCH];
     const int s = blockIdx.x, tid = threadIdx.x;
     load_tables(tb, f);
-    for (int i = tid; i < 4 * T; i += blockDim.x) Hs[i] = taps_in[(long)s * 4 * T + i];
+    for (int i = tid; i < 4 * L; i += blockDim.x) Hs[i] = taps_in[(long)s * 4 * L + i];
     const long xoff = (long)s * 2 * ns;
     const int qt_step = 4 / f.S;
     for (int c0 = 0; c0 < n_upd; c0 += kCH) {
@@ -525,10 +545,17 @@ lms_block_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__
                 const int kk = it >> 3, q = (it >> 2) & 1, pp = (it >> 1) & 1, half = it & 1;
                 float2 acc = make_float2(0.f, 0.f);
                 if (act) {
-                    const float2 *hq = Hs + (q * 2 + pp) * T;
+                    const float2 *hq = Hs + (q * 2 + pp) * L;
                     const float2 *xp = xs[pp] + 2 * (g0 + kk) + 2 * D;
-                    const int t1 = half ? T : (T < 16 ? T : 16);
-                    for (int t = half ? 16 : 0; t < t1; ++t) acc = cadd(acc, cmulc(hq[t], xp[-t]));
+                    if (wl) {                        // half 0: taps on x, half 1: on conj(x)
+                        for (int t = 0; t < T; ++t) {
+                            const float2 v = xp[-t];
+                            acc = cadd(acc, cmulc(hq[half * T + t], half ? make_float2(v.x, -v.y) : v));
+                        }
+                    } else {
+                        const int t1 = half ? T : (T < 16 ? T : 16);
+                        for (int t = half ? 16 : 0; t < t1; ++t) acc = cadd(acc, cmulc(hq[t], xp[-t]));
+                    }
                 }
                 acc.x += __shfl_xor_sync(0xffffffffu, acc.x, 1);
                 acc.y += __shfl_xor_sync(0xffffffffu, acc.y, 1);
@@ -562,17 +589,21 @@ lms_block_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__
                 es[tid][1] = e1;
             }
             __syncthreads();
-            if (tid < 4 * T) {
-                const int q = tid / (2 * T), rem = tid - q * 2 * T, pp = rem / T, t = rem - pp * T;
-                const float2 *xp = xs[pp] + 2 * g0 + 2 * D - t;
+            if (tid < 4 * L) {
+                const int q = tid / (2 * L), rem = tid - q * 2 * L, pp = rem / L, tt = rem - pp * L;
+                const bool cj = tt >= T;
+                const float2 *xp = xs[pp] + 2 * g0 + 2 * D - (cj ? tt - T : tt);
                 float2 acc = make_float2(0.f, 0.f);
-                for (int i = 0; i < m; ++i) acc = cadd(acc, cmulc(es[i][q], xp[2 * i]));
+                for (int i = 0; i < m; ++i) {
+                    const float2 v = xp[2 * i];
+                    acc = cadd(acc, cmulc(es[i][q], cj ? make_float2(v.x, -v.y) : v));
+                }
                 Hs[tid] = cadd(Hs[tid], make_float2(mu * acc.x, mu * acc.y));
             }
             __syncthreads();
         }
     }
-    for (int i = tid; i < 4 * T; i += blockDim.x) taps_out[(long)s * 4 * T + i] = Hs[i];
+    for (int i = tid; i < 4 * L; i += blockDim.x) taps_out[(long)s * 4 * L + i] = Hs[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -590,7 +621,7 @@ align_kernel(const void *__restrict__ y, long ystride, float2 *__restrict__ taps
     __shared__ double red[8][256];
     __shared__ float2 rot[2];
     __shared__ int src[2];
-    __shared__ float2 hs[4 * 31];
+    __shared__ float2 hs[4 * 62];
     const int s = blockIdx.x, tid = threadIdx.x;
     double acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // C[q][p] re, im
     for (int k = tid; k < n_train; k += 256) {
@@ -709,7 +740,7 @@ __global__ void ref_labels_kernel(const uint8_t *__restrict__ bits, uint8_t *__r
 template <int T, int DIMS, int MODE>
 cudaError_t lms_launch_one(const void *x, long ns, const float2 *ti, float2 *to, long k0, int n_upd,
                            const uint16_t *pcode, long pstride, int passes, float mu,
-                           const uint8_t *ref, long rstride, int S, const FmtDev &f, cudaStream_t st, int sk) {
+                           const uint8_t *ref, long rstride, int S, const FmtDev &f, cudaStream_t st, int sk, int wl) {
     auto kern = lms_kernel<T, DIMS, MODE>;
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, kern);
@@ -721,7 +752,7 @@ cudaError_t lms_launch_one(const void *x, long ns, const float2 *ti, float2 *to,
     if (dyn < (int)(lms_smem_f2(T) * sizeof(float2))) return cudaErrorInvalidValue;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
     if (e != cudaSuccess) return e;
-    kern<<<S, kThreads, dyn, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, sk, f);
+    kern<<<S, kThreads, dyn, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, sk, wl, f);
     return cudaGetLastError();
 }
 
@@ -729,12 +760,12 @@ template <int T, int MODE>
 cudaError_t lms_launch_mode(const void *x, long ns, const float2 *ti, float2 *to, long k0,
                             int n_upd, const uint16_t *pcode, long pstride, int passes, float mu,
                             const uint8_t *ref, long rstride, int S, const FmtDev &f,
-                            cudaStream_t st, int sk) {
+                            cudaStream_t st, int sk, int wl) {
     if (f.dims == 4)
         return lms_launch_one<T, 4, MODE>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref,
-                                          rstride, S, f, st, sk);
+                                          rstride, S, f, st, sk, wl);
     return lms_launch_one<T, 2, MODE>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref,
-                                      rstride, S, f, st, sk);
+                                      rstride, S, f, st, sk, wl);
 }
 
 template <int T>
@@ -742,24 +773,24 @@ cudaError_t lms_dispatch_dims(const void *x, long ns, const float2 *ti, float2 *
                               int n_upd, const uint16_t *pcode, long pstride, int mode,
                               int passes, unsigned long long u0, int n_cma, float mu,
                               const uint8_t *ref, long rstride, int S, const FmtDev &f,
-                              cudaStream_t st, int sk) {
+                              cudaStream_t st, int sk, int wl) {
     switch (mode) {
-        case 0: return lms_launch_mode<T, 0>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk);
-        case 1: return lms_launch_mode<T, 1>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk);
-        case 3: return lms_launch_mode<T, 3>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk);
+        case 0: return lms_launch_mode<T, 0>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk, wl);
+        case 1: return lms_launch_mode<T, 1>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk, wl);
+        case 3: return lms_launch_mode<T, 3>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk, wl);
         case 2: {
             // CMA while the update count is below n_cma, DD after (one pass)
             const long ncma = (u0 >= (unsigned long long)n_cma) ? 0 : std::min<long>(n_upd, (long)(n_cma - u0));
             cudaError_t e = cudaSuccess;
             const float2 *src = ti;
             if (ncma > 0) {
-                e = lms_launch_mode<T, 0>(x, ns, src, to, k0, (int)ncma, pcode, pstride, 1, mu, ref, rstride, S, f, st, sk);
+                e = lms_launch_mode<T, 0>(x, ns, src, to, k0, (int)ncma, pcode, pstride, 1, mu, ref, rstride, S, f, st, sk, wl);
                 if (e != cudaSuccess) return e;
                 src = to;
             }
             if (n_upd - ncma > 0)
                 e = lms_launch_mode<T, 1>(x, ns, src, to, k0 + ncma, (int)(n_upd - ncma), pcode, pstride, 1, mu,
-                                          ref, rstride, S, f, st, sk);
+                                          ref, rstride, S, f, st, sk, wl);
             return e;
         }
         default: return cudaErrorInvalidValue;
@@ -771,7 +802,7 @@ cudaError_t lms_dispatch_dims(const void *x, long ns, const float2 *ti, float2 *
 cudaError_t launch_lms(const void *x, long ns, const float2 *taps_in, float2 *taps_out, long k0,
                        int n_upd, const uint16_t *pcode, long pcode_stride, int mode, int passes,
                        unsigned long long u0, int n_cma, float mu, const uint8_t *ref_lab,
-                       long ref_stride, int n_streams, int T, const FmtDev &f, cudaStream_t st, int sk) {
+                       long ref_stride, int n_streams, int T, const FmtDev &f, cudaStream_t st, int sk, int wl) {
     if (n_upd <= 0 || n_streams <= 0) {
         if (taps_in != taps_out)
             return cudaMemcpyAsync(taps_out, taps_in, sizeof(float2) * 4 * T * (size_t)n_streams,
@@ -779,9 +810,9 @@ cudaError_t launch_lms(const void *x, long ns, const float2 *taps_in, float2 *ta
         return cudaSuccess;
     }
     switch (T) {
-        case 7: return lms_dispatch_dims<7>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk);
-        case 15: return lms_dispatch_dims<15>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk);
-        case 31: return lms_dispatch_dims<31>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk);
+        case 7: return lms_dispatch_dims<7>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk, wl);
+        case 15: return lms_dispatch_dims<15>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk, wl);
+        case 31: return lms_dispatch_dims<31>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk, wl);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -789,11 +820,11 @@ cudaError_t launch_lms(const void *x, long ns, const float2 *taps_in, float2 *ta
 cudaError_t launch_lms_block(const void *x, long ns, const float2 *taps_in, float2 *taps_out, long k0,
                              int n_upd, const uint16_t *pcode, long pcode_stride, int mode,
                              unsigned long long u0, int n_cma, float mu, int P, int n_streams, int T,
-                             const FmtDev &f, cudaStream_t st, int sk) {
+                             const FmtDev &f, cudaStream_t st, int sk, int wl) {
     if (P < 1 || P > 64) return cudaErrorInvalidValue;
     if (n_upd <= 0 || n_streams <= 0) {
         if (taps_in != taps_out)
-            return cudaMemcpyAsync(taps_out, taps_in, sizeof(float2) * 4 * T * (size_t)n_streams,
+            return cudaMemcpyAsync(taps_out, taps_in, sizeof(float2) * 4 * (wl ? 2 * T : T) * (size_t)n_streams,
                                    cudaMemcpyDeviceToDevice, st);
         return cudaSuccess;
     }
@@ -802,7 +833,7 @@ cudaError_t launch_lms_block(const void *x, long ns, const float2 *taps_in, floa
     if (mode != 0 && !pcode) return cudaErrorInvalidValue;
 #define RX_LB(TT, DD)                                                                                      \
     lms_block_kernel<TT, DD><<<n_streams, 256, 0, st>>>(x, ns, taps_in, taps_out, k0, n_upd, pcode,          \
-                                                       pcode_stride, (long)u0, ncma, mu, P, sk, f)
+                                                       pcode_stride, (long)u0, ncma, mu, P, sk, wl, f)
     const bool d4 = f.dims == 4;
     switch (T) {
         case 7: if (d4) RX_LB(7, 4); else RX_LB(7, 2); break;
@@ -818,7 +849,7 @@ cudaError_t launch_align(const void *y, long ystride, float2 *taps, const uint8_
                          long ref_stride, int n_train, int n_streams, int T, const FmtDev &f,
                          cudaStream_t st, int sk) {
     if (n_train <= 0 || n_streams <= 0) return cudaSuccess;
-    if (T != 7 && T != 15 && T != 31) return cudaErrorInvalidValue;
+    if (T < 1 || T > 62) return cudaErrorInvalidValue;      // taps per branch (2 x 31 widely linear)
     if (f.dims == 4)
         align_kernel<4><<<n_streams, 256, 0, st>>>(y, ystride, taps, T, ref_lab, ref_stride, n_train, sk, f);
     else

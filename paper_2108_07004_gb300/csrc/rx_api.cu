@@ -72,6 +72,7 @@ struct rx_handle {
     int cma_passes = 1;
     long n_cma = 0;
     int lms_block = 1;       // block-wise updates in groups of this many (1: sequential)
+    int wl = 0;              // widely-linear butterfly: taps [S][2][2][2T] (x, then conj x)
     long n_train = 1024;
     int train_passes = 3;
     double sigma2_fixed = 0.0;
@@ -102,7 +103,7 @@ struct rx_handle {
     bool tables_dirty = true;
     // device buffers
     long cap_n = 0;
-    int cap_s = 0, cap_lag = 0;
+    int cap_s = 0, cap_lag = 0, cap_wl = 0;
     void *x = nullptr, *y = nullptr;                  // CDC and FIR outputs, storage kind prec
     float2 *ring = nullptr;
     uint8_t *bidx = nullptr;
@@ -345,16 +346,21 @@ int ensure_symbol_buffers(rx_handle *h, long N) {
     return RX_OK;
 }
 
+// taps per butterfly branch (widely linear: T on x, then T on conj x)
+int tl(const rx_handle *h) { return h->wl ? 2 * h->T : h->T; }
+
 int ensure_buffers(rx_handle *h, long N) {
     const int S = h->streams;
-    if (h->cap_n >= N && h->cap_s == S && h->cap_lag == h->lag && h->cap_prec == h->prec && h->sd) return RX_OK;
+    if (h->cap_n >= N && h->cap_s == S && h->cap_lag == h->lag && h->cap_prec == h->prec && h->cap_wl == h->wl &&
+        h->sd)
+        return RX_OK;
     free_buffers(h);
     const long ns = 2 * N;
     const long ncta = (N + bps_cta_range(1) - 1) / bps_cta_range(1) + 2;
     const long ncta_d = (h->block + 2 * h->W + 255) / 256 + 2;
     CK(cudaMalloc(&h->x, store_bytes(h->prec) * (size_t)S * 2 * ns));
     CK(cudaMalloc(&h->y, store_bytes(h->prec) * (size_t)S * 2 * N));
-    CK(cudaMalloc(&h->ring, sizeof(float2) * (size_t)(h->lag + 1) * S * 4 * h->T));
+    CK(cudaMalloc(&h->ring, sizeof(float2) * (size_t)(h->lag + 1) * S * 4 * tl(h)));
     CK(cudaMalloc(&h->bidx, (size_t)S * N));
     CK(cudaMalloc(&h->pcode, sizeof(uint16_t) * (size_t)S * N));
     CK(cudaMalloc(&h->dsum, sizeof(int) * 2 * (size_t)S * ncta));        // by block parity
@@ -368,6 +374,7 @@ int ensure_buffers(rx_handle *h, long N) {
     h->cap_dsum = ncta;
     h->cap_pd = ncta_d;
     h->cap_n = N;
+    h->cap_wl = h->wl;
     h->cap_s = S;
     h->cap_lag = h->lag;
     h->cap_prec = h->prec;
@@ -416,18 +423,18 @@ int check_config(rx_handle *h) {
 }
 
 void center_spike(const rx_handle *h, std::vector<float2> &v) {
-    const int T = h->T, D = (T - 1) / 2;
-    v.assign((size_t)h->streams * 4 * T, make_float2(0.f, 0.f));
+    const int T = h->T, D = (T - 1) / 2, L = tl(h);
+    v.assign((size_t)h->streams * 4 * L, make_float2(0.f, 0.f));
     for (int s = 0; s < h->streams; ++s) {
-        v[(size_t)s * 4 * T + 0 * T + D] = make_float2(1.f, 0.f);       // h_XX
-        v[(size_t)s * 4 * T + 3 * T + D] = make_float2(1.f, 0.f);       // h_YY
+        v[(size_t)s * 4 * L + 0 * L + D] = make_float2(1.f, 0.f);       // h_XX
+        v[(size_t)s * 4 * L + 3 * L + D] = make_float2(1.f, 0.f);       // h_YY
     }
 }
 
 float2 *slot(rx_handle *h, long n) {
     const int L1 = h->lag + 1;
     const long i = ((n % L1) + L1) % L1;
-    return h->ring + (size_t)i * h->streams * 4 * h->T;
+    return h->ring + (size_t)i * h->streams * 4 * tl(h);
 }
 
 enum { ST_CDC = 0, ST_FIR, ST_BPS, ST_UNWRAP, ST_DEMAP, ST_LMS, ST_STARTUP, ST_N };
@@ -481,15 +488,15 @@ int train_stage(rx_handle *h, const void *x, long ns, float2 *taps, long ntr, ui
         CK(cudaMalloc(&h->ytr, need));
         h->ytr_cap = need;
     }
-    STAGE(ST_STARTUP, st, 1, launch_fir(x, ns, taps, 0, ntr, h->ytr, ntr, 0, S, T, st, sk));
-    STAGE(ST_STARTUP, st, 1, launch_align(h->ytr, ntr, taps, h->ref, h->ref_n, (int)ntr, S, T, h->fmt, st, sk));
-    STAGE(ST_STARTUP, st, 1, launch_fir(x, ns, taps, 0, ntr, h->ytr, ntr, 0, S, T, st, sk));
+    STAGE(ST_STARTUP, st, 1, launch_fir(x, ns, taps, 0, ntr, h->ytr, ntr, 0, S, T, st, sk, 0, h->wl));
+    STAGE(ST_STARTUP, st, 1, launch_align(h->ytr, ntr, taps, h->ref, h->ref_n, (int)ntr, S, tl(h), h->fmt, st, sk));
+    STAGE(ST_STARTUP, st, 1, launch_fir(x, ns, taps, 0, ntr, h->ytr, ntr, 0, S, T, st, sk, 0, h->wl));
     STAGE(ST_STARTUP, st, 1, launch_train_phase(h->ytr, ntr, h->ref, h->ref_n, (int)ntr, h->W, pcode,
                                                 pcode_stride, carry, carry_stride, S, h->fmt, st, sk));
     if (h->train_passes > 0)
         STAGE(ST_STARTUP, st, 1, launch_lms(x, ns, taps, taps, 0, (int)ntr, pcode, pcode_stride, 3,
                                             h->train_passes, 0, 0, (float)h->mu, h->ref, h->ref_n,
-                                            S, T, h->fmt, st, sk));
+                                            S, T, h->fmt, st, sk, h->wl));
     return RX_OK;
 }
 
@@ -523,7 +530,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     const int S = h->streams, T = h->T, L = h->lag;
     const long Nb = h->block, ns = 2 * N;
     const long nblk = (N + Nb - 1) / Nb;
-    const size_t tapsz = sizeof(float2) * (size_t)S * 4 * T;
+    const size_t tapsz = sizeof(float2) * (size_t)S * 4 * tl(h);
     cudaStream_t st = h->st;
     int rc;
     if ((rc = upload_tables(h)) != RX_OK) return rc;
@@ -563,7 +570,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         CK(cudaMemcpyAsync(w0, cs.data(), tapsz, cudaMemcpyHostToDevice, ss));
         const long npre = std::min(h->n_pre, N);
         STAGE(ST_STARTUP, ss, 1, launch_lms(h->x, ns, w0, w0, 0, (int)npre, nullptr, 0, 0, h->cma_passes,
-                                            0, 0, (float)h->mu, nullptr, 0, S, T, f, ss, h->prec));
+                                            0, 0, (float)h->mu, nullptr, 0, S, T, f, ss, h->prec, h->wl));
         // stream state: counters zero, unwrap carry phi_hat = 0
         std::vector<StreamDev> &sd0 = h->h_sd0;
         sd0.assign(S, StreamDev{});
@@ -625,7 +632,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         const float2 *wn = slot(h, n - L);
         cudaEvent_t blk0 = nullptr;
         if (h->profile == 1 && (blk0 = prof_event(h))) CK(cudaEventRecord(blk0, st));
-        STAGE(ST_FIR, st, 1, launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st, h->prec, avail));
+        STAGE(ST_FIR, st, 1, launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st, h->prec, avail, h->wl));
         const long a = std::max(0L, k0 - h->W / 2);
         const long e = (n == nblk - 1) ? N : k1 - h->W / 2;
         const int chunks = bps_chunks(e - a, S, avail);
@@ -680,11 +687,11 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         if (h->lms_block > 1)
             STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
                   launch_lms_block(h->x, ns, slot(h, n - 1), slot(h, n), k0, (int)span, h->pcode, N, 2, h->u,
-                                   (int)h->n_cma, (float)h->mu, h->lms_block, S, T, f, ls, h->prec));
+                                   (int)h->n_cma, (float)h->mu, h->lms_block, S, T, f, ls, h->prec, h->wl));
         else
             STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
                   launch_lms(h->x, ns, slot(h, n - 1), slot(h, n), k0, (int)span, h->pcode, N, 2, 1,
-                             h->u, (int)h->n_cma, (float)h->mu, nullptr, 0, S, T, f, ls, h->prec));
+                             h->u, (int)h->n_cma, (float)h->mu, nullptr, 0, S, T, f, ls, h->prec, h->wl));
         if (L >= 2) CK(cudaEventRecord(h->ev_lms[n % (L + 1)], h->side));
         h->u += span;
         h->blocks_done = n + 1;
@@ -737,6 +744,7 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     else if (k == "cma_passes") { rc = as_int(0, 16, t); h->cma_passes = (int)t; }
     else if (k == "n_cma") { rc = as_int(0, 1L << 40, t); h->n_cma = t; }
     else if (k == "lms_block") { rc = as_int(1, 64, t); h->lms_block = (int)t; }
+    else if (k == "widely_linear") { rc = as_int(0, 1, t); h->wl = (int)t; h->started = false; }
     else if (k == "n_train") { rc = as_int(0, 20000, t); h->n_train = t; }
     else if (k == "train_passes") { rc = as_int(0, 64, t); h->train_passes = (int)t; }
     else if (k == "sigma2") { if (!(v >= 0)) return fail(RX_EINVAL, "sigma2 < 0"); h->sigma2_fixed = v; }
@@ -801,7 +809,7 @@ StateLayout state_layout(const rx_handle *h) {
     const size_t S = (size_t)h->streams;
     StateLayout l{};
     l.taps = sizeof(rx_state_header);
-    l.carry = l.taps + (size_t)h->lag * S * 4 * h->T * sizeof(float2);
+    l.carry = l.taps + (size_t)h->lag * S * 4 * tl(h) * sizeof(float2);
     l.y_tail = l.carry + S * 2 * sizeof(int32_t);
     l.counters = l.y_tail + S * 2 * (size_t)h->W * sizeof(float2);
     l.total = l.counters + S * sizeof(rx_state_counters);
@@ -901,6 +909,7 @@ int rx_get_param(const rx_handle *h, const char *key, double *value) {
     else if (k == "cma_passes") *value = h->cma_passes;
     else if (k == "n_cma") *value = (double)h->n_cma;
     else if (k == "lms_block") *value = h->lms_block;
+    else if (k == "widely_linear") *value = h->wl;
     else if (k == "n_train") *value = (double)h->n_train;
     else if (k == "train_passes") *value = h->train_passes;
     else if (k == "sigma2") *value = h->sigma2_fixed;
@@ -1199,7 +1208,7 @@ int rx_get_state(rx_handle *h, void *buf, size_t *len) {
         *len = lay.total;
         return fail(RX_EINVAL, "state needs %zu bytes", lay.total);
     }
-    const int S = h->streams, T = h->T, L = h->lag, W = h->W;
+    const int S = h->streams, T = tl(h), L = h->lag, W = h->W;   // T: taps per branch
     const long n = h->blocks_done, N = h->cur_n, K = n * h->block;
     unsigned char *out = static_cast<unsigned char *>(buf);
     std::memset(out, 0, lay.total);
@@ -1244,11 +1253,11 @@ int rx_set_state(rx_handle *h, const void *buf, size_t len) {
     std::memcpy(&hd, buf, sizeof hd);
     if (hd.magic != RX_STATE_MAGIC || hd.version != RX_STATE_VERSION)
         return fail(RX_EINVAL, "not a version-%u receiver state", RX_STATE_VERSION);
-    if (hd.streams != h->streams || hd.taps != h->T || hd.lag != h->lag || hd.bps_window != h->W ||
+    if (hd.streams != h->streams || hd.taps != tl(h) || hd.lag != h->lag || hd.bps_window != h->W ||
         hd.bps_phases != h->B || hd.m_bits != h->fmt.m || hd.block != h->block)
         return fail(RX_EINVAL, "state (S %d, T %d, lag %d, W %d, B %d, m %d, block %lld) does not match the "
                     "handle (S %d, T %d, lag %d, W %d, B %d, m %d, block %ld)", hd.streams, hd.taps, hd.lag,
-                    hd.bps_window, hd.bps_phases, hd.m_bits, (long long)hd.block, h->streams, h->T, h->lag,
+                    hd.bps_window, hd.bps_phases, hd.m_bits, (long long)hd.block, h->streams, tl(h), h->lag,
                     h->W, h->B, h->fmt.m, h->block);
     const long N = (long)hd.n_sym, n = (long)hd.blocks_done;
     const long nblk = N > 0 ? (N + h->block - 1) / h->block : 0;
@@ -1261,7 +1270,7 @@ int rx_set_state(rx_handle *h, const void *buf, size_t len) {
     if ((rc = upload_tables(h)) != RX_OK) return rc;
     if ((rc = ensure_buffers(h, N)) != RX_OK) return rc;
     if ((rc = ensure_streams(h)) != RX_OK) return rc;
-    const int S = h->streams, T = h->T, L = h->lag, W = h->W;
+    const int S = h->streams, T = tl(h), L = h->lag, W = h->W;   // T: taps per branch
     const long K = n * h->block;
     const unsigned char *in = static_cast<const unsigned char *>(buf);
     CK(cudaStreamSynchronize(h->st));
@@ -1312,7 +1321,7 @@ int rx_fir(rx_handle *h, const void *x, size_t n_samples, const void *taps, size
     if (!h || !x || !taps || !y) return fail(RX_EINVAL, "NULL argument");
     if (k1 < k0) return fail(RX_EINVAL, "k1 < k0");
     CK(launch_fir((const float2 *)x, (long)n_samples, (const float2 *)taps, (long)k0, (long)k1,
-                  (float2 *)y, (long)(k1 - k0), 0, h->streams, h->T, h->st));
+                  (float2 *)y, (long)(k1 - k0), 0, h->streams, h->T, h->st, SK_F32, 0, h->wl));
     return RX_OK;
 }
 
@@ -1330,12 +1339,12 @@ int rx_lms(rx_handle *h, const void *x, size_t n_samples, void *taps, size_t k0,
         for (int pass = 0; pass < passes; ++pass)
             CK(launch_lms_block((const float2 *)x, (long)n_samples, (const float2 *)taps, (float2 *)taps,
                                 (long)k0, (int)n_upd, pcode, N, mode, u0, (int)h->n_cma, (float)h->mu,
-                                h->lms_block, h->streams, h->T, h->fmt, h->st));
+                                h->lms_block, h->streams, h->T, h->fmt, h->st, SK_F32, h->wl));
         return RX_OK;
     }
     CK(launch_lms((const float2 *)x, (long)n_samples, (const float2 *)taps, (float2 *)taps, (long)k0,
                   (int)n_upd, pcode, N, mode, passes, u0, (int)h->n_cma, (float)h->mu, h->ref,
-                  h->ref_n, h->streams, h->T, h->fmt, h->st));
+                  h->ref_n, h->streams, h->T, h->fmt, h->st, SK_F32, h->wl));
     return RX_OK;
 }
 

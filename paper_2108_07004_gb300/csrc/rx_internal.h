@@ -143,22 +143,24 @@ cudaError_t launch_cdc(const float2 *in, void *out, long ns, int n_streams2, int
                        int n_ov, const float2 *H, const float2 *tw, cudaStream_t st,
                        long f0 = 0, long f1 = -1, int sk = SK_F32);
 
+// wl: widely-linear taps [S][2][2][2T] (T on x, then T on conj(x))
 cudaError_t launch_fir(const void *x, long ns, const float2 *taps, long k0, long k1,
                        void *y, long y_stride, long y_off, int n_streams, int T,
-                       cudaStream_t st, int sk = SK_F32, int sm_avail = 0);
+                       cudaStream_t st, int sk = SK_F32, int sm_avail = 0, int wl = 0);
 
 cudaError_t launch_lms(const void *x, long ns, const float2 *taps_in, float2 *taps_out,
                        long k0, int n_upd, const uint16_t *pcode, long pcode_stride,
                        int mode, int passes, unsigned long long u0, int n_cma, float mu,
                        const uint8_t *ref_lab, long ref_stride,
-                       int n_streams, int T, const FmtDev &f, cudaStream_t st, int sk = SK_F32);
+                       int n_streams, int T, const FmtDev &f, cudaStream_t st, int sk = SK_F32,
+                       int wl = 0);
 
 // Block LMS: groups of P (1..64) updates share the taps at the group start
 // (mode 0 CMA, 1 DD, 2 CMA below n_cma updates then DD).
 cudaError_t launch_lms_block(const void *x, long ns, const float2 *taps_in, float2 *taps_out, long k0,
                              int n_upd, const uint16_t *pcode, long pcode_stride, int mode,
                              unsigned long long u0, int n_cma, float mu, int P, int n_streams, int T,
-                             const FmtDev &f, cudaStream_t st, int sk = SK_F32);
+                             const FmtDev &f, cudaStream_t st, int sk = SK_F32, int wl = 0);
 
 // Training stage kernels on the equalised training span y [S][2][ystride]
 // (storage kind sk): data-aided phase codes, and the output order / phase

@@ -165,8 +165,15 @@ def make_stream(fmt: TxFormat | str, n_sym: int, *, seed: int, esn0_db: float,
                 rolloff: float = 0.1, symbol_rate: float = 28e9,
                 wavelength: float = LAMBDA_1550, rotation: bool = True,
                 noise: bool = True, pad_samples: int = 4096,
-                phase0: float | None = None) -> Stream:
-    """Generate one seeded stream of ``n_sym`` 4D symbols."""
+                phase0: float | None = None,
+                iq_imbalance: tuple[float, float] | None = None) -> Stream:
+    """Generate one seeded stream of ``n_sym`` 4D symbols.
+
+    ``iq_imbalance`` = (gain error eps, phase error phi in rad) of the
+    transmitter's IQ modulators: each polarisation's symbols become
+    alpha s + beta conj(s), alpha = (1 + (1 + eps) e^{-j phi}) / 2,
+    beta = (1 - (1 + eps) e^{j phi}) / 2 (before the real pulse shaping).
+    The reference symbols and bits stay the ideal ones."""
     if isinstance(fmt, str):
         fmt = tx_format(fmt)
     rng = np.random.Generator(np.random.PCG64(seed))
@@ -178,7 +185,13 @@ def make_stream(fmt: TxFormat | str, n_sym: int, *, seed: int, esn0_db: float,
     ns = sps * n_sym
     nfft = sfft.next_fast_len(ns + pad_samples)
     u = np.zeros((2, nfft), dtype=np.complex128)
-    u[:, 0:ns:sps] = sym
+    if iq_imbalance is not None:
+        eps, phi = iq_imbalance
+        alpha = (1 + (1 + eps) * np.exp(-1j * phi)) / 2
+        beta = (1 - (1 + eps) * np.exp(1j * phi)) / 2
+        u[:, 0:ns:sps] = alpha * sym + beta * np.conj(sym)
+    else:
+        u[:, 0:ns:sps] = sym
     f = sfft.fftfreq(nfft, d=1.0 / (sps * symbol_rate))
     g = np.sqrt(sps * raised_cosine_shape(f, symbol_rate, rolloff))
     h = g * cd_channel_response(f, cd_ps_per_nm, wavelength)
