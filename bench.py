@@ -86,6 +86,8 @@ def rx_params(wl: dict = WL):
     out = {k: wl[k] for k in keys}
     if wl.get("lms_block", 1) > 1:
         out["lms_block"] = wl["lms_block"]
+    if wl.get("widely_linear"):
+        out["widely_linear"] = 1
     return out
 
 
@@ -144,7 +146,8 @@ def oracle_params(wl: dict, **over):
               bps_phases=wl["bps_phases"], bps_window=wl["bps_window"], block=wl["block"],
               n_upd=wl["n_upd"], lag=wl["lag"], mu=wl["mu"], n_pre=wl["n_pre"], cma_passes=wl["cma_passes"],
               n_cma=wl["n_cma"], n_train=wl["n_train"], train_passes=wl["train_passes"],
-              skip_head=wl["skip_head"], skip_tail=wl["skip_tail"], lms_block=wl.get("lms_block", 1))
+              skip_head=wl["skip_head"], skip_tail=wl["skip_tail"], lms_block=wl.get("lms_block", 1),
+              widely_linear=bool(wl.get("widely_linear", 0)))
     kw.update(over)
     return chain.RxParams(**kw)
 
@@ -154,7 +157,8 @@ def cpu_baseline(n_sym: int, wl: dict = WL, esn0_db: float = 12.0, seed: int | N
     symbols; returns (Gbit/s, seconds, stream, oracle result)."""
     from oracle import chain, oracle_format
     st = synth.make_stream(wl["fmt"], n_sym, seed=seed if seed is not None else synth.stream_seed(2, 4),
-                           esn0_db=esn0_db, cd_ps_per_nm=wl["cd_ps_per_nm"], linewidth_ts=wl["linewidth_ts"])
+                           esn0_db=esn0_db, cd_ps_per_nm=wl["cd_ps_per_nm"], linewidth_ts=wl["linewidth_ts"],
+                           iq_imbalance=wl.get("iq"))
     fmt = oracle_format(wl["fmt"])
     t0 = time.perf_counter()
     res = chain.run_chain(st.rx, fmt, oracle_params(wl), ref_bits=st.bits)
@@ -451,6 +455,74 @@ def run_block_lms(args):
     print(json.dumps(line), flush=True)
 
 
+# ---- widely-linear butterfly (next row F3): DP-16QAM with a transmitter IQ imbalance ----
+# no carrier phase noise: the regime of the paper's widely-linear equaliser (its KK receiver
+# has none); with phase noise the conjugate term turns against the carrier before the phase
+# search and a butterfly in front of it cannot hold its conjugate taps
+WLIN = dict(workload="dp_16qam_80km_18dB_iq15pct_no_phase_noise", fmt="dp_16qam", n_sym=1 << 20, streams=9,
+            esn0_db=18.0, cd_ps_per_nm=1360.0, linewidth_ts=0.0, iq=(0.15, 0.12), fft=1024, overlap=256,
+            taps=15, bps_phases=32, bps_window=64, block=1 << 16, n_upd=1024, lag=2, mu=1e-3, n_pre=4096,
+            cma_passes=1, n_cma=0, n_train=1024, train_passes=3, skip_head=65536, skip_tail=512)
+
+
+def run_widely_linear(args):
+    """Nine DP-16QAM streams with a transmitter IQ imbalance (15 %, 0.12 rad):
+    the linear butterfly, the widely-linear one, and the linear one on the
+    same streams without the imbalance; Gbit/s and bit errors of each."""
+    import torch
+    from paper_2108_07004_gb300 import rx as rx_mod
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    wl0 = WLIN
+    S = wl0["streams"]
+    n = args.n_sym if args.n_sym != WL["n_sym"] else wl0["n_sym"]
+    m = 8
+    forms = {}
+    for name, iq, wlin in (("linear", wl0["iq"], 0), ("widely_linear", wl0["iq"], 1), ("linear_no_iq", None, 0)):
+        rxs, bits = [], []
+        for p_ in range(S):
+            st = synth.make_stream(wl0["fmt"], n, seed=synth.stream_seed(14, p_), esn0_db=wl0["esn0_db"],
+                                   cd_ps_per_nm=wl0["cd_ps_per_nm"], linewidth_ts=wl0["linewidth_ts"],
+                                   iq_imbalance=iq)
+            rxs.append(st.rx)
+            bits.append(st.bits)
+        samples = torch.from_numpy(np.stack(rxs)).cuda()
+        bits_d = torch.from_numpy(np.stack(bits)).cuda()
+        del rxs
+        wcfg = dict(wl0, widely_linear=wlin)
+        r = rx_mod.Receiver(wl0["fmt"], cd_ps_per_nm=wl0["cd_ps_per_nm"], taps=wl0["taps"],
+                            bps_phases=wl0["bps_phases"], streams=S, **rx_params(wcfg))
+        r.set_reference(bits_d)
+        llr = torch.empty((S, n, m), dtype=torch.float32, device="cuda")
+        ms, stg, st_ = timed_steps(r, samples, llr, args.steps, args.warmup)
+        forms[name] = {"gbps": S * n * m / (ms * 1e-3) / 1e9, "ms_per_step": ms, "stages_ms": stg,
+                       "bit_errors": int(sum(x["bit_errors"] for x in st_)),
+                       "n_bits": int(sum(x["n_bits"] for x in st_)),
+                       "ber": sum(x["bit_errors"] for x in st_) / max(1, sum(x["n_bits"] for x in st_))}
+        r.close()
+        del samples, bits_d, llr
+    head = forms["widely_linear"]
+    line = {
+        "metric": METRIC, "value": head["gbps"], "unit": "Gbit/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": head["ms_per_step"],
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": wl0["workload"], "streams": S, "symbols_per_stream": n, "format": wl0["fmt"],
+                   "fft": wl0["fft"], "overlap": wl0["overlap"], "taps": wl0["taps"],
+                   "bps_phases": wl0["bps_phases"], "block": wl0["block"], "lag": wl0["lag"],
+                   "iq_imbalance": list(wl0["iq"]), "widely_linear": 1},
+        "forms": forms,
+    }
+    if not args.no_cpu_baseline:
+        wcfg = dict(wl0, widely_linear=1)
+        v, dt, st_o, res_o = cpu_baseline(1 << 16, wcfg, wl0["esn0_db"], synth.stream_seed(14, 99))
+        line["cpu_baseline"] = {"value": v, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one stream of 65536 16QAM symbols with the IQ imbalance, widely "
+                                          f"linear, {dt:.1f} s"}
+        if not args.no_parity:
+            line["parity"] = parity_on(rx_mod, torch, st_o, res_o, wcfg)
+    print(json.dumps(line), flush=True)
+
+
 def run_precision(args):
     import torch
     from paper_2108_07004_gb300 import rx as rx_mod
@@ -712,7 +784,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision", "serving", "block_lms"],
+    ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision", "serving", "block_lms", "widely_linear"],
                     help="learned: train the MLP demapper on chain output, compare with the exact one; "
                          "precision: DP-QPSK chain with CDC/FIR data in float32, half and bfloat16; "
                          "serving: 64 mixed streams with Poisson arrivals through the continuous-batching server")
@@ -722,6 +794,8 @@ def main():
         run_reference(args)
     elif args.variant == "learned":
         run_learned(args)
+    elif args.variant == "widely_linear":
+        run_widely_linear(args)
     elif args.variant == "block_lms":
         run_block_lms(args)
     elif args.variant == "precision":
