@@ -72,6 +72,7 @@ struct rx_handle {
     int cma_passes = 1;
     long n_cma = 0;
     int lms_block = 1;       // block-wise updates in groups of this many (1: sequential)
+    double sig_fixed_up = 0; // fixed sigma^2 value on the device (0: none yet)
     int wl = 0;              // widely-linear butterfly: taps [S][2][2][2T] (x, then conj x)
     long n_train = 1024;
     int train_passes = 3;
@@ -96,6 +97,10 @@ struct rx_handle {
     // host-buffer entry: input and output copies on their own streams
     cudaStream_t cp_in = nullptr, cp_out = nullptr;
     cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    // the input of the first group beyond the start-up's frames (the main
+    // stream waits for it before the CDC of the remaining frames)
+    cudaEvent_t ev_in_rest = nullptr;
+    bool wait_rest = false;
     std::vector<cudaEvent_t> ev_lms;
     // device tables
     float2 *H = nullptr, *tw = nullptr;
@@ -369,6 +374,7 @@ int ensure_buffers(rx_handle *h, long N) {
     CK(cudaMalloc(&h->part_d, sizeof(double) * 5 * (size_t)S * ncta_d));
     CK(cudaMalloc(&h->sig, sizeof(double) * S));
     CK(cudaMalloc(&h->sig_fixed, sizeof(double) * S));
+    h->sig_fixed_up = 0;
     CK(cudaMalloc(&h->sd, sizeof(StreamDev) * S));
     CK(cudaMemset(h->sd, 0, sizeof(StreamDev) * S));
     h->cap_dsum = ncta;
@@ -558,6 +564,10 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
             CK(cudaEventRecord(h->ev_cdc0, st));
             CK(cudaStreamWaitEvent(h->side, h->ev_cdc0, 0));
         }
+        if (h->wait_rest) {
+            CK(cudaStreamWaitEvent(st, h->ev_in_rest, 0));
+            h->wait_rest = false;
+        }
         if (f1 > fs)
             STAGE(ST_CDC, st, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st, fs, f1,
                                             h->prec));
@@ -595,9 +605,11 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     // grids of the main stream leave room for the side-stream LMS (one SM
     // per stream) when it runs beside them
     const int avail = (L >= 2 && h->lms_block == 1) ? std::max(sm_count() / 2, sm_count() - S) : sm_count();
-    if (h->sigma2_fixed > 0) {
+    if (h->sigma2_fixed > 0 && h->sig_fixed_up != h->sigma2_fixed) {
+        // uploaded when it changes (demaps of an earlier call may still read it)
         h->h_sig.assign(S, h->sigma2_fixed);
         CK(cudaMemcpyAsync(h->sig_fixed, h->h_sig.data(), sizeof(double) * S, cudaMemcpyHostToDevice, st));
+        h->sig_fixed_up = h->sigma2_fixed;
     }
     const int m = f.m;
     const long sd_stride = sizeof(StreamDev) / sizeof(int32_t);
@@ -640,7 +652,9 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         int *dsum_n = h->dsum + (size_t)par * S * h->cap_dsum;
         double *mdsum_n = h->mdsum + (size_t)par * S * h->cap_dsum;
         // the partial sums of this parity were read by the demap of block n - 2
-        if (n - 2 >= b0) CK(cudaStreamWaitEvent(st, h->ev_dm[par], 0));
+        // (possibly of an earlier call: the demap stream is not joined between
+        // the host entry's groups)
+        if (n >= 2) CK(cudaStreamWaitEvent(st, h->ev_dm[par], 0));
         STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, dsum_n, mdsum_n, chunks, S,
                                         f, st, h->prec));
         CK(cudaEventRecord(h->ev_bps[par], st));
@@ -697,7 +711,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         h->blocks_done = n + 1;
     }
     // the caller's stream sees the demaps (LLRs, counters, carries) done
-    if (b1 > b0) CK(cudaStreamWaitEvent(st, h->ev_dm[(int)((b1 - 1) & 1)], 0));
+    if (join && b1 > b0) CK(cudaStreamWaitEvent(st, h->ev_dm[(int)((b1 - 1) & 1)], 0));
     if (join && L >= 2 && b1 > b0) CK(cudaStreamWaitEvent(st, h->ev_lms[(b1 - 1) % (L + 1)], 0));
     return RX_OK;
 }
@@ -865,6 +879,7 @@ void rx_destroy(rx_handle *h) {
     if (h->cp_out) { cudaStreamSynchronize(h->cp_out); cudaStreamDestroy(h->cp_out); }
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
+    if (h->ev_in_rest) cudaEventDestroy(h->ev_in_rest);
     if (h->ev_unwrap) cudaEventDestroy(h->ev_unwrap);
     if (h->ev_cdc0) cudaEventDestroy(h->ev_cdc0);
     if (h->ev_start) cudaEventDestroy(h->ev_start);
@@ -1092,6 +1107,7 @@ int rx_process_host(rx_handle *h, const void *samples, size_t n_samples, float *
         CK(cudaStreamCreateWithFlags(&h->cp_out, cudaStreamNonBlocking));
         CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&h->ev_in_rest, cudaEventDisableTiming));
     }
     // the previous call's output copies and this call's device buffers
     CK(cudaEventRecord(h->ev_out, h->st));
@@ -1112,18 +1128,34 @@ int rx_process_host(rx_handle *h, const void *samples, size_t n_samples, float *
         const long g1 = std::min(nblk, g0 + G);
         const CdcFrames cf = cdc_frames(h, N, g0, g1);
         const long hi = std::min(ns, (cf.f1 - 1) * Sk - half + h->n_fft);
+        if (g0 == 0 && cf.fs > cf.f0) {
+            // the start-up's frames first: the start-up runs while the rest
+            // of the first group comes in
+            const long hs = std::min(hi, (cf.fs - 1) * Sk - half + h->n_fft);
+            CK(cudaMemcpy2DAsync(h->d_in, pin, src, pin, sizeof(float2) * (size_t)hs, (size_t)(2 * S),
+                                 cudaMemcpyHostToDevice, h->cp_in));
+            CK(cudaEventRecord(h->ev_in, h->cp_in));
+            copied = hs;
+        }
         if (hi > copied) {
             CK(cudaMemcpy2DAsync(h->d_in + copied, pin, src + copied, pin, sizeof(float2) * (size_t)(hi - copied),
                                  (size_t)(2 * S), cudaMemcpyHostToDevice, h->cp_in));
             copied = hi;
         }
-        CK(cudaEventRecord(h->ev_in, h->cp_in));
+        if (g0 == 0 && cf.fs > cf.f0) {
+            CK(cudaEventRecord(h->ev_in_rest, h->cp_in));
+            h->wait_rest = true;
+        } else {
+            CK(cudaEventRecord(h->ev_in, h->cp_in));
+        }
         CK(cudaStreamWaitEvent(h->st, h->ev_in, 0));
         const int rc = run_blocks(h, h->d_in, N, g0, g1, h->d_out, g0 == 0, g1 == nblk);
+        h->wait_rest = false;
         if (rc != RX_OK) return rc;
         // block n writes rows [k0 - W/2, k1 - W/2) (the last block up to N)
         const long e = (g1 == nblk) ? N : std::min(N, g1 * Nb) - h->W / 2;
-        CK(cudaEventRecord(h->ev_out, h->st));
+        // the group's LLR rows are final when its last demap is (demap stream)
+        CK(cudaEventRecord(h->ev_out, h->dst));
         CK(cudaStreamWaitEvent(h->cp_out, h->ev_out, 0));
         if (e > out_done) {
             CK(cudaMemcpy2DAsync(llr_out + out_done * m, pout, h->d_out + out_done * m, pout,
