@@ -137,6 +137,16 @@ int rx_set_stream(rx_handle *h, void *cuda_stream);
  * over the first n_train symbols and BER/GMI counting.  Copied. */
 int rx_set_reference(rx_handle *h, const uint8_t *bits, size_t n_sym);
 
+/* rx_set_reference with the bits left in host memory ([S][n_sym][m] uint8,
+ * as above): the next rx_process_host copies them in group by group beside
+ * the samples (rows a group's blocks count with, and for the first group
+ * the training span), so that the copy overlaps the chain.  Any other entry
+ * point that needs the reference first copies it whole on the handle's
+ * stream.  `bits` must stay valid and unchanged until that call returns;
+ * pinned memory keeps the copies asynchronous.  Device memory for the bits
+ * (S * n_sym * m bytes) and the labels is kept by the handle. */
+int rx_set_reference_host(rx_handle *h, const uint8_t *bits, size_t n_sym);
+
 /* Forget the stream state (taps, phase, counters): the next rx_process
  * starts a new stream. */
 int rx_reset(rx_handle *h);

@@ -723,11 +723,12 @@ train_phase_kernel(const void *__restrict__ y, long ystride, const uint8_t *__re
     }
 }
 
+// labels of rows i0 .. i1 - 1 of bits [S][n][m] into lab [S][n]
 __global__ void ref_labels_kernel(const uint8_t *__restrict__ bits, uint8_t *__restrict__ lab,
-                                  long n, int m) {
-    const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+                                  long n, long i0, long i1, int m) {
+    const long i = i0 + (long)blockIdx.x * blockDim.x + threadIdx.x;
     const int s = blockIdx.y;
-    if (i >= n) return;
+    if (i >= i1) return;
     const uint8_t *b = bits + ((long)s * n + i) * m;
     int v = 0;
     for (int c = 0; c < m; ++c) v = (v << 1) | (b[c] & 1);
@@ -883,8 +884,13 @@ cudaError_t launch_ref_labels(const uint8_t *bits, uint8_t *lab, long n_sym, int
                               int dims, int m_pol, cudaStream_t st) {
     (void)dims;
     (void)m_pol;
-    if (n_sym <= 0 || n_streams <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((n_sym + 255) / 256), (unsigned)n_streams);
-    ref_labels_kernel<<<grid, 256, 0, st>>>(bits, lab, n_sym, m);
+    return launch_ref_labels_rows(bits, lab, n_sym, 0, n_sym, n_streams, m, st);
+}
+
+cudaError_t launch_ref_labels_rows(const uint8_t *bits, uint8_t *lab, long n_sym, long i0, long i1,
+                                   int n_streams, int m, cudaStream_t st) {
+    if (i1 <= i0 || n_streams <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((i1 - i0 + 255) / 256), (unsigned)n_streams);
+    ref_labels_kernel<<<grid, 256, 0, st>>>(bits, lab, n_sym, i0, i1, m);
     return cudaGetLastError();
 }

@@ -101,6 +101,11 @@ struct rx_handle {
     // stream waits for it before the CDC of the remaining frames)
     cudaEvent_t ev_in_rest = nullptr;
     bool wait_rest = false;
+    // reference bits left in host memory (rx_set_reference_host): copied in
+    // with the next host-entry call, group by group, into ref_bits
+    const uint8_t *ref_host = nullptr;
+    uint8_t *ref_bits = nullptr;
+    size_t ref_bits_cap = 0;
     std::vector<cudaEvent_t> ev_lms;
     // device tables
     float2 *H = nullptr, *tw = nullptr;
@@ -479,6 +484,18 @@ void prof_end(rx_handle *h, int stage, cudaEvent_t a, cudaStream_t s, int launch
         prof_end(h, stage, ev_a_, stream, nl);         \
     } while (0)
 
+// A host reference that no host-entry call has taken in yet: copied and
+// labelled whole on the main stream before a device entry point uses it.
+int flush_ref(rx_handle *h) {
+    if (!h->ref_host) return RX_OK;
+    const uint8_t *rh = h->ref_host;
+    h->ref_host = nullptr;
+    const size_t nb = (size_t)h->ref_s * h->ref_n * h->fmt.m;
+    CK(cudaMemcpyAsync(h->ref_bits, rh, nb, cudaMemcpyHostToDevice, h->st));
+    CK(launch_ref_labels_rows(h->ref_bits, h->ref, h->ref_n, 0, h->ref_n, h->ref_s, h->fmt.m, h->st));
+    return RX_OK;
+}
+
 // Training stage (Sec. 2: the equaliser converges on a known sequence before
 // it runs blind): output order and phases from the correlation with the
 // known symbols, data-aided phase codes over the span, then train_passes
@@ -539,6 +556,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     const size_t tapsz = sizeof(float2) * (size_t)S * 4 * tl(h);
     cudaStream_t st = h->st;
     int rc;
+    if ((rc = flush_ref(h)) != RX_OK) return rc;
     if ((rc = upload_tables(h)) != RX_OK) return rc;
     if ((rc = ensure_buffers(h, N)) != RX_OK) return rc;
     if ((rc = ensure_streams(h)) != RX_OK) return rc;
@@ -900,6 +918,7 @@ void rx_destroy(rx_handle *h) {
     cudaFree(h->d_in);
     cudaFree(h->d_out);
     cudaFree(h->ytr);
+    cudaFree(h->ref_bits);
     if (h->h_in) cudaFreeHost(h->h_in);
     if (h->h_out) cudaFreeHost(h->h_out);
     delete h;
@@ -1060,12 +1079,33 @@ int rx_set_reference(rx_handle *h, const uint8_t *bits, size_t n_sym) {
     if (h->ref && (h->ref_n != (long)n_sym || h->ref_s != S)) { cudaFree(h->ref); h->ref = nullptr; }
     h->ref_n = (long)n_sym;
     h->ref_s = S;
+    h->ref_host = nullptr;
     if (!n_sym) return RX_OK;
     if (!h->ref) CK(cudaMalloc(&h->ref, (size_t)S * n_sym));
     CK(launch_ref_labels(bits, h->ref, (long)n_sym, S, h->fmt.m, h->fmt.dims, h->fmt.m_pol, h->st));
     h->started = false;
     return RX_OK;
 }
+
+int rx_set_reference_host(rx_handle *h, const uint8_t *bits, size_t n_sym) {
+    if (!h || !bits || !n_sym) return fail(RX_EINVAL, "NULL argument");
+    const int S = h->streams;
+    if (h->ref && (h->ref_n != (long)n_sym || h->ref_s != S)) { cudaFree(h->ref); h->ref = nullptr; }
+    h->ref_n = (long)n_sym;
+    h->ref_s = S;
+    if (!h->ref) CK(cudaMalloc(&h->ref, (size_t)S * n_sym));
+    const size_t need = (size_t)S * n_sym * h->fmt.m;
+    if (h->ref_bits_cap < need) {
+        cudaFree(h->ref_bits);
+        h->ref_bits = nullptr;
+        CK(cudaMalloc(&h->ref_bits, need));
+        h->ref_bits_cap = need;
+    }
+    h->ref_host = bits;
+    h->started = false;
+    return RX_OK;
+}
+
 
 int rx_reset(rx_handle *h) {
     if (!h) return fail(RX_EINVAL, "NULL handle");
@@ -1123,7 +1163,23 @@ int rx_process_host(rx_handle *h, const void *samples, size_t n_samples, float *
     const size_t pin = sizeof(float2) * (size_t)ns, pout = sizeof(float) * (size_t)N * m;
     long copied = 0;                          // samples [0, copied) of every row are on the device
     long out_done = 0;                        // LLR rows [0, out_done) copied out
+    long ref_done = 0;                        // reference rows [0, ref_done) copied in and labelled
+    const uint8_t *rh = h->ref_host;
+    h->ref_host = nullptr;                    // this call takes the reference in
+    const size_t pref = (size_t)h->ref_n * m;
     const float2 *src = static_cast<const float2 *>(samples);
+    // reference rows [ref_done, r_hi): bits in, then their labels, both on
+    // the input copy stream so that the events below cover them
+    auto ref_rows = [&](long r_hi) -> int {
+        r_hi = std::min(r_hi, h->ref_n);
+        if (!rh || r_hi <= ref_done) return RX_OK;
+        CK(cudaMemcpy2DAsync(h->ref_bits + ref_done * m, pref, rh + ref_done * m, pref,
+                             (size_t)((r_hi - ref_done) * m), (size_t)S, cudaMemcpyHostToDevice, h->cp_in));
+        CK(launch_ref_labels_rows(h->ref_bits, h->ref, h->ref_n, ref_done, r_hi, S, m, h->cp_in));
+        ref_done = r_hi;
+        return RX_OK;
+    };
+    int rc;
     for (long g0 = 0; g0 < nblk; g0 += G) {
         const long g1 = std::min(nblk, g0 + G);
         const CdcFrames cf = cdc_frames(h, N, g0, g1);
@@ -1134,6 +1190,7 @@ int rx_process_host(rx_handle *h, const void *samples, size_t n_samples, float *
             const long hs = std::min(hi, (cf.fs - 1) * Sk - half + h->n_fft);
             CK(cudaMemcpy2DAsync(h->d_in, pin, src, pin, sizeof(float2) * (size_t)hs, (size_t)(2 * S),
                                  cudaMemcpyHostToDevice, h->cp_in));
+            if ((rc = ref_rows(std::min(N, h->n_train))) != RX_OK) return rc;
             CK(cudaEventRecord(h->ev_in, h->cp_in));
             copied = hs;
         }
@@ -1142,6 +1199,8 @@ int rx_process_host(rx_handle *h, const void *samples, size_t n_samples, float *
                                  (size_t)(2 * S), cudaMemcpyHostToDevice, h->cp_in));
             copied = hi;
         }
+        // reference rows the group's blocks (and the training span) count with
+        if ((rc = ref_rows(std::min(N, std::max(g1 * Nb, g0 == 0 ? h->n_train : 0L)))) != RX_OK) return rc;
         if (g0 == 0 && cf.fs > cf.f0) {
             CK(cudaEventRecord(h->ev_in_rest, h->cp_in));
             h->wait_rest = true;
@@ -1149,7 +1208,7 @@ int rx_process_host(rx_handle *h, const void *samples, size_t n_samples, float *
             CK(cudaEventRecord(h->ev_in, h->cp_in));
         }
         CK(cudaStreamWaitEvent(h->st, h->ev_in, 0));
-        const int rc = run_blocks(h, h->d_in, N, g0, g1, h->d_out, g0 == 0, g1 == nblk);
+        rc = run_blocks(h, h->d_in, N, g0, g1, h->d_out, g0 == 0, g1 == nblk);
         h->wait_rest = false;
         if (rc != RX_OK) return rc;
         // block n writes rows [k0 - W/2, k1 - W/2) (the last block up to N)
@@ -1362,6 +1421,7 @@ int rx_lms(rx_handle *h, const void *x, size_t n_samples, void *taps, size_t k0,
     if (!h || !x || !taps) return fail(RX_EINVAL, "NULL argument");
     if (mode < 0 || mode > 3) return fail(RX_EINVAL, "mode must be 0, 1, 2 or 3");
     if (mode != 0 && !pcode) return fail(RX_EINVAL, "DD mode needs phase codes");
+    if (mode == 3 && flush_ref(h) != RX_OK) return RX_ECUDA;
     if (mode == 3 && (!h->ref || h->ref_n < (long)(k0 + n_upd)))
         return fail(RX_ESTATE, "data-aided mode needs a reference covering the span");
     const long N = (long)n_samples / 2;
@@ -1385,6 +1445,7 @@ int rx_train(rx_handle *h, const void *x, size_t n_samples, void *taps, uint16_t
     const long N = (long)n_samples / 2;
     const long ntr = std::min(h->n_train, N);
     if (!h->ref || h->ref_n < ntr) return fail(RX_ESTATE, "training needs a reference (rx_set_reference)");
+    if (flush_ref(h) != RX_OK) return RX_ECUDA;
     return train_stage(h, x, (long)n_samples, (float2 *)taps, ntr, pcode, ntr, nullptr, 0, h->st, SK_F32);
 }
 

@@ -276,3 +276,6 @@ cudaError_t launch_demap(const float2 *z, long z_stride, long z_off, long a, lon
 
 cudaError_t launch_ref_labels(const uint8_t *bits, uint8_t *lab, long n_sym, int n_streams,
                               int m, int dims, int m_pol, cudaStream_t st);
+// rows i0 .. i1 - 1 only (bits [S][n_sym][m], labels [S][n_sym])
+cudaError_t launch_ref_labels_rows(const uint8_t *bits, uint8_t *lab, long n_sym, long i0, long i1,
+                                   int n_streams, int m, cudaStream_t st);

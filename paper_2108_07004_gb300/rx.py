@@ -58,6 +58,7 @@ _PROTOS = {
     "rx_get_param": (_I, [_VP, C.c_char_p, C.POINTER(_D)]),
     "rx_set_stream": (_I, [_VP, _VP]),
     "rx_set_reference": (_I, [_VP, _VP, _SZ]),
+    "rx_set_reference_host": (_I, [_VP, _VP, _SZ]),
     "rx_reset": (_I, [_VP]),
     "rx_process": (_I, [_VP, _VP, _SZ, _VP, _VP]),
     "rx_process_host": (_I, [_VP, _VP, _SZ, _VP, _VP]),
@@ -255,6 +256,15 @@ class Receiver:
     def set_reference(self, bits: torch.Tensor):
         """bits: [S, N, m] uint8 on the device."""
         _ck(lib().rx_set_reference(self.h, _ptr(bits), bits.shape[1]))
+
+    def set_reference_host(self, bits: torch.Tensor):
+        """bits: [S, N, m] uint8 in host memory (pinned for asynchronous
+        copies), taken in by the next process_host; the tensor must stay
+        alive and unchanged until then."""
+        if bits.is_cuda or not bits.is_contiguous() or bits.dtype != torch.uint8:
+            raise ValueError("bits must be a contiguous uint8 host tensor")
+        self._ref_host = bits
+        _ck(lib().rx_set_reference_host(self.h, _ptr(bits), bits.shape[1]))
 
     def reset(self):
         _ck(lib().rx_reset(self.h))
