@@ -16,8 +16,12 @@ Parity status: every function here is pinned by a ``-m "not gpu"`` test in
 fact or brute force, except ``gs4d64`` table design (the authors' own
 constellation is not printed: parity with it is unpinned).  ``mlp`` is the
 learned demapper (forward, BCE, backward, Adam), pinned by identities,
-finite differences and closed forms.
+finite differences and closed forms.  ``kk`` is the Kramers-Kronig
+front-end (intensity -> field by the frequency-domain Hilbert transform),
+pinned by the library's analytic-signal routine, exact minimum-phase tones
+and the KK reconstruction error against CSPR.
 """
 from .formats import OracleFormat, oracle_format  # noqa: F401
 from . import chain  # noqa: F401
 from . import mlp  # noqa: F401
+from . import kk  # noqa: F401

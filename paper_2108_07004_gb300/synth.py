@@ -233,3 +233,81 @@ def mlp_init_params(seed: int) -> np.ndarray:
         parts.append(rng.uniform(-lim, lim, size=(n_out, n_in)).astype(np.float32).ravel())
         parts.append(np.zeros(n_out, np.float32))
     return np.concatenate(parts)
+
+
+# ---- Kramers-Kronig (single-polarisation, carrier-assisted) signals --------
+
+@dataclass
+class KKStream:
+    codes: np.ndarray      # [sps*N] int16 ADC codes of the AC-coupled photocurrent
+    intensity: np.ndarray  # [sps*N] float64 photocurrent before AC coupling
+    scale: float           # photocurrent per ADC code
+    dc: float              # mean photocurrent (the term the AC coupling removed)
+    fc_step: int           # carrier offset from the signal centre, cycles/sample * 2^32
+    carrier: float         # carrier amplitude A
+    field: np.ndarray      # [sps*N] complex128 noiseless signal s at baseband
+    sym: np.ndarray        # [N] complex128 transmitted symbols
+    bits: np.ndarray       # [N, m_pol] uint8
+    n0: float
+    sps: int
+
+
+def kk_phase(fc_step: int, n: np.ndarray) -> np.ndarray:
+    """exp(j 2 pi (fc_step * n mod 2^32) / 2^32): the carrier offset as a
+    32-bit phase increment per sample."""
+    u = (np.asarray(n, dtype=np.uint64) * np.uint64(fc_step)) & np.uint64(0xFFFFFFFF)
+    return np.exp(2j * np.pi * (u.astype(np.float64) / 2.0 ** 32))
+
+
+def make_kk_stream(fmt: TxFormat | str, n_sym: int, *, seed: int, cspr_db: float,
+                   esn0_db: float, sps: int = 4, rolloff: float = 0.01, gap: float = 0.011,
+                   adc_bits: int = 12, noise: bool = True, pad_samples: int = 4096) -> KKStream:
+    """One seeded single-polarisation signal for Kramers-Kronig detection.
+
+    The transmitter places the RRC-shaped signal s (unit-energy symbols,
+    ``sps`` samples per symbol) below a real carrier A: the optical field is
+    E = A + s * exp(-j 2 pi fc n) with fc = ((1 + rolloff)/2 + gap)/sps
+    cycles per sample (held as a 32-bit phase increment), so that the
+    carrier sits ``gap`` symbol rates above the signal's upper band edge
+    (Sec. 3: 1 GBd, roll-off 0.01, carrier 11 MHz above the band).
+    CSPR = A^2 / mean|s|^2.  Complex AWGN of variance N0 per sample
+    (N0 = 10^(-EsN0/10), the matched-filter convention of ``make_stream``)
+    is added to the field, a photodiode detects I = |E + n|^2, the AC
+    coupling removes its mean and an ADC of ``adc_bits`` bits samples it
+    with a full scale of 1.1 max|I - mean I|.  For 2D formats only (the
+    symbols of the first polarisation of the 2D table)."""
+    if isinstance(fmt, str):
+        fmt = tx_format(fmt)
+    if fmt.dims != 2:
+        raise ValueError("KK signals use a 2D format")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    m_pol = fmt.bits_per_4d // 2
+    bits = rng.integers(0, 2, size=(n_sym, m_pol), dtype=np.uint8)
+    w = (1 << np.arange(m_pol - 1, -1, -1)).astype(np.int64)
+    sym = fmt.points[bits.astype(np.int64) @ w]
+
+    ns = sps * n_sym
+    nfft = sfft.next_fast_len(ns + pad_samples)
+    u = np.zeros(nfft, dtype=np.complex128)
+    u[0:ns:sps] = sym
+    f = sfft.fftfreq(nfft, d=1.0 / sps)                 # in symbol rates
+    g = np.sqrt(sps * raised_cosine_shape(f, 1.0, rolloff))
+    s = sfft.ifft(sfft.fft(u) * g)[:ns]
+
+    fc = ((1 + rolloff) / 2 + gap) / sps
+    fc_step = int(round(fc * 2.0 ** 32))
+    p_s = 1.0 / sps                                     # mean |s|^2 per sample
+    A = float(np.sqrt(10.0 ** (cspr_db / 10.0) * p_s))
+    n_idx = np.arange(ns)
+    E = A + s * np.conj(kk_phase(fc_step, n_idx))
+    n0 = 10.0 ** (-esn0_db / 10.0)
+    if noise:
+        wn = rng.standard_normal((2, ns))
+        E = E + np.sqrt(n0 / 2) * (wn[0] + 1j * wn[1])
+    I = np.abs(E) ** 2
+    dc = float(np.mean(I))
+    ac = I - dc
+    full = (1 << (adc_bits - 1)) - 1
+    scale = float(1.1 * np.max(np.abs(ac)) / full)
+    codes = np.clip(np.round(ac / scale), -full - 1, full).astype(np.int16)
+    return KKStream(codes, I, scale, dc, fc_step, A, s, sym, bits, n0, sps)
