@@ -521,6 +521,95 @@ def run_widely_linear(args):
     print(json.dumps(line), flush=True)
 
 
+# ---- Kramers-Kronig front-end (Sec. 2): 32 streams of 2^22 ADC samples ----
+KKW = dict(workload="kk_frontend_32x2p22", streams=32, n=1 << 22, distinct=4, fmt="dp_16qam", cspr_db=12.0,
+           esn0_db=20.0, n_ov=512, floor=1e-3)
+
+
+def run_kk(args):
+    """KK front-end alone: int16 ADC codes at 4 samples per symbol -> the
+    downconverted field (complex64), one launch per step over 32 streams of
+    2^22 samples (the paper's buffer size); GSa/s of field out."""
+    import torch
+    from paper_2108_07004_gb300 import rx as rx_mod
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    w = KKW
+    S, n = w["streams"], w["n"]
+    ks = [synth.make_kk_stream(w["fmt"], n // 4, seed=synth.stream_seed(15, p_), cspr_db=w["cspr_db"],
+                               esn0_db=w["esn0_db"]) for p_ in range(w["distinct"])]
+    codes_h = np.stack([ks[p_ % w["distinct"]].codes for p_ in range(S)])
+    levels = np.array([[ks[p_ % w["distinct"]].scale, ks[p_ % w["distinct"]].dc] for p_ in range(S)],
+                      dtype=np.float32)
+    codes = torch.from_numpy(codes_h).cuda()
+    out = torch.empty((S, n), dtype=torch.complex64, device="cuda")
+    k = rx_mod.KK(ks[0].fc_step, n_ov=w["n_ov"], floor=w["floor"])
+    for _ in range(max(3, args.warmup)):
+        k.field(codes, levels, out)
+    torch.cuda.synchronize()
+    clk = Clocks(torch.cuda.current_device())
+    clk.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        k.field(codes, levels, out)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = clk.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    value = S * n / (ms * 1e-3) / 1e9
+    pk, pk_kind = peaks()
+    hbm = pk.get("hbm_gbs", 6800.0)
+    alg = S * n * (2 + 8)                       # int16 in, complex64 out
+    line = {
+        "metric": "KK front-end field samples out per second", "value": value, "unit": "GSa/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w["workload"], "streams": S, "samples_per_stream": n, "sps": 4, "fft": 1024,
+                   "overlap": w["n_ov"], "format": w["fmt"], "cspr_db": w["cspr_db"],
+                   "l2": "inputs 256 MiB and outputs 1 GiB > L2, no flush"},
+        "realtime_1gbd_channels": value / 4.0,
+        "roofline": {"bound": "hbm", "kernel": "kk1024", "achieved": alg / (ms * 1e-3) / 1e9, "peak": hbm,
+                     "unit": "GB/s", "frac": alg / (ms * 1e-3) / 1e9 / hbm, "traffic": None,
+                     "peak_kind": pk_kind, "bytes_per_sample": 10},
+        "gpu_launches": args.steps, "clocks": clocks,
+    }
+    # end to end: pinned host codes in, field out, every step
+    if not args.no_e2e:
+        c_h = torch.from_numpy(codes_h).pin_memory()
+        o_h = torch.empty((S, n), dtype=torch.complex64).pin_memory()
+        for _ in range(2):
+            codes.copy_(c_h, non_blocking=True)
+            k.field(codes, levels, out)
+            o_h.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ke = max(3, args.steps // 4)
+        for _ in range(ke):
+            codes.copy_(c_h, non_blocking=True)
+            k.field(codes, levels, out)
+            o_h.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / ke
+        line["e2e"] = {"value": S * n / dt / 1e9, "unit": "GSa/s", "h2d_bytes_per_step": int(codes_h.nbytes),
+                       "d2h_bytes_per_step": int(o_h.numel() * 8), "ms_per_step": dt * 1e3}
+    if not args.no_cpu_baseline:
+        from oracle import kk as okk
+        ns = 1 << 20
+        t0 = time.perf_counter()
+        ref = okk.kk_field_from_codes(ks[0].codes[:ns], scale=float(levels[0, 0]), dc=float(levels[0, 1]),
+                                      fc_step=ks[0].fc_step, n_ov=w["n_ov"], floor=float(np.float32(w["floor"])))
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": ns / dt / 1e9, "unit": "GSa/s", "cores": 1, "kind": "oracle",
+                                "sample": f"the first {ns} samples of one stream, {dt:.1f} s"}
+        if not args.no_parity:
+            g = out[0, :ns - 1024].cpu().numpy()
+            r_ = ref[:ns - 1024]
+            err = np.abs(g - r_) / (ks[0].carrier + np.abs(r_))
+            line["parity"] = {"sample": f"stream 0, samples 0..{ns - 1024}", "max_err_rel_carrier": float(err.max()),
+                              "tolerance": 2e-5}
+    print(json.dumps(line), flush=True)
+
+
 def run_precision(args):
     import torch
     from paper_2108_07004_gb300 import rx as rx_mod
@@ -782,7 +871,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision", "serving", "block_lms", "widely_linear"],
+    ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision", "serving", "block_lms", "widely_linear", "kk"],
                     help="learned: train the MLP demapper on chain output, compare with the exact one; "
                          "precision: DP-QPSK chain with CDC/FIR data in float32, half and bfloat16; "
                          "serving: 64 mixed streams with Poisson arrivals through the continuous-batching server")
@@ -796,6 +885,8 @@ def main():
         run_widely_linear(args)
     elif args.variant == "block_lms":
         run_block_lms(args)
+    elif args.variant == "kk":
+        run_kk(args)
     elif args.variant == "precision":
         run_precision(args)
     elif args.variant == "serving":

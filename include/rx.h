@@ -442,6 +442,47 @@ int rx_unwrap_static(rx_handle *h, const void *y, size_t n_y, const uint8_t *b, 
 int rx_demap(rx_handle *h, const void *z, size_t K, const double *sigma2,
              float *llr);
 
+/* ---- Kramers-Kronig front-end (Sec. 2) ------------------------------------
+ * The paper's receiver detects a carrier-assisted single-polarisation
+ * signal with one photodiode and recovers the field by the Kramers-Kronig
+ * relation: ADC codes are converted to floating point with the DC term that
+ * the AC-coupled detector lost added back, square root and logarithm give
+ * ln|E|, and an overlap-save pair of 1024-point FFTs applies the
+ * frequency-domain Hilbert transform that yields the phase; the field is
+ * then downconverted.  Format-agnostic: no table is involved.
+ *
+ * Readings of the steps the paper leaves open (the signal below the
+ * carrier: E = A + s e^{-j 2 pi fc n}):
+ *   phase      phi = IFFT(G FFT(ln|E|)) per frame, G = +j on the positive
+ *              bins, -j on the negative bins, 0 at DC and N/2;
+ *   carrier    A = exp(frame mean of ln|E|), subtracted from the field;
+ *   output     s[n] = (sqrt(I[n]) e^{j phi[n]} - A) e^{+j 2 pi u / 2^32},
+ *              u = fc_step * n mod 2^32, n counted from the stream start;
+ *   frames     1024 samples starting at f*(1024 - n_ov) - n_ov/2, the
+ *              centre 1024 - n_ov kept; outside the stream the codes are 0
+ *              (intensity = the DC term);
+ *   clamp      I = max(scale * code + dc, floor) before sqrt and log. */
+typedef struct rx_kk rx_kk;
+typedef struct {
+    int n_ov;            /* frame overlap, even, 0 < n_ov < 1024 (512: the paper's 100 % overlap-save) */
+    float floor;         /* intensity clamp (> 0) */
+    uint32_t fc_step;    /* carrier offset from the signal centre, cycles per sample * 2^32 */
+} rx_kk_params;
+/* NULL on error (rx_last_error).  The parameters are copied. */
+rx_kk *rx_kk_create(const rx_kk_params *p);
+void rx_kk_destroy(rx_kk *k);                       /* NULL-safe; synchronises its stream */
+int rx_kk_set_stream(rx_kk *k, void *cuda_stream);
+/* codes      device, [n_streams][n] int16 ADC codes (12-bit values or any
+ *            int16), 1 <= n_streams <= 256.
+ * levels     host, [n_streams][2] float32: photocurrent per code and the DC
+ *            term of each stream; copied by value into the launch.
+ * field_out  device, [n_streams][n] complex64 (interleaved float pairs),
+ *            caller-allocated; every sample is written.
+ * Asynchronous on the object's stream.  RX_EINVAL for NULL pointers, n = 0
+ * or n_streams out of range. */
+int rx_kk_field(rx_kk *k, const int16_t *codes, size_t n_streams, size_t n, const float *levels,
+                float *field_out);
+
 #ifdef __cplusplus
 }
 #endif

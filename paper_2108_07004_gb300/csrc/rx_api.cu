@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "rx_internal.h"
+#include "k_kk.h"
 
 namespace {
 
@@ -51,6 +52,12 @@ struct rx_mlp {
     cudaStream_t st = nullptr;
     int t = 0;                       // Adam steps taken
     long scratch_n = 0;
+};
+
+struct rx_kk {
+    rx_kk_params p{};
+    float2 *tw = nullptr;            // exp(-2 pi i e / 1024)
+    cudaStream_t st = nullptr;
 };
 
 struct rx_handle {
@@ -1530,6 +1537,57 @@ int rx_demap(rx_handle *h, const void *z, size_t K, const double *sigma2, float 
     DemapCount cnt{};
     CK(launch_demap((const float2 *)z, (long)K, 0, 0, (long)K, sigma2, 1, llr, (long)K * h->fmt.m, cnt,
                     h->streams, h->fmt, h->st));
+    return RX_OK;
+}
+
+rx_kk *rx_kk_create(const rx_kk_params *p) {
+    if (!p) { fail(RX_EINVAL, "NULL argument"); return nullptr; }
+    if (p->n_ov <= 0 || p->n_ov >= 1024 || (p->n_ov & 1)) {
+        fail(RX_EINVAL, "n_ov must be even, 0 < n_ov < 1024");
+        return nullptr;
+    }
+    if (!(p->floor > 0.f)) { fail(RX_EINVAL, "floor must be > 0"); return nullptr; }
+    rx_kk *k = new rx_kk();
+    k->p = *p;
+    std::vector<float2> tw(1024);
+    for (int e = 0; e < 1024; ++e)
+        tw[e] = make_float2((float)std::cos(2 * kPi * e / 1024), (float)(-std::sin(2 * kPi * e / 1024)));
+    if (cudaMalloc(&k->tw, sizeof(float2) * 1024) != cudaSuccess ||
+        cudaMemcpy(k->tw, tw.data(), sizeof(float2) * 1024, cudaMemcpyHostToDevice) != cudaSuccess) {
+        fail(RX_ENOMEM, "rx_kk_create: twiddle table");
+        cudaFree(k->tw);
+        delete k;
+        return nullptr;
+    }
+    return k;
+}
+
+void rx_kk_destroy(rx_kk *k) {
+    if (!k) return;
+    if (k->st) cudaStreamSynchronize(k->st);
+    else cudaDeviceSynchronize();
+    cudaFree(k->tw);
+    delete k;
+}
+
+int rx_kk_set_stream(rx_kk *k, void *cuda_stream) {
+    if (!k) return fail(RX_EINVAL, "NULL handle");
+    k->st = (cudaStream_t)cuda_stream;
+    return RX_OK;
+}
+
+int rx_kk_field(rx_kk *k, const int16_t *codes, size_t n_streams, size_t n, const float *levels,
+                float *field_out) {
+    if (!k || !codes || !levels || !field_out) return fail(RX_EINVAL, "NULL argument");
+    if (n == 0) return fail(RX_EINVAL, "n must be > 0");
+    if (n_streams < 1 || n_streams > (size_t)kKKMaxStreams)
+        return fail(RX_EINVAL, "n_streams must be 1 .. %d", kKKMaxStreams);
+    KKDev d{};
+    d.floor = k->p.floor;
+    d.fc_step = k->p.fc_step;
+    d.n_streams = (int)n_streams;
+    for (size_t s = 0; s < n_streams; ++s) d.lv[s] = make_float2(levels[2 * s], levels[2 * s + 1]);
+    CK(launch_kk(codes, reinterpret_cast<float2 *>(field_out), (long)n, k->p.n_ov, d, k->tw, k->st));
     return RX_OK;
 }
 

@@ -78,6 +78,10 @@ _PROTOS = {
     "rx_server_last_error": (C.c_char_p, []),
     "rx_set_demapper": (_I, [_VP, _VP]),
     "rx_set_symbol_output": (_I, [_VP, _VP, _VP]),
+    "rx_kk_create": (_VP, [_VP]),
+    "rx_kk_destroy": (None, [_VP]),
+    "rx_kk_set_stream": (_I, [_VP, _VP]),
+    "rx_kk_field": (_I, [_VP, _VP, _SZ, _SZ, _VP, _VP]),
     "rx_mlp_create": (_VP, [_VP]),
     "rx_mlp_destroy": (None, [_VP]),
     "rx_mlp_set_stream": (_I, [_VP, _VP]),
@@ -390,6 +394,48 @@ class Receiver:
 
 
 MLP_PARAMS = 17926
+
+
+class RxKKParams(C.Structure):
+    _fields_ = [("n_ov", C.c_int), ("floor", C.c_float), ("fc_step", C.c_uint32)]
+
+
+class KK:
+    """Kramers-Kronig front-end: int16 ADC codes [S, n] (device) -> the
+    downconverted signal field [S, n] complex64 (device)."""
+
+    def __init__(self, fc_step: int, n_ov: int = 512, floor: float = 1e-6,
+                 stream: torch.cuda.Stream | None = None):
+        L = lib()
+        p = RxKKParams(int(n_ov), float(floor), int(fc_step) & 0xFFFFFFFF)
+        h = L.rx_kk_create(C.byref(p))
+        if not h:
+            raise RxError(-1, L.rx_last_error().decode())
+        self.h = h
+        st = stream if stream is not None else torch.cuda.current_stream()
+        _ck(L.rx_kk_set_stream(h, st.cuda_stream))
+
+    def field(self, codes: torch.Tensor, levels, out: torch.Tensor | None = None) -> torch.Tensor:
+        """levels: [S, 2] (photocurrent per code, DC term) per stream."""
+        if codes.dtype != torch.int16 or not codes.is_cuda or codes.dim() != 2 or not codes.is_contiguous():
+            raise ValueError("codes must be a contiguous [S, n] int16 device tensor")
+        S, n = codes.shape
+        lv = np.ascontiguousarray(np.asarray(levels, dtype=np.float32).reshape(S, 2))
+        if out is None:
+            out = torch.empty((S, n), dtype=torch.complex64, device=codes.device)
+        _ck(lib().rx_kk_field(self.h, _ptr(codes), S, n, lv.ctypes.data, _ptr(out)))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rx_kk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Mlp:
