@@ -19,9 +19,13 @@ learned demapper (forward, BCE, backward, Adam), pinned by identities,
 finite differences and closed forms.  ``kk`` is the Kramers-Kronig
 front-end (intensity -> field by the frequency-domain Hilbert transform),
 pinned by the library's analytic-signal routine, exact minimum-phase tones
-and the KK reconstruction error against CSPR.
+and the KK reconstruction error against CSPR.  ``fde`` is the trained static
+frequency-domain equaliser with 4-to-2 resampling, pinned by the library
+least-squares solve, exact inversion of a short pulse, exact resampling of
+frame-periodic tones and the EVM gain after the KK front-end.
 """
 from .formats import OracleFormat, oracle_format  # noqa: F401
 from . import chain  # noqa: F401
 from . import mlp  # noqa: F401
 from . import kk  # noqa: F401
+from . import fde  # noqa: F401
