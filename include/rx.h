@@ -483,6 +483,39 @@ int rx_kk_set_stream(rx_kk *k, void *cuda_stream);
 int rx_kk_field(rx_kk *k, const int16_t *codes, size_t n_streams, size_t n, const float *levels,
                 float *field_out);
 
+/* ---- static frequency-domain equaliser with resampling (Sec. 2) ----------
+ * The paper's second FFT pair: a static equaliser of 203 taps, optimised
+ * offline from a training sequence whenever acquisition starts, applied in
+ * the frequency domain together with the resampling from 4 to 2 samples
+ * per symbol.  Readings of what the paper leaves open:
+ *   taps       h[t], t < T, at the input rate, centred: z[n] = sum_t h[t] x[n + D - t], D = (T-1)/2;
+ *   training   regularised least squares on the symbol instants:
+ *              (R + lam I) h = U^H d, R = U^H U, U[i][t] = x[sps*i + D - t]
+ *              (0 outside the stream), lam = delta * trace(R) / T, in float64;
+ *   applying   overlap-save frames of 1024 input samples starting at
+ *              f*(1024 - n_ov) - n_ov/2, spectrum times
+ *              H[k] = sum_t h[t] e^{-j 2 pi k (t - D)/1024} on |f| < fs/4
+ *              (k < 256 or k >= 768) and 0 elsewhere, inverse FFT, centre
+ *              1024 - n_ov samples kept, every second one output. */
+typedef struct rx_fde rx_fde;
+/* taps odd, 1 <= taps <= n_ov + 1; n_ov even, 0 < n_ov < 1024.  NULL on error. */
+rx_fde *rx_fde_create(int taps, int n_ov);
+void rx_fde_destroy(rx_fde *e);                     /* NULL-safe; synchronises its stream */
+int rx_fde_set_stream(rx_fde *e, void *cuda_stream);
+/* x      device, [n] complex64, one stream at the input rate (sps samples per symbol).
+ * d      device, [K] complex64, the known symbols; symbol i sits at input sample sps*i.
+ * Asynchronous; the taps replace the previous ones.  Scratch of T*T*16
+ * bytes is kept by the object. */
+int rx_fde_train(rx_fde *e, const float *x, size_t n, const float *d, size_t K, int sps, double delta);
+/* taps: host, [T][2] float64 (re, im).  set: replaces the taps (and the
+ * response); get: synchronises and copies them out. */
+int rx_fde_set_taps(rx_fde *e, const double *taps);
+int rx_fde_get_taps(rx_fde *e, double *taps);
+/* x  device, [n_streams][n] complex64 (n even); y device, [n_streams][n/2]
+ * complex64, caller-allocated.  RX_ESTATE before any taps were set or
+ * trained.  Asynchronous. */
+int rx_fde_apply(rx_fde *e, const float *x, size_t n_streams, size_t n, float *y);
+
 #ifdef __cplusplus
 }
 #endif

@@ -18,6 +18,7 @@
 
 #include "rx_internal.h"
 #include "k_kk.h"
+#include "k_fde.h"
 
 namespace {
 
@@ -58,6 +59,15 @@ struct rx_kk {
     rx_kk_params p{};
     float2 *tw = nullptr;            // exp(-2 pi i e / 1024)
     cudaStream_t st = nullptr;
+};
+
+struct rx_fde {
+    int T = 203, n_ov = 256;
+    double2 *R = nullptr, *p = nullptr, *y = nullptr, *h = nullptr;   // float64 training scratch, taps
+    float2 *H = nullptr;             // response on the 1024 bins (1/1024 included)
+    float2 *tw = nullptr;            // exp(-2 pi i e / 1024)
+    cudaStream_t st = nullptr;
+    bool ready = false;              // taps set or trained
 };
 
 struct rx_handle {
@@ -1588,6 +1598,81 @@ int rx_kk_field(rx_kk *k, const int16_t *codes, size_t n_streams, size_t n, cons
     d.n_streams = (int)n_streams;
     for (size_t s = 0; s < n_streams; ++s) d.lv[s] = make_float2(levels[2 * s], levels[2 * s + 1]);
     CK(launch_kk(codes, reinterpret_cast<float2 *>(field_out), (long)n, k->p.n_ov, d, k->tw, k->st));
+    return RX_OK;
+}
+
+rx_fde *rx_fde_create(int taps, int n_ov) {
+    if (n_ov <= 0 || n_ov >= 1024 || (n_ov & 1)) { fail(RX_EINVAL, "n_ov must be even, 0 < n_ov < 1024"); return nullptr; }
+    if (taps < 1 || !(taps & 1) || taps > n_ov + 1) { fail(RX_EINVAL, "taps must be odd, 1 .. n_ov + 1"); return nullptr; }
+    rx_fde *e = new rx_fde();
+    e->T = taps;
+    e->n_ov = n_ov;
+    std::vector<float2> tw(1024);
+    for (int k = 0; k < 1024; ++k)
+        tw[k] = make_float2((float)std::cos(2 * kPi * k / 1024), (float)(-std::sin(2 * kPi * k / 1024)));
+    const size_t T = (size_t)taps;
+    if (cudaMalloc(&e->R, sizeof(double2) * T * T) != cudaSuccess || cudaMalloc(&e->p, sizeof(double2) * T) != cudaSuccess ||
+        cudaMalloc(&e->y, sizeof(double2) * T) != cudaSuccess || cudaMalloc(&e->h, sizeof(double2) * T) != cudaSuccess ||
+        cudaMalloc(&e->H, sizeof(float2) * 1024) != cudaSuccess || cudaMalloc(&e->tw, sizeof(float2) * 1024) != cudaSuccess ||
+        cudaMemcpy(e->tw, tw.data(), sizeof(float2) * 1024, cudaMemcpyHostToDevice) != cudaSuccess) {
+        fail(RX_ENOMEM, "rx_fde_create: device buffers");
+        cudaFree(e->R); cudaFree(e->p); cudaFree(e->y); cudaFree(e->h); cudaFree(e->H); cudaFree(e->tw);
+        delete e;
+        return nullptr;
+    }
+    return e;
+}
+
+void rx_fde_destroy(rx_fde *e) {
+    if (!e) return;
+    if (e->st) cudaStreamSynchronize(e->st);
+    else cudaDeviceSynchronize();
+    cudaFree(e->R); cudaFree(e->p); cudaFree(e->y); cudaFree(e->h); cudaFree(e->H); cudaFree(e->tw);
+    delete e;
+}
+
+int rx_fde_set_stream(rx_fde *e, void *cuda_stream) {
+    if (!e) return fail(RX_EINVAL, "NULL handle");
+    e->st = (cudaStream_t)cuda_stream;
+    return RX_OK;
+}
+
+int rx_fde_train(rx_fde *e, const float *x, size_t n, const float *d, size_t K, int sps, double delta) {
+    if (!e || !x || !d) return fail(RX_EINVAL, "NULL argument");
+    if (n == 0 || K == 0 || sps < 1 || !(delta >= 0.0)) return fail(RX_EINVAL, "n, K, sps must be > 0, delta >= 0");
+    if (K > (size_t)INT32_MAX) return fail(RX_EINVAL, "K too large");
+    CK(launch_fde_corr(reinterpret_cast<const float2 *>(x), (long)n, reinterpret_cast<const float2 *>(d), (int)K,
+                       e->T, sps, e->R, e->p, e->st));
+    CK(launch_fde_solve(e->R, e->p, e->y, e->T, delta, e->h, e->st));
+    CK(launch_fde_response(e->h, e->T, e->H, e->st));
+    e->ready = true;
+    return RX_OK;
+}
+
+int rx_fde_set_taps(rx_fde *e, const double *taps) {
+    if (!e || !taps) return fail(RX_EINVAL, "NULL argument");
+    CK(cudaMemcpyAsync(e->h, taps, sizeof(double2) * e->T, cudaMemcpyHostToDevice, e->st));
+    CK(launch_fde_response(e->h, e->T, e->H, e->st));
+    CK(cudaStreamSynchronize(e->st));     // the host taps may go away
+    e->ready = true;
+    return RX_OK;
+}
+
+int rx_fde_get_taps(rx_fde *e, double *taps) {
+    if (!e || !taps) return fail(RX_EINVAL, "NULL argument");
+    if (!e->ready) return fail(RX_ESTATE, "no taps yet");
+    CK(cudaStreamSynchronize(e->st));
+    CK(cudaMemcpy(taps, e->h, sizeof(double2) * e->T, cudaMemcpyDeviceToHost));
+    return RX_OK;
+}
+
+int rx_fde_apply(rx_fde *e, const float *x, size_t n_streams, size_t n, float *y) {
+    if (!e || !x || !y) return fail(RX_EINVAL, "NULL argument");
+    if (n == 0 || (n & 1)) return fail(RX_EINVAL, "n must be a positive even number");
+    if (n_streams == 0 || n_streams > 65535) return fail(RX_EINVAL, "n_streams must be 1 .. 65535");
+    if (!e->ready) return fail(RX_ESTATE, "the equaliser has no taps (rx_fde_train or rx_fde_set_taps)");
+    CK(launch_fde_apply(reinterpret_cast<const float2 *>(x), reinterpret_cast<float2 *>(y), (long)n, (int)n_streams,
+                        e->n_ov, e->H, e->tw, e->st));
     return RX_OK;
 }
 

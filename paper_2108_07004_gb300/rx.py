@@ -82,6 +82,13 @@ _PROTOS = {
     "rx_kk_destroy": (None, [_VP]),
     "rx_kk_set_stream": (_I, [_VP, _VP]),
     "rx_kk_field": (_I, [_VP, _VP, _SZ, _SZ, _VP, _VP]),
+    "rx_fde_create": (_VP, [_I, _I]),
+    "rx_fde_destroy": (None, [_VP]),
+    "rx_fde_set_stream": (_I, [_VP, _VP]),
+    "rx_fde_train": (_I, [_VP, _VP, _SZ, _VP, _SZ, _I, _D]),
+    "rx_fde_set_taps": (_I, [_VP, _VP]),
+    "rx_fde_get_taps": (_I, [_VP, _VP]),
+    "rx_fde_apply": (_I, [_VP, _VP, _SZ, _SZ, _VP]),
     "rx_mlp_create": (_VP, [_VP]),
     "rx_mlp_destroy": (None, [_VP]),
     "rx_mlp_set_stream": (_I, [_VP, _VP]),
@@ -429,6 +436,57 @@ class KK:
     def close(self):
         if getattr(self, "h", None):
             lib().rx_kk_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class FDE:
+    """Static frequency-domain equaliser with 4 -> 2 resampling: taps
+    trained by float64 least squares on known symbols, applied by the
+    overlap-save kernel.  Buffers are torch complex64 device tensors."""
+
+    def __init__(self, taps: int = 203, n_ov: int = 256, stream: torch.cuda.Stream | None = None):
+        L = lib()
+        h = L.rx_fde_create(int(taps), int(n_ov))
+        if not h:
+            raise RxError(-1, L.rx_last_error().decode())
+        self.h, self.T = h, int(taps)
+        st = stream if stream is not None else torch.cuda.current_stream()
+        _ck(L.rx_fde_set_stream(h, st.cuda_stream))
+
+    def train(self, x: torch.Tensor, d: torch.Tensor, sps: int = 4, delta: float = 1e-6):
+        """x [n] complex64 (input rate), d [K] complex64 known symbols."""
+        _ck(lib().rx_fde_train(self.h, _ptr(x), x.shape[-1], _ptr(d), d.shape[-1], int(sps), float(delta)))
+
+    def set_taps(self, taps: np.ndarray):
+        buf = np.ascontiguousarray(np.asarray(taps, dtype=np.complex128))
+        if buf.shape != (self.T,):
+            raise ValueError(f"expected {self.T} taps")
+        _ck(lib().rx_fde_set_taps(self.h, buf.ctypes.data))
+
+    def taps(self) -> np.ndarray:
+        out = np.empty(self.T, dtype=np.complex128)
+        _ck(lib().rx_fde_get_taps(self.h, out.ctypes.data))
+        return out
+
+    def apply(self, x: torch.Tensor, y: torch.Tensor | None = None) -> torch.Tensor:
+        """x [S, n] complex64 -> y [S, n/2] complex64."""
+        if x.dim() == 1:
+            x = x[None]
+        S, n = x.shape
+        if y is None:
+            y = torch.empty((S, n // 2), dtype=torch.complex64, device=x.device)
+        _ck(lib().rx_fde_apply(self.h, _ptr(x), S, n, _ptr(y)))
+        return y
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().rx_fde_destroy(self.h)
             self.h = None
 
     def __del__(self):
