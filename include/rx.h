@@ -498,7 +498,7 @@ int rx_kk_field(rx_kk *k, const int16_t *codes, size_t n_streams, size_t n, cons
  *              (k < 256 or k >= 768) and 0 elsewhere, inverse FFT, centre
  *              1024 - n_ov samples kept, every second one output. */
 typedef struct rx_fde rx_fde;
-/* taps odd, 1 <= taps <= n_ov + 1; n_ov even, 0 < n_ov < 1024.  NULL on error. */
+/* taps odd, 1 <= taps <= n_ov + 1; n_ov a multiple of 4, 0 < n_ov < 1024.  NULL on error. */
 rx_fde *rx_fde_create(int taps, int n_ov);
 void rx_fde_destroy(rx_fde *e);                     /* NULL-safe; synchronises its stream */
 int rx_fde_set_stream(rx_fde *e, void *cuda_stream);

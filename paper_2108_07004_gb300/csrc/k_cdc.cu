@@ -113,11 +113,9 @@ cdc4096_kernel(const float2 *__restrict__ in, typename Store<SK>::T *__restrict_
 }
 
 // ---------------------------------------------------------------------------
-// 1024 points, one warp per frame.  DEC = 2 keeps every second kept output
-// (output o/2 for even o, rows of ns/2): the static equaliser's resampling
-// from 4 to 2 samples per symbol, with H zero outside |f| < fs/4.
+// 1024 points, one warp per frame
 // ---------------------------------------------------------------------------
-template <int SK, int DEC = 1>
+template <int SK>
 __global__ void __launch_bounds__(128)
 cdc1024_kernel(const float2 *__restrict__ in, typename Store<SK>::T *__restrict__ out, long ns, int S, int half,
                long f0, long f1, const float2 *__restrict__ H, const float2 *__restrict__ tw) {
@@ -128,7 +126,7 @@ cdc1024_kernel(const float2 *__restrict__ in, typename Store<SK>::T *__restrict_
     if (f >= f1) return;
     float2 *sm = smem[w];
     const float2 *src = in + (long)blockIdx.y * ns;
-    typename Store<SK>::T *dst = out + (long)blockIdx.y * (ns / DEC);
+    typename Store<SK>::T *dst = out + (long)blockIdx.y * ns;
     const long start = f * S - half;
     float2 v[32];
 #pragma unroll
@@ -168,11 +166,7 @@ cdc1024_kernel(const float2 *__restrict__ in, typename Store<SK>::T *__restrict_
         const int pos = l + 32 * n1;
         if (pos >= half && pos < half + S) {
             long o = f * S + (pos - half);
-            if (DEC == 1) {
-                if (o < ns) Store<SK>::st(dst, o, v[n1]);
-            } else if (o < ns && (o % DEC) == 0) {
-                Store<SK>::st(dst, o / DEC, v[n1]);
-            }
+            if (o < ns) Store<SK>::st(dst, o, v[n1]);
         }
     }
 }
@@ -210,19 +204,4 @@ cudaError_t launch_cdc(const float2 *in, void *out, long ns, int n_streams2, int
         case SK_BF16: return cdc_t<SK_BF16>(in, out, ns, n_streams2, n_fft, S, half, f0, f1, H, tw, st);
         default: return cudaErrorInvalidValue;
     }
-}
-
-// Static equaliser application (Sec. 2): overlap-save 1024-point frames of
-// `in` (rows of ns samples, ns even), spectrum times H (1/1024 included,
-// zero outside the output band), inverse FFT, every second kept sample out
-// (rows of ns/2).
-cudaError_t launch_fde_apply(const float2 *in, float2 *out, long ns, int n_rows, int n_ov, const float2 *H,
-                             const float2 *tw, cudaStream_t st) {
-    const int S = 1024 - n_ov, half = n_ov / 2;
-    if (n_ov <= 0 || n_ov >= 1024 || (n_ov & 1) || (ns & 1)) return cudaErrorInvalidValue;
-    const long nframes = (ns + S - 1) / S;
-    if (nframes <= 0 || n_rows <= 0) return cudaSuccess;
-    dim3 grid((unsigned)((nframes + 3) / 4), (unsigned)n_rows);
-    cdc1024_kernel<SK_F32, 2><<<grid, 128, 0, st>>>(in, out, ns, S, half, 0, nframes, H, tw);
-    return cudaGetLastError();
 }

@@ -1,13 +1,28 @@
-// Training of the static frequency-domain equaliser (Sec. 2: 203 taps
-// optimised offline from a training sequence whenever acquisition starts),
-// in float64: the regularised least-squares normal equations over the
-// symbol instants, their Cholesky solution in one block, and the
-// equaliser's response on the output band for the overlap-save kernel.
+// Static frequency-domain equaliser (Sec. 2: 203 taps optimised offline
+// from a training sequence whenever acquisition starts, applied by an FFT
+// pair that also resamples from 4 to 2 samples per symbol).
+//
+// Training, in float64: the regularised least-squares normal equations over
+// the symbol instants, their Cholesky solution in one block, and the
+// equaliser's response on the output band.
+//
+// Application: one warp per overlap-save frame of 1024 input samples.  The
+// forward 1024-point FFT is the radix 32 x 32 of the CDC kernel; of its
+// output lane l holds bins l + 32 k2, and the output band (k < 256 or
+// k >= 768) is k2 < 8 or k2 >= 24, i.e. the 512-point spectrum index
+// k' = l + 32 k2' (k2' = k2, or k2 - 16).  The inverse is a 512-point FFT
+// at the output rate, m = m1 + 16 m2:
+//   y[m] = sum_l e^{j 2 pi l m2/32} e^{j 2 pi l m1/512} sum_k2' Y[l + 32 k2'] e^{j 2 pi k2' m1/16}
+// the inner 16-point DFTs in registers (one per lane), then for each m1 a
+// 32-point DFT over l split into even / odd l (lanes m1 and m1 + 16, 16
+// points each) joined by one radix-2 step through a shuffle.
 #include "k_fde.h"
 
-#include "rx_internal.h"
+#include "fft_dev.h"
 
 namespace {
+
+using namespace fftdev;
 
 __device__ __forceinline__ double2 dconj_mul(double2 a, double2 b) {   // conj(a) * b
     return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
@@ -143,7 +158,89 @@ __global__ void fde_response_kernel(const double2 *__restrict__ h, int T, float2
     H[k] = make_float2((float)(ax / N), (float)(ay / N));
 }
 
+__global__ void __launch_bounds__(128)
+fde1024_kernel(const float2 *__restrict__ in, float2 *__restrict__ out, long ns, int step, int half, long f1,
+               const float2 *__restrict__ H, const float2 *__restrict__ tw) {
+    constexpr int RP = 33;
+    __shared__ float2 smem[4][32 * RP];
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const long f = (long)blockIdx.x * 4 + w;
+    if (f >= f1) return;
+    float2 *sm = smem[w];
+    const float2 *src = in + (long)blockIdx.y * ns;
+    float2 *dst = out + (long)blockIdx.y * (ns / 2);
+    const long start = f * step - half;
+    float2 v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) {
+        const long idx = start + l + 32 * i;
+        v[i] = (idx >= 0 && idx < ns) ? src[idx] : make_float2(0.f, 0.f);
+    }
+    // forward: lane n2 = l, DFT over n1 -> k1, twiddle W1024^{n2 k1}
+    dft32<false>(v);
+#pragma unroll
+    for (int k1 = 1; k1 < 32; ++k1) v[k1] = cmul(v[k1], twid(tw, l * k1, 1023, false));
+#pragma unroll
+    for (int k1 = 0; k1 < 32; ++k1) sm[k1 * RP + l] = v[k1];
+    __syncwarp();
+    // lane k1 = l: DFT over n2 -> k2: X[l + 32 k2]
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = sm[l * RP + i];
+    dft32<false>(v);
+    // output band times H (1/1024 included): Y[l + 32 k2']
+    float2 u[16];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        u[j] = cmul(v[j], __ldg(H + l + 32 * j));
+        u[j + 8] = cmul(v[j + 24], __ldg(H + l + 32 * (j + 24)));
+    }
+    // inner inverse 16-point DFT over k2' -> m1, twiddle e^{j 2 pi l m1 / 512}
+    dft16<true>(u);
+#pragma unroll
+    for (int m1 = 1; m1 < 16; ++m1) u[m1] = cmul(u[m1], twid(tw, 2 * l * m1, 1023, true));
+    __syncwarp();
+#pragma unroll
+    for (int m1 = 0; m1 < 16; ++m1) sm[m1 * RP + l] = u[m1];
+    __syncwarp();
+    // lane (m1, q): 16-point inverse DFT over r of the values of l = 2r + q
+    const int m1 = l & 15, q = l >> 4;
+#pragma unroll
+    for (int r = 0; r < 16; ++r) u[r] = sm[m1 * RP + 2 * r + q];
+    dft16<true>(u);
+    if (q) {
+#pragma unroll
+        for (int m2 = 1; m2 < 16; ++m2) u[m2] = cmul(u[m2], twid(tw, 32 * m2, 1023, true));
+    }
+    // radix 2 with the partner lane: q = 0 keeps E + w O (m2 < 16), q = 1 E - w O
+    const int hm = half / 2, sm_out = step / 2;
+    const long o0 = f * sm_out - hm;
+#pragma unroll
+    for (int m2 = 0; m2 < 16; ++m2) {
+        const float2 other = make_float2(__shfl_xor_sync(0xffffffffu, u[m2].x, 16),
+                                         __shfl_xor_sync(0xffffffffu, u[m2].y, 16));
+        const float2 y = q ? csub(other, u[m2]) : cadd(u[m2], other);
+        const int m = m1 + 16 * (m2 + 16 * q);
+        if (m >= hm && m < hm + sm_out) {
+            const long o = o0 + m;
+            if (o < ns / 2) dst[o] = y;
+        }
+    }
+}
+
 }  // namespace
+
+// Overlap-save application with 4 -> 2 resampling: rows of ns input
+// samples (ns even) -> rows of ns/2 outputs; n_ov a multiple of 4.
+cudaError_t launch_fde_apply(const float2 *in, float2 *out, long ns, int n_rows, int n_ov, const float2 *H,
+                             const float2 *tw, cudaStream_t st) {
+    const int step = 1024 - n_ov, half = n_ov / 2;
+    if (n_ov <= 0 || n_ov >= 1024 || (n_ov & 3) || (ns & 1)) return cudaErrorInvalidValue;
+    const long nframes = (ns + step - 1) / step;
+    if (nframes <= 0 || n_rows <= 0) return cudaSuccess;
+    dim3 grid((unsigned)((nframes + 3) / 4), (unsigned)n_rows);
+    fde1024_kernel<<<grid, 128, 0, st>>>(in, out, ns, step, half, nframes, H, tw);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_fde_corr(const float2 *x, long n, const float2 *d, int K, int T, int sps, double2 *R,
                             double2 *p, cudaStream_t st) {

@@ -1,5 +1,4 @@
-// Static frequency-domain equaliser kernels (host side of k_fde.cu and of
-// the decimating overlap-save launch in k_cdc.cu).
+// Static frequency-domain equaliser kernels (host side of k_fde.cu).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -13,6 +12,6 @@ cudaError_t launch_fde_solve(double2 *R, const double2 *p, double2 *y, int T, do
                              cudaStream_t st);
 // H[k] = B[k] / 1024 * sum_t h[t] e^{-j 2 pi k (t - D) / 1024}, B the output band.
 cudaError_t launch_fde_response(const double2 *h, int T, float2 *H, cudaStream_t st);
-// Overlap-save application with 4 -> 2 resampling (k_cdc.cu).
+// Overlap-save application with 4 -> 2 resampling (n_ov a multiple of 4).
 cudaError_t launch_fde_apply(const float2 *in, float2 *out, long ns, int n_rows, int n_ov, const float2 *H,
                              const float2 *tw, cudaStream_t st);

@@ -1602,7 +1602,10 @@ int rx_kk_field(rx_kk *k, const int16_t *codes, size_t n_streams, size_t n, cons
 }
 
 rx_fde *rx_fde_create(int taps, int n_ov) {
-    if (n_ov <= 0 || n_ov >= 1024 || (n_ov & 1)) { fail(RX_EINVAL, "n_ov must be even, 0 < n_ov < 1024"); return nullptr; }
+    if (n_ov <= 0 || n_ov >= 1024 || (n_ov & 3)) {
+        fail(RX_EINVAL, "n_ov must be a multiple of 4, 0 < n_ov < 1024");
+        return nullptr;
+    }
     if (taps < 1 || !(taps & 1) || taps > n_ov + 1) { fail(RX_EINVAL, "taps must be odd, 1 .. n_ov + 1"); return nullptr; }
     rx_fde *e = new rx_fde();
     e->T = taps;
