@@ -48,6 +48,7 @@ extern "C" {
 #define RX_FMT_CUSTOM   0
 #define RX_FMT_DP_QPSK  1
 #define RX_FMT_DP_16QAM 2
+#define RX_FMT_DP_64QAM 3
 
 typedef struct rx_handle rx_handle;
 
@@ -58,8 +59,10 @@ typedef struct rx_handle rx_handle;
  *   kind      RX_FMT_*; for built-ins the other fields are ignored.
  *   dims      2: one 2D table used on each polarisation (m_bits per pol);
  *             4: one joint 4D table over both polarisations.
- *   m_bits    bits per table entry (table size 2^m_bits; dims 2: 2 or 4,
- *             dims 4: 6).
+ *   m_bits    bits per table entry (table size 2^m_bits; dims 2: 2 .. 6,
+ *             i.e. 4 to 64 points per polarisation, the paper's 4- to
+ *             64-QAM and GS-8; dims 4: 6), with at most 16 orbits under
+ *             the rotation by 2 pi / sym_order.
  *   points    host, [2^m_bits][dims] float32 (re, im [, re_y, im_y]),
  *             copied at creation.
  *   labels    host, [2^m_bits] bit label of each row, a permutation of

@@ -79,6 +79,29 @@ def _qam16() -> OracleFormat:
     return OracleFormat("dp_16qam", 2, pts, 4, 8)
 
 
+def _qam64() -> OracleFormat:
+    # per-axis Gray over 8 levels, bit 0 of the first axis bit on the positive side:
+    # 000 +7, 001 +5, 011 +3, 010 +1, 110 -1, 111 -3, 101 -5, 100 -7
+    lev = {0b000: 7.0, 0b001: 5.0, 0b011: 3.0, 0b010: 1.0, 0b110: -1.0, 0b111: -3.0, 0b101: -5.0, 0b100: -7.0}
+    pts = np.empty(64, dtype=np.complex128)
+    for lab in range(64):
+        pts[lab] = lev[lab >> 3] + 1j * lev[lab & 7]
+    pts /= np.sqrt(42.0)
+    return OracleFormat("dp_64qam", 2, pts, 6, 12)
+
+
+def _gs2d(name: str) -> OracleFormat:
+    """A 2D table file (``points`` [M][2], ``labels``), used on each polarisation."""
+    with open(os.path.join(os.path.dirname(_TABLE), f"{name}_v1.json")) as f:
+        d = json.load(f)
+    p = np.asarray(d["points"], dtype=np.float64)
+    lab = np.asarray(d["labels"], dtype=np.int64)
+    pts = np.empty(len(lab), dtype=np.complex128)
+    pts[lab] = p[:, 0] + 1j * p[:, 1]
+    mp = int(d["m_bits"])
+    return OracleFormat(name, 2, pts, mp, 2 * mp, int(d.get("sym_order", 4)))
+
+
 def _gs4d64(path: str = _TABLE) -> OracleFormat:
     with open(path) as f:
         d = json.load(f)
@@ -97,4 +120,8 @@ def oracle_format(name: str) -> OracleFormat:
         return _qam16()
     if name == "gs4d64":
         return _gs4d64()
+    if name == "dp_64qam":
+        return _qam64()
+    if name in ("gs8", "gs128"):
+        return _gs2d(name)
     raise ValueError(name)

@@ -601,6 +601,8 @@ cudaError_t launch_bps(const void *y, long y_stride, long a, long e, long n_vali
         case 1: RX_BPS(2, 1);
         case 2: RX_BPS(2, 2);
         case 4: RX_BPS(2, 4);
+        case 8: RX_BPS(2, 8);
+        case 16: RX_BPS(2, 16);
         default: return cudaErrorInvalidValue;
     }
 #undef RX_BPS
@@ -626,10 +628,11 @@ cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long
                                                     z + z_off, z_stride, pcode + pcode_off, pcode_stride,
                                                     partial, sigma2_out, sigma2_stride, ticket, ticket_stride, kR, mdsum, f);
     } else {
-        unwrap_kernel<2, 4><<<grid, 256, 0, st>>>(y, y_stride, b + b_off, b_stride, a, e, dsum, n_cta,
-                                                   carry_in, carry_in_stride, carry_out, carry_out_stride,
-                                                   z + z_off, z_stride, pcode + pcode_off, pcode_stride,
-                                                   partial, sigma2_out, sigma2_stride, ticket, ticket_stride, kR, mdsum, f);
+        // NORB bounds the orbit loop (predicated on f.n_orb): 16 covers every 2D table
+        unwrap_kernel<2, 16><<<grid, 256, 0, st>>>(y, y_stride, b + b_off, b_stride, a, e, dsum, n_cta,
+                                                    carry_in, carry_in_stride, carry_out, carry_out_stride,
+                                                    z + z_off, z_stride, pcode + pcode_off, pcode_stride,
+                                                    partial, sigma2_out, sigma2_stride, ticket, ticket_stride, kR, mdsum, f);
     }
     return cudaGetLastError();
 }

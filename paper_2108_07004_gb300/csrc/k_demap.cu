@@ -639,7 +639,10 @@ cudaError_t launch_derot_demap(const void *y, long y_stride, const uint8_t *b, l
                                      s2_stride, llr, llr_stride, cnt, sym, n_streams, f, st, sk)
     if (f.dims == 4 && f.M == 64) RX_DD(4, 64, 6);
     if (f.dims == 2 && f.M == 4) RX_DD(2, 4, 2);
+    if (f.dims == 2 && f.M == 8) RX_DD(2, 8, 3);
     if (f.dims == 2 && f.M == 16) RX_DD(2, 16, 4);
+    if (f.dims == 2 && f.M == 32) RX_DD(2, 32, 5);
+    if (f.dims == 2 && f.M == 64) RX_DD(2, 64, 6);
 #undef RX_DD
     return cudaErrorInvalidValue;
 }
@@ -655,8 +658,14 @@ cudaError_t launch_count_llr(const float *llr, long llr_stride, const float *x4,
         count_llr_kernel<4, 6><<<grid, 256, 0, st>>>(llr, llr_stride, xv, x_stride, a, e, sigma2, s2_stride, cnt, f);
     else if (f.dims == 2 && f.m_pol == 2)
         count_llr_kernel<2, 2><<<grid, 256, 0, st>>>(llr, llr_stride, xv, x_stride, a, e, sigma2, s2_stride, cnt, f);
+    else if (f.dims == 2 && f.m_pol == 3)
+        count_llr_kernel<2, 3><<<grid, 256, 0, st>>>(llr, llr_stride, xv, x_stride, a, e, sigma2, s2_stride, cnt, f);
     else if (f.dims == 2 && f.m_pol == 4)
         count_llr_kernel<2, 4><<<grid, 256, 0, st>>>(llr, llr_stride, xv, x_stride, a, e, sigma2, s2_stride, cnt, f);
+    else if (f.dims == 2 && f.m_pol == 5)
+        count_llr_kernel<2, 5><<<grid, 256, 0, st>>>(llr, llr_stride, xv, x_stride, a, e, sigma2, s2_stride, cnt, f);
+    else if (f.dims == 2 && f.m_pol == 6)
+        count_llr_kernel<2, 6><<<grid, 256, 0, st>>>(llr, llr_stride, xv, x_stride, a, e, sigma2, s2_stride, cnt, f);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -671,7 +680,13 @@ cudaError_t launch_demap(const float2 *z, long z_stride, long z_off, long a, lon
         return demap_t<4, 64, 6>(zz, z_stride, a, e, sigma2, sigma2_stride, llr, llr_stride, cnt, n_streams, f, st);
     if (f.dims == 2 && f.M == 4)
         return demap_t<2, 4, 2>(zz, z_stride, a, e, sigma2, sigma2_stride, llr, llr_stride, cnt, n_streams, f, st);
+    if (f.dims == 2 && f.M == 8)
+        return demap_t<2, 8, 3>(zz, z_stride, a, e, sigma2, sigma2_stride, llr, llr_stride, cnt, n_streams, f, st);
     if (f.dims == 2 && f.M == 16)
         return demap_t<2, 16, 4>(zz, z_stride, a, e, sigma2, sigma2_stride, llr, llr_stride, cnt, n_streams, f, st);
+    if (f.dims == 2 && f.M == 32)
+        return demap_t<2, 32, 5>(zz, z_stride, a, e, sigma2, sigma2_stride, llr, llr_stride, cnt, n_streams, f, st);
+    if (f.dims == 2 && f.M == 64)
+        return demap_t<2, 64, 6>(zz, z_stride, a, e, sigma2, sigma2_stride, llr, llr_stride, cnt, n_streams, f, st);
     return cudaErrorInvalidValue;
 }

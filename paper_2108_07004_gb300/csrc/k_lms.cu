@@ -44,7 +44,7 @@ __host__ __device__ constexpr int lms_off_b(int T) { return lms_off_rp(T) + kSB 
 __host__ __device__ constexpr int lms_off_e(int T) { return lms_off_b(T) + 2 * kSB * 2; }
 __host__ __device__ constexpr int lms_off_rot(int T) { return lms_off_e(T) + 2 * kSB * 2; }
 __host__ __device__ constexpr int lms_off_pc(int T) { return lms_off_rot(T) + 3 * kCH; }
-__host__ __device__ constexpr int lms_smem_f2(int T) { return lms_off_pc(T) + kCH / 4 + kCH / 8; }
+__host__ __device__ constexpr int lms_smem_f2(int T) { return lms_off_pc(T) + kCH / 4 + kCH / 4; }
 
 __device__ __forceinline__ void bar_sync(int id, int n) {
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(n) : "memory");
@@ -121,7 +121,7 @@ template <int T, int DIMS, int MODE>
 __global__ void __launch_bounds__(kThreads, 1)
 lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_in,
            float2 *__restrict__ taps_out, long k0, int n_upd, const uint16_t *__restrict__ pcode,
-           long pcode_stride, int passes, float mu, const uint8_t *__restrict__ ref_lab,
+           long pcode_stride, int passes, float mu, const reflab_t *__restrict__ ref_lab,
            long ref_stride, int sk, int wl, const __grid_constant__ FmtDev f) {
     constexpr int D = (T - 1) / 2;
     constexpr int NSX = lms_nsx(T);
@@ -138,7 +138,7 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
     float2 *rots = dyn_sm + lms_off_rot(T);           // exp(j phi_k) (MODE 1, 3)
     float2 *tg0 = rots + kCH, *tg1 = rots + 2 * kCH;  // d_q exp(j phi_k) (MODE 3)
     uint16_t *pc = reinterpret_cast<uint16_t *>(dyn_sm + lms_off_pc(T));
-    uint8_t *rl = reinterpret_cast<uint8_t *>(pc + kCH);
+    reflab_t *rl = reinterpret_cast<reflab_t *>(pc + kCH);
     const int s_id = blockIdx.x;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int hw = (warp & 3) ? warp - 1 - (warp >> 2) : -1;   // helper index 0 .. 8
@@ -616,7 +616,7 @@ lms_block_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__
 template <int DIMS>
 __global__ void __launch_bounds__(256)
 align_kernel(const void *__restrict__ y, long ystride, float2 *__restrict__ taps, int T,
-             const uint8_t *__restrict__ ref_lab, long ref_stride, int n_train, int sk,
+             const reflab_t *__restrict__ ref_lab, long ref_stride, int n_train, int sk,
              const __grid_constant__ FmtDev f) {
     __shared__ double red[8][256];
     __shared__ float2 rot[2];
@@ -684,7 +684,7 @@ align_kernel(const void *__restrict__ y, long ystride, float2 *__restrict__ taps
 //   b = n_k + B/2 - m B, m = floor((n_k + B/2) / B).
 template <int DIMS>
 __global__ void __launch_bounds__(256)
-train_phase_kernel(const void *__restrict__ y, long ystride, const uint8_t *__restrict__ ref_lab,
+train_phase_kernel(const void *__restrict__ y, long ystride, const reflab_t *__restrict__ ref_lab,
                    long ref_stride, int n, int W, uint16_t *__restrict__ pcode, long pcode_stride,
                    int32_t *__restrict__ carry, int carry_stride, int sk, const __grid_constant__ FmtDev f) {
     extern __shared__ float2 rs[];      // [n] per-symbol correlations
@@ -724,7 +724,7 @@ train_phase_kernel(const void *__restrict__ y, long ystride, const uint8_t *__re
 }
 
 // labels of rows i0 .. i1 - 1 of bits [S][n][m] into lab [S][n]
-__global__ void ref_labels_kernel(const uint8_t *__restrict__ bits, uint8_t *__restrict__ lab,
+__global__ void ref_labels_kernel(const uint8_t *__restrict__ bits, reflab_t *__restrict__ lab,
                                   long n, long i0, long i1, int m) {
     const long i = i0 + (long)blockIdx.x * blockDim.x + threadIdx.x;
     const int s = blockIdx.y;
@@ -732,7 +732,7 @@ __global__ void ref_labels_kernel(const uint8_t *__restrict__ bits, uint8_t *__r
     const uint8_t *b = bits + ((long)s * n + i) * m;
     int v = 0;
     for (int c = 0; c < m; ++c) v = (v << 1) | (b[c] & 1);
-    lab[(long)s * n + i] = (uint8_t)v;
+    lab[(long)s * n + i] = (reflab_t)v;
 }
 
 // The recursion is latency-bound: a block asks for (nearly) all of an SM's
@@ -741,7 +741,7 @@ __global__ void ref_labels_kernel(const uint8_t *__restrict__ bits, uint8_t *__r
 template <int T, int DIMS, int MODE>
 cudaError_t lms_launch_one(const void *x, long ns, const float2 *ti, float2 *to, long k0, int n_upd,
                            const uint16_t *pcode, long pstride, int passes, float mu,
-                           const uint8_t *ref, long rstride, int S, const FmtDev &f, cudaStream_t st, int sk, int wl) {
+                           const reflab_t *ref, long rstride, int S, const FmtDev &f, cudaStream_t st, int sk, int wl) {
     auto kern = lms_kernel<T, DIMS, MODE>;
     cudaFuncAttributes fa;
     cudaError_t e = cudaFuncGetAttributes(&fa, kern);
@@ -760,7 +760,7 @@ cudaError_t lms_launch_one(const void *x, long ns, const float2 *ti, float2 *to,
 template <int T, int MODE>
 cudaError_t lms_launch_mode(const void *x, long ns, const float2 *ti, float2 *to, long k0,
                             int n_upd, const uint16_t *pcode, long pstride, int passes, float mu,
-                            const uint8_t *ref, long rstride, int S, const FmtDev &f,
+                            const reflab_t *ref, long rstride, int S, const FmtDev &f,
                             cudaStream_t st, int sk, int wl) {
     if (f.dims == 4)
         return lms_launch_one<T, 4, MODE>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref,
@@ -773,7 +773,7 @@ template <int T>
 cudaError_t lms_dispatch_dims(const void *x, long ns, const float2 *ti, float2 *to, long k0,
                               int n_upd, const uint16_t *pcode, long pstride, int mode,
                               int passes, unsigned long long u0, int n_cma, float mu,
-                              const uint8_t *ref, long rstride, int S, const FmtDev &f,
+                              const reflab_t *ref, long rstride, int S, const FmtDev &f,
                               cudaStream_t st, int sk, int wl) {
     switch (mode) {
         case 0: return lms_launch_mode<T, 0>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk, wl);
@@ -802,7 +802,7 @@ cudaError_t lms_dispatch_dims(const void *x, long ns, const float2 *ti, float2 *
 
 cudaError_t launch_lms(const void *x, long ns, const float2 *taps_in, float2 *taps_out, long k0,
                        int n_upd, const uint16_t *pcode, long pcode_stride, int mode, int passes,
-                       unsigned long long u0, int n_cma, float mu, const uint8_t *ref_lab,
+                       unsigned long long u0, int n_cma, float mu, const reflab_t *ref_lab,
                        long ref_stride, int n_streams, int T, const FmtDev &f, cudaStream_t st, int sk, int wl) {
     if (n_upd <= 0 || n_streams <= 0) {
         if (taps_in != taps_out)
@@ -846,7 +846,7 @@ cudaError_t launch_lms_block(const void *x, long ns, const float2 *taps_in, floa
     return cudaGetLastError();
 }
 
-cudaError_t launch_align(const void *y, long ystride, float2 *taps, const uint8_t *ref_lab,
+cudaError_t launch_align(const void *y, long ystride, float2 *taps, const reflab_t *ref_lab,
                          long ref_stride, int n_train, int n_streams, int T, const FmtDev &f,
                          cudaStream_t st, int sk) {
     if (n_train <= 0 || n_streams <= 0) return cudaSuccess;
@@ -858,7 +858,7 @@ cudaError_t launch_align(const void *y, long ystride, float2 *taps, const uint8_
     return cudaGetLastError();
 }
 
-cudaError_t launch_train_phase(const void *y, long ystride, const uint8_t *ref_lab, long ref_stride, int n,
+cudaError_t launch_train_phase(const void *y, long ystride, const reflab_t *ref_lab, long ref_stride, int n,
                                int W, uint16_t *pcode, long pcode_stride, int32_t *carry, int carry_stride,
                                int n_streams, const FmtDev &f, cudaStream_t st, int sk) {
     if (n <= 0 || n_streams <= 0) return cudaSuccess;
@@ -880,14 +880,14 @@ cudaError_t launch_train_phase(const void *y, long ystride, const uint8_t *ref_l
     return cudaGetLastError();
 }
 
-cudaError_t launch_ref_labels(const uint8_t *bits, uint8_t *lab, long n_sym, int n_streams, int m,
+cudaError_t launch_ref_labels(const uint8_t *bits, reflab_t *lab, long n_sym, int n_streams, int m,
                               int dims, int m_pol, cudaStream_t st) {
     (void)dims;
     (void)m_pol;
     return launch_ref_labels_rows(bits, lab, n_sym, 0, n_sym, n_streams, m, st);
 }
 
-cudaError_t launch_ref_labels_rows(const uint8_t *bits, uint8_t *lab, long n_sym, long i0, long i1,
+cudaError_t launch_ref_labels_rows(const uint8_t *bits, reflab_t *lab, long n_sym, long i0, long i1,
                                    int n_streams, int m, cudaStream_t st) {
     if (i1 <= i0 || n_streams <= 0) return cudaSuccess;
     dim3 grid((unsigned)((i1 - i0 + 255) / 256), (unsigned)n_streams);

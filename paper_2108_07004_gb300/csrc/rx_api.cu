@@ -141,7 +141,7 @@ struct rx_handle {
     StreamDev *sd = nullptr;
     long cap_dsum = 0, cap_pd = 0;
     // reference
-    uint8_t *ref = nullptr;
+    reflab_t *ref = nullptr;
     long ref_n = 0;
     int ref_s = 0;
     // stream state (host mirror of the scalars)
@@ -223,9 +223,9 @@ void rot_q(const float *p, int dims, int k, float *out) {
 int build_format(const rx_format *f, FmtDev &d) {
     std::vector<float> pts;
     int dims, mb, S;
-    if (f->kind == RX_FMT_DP_QPSK || f->kind == RX_FMT_DP_16QAM) {
+    if (f->kind == RX_FMT_DP_QPSK || f->kind == RX_FMT_DP_16QAM || f->kind == RX_FMT_DP_64QAM) {
         dims = 2;
-        mb = f->kind == RX_FMT_DP_QPSK ? 2 : 4;
+        mb = f->kind == RX_FMT_DP_QPSK ? 2 : (f->kind == RX_FMT_DP_16QAM ? 4 : 6);
         S = 4;
         gray_qam(mb, pts);
     } else if (f->kind == RX_FMT_CUSTOM) {
@@ -249,7 +249,7 @@ int build_format(const rx_format *f, FmtDev &d) {
     }
     const int M = 1 << mb;
     if (S != 1 && S != 2 && S != 4) return fail(RX_EINVAL, "sym_order must be 1, 2 or 4");
-    if (dims == 2 && !(M == 4 || M == 16)) return fail(RX_EINVAL, "2D tables of 4 or 16 points are supported");
+    if (dims == 2 && (M < 4 || M > 64)) return fail(RX_EINVAL, "2D tables of 4 to 64 points are supported");
     if (dims == 4 && M != 64) return fail(RX_EINVAL, "4D tables of 64 points are supported");
     std::memset(&d, 0, sizeof d);
     d.dims = dims;
@@ -298,6 +298,7 @@ int build_format(const rx_format *f, FmtDev &d) {
         ++no;
     }
     d.n_orb = no;
+    if (no > 16) return fail(RX_EINVAL, "%d orbits under the rotation by 2pi/%d; at most 16 are supported", no, S);
     return RX_OK;
 }
 
@@ -887,13 +888,8 @@ rx_handle *rx_create(const rx_format *format, double symbol_rate, int sps, doubl
     h->B = bps_phases;
     if (check_config(h) != RX_OK) { delete h; return nullptr; }
     set_phases(h->fmt, bps_phases);
-    if (h->fmt.dims == 4 && h->fmt.n_orb > 16) {
+    if (h->fmt.n_orb > 16) {
         fail(RX_EINVAL, "phase search needs at most 16 orbits (use sym_order 4)");
-        delete h;
-        return nullptr;
-    }
-    if (h->fmt.dims == 2 && h->fmt.n_orb > 4) {
-        fail(RX_EINVAL, "phase search needs at most 4 orbits per polarisation");
         delete h;
         return nullptr;
     }
@@ -1098,7 +1094,7 @@ int rx_set_reference(rx_handle *h, const uint8_t *bits, size_t n_sym) {
     h->ref_s = S;
     h->ref_host = nullptr;
     if (!n_sym) return RX_OK;
-    if (!h->ref) CK(cudaMalloc(&h->ref, (size_t)S * n_sym));
+    if (!h->ref) CK(cudaMalloc(&h->ref, sizeof(reflab_t) * (size_t)S * n_sym));
     CK(launch_ref_labels(bits, h->ref, (long)n_sym, S, h->fmt.m, h->fmt.dims, h->fmt.m_pol, h->st));
     h->started = false;
     return RX_OK;
@@ -1110,7 +1106,7 @@ int rx_set_reference_host(rx_handle *h, const uint8_t *bits, size_t n_sym) {
     if (h->ref && (h->ref_n != (long)n_sym || h->ref_s != S)) { cudaFree(h->ref); h->ref = nullptr; }
     h->ref_n = (long)n_sym;
     h->ref_s = S;
-    if (!h->ref) CK(cudaMalloc(&h->ref, (size_t)S * n_sym));
+    if (!h->ref) CK(cudaMalloc(&h->ref, sizeof(reflab_t) * (size_t)S * n_sym));
     const size_t need = (size_t)S * n_sym * h->fmt.m;
     if (h->ref_bits_cap < need) {
         cudaFree(h->ref_bits);

@@ -10,6 +10,8 @@
 #include <cuda_bf16.h>
 
 #define RX_MAXM 64        // largest table (4D: 64 points; 2D: 16 points per polarisation)
+// reference label of one 4D symbol (m bits, MSB first): up to 12 bits (DP-64QAM)
+typedef uint16_t reflab_t;
 #define RX_MAXB 64        // largest number of BPS test phases
 #define RX_NCHUNK 10      // BPS ring of 32-symbol chunks
 
@@ -151,7 +153,7 @@ cudaError_t launch_fir(const void *x, long ns, const float2 *taps, long k0, long
 cudaError_t launch_lms(const void *x, long ns, const float2 *taps_in, float2 *taps_out,
                        long k0, int n_upd, const uint16_t *pcode, long pcode_stride,
                        int mode, int passes, unsigned long long u0, int n_cma, float mu,
-                       const uint8_t *ref_lab, long ref_stride,
+                       const reflab_t *ref_lab, long ref_stride,
                        int n_streams, int T, const FmtDev &f, cudaStream_t st, int sk = SK_F32,
                        int wl = 0);
 
@@ -165,11 +167,11 @@ cudaError_t launch_lms_block(const void *x, long ns, const float2 *taps_in, floa
 // Training stage kernels on the equalised training span y [S][2][ystride]
 // (storage kind sk): data-aided phase codes, and the output order / phase
 // alignment of the taps [S][2][2][T] (in place).
-cudaError_t launch_train_phase(const void *y, long ystride, const uint8_t *ref_lab, long ref_stride, int n,
+cudaError_t launch_train_phase(const void *y, long ystride, const reflab_t *ref_lab, long ref_stride, int n,
                                int W, uint16_t *pcode, long pcode_stride, int32_t *carry, int carry_stride,
                                int n_streams, const FmtDev &f, cudaStream_t st, int sk = SK_F32);
 
-cudaError_t launch_align(const void *y, long ystride, float2 *taps, const uint8_t *ref_lab,
+cudaError_t launch_align(const void *y, long ystride, float2 *taps, const reflab_t *ref_lab,
                          long ref_stride, int n_train, int n_streams, int T, const FmtDev &f,
                          cudaStream_t st, int sk = SK_F32);
 
@@ -201,7 +203,7 @@ cudaError_t launch_dsum_from_b(const uint8_t *b, long b_stride, long a, long e, 
                                int chunks, int n_streams, int B, cudaStream_t st);
 
 struct DemapCount {
-    const uint8_t *ref_lab;   // [S][N] labels of the reference (or null)
+    const reflab_t *ref_lab;   // [S][N] labels of the reference (or null)
     long ref_stride;
     long c0, c1;              // count symbols with c0 <= k < c1 (stream index)
     StreamDev *sd;            // per-stream accumulators (or null)
@@ -274,8 +276,8 @@ cudaError_t launch_demap(const float2 *z, long z_stride, long z_off, long a, lon
                          long llr_stride, const DemapCount &cnt, int n_streams,
                          const FmtDev &f, cudaStream_t st);
 
-cudaError_t launch_ref_labels(const uint8_t *bits, uint8_t *lab, long n_sym, int n_streams,
+cudaError_t launch_ref_labels(const uint8_t *bits, reflab_t *lab, long n_sym, int n_streams,
                               int m, int dims, int m_pol, cudaStream_t st);
 // rows i0 .. i1 - 1 only (bits [S][n_sym][m], labels [S][n_sym])
-cudaError_t launch_ref_labels_rows(const uint8_t *bits, uint8_t *lab, long n_sym, long i0, long i1,
+cudaError_t launch_ref_labels_rows(const uint8_t *bits, reflab_t *lab, long n_sym, long i0, long i1,
                                    int n_streams, int m, cudaStream_t st);

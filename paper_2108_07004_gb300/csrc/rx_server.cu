@@ -46,9 +46,9 @@ struct Req {
 
 size_t estimate_bytes(const rx_request &r) {
     // per symbol: CDC output 32 B, FIR output 16 B, phase index 1 B, phase
-    // code 2 B, reference labels 1 B; plus tables, taps ring and partials
+    // code 2 B, reference labels 2 B; plus tables, taps ring and partials
     const size_t N = r.n_samples / 2;
-    return 52 * N + (1u << 20);
+    return 53 * N + (1u << 20);
 }
 
 }  // namespace

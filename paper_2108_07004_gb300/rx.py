@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librx.so")
 _lib = None
 
-RX_FMT_CUSTOM, RX_FMT_DP_QPSK, RX_FMT_DP_16QAM = 0, 1, 2
+RX_FMT_CUSTOM, RX_FMT_DP_QPSK, RX_FMT_DP_16QAM, RX_FMT_DP_64QAM = 0, 1, 2, 3
 
 
 class RxError(RuntimeError):
@@ -215,6 +215,8 @@ def make_format(fmt: str):
         f.kind = RX_FMT_DP_QPSK
     elif fmt == "dp_16qam":
         f.kind = RX_FMT_DP_16QAM
+    elif fmt == "dp_64qam":
+        f.kind = RX_FMT_DP_64QAM
     else:
         d = load_table(fmt)
         pts = np.ascontiguousarray(np.asarray(d["points"], dtype=np.float32))

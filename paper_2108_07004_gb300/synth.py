@@ -93,11 +93,27 @@ def tx_table4d(path: str) -> TxFormat:
     return TxFormat(d.get("name", "table4d"), 4, pts, int(np.log2(len(lab))))
 
 
+def tx_table2d(path: str) -> TxFormat:
+    """2D table (the same on each polarisation) from a JSON file holding
+    ``points`` as [M][2] reals and ``labels`` (a permutation of 0..M-1)."""
+    with open(path) as f:
+        d = json.load(f)
+    p = np.asarray(d["points"], dtype=np.float64)
+    lab = np.asarray(d["labels"], dtype=np.int64)
+    pts = np.empty(len(lab), dtype=np.complex128)
+    pts[lab] = p[:, 0] + 1j * p[:, 1]
+    return TxFormat(d.get("name", "table2d"), 2, pts, 2 * int(np.log2(len(lab))))
+
+
 def tx_format(name: str) -> TxFormat:
     if name == "dp_qpsk":
         return tx_qam_gray(2)
     if name == "dp_16qam":
         return tx_qam_gray(4)
+    if name == "dp_64qam":
+        return tx_qam_gray(6)
+    if name in ("gs8", "gs128"):
+        return tx_table2d(os.path.join(_DATA, f"{name}_v1.json"))
     if name == "gs4d64":
         return tx_table4d(os.path.join(_DATA, "gs4d64_v1.json"))
     raise ValueError(f"unknown format {name!r}")

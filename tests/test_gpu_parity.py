@@ -47,6 +47,8 @@ CASES = {
     "qpsk80km": ("dp_qpsk", 1 << 14, 1360.0, 1024, 256, 15, 32, 4096, 12.0, 1e-5),
     "gs1000km": ("gs4d64", 1 << 14, 17000.0, 4096, 1024, 31, 64, 4096, 12.0, 2e-5),
     "qam16": ("dp_16qam", 12000, 2000.0, 1024, 256, 15, 32, 4096, 18.0, 1e-5),
+    "qam64": ("dp_64qam", 12000, 1000.0, 1024, 256, 15, 64, 4096, 24.0, 1e-6),
+    "gs8": ("gs8", 12000, 500.0, 1024, 256, 15, 32, 4096, 14.0, 1e-5),
 }
 
 
@@ -256,7 +258,7 @@ def test_demap_parity(case):
     assert np.all(err <= LLR_RTOL * np.maximum(1.0, np.abs(ref)))
 
 
-@pytest.mark.parametrize("name", ["gs4d64", "dp_16qam", "dp_qpsk"])
+@pytest.mark.parametrize("name", ["gs4d64", "dp_16qam", "dp_qpsk", "dp_64qam", "gs8"])
 def test_demap_extreme_llrs(name):
     """Subset sums beyond the float range of the common shift use their own
     shift: every symbol extreme (small sigma^2), and a ragged length with

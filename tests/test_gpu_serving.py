@@ -80,7 +80,7 @@ def test_served_request_equals_a_handle(streams):
 def test_small_budget_queues_without_changing_results(streams):
     alone = {i: _serve([i], streams)[0][i] for i in range(len(REQS))}
     # room for about two of the requests at a time
-    budget = 52 * 2 * 70001 + 3 * (1 << 20)
+    budget = 53 * 2 * 70001 + 3 * (1 << 20)
     mix, info = _serve(range(len(REQS)), streams, budget=budget)
     assert 1 <= info["max_active"] <= 3
     assert info["mem_used"] == 0
