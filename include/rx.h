@@ -113,6 +113,10 @@ void rx_destroy(rx_handle *h);                      /* NULL-safe */
  *   (<= 20000), "train_passes" [3],
  *   "sigma2" [0 = estimate per block], "skip_head" [4096],
  *   "skip_tail" [512], "streams" [1], "rolloff" [0.1],
+ *   "matched_filter" [1]: 0 leaves the root-raised-cosine matched filter
+ *   out of the CDC's spectral multiply, for input that an earlier stage has
+ *   already filtered (the static equaliser after the KK front-end, Sec. 2;
+ *   with cd_ps_per_nm = 0 the CDC is then the identity),
  *   "widely_linear" [0]: 1 makes the butterfly widely linear, y_q =
  *   sum_p sum_t conj(h_qp[t]) x_p[2k+D-t] + conj(g_qp[t]) conj(x_p[2k+D-t])
  *   (the paper's equaliser acts on the signal and its conjugate, Sec. 2);

@@ -35,6 +35,7 @@ class RxParams:
     cd_ps_per_nm: float = 0.0
     wavelength: float = 1550e-9
     rolloff: float = 0.1
+    matched_filter: bool = True  # False: input already filtered (static equaliser after KK)
     n_fft: int = 1024          # overlap-save FFT size
     n_ov: int = 256            # overlap (discarded samples per frame)
     taps: int = 15             # FIR taps per butterfly branch (odd)
@@ -88,7 +89,7 @@ def cdc_filter(p: RxParams) -> np.ndarray:
     (reading: the paper's static FD equaliser is replaced by CD inversion
     plus matched filtering in the same FFT pair)."""
     f = np.fft.fftfreq(p.n_fft, d=1.0 / (p.sps * p.symbol_rate))
-    hmf = np.sqrt(p.sps * raised_cosine(f, p.symbol_rate, p.rolloff))
+    hmf = np.sqrt(p.sps * raised_cosine(f, p.symbol_rate, p.rolloff)) if p.matched_filter else 1.0
     return np.conj(cd_response(f, p.cd_ps_per_nm, p.wavelength)) * hmf
 
 

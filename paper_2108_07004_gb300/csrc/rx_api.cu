@@ -97,6 +97,7 @@ struct rx_handle {
     long skip_head = 4096, skip_tail = 512;
     int streams = 1;
     double rolloff = 0.1;
+    bool matched_filter = true;     // root-raised-cosine matched filter in the CDC multiply
     double wavelength = 1550e-9;
     // CUDA
     cudaStream_t st = nullptr;
@@ -330,7 +331,7 @@ int upload_tables(rx_handle *h) {
         const double f = (k < n / 2 ? k : k - n) * fs / n;
         const double w = 2 * kPi * f;
         const double ph = -dl * h->wavelength * h->wavelength * w * w / (4 * kPi * kC);   // conj(H_CD)
-        const double mag = std::sqrt(h->sps * raised_cosine(f, h->symbol_rate, h->rolloff)) / n;
+        const double mag = (h->matched_filter ? std::sqrt(h->sps * raised_cosine(f, h->symbol_rate, h->rolloff)) : 1.0) / n;
         H[k] = make_float2((float)(mag * std::cos(ph)), (float)(mag * std::sin(ph)));
         tw[k] = make_float2((float)std::cos(2 * kPi * k / n), (float)(-std::sin(2 * kPi * k / n)));
     }
@@ -802,6 +803,7 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     else if (k == "skip_tail") { rc = as_int(0, 1L << 40, t); h->skip_tail = t; }
     else if (k == "streams") { rc = as_int(1, 4096, t); h->streams = (int)t; }
     else if (k == "rolloff") { if (!(v > 0 && v <= 1)) return fail(RX_EINVAL, "rolloff out of range"); h->rolloff = v; h->tables_dirty = true; }
+    else if (k == "matched_filter") { if (v != 0 && v != 1) return fail(RX_EINVAL, "matched_filter is 0 or 1"); h->matched_filter = v != 0; h->tables_dirty = true; }
     else if (k == "wavelength_nm") { if (!(v > 100 && v < 10000)) return fail(RX_EINVAL, "wavelength out of range"); h->wavelength = v * 1e-9; h->tables_dirty = true; }
     else if (k == "profile") { rc = as_int(0, 2, t); h->profile = (int)t; }
     else if (k == "precision") { rc = as_int(0, 2, t); h->prec = (int)t; }
@@ -964,6 +966,7 @@ int rx_get_param(const rx_handle *h, const char *key, double *value) {
     else if (k == "skip_tail") *value = (double)h->skip_tail;
     else if (k == "streams") *value = h->streams;
     else if (k == "rolloff") *value = h->rolloff;
+    else if (k == "matched_filter") *value = h->matched_filter ? 1.0 : 0.0;
     else if (k == "wavelength_nm") *value = h->wavelength * 1e9;
     else if (k == "taps") *value = h->T;
     else if (k == "bps_phases") *value = h->B;

@@ -83,3 +83,15 @@ def test_cdc_unitary_spectrum_parseval():
     s = chain.raised_cosine(ff, 28e9, 0.1) + chain.raised_cosine(ff - 28e9, 28e9, 0.1)
     assert np.max(np.abs(s - 1)) < 1e-12
     assert rc.max() == 1.0
+
+
+def test_cdc_without_matched_filter_and_dispersion_is_the_identity():
+    """matched_filter = False with no dispersion leaves the multiply at 1:
+    overlap-save returns its input exactly (the chain after the KK front-end
+    and the static equaliser, which did the matched filtering)."""
+    rng = np.random.default_rng(4)
+    r = rng.standard_normal((2, 5000)) + 1j * rng.standard_normal((2, 5000))
+    for nfft, nov in ((1024, 256), (4096, 1024)):
+        p = chain.RxParams(cd_ps_per_nm=0.0, n_fft=nfft, n_ov=nov, matched_filter=False)
+        assert np.max(np.abs(chain.cdc(r, p) - r)) < 1e-12
+        assert np.max(np.abs(chain.cdc(r, chain.RxParams(cd_ps_per_nm=0.0, n_fft=nfft, n_ov=nov)) - r)) > 0.1
