@@ -105,6 +105,8 @@ def rx_params(wl: dict = WL):
         out["lms_block"] = wl["lms_block"]
     if wl.get("widely_linear"):
         out["widely_linear"] = 1
+    if wl.get("lms_start"):
+        out["lms_start"] = 1
     return out
 
 
@@ -164,7 +166,7 @@ def oracle_params(wl: dict, **over):
               n_upd=wl["n_upd"], lag=wl["lag"], mu=wl["mu"], n_pre=wl["n_pre"], cma_passes=wl["cma_passes"],
               n_cma=wl["n_cma"], n_train=wl["n_train"], train_passes=wl["train_passes"],
               skip_head=wl["skip_head"], skip_tail=wl["skip_tail"], lms_block=wl.get("lms_block", 1),
-              widely_linear=bool(wl.get("widely_linear", 0)))
+              widely_linear=bool(wl.get("widely_linear", 0)), lms_start=int(wl.get("lms_start", 0)))
     kw.update(over)
     return chain.RxParams(**kw)
 
@@ -370,8 +372,8 @@ def run_ours(args):
 # ---- precision variant (config 3): DP-QPSK, 80 km, CDC/FIR data in half / bfloat16 ----
 WL3 = dict(workload="dp_qpsk_80km_12dB_2p24_symbols", fmt="dp_qpsk", n_sym=1 << 20, streams=16, esn0_db=12.0,
            cd_ps_per_nm=1360.0, linewidth_ts=1e-5, symbol_rate=28e9, sps=2, fft=1024, overlap=256, taps=15,
-           bps_phases=32, bps_window=64, block=1 << 16, n_upd=1024, lag=2, mu=1e-3, n_pre=2048, cma_passes=1,
-           n_cma=0, n_train=1024, train_passes=3, skip_head=16384, skip_tail=512)
+           bps_phases=32, bps_window=64, block=1 << 16, n_upd=1024, lag=3, mu=1e-3, n_pre=2048, cma_passes=1,
+           n_cma=0, n_train=1024, train_passes=3, skip_head=16384, skip_tail=512, lms_start=1)
 
 
 def chain_bytes_per_symbol(wl: dict, store: int) -> float:
@@ -675,8 +677,8 @@ def run_kk(args):
 KKC = dict(workload="kk_receiver_dp16qam_16x2p20", fmt="dp_16qam", pairs=16, n_sym=1 << 20, distinct=4,
            cspr_db=14.0, esn0_db=20.0, kk_ov=512, floor=1e-3, fde_taps=203, fde_ov=256, fde_train=4096,
            cd_ps_per_nm=0.0, fft=1024, overlap=256, taps=15, bps_phases=32, bps_window=64, block=1 << 16,
-           n_upd=1024, lag=2, mu=1e-3, n_pre=4096, cma_passes=1, n_cma=0, n_train=1024, train_passes=3,
-           skip_head=16384, skip_tail=512)
+           n_upd=1024, lag=3, mu=1e-3, n_pre=4096, cma_passes=1, n_cma=0, n_train=1024, train_passes=3,
+           skip_head=16384, skip_tail=512, lms_start=1)
 
 
 def _kk_pipeline_gpu(rx_mod, torch, w, codes, levels, fc_step, bits, d_train, pairs, n_sym):
@@ -742,7 +744,7 @@ def run_kk_chain(args):
         "config": {"workload": w["workload"], "kk_signals": 2 * P, "streams": P, "symbols_per_stream": n,
                    "format": w["fmt"], "cspr_db": w["cspr_db"], "esn0_db": w["esn0_db"], "sps_in": 4,
                    "kk_fft": 1024, "kk_overlap": w["kk_ov"], "fde_taps": w["fde_taps"], "taps": w["taps"],
-                   "bps_phases": w["bps_phases"], "block": w["block"], "lag": w["lag"],
+                   "bps_phases": w["bps_phases"], "block": w["block"], "lag": w["lag"], "lms_start": w["lms_start"],
                    "l2": "inputs 256 MiB, field 1 GiB > L2, no flush"},
         "stages_ms": {"kk": ms_kk, "fde": ms_fde, "chain": ms_chain},
         "ber": ne / max(nb, 1), "bit_errors": int(ne), "n_bits": int(nb),
@@ -832,7 +834,7 @@ def run_precision(args):
         "data": "synthetic",
         "config": {"workload": wl["workload"], "streams": S, "symbols_per_stream": n, "format": wl["fmt"],
                    "fft": wl["fft"], "overlap": wl["overlap"], "taps": wl["taps"], "bps_phases": wl["bps_phases"],
-                   "block": wl["block"], "lag": wl["lag"]},
+                   "block": wl["block"], "lag": wl["lag"], "lms_start": wl.get("lms_start", 0)},
         "forms": forms, "hbm_peak_gbs": hbm, "hbm_peak_kind": pk_kind,
     }
     if not args.no_cpu_baseline:

@@ -126,6 +126,11 @@ void rx_destroy(rx_handle *h);                      /* NULL-safe */
  *   many (1..64) whose outputs and errors all use the taps at the group's
  *   start (block LMS, a parallel variant beside the exact recursion; also
  *   rx_lms modes 0-2; the start-up training stays sequential),
+ *   "lms_start" [0]: where the update over block n starts: 0 from U_{n-1}
+ *   (one chain through all blocks), 1 from W_n = U_{n-lag}, the taps that
+ *   equalised block n (Sec. 2's "part of a buffer updates the taps for
+ *   later buffers" read per buffer), so the blocks n = r (mod lag) form lag
+ *   independent chains that run concurrently on lag streams,
  *   "wavelength_nm" [1550], "profile" [0] (1: time every launch group and
  *   every block, 2: time the BPS launches only),
  *   "precision" [0]: storage of the chain's CDC and FIR outputs, 0 float32,

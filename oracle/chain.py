@@ -49,6 +49,7 @@ class RxParams:
     cma_passes: int = 1
     n_cma: int = 0             # block-wise updates run as CMA before DD
     lms_block: int = 1         # block-wise updates in groups of this many (1: sequential)
+    lms_start: int = 0         # update of block n starts from U_{n-1} (0) or from W_n = U_{n-lag} (1)
     widely_linear: bool = False  # butterfly on x and conj(x) (augmented taps, 2T per branch)
     n_train: int = 1024        # known training symbols at the stream start
     train_passes: int = 3      # data-aided LMS passes over the training span
@@ -556,8 +557,9 @@ def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
          block runs to the stream end), which needs FIR output of block n only;
          in block 0 the unwrap's start quadrant comes from the training phases;
       3. LMS over the first n_upd symbols of block n starting from U_{n-1}
-         (U_{-1} = W_0) -> U_n  (Sec. 2: part of a buffer updates the taps
-         used for subsequent buffers).
+         (U_{-1} = W_0), or with lms_start = 1 from W_n, the taps that
+         equalised block n -> U_n  (Sec. 2: part of a buffer updates the
+         taps used for subsequent buffers).
     resume = (n, state_at(...) of block n): skip the start-up and blocks
     before n and continue from that state (outputs before block n's range
     stay zero; counting still covers skip_head .. N - skip_tail)."""
@@ -623,10 +625,11 @@ def run_chain(r: np.ndarray, fmt: OracleFormat, p: RxParams,
         out[a:e] = llr(z[:, a:e], s2, fmt)
         span = range(k0, min(k0 + p.n_upd, N))
         phase = {k: phi[k - a] for k in span}
+        h_in = wn if p.lms_start else ring[(n - 1) % (L + 1)]
         if p.lms_block > 1:
-            hn = lms_block(x, ring[(n - 1) % (L + 1)], span, fmt, p, p.lms_block, u0=u, phase=phase, info=info)
+            hn = lms_block(x, h_in, span, fmt, p, p.lms_block, u0=u, phase=phase, info=info)
         else:
-            hn = lms(x, ring[(n - 1) % (L + 1)], span, fmt, p, u0=u, phase=phase, info=info)
+            hn = lms(x, h_in, span, fmt, p, u0=u, phase=phase, info=info)
         u += len(span)
         ring[n % (L + 1)] = hn
         after.append(hn.copy())

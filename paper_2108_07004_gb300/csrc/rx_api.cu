@@ -124,14 +124,19 @@ struct rx_handle {
     const uint8_t *ref_host = nullptr;
     uint8_t *ref_bits = nullptr;
     size_t ref_bits_cap = 0;
-    std::vector<cudaEvent_t> ev_lms;
+    std::vector<cudaEvent_t> ev_lms;     // one per tap-ring slot: the LMS that wrote it is done
+    // lms_start = 1: the update of block n starts from W_n = U_{n-lag}, so the
+    // blocks n = r (mod lag) form lag independent chains, chain r on
+    // side (r = 0) or side_x[r - 1]
+    int lms_start = 0;
+    cudaStream_t side_x[3] = {nullptr, nullptr, nullptr};
     // device tables
     float2 *H = nullptr, *tw = nullptr;
     int tab_fft = 0;
     bool tables_dirty = true;
     // device buffers
     long cap_n = 0;
-    int cap_s = 0, cap_lag = 0, cap_wl = 0;
+    int cap_s = 0, cap_lag = 0, cap_wl = 0, cap_ring = 0;
     void *x = nullptr, *y = nullptr;                  // CDC and FIR outputs, storage kind prec
     float2 *ring = nullptr;
     uint8_t *bidx = nullptr;
@@ -359,7 +364,7 @@ void free_buffers(rx_handle *h) {
     h->bidx = nullptr; h->pcode = nullptr; h->dsum = nullptr;
     h->part_u = h->part_d = h->sig = h->sig_fixed = nullptr;
     h->sd = nullptr;
-    h->cap_n = 0; h->cap_s = 0; h->cap_lag = 0;
+    h->cap_n = 0; h->cap_s = 0; h->cap_lag = 0; h->cap_ring = 0;
 }
 
 int ensure_symbol_buffers(rx_handle *h, long N) {
@@ -378,10 +383,18 @@ int ensure_symbol_buffers(rx_handle *h, long N) {
 // taps per butterfly branch (widely linear: T on x, then T on conj x)
 int tl(const rx_handle *h) { return h->wl ? 2 * h->T : h->T; }
 
+// Tap-ring slots.  U_n goes to slot n; it is read by the FIR of block
+// n + lag and by the update that starts from it.  Sequential chain
+// (lms_start 0): lag + 1 slots.  Independent chains (lms_start 1, lag >= 2):
+// 2 lag slots, so that the update that overwrites slot n (that of block
+// n + 2 lag) runs on the same chain stream after the reader of slot n
+// (the update of block n + lag) and after the FIR of block n + lag.
+int ring_size(const rx_handle *h) { return (h->lms_start && h->lag >= 2) ? 2 * h->lag : h->lag + 1; }
+
 int ensure_buffers(rx_handle *h, long N) {
     const int S = h->streams;
     if (h->cap_n >= N && h->cap_s == S && h->cap_lag == h->lag && h->cap_prec == h->prec && h->cap_wl == h->wl &&
-        h->sd)
+        h->cap_ring == ring_size(h) && h->sd)
         return RX_OK;
     free_buffers(h);
     const long ns = 2 * N;
@@ -389,7 +402,7 @@ int ensure_buffers(rx_handle *h, long N) {
     const long ncta_d = (h->block + 2 * h->W + 255) / 256 + 2;
     CK(cudaMalloc(&h->x, store_bytes(h->prec) * (size_t)S * 2 * ns));
     CK(cudaMalloc(&h->y, store_bytes(h->prec) * (size_t)S * 2 * N));
-    CK(cudaMalloc(&h->ring, sizeof(float2) * (size_t)(h->lag + 1) * S * 4 * tl(h)));
+    CK(cudaMalloc(&h->ring, sizeof(float2) * (size_t)ring_size(h) * S * 4 * tl(h)));
     CK(cudaMalloc(&h->bidx, (size_t)S * N));
     CK(cudaMalloc(&h->pcode, sizeof(uint16_t) * (size_t)S * N));
     CK(cudaMalloc(&h->dsum, sizeof(int) * 2 * (size_t)S * ncta));        // by block parity
@@ -407,6 +420,7 @@ int ensure_buffers(rx_handle *h, long N) {
     h->cap_wl = h->wl;
     h->cap_s = S;
     h->cap_lag = h->lag;
+    h->cap_ring = ring_size(h);
     h->cap_prec = h->prec;
     return RX_OK;
 }
@@ -428,7 +442,13 @@ int ensure_streams(rx_handle *h) {
         }
         CK(cudaEventCreateWithFlags(&h->ev_setup, cudaEventDisableTiming));
     }
-    while ((int)h->ev_lms.size() < h->lag + 1) {
+    if (h->lms_start) {
+        int least = 0, greatest = 0;
+        CK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        for (int r = 1; r < h->lag; ++r)
+            if (!h->side_x[r - 1]) CK(cudaStreamCreateWithPriority(&h->side_x[r - 1], cudaStreamNonBlocking, greatest));
+    }
+    while ((int)h->ev_lms.size() < ring_size(h)) {
         cudaEvent_t e;
         CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
         h->ev_lms.push_back(e);
@@ -462,7 +482,7 @@ void center_spike(const rx_handle *h, std::vector<float2> &v) {
 }
 
 float2 *slot(rx_handle *h, long n) {
-    const int L1 = h->lag + 1;
+    const int L1 = ring_size(h);
     const long i = ((n % L1) + L1) % L1;
     return h->ring + (size_t)i * h->streams * 4 * tl(h);
 }
@@ -631,7 +651,8 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
             int rc2 = train_stage(h, h->x, ns, w0, ntr, h->pcode, N, nullptr, 0, ss, h->prec);
             if (rc2 != RX_OK) return rc2;
         }
-        for (int i = 1; i <= L; ++i) CK(cudaMemcpyAsync(slot(h, i), w0, tapsz, cudaMemcpyDeviceToDevice, ss));
+        // W_0 into the slots of U_{-lag} .. U_{-1}
+        for (int i = 1; i <= L; ++i) CK(cudaMemcpyAsync(slot(h, -i), w0, tapsz, cudaMemcpyDeviceToDevice, ss));
         CK(cudaEventRecord(h->ev_start, ss));
         CK(cudaStreamWaitEvent(st, h->ev_start, 0));
         h->u = 0;
@@ -641,7 +662,9 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     }
     // grids of the main stream leave room for the side-stream LMS (one SM
     // per stream) when it runs beside them
-    const int avail = (L >= 2 && h->lms_block == 1) ? std::max(sm_count() / 2, sm_count() - S) : sm_count();
+    const int chains = (h->lms_start && L >= 2) ? L : 1;
+    const int avail = (L >= 2 && h->lms_block == 1) ? std::max(sm_count() / 2, sm_count() - chains * S) : sm_count();
+    const int R = ring_size(h);
     if (h->sigma2_fixed > 0 && h->sig_fixed_up != h->sigma2_fixed) {
         // uploaded when it changes (demaps of an earlier call may still read it)
         h->h_sig.assign(S, h->sigma2_fixed);
@@ -676,7 +699,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     CK(cudaStreamWaitEvent(ds, h->ev_setup, 0));
     for (long n = b0; n < b1; ++n) {
         const long k0 = n * Nb, k1 = std::min(k0 + Nb, N);
-        if (L >= 2 && n >= L) CK(cudaStreamWaitEvent(st, h->ev_lms[(n - L) % (L + 1)], 0));
+        if (L >= 2 && n >= L) CK(cudaStreamWaitEvent(st, h->ev_lms[(n - L) % R], 0));
         // W_n = U_{n-lag}; for n < lag the slot read has not been written since start-up (W_0)
         const float2 *wn = slot(h, n - L);
         cudaEvent_t blk0 = nullptr;
@@ -730,26 +753,30 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         CK(cudaEventRecord(h->ev_unwrap, ds));
         cudaStream_t ls = st;
         if (L >= 2) {
-            CK(cudaStreamWaitEvent(h->side, h->ev_unwrap, 0));
-            ls = h->side;
+            const int r = (int)(n % chains);
+            ls = r == 0 ? h->side : h->side_x[r - 1];
+            CK(cudaStreamWaitEvent(ls, h->ev_unwrap, 0));
         } else {
             CK(cudaStreamWaitEvent(st, h->ev_unwrap, 0));
         }
+        // the update starts from U_{n-1} (one chain) or from W_n = U_{n-lag}
+        const float2 *u_in = slot(h, chains > 1 ? n - L : n - 1);
         if (h->lms_block > 1)
             STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
-                  launch_lms_block(h->x, ns, slot(h, n - 1), slot(h, n), k0, (int)span, h->pcode, N, 2, h->u,
+                  launch_lms_block(h->x, ns, u_in, slot(h, n), k0, (int)span, h->pcode, N, 2, h->u,
                                    (int)h->n_cma, (float)h->mu, h->lms_block, S, T, f, ls, h->prec, h->wl));
         else
             STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
-                  launch_lms(h->x, ns, slot(h, n - 1), slot(h, n), k0, (int)span, h->pcode, N, 2, 1,
+                  launch_lms(h->x, ns, u_in, slot(h, n), k0, (int)span, h->pcode, N, 2, 1,
                              h->u, (int)h->n_cma, (float)h->mu, nullptr, 0, S, T, f, ls, h->prec, h->wl));
-        if (L >= 2) CK(cudaEventRecord(h->ev_lms[n % (L + 1)], h->side));
+        if (L >= 2) CK(cudaEventRecord(h->ev_lms[n % R], ls));
         h->u += span;
         h->blocks_done = n + 1;
     }
     // the caller's stream sees the demaps (LLRs, counters, carries) done
     if (join && b1 > b0) CK(cudaStreamWaitEvent(st, h->ev_dm[(int)((b1 - 1) & 1)], 0));
-    if (join && L >= 2 && b1 > b0) CK(cudaStreamWaitEvent(st, h->ev_lms[(b1 - 1) % (L + 1)], 0));
+    if (join && L >= 2)
+        for (long n = std::max(b0, b1 - chains); n < b1; ++n) CK(cudaStreamWaitEvent(st, h->ev_lms[n % R], 0));
     return RX_OK;
 }
 
@@ -795,6 +822,7 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     else if (k == "cma_passes") { rc = as_int(0, 16, t); h->cma_passes = (int)t; }
     else if (k == "n_cma") { rc = as_int(0, 1L << 40, t); h->n_cma = t; }
     else if (k == "lms_block") { rc = as_int(1, 64, t); h->lms_block = (int)t; }
+    else if (k == "lms_start") { rc = as_int(0, 1, t); h->lms_start = (int)t; }
     else if (k == "widely_linear") { rc = as_int(0, 1, t); h->wl = (int)t; h->started = false; }
     else if (k == "n_train") { rc = as_int(0, 20000, t); h->n_train = t; }
     else if (k == "train_passes") { rc = as_int(0, 64, t); h->train_passes = (int)t; }
@@ -908,6 +936,8 @@ void rx_destroy(rx_handle *h) {
     if (!h) return;
     if (h->st) cudaStreamSynchronize(h->st);
     if (h->side) { cudaStreamSynchronize(h->side); cudaStreamDestroy(h->side); }
+    for (auto &x : h->side_x)
+        if (x) { cudaStreamSynchronize(x); cudaStreamDestroy(x); }
     if (h->cp_in) { cudaStreamSynchronize(h->cp_in); cudaStreamDestroy(h->cp_in); }
     if (h->cp_out) { cudaStreamSynchronize(h->cp_out); cudaStreamDestroy(h->cp_out); }
     if (h->ev_in) cudaEventDestroy(h->ev_in);
@@ -958,6 +988,7 @@ int rx_get_param(const rx_handle *h, const char *key, double *value) {
     else if (k == "cma_passes") *value = h->cma_passes;
     else if (k == "n_cma") *value = (double)h->n_cma;
     else if (k == "lms_block") *value = h->lms_block;
+    else if (k == "lms_start") *value = h->lms_start;
     else if (k == "widely_linear") *value = h->wl;
     else if (k == "n_train") *value = (double)h->n_train;
     else if (k == "train_passes") *value = h->train_passes;
@@ -1382,6 +1413,8 @@ int rx_set_state(rx_handle *h, const void *buf, size_t len) {
     const unsigned char *in = static_cast<const unsigned char *>(buf);
     CK(cudaStreamSynchronize(h->st));
     if (h->side) CK(cudaStreamSynchronize(h->side));
+    for (auto x : h->side_x)
+        if (x) CK(cudaStreamSynchronize(x));
     const size_t tapsz = sizeof(float2) * (size_t)S * 4 * T;
     for (int j = 0; j < L; ++j)
         CK(cudaMemcpy(slot(h, n - L + j), in + lay.taps + j * tapsz, tapsz, cudaMemcpyHostToDevice));

@@ -455,9 +455,24 @@ def test_chain_end_to_end(case):
     resumes, lag blocks later, from the oracle's state (rx_set_state).  Every
     row is compared, against the envelope of the LLRs that the valid choices
     at BPS near-ties allow (exactly the oracle's LLR where a block has none)."""
-    rx = _rx()
     st, p, res = _oracle_run(case)
-    r = _receiver(case)
+    _e2e_check(case, st, p, res, _receiver(case))
+
+
+@pytest.mark.parametrize("case", ["qpsk80km", "qam16", "gs1000km"])
+def test_chain_end_to_end_independent_lms_chains(case):
+    """lms_start = 1 at lag 3: the update of block n starts from the taps
+    that equalised it, and the three interleaved chains run concurrently on
+    three streams; the same protocol against the oracle's schedule."""
+    st, _, _ = _oracle_run(case)
+    p = _params(case)
+    p.lag, p.lms_start = 3, 1
+    res = chain.run_chain(st.rx, oracle_format(CASES[case][0]), p, ref_bits=st.bits)
+    _e2e_check(case, st, p, res, _receiver(case, lag=3, lms_start=1))
+
+
+def _e2e_check(case, st, p, res, r):
+    rx = _rx()
     fmt = oracle_format(CASES[case][0])
     r.set_reference(_dev(st.bits[None]))
     samples = _dev(st.rx[None])
