@@ -53,7 +53,7 @@ BPS_TRAFFIC = {"bytes": 9462016, "sources": {
 # DRAM bytes per launch of the KK front-end and of the static equaliser on
 # 32 x 2^22 samples (ncu, dram__bytes_read.sum + dram__bytes_write.sum)
 KK_TRAFFIC = {"bytes": 1322521256, "sources": {
-    "paper_2108_07004_gb300/csrc/k_kk.cu": "2b34615114016bb54bc3f99f7d62f3f93f418ddd041ee280a1b1dfce8c09016c",
+    "paper_2108_07004_gb300/csrc/k_kk.cu": "8667bb3ed4ad43300d87bdc8d8d547e87dd84ebd341a9a4a3b2772f26a0b842c",
     "paper_2108_07004_gb300/csrc/k_kk.h": "05cdf23e99f0a71be65778a0c3732065e56779d3321528217a13afbb237b5906",
     "paper_2108_07004_gb300/csrc/fft_dev.h": "92a928291a79b5288f304fd8c6240edefe3569028d1f823498bb1d7ee0a7ac28"}}
 FDE_TRAFFIC = {"bytes": 1580040768, "sources": {
