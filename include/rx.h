@@ -113,6 +113,7 @@ void rx_destroy(rx_handle *h);                      /* NULL-safe */
  *   (<= 20000), "train_passes" [3],
  *   "sigma2" [0 = estimate per block], "skip_head" [4096],
  *   "skip_tail" [512], "streams" [1], "rolloff" [0.1],
+ *   "cd_ps_per_nm" [the value given to rx_create]: the dispersion to undo,
  *   "matched_filter" [1]: 0 leaves the root-raised-cosine matched filter
  *   out of the CDC's spectral multiply, for input that an earlier stage has
  *   already filtered (the static equaliser after the KK front-end, Sec. 2;
@@ -348,9 +349,13 @@ typedef struct {
 } rx_request;
 
 /* A server admits queued requests in arrival order while fewer than
- * max_slots run and the running ones' device-memory estimates (about 52 B
+ * max_slots run and the running ones' device-memory estimates (about 53 B
  * per symbol plus 1 MiB) leave room in mem_budget_bytes; each admitted
- * request gets its own handle and CUDA stream, and every step issues one
+ * request gets a handle and CUDA stream (a finished request's, kept idle for
+ * the next request with the same format, symbol rate, sps, taps and test
+ * phases, so that no device memory is freed while others run; idle handles
+ * count against the budget and are destroyed when room is needed), and
+ * every step issues one
  * block of every running request, so requests that arrived at different
  * times overlap on the device (the paper's multiple processing streams,
  * Sec. 2).  A finished request frees its slot and memory at the next step.

@@ -122,6 +122,7 @@ struct rx_handle {
     // reference bits left in host memory (rx_set_reference_host): copied in
     // with the next host-entry call, group by group, into ref_bits
     const uint8_t *ref_host = nullptr;
+    size_t ref_cap = 0;                       // reflab_t entries the label buffer holds
     uint8_t *ref_bits = nullptr;
     size_t ref_bits_cap = 0;
     std::vector<cudaEvent_t> ev_lms;     // one per tap-ring slot: the LMS that wrote it is done
@@ -831,6 +832,7 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     else if (k == "skip_tail") { rc = as_int(0, 1L << 40, t); h->skip_tail = t; }
     else if (k == "streams") { rc = as_int(1, 4096, t); h->streams = (int)t; }
     else if (k == "rolloff") { if (!(v > 0 && v <= 1)) return fail(RX_EINVAL, "rolloff out of range"); h->rolloff = v; h->tables_dirty = true; }
+    else if (k == "cd_ps_per_nm") { if (!std::isfinite(v)) return fail(RX_EINVAL, "cd_ps_per_nm must be finite"); h->cd = v; h->tables_dirty = true; }
     else if (k == "matched_filter") { if (v != 0 && v != 1) return fail(RX_EINVAL, "matched_filter is 0 or 1"); h->matched_filter = v != 0; h->tables_dirty = true; }
     else if (k == "wavelength_nm") { if (!(v > 100 && v < 10000)) return fail(RX_EINVAL, "wavelength out of range"); h->wavelength = v * 1e-9; h->tables_dirty = true; }
     else if (k == "profile") { rc = as_int(0, 2, t); h->profile = (int)t; }
@@ -1123,12 +1125,14 @@ int rx_format_info(const rx_handle *h, int *dims, int *m, int *M) {
 int rx_set_reference(rx_handle *h, const uint8_t *bits, size_t n_sym) {
     if (!h || (!bits && n_sym)) return fail(RX_EINVAL, "NULL argument");
     const int S = h->streams;
-    if (h->ref && (h->ref_n != (long)n_sym || h->ref_s != S)) { cudaFree(h->ref); h->ref = nullptr; }
+    // the label buffer is kept while it is large enough (no free, which
+    // would synchronise the device, when a handle is reused)
+    if (h->ref && h->ref_cap < (size_t)S * n_sym) { cudaFree(h->ref); h->ref = nullptr; h->ref_cap = 0; }
     h->ref_n = (long)n_sym;
     h->ref_s = S;
     h->ref_host = nullptr;
     if (!n_sym) return RX_OK;
-    if (!h->ref) CK(cudaMalloc(&h->ref, sizeof(reflab_t) * (size_t)S * n_sym));
+    if (!h->ref) { CK(cudaMalloc(&h->ref, sizeof(reflab_t) * (size_t)S * n_sym)); h->ref_cap = (size_t)S * n_sym; }
     CK(launch_ref_labels(bits, h->ref, (long)n_sym, S, h->fmt.m, h->fmt.dims, h->fmt.m_pol, h->st));
     h->started = false;
     return RX_OK;
@@ -1137,10 +1141,10 @@ int rx_set_reference(rx_handle *h, const uint8_t *bits, size_t n_sym) {
 int rx_set_reference_host(rx_handle *h, const uint8_t *bits, size_t n_sym) {
     if (!h || !bits || !n_sym) return fail(RX_EINVAL, "NULL argument");
     const int S = h->streams;
-    if (h->ref && (h->ref_n != (long)n_sym || h->ref_s != S)) { cudaFree(h->ref); h->ref = nullptr; }
+    if (h->ref && h->ref_cap < (size_t)S * n_sym) { cudaFree(h->ref); h->ref = nullptr; h->ref_cap = 0; }
     h->ref_n = (long)n_sym;
     h->ref_s = S;
-    if (!h->ref) CK(cudaMalloc(&h->ref, sizeof(reflab_t) * (size_t)S * n_sym));
+    if (!h->ref) { CK(cudaMalloc(&h->ref, sizeof(reflab_t) * (size_t)S * n_sym)); h->ref_cap = (size_t)S * n_sym; }
     const size_t need = (size_t)S * n_sym * h->fmt.m;
     if (h->ref_bits_cap < need) {
         cudaFree(h->ref_bits);

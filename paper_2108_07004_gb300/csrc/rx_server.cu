@@ -13,6 +13,7 @@
 //
 // Host code only; everything on the device goes through the public entry
 // points (rx_create, rx_process_blocks, rx_get_stats, ...).
+#include <algorithm>
 #include <cstring>
 #include <deque>
 #include <memory>
@@ -41,15 +42,50 @@ struct Req {
     size_t mem = 0;
     rx_stats stats{};
     std::string err;
+    std::string key;                    // handle_key of the request
+    long cap_n = 0;                     // symbols the handle's buffers hold (reused handles: >= N)
     double t_submit = 0, t_admit = 0, t_done = 0;   // server step counters
 };
 
-size_t estimate_bytes(const rx_request &r) {
+size_t estimate_bytes_n(size_t N) {
     // per symbol: CDC output 32 B, FIR output 16 B, phase index 1 B, phase
     // code 2 B, reference labels 2 B; plus tables, taps ring and partials
-    const size_t N = r.n_samples / 2;
     return 53 * N + (1u << 20);
 }
+
+size_t estimate_bytes(const rx_request &r) { return estimate_bytes_n(r.n_samples / 2); }
+
+// What rx_create fixes: requests with equal keys can share a handle (the
+// dispersion and the FFT / block settings are parameters set per request).
+std::string handle_key(const rx_request &r, const std::vector<float> &pts, const std::vector<uint32_t> &labs) {
+    std::string k;
+    auto put = [&k](const void *p, size_t n) { k.append(static_cast<const char *>(p), n); };
+    put(&r.format.kind, sizeof r.format.kind);
+    put(&r.format.dims, sizeof r.format.dims);
+    put(&r.format.m_bits, sizeof r.format.m_bits);
+    put(&r.format.sym_order, sizeof r.format.sym_order);
+    put(&r.symbol_rate, sizeof r.symbol_rate);
+    put(&r.sps, sizeof r.sps);
+    put(&r.taps, sizeof r.taps);
+    put(&r.bps_phases, sizeof r.bps_phases);
+    if (r.format.kind == RX_FMT_CUSTOM) {
+        put(pts.data(), sizeof(float) * pts.size());
+        put(labs.data(), sizeof(uint32_t) * labs.size());
+    }
+    return k;
+}
+
+// A finished request's handle, kept with its stream and buffers for the
+// next compatible request: destroying a handle frees device memory, which
+// synchronises the whole device and would stall every running request.
+struct Pooled {
+    std::string key;
+    rx_handle *h = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t done = nullptr;
+    long cap_n = 0;      // symbols its buffers hold
+    size_t mem = 0;
+};
 
 }  // namespace
 
@@ -61,6 +97,8 @@ struct rx_server {
     std::deque<Req *> queue;
     std::vector<Req *> active;
     std::unordered_map<uint64_t, std::unique_ptr<Req>> all;
+    std::vector<Pooled> pool;           // idle handles, oldest first
+    size_t pooled = 0;                  // their memory estimates
     int max_active_seen = 0;
 };
 
@@ -73,33 +111,103 @@ int srv_fail(int code, const std::string &msg) {
     return code;
 }
 
+void destroy_handle(rx_handle *h, cudaStream_t st, cudaEvent_t done) {
+    if (h) rx_destroy(h);
+    if (done) cudaEventDestroy(done);
+    if (st) cudaStreamDestroy(st);
+}
+
 void release(rx_server *s, Req *q) {
-    if (q->h) { rx_destroy(q->h); q->h = nullptr; }
-    if (q->done) { cudaEventDestroy(q->done); q->done = nullptr; }
-    if (q->st) { cudaStreamDestroy(q->st); q->st = nullptr; }
+    if (q->h && q->state == Q_DONE) {
+        // keep the handle for a later request with the same key
+        Pooled p;
+        p.key = q->key;
+        p.h = q->h;
+        p.st = q->st;
+        p.done = q->done;
+        p.cap_n = std::max(q->cap_n, q->N);
+        p.mem = estimate_bytes_n((size_t)p.cap_n);
+        s->pool.push_back(p);
+        s->pooled += p.mem;
+    } else {
+        destroy_handle(q->h, q->st, q->done);
+    }
+    q->h = nullptr;
+    q->st = nullptr;
+    q->done = nullptr;
     s->used -= q->mem;
+}
+
+// index of the pooled handle for q (same key; the smallest that holds q's
+// symbols, else the largest), -1 if none
+int find_pooled(const rx_server *s, const Req *q) {
+    int best = -1;
+    for (int i = 0; i < (int)s->pool.size(); ++i) {
+        const Pooled &p = s->pool[i];
+        if (p.key != q->key) continue;
+        if (best < 0) { best = i; continue; }
+        const Pooled &b = s->pool[best];
+        const bool fits = p.cap_n >= q->N, bfits = b.cap_n >= q->N;
+        if ((fits && (!bfits || p.cap_n < b.cap_n)) || (!fits && !bfits && p.cap_n > b.cap_n)) best = i;
+    }
+    return best;
+}
+
+// true if q can be admitted within the budget, destroying idle handles
+// (oldest first, never the one q will reuse) while that is what is missing
+bool make_room(rx_server *s, const Req *q) {
+    const int reuse = find_pooled(s, q);
+    const size_t reuse_mem = reuse >= 0 ? s->pool[reuse].mem : 0;
+    auto fits = [&] { return s->used + (s->pooled - reuse_mem) + q->mem <= s->budget; };
+    for (size_t i = 0; !fits() && i < s->pool.size();) {
+        if ((int)i == find_pooled(s, q)) { ++i; continue; }
+        Pooled p = s->pool[i];
+        s->pool.erase(s->pool.begin() + (long)i);
+        s->pooled -= p.mem;
+        destroy_handle(p.h, p.st, p.done);
+    }
+    return fits();
 }
 
 // create the handle of an admitted request; false (and FAILED) on error
 bool admit(rx_server *s, Req *q) {
-    rx_format f = q->r.format;
-    if (f.kind == RX_FMT_CUSTOM) {
-        f.points = q->points.data();
-        f.labels = q->labels.data();
-    }
-    q->h = rx_create(&f, q->r.symbol_rate, q->r.sps, q->r.cd_ps_per_nm, q->r.taps, q->r.bps_phases);
-    if (!q->h) {
-        q->err = rx_last_error();
-        q->state = Q_FAILED;
-        return false;
-    }
     int rc = RX_OK;
-    if (q->r.fft) rc |= rx_set_param(q->h, "fft", q->r.fft);
-    if (q->r.overlap) rc |= rx_set_param(q->h, "overlap", q->r.overlap);
-    if (q->r.block) rc |= rx_set_param(q->h, "block", q->r.block);
-    if (q->r.n_pre) rc |= rx_set_param(q->h, "n_pre", q->r.n_pre);
-    if (rc == RX_OK && cudaStreamCreateWithFlags(&q->st, cudaStreamNonBlocking) != cudaSuccess) rc = RX_ECUDA;
-    if (rc == RX_OK && cudaEventCreateWithFlags(&q->done, cudaEventDisableTiming) != cudaSuccess) rc = RX_ECUDA;
+    const int reuse = find_pooled(s, q);
+    if (reuse >= 0) {
+        // a finished request's handle: every per-request setting is set
+        // again (the defaults where the request leaves one at 0), which also
+        // resets its stream state
+        Pooled p = s->pool[reuse];
+        s->pool.erase(s->pool.begin() + reuse);
+        s->pooled -= p.mem;
+        q->h = p.h;
+        q->st = p.st;
+        q->done = p.done;
+        q->cap_n = p.cap_n;
+        rc |= rx_set_param(q->h, "cd_ps_per_nm", q->r.cd_ps_per_nm);
+        rc |= rx_set_param(q->h, "fft", q->r.fft ? q->r.fft : 1024);
+        rc |= rx_set_param(q->h, "overlap", q->r.overlap ? q->r.overlap : 256);
+        rc |= rx_set_param(q->h, "block", q->r.block ? q->r.block : 4096);
+        rc |= rx_set_param(q->h, "n_pre", q->r.n_pre ? q->r.n_pre : 2048);
+    } else {
+        rx_format f = q->r.format;
+        if (f.kind == RX_FMT_CUSTOM) {
+            f.points = q->points.data();
+            f.labels = q->labels.data();
+        }
+        q->h = rx_create(&f, q->r.symbol_rate, q->r.sps, q->r.cd_ps_per_nm, q->r.taps, q->r.bps_phases);
+        if (!q->h) {
+            q->err = rx_last_error();
+            q->state = Q_FAILED;
+            return false;
+        }
+        if (q->r.fft) rc |= rx_set_param(q->h, "fft", q->r.fft);
+        if (q->r.overlap) rc |= rx_set_param(q->h, "overlap", q->r.overlap);
+        if (q->r.block) rc |= rx_set_param(q->h, "block", q->r.block);
+        if (q->r.n_pre) rc |= rx_set_param(q->h, "n_pre", q->r.n_pre);
+        if (rc == RX_OK && cudaStreamCreateWithFlags(&q->st, cudaStreamNonBlocking) != cudaSuccess) rc = RX_ECUDA;
+        if (rc == RX_OK && cudaEventCreateWithFlags(&q->done, cudaEventDisableTiming) != cudaSuccess) rc = RX_ECUDA;
+    }
     if (rc == RX_OK) rc = rx_set_stream(q->h, q->st);
     if (rc == RX_OK && q->r.ref_bits) rc = rx_set_reference(q->h, q->r.ref_bits, q->N);
     if (rc != RX_OK) {
@@ -139,8 +247,10 @@ void rx_server_destroy(rx_server *s) {
     if (!s) return;
     for (Req *q : s->active) {
         if (q->st) cudaStreamSynchronize(q->st);
-        release(s, q);
+        destroy_handle(q->h, q->st, q->done);
+        q->h = nullptr;
     }
+    for (Pooled &p : s->pool) destroy_handle(p.h, p.st, p.done);
     delete s;
 }
 
@@ -160,6 +270,7 @@ int rx_server_submit(rx_server *s, const rx_request *r, uint64_t *id) {
     }
     q->N = (long)(r->n_samples / 2);
     q->mem = estimate_bytes(*r);
+    q->key = handle_key(*r, q->points, q->labels);
     if (q->mem > s->budget)
         return srv_fail(RX_EINVAL, "request needs about " + std::to_string(q->mem) +
                                        " bytes, more than the whole budget");
@@ -187,8 +298,7 @@ int rx_server_step(rx_server *s, int *n_active) {
         }
     }
     // admit from the head of the queue while a slot and memory are free
-    while (!s->queue.empty() && (int)s->active.size() < s->max_slots &&
-           s->used + s->queue.front()->mem <= s->budget) {
+    while (!s->queue.empty() && (int)s->active.size() < s->max_slots && make_room(s, s->queue.front())) {
         Req *q = s->queue.front();
         s->queue.pop_front();
         if (admit(s, q)) s->active.push_back(q);
