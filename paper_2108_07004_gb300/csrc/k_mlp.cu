@@ -3,7 +3,8 @@
 // (Re z_X, Im z_X, Re z_Y, Im z_Y); output o = sigma^2 * LLR (LLR > 0 means
 // bit 0), trained with the mean binary cross-entropy over the bits and Adam.
 //
-// Kernels (batch of n samples):
+// Kernels (batch of n samples; inference uses infer_tc_kernel, the tensor-core
+// forward pass below, training the float32 kernels):
 //   layer1_kernel      a1 = x W1^T + b1, h1 = gelu(a1)
 //   gemm_kernel        tiled float32 GEMM (64 x 64 tiles, 4 x 4 per thread)
 //                      with bfloat16 weight operands and fused epilogues:
@@ -18,6 +19,7 @@
 //                      bfloat16 copies the layers use
 // Every reduction over the batch is in a fixed order, so a step gives the
 // same bits on every run.
+#include <algorithm>
 #include <cmath>
 
 #include "rx_internal.h"
@@ -169,6 +171,141 @@ layer3_kernel(const float *__restrict__ h2, long n, const uint16_t *__restrict__
         }
     }
     if (bits) loss_s[s] = ls * scale;
+}
+
+// ---------------------------------------------------------------------------
+// Inference on the tensor cores: one warp per 16 samples, the 128 x 128
+// layer as bfloat16 mma.sync m16n8k16 with float32 accumulation.  The
+// weights are bfloat16 already; each float32 activation h is split into
+// three bfloat16 terms, hi = bf16(h), mid = bf16(h - hi), lo = bf16(h - hi -
+// mid) (what is left is below 2^-24 |h|, float32's own rounding), and the
+// layer is the three products W hi + W mid + W lo, each exact in the float32
+// accumulator's inputs.  Layer 1 is computed straight into the A
+// fragments (lane: rows g = lane/4 and g + 8, columns 2 (lane % 4) + {0, 1}
+// and + 8 of every 16-column step); the accumulators of layer 2 (rows g,
+// g + 8, columns 2 (lane % 4) + {0, 1} of every 8-column tile) feed layer 3
+// as per-lane partial sums reduced over the four lanes of a row.
+// Persistent blocks stage W2 once (rows padded to 136 bfloat16, so that the
+// B-fragment loads of a warp hit 32 banks) and loop over 64-sample tiles.
+// ---------------------------------------------------------------------------
+constexpr int kW2P = H + 8;   // padded row of the staged W2 (bfloat16)
+
+__device__ __forceinline__ unsigned pack_bf16(uint16_t lo_col, uint16_t hi_col) {
+    return (unsigned)lo_col | ((unsigned)hi_col << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__global__ void __launch_bounds__(128)
+infer_tc_kernel(const float *__restrict__ x, const float *__restrict__ sigma2, long n,
+                const uint16_t *__restrict__ W1q, const float *__restrict__ b1, const uint16_t *__restrict__ W2q,
+                const float *__restrict__ b2, const uint16_t *__restrict__ W3q, const float *__restrict__ b3,
+                float *__restrict__ llr) {
+    __shared__ __align__(16) uint16_t w2[H * kW2P];
+    __shared__ float w1[H][4], bb1[H], bb2[H], w3[NOUT][H], bb3[NOUT];
+    for (int i = threadIdx.x; i < H * H; i += blockDim.x) w2[(i / H) * kW2P + (i % H)] = W2q[i];
+    for (int i = threadIdx.x; i < H * 4; i += blockDim.x) w1[i / 4][i % 4] = bf16_to_f(W1q[i]);
+    for (int i = threadIdx.x; i < NOUT * H; i += blockDim.x) w3[i / H][i % H] = bf16_to_f(W3q[i]);
+    for (int i = threadIdx.x; i < H; i += blockDim.x) { bb1[i] = b1[i]; bb2[i] = b2[i]; }
+    if (threadIdx.x < NOUT) bb3[threadIdx.x] = b3[threadIdx.x];
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, c0 = 2 * (lane & 3);
+    const long n_tiles = (n + 63) / 64;
+    for (long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const long r0 = tile * 64 + warp * 16 + g, r1 = r0 + 8;     // this lane's two samples
+        float xa[4], xb[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            xa[c] = r0 < n ? x[r0 * 4 + c] : 0.f;
+            xb[c] = r1 < n ? x[r1 * 4 + c] : 0.f;
+        }
+        // layer 1 into the A fragments (hi and lo) of the 8 k-steps
+        unsigned ah[8][4], am[8][4], al[8][4];
+#pragma unroll
+        for (int kk = 0; kk < 8; ++kk) {
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {          // columns + 0 / + 8
+                uint16_t hr[2][2], mr[2][2], lr[2][2];       // [row g / g+8][col +0 / +1]
+#pragma unroll
+                for (int e = 0; e < 2; ++e) {
+                    const int j = kk * 16 + half * 8 + c0 + e;
+                    float pa = bb1[j], pb = bb1[j];
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) {
+                        pa = fmaf(xa[c], w1[j][c], pa);
+                        pb = fmaf(xb[c], w1[j][c], pb);
+                    }
+                    const float hv[2] = {gelu(pa), gelu(pb)};
+#pragma unroll
+                    for (int r = 0; r < 2; ++r) {
+                        hr[r][e] = f_to_bf16(hv[r]);
+                        const float rest = hv[r] - bf16_to_f(hr[r][e]);
+                        mr[r][e] = f_to_bf16(rest);
+                        lr[r][e] = f_to_bf16(rest - bf16_to_f(mr[r][e]));
+                    }
+                }
+                ah[kk][2 * half] = pack_bf16(hr[0][0], hr[0][1]);
+                ah[kk][2 * half + 1] = pack_bf16(hr[1][0], hr[1][1]);
+                am[kk][2 * half] = pack_bf16(mr[0][0], mr[0][1]);
+                am[kk][2 * half + 1] = pack_bf16(mr[1][0], mr[1][1]);
+                al[kk][2 * half] = pack_bf16(lr[0][0], lr[0][1]);
+                al[kk][2 * half + 1] = pack_bf16(lr[1][0], lr[1][1]);
+            }
+        }
+        // layer 2 per 8-column tile, then its GELU and layer 3's partial sums
+        float o0[NOUT], o1[NOUT];
+#pragma unroll
+        for (int k = 0; k < NOUT; ++k) { o0[k] = 0.f; o1[k] = 0.f; }
+#pragma unroll 2
+        for (int nt = 0; nt < 16; ++nt) {
+            float acc[4] = {0.f, 0.f, 0.f, 0.f};
+            const uint16_t *wrow = w2 + (nt * 8 + g) * kW2P + c0;
+#pragma unroll
+            for (int kk = 0; kk < 8; ++kk) {
+                const unsigned bq0 = *reinterpret_cast<const unsigned *>(wrow + kk * 16);
+                const unsigned bq1 = *reinterpret_cast<const unsigned *>(wrow + kk * 16 + 8);
+                mma_bf16(acc, al[kk], bq0, bq1);      // smallest terms first
+                mma_bf16(acc, am[kk], bq0, bq1);
+                mma_bf16(acc, ah[kk], bq0, bq1);
+            }
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int j = nt * 8 + c0 + e;
+                const float ha = gelu(acc[e] + bb2[j]), hb = gelu(acc[2 + e] + bb2[j]);
+#pragma unroll
+                for (int k = 0; k < NOUT; ++k) {
+                    o0[k] = fmaf(ha, w3[k][j], o0[k]);
+                    o1[k] = fmaf(hb, w3[k][j], o1[k]);
+                }
+            }
+        }
+        // the four lanes of a row hold disjoint columns: sum them
+#pragma unroll
+        for (int k = 0; k < NOUT; ++k) {
+            o0[k] += __shfl_xor_sync(0xffffffffu, o0[k], 1);
+            o0[k] += __shfl_xor_sync(0xffffffffu, o0[k], 2);
+            o1[k] += __shfl_xor_sync(0xffffffffu, o1[k], 1);
+            o1[k] += __shfl_xor_sync(0xffffffffu, o1[k], 2);
+        }
+        if ((lane & 3) == 0) {
+            if (r0 < n) {
+                const float inv = 1.f / sigma2[r0];
+#pragma unroll
+                for (int k = 0; k < NOUT; ++k) llr[r0 * NOUT + k] = (o0[k] + bb3[k]) * inv;
+            }
+            if (r1 < n) {
+                const float inv = 1.f / sigma2[r1];
+#pragma unroll
+                for (int k = 0; k < NOUT; ++k) llr[r1 * NOUT + k] = (o1[k] + bb3[k]) * inv;
+            }
+        }
+    }
 }
 
 // da2[s][j] = (sum_k dO[s][k] W3[k][j]) * gelu'(a2[s][j])
@@ -354,5 +491,10 @@ cudaError_t mlp_adam(MlpDev &d, int t, float lr, cudaStream_t st) {
 }
 
 cudaError_t mlp_infer(MlpDev &d, const float *x, const float *s2, long n, float *llr, cudaStream_t st) {
-    return mlp_forward(d, x, s2, nullptr, n, llr, st);
+    if (n <= 0) return cudaSuccess;
+    const long tiles = (n + 63) / 64;
+    const int grid = (int)std::min<long>(tiles, 4L * sm_count());
+    infer_tc_kernel<<<grid, 128, 0, st>>>(x, s2, n, d.W1q, d.theta + OFF_B1, d.W2q, d.theta + OFF_B2, d.W3q,
+                                          d.theta + OFF_B3, llr);
+    return cudaGetLastError();
 }
