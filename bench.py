@@ -791,6 +791,46 @@ def run_kk_chain(args):
     print(json.dumps(line), flush=True)
 
 
+def run_mlp_infer(args):
+    """The learned demapper's inference alone (config 4's tensor-core
+    contraction): 2^24 4D-64 symbols at 12 dB with seeded He-initialised
+    weights, one rx_mlp_infer per step; the roofline counts the MLP's
+    algorithmic flops, 2 (4*128 + 128*128 + 128*6) per symbol, against the
+    measured bfloat16 tensor peak."""
+    import torch
+    from paper_2108_07004_gb300 import rx as rx_mod
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    n = args.mlp_sym
+    fmt = synth.tx_format("gs4d64")
+    rng = np.random.default_rng(synth.stream_seed(17, 0))
+    lab = rng.integers(0, 64, size=n)
+    n0 = 10 ** (-12 / 10)
+    z = fmt.points[lab] + np.sqrt(n0 / 2) * (rng.standard_normal((n, 2)) + 1j * rng.standard_normal((n, 2)))
+    x = torch.from_numpy(np.stack([z[:, 0].real, z[:, 0].imag, z[:, 1].real, z[:, 1].imag], axis=1)
+                         .astype(np.float32)).cuda()
+    s2 = torch.full((n,), n0 / 2, dtype=torch.float32, device="cuda")
+    m = rx_mod.Mlp(synth.mlp_init_params(LEARN["init_seed"]))
+    llr = torch.empty((n, 6), dtype=torch.float32, device="cuda")
+    ms = _event_ms(lambda: m.infer(x, s2, llr), args.steps, args.warmup)
+    pk, pk_kind = peaks()
+    flops = 2.0 * (4 * 128 + 128 * 128 + 128 * 6) * n
+    tf = flops / (ms * 1e-3) / 1e12
+    peak = pk.get("bf16_tflops", 1900.0)
+    line = {
+        "metric": "learned demapper inference, 4D symbols per second", "value": n / (ms * 1e-3) / 1e9,
+        "unit": "Gsym/s", "n_gpus": 1, "steps": args.steps, "warmup": max(3, args.warmup), "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 weights / f32",
+        "data": "synthetic",
+        "config": {"workload": f"mlp_4x128x128x6_infer_{n}", "symbols": n, "esn0_db": 12.0,
+                   "l2": "inputs 256 MiB, outputs 384 MiB > L2, no flush"},
+        "roofline": {"bound": "tensor", "kernel": "infer_tc_kernel", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+                     "frac": tf / peak, "traffic": None, "peak_kind": pk_kind,
+                     "note": "algorithmic flops; the kernel issues 3 products per layer-2 term (bfloat16 split)"},
+        "gpu_launches": args.steps,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_precision(args):
     import torch
     from paper_2108_07004_gb300 import rx as rx_mod
@@ -1052,11 +1092,12 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision", "serving", "block_lms", "widely_linear", "kk", "kk_chain"],
+    ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision", "serving", "block_lms", "widely_linear", "kk", "kk_chain", "mlp_infer"],
                     help="learned: train the MLP demapper on chain output, compare with the exact one; "
                          "precision: DP-QPSK chain with CDC/FIR data in float32, half and bfloat16; "
                          "serving: 64 mixed streams with Poisson arrivals through the continuous-batching server")
     ap.add_argument("--learned-sym", type=int, default=LEARN["infer_sym"])
+    ap.add_argument("--mlp-sym", type=int, default=1 << 24)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -1070,6 +1111,8 @@ def main():
         run_kk(args)
     elif args.variant == "kk_chain":
         run_kk_chain(args)
+    elif args.variant == "mlp_infer":
+        run_mlp_infer(args)
     elif args.variant == "precision":
         run_precision(args)
     elif args.variant == "serving":
