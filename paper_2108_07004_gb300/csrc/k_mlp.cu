@@ -180,9 +180,12 @@ layer3_kernel(const float *__restrict__ h2, long n, const uint16_t *__restrict__
 // three bfloat16 terms, hi = bf16(h), mid = bf16(h - hi), lo = bf16(h - hi -
 // mid) (what is left is below 2^-24 |h|, float32's own rounding), and the
 // layer is the three products W hi + W mid + W lo, each exact in the float32
-// accumulator's inputs.  Layer 1 is computed straight into the A
-// fragments (lane: rows g = lane/4 and g + 8, columns 2 (lane % 4) + {0, 1}
-// and + 8 of every 16-column step); the accumulators of layer 2 (rows g,
+// accumulator's inputs.  Layer 2 runs k-step by k-step: layer 1's 16
+// columns of the step are computed straight into the A fragments (lane:
+// rows g = lane/4 and g + 8, columns 2 (lane % 4) + {0, 1} and + 8) and
+// multiplied into the accumulators of all 16 output tiles, so only one
+// step's fragments are live (125 registers, 4 blocks per SM); the
+// accumulators of layer 2 (rows g,
 // g + 8, columns 2 (lane % 4) + {0, 1} of every 8-column tile) feed layer 3
 // as per-lane partial sums reduced over the four lanes of a row.
 // Persistent blocks stage W2 once (rows padded to 136 bfloat16, so that the
@@ -202,7 +205,7 @@ __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], 
         : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(128, 4)
 infer_tc_kernel(const float *__restrict__ x, const float *__restrict__ sigma2, long n,
                 const uint16_t *__restrict__ W1q, const float *__restrict__ b1, const uint16_t *__restrict__ W2q,
                 const float *__restrict__ b2, const uint16_t *__restrict__ W3q, const float *__restrict__ b3,
@@ -225,10 +228,16 @@ infer_tc_kernel(const float *__restrict__ x, const float *__restrict__ sigma2, l
             xa[c] = r0 < n ? x[r0 * 4 + c] : 0.f;
             xb[c] = r1 < n ? x[r1 * 4 + c] : 0.f;
         }
-        // layer 1 into the A fragments (hi and lo) of the 8 k-steps
-        unsigned ah[8][4], am[8][4], al[8][4];
+        // layer 2 k-step by k-step: that step's 16 columns of layer 1 are made
+        // straight into the A fragments (three bfloat16 terms), then multiplied
+        // into the accumulators of all 16 output tiles, so only one step's
+        // fragments are live
+        float acc[16][4];
 #pragma unroll
+        for (int nt = 0; nt < 16; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+#pragma unroll 1
         for (int kk = 0; kk < 8; ++kk) {
+            unsigned ah[4], am[4], al[4];
 #pragma unroll
             for (int half = 0; half < 2; ++half) {          // columns + 0 / + 8
                 uint16_t hr[2][2], mr[2][2], lr[2][2];       // [row g / g+8][col +0 / +1]
@@ -250,34 +259,33 @@ infer_tc_kernel(const float *__restrict__ x, const float *__restrict__ sigma2, l
                         lr[r][e] = f_to_bf16(rest - bf16_to_f(mr[r][e]));
                     }
                 }
-                ah[kk][2 * half] = pack_bf16(hr[0][0], hr[0][1]);
-                ah[kk][2 * half + 1] = pack_bf16(hr[1][0], hr[1][1]);
-                am[kk][2 * half] = pack_bf16(mr[0][0], mr[0][1]);
-                am[kk][2 * half + 1] = pack_bf16(mr[1][0], mr[1][1]);
-                al[kk][2 * half] = pack_bf16(lr[0][0], lr[0][1]);
-                al[kk][2 * half + 1] = pack_bf16(lr[1][0], lr[1][1]);
+                ah[2 * half] = pack_bf16(hr[0][0], hr[0][1]);
+                ah[2 * half + 1] = pack_bf16(hr[1][0], hr[1][1]);
+                am[2 * half] = pack_bf16(mr[0][0], mr[0][1]);
+                am[2 * half + 1] = pack_bf16(mr[1][0], mr[1][1]);
+                al[2 * half] = pack_bf16(lr[0][0], lr[0][1]);
+                al[2 * half + 1] = pack_bf16(lr[1][0], lr[1][1]);
+            }
+#pragma unroll
+            for (int nt = 0; nt < 16; ++nt) {
+                const uint16_t *wrow = w2 + (nt * 8 + g) * kW2P + c0 + kk * 16;
+                const unsigned bq0 = *reinterpret_cast<const unsigned *>(wrow);
+                const unsigned bq1 = *reinterpret_cast<const unsigned *>(wrow + 8);
+                mma_bf16(acc[nt], al, bq0, bq1);      // smallest terms first
+                mma_bf16(acc[nt], am, bq0, bq1);
+                mma_bf16(acc[nt], ah, bq0, bq1);
             }
         }
-        // layer 2 per 8-column tile, then its GELU and layer 3's partial sums
+        // GELU of layer 2 and layer 3's partial sums over this lane's columns
         float o0[NOUT], o1[NOUT];
 #pragma unroll
         for (int k = 0; k < NOUT; ++k) { o0[k] = 0.f; o1[k] = 0.f; }
-#pragma unroll 2
-        for (int nt = 0; nt < 16; ++nt) {
-            float acc[4] = {0.f, 0.f, 0.f, 0.f};
-            const uint16_t *wrow = w2 + (nt * 8 + g) * kW2P + c0;
 #pragma unroll
-            for (int kk = 0; kk < 8; ++kk) {
-                const unsigned bq0 = *reinterpret_cast<const unsigned *>(wrow + kk * 16);
-                const unsigned bq1 = *reinterpret_cast<const unsigned *>(wrow + kk * 16 + 8);
-                mma_bf16(acc, al[kk], bq0, bq1);      // smallest terms first
-                mma_bf16(acc, am[kk], bq0, bq1);
-                mma_bf16(acc, ah[kk], bq0, bq1);
-            }
+        for (int nt = 0; nt < 16; ++nt) {
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
                 const int j = nt * 8 + c0 + e;
-                const float ha = gelu(acc[e] + bb2[j]), hb = gelu(acc[2 + e] + bb2[j]);
+                const float ha = gelu(acc[nt][e] + bb2[j]), hb = gelu(acc[nt][2 + e] + bb2[j]);
 #pragma unroll
                 for (int k = 0; k < NOUT; ++k) {
                     o0[k] = fmaf(ha, w3[k][j], o0[k]);
