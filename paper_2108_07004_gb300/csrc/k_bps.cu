@@ -477,8 +477,17 @@ cudaError_t bps_launch_t(const void *y, long ys, long a, long e, long nv, int W,
     const int n_cta = (int)((e - a + kR - 1) / kR);
     const size_t smem = sizeof(float) * (RX_NCHUNK * f.B * 33 + RX_NCHUNK * f.B + 8 * f.B) + kR + 16;
     auto kern = bps_kernel<DIMS, NORB, SS>;
-    cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the dynamic shared-memory limit is raised only when a launch needs more
+    // than this device's setting so far (one host call, not one per launch)
+    static size_t set_of[64] = {};
+    int dev = 0;
+    cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
+    if (dev >= 64 || smem > set_of[dev]) {
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (err != cudaSuccess) return err;
+        if (dev < 64) set_of[dev] = smem;
+    }
     dim3 grid((unsigned)n_cta, (unsigned)n_streams);
     kern<<<grid, 256, smem, st>>>(y, ys, a, e, nv, W, bout, bst, dsum, mdsum, n_cta, chunks, sk, f);
     return cudaGetLastError();

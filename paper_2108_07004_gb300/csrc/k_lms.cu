@@ -743,16 +743,23 @@ cudaError_t lms_launch_one(const void *x, long ns, const float2 *ti, float2 *to,
                            const uint16_t *pcode, long pstride, int passes, float mu,
                            const reflab_t *ref, long rstride, int S, const FmtDev &f, cudaStream_t st, int sk, int wl) {
     auto kern = lms_kernel<T, DIMS, MODE>;
-    cudaFuncAttributes fa;
-    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    // the opt-in size is looked up and set once per device (host queries per
+    // launch cost more than the launch when a handle runs one stream)
+    static int dyn_of[64] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    int dev = 0, optin = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-    const int dyn = optin - (int)fa.sharedSizeBytes;
-    if (dyn < (int)(lms_smem_f2(T) * sizeof(float2))) return cudaErrorInvalidValue;
-    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn);
-    if (e != cudaSuccess) return e;
+    int dyn = dev < 64 ? dyn_of[dev] : 0;
+    if (dyn == 0) {
+        cudaFuncAttributes fa;
+        if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
+        int optin = 0;
+        if ((e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+        dyn = optin - (int)fa.sharedSizeBytes;
+        if (dyn < (int)(lms_smem_f2(T) * sizeof(float2))) return cudaErrorInvalidValue;
+        if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
+        if (dev < 64) dyn_of[dev] = dyn;
+    }
     kern<<<S, kThreads, dyn, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, sk, wl, f);
     return cudaGetLastError();
 }
