@@ -46,7 +46,7 @@ FP32_LANES_PER_SM, N_SM, SM_MAX_MHZ = 128, 152, 2070.0
 # (dram__bytes_read.sum + dram__bytes_write.sum); reported only while the
 # kernel's sources hash to the captured ones.
 BPS_TRAFFIC = {"bytes": 9462016, "sources": {
-    "paper_2108_07004_gb300/csrc/k_bps.cu": "b825cc820c11b9bbfcec77a62da9bd272b9ffce4178db1ca2ae44385252a405e",
+    "paper_2108_07004_gb300/csrc/k_bps.cu": "a5fea97b87708ad26ef3bcf3431491c0e200869640e53382bed68f6444c3cf94",
     "paper_2108_07004_gb300/csrc/rx_internal.h": "cc624a6c259edf506844e02973378bd952ed10bc1ed4b48e42142749b5323220"}}
 
 
