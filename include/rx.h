@@ -183,7 +183,9 @@ int rx_process(rx_handle *h, const void *samples, size_t n_samples,
  * run in groups of two: the input samples a group's CDC frames read are
  * copied in on one copy stream and its LLR rows copied out on another, so
  * the copies overlap the chain of the neighbouring groups (asynchronously
- * when the host buffers are pinned; pageable buffers also work).  Device
+ * when the host buffers are pinned; pageable buffers also work); from the
+ * second group on, a group's CDC runs on a stream of its own as soon as
+ * its samples are in.  Device
  * copies of the input and output are kept by the handle (allocated on first
  * use).  Returns when the LLRs are in llr_out. */
 int rx_process_host(rx_handle *h, const void *samples, size_t n_samples,

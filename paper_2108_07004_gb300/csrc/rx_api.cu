@@ -119,6 +119,11 @@ struct rx_handle {
     // stream waits for it before the CDC of the remaining frames)
     cudaEvent_t ev_in_rest = nullptr;
     bool wait_rest = false;
+    // host entry, groups after the first: their CDC runs on cst as soon as
+    // their samples are in (ev_in), beside the previous group's kernels
+    bool cdc_side = false;
+    cudaStream_t cst = nullptr;
+    cudaEvent_t ev_cdcg = nullptr;
     // reference bits left in host memory (rx_set_reference_host): copied in
     // with the next host-entry call, group by group, into ref_bits
     const uint8_t *ref_host = nullptr;
@@ -626,9 +631,18 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
             CK(cudaStreamWaitEvent(st, h->ev_in_rest, 0));
             h->wait_rest = false;
         }
-        if (f1 > fs)
+        if (f1 > fs && h->cdc_side && fs == f0) {
+            // frames shared with the previous group are recomputed to the
+            // same values, so its readers are not disturbed
+            CK(cudaStreamWaitEvent(h->cst, h->ev_in, 0));
+            STAGE(ST_CDC, h->cst, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, h->cst, fs,
+                                                f1, h->prec));
+            CK(cudaEventRecord(h->ev_cdcg, h->cst));
+            CK(cudaStreamWaitEvent(st, h->ev_cdcg, 0));
+        } else if (f1 > fs) {
             STAGE(ST_CDC, st, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st, fs, f1,
                                             h->prec));
+        }
     }
     if (b0 == 0) {
         const cudaStream_t ss = h->side;     // start-up stream
@@ -945,6 +959,8 @@ void rx_destroy(rx_handle *h) {
     if (h->ev_in) cudaEventDestroy(h->ev_in);
     if (h->ev_out) cudaEventDestroy(h->ev_out);
     if (h->ev_in_rest) cudaEventDestroy(h->ev_in_rest);
+    if (h->cst) { cudaStreamSynchronize(h->cst); cudaStreamDestroy(h->cst); }
+    if (h->ev_cdcg) cudaEventDestroy(h->ev_cdcg);
     if (h->ev_unwrap) cudaEventDestroy(h->ev_unwrap);
     if (h->ev_cdc0) cudaEventDestroy(h->ev_cdc0);
     if (h->ev_start) cudaEventDestroy(h->ev_start);
@@ -1199,6 +1215,8 @@ int rx_process_host(rx_handle *h, const void *samples, size_t n_samples, float *
         CK(cudaEventCreateWithFlags(&h->ev_in, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&h->ev_out, cudaEventDisableTiming));
         CK(cudaEventCreateWithFlags(&h->ev_in_rest, cudaEventDisableTiming));
+        CK(cudaStreamCreateWithFlags(&h->cst, cudaStreamNonBlocking));
+        CK(cudaEventCreateWithFlags(&h->ev_cdcg, cudaEventDisableTiming));
     }
     // the previous call's output copies and this call's device buffers
     CK(cudaEventRecord(h->ev_out, h->st));
@@ -1258,8 +1276,12 @@ int rx_process_host(rx_handle *h, const void *samples, size_t n_samples, float *
         } else {
             CK(cudaEventRecord(h->ev_in, h->cp_in));
         }
-        CK(cudaStreamWaitEvent(h->st, h->ev_in, 0));
+        // the first group's kernels start after its input; later groups'
+        // CDC waits for theirs on its own stream (run_blocks)
+        if (g0 == 0) CK(cudaStreamWaitEvent(h->st, h->ev_in, 0));
+        h->cdc_side = g0 > 0;
         rc = run_blocks(h, h->d_in, N, g0, g1, h->d_out, g0 == 0, g1 == nblk);
+        h->cdc_side = false;
         h->wait_rest = false;
         if (rc != RX_OK) return rc;
         // block n writes rows [k0 - W/2, k1 - W/2) (the last block up to N)
