@@ -22,6 +22,8 @@
 #include <algorithm>
 #include <cmath>
 
+#include <cuda_bf16.h>
+
 #include "rx_internal.h"
 
 namespace {
@@ -193,8 +195,21 @@ layer3_kernel(const float *__restrict__ h2, long n, const uint16_t *__restrict__
 // ---------------------------------------------------------------------------
 constexpr int kW2P = H + 8;   // padded row of the staged W2 (bfloat16)
 
-__device__ __forceinline__ unsigned pack_bf16(uint16_t lo_col, uint16_t hi_col) {
-    return (unsigned)lo_col | ((unsigned)hi_col << 16);
+// two float32 values rounded to bfloat16 (nearest, ties to even: the same
+// rounding as f_to_bf16) in one register, the first in the low half
+__device__ __forceinline__ unsigned cvt_bf16x2(float first, float second) {
+    const __nv_bfloat162 v = __floats2bfloat162_rn(first, second);
+    return *reinterpret_cast<const unsigned *>(&v);
+}
+__device__ __forceinline__ float bf16_lo(unsigned v) { return __uint_as_float(v << 16); }
+__device__ __forceinline__ float bf16_hi(unsigned v) { return __uint_as_float(v & 0xffff0000u); }
+
+// (hi, mid, lo) bfloat16 pairs of two float32 values
+__device__ __forceinline__ void split3_bf16x2(float a, float b, unsigned &hi, unsigned &mid, unsigned &lo) {
+    hi = cvt_bf16x2(a, b);
+    const float ra = a - bf16_lo(hi), rb = b - bf16_hi(hi);
+    mid = cvt_bf16x2(ra, rb);
+    lo = cvt_bf16x2(ra - bf16_lo(mid), rb - bf16_hi(mid));
 }
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
@@ -240,31 +255,20 @@ infer_tc_kernel(const float *__restrict__ x, const float *__restrict__ sigma2, l
             unsigned ah[4], am[4], al[4];
 #pragma unroll
             for (int half = 0; half < 2; ++half) {          // columns + 0 / + 8
-                uint16_t hr[2][2], mr[2][2], lr[2][2];       // [row g / g+8][col +0 / +1]
+                const int j0 = kk * 16 + half * 8 + c0;
+                float pa[2], pb[2];                          // rows g / g + 8, columns j0, j0 + 1
 #pragma unroll
                 for (int e = 0; e < 2; ++e) {
-                    const int j = kk * 16 + half * 8 + c0 + e;
-                    float pa = bb1[j], pb = bb1[j];
+                    pa[e] = bb1[j0 + e];
+                    pb[e] = bb1[j0 + e];
 #pragma unroll
                     for (int c = 0; c < 4; ++c) {
-                        pa = fmaf(xa[c], w1[j][c], pa);
-                        pb = fmaf(xb[c], w1[j][c], pb);
-                    }
-                    const float hv[2] = {gelu(pa), gelu(pb)};
-#pragma unroll
-                    for (int r = 0; r < 2; ++r) {
-                        hr[r][e] = f_to_bf16(hv[r]);
-                        const float rest = hv[r] - bf16_to_f(hr[r][e]);
-                        mr[r][e] = f_to_bf16(rest);
-                        lr[r][e] = f_to_bf16(rest - bf16_to_f(mr[r][e]));
+                        pa[e] = fmaf(xa[c], w1[j0 + e][c], pa[e]);
+                        pb[e] = fmaf(xb[c], w1[j0 + e][c], pb[e]);
                     }
                 }
-                ah[2 * half] = pack_bf16(hr[0][0], hr[0][1]);
-                ah[2 * half + 1] = pack_bf16(hr[1][0], hr[1][1]);
-                am[2 * half] = pack_bf16(mr[0][0], mr[0][1]);
-                am[2 * half + 1] = pack_bf16(mr[1][0], mr[1][1]);
-                al[2 * half] = pack_bf16(lr[0][0], lr[0][1]);
-                al[2 * half + 1] = pack_bf16(lr[1][0], lr[1][1]);
+                split3_bf16x2(gelu(pa[0]), gelu(pa[1]), ah[2 * half], am[2 * half], al[2 * half]);
+                split3_bf16x2(gelu(pb[0]), gelu(pb[1]), ah[2 * half + 1], am[2 * half + 1], al[2 * half + 1]);
             }
 #pragma unroll
             for (int nt = 0; nt < 16; ++nt) {
