@@ -19,6 +19,7 @@
 #include "rx_internal.h"
 #include "k_kk.h"
 #include "k_fde.h"
+#include "k_init.h"
 
 namespace {
 
@@ -179,8 +180,6 @@ struct rx_handle {
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> blk;
     unsigned long long nlaunch[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // host sources of asynchronous uploads (kept alive until the next call)
-    std::vector<float2> h_taps0;
-    std::vector<StreamDev> h_sd0;
     std::vector<double> h_sig;
     // host staging
     void *h_in = nullptr, *h_out = nullptr;
@@ -478,15 +477,6 @@ int check_config(rx_handle *h) {
     return RX_OK;
 }
 
-void center_spike(const rx_handle *h, std::vector<float2> &v) {
-    const int T = h->T, D = (T - 1) / 2, L = tl(h);
-    v.assign((size_t)h->streams * 4 * L, make_float2(0.f, 0.f));
-    for (int s = 0; s < h->streams; ++s) {
-        v[(size_t)s * 4 * L + 0 * L + D] = make_float2(1.f, 0.f);       // h_XX
-        v[(size_t)s * 4 * L + 3 * L + D] = make_float2(1.f, 0.f);       // h_YY
-    }
-}
-
 float2 *slot(rx_handle *h, long n) {
     const int L1 = ring_size(h);
     const long i = ((n % L1) + L1) % L1;
@@ -646,19 +636,15 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     }
     if (b0 == 0) {
         const cudaStream_t ss = h->side;     // start-up stream
-        std::vector<float2> &cs = h->h_taps0;
-        center_spike(h, cs);
+        // the identity butterfly and the stream state are written by kernels:
+        // a copy from pageable host memory would synchronise its stream first
         float2 *w0 = slot(h, 0);
-        CK(cudaMemcpyAsync(w0, cs.data(), tapsz, cudaMemcpyHostToDevice, ss));
+        CK(launch_center_spike(w0, S, tl(h), (h->T - 1) / 2, ss));
         const long npre = std::min(h->n_pre, N);
         STAGE(ST_STARTUP, ss, 1, launch_lms(h->x, ns, w0, w0, 0, (int)npre, nullptr, 0, 0, h->cma_passes,
                                             0, 0, (float)h->mu, nullptr, 0, S, T, f, ss, h->prec, h->wl));
         // stream state: counters zero, unwrap carry phi_hat = 0
-        std::vector<StreamDev> &sd0 = h->h_sd0;
-        sd0.assign(S, StreamDev{});
-        std::memset(sd0.data(), 0, sizeof(StreamDev) * S);
-        for (int s = 0; s < S; ++s) { sd0[s].carry[0][0] = 0; sd0[s].carry[0][1] = h->B / 2; }
-        CK(cudaMemcpyAsync(h->sd, sd0.data(), sizeof(StreamDev) * S, cudaMemcpyHostToDevice, st));
+        CK(launch_stream_init(h->sd, S, h->B, st));
         const long ntr = std::min(h->n_train, N);
         h->trained = false;
         if (h->ref && ntr > 0 && h->ref_n >= ntr) {
