@@ -27,6 +27,8 @@
 // unwrap kernel adds the block boundaries and scans its own range.
 #include <algorithm>
 
+#include <atomic>
+
 #include "rx_internal.h"
 
 namespace {
@@ -477,16 +479,20 @@ cudaError_t bps_launch_t(const void *y, long ys, long a, long e, long nv, int W,
     const int n_cta = (int)((e - a + kR - 1) / kR);
     const size_t smem = sizeof(float) * (RX_NCHUNK * f.B * 33 + RX_NCHUNK * f.B + 8 * f.B) + kR + 16;
     auto kern = bps_kernel<DIMS, NORB, SS>;
-    // the dynamic shared-memory limit is raised only when a launch needs more
-    // than this device's setting so far (one host call, not one per launch)
-    static size_t set_of[64] = {};
+    // the dynamic shared-memory limit is set once per device, to the largest
+    // any launch can ask for (RX_MAXB phases, kMaxChunks chunks), so that host
+    // threads issuing concurrently never lower it under one another's launch
+    constexpr size_t kMaxSmem =
+        sizeof(float) * (RX_NCHUNK * RX_MAXB * 33 + RX_NCHUNK * RX_MAXB + 8 * RX_MAXB) + 32 * kMaxChunks + 16;
+    if (smem > kMaxSmem) return cudaErrorInvalidValue;
+    static std::atomic<unsigned long long> set_on{0};   // bit d: set on device d
     int dev = 0;
     cudaError_t err = cudaGetDevice(&dev);
     if (err != cudaSuccess) return err;
-    if (dev >= 64 || smem > set_of[dev]) {
-        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (dev >= 64 || !((set_on.load(std::memory_order_relaxed) >> dev) & 1ull)) {
+        err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxSmem);
         if (err != cudaSuccess) return err;
-        if (dev < 64) set_of[dev] = smem;
+        if (dev < 64) set_on.fetch_or(1ull << dev, std::memory_order_relaxed);
     }
     dim3 grid((unsigned)n_cta, (unsigned)n_streams);
     kern<<<grid, 256, smem, st>>>(y, ys, a, e, nv, W, bout, bst, dsum, mdsum, n_cta, chunks, sk, f);
@@ -498,11 +504,13 @@ cudaError_t bps_launch_t(const void *y, long ys, long a, long e, long nv, int W,
 int bps_cta_range(int chunks) { return range_of(chunks); }
 
 int sm_count() {
-    static int n = 0;
+    static std::atomic<int> cached{0};
+    int n = cached.load(std::memory_order_relaxed);
     if (!n) {
         int dev = 0;
         cudaGetDevice(&dev);
         if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 152;
+        cached.store(n, std::memory_order_relaxed);
     }
     return n;
 }

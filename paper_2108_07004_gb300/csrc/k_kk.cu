@@ -20,6 +20,8 @@
 // outside the stream) and writes outputs f*step .. f*step + step - 1.
 #include "k_kk.h"
 
+#include <atomic>
+
 #include "fft_dev.h"
 
 namespace {
@@ -203,15 +205,15 @@ cudaError_t launch_kk(const int16_t *codes, float2 *out, long ns, int n_ov, cons
     if (f1 <= f0 || ns <= 0) return cudaSuccess;
     const size_t smem = sizeof(float) * 2 * ((3 * step + N + 3) & ~3) + sizeof(float2) * 4 * 32 * 33;
     // > 48 KB of dynamic shared memory needs the opt-in, once per device
-    static unsigned long long attr_done = 0;   // bit d: set on device d
+    static std::atomic<unsigned long long> attr_done{0};   // bit d: set on device d
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    if (dev >= 64 || !((attr_done >> dev) & 1ull)) {
+    if (dev >= 64 || !((attr_done.load(std::memory_order_relaxed) >> dev) & 1ull)) {
         e = cudaFuncSetAttribute(kk1024_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)(sizeof(float) * 2 * ((3 * 1022 + N + 3) & ~3) + sizeof(float2) * 4 * 32 * 33));
         if (e != cudaSuccess) return e;
-        if (dev < 64) attr_done |= 1ull << dev;
+        if (dev < 64) attr_done.fetch_or(1ull << dev, std::memory_order_relaxed);
     }
     dim3 grid((unsigned)((f1 - f0 + 3) / 4), (unsigned)((p.n_streams + 1) / 2));
     kk1024_kernel<<<grid, 128, smem, st>>>(codes, out, ns, step, half, f0, f1, p, tw);

@@ -20,6 +20,8 @@
 #include <algorithm>
 #include <type_traits>
 
+#include <atomic>
+
 #include "rx_internal.h"
 
 namespace {
@@ -745,11 +747,11 @@ cudaError_t lms_launch_one(const void *x, long ns, const float2 *ti, float2 *to,
     auto kern = lms_kernel<T, DIMS, MODE>;
     // the opt-in size is looked up and set once per device (host queries per
     // launch cost more than the launch when a handle runs one stream)
-    static int dyn_of[64] = {};
+    static std::atomic<int> dyn_of[64] = {};
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    int dyn = dev < 64 ? dyn_of[dev] : 0;
+    int dyn = dev < 64 ? dyn_of[dev].load(std::memory_order_relaxed) : 0;
     if (dyn == 0) {
         cudaFuncAttributes fa;
         if ((e = cudaFuncGetAttributes(&fa, kern)) != cudaSuccess) return e;
@@ -758,7 +760,7 @@ cudaError_t lms_launch_one(const void *x, long ns, const float2 *ti, float2 *to,
         dyn = optin - (int)fa.sharedSizeBytes;
         if (dyn < (int)(lms_smem_f2(T) * sizeof(float2))) return cudaErrorInvalidValue;
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
-        if (dev < 64) dyn_of[dev] = dyn;
+        if (dev < 64) dyn_of[dev].store(dyn, std::memory_order_relaxed);
     }
     kern<<<S, kThreads, dyn, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, sk, wl, f);
     return cudaGetLastError();

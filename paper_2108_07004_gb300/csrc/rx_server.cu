@@ -18,6 +18,7 @@
 #include <deque>
 #include <memory>
 #include <string>
+#include <thread>
 #include <unordered_map>
 #include <vector>
 
@@ -98,6 +99,7 @@ struct rx_server {
     std::vector<Req *> active;
     std::unordered_map<uint64_t, std::unique_ptr<Req>> all;
     std::vector<Pooled> pool;           // idle handles, oldest first
+    size_t issue_threads = 1;           // host threads that issue a step's blocks
     size_t pooled = 0;                  // their memory estimates
     int max_active_seen = 0;
 };
@@ -238,6 +240,8 @@ rx_server *rx_server_create(size_t mem_budget_bytes, int max_slots) {
         return nullptr;
     }
     rx_server *s = new rx_server();
+    const unsigned hc = std::thread::hardware_concurrency();
+    s->issue_threads = std::max(1u, std::min(8u, hc ? hc : 1u));
     s->budget = mem_budget_bytes;
     s->max_slots = max_slots;
     return s;
@@ -304,13 +308,41 @@ int rx_server_step(rx_server *s, int *n_active) {
         if (admit(s, q)) s->active.push_back(q);
     }
     if ((int)s->active.size() > s->max_active_seen) s->max_active_seen = (int)s->active.size();
-    // one block of every running request, each on its own stream
-    for (Req *q : s->active) {
-        if (q->next >= q->nblk) continue;
-        const int rc = rx_process_blocks(q->h, q->r.samples, q->r.n_samples, (size_t)q->next,
-                                         (size_t)q->next + 1, q->r.llr_out, nullptr);
-        if (rc != RX_OK) {
-            q->err = rx_last_error();
+    // one block of every running request, each on its own stream.  Issuing
+    // a block costs the host some twenty launches and event operations, so
+    // the requests are split over a few host threads (each touches only its
+    // own requests' handles; the results are those of one thread)
+    std::vector<Req *> todo;
+    for (Req *q : s->active)
+        if (q->next < q->nblk) todo.push_back(q);
+    std::vector<int> rcs(todo.size(), RX_OK);
+    std::vector<std::string> errs(todo.size());
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto issue = [&](size_t i0, size_t i1) {
+        cudaSetDevice(dev);                 // a new host thread starts on device 0
+        for (size_t i = i0; i < i1; ++i) {
+            Req *q = todo[i];
+            rcs[i] = rx_process_blocks(q->h, q->r.samples, q->r.n_samples, (size_t)q->next, (size_t)q->next + 1,
+                                       q->r.llr_out, nullptr);
+            if (rcs[i] != RX_OK) errs[i] = rx_last_error();
+        }
+    };
+    const size_t nt = std::min<size_t>(s->issue_threads, todo.size() / 4 + 1);
+    if (nt <= 1) {
+        issue(0, todo.size());
+    } else {
+        std::vector<std::thread> pool;
+        const size_t per = (todo.size() + nt - 1) / nt;
+        for (size_t t = 1; t < nt; ++t)
+            pool.emplace_back(issue, std::min(todo.size(), t * per), std::min(todo.size(), (t + 1) * per));
+        issue(0, std::min(todo.size(), per));
+        for (auto &th : pool) th.join();
+    }
+    for (size_t i = 0; i < todo.size(); ++i) {
+        Req *q = todo[i];
+        if (rcs[i] != RX_OK) {
+            q->err = errs[i];
             q->next = q->nblk;
         } else {
             ++q->next;
