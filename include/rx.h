@@ -357,7 +357,8 @@ typedef struct {
  * the next request with the same format, symbol rate, sps, taps and test
  * phases, so that no device memory is freed while others run; idle handles
  * count against the budget and are destroyed when room is needed), and
- * every step issues one
+ * every step issues (from up to eight host threads of the library, one
+ * request's blocks always from one thread) one
  * block of every running request, so requests that arrived at different
  * times overlap on the device (the paper's multiple processing streams,
  * Sec. 2).  A finished request frees its slot and memory at the next step.
