@@ -94,3 +94,23 @@ def test_request_larger_than_the_budget_is_refused(streams):
     with pytest.raises(rx.RxError):
         _submit(srv, 1, *streams[1])
     srv.close()
+
+
+def test_many_concurrent_requests_issued_from_several_threads(streams):
+    """Four copies of every request at once (24 running): a step's blocks are
+    issued from several host threads, with first launches of different
+    formats and test-phase counts (different shared-memory sizes) racing;
+    every copy must finish with the result of the request served alone."""
+    from paper_2108_07004_gb300 import rx
+    alone = {i: _serve([i], streams)[0][i] for i in range(len(REQS))}
+    srv = rx.Server(1 << 34, 64)
+    got = [(i, _submit(srv, i, *streams[i])) for _ in range(4) for i in range(len(REQS))]
+    srv.run()
+    torch.cuda.synchronize()
+    for i, (rid, llr) in got:
+        state, stats = srv.poll(rid)
+        assert state == rx.REQ_DONE, (i, rx.lib().rx_server_last_error().decode())
+        assert np.array_equal(llr.cpu().numpy(), alone[i][0]), i
+        assert stats["bit_errors"] == alone[i][1]["bit_errors"]
+    assert srv.info()["max_active"] == 4 * len(REQS)
+    srv.close()
