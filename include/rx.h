@@ -90,9 +90,13 @@ typedef struct {
     double   evm_num;      /* sum |z - d|^2 (d: nearest point)                 */
     double   evm_den;      /* sum |d|^2                                        */
     double   sigma2_last;  /* noise variance used for the last block           */
-    uint64_t n_out;        /* LLR rows written for this stream                 */
+    uint64_t n_out;        /* LLR rows written for this stream (rx_push /      */
+                           /* rx_flush: valid rows handed out so far)          */
     uint32_t blocks;       /* blocks processed                                 */
     uint32_t reserved;
+    uint64_t first_valid;  /* rx_push: index in this call's llr_out of the     */
+                           /* first row that holds a symbol (the rows before   */
+                           /* it are the stream delay's zeros); otherwise 0    */
 } rx_stats;
 
 /* ---- lifetime ---------------------------------------------------------- */
@@ -193,6 +197,60 @@ int rx_process_host(rx_handle *h, const void *samples, size_t n_samples,
 
 /* Statistics of the last rx_process (host [S]); synchronises. */
 int rx_get_stats(rx_handle *h, rx_stats *stats);
+
+/* ---- streaming: one call per buffer of a continuous stream ---------------
+ * Sec. 2 of the paper processes the ADC's DMA buffers one after another in
+ * real time, the equaliser taps learned on part of one buffer serving the
+ * buffers after it.  rx_push takes the next n_samples samples per
+ * polarisation of each of the S streams (device or host memory,
+ * [S][2][n_samples] c64; any even count, 0 included) and writes exactly
+ * n_samples / 2 LLR rows per stream into llr_out (device, [S][n_samples/2]
+ * [m] float32): output row r of a stream (counted over all its pushes)
+ * holds symbol r - d, where d is the fixed stream delay of rx_stream_delay;
+ * rows r < d are zeros, and stats.first_valid gives the first row of this
+ * call that holds a symbol.  rx_flush ends the stream: the samples pushed so
+ * far are the whole stream (zeros after its end, as in rx_process), and the
+ * symbols not yet handed out come out: r = min(N, d) rows per stream,
+ * written packed as [S][r][m] into llr_out (N = the stream's symbols, the
+ * samples pushed / 2); *n_rows receives r.  The pushed rows after
+ * the delay followed by the flushed rows are bit for bit the LLRs of one
+ * rx_process over the concatenated samples, and the counters equal its
+ * counters when the reference (rx_set_reference, set before the first push)
+ * holds exactly the stream's N symbols: counting covers symbols skip_head
+ * .. ref_n - skip_tail - 1, since the stream's end is not known before the
+ * flush.
+ *
+ * The delay: the chain is block-wise (the noise variance and the LMS span
+ * of a block use the whole block), so the symbols of block n leave once the
+ * samples of every CDC frame the block reads are in.  With
+ * need(n) = ceil((2 max((n+1) block, max(n_pre, n_train)) + D) / hop) hop
+ * + overlap/2 samples (hop = fft - overlap, D = (taps-1)/2) for blocks
+ * 0 .. n and C(n) = n block - bps_window/2 symbols done after blocks
+ * 0 .. n-1, d = max over n of (floor((need(n) - 1) / 2) - C(n)), about
+ * block + bps_window/2 + (hop + overlap/2 + D)/2 symbols; at the
+ * benchmark's settings (block 2^16, FFT 4096 / overlap 1024, 31 taps,
+ * window 64) d = 67 359.
+ *
+ * The handle keeps a window of about (3 + hop / gcd(2 block, hop)) blocks
+ * of the stream (input samples and LLR rows twice each), allocated by the
+ * first push; a push of many samples is taken in pieces of one block.  A
+ * parameter change, rx_set_reference, rx_reset or a whole-stream call
+ * (rx_process, rx_process_blocks, rx_process_host, rx_set_state) ends the
+ * stream without output; the next push starts a new one.  Symbol outputs
+ * (rx_set_symbol_output) are not available while streaming (RX_EINVAL).
+ * Both calls return after queuing the work when stats is NULL; with stats
+ * they synchronise and fill it ([S]).  Errors: RX_EINVAL (odd n_samples,
+ * NULL buffers), RX_ESTATE (rx_flush without a stream). */
+int rx_stream_delay(rx_handle *h, size_t *delay);
+int rx_push(rx_handle *h, const void *samples, size_t n_samples, float *llr_out, rx_stats *stats);
+int rx_flush(rx_handle *h, float *llr_out, size_t *n_rows, rx_stats *stats);
+
+/* Wait at most timeout_ms (>= 0) of host time for the work queued on the
+ * handle's CUDA stream: RX_OK when it is done, RX_ETIMEDOUT (the work goes
+ * on; wait again later) when the time ran out first.  For callers that may
+ * not block without a bound, e.g. a real-time loop that must take the next
+ * DMA buffer in time. */
+int rx_wait(rx_handle *h, double timeout_ms);
 
 /* Device time of the last rx_process per stage, from CUDA events recorded
  * around every launch on its own stream when the parameter "profile" is 1
@@ -389,16 +447,30 @@ int rx_format_info(const rx_handle *h, int *dims, int *m, int *M);
 
 const char *rx_last_error(void);
 
+/* ---- measurement aid -------------------------------------------------------
+ * The paper has no counterpart: this measures the denominator of the phase
+ * search's roofline.  Issue rate of one FP32 instruction kind on the current
+ * device, in lane-instructions per second: kind 0 fma.rn.f32 (FFMA), 1
+ * fma.rn.f32x2 (FFMA2, two multiply-adds per lane-instruction), 2 min.f32
+ * (FMNMX).  Two blocks of 1024 threads per SM run 8 independent chains per
+ * thread for iters x 16 x 8 instructions (one warm-up launch first); *ms
+ * (may be NULL) receives the timed launch's device time.  Synchronises its
+ * own stream; RX_EINVAL for a bad kind or iters < 1. */
+int rx_issue_rate(int kind, int iters, double *lane_instr_per_s, double *ms);
+
 /* ---- single stages (the steps rx_process chains; for tests and custom
  *      pipelines).  All arrays are device memory with a leading [S]. ----- */
 
 /* A1 CDC: overlap-save FFT filtering with conj(H_CD) * H_MF, global
- * framing from sample 0.  in, out: [S][2][n_samples] c64 (out != in). */
+ * framing from sample 0.  in, out: [S][2][n_samples] c64 (out != in).
+ * With "precision" 1 or 2, out holds half or bfloat16 (re, im) pairs
+ * (4 bytes per sample), as the chain stores its CDC output. */
 int rx_cdc(rx_handle *h, const void *in, void *out, size_t n_samples);
 
 /* A2 FIR: y_q[k] = sum_p sum_t conj(h_qp[t]) x_p[2k + D - t], D = (T-1)/2,
  * for k0 <= k < k1.  x: [S][2][n_samples], taps: [S][2][2][T] c64
- * (index [q][p][t]), y: [S][2][k1 - k0]. */
+ * (index [q][p][t]), y: [S][2][k1 - k0].  With "precision" 1 or 2, x and y
+ * are half or bfloat16 pairs (the chain's storage); arithmetic is float32. */
 int rx_fir(rx_handle *h, const void *x, size_t n_samples, const void *taps,
            size_t k0, size_t k1, void *y);
 

@@ -10,9 +10,15 @@
 //         (distance, label) min over 16 lanes, ties -> lowest label);
 //         e_q = d_q exp(j phi_k) - y_q
 //   h_qp[t] += mu conj(e_q) x_p[2k + D - t]
-// Per stream one block: a decision warp and a tap warp run it together (see
-// lms_kernel); the samples of up to 1024 updates are staged in shared memory
-// by the whole block before the two warps run through them.
+// Per stream one block of 12 warps (see lms_kernel), in sub-blocks of 16
+// updates with a look-ahead of one sub-block: a decision warp takes the
+// sequential decisions (each lane holds the partial output of one update and
+// adds one correlation term per decision); a tap group of four warps applies
+// the previous sub-block's updates to the taps and forms the next
+// sub-block's outputs from them; a correlation group of four warps forms the
+// window correlations r(j, j + d) the decision warp's corrections need.  The
+// samples of up to 1024 updates are staged in shared memory by the whole
+// block before the warps run through them.
 //
 // The start-up training alignment (Sec. 2: the equaliser first converges on
 // a known sequence) is align_kernel: it correlates the equalised training

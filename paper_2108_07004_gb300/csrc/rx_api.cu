@@ -12,8 +12,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <chrono>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "rx_internal.h"
@@ -36,12 +38,17 @@ int fail(int code, const char *fmt, ...) {
     return code;
 }
 
+// A failed runtime call is reported through rx_last_error; the runtime's
+// own last-error state is cleared (cudaGetLastError), so that the caller's
+// next CUDA call does not see a stale error of the library's.
 #define CK(call)                                                                      \
     do {                                                                              \
         cudaError_t e_ = (call);                                                      \
-        if (e_ != cudaSuccess)                                                        \
+        if (e_ != cudaSuccess) {                                                      \
+            (void)cudaGetLastError();                                                 \
             return fail(e_ == cudaErrorMemoryAllocation ? RX_ENOMEM : RX_ECUDA,       \
                         "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+        }                                                                             \
     } while (0)
 
 constexpr double kPi = 3.14159265358979323846;
@@ -181,6 +188,26 @@ struct rx_handle {
     unsigned long long nlaunch[8] = {0, 0, 0, 0, 0, 0, 0, 0};
     // host sources of asynchronous uploads (kept alive until the next call)
     std::vector<double> h_sig;
+    // streaming entry (rx_push / rx_flush): the stream is held in a window of
+    // `cap` symbols whose local symbol 0 is global symbol `origin`; input and
+    // LLR windows are double-buffered so that a move of the window's origin
+    // is a copy between the two
+    struct Push {
+        bool on = false;
+        long tot = 0;         // samples per polarisation pushed so far
+        long origin = 0;      // global symbol of local symbol 0
+        long nb = 0;          // next block to run (global)
+        long emitted = 0;     // output rows handed out so far
+        long delay = 0;       // fixed stream delay d in symbols
+        long cap = 0;         // window length in symbols
+        long step = 0;        // origin moves in multiples of this many symbols
+        long piece = 0;       // largest number of samples appended at once
+        float2 *in[2] = {nullptr, nullptr};
+        float *llr[2] = {nullptr, nullptr};
+        int cur = 0;
+        void *halo = nullptr; // [S][2][W] FIR output, moved on a flush
+        size_t in_bytes = 0, llr_bytes = 0, halo_bytes = 0;
+    } push;
     // host staging
     void *h_in = nullptr, *h_out = nullptr;
     size_t h_in_cap = 0, h_out_cap = 0;
@@ -578,14 +605,27 @@ CdcFrames cdc_frames(const rx_handle *h, long N, long b0, long b1) {
     return c;
 }
 
+// A window of a longer stream (the streaming entry points): local symbol 0
+// of the buffers is global symbol `origin`, a multiple of the block length
+// with 2 origin a multiple of the CDC hop, so blocks and CDC frames fall as
+// in the whole stream.  Blocks keep their global numbers (bofs = origin /
+// block) for the tap ring, the events and the parity-indexed buffers;
+// counting covers global symbols [c0, c1) against the reference indexed
+// globally.
+struct Window {
+    long bofs = 0, origin = 0, c0 = 0, c1 = 0;
+};
+
 // Run blocks [b0, b1) of S streams of N symbols whose samples are at `in`;
 // `fresh` starts new per-call records (stage times, block latencies);
 // `join` makes the main stream wait for the side stream's last LMS, so that
 // the state is complete when the main stream's work is (calls that return
 // to the user; the host entry's groups pass false except for the last).
+// `win` (may be null): the buffers hold a window of a longer stream.
 int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *llr, bool fresh = true,
-               bool join = true) {
+               bool join = true, const Window *win = nullptr) {
     const int S = h->streams, T = h->T, L = h->lag;
+    const long G = win ? win->bofs : 0;   // global number of local block 0
     const long Nb = h->block, ns = 2 * N;
     const long nblk = (N + Nb - 1) / Nb;
     const size_t tapsz = sizeof(float2) * (size_t)S * 4 * tl(h);
@@ -634,7 +674,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
                                             h->prec));
         }
     }
-    if (b0 == 0) {
+    if (b0 == 0 && G == 0) {
         const cudaStream_t ss = h->side;     // start-up stream
         // the identity butterfly and the stream state are written by kernels:
         // a copy from pageable host memory would synchronise its stream first
@@ -692,6 +732,12 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     cnt.ref_stride = h->ref_n;
     cnt.c0 = std::min(h->skip_head, N);
     cnt.c1 = std::max(cnt.c0, N - h->skip_tail);
+    if (win) {
+        // global counting window, the reference indexed from the origin
+        cnt.c0 = std::min(N, std::max(0L, win->c0 - win->origin));
+        cnt.c1 = std::max(cnt.c0, std::min(N, std::min(win->c1, (long)h->ref_n) - win->origin));
+        cnt.ref_lab = (h->ref && cnt.c1 > cnt.c0) ? h->ref + win->origin : nullptr;
+    }
     cnt.sd = h->sd;
     cnt.partial = h->part_d;
     const cudaStream_t ds = h->dst;
@@ -699,29 +745,30 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     CK(cudaEventRecord(h->ev_setup, st));
     CK(cudaStreamWaitEvent(ds, h->ev_setup, 0));
     for (long n = b0; n < b1; ++n) {
+        const long g = n + G;                 // global block number
         const long k0 = n * Nb, k1 = std::min(k0 + Nb, N);
-        if (L >= 2 && n >= L) CK(cudaStreamWaitEvent(st, h->ev_lms[(n - L) % R], 0));
-        // W_n = U_{n-lag}; for n < lag the slot read has not been written since start-up (W_0)
-        const float2 *wn = slot(h, n - L);
+        if (L >= 2 && g >= L) CK(cudaStreamWaitEvent(st, h->ev_lms[(g - L) % R], 0));
+        // W_g = U_{g-lag}; for g < lag the slot read has not been written since start-up (W_0)
+        const float2 *wn = slot(h, g - L);
         cudaEvent_t blk0 = nullptr;
         if (h->profile == 1 && (blk0 = prof_event(h))) CK(cudaEventRecord(blk0, st));
         STAGE(ST_FIR, st, 1, launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st, h->prec, avail, h->wl));
         const long a = std::max(0L, k0 - h->W / 2);
         const long e = (n == nblk - 1) ? N : k1 - h->W / 2;
         const int chunks = bps_chunks(e - a, S, avail);
-        const int par = (int)(n & 1);
+        const int par = (int)(g & 1);
         int *dsum_n = h->dsum + (size_t)par * S * h->cap_dsum;
         double *mdsum_n = h->mdsum + (size_t)par * S * h->cap_dsum;
         // the partial sums of this parity were read by the demap of block n - 2
         // (possibly of an earlier call: the demap stream is not joined between
         // the host entry's groups)
-        if (n >= 2) CK(cudaStreamWaitEvent(st, h->ev_dm[par], 0));
+        if (g >= 2) CK(cudaStreamWaitEvent(st, h->ev_dm[par], 0));
         STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, dsum_n, mdsum_n, chunks, S,
                                         f, st, h->prec));
         CK(cudaEventRecord(h->ev_bps[par], st));
         CK(cudaStreamWaitEvent(ds, h->ev_bps[par], 0));
-        const int cin = (int)(n & 1), cout = 1 - cin;
-        if (n == 0 && h->trained) {
+        const int cin = (int)(g & 1), cout = 1 - cin;
+        if (g == 0 && h->trained) {
             // the training phases fix the start quadrant of the unwrap
             STAGE(ST_UNWRAP, ds, 1, launch_anchor(h->bidx, N, h->pcode, N, (int)std::min(h->n_train, e),
                                                   carry_base, (int)sd_stride, S, h->B, f.S, ds));
@@ -754,30 +801,30 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         CK(cudaEventRecord(h->ev_unwrap, ds));
         cudaStream_t ls = st;
         if (L >= 2) {
-            const int r = (int)(n % chains);
+            const int r = (int)(g % chains);
             ls = r == 0 ? h->side : h->side_x[r - 1];
             CK(cudaStreamWaitEvent(ls, h->ev_unwrap, 0));
         } else {
             CK(cudaStreamWaitEvent(st, h->ev_unwrap, 0));
         }
         // the update starts from U_{n-1} (one chain) or from W_n = U_{n-lag}
-        const float2 *u_in = slot(h, chains > 1 ? n - L : n - 1);
+        const float2 *u_in = slot(h, chains > 1 ? g - L : g - 1);
         if (h->lms_block > 1)
             STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
-                  launch_lms_block(h->x, ns, u_in, slot(h, n), k0, (int)span, h->pcode, N, 2, h->u,
+                  launch_lms_block(h->x, ns, u_in, slot(h, g), k0, (int)span, h->pcode, N, 2, h->u,
                                    (int)h->n_cma, (float)h->mu, h->lms_block, S, T, f, ls, h->prec, h->wl));
         else
             STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
-                  launch_lms(h->x, ns, u_in, slot(h, n), k0, (int)span, h->pcode, N, 2, 1,
+                  launch_lms(h->x, ns, u_in, slot(h, g), k0, (int)span, h->pcode, N, 2, 1,
                              h->u, (int)h->n_cma, (float)h->mu, nullptr, 0, S, T, f, ls, h->prec, h->wl));
-        if (L >= 2) CK(cudaEventRecord(h->ev_lms[n % R], ls));
+        if (L >= 2) CK(cudaEventRecord(h->ev_lms[g % R], ls));
         h->u += span;
-        h->blocks_done = n + 1;
+        h->blocks_done = g + 1;
     }
     // the caller's stream sees the demaps (LLRs, counters, carries) done
-    if (join && b1 > b0) CK(cudaStreamWaitEvent(st, h->ev_dm[(int)((b1 - 1) & 1)], 0));
+    if (join && b1 > b0) CK(cudaStreamWaitEvent(st, h->ev_dm[(int)((b1 - 1 + G) & 1)], 0));
     if (join && L >= 2)
-        for (long n = std::max(b0, b1 - chains); n < b1; ++n) CK(cudaStreamWaitEvent(st, h->ev_lms[n % R], 0));
+        for (long n = std::max(b0, b1 - chains); n < b1; ++n) CK(cudaStreamWaitEvent(st, h->ev_lms[(n + G) % R], 0));
     return RX_OK;
 }
 
@@ -785,7 +832,9 @@ int fill_stats(rx_handle *h, rx_stats *out) {
     const int S = h->streams;
     std::vector<StreamDev> sd(S);
     CK(cudaStreamSynchronize(h->st));
-    CK(cudaMemcpy(sd.data(), h->sd, sizeof(StreamDev) * S, cudaMemcpyDeviceToHost));
+    // before the first block of a handle there are no device counters yet
+    if (h->sd) CK(cudaMemcpy(sd.data(), h->sd, sizeof(StreamDev) * S, cudaMemcpyDeviceToHost));
+    else std::memset(sd.data(), 0, sizeof(StreamDev) * S);
     for (int s = 0; s < S; ++s) {
         rx_stats &o = out[s];
         std::memset(&o, 0, sizeof o);
@@ -800,6 +849,231 @@ int fill_stats(rx_handle *h, rx_stats *out) {
         o.sigma2_last = sd[s].sigma2;
         o.n_out = (uint64_t)h->cur_n;
         o.blocks = (uint32_t)h->blocks_done;
+    }
+    return RX_OK;
+}
+
+// ---------------------------------------------------------------------------
+// streaming entry (rx_push / rx_flush): Sec. 2 processes the ADC's DMA
+// buffers one after another, the taps learned on one buffer serving later
+// ones.  The stream is held in a window of the handle's buffers; blocks run
+// as soon as the samples their CDC frames read are in, and LLR rows leave
+// with a fixed delay.
+// ---------------------------------------------------------------------------
+long cdc_hop(const rx_handle *h) { return h->n_fft - h->n_ov; }
+
+// Input samples per polarisation that blocks 0 .. n of a stream read (their
+// CDC frames and the start-up's): frame f reads samples f*hop - n_ov/2 ..
+// f*hop + hop + n_ov/2 - 1, and block n's FIR / LMS outputs k < (n+1)*block
+// read CDC outputs up to 2k + D.
+long need_samples(const rx_handle *h, long n) {
+    const long Sk = cdc_hop(h), D = (h->T - 1) / 2;
+    const long k_hi = (n + 1) * h->block;
+    const long k_st = std::max(h->n_pre, h->n_train);
+    const long f1 = (2 * std::max(k_hi, k_st) + D + Sk - 1) / Sk;
+    return f1 * Sk + h->n_ov / 2;
+}
+
+long gcd_l(long a, long b) {
+    while (b) {
+        const long t = a % b;
+        a = b;
+        b = t;
+    }
+    return a;
+}
+
+// Origin step, fixed delay and window length of the streaming entry.
+void push_geometry(rx_handle *h) {
+    auto &P = h->push;
+    const long Nb = h->block, Sk = cdc_hop(h), W2 = h->W / 2, D = (h->T - 1) / 2;
+    // the window's origin moves in whole blocks that are also whole CDC hops
+    // (2 origin a multiple of hop), so blocks and frames fall as in the stream
+    const long per = Sk / gcd_l(2 * Nb, Sk);
+    P.step = per * Nb;
+    // With tot samples in, blocks 0 .. n-1 have run exactly when
+    // need(n-1) <= tot < need(n); their LLRs cover symbols < C(n) =
+    // n*block - W/2 (C(0) = 0).  Output row r = tot/2 - 1 holds symbol
+    // r - d, so every row handed out is computed when d >= (need(n) - 1)/2
+    // - C(n) for all n.  The pattern repeats every `per` blocks once the
+    // start-up span is passed.
+    const long st_blocks = (std::max(h->n_pre, h->n_train) + Nb - 1) / Nb;
+    long d = 0;
+    for (long n = 0; n <= per + st_blocks + 2; ++n) {
+        const long C = n == 0 ? 0 : n * Nb - W2;
+        d = std::max(d, (need_samples(h, n) - 1) / 2 - C);
+    }
+    P.delay = d;
+    // appended at most one block of symbols at a time; after each piece the
+    // window keeps the symbols from min((nb-1) block, the first CDC frame of
+    // block nb, the first row not yet handed out) rounded down to the step:
+    // less than step + max(2 block + 2 hop + n_ov + 2 D + W, d) symbols
+    P.piece = 2 * Nb;
+    const long cap = std::max(std::max(P.step + 3 * Nb + 2 * Sk + h->n_ov + 2 * D + h->W + 64,
+                                       (need_samples(h, 0) + 1) / 2 + Nb + 64),
+                              d + P.step + Nb + 64);
+    P.cap = (cap + 255) / 256 * 256;
+}
+
+int push_alloc(rx_handle *h) {
+    auto &P = h->push;
+    const int S = h->streams, m = h->fmt.m;
+    const size_t in_b = sizeof(float2) * (size_t)S * 2 * 2 * P.cap;
+    const size_t llr_b = sizeof(float) * (size_t)S * P.cap * m;
+    const size_t halo_b = store_bytes(h->prec) * (size_t)S * 2 * h->W;
+    if (P.in_bytes < in_b) {
+        for (auto &b : P.in) { cudaFree(b); b = nullptr; }
+        P.in_bytes = 0;
+        for (auto &b : P.in) CK(cudaMalloc(&b, in_b));
+        P.in_bytes = in_b;
+    }
+    if (P.llr_bytes < llr_b) {
+        for (auto &b : P.llr) { cudaFree(b); b = nullptr; }
+        P.llr_bytes = 0;
+        for (auto &b : P.llr) CK(cudaMalloc(&b, llr_b));
+        P.llr_bytes = llr_b;
+    }
+    if (P.halo_bytes < halo_b) {
+        cudaFree(P.halo);
+        P.halo = nullptr;
+        P.halo_bytes = 0;
+        CK(cudaMalloc(&P.halo, halo_b));
+        P.halo_bytes = halo_b;
+    }
+    return RX_OK;
+}
+
+void push_free(rx_handle *h) {
+    auto &P = h->push;
+    for (auto &b : P.in) { cudaFree(b); b = nullptr; }
+    for (auto &b : P.llr) { cudaFree(b); b = nullptr; }
+    cudaFree(P.halo);
+    P.halo = nullptr;
+    P.in_bytes = P.llr_bytes = P.halo_bytes = 0;
+}
+
+Window push_window(const rx_handle *h) {
+    Window w;
+    w.origin = h->push.origin;
+    w.bofs = h->push.origin / h->block;
+    // counting over the stream's symbols skip_head .. ref_n - skip_tail - 1:
+    // the reference covers the stream, whose end is not known before rx_flush
+    w.c0 = h->skip_head;
+    w.c1 = (long)h->ref_n - h->skip_tail;
+    return w;
+}
+
+// symbols whose LLRs are computed (global): those of blocks 0 .. nb-1
+long push_done(const rx_handle *h) { return h->push.nb == 0 ? 0 : h->push.nb * h->block - h->W / 2; }
+
+// Rows [row0, row0 + cnt) of the output (row r holds symbol r - d; rows
+// r < d are zeros) into out, [S][out_rows][m], from row out_off on.
+int push_emit(rx_handle *h, float *out, long out_rows, long out_off, long row0, long cnt) {
+    auto &P = h->push;
+    const int S = h->streams, m = h->fmt.m;
+    const size_t rb = sizeof(float) * m;
+    const long z = std::min(cnt, std::max(0L, P.delay - row0));
+    if (z > 0) CK(cudaMemset2DAsync(out + (size_t)out_off * m, rb * out_rows, 0, rb * z, S, h->st));
+    const long k0 = row0 + z - P.delay, k1 = row0 + cnt - P.delay;
+    if (k1 > k0) {
+        if (k0 < P.origin || k1 > push_done(h))
+            return fail(RX_EINVAL, "internal: rows %ld .. %ld not in the stream window", k0, k1);
+        CK(cudaMemcpy2DAsync(out + (size_t)(out_off + z) * m, rb * out_rows,
+                             P.llr[P.cur] + (size_t)(k0 - P.origin) * m, rb * P.cap, rb * (k1 - k0), S,
+                             cudaMemcpyDeviceToDevice, h->st));
+    }
+    return RX_OK;
+}
+
+// Run every block whose samples are in.
+int push_run(rx_handle *h, bool fresh) {
+    auto &P = h->push;
+    long n1 = P.nb;
+    while (need_samples(h, n1) <= P.tot) ++n1;
+    if (n1 == P.nb) return RX_OK;
+    const Window w = push_window(h);
+    int rc = run_blocks(h, P.in[P.cur], P.cap, P.nb - w.bofs, n1 - w.bofs, P.llr[P.cur], fresh, true, &w);
+    if (rc != RX_OK) return rc;
+    P.nb = n1;
+    return RX_OK;
+}
+
+// Move the window's origin forward as far as the next blocks, their CDC
+// frames and the rows not yet handed out allow (a copy into the other
+// buffer of each pair, and the phase-search halo of block nb).
+int push_rebase(rx_handle *h) {
+    auto &P = h->push;
+    if (P.nb < 1) return RX_OK;
+    const long Nb = h->block, Sk = cdc_hop(h), D = (h->T - 1) / 2;
+    const long f0 = (2 * P.nb * Nb - D) / Sk;           // first CDC frame of block nb
+    const long e0 = P.emitted - P.delay;                // first symbol not handed out
+    const long lim = std::min(std::min((P.nb - 1) * Nb, (f0 - 1) * Sk / 2), e0);
+    if (lim <= P.origin) return RX_OK;
+    const long o = lim / P.step * P.step;
+    if (o <= P.origin) return RX_OK;
+    const long dl = o - P.origin;
+    const int S = h->streams, m = h->fmt.m, nx = 1 - P.cur;
+    const size_t ip = sizeof(float2) * 2 * P.cap, rb = sizeof(float) * m;
+    const long keep = P.tot - 2 * o;
+    if (keep > 0)
+        CK(cudaMemcpy2DAsync(P.in[nx], ip, P.in[P.cur] + 2 * dl, ip, sizeof(float2) * keep, (size_t)2 * S,
+                             cudaMemcpyDeviceToDevice, h->st));
+    const long c = push_done(h), r0 = std::max(e0, o);
+    if (c > r0)
+        CK(cudaMemcpy2DAsync(P.llr[nx] + (size_t)(r0 - o) * m, rb * P.cap, P.llr[P.cur] + (size_t)(r0 - P.origin) * m,
+                             rb * P.cap, rb * (c - r0), S, cudaMemcpyDeviceToDevice, h->st));
+    // FIR output of symbols nb*block - W .. nb*block - 1 (the window moves by
+    // at least one block >= W, so source and destination do not overlap)
+    const size_t eb = store_bytes(h->prec);
+    char *y = static_cast<char *>(h->y);
+    const long ys = P.nb * Nb - P.origin - h->W, yd = P.nb * Nb - o - h->W;
+    CK(cudaMemcpy2DAsync(y + eb * yd, eb * P.cap, y + eb * ys, eb * P.cap, eb * h->W, (size_t)2 * S,
+                         cudaMemcpyDeviceToDevice, h->st));
+    P.origin = o;
+    P.cur = nx;
+    return RX_OK;
+}
+
+// Append n samples per polarisation (columns col .. col+n-1 of src,
+// [S][2][src_ns]), run what they complete, hand out n/2 rows.
+int push_piece(rx_handle *h, const float2 *src, long src_ns, long col, long n, float *out, long out_rows,
+               long out_off, bool fresh) {
+    auto &P = h->push;
+    const int S = h->streams;
+    if (P.tot - 2 * P.origin + n > 2 * P.cap)
+        return fail(RX_EINVAL, "internal: stream window of %ld symbols overflows", P.cap);
+    const size_t ip = sizeof(float2) * 2 * P.cap;
+    CK(cudaMemcpy2DAsync(P.in[P.cur] + (P.tot - 2 * P.origin), ip, src + col, sizeof(float2) * src_ns,
+                         sizeof(float2) * n, (size_t)2 * S, cudaMemcpyDefault, h->st));
+    P.tot += n;
+    int rc;
+    if ((rc = push_run(h, fresh)) != RX_OK) return rc;
+    if ((rc = push_emit(h, out, out_rows, out_off, P.emitted, n / 2)) != RX_OK) return rc;
+    P.emitted += n / 2;
+    return push_rebase(h);
+}
+
+int push_begin(rx_handle *h) {
+    auto &P = h->push;
+    if (P.on) return RX_OK;
+    if (h->user_x4 || h->user_s2) return fail(RX_EINVAL, "symbol outputs are not available when streaming");
+    P.tot = P.origin = P.nb = P.emitted = 0;
+    P.cur = 0;
+    push_geometry(h);
+    int rc = push_alloc(h);
+    if (rc != RX_OK) return rc;
+    h->started = false;
+    P.on = true;
+    return RX_OK;
+}
+
+int push_stats(rx_handle *h, rx_stats *stats, long first_valid) {
+    int rc = fill_stats(h, stats);
+    if (rc != RX_OK) return rc;
+    const long valid = std::max(0L, h->push.emitted - h->push.delay);
+    for (int s = 0; s < h->streams; ++s) {
+        stats[s].n_out = (uint64_t)valid;
+        stats[s].first_valid = (uint64_t)first_valid;
     }
     return RX_OK;
 }
@@ -841,6 +1115,7 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     if (rc != RX_OK) return rc;
     if (k == "overlap") h->tables_dirty = true;
     h->started = false;
+    h->push.on = false;
     return check_config(h);
 }
 
@@ -959,6 +1234,7 @@ void rx_destroy(rx_handle *h) {
     for (auto e : h->ev_lms) cudaEventDestroy(e);
     for (auto e : h->ev_pool) cudaEventDestroy(e);
     free_buffers(h);
+    push_free(h);
     cudaFree(h->x4);
     cudaFree(h->s2sym);
     cudaFree(h->H);
@@ -1133,6 +1409,7 @@ int rx_set_reference(rx_handle *h, const uint8_t *bits, size_t n_sym) {
     h->ref_n = (long)n_sym;
     h->ref_s = S;
     h->ref_host = nullptr;
+    h->push.on = false;
     if (!n_sym) return RX_OK;
     if (!h->ref) { CK(cudaMalloc(&h->ref, sizeof(reflab_t) * (size_t)S * n_sym)); h->ref_cap = (size_t)S * n_sym; }
     CK(launch_ref_labels(bits, h->ref, (long)n_sym, S, h->fmt.m, h->fmt.dims, h->fmt.m_pol, h->st));
@@ -1156,12 +1433,14 @@ int rx_set_reference_host(rx_handle *h, const uint8_t *bits, size_t n_sym) {
     }
     h->ref_host = bits;
     h->started = false;
+    h->push.on = false;
     return RX_OK;
 }
 
 
 int rx_reset(rx_handle *h) {
     if (!h) return fail(RX_EINVAL, "NULL handle");
+    h->push.on = false;
     h->started = false;
     h->blocks_done = 0;
     h->u = 0;
@@ -1173,11 +1452,116 @@ int rx_process(rx_handle *h, const void *samples, size_t n_samples, float *llr_o
     if (n_samples < 2 || (n_samples & 1)) return fail(RX_EINVAL, "n_samples must be a positive multiple of 2");
     const long N = (long)n_samples / 2;
     const long nblk = (N + h->block - 1) / h->block;
+    h->push.on = false;
     int rc = run_blocks(h, (const float2 *)samples, N, 0, nblk, llr_out);
     if (rc != RX_OK) return rc;
     CK(cudaGetLastError());
     if (stats) return fill_stats(h, stats);
     return RX_OK;
+}
+
+int rx_stream_delay(rx_handle *h, size_t *delay) {
+    if (!h || !delay) return fail(RX_EINVAL, "NULL argument");
+    int rc = check_config(h);
+    if (rc != RX_OK) return rc;
+    if (!h->push.on) push_geometry(h);
+    *delay = (size_t)h->push.delay;
+    return RX_OK;
+}
+
+int rx_push(rx_handle *h, const void *samples, size_t n_samples, float *llr_out, rx_stats *stats) {
+    if (!h) return fail(RX_EINVAL, "NULL handle");
+    if (n_samples % 2) return fail(RX_EINVAL, "n_samples must be a multiple of 2 (sps)");
+    if (n_samples && (!samples || !llr_out)) return fail(RX_EINVAL, "NULL argument");
+    int rc = check_config(h);
+    if (rc != RX_OK) return rc;
+    if ((rc = push_begin(h)) != RX_OK) return rc;
+    auto &P = h->push;
+    const long n = (long)n_samples, rows = n / 2;
+    const long first_valid = std::min(rows, std::max(0L, P.delay - P.emitted));
+    for (long c = 0; c < n;) {
+        const long piece = std::min(P.piece, n - c);
+        if ((rc = push_piece(h, static_cast<const float2 *>(samples), n, c, piece, llr_out, rows, c / 2, c == 0)) !=
+            RX_OK) {
+            P.on = false;
+            return rc;
+        }
+        c += piece;
+    }
+    CK(cudaGetLastError());
+    if (stats) return push_stats(h, stats, first_valid);
+    return RX_OK;
+}
+
+int rx_flush(rx_handle *h, float *llr_out, size_t *n_rows, rx_stats *stats) {
+    if (!h || !n_rows) return fail(RX_EINVAL, "NULL argument");
+    auto &P = h->push;
+    if (!P.on) return fail(RX_ESTATE, "no stream is being pushed");
+    const long N = P.tot / 2, e0 = std::max(0L, P.emitted - P.delay);
+    const long rows = N - e0;
+    if (rows > 0 && !llr_out) return fail(RX_EINVAL, "NULL llr_out");
+    const int S = h->streams, m = h->fmt.m;
+    const size_t rb = sizeof(float) * m;
+    int rc;
+    if (N > 0) {
+        // rows computed before the flush go first
+        const long c = push_done(h);
+        long off = 0;
+        if (c > e0) {
+            CK(cudaMemcpy2DAsync(llr_out, rb * rows, P.llr[P.cur] + (size_t)(e0 - P.origin) * m, rb * P.cap,
+                                 rb * (c - e0), S, cudaMemcpyDeviceToDevice, h->st));
+            off = c - e0;
+        }
+        // the rest as the end of a stream of N - origin symbols in the
+        // window (zeros after it, as in rx_process): the window's samples
+        // and the phase-search halo laid out for that length
+        const long Nf = N - P.origin, Nb = h->block;
+        const int nx = 1 - P.cur;
+        CK(cudaMemcpy2DAsync(P.in[nx], sizeof(float2) * 2 * Nf, P.in[P.cur], sizeof(float2) * 2 * P.cap,
+                             sizeof(float2) * 2 * Nf, (size_t)2 * S, cudaMemcpyDeviceToDevice, h->st));
+        if (P.nb > 0) {
+            const size_t eb = store_bytes(h->prec);
+            char *y = static_cast<char *>(h->y);
+            const long col = P.nb * Nb - P.origin - h->W;
+            CK(cudaMemcpy2DAsync(P.halo, eb * h->W, y + eb * col, eb * P.cap, eb * h->W, (size_t)2 * S,
+                                 cudaMemcpyDeviceToDevice, h->st));
+            CK(cudaMemcpy2DAsync(y + eb * col, eb * Nf, P.halo, eb * h->W, eb * h->W, (size_t)2 * S,
+                                 cudaMemcpyDeviceToDevice, h->st));
+        }
+        const Window w = push_window(h);
+        const long lb0 = P.nb - w.bofs, lb1 = (Nf + Nb - 1) / Nb;
+        if ((rc = run_blocks(h, P.in[nx], Nf, lb0, lb1, P.llr[nx], true, true, &w)) != RX_OK) {
+            P.on = false;
+            return rc;
+        }
+        const long k0 = std::max(c, e0);
+        if (N > k0)
+            CK(cudaMemcpy2DAsync(llr_out + (size_t)off * m, rb * rows, P.llr[nx] + (size_t)(k0 - P.origin) * m,
+                                 rb * Nf, rb * (N - k0), S, cudaMemcpyDeviceToDevice, h->st));
+        P.nb = w.bofs + lb1;
+    }
+    P.emitted = N + P.delay;
+    *n_rows = (size_t)std::max(0L, rows);
+    CK(cudaGetLastError());
+    rc = stats ? push_stats(h, stats, 0) : RX_OK;
+    if (stats)
+        for (int s = 0; s < S; ++s) stats[s].n_out = (uint64_t)N;
+    P.on = false;
+    return rc;
+}
+
+int rx_wait(rx_handle *h, double timeout_ms) {
+    if (!h || !(timeout_ms >= 0)) return fail(RX_EINVAL, "NULL handle or negative timeout");
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaStreamQuery(h->st);
+        if (e == cudaSuccess) return RX_OK;
+        if (e != cudaErrorNotReady) return fail(RX_ECUDA, "rx_wait: %s", cudaGetErrorString(e));
+        const double ms =
+            std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+        if (ms >= timeout_ms) return fail(RX_ETIMEDOUT, "the handle's work did not finish within %.3f ms", timeout_ms);
+        std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
 }
 
 int rx_get_stats(rx_handle *h, rx_stats *stats) {
@@ -1191,6 +1575,7 @@ int rx_process_host(rx_handle *h, const void *samples, size_t n_samples, float *
     if (n_samples < 2 || (n_samples & 1)) return fail(RX_EINVAL, "n_samples must be a positive multiple of 2");
     const int S = h->streams, m = h->fmt.m;
     const long N = (long)n_samples / 2, ns = (long)n_samples;
+    h->push.on = false;
     const size_t in_b = sizeof(float2) * (size_t)S * 2 * n_samples;
     const size_t out_b = sizeof(float) * (size_t)S * N * m;
     if (h->d_in_cap < in_b) { cudaFree(h->d_in); h->d_in = nullptr; CK(cudaMalloc(&h->d_in, in_b)); h->d_in_cap = in_b; }
@@ -1338,6 +1723,7 @@ int rx_process_blocks(rx_handle *h, const void *samples, size_t n_samples, size_
     const long nblk = (N + h->block - 1) / h->block;
     if (b1 <= b0 || (long)b1 > nblk)
         return fail(RX_EINVAL, "block range [%zu, %zu) not inside the stream's %ld blocks", b0, b1, nblk);
+    if (h->push.on) return fail(RX_ESTATE, "the handle is streaming (rx_push): rx_flush or rx_reset first");
     if (b0 > 0 && !(h->started && h->cur_n == N && h->blocks_done == (long)b0))
         return fail(RX_ESTATE, "block %zu does not continue the handle's stream (at block %ld of a %ld-symbol "
                     "stream%s)", b0, h->blocks_done, h->cur_n, h->started ? "" : ", not started");
@@ -1350,6 +1736,7 @@ int rx_process_blocks(rx_handle *h, const void *samples, size_t n_samples, size_
 
 int rx_get_state(rx_handle *h, void *buf, size_t *len) {
     if (!h || !len) return fail(RX_EINVAL, "NULL argument");
+    if (h->push.on) return fail(RX_ESTATE, "the handle is streaming (rx_push): rx_flush or rx_reset first");
     if (h->prec != SK_F32) return fail(RX_EINVAL, "stream state is kept for float32 storage only (precision 0)");
     if (!h->started || h->blocks_done < 1) return fail(RX_ESTATE, "no block of a stream has run yet");
     const StateLayout lay = state_layout(h);
@@ -1397,6 +1784,7 @@ int rx_get_state(rx_handle *h, void *buf, size_t *len) {
 
 int rx_set_state(rx_handle *h, const void *buf, size_t len) {
     if (!h || !buf) return fail(RX_EINVAL, "NULL argument");
+    h->push.on = false;
     if (h->prec != SK_F32) return fail(RX_EINVAL, "stream state is kept for float32 storage only (precision 0)");
     if (len < sizeof(rx_state_header)) return fail(RX_EINVAL, "state of %zu bytes is shorter than its header", len);
     rx_state_header hd;
@@ -1464,16 +1852,16 @@ int rx_cdc(rx_handle *h, const void *in, void *out, size_t n_samples) {
     if (in == out) return fail(RX_EINVAL, "in and out must differ");
     int rc = upload_tables(h);
     if (rc != RX_OK) return rc;
-    CK(launch_cdc((const float2 *)in, (float2 *)out, (long)n_samples, 2 * h->streams, h->n_fft,
-                  h->n_ov, h->H, h->tw, h->st));
+    CK(launch_cdc((const float2 *)in, out, (long)n_samples, 2 * h->streams, h->n_fft,
+                  h->n_ov, h->H, h->tw, h->st, 0, -1, h->prec));
     return RX_OK;
 }
 
 int rx_fir(rx_handle *h, const void *x, size_t n_samples, const void *taps, size_t k0, size_t k1, void *y) {
     if (!h || !x || !taps || !y) return fail(RX_EINVAL, "NULL argument");
     if (k1 < k0) return fail(RX_EINVAL, "k1 < k0");
-    CK(launch_fir((const float2 *)x, (long)n_samples, (const float2 *)taps, (long)k0, (long)k1,
-                  (float2 *)y, (long)(k1 - k0), 0, h->streams, h->T, h->st, SK_F32, 0, h->wl));
+    CK(launch_fir(x, (long)n_samples, (const float2 *)taps, (long)k0, (long)k1,
+                  y, (long)(k1 - k0), 0, h->streams, h->T, h->st, h->prec, 0, h->wl));
     return RX_OK;
 }
 

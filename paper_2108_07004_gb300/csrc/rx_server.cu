@@ -6,8 +6,10 @@
 // its own handle and CUDA stream and is processed one block at a time,
 // interleaved with every other admitted request, so the work of requests
 // that arrived at different times overlaps on the device.  A finished
-// request frees its handle (memory and slot) and the queue's head is
-// admitted at the next step.  Each request's computation is that of a
+// request frees its slot and its memory estimate; its handle (with its CUDA
+// stream and buffers) is kept idle for the next request with the same
+// creation key, so that no cudaFree stalls the running requests, and the
+// queue's head is admitted at the next step.  Each request's computation is that of a
 // handle processing the stream alone (the library's kernels are
 // deterministic), so its results do not depend on the mix.
 //
@@ -211,7 +213,10 @@ bool admit(rx_server *s, Req *q) {
         if (rc == RX_OK && cudaEventCreateWithFlags(&q->done, cudaEventDisableTiming) != cudaSuccess) rc = RX_ECUDA;
     }
     if (rc == RX_OK) rc = rx_set_stream(q->h, q->st);
-    if (rc == RX_OK && q->r.ref_bits) rc = rx_set_reference(q->h, q->r.ref_bits, q->N);
+    // a request without reference bits clears what a reused handle still
+    // holds from its previous request (no training stage, no counting)
+    if (rc == RX_OK) rc = q->r.ref_bits ? rx_set_reference(q->h, q->r.ref_bits, q->N)
+                                        : rx_set_reference(q->h, nullptr, 0);
     if (rc != RX_OK) {
         q->err = rx_last_error();
         q->state = Q_FAILED;

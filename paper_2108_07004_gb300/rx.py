@@ -44,7 +44,8 @@ class RxStats(C.Structure):
     _fields_ = [("n_sym", C.c_uint64), ("n_bits", C.c_uint64), ("bit_errors", C.c_uint64),
                 ("gmi_sum", C.c_double), ("gmi", C.c_double), ("ber", C.c_double),
                 ("evm_num", C.c_double), ("evm_den", C.c_double), ("sigma2_last", C.c_double),
-                ("n_out", C.c_uint64), ("blocks", C.c_uint32), ("reserved", C.c_uint32)]
+                ("n_out", C.c_uint64), ("blocks", C.c_uint32), ("reserved", C.c_uint32),
+                ("first_valid", C.c_uint64)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
@@ -63,6 +64,11 @@ _PROTOS = {
     "rx_process": (_I, [_VP, _VP, _SZ, _VP, _VP]),
     "rx_process_host": (_I, [_VP, _VP, _SZ, _VP, _VP]),
     "rx_get_stats": (_I, [_VP, _VP]),
+    "rx_stream_delay": (_I, [_VP, C.POINTER(_SZ)]),
+    "rx_push": (_I, [_VP, _VP, _SZ, _VP, _VP]),
+    "rx_flush": (_I, [_VP, _VP, C.POINTER(_SZ), _VP]),
+    "rx_wait": (_I, [_VP, _D]),
+    "rx_issue_rate": (_I, [_I, _I, C.POINTER(_D), C.POINTER(_D)]),
     "rx_get_profile": (_I, [_VP, C.c_char_p, C.POINTER(_D), C.POINTER(C.c_uint64)]),
     "rx_get_block_latency": (_I, [_VP, C.POINTER(_D), _SZ, C.POINTER(_SZ)]),
     "rx_get_state": (_I, [_VP, _VP, C.POINTER(_SZ)]),
@@ -307,6 +313,45 @@ class Receiver:
                                     C.cast(st, C.c_void_p) if st is not None else None))
         return llr, ([s.as_dict() for s in st] if st is not None else None)
 
+    # ---- streaming ----
+    def stream_delay(self) -> int:
+        """Fixed delay d (symbols) of push(): output row r holds symbol r - d."""
+        d = C.c_size_t()
+        _ck(lib().rx_stream_delay(self.h, C.byref(d)))
+        return d.value
+
+    def push(self, samples: torch.Tensor, llr: torch.Tensor | None = None, stats: bool = True):
+        """Next samples [S, 2, n] complex64 of a continuous stream -> n/2 LLR
+        rows [S, n/2, m] (row r of the stream holds symbol r - d)."""
+        S, _, n = samples.shape
+        if llr is None:
+            llr = torch.empty((S, n // 2, self.m), dtype=torch.float32, device="cuda")
+        st = (RxStats * S)() if stats else None
+        _ck(lib().rx_push(self.h, _ptr(samples), n, _ptr(llr),
+                          C.cast(st, C.c_void_p) if st is not None else None))
+        return llr, ([s.as_dict() for s in st] if st is not None else None)
+
+    def flush(self, llr: torch.Tensor | None = None, stats: bool = True):
+        """End the stream: the rows of the last min(N, d) symbols [S, rows, m]."""
+        S = self.streams
+        if llr is None:
+            llr = torch.empty((S, max(1, self.stream_delay()), self.m), dtype=torch.float32, device="cuda")
+        n = C.c_size_t()
+        st = (RxStats * S)() if stats else None
+        _ck(lib().rx_flush(self.h, _ptr(llr), C.byref(n),
+                           C.cast(st, C.c_void_p) if st is not None else None))
+        r = n.value                       # rows are packed: [S][r][m]
+        llr = llr.reshape(-1)[: S * r * self.m].view(S, r, self.m)
+        return llr, ([s.as_dict() for s in st] if st is not None else None)
+
+    def wait(self, timeout_ms: float) -> bool:
+        """True when the handle's queued work is done within timeout_ms."""
+        rc = lib().rx_wait(self.h, float(timeout_ms))
+        if rc == -4:
+            return False
+        _ck(rc)
+        return True
+
     def set_demapper(self, mlp: "Mlp | None"):
         """Use the learned demapper (None: the exact one)."""
         _ck(lib().rx_set_demapper(self.h, mlp.h if mlp is not None else None))
@@ -550,6 +595,14 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+
+def issue_rate(kind: int, iters: int = 4096) -> tuple[float, float]:
+    """(lane-instructions per second, device ms) of one FP32 instruction kind
+    (0 FFMA, 1 FFMA2, 2 FMNMX) on the current device."""
+    rate, ms = C.c_double(), C.c_double()
+    _ck(lib().rx_issue_rate(int(kind), int(iters), C.byref(rate), C.byref(ms)))
+    return rate.value, ms.value
 
 
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3

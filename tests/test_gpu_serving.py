@@ -114,3 +114,39 @@ def test_many_concurrent_requests_issued_from_several_threads(streams):
         assert stats["bit_errors"] == alone[i][1]["bit_errors"]
     assert srv.info()["max_active"] == 4 * len(REQS)
     srv.close()
+
+
+def test_reused_handle_without_reference_forgets_the_previous_one(streams):
+    """A request without reference bits that reuses a pooled handle (same
+    format, rate, taps and test phases) after a longer request with
+    reference bits: no training stage and no counting, exactly as when it
+    is served alone on a fresh server."""
+    from paper_2108_07004_gb300 import rx
+    i_long, i_short = 3, 1                  # gs4d64, 70001 and 50000 symbols, 31 taps, B = 64
+    fmt, n, km, esn0, T, B = REQS[i_short]
+    samples, _ = streams[i_short]
+
+    def submit_plain(srv):
+        llr = torch.full((n, M[fmt]), float("nan"), dtype=torch.float32, device="cuda")
+        rid = srv.submit(fmt, samples, llr, None, cd_ps_per_nm=17.0 * km, taps=T, bps_phases=B,
+                         fft=4096, overlap=1024, block=16384, n_pre=2048)
+        return rid, llr
+
+    alone = rx.Server(1 << 33, 4)
+    rid_a, llr_a = submit_plain(alone)
+    alone.run()
+    torch.cuda.synchronize()
+    _, stats_a = alone.poll(rid_a)
+    alone.close()
+
+    srv = rx.Server(1 << 33, 4)
+    _submit(srv, i_long, *streams[i_long])  # with reference bits: trains and counts
+    srv.run()
+    rid, llr = submit_plain(srv)            # takes over that request's pooled handle
+    srv.run()
+    torch.cuda.synchronize()
+    state, stats = srv.poll(rid)
+    srv.close()
+    assert state == rx.REQ_DONE
+    assert stats_a["n_sym"] == 0 and stats["n_sym"] == 0 and stats["bit_errors"] == 0
+    assert np.array_equal(llr.cpu().numpy(), llr_a.cpu().numpy())
