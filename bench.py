@@ -61,6 +61,30 @@ FDE_TRAFFIC = {"bytes": 1580040768, "sources": {
     "paper_2108_07004_gb300/csrc/fft_dev.h": "92a928291a79b5288f304fd8c6240edefe3569028d1f823498bb1d7ee0a7ac28"}}
 
 
+def issue_peaks(rx_mod, gpu: int) -> dict:
+    """Measured FP32 issue rates (lane-instructions/s) of FFMA, FFMA2 and
+    FMNMX on this GPU (rx_issue_rate: two blocks of 1024 threads per SM,
+    eight independent chains per thread), with the SM clock sampled while
+    the probes run; per_sm_clk = rate / (SMs x median SM clock)."""
+    import torch
+    n_sm = torch.cuda.get_device_properties(gpu).multi_processor_count
+    clk = Clocks(gpu)
+    clk.start()
+    time.sleep(0.3)
+    out = {}
+    for kind, name in ((0, "ffma"), (1, "ffma2"), (2, "fmnmx")):
+        rx_mod.issue_rate(kind, 2048)                        # ramp the clock
+        best = max(rx_mod.issue_rate(kind, 8192)[0] for _ in range(5))
+        out[name] = best
+    clocks = clk.stop()
+    mhz = clocks.get("sm_mhz")
+    res = {k: {"lane_instr_per_s": v,
+               "per_sm_clk": (v / (n_sm * mhz * 1e6)) if mhz else None} for k, v in out.items()}
+    res["clocks"] = clocks
+    res["sms"] = n_sm
+    return res
+
+
 def pinned_traffic(pin: dict):
     """The captured DRAM bytes while the kernel's sources hash to the captured ones, else None."""
     import hashlib
@@ -254,6 +278,43 @@ def parity_on(rx_mod, torch, st, res, wl: dict = WL, precision: int = 0):
             "bit_errors_gpu": int(stats[0]["bit_errors"]), "bit_errors_oracle": int(res.stats["bit_errors"])}
 
 
+def stage_errors(rx_mod, torch, st, res, wl: dict, precision: int) -> dict:
+    """Per-stage error of a storage form against the oracle on its sample:
+    EVM of the stored CDC output x (rx_cdc) and of the stored FIR output y
+    (rx_fir reading the stored x, with the oracle's taps of block 1)."""
+    from oracle import chain
+    r = rx_mod.Receiver(wl["fmt"], cd_ps_per_nm=wl["cd_ps_per_nm"], taps=wl["taps"],
+                        bps_phases=wl["bps_phases"], **rx_params(wl), precision=precision)
+    ns = st.rx.shape[1]
+    x_in = torch.from_numpy(st.rx[None]).cuda()
+    if precision:
+        xs = torch.zeros((1, 2, ns), dtype=torch.int32, device="cuda")
+        dt = torch.float16 if precision == 1 else torch.bfloat16
+
+        def unpack(t):
+            v = t.view(dt).float().cpu().numpy().astype(np.float64)
+            return v[..., 0::2] + 1j * v[..., 1::2]
+    else:
+        xs = torch.zeros((1, 2, ns), dtype=torch.complex64, device="cuda")
+
+        def unpack(t):
+            return t.cpu().numpy().astype(np.complex128)
+    r.cdc(x_in, xs)
+    x = unpack(xs)[0]
+    blk = wl["block"]
+    k0, k1 = blk, min(2 * blk, ns // 2)
+    taps = res.taps_used[1]
+    ys = torch.zeros((1, 2, k1 - k0), dtype=xs.dtype, device="cuda")
+    r.fir(xs, torch.from_numpy(taps.astype(np.complex64)[None]).cuda(), k0, k1, ys)
+    y = unpack(ys)[0]
+    yref = chain.fir(res.x, taps.astype(np.complex64).astype(np.complex128), k0, k1)
+    r.close()
+
+    def evm(a, b):
+        return float(np.sqrt(np.mean(np.abs(a - b) ** 2) / np.mean(np.abs(b) ** 2)))
+    return {"cdc_x_evm": evm(x, res.x), "fir_y_evm": evm(y, yref)}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -306,6 +367,11 @@ def run_ours(args):
     # live kernel time); the stage breakdown comes from profiled steps after
     r.set("profile", 2)
     for _ in range(args.warmup):
+        r.process(samples, llr, stats=False)
+    torch.cuda.synchronize()
+    # the roofline's denominator, measured on this GPU before the timed steps
+    ipk = issue_peaks(rx_mod, local) if rank == 0 else None
+    for _ in range(2):
         r.process(samples, llr, stats=False)
     torch.cuda.synchronize()
     clk = Clocks(local)
@@ -370,7 +436,16 @@ def run_ours(args):
     pk, pk_kind = peaks()
     bps_ms, bps_n = bps_live
     ops = S * n_sym * WL["bps_phases"] * 64            # candidate (phase, point) distances
+    # peak: one candidate per FP32 lane-instruction at the measured FFMA
+    # issue rate (the nominal 128 lanes x SMs x max clock if the probe fails)
     peak_ops = FP32_LANES_PER_SM * N_SM * SM_MAX_MHZ * 1e6 / 1e12
+    peak_from = "nominal: 128 FP32 lanes x 152 SMs x 2070 MHz (probe unavailable)"
+    if ipk and ipk["ffma"]["lane_instr_per_s"] > 0:
+        peak_ops = ipk["ffma"]["lane_instr_per_s"] / 1e12
+        c = ipk["clocks"]
+        peak_from = (f"measured: FFMA issue probe (rx_issue_rate), "
+                     f"{ipk['ffma']['per_sm_clk']:.1f} lane-instr/SM/clk at {c.get('sm_mhz')} MHz median"
+                     if ipk["ffma"]["per_sm_clk"] else "measured: FFMA issue probe (rx_issue_rate)")
     achieved = ops / (bps_ms * 1e-3) / 1e12 if bps_ms > 0 else None
     cdc_ms = stage["cdc"][0]
     cdc_bytes = S * 2 * 2 * n_sym * 8 * (WL["fft"] / (WL["fft"] - WL["overlap"]) + 1)
@@ -390,7 +465,8 @@ def run_ours(args):
                      "unit": "Top/s", "frac": (achieved / peak_ops) if achieved else None,
                      "traffic": bps_traffic() if n_sym == WL["n_sym"] and S == 9 else None,
                      "op": "one (test phase, constellation point) candidate distance",
-                     "peak_from": "128 FP32 lanes x 152 SMs x 2070 MHz"},
+                     "peak_from": peak_from,
+                     "issue_probe": ipk},
         "realtime_channels": value / (WL["symbol_rate"] * 6 / 1e9),
         "stages_ms": {k: v[0] for k, v in stage.items()},
         "stage_hbm": {"cdc": {"achieved_gbs": cdc_bytes / (cdc_ms * 1e-3) / 1e9 if cdc_ms else None,
@@ -933,6 +1009,17 @@ def run_precision(args):
         if not args.no_parity:
             line["parity"] = {name: parity_on(rx_mod, torch, st_o, res_o, wl, prec)
                               for prec, name in ((0, "f32"), (1, "f16"), (2, "bf16"))}
+            # the error against the oracle stage by stage: stored x, stored y,
+            # de-rotated z, LLRs, and the bit errors against the oracle's
+            per_stage = {}
+            for prec, name in ((0, "f32"), (1, "f16"), (2, "bf16")):
+                pe = stage_errors(rx_mod, torch, st_o, res_o, wl, prec)
+                pq = line["parity"][name]
+                pe.update({"z_evm": pq["evm_vs_oracle"], "max_rel_llr_err": pq["max_rel_llr_err"],
+                           "ber_delta_vs_oracle": (pq["bit_errors_gpu"] - pq["bit_errors_oracle"]) /
+                           max(1, pq["bit_errors_oracle"])})
+                per_stage[name] = pe
+            line["per_stage_error"] = per_stage
     print(json.dumps(line), flush=True)
 
 

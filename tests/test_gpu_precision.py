@@ -1,13 +1,16 @@
 """The precision variant: the chain's CDC and FIR outputs stored as half or
 bfloat16 pairs (float32 arithmetic, LMS and unwrap in float32), against the
-FP64 oracle: error of the de-rotated symbols (EVM against the oracle's z),
-the largest LLR error, and the BER against the oracle's.
+FP64 oracle, stage by stage: EVM of the stored CDC output x and of the
+stored FIR output y, error of the de-rotated symbols (EVM against the
+oracle's z), the largest LLR error, and the BER against the oracle's.
 
 Bounds follow the storage rounding: a stored sample carries a relative
 error up to 2^-11 (half) or 2^-8 (bfloat16); x passes through the 31-tap
 FIR and y is read again, so z carries about sqrt(2 * 31) rounding errors of
 x-size plus one of y-size: relative RMS below 3 * 2^-11 (half) and 3 * 2^-8
-(bfloat16) of |z| beside the float32 chain's own ~1e-6."""
+(bfloat16) of |z| beside the float32 chain's own ~1e-6.  The stored x
+itself carries one rounding (RMS below the unit of its format), and y the
+FIR of x's roundings plus its own (below 3 units, as z)."""
 import numpy as np
 import pytest
 
@@ -73,3 +76,39 @@ def test_state_needs_float32_storage(case):
     with pytest.raises(rx.RxError) as e:
         r.get_state()
     assert e.value.code == -1
+
+
+def _evm(a, ref):
+    return float(np.sqrt(np.mean(np.abs(a - ref) ** 2) / np.mean(np.abs(ref) ** 2)))
+
+
+def _pairs(t, prec):
+    """[S][2][n] half / bfloat16 pairs (stored as int32 words) -> complex128."""
+    dt = torch.float16 if prec == 1 else torch.bfloat16
+    v = t.view(dt).float().cpu().numpy().astype(np.float64)
+    return v[..., 0::2] + 1j * v[..., 1::2]
+
+
+@pytest.mark.parametrize("prec,unit", [(1, 2.0 ** -11), (2, 2.0 ** -8)])
+def test_stage_storage_error_cdc_and_fir(case, prec, unit):
+    """Per stage: rx_cdc and rx_fir with the reduced storage (x stored, the
+    FIR reading the stored x and storing y) against the oracle's x and its
+    FIR with the same taps."""
+    from paper_2108_07004_gb300 import rx
+    st, p, res = case
+    r = rx.Receiver("gs4d64", cd_ps_per_nm=17000.0, taps=31, bps_phases=64)
+    for k, v in (("fft", 4096), ("overlap", 1024), ("precision", prec)):
+        r.set(k, v)
+    ns = st.rx.shape[1]
+    x_in = torch.from_numpy(st.rx[None].astype(np.complex64)).cuda()
+    xs = torch.zeros((1, 2, ns), dtype=torch.int32, device="cuda")       # 4-byte pairs
+    r.cdc(x_in, xs)
+    x = _pairs(xs, prec)[0]
+    assert _evm(x, res.x) < unit, (_evm(x, res.x), unit)
+    taps = res.taps_used[2]
+    k0, k1 = 2 * p.block, 3 * p.block
+    ys = torch.zeros((1, 2, k1 - k0), dtype=torch.int32, device="cuda")
+    r.fir(xs, torch.from_numpy(taps.astype(np.complex64)[None]).cuda(), k0, k1, ys)
+    y = _pairs(ys, prec)[0]
+    ref = chain.fir(res.x, taps.astype(np.complex64).astype(np.complex128), k0, k1)
+    assert _evm(y, ref) < 3 * unit, (_evm(y, ref), unit)
