@@ -44,11 +44,15 @@ extern "C" {
 #define RX_EBUSY     (-5)   /* handle in use / parameter locked            */
 #define RX_ESTATE    (-6)   /* call out of order (e.g. no reference set)   */
 
-/* built-in formats (Gray-mapped square QAM on each polarisation) */
+/* built-in formats: Gray-mapped square QAM on each polarisation (1-3) and
+ * the 4D 64-ary geometrically shaped format (4: the library's design by the
+ * paper's Sec. 5 optimiser, frozen in data/gs4d64_v1.json and compiled in;
+ * the paper prints no 4D table) */
 #define RX_FMT_CUSTOM   0
 #define RX_FMT_DP_QPSK  1
 #define RX_FMT_DP_16QAM 2
 #define RX_FMT_DP_64QAM 3
+#define RX_FMT_GS4D64   4
 
 typedef struct rx_handle rx_handle;
 
@@ -520,7 +524,10 @@ int rx_unwrap(rx_handle *h, const void *y, size_t n_y, const uint8_t *b,
  * block) plus 4 bytes per stream; a call that would need more than the
  * 64 KiB returns RX_EINVAL without launching anything.  The first call on
  * a device looks up the array's device address with that device current
- * (once per device; make that first call before any stream capture).  All
+ * (once per device; make that first call before any stream capture).  The
+ * address is kept for the life of the process: after cudaDeviceReset on a
+ * device, or under another context than the device's primary one, it is
+ * stale, so such a program must not call this entry point again.  All
  * calls share the array and it keeps the last call's contents: the tickets
  * are cleared at the start of every call, so calls that are ordered on the
  * GPU are independent, but calls that overlap on the GPU (different streams,

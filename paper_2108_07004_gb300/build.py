@@ -35,7 +35,7 @@ def sources() -> list[str]:
 def _compile(nvcc: str, src: str, verbose: bool) -> str:
     obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
     cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-pthread",
-           "-I", INCLUDE, "-I", CSRC, "-c", src, "-o", obj]
+           "-I", INCLUDE, "-I", CSRC, "-I", BUILD, "-c", src, "-o", obj]
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -46,14 +46,45 @@ def _compile(nvcc: str, src: str, verbose: bool) -> str:
     return obj
 
 
+TABLES = os.path.join(HERE, "data", "gs4d64_v1.json")
+
+
+def write_tables() -> str:
+    """The built-in 4D 64-ary GS table (RX_FMT_GS4D64) as C arrays from the
+    frozen design file: float32 points as exact hexadecimal literals, in the
+    file's row order, with their labels."""
+    import json
+    import struct
+    with open(TABLES) as f:
+        d = json.load(f)
+    assert d["dims"] == 4 and d["m_bits"] == 6 and len(d["points"]) == 64
+
+    def hexf(v: float) -> str:
+        x = struct.unpack("<f", struct.pack("<f", v))[0]      # the float32 value
+        return f"{float(x).hex()}f" if x != 0 else "0.0f"
+    rows = ",\n".join("    {" + ", ".join(hexf(v) for v in r) + "}" for r in d["points"])
+    labs = ", ".join(str(int(v)) for v in d["labels"])
+    out = os.path.join(BUILD, "gs4d64_table.inc")
+    text = (f"// Generated by build.py from data/gs4d64_v1.json (sha256 {d['sha256']}).\n"
+            f"static const float kGs4d64Points[64][4] = {{\n{rows}}};\n"
+            f"static const uint32_t kGs4d64Labels[64] = {{{labs}}};\n")
+    os.makedirs(BUILD, exist_ok=True)
+    if not os.path.exists(out) or open(out).read() != text:
+        with open(out, "w") as f:
+            f.write(text)
+    return out
+
+
 def build(verbose: bool = False, force: bool = False) -> str:
     srcs = sources()
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".h")]
     headers.append(os.path.join(INCLUDE, "rx.h"))
+    headers.append(TABLES)
+    os.makedirs(BUILD, exist_ok=True)
+    write_tables()
     if (not force and os.path.exists(LIB) and
             os.path.getmtime(LIB) > max(os.path.getmtime(p) for p in srcs + headers)):
         return LIB
-    os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     with cf.ThreadPoolExecutor(max_workers=min(8, len(srcs))) as ex:
         objs = list(ex.map(lambda s: _compile(nvcc, s, verbose), srcs))

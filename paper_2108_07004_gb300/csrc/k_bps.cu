@@ -144,6 +144,8 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
             const int hb = B >> 1;
             // test phases b and b + B/2 together: phi_{b+B/2} = phi_b + pi/S, a
             // rotation of P + jQ that half_turn_d applies without another multiply
+            // two phase pairs per trip: independent min chains for the scheduler
+#pragma unroll 2
             for (int b = 0; b < hb; ++b) {
                 const f32x2 *cp1 = reinterpret_cast<const f32x2 *>(f.csp[b]);
                 const f32x2 C1 = cp1[0], S1 = cp1[1];

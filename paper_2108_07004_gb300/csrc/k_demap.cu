@@ -151,64 +151,88 @@ __device__ __forceinline__ bool llr_table(float2 z0, float2 z1, const FmtDev &f,
 }
 
 // Eight consecutive labels g8 .. g8+7 as packed pairs E[v] = (e_{2v}, e_{2v+1})
-// (the low three label bits vary, the high ones are those of g8): subset
-// sums of the low three bits by a small tree, the group total for the high
-// bits.
+// (the low three label bits vary, the high ones are those of g8): packed
+// running sums for the low three bits (bit 0: evens / odds of every group;
+// bit 1: F = (e0+e4, e1+e5) / G = (e2+e6, e3+e7) per group, i.e. labels
+// with bit 1 clear / set; bit 2: H = (e0+e2, e1+e3) / I = (e4+e6, e5+e7)),
+// and the group total for the high bits, added once per group.
+struct GroupSums {
+    f32x2 b0 = 0ull, f = 0ull, g = 0ull, h = 0ull, i = 0ull;
+};
 template <int MB>
-__device__ __forceinline__ void add_group8(const f32x2 (&E)[4], int g8, f32x2 &s01, float (&s0)[MB],
+__device__ __forceinline__ void add_group8(const f32x2 (&E)[4], int g8, GroupSums &gs, float (&s0)[MB],
                                            float (&s1)[MB]) {
     const f32x2 H = add2(E[0], E[1]), I = add2(E[2], E[3]);   // (e0+e2, e1+e3), (e4+e6, e5+e7)
     const f32x2 F = add2(E[0], E[2]), G = add2(E[1], E[3]);   // (e0+e4, e1+e5), (e2+e6, e3+e7)
-    s01 = add2(s01, add2(H, I));                              // bit 0: (evens, odds)
-    float hx, hy, ix, iy, fx, fy, gx, gy;
-    upk2(H, hx, hy);
-    upk2(I, ix, iy);
-    upk2(F, fx, fy);
-    upk2(G, gx, gy);
-    s0[1] += fx + fy;
-    s1[1] += gx + gy;
-    const float q0 = hx + hy, q1 = ix + iy;
-    s0[2] += q0;
-    s1[2] += q1;
-    const float tot = q0 + q1;
+    const f32x2 HI = add2(H, I);                              // (evens, odds) of the group
+    gs.b0 = add2(gs.b0, HI);
+    gs.f = add2(gs.f, F);
+    gs.g = add2(gs.g, G);
+    gs.h = add2(gs.h, H);
+    gs.i = add2(gs.i, I);
+    if (MB > 3) {
+        float hx, hy;
+        upk2(HI, hx, hy);
+        const float tot = hx + hy;
 #pragma unroll
-    for (int i = 3; i < MB; ++i) {
-        if ((g8 >> i) & 1) s1[i] += tot;
-        else s0[i] += tot;
+        for (int b = 3; b < MB; ++b) {
+            if ((g8 >> b) & 1) s1[b] += tot;
+            else s0[b] += tot;
+        }
     }
 }
 
 // 4D table of MT points with MB label bits, streaming form: the shift is the
 // minimum distance from the orbit form (|z|^2 + |rep|^2 - 2 max(|P|,|Q|)),
-// which also gives the nearest point's energy; then every point's exact
-// distance |z - s_j|^2 (differences, no cancellation) and exponential is
-// added to the subset sums of its label bits, eight labels at a time.  The
-// loop is fully unrolled, so every table entry is a constant-bank operand
-// and every label bit is known at compile time; twelve accumulators instead
-// of 64 stored terms keep the registers low.
+// two orbits at a time as packed pairs; its orbit comes with it as the low
+// four bits of a signed-integer key (distance bits with the low four
+// cleared, so ties and 2^-19 differences go to the lower orbit; the shift
+// and the nearest point's energy need no more), and gives the nearest
+// point's energy.  Then every point's exact distance |z - s_j|^2
+// (differences, no cancellation) and exponential is added to the subset
+// sums of its label bits, eight labels at a time.  The loop is fully
+// unrolled, so every table entry is a constant-bank operand and every label
+// bit is known at compile time; a few packed accumulators instead of 64
+// stored terms keep the registers low.
 template <int MT, int MB>
 __device__ __forceinline__ bool llr_4d_stream(float2 z0, float2 z1, const FmtDev &f, float c2,
                                               float *out, float &gmin, float &emin, int ref,
                                               int &ne, float &g2) {
-    float g = 3.0e38f, eg = 0.f;
     const float zn = cnorm(z0) + cnorm(z1);
+    const f32x2 Z0 = pk2(z0.x, z0.x), Z1 = pk2(z0.y, z0.y), Z2 = pk2(z1.x, z1.x), Z3 = pk2(z1.y, z1.y);
+    {
+        // Re c and Im c of c = sum_p z_p conj(rep_p), two orbits per packed pair
+        const f32x2 N0 = pk2(-z0.x, -z0.x), N2 = pk2(-z1.x, -z1.x), ZN = pk2(zn, zn), M2 = pk2(-2.f, -2.f);
+        const f32x2 *R0 = reinterpret_cast<const f32x2 *>(f.orbT[0]);
+        const f32x2 *R1 = reinterpret_cast<const f32x2 *>(f.orbT[1]);
+        const f32x2 *R2 = reinterpret_cast<const f32x2 *>(f.orbT[2]);
+        const f32x2 *R3 = reinterpret_cast<const f32x2 *>(f.orbT[3]);
+        const f32x2 *EO = reinterpret_cast<const f32x2 *>(f.orbeP);
+        int key = 0x7fffffff;
 #pragma unroll
-    for (int o = 0; o < 16; ++o) {
-        if (o < f.n_orb) {
-            const float P = z0.x * f.orb[o][0] + z0.y * f.orb[o][1] + z1.x * f.orb[o][2] + z1.y * f.orb[o][3];
-            const float Q = z0.y * f.orb[o][0] - z0.x * f.orb[o][1] + z1.y * f.orb[o][2] - z1.x * f.orb[o][3];
-            const float v = (f.S == 4) ? fmaxf(fabsf(P), fabsf(Q)) : (f.S == 2 ? fabsf(P) : P);
-            const float d = zn + f.orbe[o] - 2.f * v;
-            if (d < g) { g = d; eg = f.orbe[o]; }
+        for (int op = 0; op < 8; ++op) {
+            if (2 * op < f.n_orb) {
+                const f32x2 P = fma2(Z3, R3[op], fma2(Z2, R2[op], fma2(Z1, R1[op], mul2(Z0, R0[op]))));
+                const f32x2 Q = fma2(N2, R3[op], fma2(Z3, R2[op], fma2(N0, R1[op], mul2(Z1, R0[op]))));
+                float p0, p1, q0, q1, v0, v1, d0, d1;
+                upk2(P, p0, p1);
+                upk2(Q, q0, q1);
+                v0 = (f.S == 4) ? fmaxf(fabsf(p0), fabsf(q0)) : (f.S == 2 ? fabsf(p0) : p0);
+                v1 = (f.S == 4) ? fmaxf(fabsf(p1), fabsf(q1)) : (f.S == 2 ? fabsf(p1) : p1);
+                upk2(fma2(M2, pk2(v0, v1), add2(ZN, EO[op])), d0, d1);   // +inf past n_orb
+                key = min(key, (__float_as_int(d0) & ~15) | (2 * op));
+                key = min(key, (__float_as_int(d1) & ~15) | (2 * op + 1));
+            }
         }
+        gmin = __int_as_float(key & ~15);
+        emin = f.orbeP[key & 15];
     }
-    const float sh = fmaf(g, c2, kOff);      // exponent of point j: sh - d_j c2
+    const float sh = fmaf(gmin, c2, kOff);   // exponent of point j: sh - d_j c2
     float s0[MB], s1[MB];
 #pragma unroll
     for (int i = 0; i < MB; ++i) { s0[i] = 0.f; s1[i] = 0.f; }
-    f32x2 s01 = pk2(0.f, 0.f);
+    GroupSums gs;
     // labels j, j+1 as packed pairs: d = sum_c (z_c - s_c)^2 per lane
-    const f32x2 Z0 = pk2(z0.x, z0.x), Z1 = pk2(z0.y, z0.y), Z2 = pk2(z1.x, z1.x), Z3 = pk2(z1.y, z1.y);
     const f32x2 NC = pk2(-c2, -c2), SH = pk2(sh, sh);
     const f32x2 *T0 = reinterpret_cast<const f32x2 *>(f.ptsT[0]);
     const f32x2 *T1 = reinterpret_cast<const f32x2 *>(f.ptsT[1]);
@@ -230,11 +254,21 @@ __device__ __forceinline__ bool llr_4d_stream(float2 z0, float2 z1, const FmtDev
             upk2(fma2(d, NC, SH), a0, a1);
             E[v] = pk2(ex2_ftz(a0), ex2_ftz(a1));
         }
-        add_group8<MB>(E, g8, s01, s0, s1);
+        add_group8<MB>(E, g8, gs, s0, s1);
     }
-    upk2(s01, s0[0], s1[0]);
-    gmin = fmaxf(g, 0.f);
-    emin = eg;
+    {
+        float x, y;
+        upk2(gs.b0, s0[0], s1[0]);
+        upk2(gs.f, x, y);
+        s0[1] = x + y;
+        upk2(gs.g, x, y);
+        s1[1] = x + y;
+        upk2(gs.h, x, y);
+        s0[2] = x + y;
+        upk2(gs.i, x, y);
+        s1[2] = x + y;
+    }
+    gmin = fmaxf(gmin, 0.f);
     bool low = false;
     ne = 0;
     g2 = 0.f;

@@ -35,10 +35,16 @@ struct __align__(16) FmtDev {
     int orb_lab[RX_MAXM][4];    // label of representative o rotated by k quarter turns (k < S)
     float cs[RX_MAXB][2];       // cos, sin of the test phases phi_b
     float csp[RX_MAXB][4];      // (cos, cos, sin, sin) of phi_b, for packed pairs
+    // the (at most 16) orbit representatives component-major (orbits o, o+1
+    // adjacent: packed pairs) and their energies, +inf past n_orb
+    float orbT[4][16];
+    float orbeP[16];
 };
 static_assert(offsetof(FmtDev, csp) % 16 == 0, "packed phase table must be 16-byte aligned");
 static_assert(offsetof(FmtDev, ptsT) % 8 == 0, "packed point pairs must be 8-byte aligned");
 static_assert(alignof(FmtDev) == 16, "FmtDev alignment");
+static_assert(offsetof(FmtDev, orbT) % 8 == 0 && offsetof(FmtDev, orbeP) % 8 == 0,
+              "packed orbit pairs must be 8-byte aligned");
 
 // Per-stream device state.
 struct StreamDev {
@@ -184,6 +190,20 @@ cudaError_t launch_bps(const void *y, long y_stride, long a, long e, long n_vali
                        int W, uint8_t *bout, long bout_stride, long bout_off,
                        int *dsum, double *mdsum, int chunks, int n_streams, const FmtDev &f,
                        cudaStream_t st, int sk = SK_F32);
+
+// Phase search with the correlations on the tensor cores (k_bps_tc.cu): 4D
+// tables of 16 orbits with S = 4 and B a multiple of 16.  W: the B operand
+// (bps_tc_table_floats(B) floats, built by bps_tc_table), device memory.
+bool bps_tc_supported(const FmtDev &f);
+size_t bps_tc_table_floats(int B);
+void bps_tc_table(const FmtDev &f, float *out);
+int bps_chunks_tc(long len, int n_streams, int sm_avail = 0);
+cudaError_t launch_bps_tc(const void *y, long y_stride, long a, long e, long n_valid, int W, uint8_t *bout,
+                          long bout_stride, long bout_off, int *dsum, double *mdsum, int chunks, int n_streams,
+                          const float *Wg, const FmtDev &f, cudaStream_t st, int sk = SK_F32);
+// 1 if a bounded wait of the tensor-core phase search gave up since the last
+// call (the flag is then cleared)
+cudaError_t bps_tc_status(unsigned int *flag);
 
 cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long b_stride,
                           long b_off, long a, long e, const int *dsum,

@@ -17,7 +17,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "librx.so")
 _lib = None
 
-RX_FMT_CUSTOM, RX_FMT_DP_QPSK, RX_FMT_DP_16QAM, RX_FMT_DP_64QAM = 0, 1, 2, 3
+RX_FMT_CUSTOM, RX_FMT_DP_QPSK, RX_FMT_DP_16QAM, RX_FMT_DP_64QAM, RX_FMT_GS4D64 = 0, 1, 2, 3, 4
 
 
 class RxError(RuntimeError):
@@ -213,8 +213,9 @@ def load_table(name: str) -> dict:
 
 
 def make_format(fmt: str):
-    """rx_format for a built-in name or a table file; returns (format, arrays
-    that must stay alive while it is used)."""
+    """rx_format for a built-in name or a table file ("table:<name>" forces
+    the table file of a built-in); returns (format, arrays that must stay
+    alive while it is used)."""
     f = RxFormat()
     keep = []
     if fmt == "dp_qpsk":
@@ -223,8 +224,10 @@ def make_format(fmt: str):
         f.kind = RX_FMT_DP_16QAM
     elif fmt == "dp_64qam":
         f.kind = RX_FMT_DP_64QAM
+    elif fmt == "gs4d64":
+        f.kind = RX_FMT_GS4D64
     else:
-        d = load_table(fmt)
+        d = load_table(fmt[len("table:"):] if fmt.startswith("table:") else fmt)
         pts = np.ascontiguousarray(np.asarray(d["points"], dtype=np.float32))
         labs = np.ascontiguousarray(np.asarray(d["labels"], dtype=np.uint32))
         keep += [pts, labs]

@@ -46,3 +46,18 @@ def test_error_path_without_device(lib):
     assert lib.rx_create(None, ctypes.c_double(28e9), 2, ctypes.c_double(0.0), 15, 32) is None
     assert b"format" in lib.rx_last_error()
     lib.rx_destroy(None)    # NULL-safe
+
+
+def test_builtin_gs4d64_table_is_the_design_file():
+    """The C arrays build.py writes for RX_FMT_GS4D64 hold exactly the float32
+    points and labels of data/gs4d64_v1.json."""
+    import json
+    import numpy as np
+    from paper_2108_07004_gb300 import build
+    text = open(build.write_tables()).read()
+    body = text.split("kGs4d64Points[64][4] = {", 1)[1].split("};", 1)[0]
+    vals = [float.fromhex(v.strip().rstrip("f")) for v in re.findall(r"-?0x[0-9a-fp.+-]+f|0\.0f", body)]
+    labs = [int(v) for v in text.split("kGs4d64Labels[64] = {", 1)[1].split("}", 1)[0].split(",")]
+    d = json.load(open(os.path.join(ROOT, "paper_2108_07004_gb300", "data", "gs4d64_v1.json")))
+    assert np.array_equal(np.array(vals, np.float32).reshape(64, 4), np.array(d["points"], np.float32))
+    assert labs == d["labels"]

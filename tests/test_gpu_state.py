@@ -110,3 +110,19 @@ def test_state_and_range_errors(stream):
     assert e.value.code == -1
     # a rejected state changed nothing: the stream still continues at block 2
     r.process_blocks(x, 2, 3)
+
+
+def test_builtin_gs4d64_equals_its_table_file():
+    """RX_FMT_GS4D64 (the table compiled in from data/gs4d64_v1.json) gives
+    the same receiver as the same table passed as a custom format."""
+    from paper_2108_07004_gb300 import rx
+    st = synth.make_stream("gs4d64", 20000, seed=synth.stream_seed(9, 77), esn0_db=13.0,
+                           cd_ps_per_nm=2000.0, linewidth_ts=1e-5)
+    out = []
+    for fmt in ("gs4d64", "table:gs4d64"):
+        r = rx.Receiver(fmt, cd_ps_per_nm=2000.0, taps=31, bps_phases=64, fft=4096, overlap=1024, block=4096)
+        assert (r.dims, r.m, r.M) == (4, 6, 64)
+        r.set_reference(torch.from_numpy(st.bits[None]).cuda())
+        llr, stats = r.process(torch.from_numpy(st.rx[None]).cuda())
+        out.append((llr.cpu().numpy(), stats[0]["bit_errors"]))
+    assert np.array_equal(out[0][0], out[1][0]) and out[0][1] == out[1][1]
