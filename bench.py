@@ -1227,6 +1227,56 @@ def run_learned(args):
     print(json.dumps(line), flush=True)
 
 
+def run_bps_paths(args):
+    """The phase search alone at the bench's launch shape (9 streams x one
+    2^16-symbol block, 64 test phases, window 64), SIMT kernel against the
+    tensor-core one (bps_tc = 1): candidates per second, fraction of the
+    measured FFMA issue peak, and the share of indices on which they differ."""
+    import torch
+    from paper_2108_07004_gb300 import rx as rx_mod
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    S, blk = 9, 1 << 16
+    rng = np.random.default_rng(2108)
+    pts = np.array(rx_mod.load_table("gs4d64")["points"], np.float64)
+    lab = rng.integers(0, 64, size=(S, 2 * blk))
+    sym = pts[lab]
+    y = np.stack([sym[..., 0] + 1j * sym[..., 1], sym[..., 2] + 1j * sym[..., 3]], axis=1)
+    ph = np.cumsum(rng.standard_normal((S, 2 * blk)) * 0.01, axis=1)[:, None, :]
+    y = y * np.exp(1j * ph) + 0.12 * (rng.standard_normal(y.shape) + 1j * rng.standard_normal(y.shape))
+    yd = torch.from_numpy(y.astype(np.complex64)).cuda()
+    a, e = blk - 32, 2 * blk - 32
+    cand = S * (e - a) * 64 * 64
+    ipk = issue_peaks(rx_mod, 0)
+    peak = ipk["ffma"]["lane_instr_per_s"]
+    out, idx = {}, {}
+    for tc, name in ((0, "simt"), (1, "tensor_cores")):
+        r = rx_mod.Receiver("gs4d64", cd_ps_per_nm=0.0, taps=31, bps_phases=64, streams=S)
+        r.set("bps_tc", tc)
+        bo = torch.zeros((S, e - a), dtype=torch.uint8, device="cuda")
+        for _ in range(max(3, args.warmup)):
+            r.bps(yd, a, e, 2 * blk, bo)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.steps):
+            r.bps(yd, a, e, 2 * blk, bo)
+        e1.record()
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) / args.steps * 1e3
+        idx[name] = bo.cpu().numpy()
+        out[name] = {"us_per_launch": us, "Tcand_per_s": cand / (us * 1e-6) / 1e12,
+                     "frac_of_ffma_peak": cand / (us * 1e-6) / peak}
+        r.close()
+    line = {"metric": "phase-search candidates per second (one (test phase, point) distance)",
+            "value": out["simt"]["Tcand_per_s"], "unit": "Tcand/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic 4D-64 symbols with phase drift and noise",
+            "config": {"workload": "bps_9x2p16_gs4d64_B64_W64", "streams": S, "block": blk},
+            "paths": out, "differ_frac": float(np.mean(idx["simt"] != idx["tensor_cores"])),
+            "peak_ffma_lane_instr_per_s": peak, "clocks": ipk["clocks"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -1240,7 +1290,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision", "serving", "block_lms", "widely_linear", "kk", "kk_chain", "mlp_infer"],
+    ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision", "serving", "block_lms", "widely_linear", "kk", "kk_chain", "mlp_infer", "bps_paths"],
                     help="learned: train the MLP demapper on chain output, compare with the exact one; "
                          "precision: DP-QPSK chain with CDC/FIR data in float32, half and bfloat16; "
                          "serving: 64 mixed streams with Poisson arrivals through the continuous-batching server")
@@ -1263,6 +1313,8 @@ def main():
         run_mlp_infer(args)
     elif args.variant == "precision":
         run_precision(args)
+    elif args.variant == "bps_paths":
+        run_bps_paths(args)
     elif args.variant == "serving":
         run_serving(args)
     else:

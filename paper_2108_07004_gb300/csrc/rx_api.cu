@@ -13,12 +13,14 @@
 #include <cstdlib>
 #include <cstring>
 #include <chrono>
+#include <limits>
 #include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
 
 #include "rx_internal.h"
+#include "gs4d64_table.inc"   // kGs4d64Points, kGs4d64Labels (written by build.py)
 #include "k_kk.h"
 #include "k_fde.h"
 #include "k_init.h"
@@ -146,6 +148,10 @@ struct rx_handle {
     cudaStream_t side_x[3] = {nullptr, nullptr, nullptr};
     // device tables
     float2 *H = nullptr, *tw = nullptr;
+    // the tensor-core phase search (parameter "bps_tc", default on where the
+    // format allows): its B operand, built for the table and B test phases
+    int bps_tc = 0;
+    float *bps_w = nullptr;
     int tab_fft = 0;
     bool tables_dirty = true;
     // device buffers
@@ -266,21 +272,24 @@ int build_format(const rx_format *f, FmtDev &d) {
         mb = f->kind == RX_FMT_DP_QPSK ? 2 : (f->kind == RX_FMT_DP_16QAM ? 4 : 6);
         S = 4;
         gray_qam(mb, pts);
-    } else if (f->kind == RX_FMT_CUSTOM) {
-        dims = f->dims;
-        mb = f->m_bits;
-        S = f->sym_order;
+    } else if (f->kind == RX_FMT_CUSTOM || f->kind == RX_FMT_GS4D64) {
+        const bool gs = f->kind == RX_FMT_GS4D64;
+        dims = gs ? 4 : f->dims;
+        mb = gs ? 6 : f->m_bits;
+        S = gs ? 4 : f->sym_order;
+        const float *fp = gs ? &kGs4d64Points[0][0] : f->points;
+        const uint32_t *fl = gs ? kGs4d64Labels : f->labels;
         if (dims != 2 && dims != 4) return fail(RX_EINVAL, "format dims must be 2 or 4");
-        if (!f->points || !f->labels) return fail(RX_EINVAL, "custom format needs points and labels");
+        if (!fp || !fl) return fail(RX_EINVAL, "custom format needs points and labels");
         if (mb < 1 || mb > 6) return fail(RX_EINVAL, "m_bits %d out of range", mb);
         const int M = 1 << mb;
         pts.assign((size_t)M * dims, 0.f);
         std::vector<int> seen(M, 0);
         for (int i = 0; i < M; ++i) {
-            const uint32_t lab = f->labels[i];
+            const uint32_t lab = fl[i];
             if (lab >= (uint32_t)M || seen[lab]) return fail(RX_EINVAL, "labels are not a permutation");
             seen[lab] = 1;
-            for (int c = 0; c < dims; ++c) pts[(size_t)lab * dims + c] = f->points[(size_t)i * dims + c];
+            for (int c = 0; c < dims; ++c) pts[(size_t)lab * dims + c] = fp[(size_t)i * dims + c];
         }
     } else {
         return fail(RX_EINVAL, "unknown format kind %d", f->kind);
@@ -336,6 +345,10 @@ int build_format(const rx_format *f, FmtDev &d) {
         ++no;
     }
     d.n_orb = no;
+    for (int o = 0; o < 16; ++o) {
+        for (int c = 0; c < 4; ++c) d.orbT[c][o] = o < no ? d.orb[o][c] : 0.f;
+        d.orbeP[o] = o < no ? d.orbe[o] : std::numeric_limits<float>::infinity();
+    }
     if (no > 16) return fail(RX_EINVAL, "%d orbits under the rotation by 2pi/%d; at most 16 are supported", no, S);
     return RX_OK;
 }
@@ -358,7 +371,16 @@ double raised_cosine(double f, double rs, double beta) {
     return 0.0;
 }
 
+// whether the chain's phase search runs on the tensor cores
+bool use_bps_tc(const rx_handle *h) { return h->bps_tc && bps_tc_supported(h->fmt); }
+
 int upload_tables(rx_handle *h) {
+    if (use_bps_tc(h) && !h->bps_w) {
+        std::vector<float> w(bps_tc_table_floats(h->B));
+        bps_tc_table(h->fmt, w.data());
+        CK(cudaMalloc(&h->bps_w, sizeof(float) * w.size()));
+        CK(cudaMemcpy(h->bps_w, w.data(), sizeof(float) * w.size(), cudaMemcpyHostToDevice));
+    }
     if (!h->tables_dirty && h->tab_fft == h->n_fft) return RX_OK;
     const int n = h->n_fft;
     std::vector<float2> H(n), tw(n);
@@ -755,7 +777,8 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         STAGE(ST_FIR, st, 1, launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st, h->prec, avail, h->wl));
         const long a = std::max(0L, k0 - h->W / 2);
         const long e = (n == nblk - 1) ? N : k1 - h->W / 2;
-        const int chunks = bps_chunks(e - a, S, avail);
+        const bool tc = use_bps_tc(h);
+        const int chunks = tc ? bps_chunks_tc(e - a, S, avail) : bps_chunks(e - a, S, avail);
         const int par = (int)(g & 1);
         int *dsum_n = h->dsum + (size_t)par * S * h->cap_dsum;
         double *mdsum_n = h->mdsum + (size_t)par * S * h->cap_dsum;
@@ -763,8 +786,12 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         // (possibly of an earlier call: the demap stream is not joined between
         // the host entry's groups)
         if (g >= 2) CK(cudaStreamWaitEvent(st, h->ev_dm[par], 0));
-        STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, dsum_n, mdsum_n, chunks, S,
-                                        f, st, h->prec));
+        if (tc)
+            STAGE(ST_BPS, st, 1, launch_bps_tc(h->y, N, a, e, k1, h->W, h->bidx, N, a, dsum_n, mdsum_n, chunks, S,
+                                               h->bps_w, f, st, h->prec));
+        else
+            STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, dsum_n, mdsum_n, chunks, S,
+                                            f, st, h->prec));
         CK(cudaEventRecord(h->ev_bps[par], st));
         CK(cudaStreamWaitEvent(ds, h->ev_bps[par], 0));
         const int cin = (int)(g & 1), cout = 1 - cin;
@@ -832,6 +859,11 @@ int fill_stats(rx_handle *h, rx_stats *out) {
     const int S = h->streams;
     std::vector<StreamDev> sd(S);
     CK(cudaStreamSynchronize(h->st));
+    if (use_bps_tc(h)) {
+        unsigned int gave_up = 0;
+        CK(bps_tc_status(&gave_up));
+        if (gave_up) return fail(RX_ETIMEDOUT, "a bounded wait of the tensor-core phase search gave up");
+    }
     // before the first block of a handle there are no device counters yet
     if (h->sd) CK(cudaMemcpy(sd.data(), h->sd, sizeof(StreamDev) * S, cudaMemcpyDeviceToHost));
     else std::memset(sd.data(), 0, sizeof(StreamDev) * S);
@@ -1111,6 +1143,7 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     else if (k == "wavelength_nm") { if (!(v > 100 && v < 10000)) return fail(RX_EINVAL, "wavelength out of range"); h->wavelength = v * 1e-9; h->tables_dirty = true; }
     else if (k == "profile") { rc = as_int(0, 2, t); h->profile = (int)t; }
     else if (k == "precision") { rc = as_int(0, 2, t); h->prec = (int)t; }
+    else if (k == "bps_tc") { rc = as_int(0, 1, t); h->bps_tc = (int)t; }
     else return fail(RX_EINVAL, "unknown parameter '%s'", k.c_str());
     if (rc != RX_OK) return rc;
     if (k == "overlap") h->tables_dirty = true;
@@ -1239,6 +1272,7 @@ void rx_destroy(rx_handle *h) {
     cudaFree(h->s2sym);
     cudaFree(h->H);
     cudaFree(h->tw);
+    cudaFree(h->bps_w);
     cudaFree(h->ref);
     cudaFree(h->d_in);
     cudaFree(h->d_out);
@@ -1281,6 +1315,7 @@ int rx_get_param(const rx_handle *h, const char *key, double *value) {
     else if (k == "wavelength_nm") *value = h->wavelength * 1e9;
     else if (k == "taps") *value = h->T;
     else if (k == "bps_phases") *value = h->B;
+    else if (k == "bps_tc") *value = use_bps_tc(h) ? 1.0 : 0.0;
     else if (k == "cd_ps_per_nm") *value = h->cd;
     else if (k == "profile") *value = h->profile;
     else if (k == "precision") *value = h->prec;
@@ -1902,11 +1937,16 @@ int rx_bps(rx_handle *h, const void *y, size_t n_y, size_t a, size_t e, size_t n
     if (!h || !y || !b_out) return fail(RX_EINVAL, "NULL argument");
     if (e < a || e > n_y || n_valid > n_y) return fail(RX_EINVAL, "bad range");
     int *dsum = nullptr;
-    const int chunks = bps_chunks((long)(e - a), h->streams);
+    int rc = upload_tables(h);
+    if (rc != RX_OK) return rc;
+    const bool tc = use_bps_tc(h);
+    const int chunks = tc ? bps_chunks_tc((long)(e - a), h->streams) : bps_chunks((long)(e - a), h->streams);
     const long ncta = ((long)(e - a) + bps_cta_range(chunks) - 1) / bps_cta_range(chunks);
     CK(cudaMallocAsync(&dsum, sizeof(int) * (size_t)h->streams * (ncta + 1), h->st));
-    cudaError_t err = launch_bps((const float2 *)y, (long)n_y, (long)a, (long)e, (long)n_valid, h->W,
-                                 b_out, (long)(e - a), 0, dsum, nullptr, chunks, h->streams, h->fmt, h->st);
+    cudaError_t err = tc ? launch_bps_tc(y, (long)n_y, (long)a, (long)e, (long)n_valid, h->W, b_out, (long)(e - a), 0,
+                                         dsum, nullptr, chunks, h->streams, h->bps_w, h->fmt, h->st)
+                         : launch_bps((const float2 *)y, (long)n_y, (long)a, (long)e, (long)n_valid, h->W,
+                                      b_out, (long)(e - a), 0, dsum, nullptr, chunks, h->streams, h->fmt, h->st);
     cudaFreeAsync(dsum, h->st);
     CK(err);
     return RX_OK;

@@ -80,6 +80,10 @@ def _resume_points(res, p):
 
 
 def test_chain_at_bench_launch_shape(oracle_runs):
+    _chain_check(oracle_runs, bps_tc=0)
+
+
+def _chain_check(oracle_runs, bps_tc):
     from oracle import chain
     from paper_2108_07004_gb300 import rx
     fmt = oracle_format(FMT)
@@ -90,6 +94,7 @@ def test_chain_at_bench_launch_shape(oracle_runs):
     nblk = len(ress[0].ranges)
     assert nblk == 4
     r = _receiver(S)
+    r.set("bps_tc", bps_tc)
     r.set_reference(torch.from_numpy(np.stack([st.bits for st in sts])).cuda())
     samples = torch.from_numpy(np.stack([st.rx for st in sts])).cuda()
     llr = torch.zeros((S, N, fmt.m), dtype=torch.float32, device="cuda")
@@ -142,3 +147,32 @@ def test_phase_search_stage_nine_streams_one_block(oracle_runs):
         diff = g[s] != res.b[a:e]
         assert np.all(res.bps_gap[a:e][diff] < pp.TIE), (s, int(diff.sum()))
         assert diff.mean() < 1e-3, s
+
+
+def test_phase_search_tensor_cores_nine_streams_one_block(oracle_runs):
+    """The same stage on the tensor cores (bps_tc = 1: the orbit correlations
+    as a tcgen05 TF32 product with a high/low split, SIMT epilogue): indices
+    equal the oracle's outside near-ties."""
+    from oracle import chain
+    from paper_2108_07004_gb300 import rx
+    p = chain.RxParams(**PARAMS)
+    S = len(oracle_runs)
+    ress = [o[1] for o in oracle_runs]
+    a, e, nv = p.block - p.bps_window // 2, 2 * p.block - p.bps_window // 2, 2 * p.block
+    y = np.stack([res.y[:, :nv] for res in ress]).astype(np.complex64)
+    r = _receiver(S)
+    r.set("bps_tc", 1)
+    assert r.get("bps_tc") == 1
+    bo = torch.zeros((S, e - a), dtype=torch.uint8, device="cuda")
+    r.bps(torch.from_numpy(y).cuda(), a, e, nv, bo)
+    g = bo.cpu().numpy().astype(np.int64)
+    for s, res in enumerate(ress):
+        diff = g[s] != res.b[a:e]
+        assert np.all(res.bps_gap[a:e][diff] < pp.TIE), (s, int(diff.sum()))
+        assert diff.mean() < 1e-3, s
+
+
+def test_chain_at_bench_launch_shape_tensor_cores(oracle_runs):
+    """The whole chain at the bench's launch shape with the phase search on
+    the tensor cores, under the same protocol as the SIMT chain."""
+    _chain_check(oracle_runs, bps_tc=1)

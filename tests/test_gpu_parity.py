@@ -320,6 +320,30 @@ def _oracle_state(rx, res, p, fmt, n, N, counters):
     return rx.pack_state(hd, taps, np.array([stt["carry"]]), stt["y_tail"][None], counters)
 
 
+def test_bps_parity_tensor_cores():
+    """The 4D-64 phase search with the orbit correlations on the tensor cores
+    (bps_tc = 1) against the oracle: exact outside near-ties."""
+    st, p, res = _oracle_run("gs1000km")
+    r = _receiver("gs1000km", bps_tc=1)
+    fmt = oracle_format("gs4d64")
+    y = res.y.astype(np.complex64)
+    N = y.shape[1]
+    a, e = 37, N - 101
+    b_ref, gap, _ = chain.bps(y.astype(np.complex128), a, e, N, p, fmt)
+    bo = torch.zeros((1, e - a), dtype=torch.uint8, device="cuda")
+    r.bps(_dev(y[None]), a, e, N, bo)
+    g = bo[0].cpu().numpy().astype(np.int64)
+    diff = g != b_ref
+    assert np.all(gap[diff] < TIE), f"{diff.sum()} choices differ outside near-ties"
+    assert diff.mean() < 1e-3
+
+
+def test_chain_end_to_end_tensor_cores():
+    """The 4D-64 chain with the tensor-core phase search, same protocol."""
+    st, p, res = _oracle_run("gs1000km")
+    _e2e_check("gs1000km", st, p, res, _receiver("gs1000km", bps_tc=1))
+
+
 @pytest.mark.parametrize("case", list(CASES))
 def test_chain_end_to_end(case):
     """rx_process_blocks against the oracle's block schedule on the same
