@@ -1124,8 +1124,11 @@ def run_serving(args):
 
 
 # ---- learned demapper (MLP 4 -> 128 -> 128 -> 6) on the same chain ------------
-LEARN = dict(train_streams=16, train_sym=(1 << 18) + (1 << 14), skip=1 << 14, epochs=20, batch=8192,
-             lr=1e-3, infer_streams=16, infer_sym=1 << 20, esn0=(8.0, 16.0), init_seed=2108070044)
+# Adam at lr 1e-3; the last `decay_epochs` epochs run at lr_final (a step
+# schedule that lets the network settle; 0 keeps the rate constant)
+LEARN = dict(train_streams=16, train_sym=(1 << 18) + (1 << 14), skip=1 << 14, epochs=40, batch=8192,
+             lr=1e-3, lr_final=1e-4, decay_epochs=10, infer_streams=16, infer_sym=1 << 20, esn0=(8.0, 16.0),
+             init_seed=2108070044)
 
 
 def learned_inputs(n_streams: int, n_sym: int, seed_base: int):
@@ -1174,11 +1177,14 @@ def run_learned(args):
     steps_per_epoch = n_train // bs
     t0 = time.perf_counter()
     losses = []
-    for ep in range(LEARN["epochs"]):
+    epochs = args.learn_epochs if args.learn_epochs else LEARN["epochs"]
+    decay = LEARN["decay_epochs"] if args.learn_decay is None else args.learn_decay
+    for ep in range(epochs):
+        lr = LEARN["lr_final"] if ep >= epochs - decay else LEARN["lr"]
         perm = torch.randperm(n_train, device="cuda", generator=gen)
         for i in range(steps_per_epoch):
             idx = perm[i * bs:(i + 1) * bs]
-            m.train_step(X[idx], S2[idx], B[idx], LEARN["lr"], loss)
+            m.train_step(X[idx], S2[idx], B[idx], lr, loss)
         losses.append(loss.item())
     torch.cuda.synchronize()
     train_s = time.perf_counter() - t0
@@ -1217,7 +1223,8 @@ def run_learned(args):
         "data": "synthetic",
         "config": {"workload": "learned_demapper_mlp_4x128x128x6_gs4d64", "streams": S,
                    "symbols_per_stream": N, "esn0_db": [round(float(v), 2) for v in esn0],
-                   "train_symbols": int(n_train), "epochs": LEARN["epochs"], "batch": bs, "lr": LEARN["lr"]},
+                   "train_symbols": int(n_train), "epochs": epochs, "batch": bs, "lr": LEARN["lr"],
+                   "lr_final": LEARN["lr_final"], "decay_epochs": decay},
         "exact_chain_gbps": out["exact"]["gbps"],
         "gmi_gap_mean": float(np.mean(ge - gl)), "gmi_gap_max": float(np.max(ge - gl)),
         "ber_delta_rel_max": float(np.max(np.abs(bl - be) / np.maximum(be, 1e-12))),
@@ -1295,6 +1302,8 @@ def main():
                          "precision: DP-QPSK chain with CDC/FIR data in float32, half and bfloat16; "
                          "serving: 64 mixed streams with Poisson arrivals through the continuous-batching server")
     ap.add_argument("--learned-sym", type=int, default=LEARN["infer_sym"])
+    ap.add_argument("--learn-epochs", type=int, default=0, help="training epochs (0: the default)")
+    ap.add_argument("--learn-decay", type=int, default=None, help="final epochs at the lower rate")
     ap.add_argument("--mlp-sym", type=int, default=1 << 24)
     args = ap.parse_args()
     if args.impl == "reference":
