@@ -195,7 +195,7 @@ __device__ __forceinline__ void add_group8(const f32x2 (&E)[4], int g8, GroupSum
 // bit is known at compile time; a few packed accumulators instead of 64
 // stored terms keep the registers low.
 template <int MT, int MB>
-__device__ __forceinline__ bool llr_4d_stream(float2 z0, float2 z1, const FmtDev &f, float c2,
+__device__ __forceinline__ bool llr_4d_stream(float2 z0, float2 z1, const FmtDev &f, const float *en, float c2,
                                               float *out, float &gmin, float &emin, int ref,
                                               int &ne, float &g2) {
     const float zn = cnorm(z0) + cnorm(z1);
@@ -225,7 +225,7 @@ __device__ __forceinline__ bool llr_4d_stream(float2 z0, float2 z1, const FmtDev
             }
         }
         gmin = __int_as_float(key & ~15);
-        emin = f.orbeP[key & 15];
+        emin = en[key & 15];       // the lanes' orbits differ: a shared-memory read
     }
     const float sh = fmaf(gmin, c2, kOff);   // exponent of point j: sh - d_j c2
     float s0[MB], s1[MB];
@@ -295,16 +295,18 @@ struct CountAcc {
 // LLRs of one symbol (z0, z1) into L[M_OUT] and its counting terms.  Every
 // lane of the warp calls it (inactive lanes on a valid symbol, writing
 // nothing), so the warp-wide rare path sees the whole warp.
+// en: shared-memory copy of the energies the nearest point is looked up in
+// (4D: the orbit energies, 2D: the point energies; see load_energies)
 template <int DIMS, int MT, int MB>
-__device__ __forceinline__ void demap_symbol(float2 z0, float2 z1, float c2, const FmtDev &f, bool active,
-                                             int ref, bool counted, float *row, CountAcc &acc) {
+__device__ __forceinline__ void demap_symbol(float2 z0, float2 z1, float c2, const FmtDev &f, const float *en,
+                                             bool active, int ref, bool counted, float *row, CountAcc &acc) {
     constexpr int M_OUT = (DIMS == 4) ? MB : 2 * MB;
     float L[M_OUT];
     int ne = 0;
     float gs = 0.f, dist_min, dmin_energy;
     if (DIMS == 4) {
         float g2;
-        const bool low = llr_4d_stream<MT, MB>(z0, z1, f, c2, L, dist_min, dmin_energy, ref, ne, g2);
+        const bool low = llr_4d_stream<MT, MB>(z0, z1, f, en, c2, L, dist_min, dmin_energy, ref, ne, g2);
         const unsigned need = __ballot_sync(0xffffffffu, low && active);
         if (need) llr_fixup_warp<4, MT, MB>(need, z0, z1, f, c2, L, ref, ne, g2);
         gs = g2;
@@ -323,7 +325,7 @@ __device__ __forceinline__ void demap_symbol(float2 z0, float2 z1, float c2, con
             ne += nep;
             gs += g2;
             dist_min += g;
-            dmin_energy += f.pe[jm];
+            dmin_energy += en[jm];
         }
     }
     if (active) {
@@ -337,6 +339,20 @@ __device__ __forceinline__ void demap_symbol(float2 z0, float2 z1, float c2, con
         acc.en += dist_min;
         acc.ed += dmin_energy;
     }
+}
+
+// The tables a block reads with lane-dependent indices, in shared memory (a
+// constant-bank read whose address differs across the warp is serialised):
+// the energies of demap_symbol and, for the de-rotation, the test phases'
+// (cos, -sin).  Callers synchronise before use.
+template <int DIMS>
+__device__ __forceinline__ void load_tables(const FmtDev &f, float *en, float2 *rot) {
+    for (int i = threadIdx.x; i < RX_MAXM; i += blockDim.x) {
+        if (DIMS == 4) { if (i < 16) en[i] = f.orbeP[i]; }
+        else en[i] = i < f.M ? f.pe[i] : 0.f;
+    }
+    if (rot)
+        for (int i = threadIdx.x; i < f.B; i += blockDim.x) rot[i] = make_float2(f.cs[i][0], -f.cs[i][1]);
 }
 
 // Block sums of the counting terms into this block's partial row, then the
@@ -409,6 +425,9 @@ demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
              const double *__restrict__ sigma2, int s2_stride, float *__restrict__ llr,
              long llr_stride, DemapCount cnt, const __grid_constant__ FmtDev f) {
     constexpr int M_OUT = (DIMS == 4) ? MB : 2 * MB;
+    __shared__ float en_sh[RX_MAXM];
+    load_tables<DIMS>(f, en_sh, nullptr);
+    __syncthreads();
     const int s = blockIdx.y, tid = threadIdx.x;
     const long k = a + (long)blockIdx.x * blockDim.x + tid;
     const float c2 = 1.4426950408889634f / (float)sigma2[s * s2_stride];
@@ -419,7 +438,7 @@ demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
     const bool counted = active && cnt.ref_lab && k >= cnt.c0 && k < cnt.c1;
     const int ref = counted ? (int)cnt.ref_lab[(long)s * cnt.ref_stride + k] : -1;
     CountAcc acc;
-    demap_symbol<DIMS, MT, MB>(zx[kk - a], zy[kk - a], c2, f, active, ref, counted,
+    demap_symbol<DIMS, MT, MB>(zx[kk - a], zy[kk - a], c2, f, en_sh, active, ref, counted,
                                llr + (long)s * llr_stride + (kk - a) * M_OUT, acc);
     if (!cnt.sd) return;
     count_reduce(acc, cnt, s, blockIdx.x, gridDim.x, sigma2[s * s2_stride]);
@@ -427,13 +446,17 @@ demap_kernel(const float2 *__restrict__ z, long z_stride, long a, long e,
 
 // ---------------------------------------------------------------------------
 // De-rotation fused with demapping (the chain's path).  A block takes a tile
-// of kTile consecutive symbols: the unwrap count m before the tile is the
+// of TILE consecutive symbols: the unwrap count m before the tile is the
 // stream carry plus the increments of the BPS ranges before it (dsum, and
 // the boundary increments) plus those of its own range up to the tile;
 // inside the tile a block scan gives m per symbol; then each symbol is
-// de-rotated by exp(-j (phi_b + m 2 pi / S)) and demapped in place.
+// de-rotated by exp(-j (phi_b + m 2 pi / S)) and demapped in place.  Tiles
+// are 1024 symbols for the 4D table (64 distances and exponentials a
+// symbol) and 4096 for 2D tables, whose per-symbol work is small against
+// the tile's prologue and reduction.
 // ---------------------------------------------------------------------------
-constexpr int kTile = 1024;
+constexpr int kTile = 1024;                 // the 4D table's tile (the smallest)
+template <int DIMS> __host__ __device__ constexpr int tile_of() { return DIMS == 4 ? 1024 : 4096; }
 
 template <int DIMS, int MT, int MB>
 __global__ void __launch_bounds__(256, (DIMS == 4 ? 4 : 2))
@@ -446,9 +469,13 @@ derot_demap_kernel(const void *__restrict__ y, long y_stride, const uint8_t *__r
                    float *__restrict__ llr, long llr_stride, DemapCount cnt, SymOut sym, int sk,
                    const __grid_constant__ FmtDev f) {
     constexpr int M_OUT = (DIMS == 4) ? MB : 2 * MB;
-    constexpr int PT = kTile / 256;
-    __shared__ uint8_t bl[kTile];
-    __shared__ uint8_t mql[kTile];
+    constexpr int TILE = tile_of<DIMS>();
+    constexpr int PT = TILE / 256;
+    __shared__ uint8_t bl[TILE];
+    __shared__ uint8_t mql[TILE];
+    __shared__ float en_sh[RX_MAXM];
+    __shared__ float2 rot_sh[RX_MAXB];
+    load_tables<DIMS>(f, en_sh, rot_sh);
     __shared__ int wsum[8];
     __shared__ int mstart_sh;
     __shared__ float c2_sh;
@@ -456,8 +483,8 @@ derot_demap_kernel(const void *__restrict__ y, long y_stride, const uint8_t *__r
     const int s = blockIdx.y, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int B = f.B, S = f.S;
     const uint8_t *bs = bsrc + (long)s * b_stride;   // index k - a
-    const long t0 = a + (long)blockIdx.x * kTile;
-    const long t1 = min(t0 + kTile, e);
+    const long t0 = a + (long)blockIdx.x * TILE;
+    const long t1 = min(t0 + TILE, e);
     const int nloc = (int)(t1 - t0);
     const int m_in = carry_in[s * cin_stride + 0], b_in = carry_in[s * cin_stride + 1];
     const int r0 = (int)((t0 - a) / kR);              // BPS range holding the tile start
@@ -548,7 +575,7 @@ derot_demap_kernel(const void *__restrict__ y, long y_stride, const uint8_t *__r
         const long k = t0 + tt;
         const int b = bl[tt], mq = mql[tt];
         // exp(-j phi) = conj(cs_b) (-j)^mq
-        float2 rot = make_float2(f.cs[b][0], -f.cs[b][1]);
+        float2 rot = rot_sh[b];
         if (S == 4) {
             if (mq & 2) rot = make_float2(-rot.x, -rot.y);
             if (mq & 1) rot = make_float2(rot.y, -rot.x);
@@ -565,7 +592,7 @@ derot_demap_kernel(const void *__restrict__ y, long y_stride, const uint8_t *__r
         if (!llr) continue;                   // symbols only (another demapper follows)
         const bool counted = active && cnt.ref_lab && k >= cnt.c0 && k < cnt.c1;
         const int ref = counted ? (int)cnt.ref_lab[(long)s * cnt.ref_stride + k] : -1;
-        demap_symbol<DIMS, MT, MB>(z0, z1, c2, f, active, ref, counted,
+        demap_symbol<DIMS, MT, MB>(z0, z1, c2, f, en_sh, active, ref, counted,
                                    llr + (long)s * llr_stride + (k - a) * M_OUT, acc);
     }
     if (!cnt.sd || !llr) return;
@@ -643,7 +670,8 @@ cudaError_t derot_demap_t(const void *y, long ys, const uint8_t *b, long bst, lo
                           int s2s, float *llr, long ls, const DemapCount &cnt, const SymOut &sym, int n_streams,
                           const FmtDev &f, cudaStream_t st, int sk) {
     const int n_rng = (int)((e - a + kR - 1) / kR);
-    dim3 grid((unsigned)((e - a + kTile - 1) / kTile), (unsigned)n_streams);
+    constexpr int TILE = tile_of<DIMS>();
+    dim3 grid((unsigned)((e - a + TILE - 1) / TILE), (unsigned)n_streams);
     derot_demap_kernel<DIMS, MT, MB><<<grid, 256, 0, st>>>(y, ys, b, bst, a, e, dsum, mdsum, n_rng, kR, cin, cis,
                                                            cout, cos, pc, pcs, s2f, s2o, s2s, llr, ls, cnt, sym, sk, f);
     return cudaGetLastError();
@@ -651,6 +679,7 @@ cudaError_t derot_demap_t(const void *y, long ys, const uint8_t *b, long bst, lo
 
 }  // namespace
 
+// the most blocks any table's tiles need (the smallest tile)
 long derot_demap_ctas(long len, int n_streams, int sm_avail) {
     (void)n_streams;
     (void)sm_avail;

@@ -420,8 +420,14 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
                                 int la, lc;
                                 best_rot_label(y0.x * q0.x + y0.y * q0.y, y0.y * q0.x - y0.x * q0.y, f.S, lab, va, la);
                                 best_rot_label(y1.x * q0.x + y1.y * q0.y, y1.y * q0.x - y1.x * q0.y, f.S, lab, vb, lc);
-                                const float4 p0 = tb.pts[argmin_label(cnorm(y0) + (eo - 2.f * va), la)];
-                                const float4 p1 = tb.pts[argmin_label(cnorm(y1) + (eo - 2.f * vb), lc)];
+                                // one orbit (e.g. QPSK): every lane holds the same candidate
+                                // (lanes past the table use orbit 0 too), so it is the decision
+                                if (f.n_orb > 1) {
+                                    la = argmin_label(cnorm(y0) + (eo - 2.f * va), la);
+                                    lc = argmin_label(cnorm(y1) + (eo - 2.f * vb), lc);
+                                }
+                                const float4 p0 = tb.pts[la];
+                                const float4 p1 = tb.pts[lc];
                                 d0 = make_float2(p0.x, p0.y);
                                 d1 = make_float2(p1.x, p1.y);
                             }
