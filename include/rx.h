@@ -144,7 +144,13 @@ void rx_destroy(rx_handle *h);                      /* NULL-safe */
  *   every block, 2: time the BPS launches only),
  *   "precision" [0]: storage of the chain's CDC and FIR outputs, 0 float32,
  *   1 half (FP16), 2 bfloat16; arithmetic, LMS taps and the phase unwrap
- *   stay float32 (the precision variant; rx_get_state / rx_set_state need 0).
+ *   stay float32 (the precision variant; rx_get_state / rx_set_state need 0),
+ *   "bps_tc" [0]: 1 forms the phase search's orbit correlations on the
+ *   tensor cores (4D tables of 16 orbits; reads 0 where unsupported),
+ *   "lms_exact" [0]: 1 runs the DD-LMS's warp-wide nearest-point search on
+ *   every update; 0 takes each decision a sub-block ahead on the update's
+ *   partial output and keeps it while the corrections added since stay
+ *   inside half its margin (the same decisions and taps, bit for bit).
  * Changing a parameter resets the stream state (rx_reset). */
 int rx_set_param(rx_handle *h, const char *key, double value);
 int rx_get_param(const rx_handle *h, const char *key, double *value);

@@ -7,7 +7,8 @@
 //   y_q   = sum conj(h_qp[t]) x_p[2k + D - t]
 //   CMA:  e_q = (R^2 - |y_q|^2) y_q
 //   DD:   z = y exp(-j phi_k); d = nearest table point (orbit per lane,
-//         (distance, label) min over 16 lanes, ties -> lowest label);
+//         (distance, label) min over 16 lanes, ties -> lowest label; taken
+//         a sub-block ahead where the margin allows, see lms_kernel);
 //         e_q = d_q exp(j phi_k) - y_q
 //   h_qp[t] += mu conj(e_q) x_p[2k + D - t]
 // Per stream one block of 12 warps (see lms_kernel), in sub-blocks of 16
@@ -63,6 +64,7 @@ struct Tables {
     float orbe[RX_MAXM];
     int orblab[RX_MAXM][4];
     float4 pts[RX_MAXM];
+    float4 rpts[RX_MAXM];   // point of orbit o turned by k (k < S) at o S + k
     float2 cs[RX_MAXB];
 };
 
@@ -74,6 +76,10 @@ __device__ __forceinline__ void load_tables(Tables &tb, const FmtDev &f) {
     }
     for (int i = threadIdx.x; i < f.M; i += blockDim.x)
         tb.pts[i] = make_float4(f.pts[i][0], f.pts[i][1], f.pts[i][2], f.pts[i][3]);
+    for (int i = threadIdx.x; i < f.n_orb * f.S; i += blockDim.x) {
+        const int lab = f.orb_lab[i / f.S][i % f.S] & 255;
+        tb.rpts[i] = make_float4(f.pts[lab][0], f.pts[lab][1], f.pts[lab][2], f.pts[lab][3]);
+    }
     for (int i = threadIdx.x; i < f.B; i += blockDim.x) tb.cs[i] = make_float2(f.cs[i][0], f.cs[i][1]);
 }
 
@@ -106,6 +112,122 @@ __device__ __forceinline__ int argmin_label(float dist, int label) {
     return (int)__reduce_min_sync(0xffffffffu, key);
 }
 
+// a b with its rounding fixed (one product rounded, then one fused
+// multiply-add), so a table point turned by a phase is the same value
+// wherever it is formed; with sub_rn the decision-directed error
+// d exp(j phi) - y is the same whichever path took the decision
+__device__ __forceinline__ float2 cmul_fixed(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -__fmul_rn(a.y, b.y)), fmaf(a.x, b.y, __fmul_rn(a.y, b.x)));
+}
+__device__ __forceinline__ float2 sub_rn(float2 a, float2 b) {
+    return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y));
+}
+
+// Orbit o's two best rotations against the running two smallest squared
+// distances d1 <= d2 (branch-free: the second smallest of {d1, d2, dA, dB}
+// with dA <= dB is min(max(d1, dA), min(d2, dB))); `best` = o S + k of the
+// nearest, k quarter turns (for S = 4 the values max and min of |P|, |Q|).
+template <int DIMS>
+__device__ __forceinline__ void orbit_two(float2 z0, float2 z1, float zz, float4 r, float e, int o, int S,
+                                          float &d1, float &d2, int &best) {
+    float P = z0.x * r.x + z0.y * r.y, Q = z0.y * r.x - z0.x * r.y;
+    if (DIMS == 4) {
+        P += z1.x * r.z + z1.y * r.w;
+        Q += z1.y * r.z - z1.x * r.w;
+    }
+    float v1, v2;
+    int k1;
+    if (S == 4) {
+        const float aP = fabsf(P), aQ = fabsf(Q);
+        v1 = fmaxf(aP, aQ);
+        v2 = fminf(aP, aQ);
+        k1 = aP >= aQ ? (P >= 0.f ? 0 : 2) : (Q >= 0.f ? 1 : 3);
+    } else if (S == 2) {
+        v1 = fabsf(P);
+        v2 = -v1;
+        k1 = P >= 0.f ? 0 : 1;
+    } else {
+        v1 = P;
+        v2 = -__int_as_float(0x7f800000);
+        k1 = 0;
+    }
+    const float base = zz + e;
+    const float dA = fmaf(-2.f, v1, base), dB = fmaf(-2.f, v2, base);
+    best = dA < d1 ? o * S + k1 : best;
+    d2 = fminf(fmaxf(d1, dA), fminf(d2, dB));
+    d1 = fminf(d1, dA);
+}
+
+// The two smallest squared distances from the de-rotated z to the table
+// (each orbit's two best rotations hold the nearest point and the
+// second-nearest).  DIMS 4: the lanes of half h take orbits o + 8 h, o < 8
+// (table entries as constant operands, chosen by h), up to 16 orbits, then
+// every second orbit past 16; DIMS 2 reads z0 alone and takes every orbit.
+// Past n_orb the energy is +inf (never a candidate).
+template <int DIMS>
+__device__ __forceinline__ void two_nearest(float2 z0, float2 z1, const FmtDev &f, int h, float &d1, float &d2,
+                                            int &best) {
+    const float zz = DIMS == 4 ? cnorm(z0) + cnorm(z1) : cnorm(z0);
+    const float inf = __int_as_float(0x7f800000);
+    const int S = f.S, n = f.n_orb;
+    d1 = inf;
+    d2 = inf;
+    best = 0;
+    if (DIMS == 4) {
+#pragma unroll
+        for (int o = 0; o < 8; ++o) {
+            const int oo = o + 8 * h;
+            const float4 r = h ? make_float4(f.orb[o + 8][0], f.orb[o + 8][1], f.orb[o + 8][2], f.orb[o + 8][3])
+                               : make_float4(f.orb[o][0], f.orb[o][1], f.orb[o][2], f.orb[o][3]);
+            const float e = oo < n ? (h ? f.orbe[o + 8] : f.orbe[o]) : inf;
+            orbit_two<4>(z0, z1, zz, r, e, oo, S, d1, d2, best);
+        }
+        for (int oo = 16 + h; oo < n; oo += 2) {
+            const float4 r = make_float4(f.orb[oo][0], f.orb[oo][1], f.orb[oo][2], f.orb[oo][3]);
+            orbit_two<4>(z0, z1, zz, r, f.orbe[oo], oo, S, d1, d2, best);
+        }
+    } else {
+#pragma unroll
+        for (int o = 0; o < 16; ++o) {
+            if (o < n) {
+                const float4 r = make_float4(f.orb[o][0], f.orb[o][1], 0.f, 0.f);
+                orbit_two<2>(z0, z0, zz, r, f.orbe[o], o, S, d1, d2, best);
+            }
+        }
+        for (int o = 16; o < n; ++o) {
+            const float4 r = make_float4(f.orb[o][0], f.orb[o][1], 0.f, 0.f);
+            orbit_two<2>(z0, z0, zz, r, f.orbe[o], o, S, d1, d2, best);
+        }
+    }
+}
+
+__device__ __forceinline__ float sqrt_approx(float x) {   // x >= 0; relative error ~1e-7
+    float y;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// The decision's margin T = |z - s_2| - |z - s_1| from the second-smallest
+// squared distance d2 and the nearest point s_1 = p (|z - s_1| from the
+// coordinate differences, free of the cancellation in |z|^2 + |s|^2 - 2 Re);
+// the hold radius' slack covers the approximate square roots
+template <int DIMS>
+__device__ __forceinline__ float margin_of(float2 z0, float2 z1, float4 p, float d2) {
+    float a = cnorm(make_float2(z0.x - p.x, z0.y - p.y));
+    if (DIMS == 4) a += cnorm(make_float2(z1.x - p.z, z1.y - p.w));
+    return sqrt_approx(fmaxf(d2, 0.f)) - sqrt_approx(a);
+}
+
+// Largest squared correction |y - z|^2 under which the decision taken on z
+// holds for y: with margin T, every other point stays at least T - 2|y - z|
+// farther from y than the nearest (triangle inequality); the slack keeps
+// that gap far above the float32 rounding of the squared distances, so the
+// warp-wide decision on y would pick the same point.  Negative: never.
+__device__ __forceinline__ float hold_radius2(float T, float zz) {
+    const float m = T - 1e-4f * (1.f + zz);
+    return m > 0.f ? 0.25f * m * m : -1.f;
+}
+
 // Sequential CMA (MODE 0), DD-LMS (MODE 1) or data-aided LMS (MODE 3).
 //
 // With X_k the stacked input window of symbol k, h_k the taps after update
@@ -119,7 +241,16 @@ __device__ __forceinline__ int argmin_label(float dist, int label) {
 //   this sub-block, l >= 16: the next); per update it takes the decision on
 //   y_k, every lane adds mu e_k r(k, 16 s + l) to its own partial (one
 //   complex FMA per output), and y_{k+1} is lane k+1's partial, fetched by a
-//   shuffle while the decision ran, plus mu e_k r(k, k + 1);
+//   shuffle while the decision ran, plus mu e_k r(k, k + 1).  DD decisions
+//   are taken ahead: at the start of a sub-block lanes l and l + 16 decide
+//   update 16 s + l on its partial p_l (which lacks only the terms of the
+//   sub-block's earlier updates) and keep the margin T_l between the
+//   nearest and the second-nearest point.  Update k then takes that point
+//   when 2 |y_k - p_k| < T_k - slack (no other point can be nearer to y_k,
+//   and the slack keeps the float32 warp-wide search on y_k from ruling
+//   otherwise); else, for a few per cent of the updates, the warp-wide
+//   search on y_k.  The decisions, and the errors (one fixed rounding on
+//   both paths), are those of the warp-wide search on every update.
 // * tap group: applies the previous sub-block's 16 updates to the taps,
 //   h += sum_j mu conj(e_j) X_j, then forms H^H X_k for the next sub-block;
 // * correlation group: r(j, j + d) for the next sub-block's rows j and lags
@@ -130,11 +261,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_in,
            float2 *__restrict__ taps_out, long k0, int n_upd, const uint16_t *__restrict__ pcode,
            long pcode_stride, int passes, float mu, const reflab_t *__restrict__ ref_lab,
-           long ref_stride, int sk, int wl, const __grid_constant__ FmtDev f) {
+           long ref_stride, int sk, int opts, const __grid_constant__ FmtDev f) {
     constexpr int D = (T - 1) / 2;
+    const int wl = opts & LMS_WL;
+    const bool ahead = (opts & LMS_EXACT_DD) == 0;   // DD decisions taken a sub-block ahead
     constexpr int NSX = lms_nsx(T);
     const int L = wl ? 2 * T : T;                     // taps per branch (widely linear: [h on x, g on conj x])
     __shared__ Tables tb;
+    // the decision warp's decisions taken ahead on the partial outputs: per
+    // update of the sub-block the partial (y_0, y_1), the chosen points
+    // turned by exp(j phi_k), and the squared hold radii (DIMS 2: per output)
+    __shared__ float4 sp_base[kSB], sp_dr[kSB];
+    __shared__ float2 sp_hold[kSB];
     extern __shared__ float2 dyn_sm[];
     // local sample index of x_p[2 (kb + k) + D - t] is 2 k + 2 D - t
     float2 *xs0 = dyn_sm, *xs1 = dyn_sm + NSX;
@@ -362,26 +500,104 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
                     c0.y = __shfl_down_sync(0xffffffffu, v0.y, 16);
                     c1.x = __shfl_down_sync(0xffffffffu, v1.x, 16);
                     c1.y = __shfl_down_sync(0xffffffffu, v1.y, 16);
-                    if (lane < kSB) {
-                        v0 = cadd(c0, bsb[(buf * kSB + lane) * 2]);
-                        v1 = cadd(c1, bsb[(buf * kSB + lane) * 2 + 1]);
-                    } else {
-                        v0 = v1 = make_float2(0.f, 0.f);
+                    // p: the partial of update 16 s + (lane & 15), in both
+                    // lanes of the pair (lane u + 16 adds the same two values)
+                    float2 p0, p1;
+                    {
+                        const float2 b0 = bsb[(buf * kSB + (lane & 15)) * 2];
+                        const float2 b1 = bsb[(buf * kSB + (lane & 15)) * 2 + 1];
+                        if (lane < kSB) {
+                            v0 = cadd(c0, b0);
+                            v1 = cadd(c1, b1);
+                            p0 = v0;
+                            p1 = v1;
+                        } else {
+                            p0 = cadd(v0, b0);
+                            p1 = cadd(v1, b1);
+                            v0 = v1 = make_float2(0.f, 0.f);
+                        }
                     }
                     const float2 *Rr = Rt + buf * kSB * kLag;
                     const int ms = min(kSB, n - kSB * s);
+                    if (MODE == 1 && ahead) {
+                        // decisions taken ahead: update 16 s + u (u < 16) on its
+                        // partial, which lacks only the terms of updates
+                        // 16 s .. 16 s + u - 1; lanes u and u + 16 share it (4D
+                        // tables: even / odd orbits, merged; 2D: polarisation h)
+                        const int u = lane & 15, h = lane >> 4;
+                        const float2 rot = rots[kSB * s + min(u, ms - 1)];
+                        const float2 rm = make_float2(rot.x, -rot.y);
+                        const float2 z0 = cmul(p0, rm), z1 = cmul(p1, rm);
+                        float d1, d2;
+                        int best;
+                        if (DIMS == 4) {
+                            two_nearest<4>(z0, z1, f, h, d1, d2, best);
+                            const float od1 = __shfl_xor_sync(0xffffffffu, d1, 16);
+                            const float od2 = __shfl_xor_sync(0xffffffffu, d2, 16);
+                            const int ob = __shfl_xor_sync(0xffffffffu, best, 16);
+                            d2 = fminf(fmaxf(d1, od1), fminf(d2, od2));
+                            best = od1 < d1 ? ob : best;   // exact ties: margin 0, never held
+                            d1 = fminf(d1, od1);
+                        } else {
+                            two_nearest<2>(h ? z1 : z0, z1, f, h, d1, d2, best);
+                        }
+                        const float4 pt = tb.rpts[best];
+                        if (u < ms) {
+                            float2 *dr2 = reinterpret_cast<float2 *>(sp_dr);
+                            float *hd = reinterpret_cast<float *>(sp_hold);
+                            if (DIMS == 4) {
+                                if (h == 0) {
+                                    const float mg = margin_of<4>(z0, z1, pt, d2);
+                                    dr2[2 * u] = cmul_fixed(make_float2(pt.x, pt.y), rot);
+                                    dr2[2 * u + 1] = cmul_fixed(make_float2(pt.z, pt.w), rot);
+                                    hd[2 * u] = hold_radius2(mg, cnorm(z0) + cnorm(z1));
+                                    sp_base[u] = make_float4(p0.x, p0.y, p1.x, p1.y);
+                                }
+                            } else {
+                                const float2 zh = h ? z1 : z0;
+                                const float mg = margin_of<2>(zh, zh, pt, d2);
+                                dr2[2 * u + h] = cmul_fixed(make_float2(pt.x, pt.y), rot);
+                                hd[2 * u + h] = hold_radius2(mg, cnorm(zh));
+                                if (h == 0) sp_base[u] = make_float4(p0.x, p0.y, p1.x, p1.y);
+                            }
+                        }
+                        __syncwarp();
+                    }
                     float2 y0, y1;
                     y0.x = __shfl_sync(0xffffffffu, v0.x, 0);
                     y0.y = __shfl_sync(0xffffffffu, v0.y, 0);
                     y1.x = __shfl_sync(0xffffffffu, v1.x, 0);
                     y1.y = __shfl_sync(0xffffffffu, v1.y, 0);
                     const float2 *Rl = Rr + lane;
+                    // the shared operands of update i are read one update ahead
+                    // (program order puts those reads before the update's store,
+                    // so their latency overlaps the update)
+                    float2 rc_n = Rl[0], r1_n = Rr[1];
+                    float4 sb_n, dr_n;
+                    float2 hr_n;
+                    if (MODE == 1) {
+                        sb_n = sp_base[0];
+                        dr_n = sp_dr[0];
+                        hr_n = sp_hold[0];
+                    }
 #pragma unroll 2
                     for (int i = 0; i < ms; ++i) {
                         const int k = kSB * s + i;
                         // mu r(k, 16 s + lane) (lanes <= i read values they never use)
-                        const float2 rc = Rl[i * (kLag - 1)];
-                        const float2 r1 = Rr[i * kLag + 1];                             // mu r(k, k + 1)
+                        const float2 rc = rc_n;
+                        const float2 r1 = r1_n;                                         // mu r(k, k + 1)
+                        const float4 sb = sb_n, dr = dr_n;
+                        const float2 hr = hr_n;
+                        {
+                            const int in = min(i + 1, kSB - 1);
+                            rc_n = Rl[in * (kLag - 1)];
+                            r1_n = Rr[in * kLag + 1];
+                            if (MODE == 1) {
+                                sb_n = sp_base[in];
+                                dr_n = sp_dr[in];
+                                hr_n = sp_hold[in];
+                            }
+                        }
                         // the next update's partial before this update's term:
                         // fetched while the decision runs
                         float2 w0, w1;
@@ -398,41 +614,55 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
                             e0 = csub(tg0[k], y0);
                             e1 = csub(tg1[k], y1);
                         } else {
-                            const float2 rot = rots[k];                               // exp(j phi)
-                            // this lane's representative turned by phi: the
-                            // correlation with y equals that of y exp(-j phi)
-                            // with the representative, and |y| = |y exp(-j phi)|
-                            const float2 q0 = cmul(make_float2(r.x, r.y), rot);
-                            float2 d0, d1;
-                            if (DIMS == 4) {
-                                const float2 q1 = cmul(make_float2(r.z, r.w), rot);
-                                const float P = (y0.x * q0.x + y0.y * q0.y) + (y1.x * q1.x + y1.y * q1.y);
-                                const float Q = (y0.y * q0.x - y0.x * q0.y) + (y1.y * q1.x - y1.x * q1.y);
-                                float v;
-                                int lb;
-                                best_rot_label(P, Q, f.S, lab, v, lb);
-                                const float dist = (cnorm(y0) + cnorm(y1)) + (eo - 2.f * v);
-                                const float4 pt = tb.pts[argmin_label(dist, lb)];
-                                d0 = make_float2(pt.x, pt.y);
-                                d1 = make_float2(pt.z, pt.w);
-                            } else {
-                                float va, vb;
-                                int la, lc;
-                                best_rot_label(y0.x * q0.x + y0.y * q0.y, y0.y * q0.x - y0.x * q0.y, f.S, lab, va, la);
-                                best_rot_label(y1.x * q0.x + y1.y * q0.y, y1.y * q0.x - y1.x * q0.y, f.S, lab, vb, lc);
-                                // one orbit (e.g. QPSK): every lane holds the same candidate
-                                // (lanes past the table use orbit 0 too), so it is the decision
-                                if (f.n_orb > 1) {
-                                    la = argmin_label(cnorm(y0) + (eo - 2.f * va), la);
-                                    lc = argmin_label(cnorm(y1) + (eo - 2.f * vb), lc);
+                            // the decision taken ahead holds while the terms added
+                            // since stay inside its hold radius (the same for every
+                            // lane: y and the shared values are warp-uniform)
+                            bool hold;
+                            if (DIMS == 4)
+                                hold = cnorm(make_float2(y0.x - sb.x, y0.y - sb.y)) +
+                                       cnorm(make_float2(y1.x - sb.z, y1.y - sb.w)) < hr.x;
+                            else
+                                hold = cnorm(make_float2(y0.x - sb.x, y0.y - sb.y)) < hr.x &&
+                                       cnorm(make_float2(y1.x - sb.z, y1.y - sb.w)) < hr.y;
+                            e0 = sub_rn(make_float2(dr.x, dr.y), y0);
+                            e1 = sub_rn(make_float2(dr.z, dr.w), y1);
+                            if (!__all_sync(0xffffffffu, hold && ahead)) {
+                                const float2 rot = rots[k];                               // exp(j phi)
+                                // this lane's representative turned by phi: the
+                                // correlation with y equals that of y exp(-j phi)
+                                // with the representative, and |y| = |y exp(-j phi)|
+                                const float2 q0 = cmul(make_float2(r.x, r.y), rot);
+                                float2 d0, d1;
+                                if (DIMS == 4) {
+                                    const float2 q1 = cmul(make_float2(r.z, r.w), rot);
+                                    const float P = (y0.x * q0.x + y0.y * q0.y) + (y1.x * q1.x + y1.y * q1.y);
+                                    const float Q = (y0.y * q0.x - y0.x * q0.y) + (y1.y * q1.x - y1.x * q1.y);
+                                    float v;
+                                    int lb;
+                                    best_rot_label(P, Q, f.S, lab, v, lb);
+                                    const float dist = (cnorm(y0) + cnorm(y1)) + (eo - 2.f * v);
+                                    const float4 pt = tb.pts[argmin_label(dist, lb)];
+                                    d0 = make_float2(pt.x, pt.y);
+                                    d1 = make_float2(pt.z, pt.w);
+                                } else {
+                                    float va, vb;
+                                    int la, lc;
+                                    best_rot_label(y0.x * q0.x + y0.y * q0.y, y0.y * q0.x - y0.x * q0.y, f.S, lab, va, la);
+                                    best_rot_label(y1.x * q0.x + y1.y * q0.y, y1.y * q0.x - y1.x * q0.y, f.S, lab, vb, lc);
+                                    // one orbit (e.g. QPSK): every lane holds the same candidate
+                                    // (lanes past the table use orbit 0 too), so it is the decision
+                                    if (f.n_orb > 1) {
+                                        la = argmin_label(cnorm(y0) + (eo - 2.f * va), la);
+                                        lc = argmin_label(cnorm(y1) + (eo - 2.f * vb), lc);
+                                    }
+                                    const float4 p0 = tb.pts[la];
+                                    const float4 p1 = tb.pts[lc];
+                                    d0 = make_float2(p0.x, p0.y);
+                                    d1 = make_float2(p1.x, p1.y);
                                 }
-                                const float4 p0 = tb.pts[la];
-                                const float4 p1 = tb.pts[lc];
-                                d0 = make_float2(p0.x, p0.y);
-                                d1 = make_float2(p1.x, p1.y);
+                                e0 = sub_rn(cmul_fixed(d0, rot), y0);
+                                e1 = sub_rn(cmul_fixed(d1, rot), y1);
                             }
-                            e0 = csub(cmul(d0, rot), y0);
-                            e1 = csub(cmul(d1, rot), y1);
                         }
                         v0 = cadd(v0, cmul(e0, rc));
                         v1 = cadd(v1, cmul(e1, rc));
@@ -755,7 +985,7 @@ __global__ void ref_labels_kernel(const uint8_t *__restrict__ bits, reflab_t *__
 template <int T, int DIMS, int MODE>
 cudaError_t lms_launch_one(const void *x, long ns, const float2 *ti, float2 *to, long k0, int n_upd,
                            const uint16_t *pcode, long pstride, int passes, float mu,
-                           const reflab_t *ref, long rstride, int S, const FmtDev &f, cudaStream_t st, int sk, int wl) {
+                           const reflab_t *ref, long rstride, int S, const FmtDev &f, cudaStream_t st, int sk, int opts) {
     auto kern = lms_kernel<T, DIMS, MODE>;
     // the opt-in size is looked up and set once per device (host queries per
     // launch cost more than the launch when a handle runs one stream)
@@ -774,7 +1004,7 @@ cudaError_t lms_launch_one(const void *x, long ns, const float2 *ti, float2 *to,
         if ((e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn)) != cudaSuccess) return e;
         if (dev < 64) dyn_of[dev].store(dyn, std::memory_order_relaxed);
     }
-    kern<<<S, kThreads, dyn, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, sk, wl, f);
+    kern<<<S, kThreads, dyn, st>>>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, sk, opts, f);
     return cudaGetLastError();
 }
 
@@ -782,12 +1012,12 @@ template <int T, int MODE>
 cudaError_t lms_launch_mode(const void *x, long ns, const float2 *ti, float2 *to, long k0,
                             int n_upd, const uint16_t *pcode, long pstride, int passes, float mu,
                             const reflab_t *ref, long rstride, int S, const FmtDev &f,
-                            cudaStream_t st, int sk, int wl) {
+                            cudaStream_t st, int sk, int opts) {
     if (f.dims == 4)
         return lms_launch_one<T, 4, MODE>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref,
-                                          rstride, S, f, st, sk, wl);
+                                          rstride, S, f, st, sk, opts);
     return lms_launch_one<T, 2, MODE>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref,
-                                      rstride, S, f, st, sk, wl);
+                                      rstride, S, f, st, sk, opts);
 }
 
 template <int T>
@@ -795,24 +1025,24 @@ cudaError_t lms_dispatch_dims(const void *x, long ns, const float2 *ti, float2 *
                               int n_upd, const uint16_t *pcode, long pstride, int mode,
                               int passes, unsigned long long u0, int n_cma, float mu,
                               const reflab_t *ref, long rstride, int S, const FmtDev &f,
-                              cudaStream_t st, int sk, int wl) {
+                              cudaStream_t st, int sk, int opts) {
     switch (mode) {
-        case 0: return lms_launch_mode<T, 0>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk, wl);
-        case 1: return lms_launch_mode<T, 1>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk, wl);
-        case 3: return lms_launch_mode<T, 3>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk, wl);
+        case 0: return lms_launch_mode<T, 0>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk, opts);
+        case 1: return lms_launch_mode<T, 1>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk, opts);
+        case 3: return lms_launch_mode<T, 3>(x, ns, ti, to, k0, n_upd, pcode, pstride, passes, mu, ref, rstride, S, f, st, sk, opts);
         case 2: {
             // CMA while the update count is below n_cma, DD after (one pass)
             const long ncma = (u0 >= (unsigned long long)n_cma) ? 0 : std::min<long>(n_upd, (long)(n_cma - u0));
             cudaError_t e = cudaSuccess;
             const float2 *src = ti;
             if (ncma > 0) {
-                e = lms_launch_mode<T, 0>(x, ns, src, to, k0, (int)ncma, pcode, pstride, 1, mu, ref, rstride, S, f, st, sk, wl);
+                e = lms_launch_mode<T, 0>(x, ns, src, to, k0, (int)ncma, pcode, pstride, 1, mu, ref, rstride, S, f, st, sk, opts);
                 if (e != cudaSuccess) return e;
                 src = to;
             }
             if (n_upd - ncma > 0)
                 e = lms_launch_mode<T, 1>(x, ns, src, to, k0 + ncma, (int)(n_upd - ncma), pcode, pstride, 1, mu,
-                                          ref, rstride, S, f, st, sk, wl);
+                                          ref, rstride, S, f, st, sk, opts);
             return e;
         }
         default: return cudaErrorInvalidValue;
@@ -824,17 +1054,17 @@ cudaError_t lms_dispatch_dims(const void *x, long ns, const float2 *ti, float2 *
 cudaError_t launch_lms(const void *x, long ns, const float2 *taps_in, float2 *taps_out, long k0,
                        int n_upd, const uint16_t *pcode, long pcode_stride, int mode, int passes,
                        unsigned long long u0, int n_cma, float mu, const reflab_t *ref_lab,
-                       long ref_stride, int n_streams, int T, const FmtDev &f, cudaStream_t st, int sk, int wl) {
+                       long ref_stride, int n_streams, int T, const FmtDev &f, cudaStream_t st, int sk, int opts) {
     if (n_upd <= 0 || n_streams <= 0) {
         if (taps_in != taps_out)
-            return cudaMemcpyAsync(taps_out, taps_in, sizeof(float2) * 4 * T * (size_t)n_streams,
+            return cudaMemcpyAsync(taps_out, taps_in, sizeof(float2) * 4 * ((opts & LMS_WL) ? 2 * T : T) * (size_t)n_streams,
                                    cudaMemcpyDeviceToDevice, st);
         return cudaSuccess;
     }
     switch (T) {
-        case 7: return lms_dispatch_dims<7>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk, wl);
-        case 15: return lms_dispatch_dims<15>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk, wl);
-        case 31: return lms_dispatch_dims<31>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk, wl);
+        case 7: return lms_dispatch_dims<7>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk, opts);
+        case 15: return lms_dispatch_dims<15>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk, opts);
+        case 31: return lms_dispatch_dims<31>(x, ns, taps_in, taps_out, k0, n_upd, pcode, pcode_stride, mode, passes, u0, n_cma, mu, ref_lab, ref_stride, n_streams, f, st, sk, opts);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -151,6 +151,10 @@ struct rx_handle {
     // the tensor-core phase search (parameter "bps_tc", default on where the
     // format allows): its B operand, built for the table and B test phases
     int bps_tc = 0;
+    // the DD-LMS's warp-wide nearest-point search on every update (parameter
+    // "lms_exact"; default 0: decisions taken a sub-block ahead where the
+    // margin allows, with the same results)
+    int lms_exact = 0;
     float *bps_w = nullptr;
     int tab_fft = 0;
     bool tables_dirty = true;
@@ -436,6 +440,7 @@ int ensure_symbol_buffers(rx_handle *h, long N) {
 
 // taps per butterfly branch (widely linear: T on x, then T on conj x)
 int tl(const rx_handle *h) { return h->wl ? 2 * h->T : h->T; }
+int lms_opts(const rx_handle *h) { return (h->wl ? LMS_WL : 0) | (h->lms_exact ? LMS_EXACT_DD : 0); }
 
 // Tap-ring slots.  U_n goes to slot n; it is read by the FIR of block
 // n + lag and by the update that starts from it.  Sequential chain
@@ -603,7 +608,7 @@ int train_stage(rx_handle *h, const void *x, long ns, float2 *taps, long ntr, ui
     if (h->train_passes > 0)
         STAGE(ST_STARTUP, st, 1, launch_lms(x, ns, taps, taps, 0, (int)ntr, pcode, pcode_stride, 3,
                                             h->train_passes, 0, 0, (float)h->mu, h->ref, h->ref_n,
-                                            S, T, h->fmt, st, sk, h->wl));
+                                            S, T, h->fmt, st, sk, lms_opts(h)));
     return RX_OK;
 }
 
@@ -704,7 +709,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         CK(launch_center_spike(w0, S, tl(h), (h->T - 1) / 2, ss));
         const long npre = std::min(h->n_pre, N);
         STAGE(ST_STARTUP, ss, 1, launch_lms(h->x, ns, w0, w0, 0, (int)npre, nullptr, 0, 0, h->cma_passes,
-                                            0, 0, (float)h->mu, nullptr, 0, S, T, f, ss, h->prec, h->wl));
+                                            0, 0, (float)h->mu, nullptr, 0, S, T, f, ss, h->prec, lms_opts(h)));
         // stream state: counters zero, unwrap carry phi_hat = 0
         CK(launch_stream_init(h->sd, S, h->B, st));
         const long ntr = std::min(h->n_train, N);
@@ -843,7 +848,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         else
             STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
                   launch_lms(h->x, ns, u_in, slot(h, g), k0, (int)span, h->pcode, N, 2, 1,
-                             h->u, (int)h->n_cma, (float)h->mu, nullptr, 0, S, T, f, ls, h->prec, h->wl));
+                             h->u, (int)h->n_cma, (float)h->mu, nullptr, 0, S, T, f, ls, h->prec, lms_opts(h)));
         if (L >= 2) CK(cudaEventRecord(h->ev_lms[g % R], ls));
         h->u += span;
         h->blocks_done = g + 1;
@@ -1144,6 +1149,7 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     else if (k == "profile") { rc = as_int(0, 2, t); h->profile = (int)t; }
     else if (k == "precision") { rc = as_int(0, 2, t); h->prec = (int)t; }
     else if (k == "bps_tc") { rc = as_int(0, 1, t); h->bps_tc = (int)t; }
+    else if (k == "lms_exact") { rc = as_int(0, 1, t); h->lms_exact = (int)t; }
     else return fail(RX_EINVAL, "unknown parameter '%s'", k.c_str());
     if (rc != RX_OK) return rc;
     if (k == "overlap") h->tables_dirty = true;
@@ -1316,6 +1322,7 @@ int rx_get_param(const rx_handle *h, const char *key, double *value) {
     else if (k == "taps") *value = h->T;
     else if (k == "bps_phases") *value = h->B;
     else if (k == "bps_tc") *value = use_bps_tc(h) ? 1.0 : 0.0;
+    else if (k == "lms_exact") *value = h->lms_exact;
     else if (k == "cd_ps_per_nm") *value = h->cd;
     else if (k == "profile") *value = h->profile;
     else if (k == "precision") *value = h->prec;
@@ -1920,7 +1927,7 @@ int rx_lms(rx_handle *h, const void *x, size_t n_samples, void *taps, size_t k0,
     }
     CK(launch_lms((const float2 *)x, (long)n_samples, (const float2 *)taps, (float2 *)taps, (long)k0,
                   (int)n_upd, pcode, N, mode, passes, u0, (int)h->n_cma, (float)h->mu, h->ref,
-                  h->ref_n, h->streams, h->T, h->fmt, h->st, SK_F32, h->wl));
+                  h->ref_n, h->streams, h->T, h->fmt, h->st, SK_F32, lms_opts(h)));
     return RX_OK;
 }
 

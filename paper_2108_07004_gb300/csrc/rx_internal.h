@@ -156,12 +156,16 @@ cudaError_t launch_fir(const void *x, long ns, const float2 *taps, long k0, long
                        void *y, long y_stride, long y_off, int n_streams, int T,
                        cudaStream_t st, int sk = SK_F32, int sm_avail = 0, int wl = 0);
 
+// opts of launch_lms: LMS_WL widely-linear taps; LMS_EXACT_DD the warp-wide
+// nearest-point search on every DD update (no decisions taken ahead; the
+// results are the same)
+enum { LMS_WL = 1, LMS_EXACT_DD = 2 };
 cudaError_t launch_lms(const void *x, long ns, const float2 *taps_in, float2 *taps_out,
                        long k0, int n_upd, const uint16_t *pcode, long pcode_stride,
                        int mode, int passes, unsigned long long u0, int n_cma, float mu,
                        const reflab_t *ref_lab, long ref_stride,
                        int n_streams, int T, const FmtDev &f, cudaStream_t st, int sk = SK_F32,
-                       int wl = 0);
+                       int opts = 0);
 
 // Block LMS: groups of P (1..64) updates share the taps at the group start
 // (mode 0 CMA, 1 DD, 2 CMA below n_cma updates then DD).
