@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256, 2)
 bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_valid, int W,
            uint8_t *__restrict__ bout, long bout_stride, int *__restrict__ dsum,
            double *__restrict__ mdsum, int n_cta, int chunks, int sk, const __grid_constant__ FmtDev f) {
-    extern __shared__ float smem[];
+    extern __shared__ __align__(16) float smem[];
     const int B = f.B;
     const int kChunks = chunks, kR = range_of(chunks);
     const int rounds = (kChunks + 2 + 7) / 8;           // chunks -1 .. kChunks
@@ -200,16 +200,32 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
             // exclusive prefix of every test phase's row over the chunk's 32
             // symbols, in place: lane l takes phases l and l + 32 (rows padded to
             // 33 floats, so the lanes' serial walks hit 32 different banks)
-            for (int b = lane; b < B; b += 32) {
-                float *row = Eb + (slot * B + b) * kRow;
-                float run = 0.f;
+            if (B == 64) {
+                // two independent rows per lane, interleaved
+                float *ra = Eb + (slot * B + lane) * kRow, *rb = ra + 32 * kRow;
+                float run_a = 0.f, run_b = 0.f;
     #pragma unroll
                 for (int j = 0; j < 32; ++j) {
-                    const float v = row[j];
-                    row[j] = run;
-                    run += v;
+                    const float va = ra[j], vb = rb[j];
+                    ra[j] = run_a;
+                    rb[j] = run_b;
+                    run_a += va;
+                    run_b += vb;
                 }
-                Tb[slot * B + b] = run;
+                Tb[slot * B + lane] = run_a;
+                Tb[slot * B + lane + 32] = run_b;
+            } else {
+                for (int b = lane; b < B; b += 32) {
+                    float *row = Eb + (slot * B + b) * kRow;
+                    float run = 0.f;
+    #pragma unroll
+                    for (int j = 0; j < 32; ++j) {
+                        const float v = row[j];
+                        row[j] = run;
+                        run += v;
+                    }
+                    Tb[slot * B + b] = run;
+                }
             }
         }
         __syncthreads();
@@ -235,9 +251,28 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
                 float best = 3.0e38f;
                 int bb = 0;
                 const float *e0 = Eb + s0 * B * kRow + l0, *e1 = Eb + s1 * B * kRow + l1;
-                if (c0 == oc - 1 && c1 == oc + 1) {
+                if (c0 == oc - 1 && c1 == oc + 1 && (B & 3) == 0) {
                     // window over chunks oc - 1 .. oc + 1: the two-chunk total
-                    // minus the head of chunk oc - 1 plus the head of oc + 1
+                    // minus the head of chunk oc - 1 plus the head of oc + 1.
+                    // Four argmin chains (phases b = 4 q + j) keep the compare
+                    // latency off a single chain; each keeps its lowest phase on
+                    // ties, and the merge takes the lowest phase of equal costs
+                    float bst[4] = {3.0e38f, 3.0e38f, 3.0e38f, 3.0e38f};
+                    int bi[4] = {0, 1, 2, 3};
+#pragma unroll 2
+                    for (int b = 0; b < B; b += 4) {
+                        const float4 t = *reinterpret_cast<const float4 *>(t2 + b);
+                        const float tt[4] = {t.x, t.y, t.z, t.w};
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const float cst = (tt[j] - e0[(b + j) * kRow]) + e1[(b + j) * kRow];
+                            if (cst < bst[j]) { bst[j] = cst; bi[j] = b + j; }
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < 4; ++j)
+                        if (bst[j] < best || (bst[j] == best && bi[j] < bb)) { best = bst[j]; bb = bi[j]; }
+                } else if (c0 == oc - 1 && c1 == oc + 1) {
 #pragma unroll 4
                     for (int b = 0; b < B; ++b) {
                         const float cst = (t2[b] - e0[b * kRow]) + e1[b * kRow];
