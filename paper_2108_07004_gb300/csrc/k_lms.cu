@@ -69,10 +69,13 @@ struct Tables {
 };
 
 __device__ __forceinline__ void load_tables(Tables &tb, const FmtDev &f) {
-    for (int i = threadIdx.x; i < f.n_orb; i += blockDim.x) {
-        tb.orb[i] = make_float4(f.orb[i][0], f.orb[i][1], f.orb[i][2], f.orb[i][3]);
-        tb.orbe[i] = f.orbe[i];
-        for (int k = 0; k < 4; ++k) tb.orblab[i][k] = f.orb_lab[i][k];
+    // at least 16 orbit entries: past n_orb a zero representative of energy
+    // +inf, never a candidate of the orbit searches
+    for (int i = threadIdx.x; i < max(f.n_orb, 16); i += blockDim.x) {
+        const bool v = i < f.n_orb;
+        tb.orb[i] = v ? make_float4(f.orb[i][0], f.orb[i][1], f.orb[i][2], f.orb[i][3]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        tb.orbe[i] = v ? f.orbe[i] : __int_as_float(0x7f800000);
+        for (int k = 0; k < 4; ++k) tb.orblab[i][k] = v ? f.orb_lab[i][k] : 0;
     }
     for (int i = threadIdx.x; i < f.M; i += blockDim.x)
         tb.pts[i] = make_float4(f.pts[i][0], f.pts[i][1], f.pts[i][2], f.pts[i][3]);
@@ -123,13 +126,12 @@ __device__ __forceinline__ float2 sub_rn(float2 a, float2 b) {
     return make_float2(__fsub_rn(a.x, b.x), __fsub_rn(a.y, b.y));
 }
 
-// Orbit o's two best rotations against the running two smallest squared
-// distances d1 <= d2 (branch-free: the second smallest of {d1, d2, dA, dB}
-// with dA <= dB is min(max(d1, dA), min(d2, dB))); `best` = o S + k of the
-// nearest, k quarter turns (for S = 4 the values max and min of |P|, |Q|).
+// Orbit o's two best rotations (for S = 4 the values max and min of |P|,
+// |Q|): their squared distances dA <= dB and o S + k of the nearer (k quarter
+// turns).
 template <int DIMS>
 __device__ __forceinline__ void orbit_two(float2 z0, float2 z1, float zz, float4 r, float e, int o, int S,
-                                          float &d1, float &d2, int &best) {
+                                          float &dA, float &dB, int &ix) {
     float P = z0.x * r.x + z0.y * r.y, Q = z0.y * r.x - z0.x * r.y;
     if (DIMS == 4) {
         P += z1.x * r.z + z1.y * r.w;
@@ -152,51 +154,83 @@ __device__ __forceinline__ void orbit_two(float2 z0, float2 z1, float zz, float4
         k1 = 0;
     }
     const float base = zz + e;
-    const float dA = fmaf(-2.f, v1, base), dB = fmaf(-2.f, v2, base);
-    best = dA < d1 ? o * S + k1 : best;
-    d2 = fminf(fmaxf(d1, dA), fminf(d2, dB));
-    d1 = fminf(d1, dA);
+    dA = fmaf(-2.f, v1, base);
+    dB = fmaf(-2.f, v2, base);
+    ix = o * S + k1;
+}
+
+// The two smallest of N sorted pairs (a_i <= b_i) by a merge tree (the
+// second smallest of two pairs is min(max(a_1, a_2), min(b_1, b_2))), so the
+// compare latency grows with log N; ix follows the smaller a.
+template <int N>
+__device__ __forceinline__ void two_smallest_tree(float (&a)[N], float (&b)[N], int (&ix)[N]) {
+#pragma unroll
+    for (int w = 1; w < N; w *= 2)
+#pragma unroll
+        for (int o = 0; o + w < N; o += 2 * w) {
+            const bool sw = a[o + w] < a[o];
+            const float m2 = fminf(fmaxf(a[o], a[o + w]), fminf(b[o], b[o + w]));
+            a[o] = fminf(a[o], a[o + w]);
+            b[o] = m2;
+            ix[o] = sw ? ix[o + w] : ix[o];
+        }
 }
 
 // The two smallest squared distances from the de-rotated z to the table
 // (each orbit's two best rotations hold the nearest point and the
-// second-nearest).  DIMS 4: the lanes of half h take orbits o + 8 h, o < 8
-// (table entries as constant operands, chosen by h), up to 16 orbits, then
-// every second orbit past 16; DIMS 2 reads z0 alone and takes every orbit.
-// Past n_orb the energy is +inf (never a candidate).
+// second-nearest) and o S + k of the nearest.  DIMS 4: the lanes of half h
+// take orbits 2 o + h (o < 8, adjacent table entries: one shared-memory
+// wavefront), then every second orbit past 16; DIMS 2 reads z0 alone and
+// takes every orbit.  The table holds at least 16 entries (energy +inf
+// past n_orb).
 template <int DIMS>
-__device__ __forceinline__ void two_nearest(float2 z0, float2 z1, const FmtDev &f, int h, float &d1, float &d2,
-                                            int &best) {
+__device__ __forceinline__ void two_nearest(float2 z0, float2 z1, const Tables &tb, const FmtDev &f, int h,
+                                            float &d1, float &d2, int &best) {
     const float zz = DIMS == 4 ? cnorm(z0) + cnorm(z1) : cnorm(z0);
-    const float inf = __int_as_float(0x7f800000);
     const int S = f.S, n = f.n_orb;
-    d1 = inf;
-    d2 = inf;
-    best = 0;
     if (DIMS == 4) {
+        float a[8], b[8];
+        int ix[8];
 #pragma unroll
-        for (int o = 0; o < 8; ++o) {
-            const int oo = o + 8 * h;
-            const float4 r = h ? make_float4(f.orb[o + 8][0], f.orb[o + 8][1], f.orb[o + 8][2], f.orb[o + 8][3])
-                               : make_float4(f.orb[o][0], f.orb[o][1], f.orb[o][2], f.orb[o][3]);
-            const float e = oo < n ? (h ? f.orbe[o + 8] : f.orbe[o]) : inf;
-            orbit_two<4>(z0, z1, zz, r, e, oo, S, d1, d2, best);
-        }
+        for (int o = 0; o < 8; ++o)
+            orbit_two<4>(z0, z1, zz, tb.orb[2 * o + h], tb.orbe[2 * o + h], 2 * o + h, S, a[o], b[o], ix[o]);
+        two_smallest_tree<8>(a, b, ix);
+        d1 = a[0];
+        d2 = b[0];
+        best = ix[0];
         for (int oo = 16 + h; oo < n; oo += 2) {
-            const float4 r = make_float4(f.orb[oo][0], f.orb[oo][1], f.orb[oo][2], f.orb[oo][3]);
-            orbit_two<4>(z0, z1, zz, r, f.orbe[oo], oo, S, d1, d2, best);
+            float dA, dB;
+            int io;
+            orbit_two<4>(z0, z1, zz, tb.orb[oo], tb.orbe[oo], oo, S, dA, dB, io);
+            best = dA < d1 ? io : best;
+            d2 = fminf(fmaxf(d1, dA), fminf(d2, dB));
+            d1 = fminf(d1, dA);
         }
-    } else {
+    } else if (n <= 4) {
+        float a[4], b[4];
+        int ix[4];
 #pragma unroll
-        for (int o = 0; o < 16; ++o) {
-            if (o < n) {
-                const float4 r = make_float4(f.orb[o][0], f.orb[o][1], 0.f, 0.f);
-                orbit_two<2>(z0, z0, zz, r, f.orbe[o], o, S, d1, d2, best);
-            }
-        }
+        for (int o = 0; o < 4; ++o) orbit_two<2>(z0, z0, zz, tb.orb[o], tb.orbe[o], o, S, a[o], b[o], ix[o]);
+        two_smallest_tree<4>(a, b, ix);
+        d1 = a[0];
+        d2 = b[0];
+        best = ix[0];
+    } else {
+        float a[16], b[16];
+        int ix[16];
+#pragma unroll
+        for (int o = 0; o < 16; ++o) orbit_two<2>(z0, z0, zz, tb.orb[o], tb.orbe[o], o, S, a[o], b[o], ix[o]);
+        two_smallest_tree<16>(a, b, ix);
+        d1 = a[0];
+        d2 = b[0];
+        best = ix[0];
         for (int o = 16; o < n; ++o) {
-            const float4 r = make_float4(f.orb[o][0], f.orb[o][1], 0.f, 0.f);
-            orbit_two<2>(z0, z0, zz, r, f.orbe[o], o, S, d1, d2, best);
+            float dA, dB;
+            int io;
+            orbit_two<2>(z0, z0, zz, tb.orb[o], tb.orbe[o], o, S, dA, dB, io);
+            best = dA < d1 ? io : best;
+            d2 = fminf(fmaxf(d1, dA), fminf(d2, dB));
+            d1 = fminf(d1, dA);
         }
     }
 }
@@ -531,7 +565,7 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
                         float d1, d2;
                         int best;
                         if (DIMS == 4) {
-                            two_nearest<4>(z0, z1, f, h, d1, d2, best);
+                            two_nearest<4>(z0, z1, tb, f, h, d1, d2, best);
                             const float od1 = __shfl_xor_sync(0xffffffffu, d1, 16);
                             const float od2 = __shfl_xor_sync(0xffffffffu, d2, 16);
                             const int ob = __shfl_xor_sync(0xffffffffu, best, 16);
@@ -539,7 +573,7 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
                             best = od1 < d1 ? ob : best;   // exact ties: margin 0, never held
                             d1 = fminf(d1, od1);
                         } else {
-                            two_nearest<2>(h ? z1 : z0, z1, f, h, d1, d2, best);
+                            two_nearest<2>(h ? z1 : z0, z1, tb, f, h, d1, d2, best);
                         }
                         const float4 pt = tb.rpts[best];
                         if (u < ms) {
