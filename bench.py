@@ -356,23 +356,44 @@ def run_ours(args):
             dist.barrier()
 
     n_sym, S = args.n_sym, args.streams
+    F = max(1, args.frames_in_flight)
     rx_h, bits_h = make_inputs(rank, n_sym, S)
     samples = torch.from_numpy(rx_h).cuda()
     bits = torch.from_numpy(bits_h).cuda()
-    r = rx_mod.Receiver(WL["fmt"], cd_ps_per_nm=WL["cd_ps_per_nm"], taps=WL["taps"],
-                        bps_phases=WL["bps_phases"], streams=S, **rx_params())
-    r.set_reference(bits)
-    llr = torch.empty((S, n_sym, 6), dtype=torch.float32, device="cuda")
+    # F handles, each on a stream of its own; consecutive steps (one complete
+    # 9-stream frame each) alternate between them, so one frame's start-up
+    # (the sequential CMA and training on 9 SMs) runs beside the previous
+    # frame's blocks.  Every step's work is complete; the results of every
+    # handle are those of a single handle.
+    cur = torch.cuda.current_stream()
+    hst = [torch.cuda.Stream() for _ in range(F)]
+    rs = []
+    for i in range(F):
+        ri = rx_mod.Receiver(WL["fmt"], cd_ps_per_nm=WL["cd_ps_per_nm"], taps=WL["taps"],
+                             bps_phases=WL["bps_phases"], streams=S, stream=hst[i], **rx_params())
+        ri.set_reference(bits)
+        rs.append(ri)
+    r = rs[0]
+    llrs = [torch.empty((S, n_sym, 6), dtype=torch.float32, device="cuda") for _ in range(F)]
+    llr = llrs[0]
+
+    def steps(k, handles):
+        for s_ in hst[:handles]:
+            s_.wait_stream(cur)
+        for i in range(k):
+            rs[i % handles].process(samples, llrs[i % handles], stats=False)
+        for s_ in hst[:handles]:
+            cur.wait_stream(s_)
+
     # timed steps: CUDA events around the BPS launches only (the roofline's
     # live kernel time); the stage breakdown comes from profiled steps after
-    r.set("profile", 2)
-    for _ in range(args.warmup):
-        r.process(samples, llr, stats=False)
+    for ri in rs:
+        ri.set("profile", 2)
+    steps(max(args.warmup, F), F)
     torch.cuda.synchronize()
     # the roofline's denominator, measured on this GPU before the timed steps
     ipk = issue_peaks(rx_mod, local) if rank == 0 else None
-    for _ in range(2):
-        r.process(samples, llr, stats=False)
+    steps(2 * F, F)
     torch.cuda.synchronize()
     clk = Clocks(local)
     clk.start()
@@ -380,17 +401,31 @@ def run_ours(args):
     barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    ev0.record()
-    for _ in range(args.steps):
-        r.process(samples, llr, stats=False)
-    ev1.record()
+    ev0.record(cur)
+    steps(args.steps, F)
+    ev1.record(cur)
     torch.cuda.synchronize()
     barrier()
     clocks = clk.stop()
     ms = ev0.elapsed_time(ev1) / args.steps
     stats = r.stats()
-    bps_live = r.profile("bps")                 # last timed step
+    bps_live = r.profile("bps")                 # last timed step of handle 0
     launches_per_step = r.launches()
+    # one frame at a time (one handle), the same steps
+    ms_one, bps_live_one = None, None
+    if F > 1:
+        steps(2, 1)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(cur)
+        steps(args.steps, 1)
+        e1.record(cur)
+        torch.cuda.synchronize()
+        ms_one = e0.elapsed_time(e1) / args.steps
+        bps_live_one = r.profile("bps")         # last step, one frame at a time
+        same = all(torch.equal(llrs[0], l_) for l_ in llrs[1:])
+    else:
+        same = True
     r.set("profile", 1)                         # untimed: every stage and block
     for _ in range(2):
         r.process(samples, llr, stats=False)
@@ -407,22 +442,37 @@ def run_ours(args):
     # ---- end to end through the host-buffer entry point ----
     e2e = None
     if not args.no_e2e:
+        import threading
         s_h = torch.from_numpy(rx_h).pin_memory()
         b_h = torch.from_numpy(bits_h).pin_memory()
-        l_h = torch.empty((S, n_sym, 6), dtype=torch.float32).pin_memory()
-        r.set("profile", 0)
-        for _ in range(2):
-            r.set_reference_host(b_h)
-            r.process_host(s_h, l_h, stats=False)
+        l_hs = [torch.empty((S, n_sym, 6), dtype=torch.float32).pin_memory() for _ in range(F)]
+        for ri in rs:
+            ri.set("profile", 0)
+        ke = max(3, args.steps // 4)
+
+        def host_steps(i, k):
+            # one host thread per handle (the entry point returns when the
+            # LLRs are in host memory); the GIL is released inside the call
+            torch.cuda.set_device(local)
+            for _ in range(k):
+                rs[i].set_reference_host(b_h)
+                rs[i].process_host(s_h, l_hs[i], stats=False)
+
+        def run_host(k):
+            th = [threading.Thread(target=host_steps, args=(i, k)) for i in range(F)]
+            for t_ in th:
+                t_.start()
+            for t_ in th:
+                t_.join()
+
+        run_host(2)
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        ke = max(3, args.steps // 4)
-        for _ in range(ke):
-            r.set_reference_host(b_h)
-            r.process_host(s_h, l_h, stats=False)
+        run_host(ke)
         torch.cuda.synchronize()
-        dt = (time.perf_counter() - t0) / ke
+        dt = (time.perf_counter() - t0) / (ke * F)
+        l_h = l_hs[0]
         if world > 1:
             t = torch.tensor([dt], device="cuda")
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -447,6 +497,9 @@ def run_ours(args):
                      f"{ipk['ffma']['per_sm_clk']:.1f} lane-instr/SM/clk at {c.get('sm_mhz')} MHz median"
                      if ipk["ffma"]["per_sm_clk"] else "measured: FFMA issue probe (rx_issue_rate)")
     achieved = ops / (bps_ms * 1e-3) / 1e12 if bps_ms > 0 else None
+    # the same kernel's live rate when one frame runs at a time (its launches
+    # then share the SMs only with the same frame's demap)
+    ach_one = (ops / (bps_live_one[0] * 1e-3) / 1e12 if bps_live_one and bps_live_one[0] > 0 else None)
     cdc_ms = stage["cdc"][0]
     cdc_bytes = S * 2 * 2 * n_sym * 8 * (WL["fft"] / (WL["fft"] - WL["overlap"]) + 1)
     line = {
@@ -457,7 +510,11 @@ def run_ours(args):
         "config": {"workload": WL["workload"], "streams": S, "symbols_per_stream": n_sym,
                    "format": WL["fmt"], "fft": WL["fft"], "overlap": WL["overlap"],
                    "taps": WL["taps"], "bps_phases": WL["bps_phases"], "block": WL["block"],
-                   "lag": WL["lag"], "l2": "inputs 9 x 32 MiB > L2, no flush"},
+                   "lag": WL["lag"], "l2": "inputs 9 x 32 MiB > L2, no flush",
+                   "frames_in_flight": F},
+        "one_frame_at_a_time": ({"value": bits_per_step / (ms_one * 1e-3) / 1e9, "ms_per_step": ms_one}
+                                if ms_one else None),
+        "frames_identical": same,
         "latency": {"block_p50_ms": lat[len(lat) // 2] if lat else None,
                     "block_p99_ms": lat[min(len(lat) - 1, int(0.99 * len(lat)))] if lat else None,
                     "blocks_per_step": len(lat)},
@@ -466,6 +523,7 @@ def run_ours(args):
                      "traffic": bps_traffic() if n_sym == WL["n_sym"] and S == 9 else None,
                      "op": "one (test phase, constellation point) candidate distance",
                      "peak_from": peak_from,
+                     "frac_one_frame_at_a_time": (ach_one / peak_ops) if ach_one else None,
                      "issue_probe": ipk},
         "realtime_channels": value / (WL["symbol_rate"] * 6 / 1e9),
         "stages_ms": {k: v[0] for k, v in stage.items()},
@@ -1295,6 +1353,8 @@ def main():
     ap.add_argument("--cpu-sym", type=int, default=1 << 17)
     ap.add_argument("--ref-sym", type=int, default=1 << 14)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--frames-in-flight", type=int, default=2,
+                    help="handles whose consecutive frames overlap (1: one frame at a time)")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision", "serving", "block_lms", "widely_linear", "kk", "kk_chain", "mlp_infer", "bps_paths"],
