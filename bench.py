@@ -570,22 +570,35 @@ def chain_bytes_per_symbol(wl: dict, store: int) -> float:
     return (32 * ovl + 4 * store) + (4 * store + 2 * store) + (2 * store + 1) + (2 * store + 1 + 2 + 4 * m)
 
 
-def timed_steps(r, samples, llr, steps: int, warmup: int):
+def timed_steps(r, samples, llr, steps: int, warmup: int, r2=None, llr2=None):
     """Device ms per step (CUDA events, library events around the BPS
     launches only), then the stage breakdown of one profiled step and the
-    statistics."""
+    statistics.  With a second handle r2 (on a stream of its own, as r's)
+    consecutive steps alternate between the two, two frames in flight."""
     import torch
-    r.set("profile", 2)
-    for _ in range(warmup):
-        r.process(samples, llr, stats=False)
+    rs, ls = ([r, r2], [llr, llr2]) if r2 is not None else ([r], [llr])
+    cur = torch.cuda.current_stream()
+    for ri in rs:
+        ri.set("profile", 2)
+
+    def run(k):
+        for ri in rs:
+            ri.stream.wait_stream(cur)
+        for i in range(k):
+            rs[i % len(rs)].process(samples, ls[i % len(rs)], stats=False)
+        for ri in rs:
+            cur.wait_stream(ri.stream)
+
+    run(max(warmup, len(rs)))
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record()
-    for _ in range(steps):
-        r.process(samples, llr, stats=False)
-    e1.record()
+    e0.record(cur)
+    run(steps)
+    e1.record(cur)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / steps
+    for ri in rs[1:]:
+        ri.set("profile", 0)
     st_ = r.stats()
     r.set("profile", 1)
     r.process(samples, llr, stats=False)
@@ -1033,20 +1046,32 @@ def run_precision(args):
     pk, pk_kind = peaks()
     hbm = pk.get("hbm_gbs", 6800.0)
     forms = {}
+    F = max(1, min(2, args.frames_in_flight))
     for prec, name, store in ((0, "f32", 8), (1, "f16", 4), (2, "bf16", 4)):
-        r = rx_mod.Receiver(wl["fmt"], cd_ps_per_nm=wl["cd_ps_per_nm"], taps=wl["taps"],
-                            bps_phases=wl["bps_phases"], streams=S, **rx_params(wl), precision=prec)
-        r.set_reference(bits_d)
+        hs = []
+        for i in range(F):
+            hs.append(rx_mod.Receiver(wl["fmt"], cd_ps_per_nm=wl["cd_ps_per_nm"], taps=wl["taps"],
+                                      bps_phases=wl["bps_phases"], streams=S, stream=torch.cuda.Stream(),
+                                      **rx_params(wl), precision=prec))
+            hs[-1].set_reference(bits_d)
+        r = hs[0]
         llr = torch.empty((S, n, m), dtype=torch.float32, device="cuda")
-        ms, stg, st_ = timed_steps(r, samples, llr, args.steps, args.warmup)
+        llr2 = torch.empty_like(llr) if F > 1 else None
+        ms, stg, st_ = timed_steps(r, samples, llr, args.steps, args.warmup,
+                                   hs[1] if F > 1 else None, llr2)
+        ms_one = timed_steps(r, samples, llr, args.steps, 2)[0] if F > 1 else ms
+        same = bool(torch.equal(llr, llr2)) if F > 1 else True
         bps = chain_bytes_per_symbol(wl, store)
         sym_s = S * n / (ms * 1e-3)
         forms[name] = {"gbps": sym_s * m / 1e9, "ms_per_step": ms, "stages_ms": stg,
+                       "one_frame_at_a_time": {"gbps": S * n * m / (ms_one * 1e-3) / 1e9, "ms_per_step": ms_one},
+                       "frames_identical": same,
                        "bytes_per_symbol": bps, "hbm_gbs": sym_s * bps / 1e9,
                        "hbm_frac": sym_s * bps / 1e9 / hbm,
                        "bit_errors": int(sum(x["bit_errors"] for x in st_)),
                        "n_bits": int(sum(x["n_bits"] for x in st_))}
-        r.close()
+        for h_ in hs:
+            h_.close()
     be32 = forms["f32"]["bit_errors"]
     for name in ("f16", "bf16"):
         forms[name]["ber_delta_rel_vs_f32"] = (forms[name]["bit_errors"] - be32) / max(be32, 1)
@@ -1057,7 +1082,8 @@ def run_precision(args):
         "data": "synthetic",
         "config": {"workload": wl["workload"], "streams": S, "symbols_per_stream": n, "format": wl["fmt"],
                    "fft": wl["fft"], "overlap": wl["overlap"], "taps": wl["taps"], "bps_phases": wl["bps_phases"],
-                   "block": wl["block"], "lag": wl["lag"], "lms_start": wl.get("lms_start", 0)},
+                   "block": wl["block"], "lag": wl["lag"], "lms_start": wl.get("lms_start", 0),
+                   "frames_in_flight": F},
         "forms": forms, "hbm_peak_gbs": hbm, "hbm_peak_kind": pk_kind,
     }
     if not args.no_cpu_baseline:

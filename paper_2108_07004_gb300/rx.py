@@ -256,6 +256,7 @@ class Receiver:
         self.dims, self.m, self.M = dims.value, m.value, M.value
         st = stream if stream is not None else torch.cuda.current_stream()
         _ck(L.rx_set_stream(h, st.cuda_stream))
+        self.stream = st
         for k, v in params.items():
             self.set(k, v)
 
@@ -274,6 +275,7 @@ class Receiver:
 
     def set_stream(self, stream: torch.cuda.Stream):
         _ck(lib().rx_set_stream(self.h, stream.cuda_stream))
+        self.stream = stream
 
     def set_reference(self, bits: torch.Tensor):
         """bits: [S, N, m] uint8 on the device."""
