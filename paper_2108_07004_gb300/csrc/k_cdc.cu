@@ -9,7 +9,9 @@
 // is needed; the spectral multiply reads H at the matching natural index.
 //
 //   n_fft = 4096 = 16*16*16: 256 threads, 16 points per thread in registers,
-//     radix-16 passes with shared-memory exchanges (rows padded to 257).
+//     radix-16 passes with shared-memory exchanges (rows padded to 257);
+//     three blocks per SM (80 registers), so that one block's exchanges and
+//     barriers overlap the others' arithmetic.
 //   n_fft = 1024 = 32*32: one warp per frame (4 frames per block), radix-32
 //     passes, warp-synchronous exchanges only.
 //
@@ -26,7 +28,7 @@ using namespace fftdev;
 // 4096 points, 256 threads
 // ---------------------------------------------------------------------------
 template <int SK>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
 cdc4096_kernel(const float2 *__restrict__ in, typename Store<SK>::T *__restrict__ out, long ns, int S, int half,
                long f0, const float2 *__restrict__ H, const float2 *__restrict__ tw) {
     constexpr int RP = 257;   // padded row
