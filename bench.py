@@ -385,6 +385,11 @@ def run_ours(args):
         for s_ in hst[:handles]:
             cur.wait_stream(s_)
 
+    # with frames in flight each handle sizes its one-wave grids to leave SMs
+    # to the other frames (their LMS blocks and their main-stream kernels)
+    reserve = 2 * S * (F - 1)
+    for ri in rs:
+        ri.set("sm_reserve", reserve)
     # timed steps: CUDA events around the BPS launches only (the roofline's
     # live kernel time); the stage breakdown comes from profiled steps after
     for ri in rs:
@@ -411,9 +416,12 @@ def run_ours(args):
     stats = r.stats()
     bps_live = r.profile("bps")                 # last timed step of handle 0
     launches_per_step = r.launches()
-    # one frame at a time (one handle), the same steps
+    same = all(torch.equal(llrs[0], l_) for l_ in llrs[1:])
+    # one frame at a time (one handle, no SMs left out), the same steps
     ms_one, bps_live_one = None, None
     if F > 1:
+        r.set("sm_reserve", 0)
+        r.set("profile", 2)
         steps(2, 1)
         torch.cuda.synchronize()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -423,9 +431,6 @@ def run_ours(args):
         torch.cuda.synchronize()
         ms_one = e0.elapsed_time(e1) / args.steps
         bps_live_one = r.profile("bps")         # last step, one frame at a time
-        same = all(torch.equal(llrs[0], l_) for l_ in llrs[1:])
-    else:
-        same = True
     r.set("profile", 1)                         # untimed: every stage and block
     for _ in range(2):
         r.process(samples, llr, stats=False)
@@ -448,6 +453,7 @@ def run_ours(args):
         l_hs = [torch.empty((S, n_sym, 6), dtype=torch.float32).pin_memory() for _ in range(F)]
         for ri in rs:
             ri.set("profile", 0)
+            ri.set("sm_reserve", reserve)
         ke = max(3, args.steps // 4)
 
         def host_steps(i, k):
@@ -511,7 +517,7 @@ def run_ours(args):
                    "format": WL["fmt"], "fft": WL["fft"], "overlap": WL["overlap"],
                    "taps": WL["taps"], "bps_phases": WL["bps_phases"], "block": WL["block"],
                    "lag": WL["lag"], "l2": "inputs 9 x 32 MiB > L2, no flush",
-                   "frames_in_flight": F},
+                   "frames_in_flight": F, "sm_reserve": 2 * S * (F - 1)},
         "one_frame_at_a_time": ({"value": bits_per_step / (ms_one * 1e-3) / 1e9, "ms_per_step": ms_one}
                                 if ms_one else None),
         "frames_identical": same,

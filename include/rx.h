@@ -150,7 +150,11 @@ void rx_destroy(rx_handle *h);                      /* NULL-safe */
  *   "lms_exact" [0]: 1 runs the DD-LMS's warp-wide nearest-point search on
  *   every update; 0 takes each decision a sub-block ahead on the update's
  *   partial output and keeps it while the corrections added since stay
- *   inside half its margin (the same decisions and taps, bit for bit).
+ *   inside half its margin (the same decisions and taps, bit for bit),
+ *   "sm_reserve" [0]: SMs the handle leaves to other work on the GPU (e.g.
+ *   another handle's frame in flight) when it sizes the phase search and
+ *   FIR grids to one wave; the phase search's range split, and with it the
+ *   summation order of the block's sigma^2, follows the grid.
  * Changing a parameter resets the stream state (rx_reset). */
 int rx_set_param(rx_handle *h, const char *key, double value);
 int rx_get_param(const rx_handle *h, const char *key, double *value);

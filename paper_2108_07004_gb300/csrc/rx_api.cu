@@ -155,6 +155,10 @@ struct rx_handle {
     // "lms_exact"; default 0: decisions taken a sub-block ahead where the
     // margin allows, with the same results)
     int lms_exact = 0;
+    // SMs left to other work on the GPU (parameter "sm_reserve"; e.g. the LMS
+    // blocks of another handle's frame in flight): the grids that size
+    // themselves to one wave count them out
+    int sm_reserve = 0;
     float *bps_w = nullptr;
     int tab_fft = 0;
     bool tables_dirty = true;
@@ -731,7 +735,8 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     // grids of the main stream leave room for the side-stream LMS (one SM
     // per stream) when it runs beside them
     const int chains = (h->lms_start && L >= 2) ? L : 1;
-    const int avail = (L >= 2 && h->lms_block == 1) ? std::max(sm_count() / 2, sm_count() - chains * S) : sm_count();
+    const int sms = std::max(sm_count() / 2, sm_count() - h->sm_reserve);
+    const int avail = (L >= 2 && h->lms_block == 1) ? std::max(sm_count() / 2, sms - chains * S) : sms;
     const int R = ring_size(h);
     if (h->sigma2_fixed > 0 && h->sig_fixed_up != h->sigma2_fixed) {
         // uploaded when it changes (demaps of an earlier call may still read it)
@@ -1150,6 +1155,7 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     else if (k == "precision") { rc = as_int(0, 2, t); h->prec = (int)t; }
     else if (k == "bps_tc") { rc = as_int(0, 1, t); h->bps_tc = (int)t; }
     else if (k == "lms_exact") { rc = as_int(0, 1, t); h->lms_exact = (int)t; }
+    else if (k == "sm_reserve") { rc = as_int(0, 1024, t); h->sm_reserve = (int)t; }
     else return fail(RX_EINVAL, "unknown parameter '%s'", k.c_str());
     if (rc != RX_OK) return rc;
     if (k == "overlap") h->tables_dirty = true;
@@ -1323,6 +1329,7 @@ int rx_get_param(const rx_handle *h, const char *key, double *value) {
     else if (k == "bps_phases") *value = h->B;
     else if (k == "bps_tc") *value = use_bps_tc(h) ? 1.0 : 0.0;
     else if (k == "lms_exact") *value = h->lms_exact;
+    else if (k == "sm_reserve") *value = h->sm_reserve;
     else if (k == "cd_ps_per_nm") *value = h->cd;
     else if (k == "profile") *value = h->profile;
     else if (k == "precision") *value = h->prec;
