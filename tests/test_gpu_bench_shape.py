@@ -83,7 +83,7 @@ def test_chain_at_bench_launch_shape(oracle_runs):
     _chain_check(oracle_runs, bps_tc=0)
 
 
-def _chain_check(oracle_runs, bps_tc):
+def _chain_check(oracle_runs, bps_tc, sm_reserve=0):
     from oracle import chain
     from paper_2108_07004_gb300 import rx
     fmt = oracle_format(FMT)
@@ -95,6 +95,7 @@ def _chain_check(oracle_runs, bps_tc):
     assert nblk == 4
     r = _receiver(S)
     r.set("bps_tc", bps_tc)
+    r.set("sm_reserve", sm_reserve)
     r.set_reference(torch.from_numpy(np.stack([st.bits for st in sts])).cuda())
     samples = torch.from_numpy(np.stack([st.rx for st in sts])).cuda()
     llr = torch.zeros((S, N, fmt.m), dtype=torch.float32, device="cuda")
@@ -176,3 +177,10 @@ def test_chain_at_bench_launch_shape_tensor_cores(oracle_runs):
     """The whole chain at the bench's launch shape with the phase search on
     the tensor cores, under the same protocol as the SIMT chain."""
     _chain_check(oracle_runs, bps_tc=1)
+
+
+def test_chain_at_bench_launch_shape_frames_in_flight_grids(oracle_runs):
+    """The grids the bench's handles use with two frames in flight (18 SMs
+    left to the other frame: fewer, longer phase-search ranges per stream,
+    another split of the blocks' sigma^2 sums), under the same protocol."""
+    _chain_check(oracle_runs, bps_tc=0, sm_reserve=18)
