@@ -1013,7 +1013,23 @@ def run_mlp_infer(args):
     s2 = torch.full((n,), n0 / 2, dtype=torch.float32, device="cuda")
     m = rx_mod.Mlp(synth.mlp_init_params(LEARN["init_seed"]))
     llr = torch.empty((n, 6), dtype=torch.float32, device="cuda")
-    ms = _event_ms(lambda: m.infer(x, s2, llr), args.steps, args.warmup)
+    # both inference paths: 2 = tcgen05 (the default), 1 = mma.sync
+    path_ms = {}
+    for path in (1, 2):
+        m.set_param("infer", path)
+        path_ms[path] = _event_ms(lambda: m.infer(x, s2, llr), args.steps, args.warmup)
+    ms = path_ms[2]
+    # one Adam step on a batch of 8192 (the training configuration's batch),
+    # tcgen05 GEMMs against the float32 SIMT GEMMs
+    nb = 8192
+    bits = torch.from_numpy(rng.integers(0, 2, size=(nb, 6), dtype=np.uint8)).cuda()
+    xb, s2b = x[:nb].contiguous(), s2[:nb].contiguous()
+    train_ms = {}
+    for tc in (0, 1):
+        mt = rx_mod.Mlp(synth.mlp_init_params(LEARN["init_seed"]))
+        mt.set_param("train_tc", tc)
+        train_ms[tc] = _event_ms(lambda: mt.train_step(xb, s2b, bits, 1e-3), max(args.steps, 20), args.warmup)
+        mt.close()
     pk, pk_kind = peaks()
     flops = 2.0 * (4 * 128 + 128 * 128 + 128 * 6) * n
     tf = flops / (ms * 1e-3) / 1e12
@@ -1025,9 +1041,11 @@ def run_mlp_infer(args):
         "data": "synthetic",
         "config": {"workload": f"mlp_4x128x128x6_infer_{n}", "symbols": n, "esn0_db": 12.0,
                    "l2": "inputs 256 MiB, outputs 384 MiB > L2, no flush"},
-        "roofline": {"bound": "tensor", "kernel": "infer_tc_kernel", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
+        "roofline": {"bound": "tensor", "kernel": "infer_umma_kernel", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
                      "frac": tf / peak, "traffic": None, "peak_kind": pk_kind,
                      "note": "algorithmic flops; the kernel issues 3 products per layer-2 term (bfloat16 split)"},
+        "paths": {"tcgen05_gsym_s": n / (path_ms[2] * 1e-3) / 1e9, "mma_sync_gsym_s": n / (path_ms[1] * 1e-3) / 1e9},
+        "train_step_ms_batch_8192": {"tcgen05": train_ms[1], "float32_simt": train_ms[0]},
         "gpu_launches": args.steps,
     }
     print(json.dumps(line), flush=True)

@@ -387,6 +387,19 @@ int rx_mlp_train_step(rx_mlp *m, const float *x, const float *sigma2, const uint
                       size_t n, float lr, float *loss);
 /* LLRs of n samples. */
 int rx_mlp_infer(rx_mlp *m, const float *x, const float *sigma2, size_t n, float *llr);
+/* Kernel paths (results equal within the tolerances stated above):
+ *   "train_tc"  1 (default): the three 128-wide GEMMs of a training step on
+ *               the tcgen05 tensor cores, float32 operands split into three
+ *               bfloat16 terms (bfloat16 weights enter exactly), float32
+ *               accumulation; 0: float32 SIMT GEMMs.
+ *   "infer"     2 (default): fused inference with the 128 x 128 layer on the
+ *               tcgen05 tensor cores (accumulators in tensor memory); 1: the
+ *               same layer as mma.sync.
+ * The tensor-core kernels' waits are bounded: a wait that gave up is
+ * reported as RX_ETIMEDOUT by the next rx_mlp_get_params (or rx_get_stats of
+ * a handle using the MLP).  RX_EINVAL for another key or value. */
+int rx_mlp_set_param(rx_mlp *m, const char *key, double value);
+int rx_mlp_get_param(const rx_mlp *m, const char *key, double *value);
 
 /* The chain's demapper: m (not owned; must outlive its use) replaces the
  * exact log-sum-exp LLRs of rx_process with the MLP's (counting unchanged);

@@ -3,8 +3,10 @@
 // (Re z_X, Im z_X, Re z_Y, Im z_Y); output o = sigma^2 * LLR (LLR > 0 means
 // bit 0), trained with the mean binary cross-entropy over the bits and Adam.
 //
-// Kernels (batch of n samples; inference uses infer_tc_kernel, the tensor-core
-// forward pass below, training the float32 kernels):
+// Kernels (batch of n samples).  Inference: infer_umma_kernel (k_mlp_tc.cu,
+// tcgen05) or infer_tc_kernel below (mma.sync).  Training: the kernels below,
+// with the three 128-wide GEMMs either on the tcgen05 tensor cores
+// (gemm_tc_kernel, k_mlp_tc.cu) or the float32 gemm_kernel:
 //   layer1_kernel      a1 = x W1^T + b1, h1 = gelu(a1)
 //   gemm_kernel        tiled float32 GEMM (64 x 64 tiles, 4 x 4 per thread)
 //                      with bfloat16 weight operands and fused epilogues:
@@ -24,25 +26,12 @@
 
 #include <cuda_bf16.h>
 
+#include "mlp_dev.h"
 #include "rx_internal.h"
 
 namespace {
 
-constexpr int H = 128;
-constexpr int NOUT = 6;
-
-__device__ __forceinline__ float bf16_to_f(uint16_t b) { return __uint_as_float((unsigned)b << 16); }
-
-__device__ __forceinline__ uint16_t f_to_bf16(float f) {   // round to nearest, ties to even
-    const unsigned u = __float_as_uint(f);
-    return (uint16_t)((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
-}
-
-__device__ __forceinline__ float gelu(float a) { return 0.5f * a * (1.f + erff(a * 0.70710678118654752f)); }
-
-__device__ __forceinline__ float gelu_grad(float a) {
-    return 0.5f * (1.f + erff(a * 0.70710678118654752f)) + a * expf(-0.5f * a * a) * 0.39894228040143268f;
-}
+using namespace mlpd;
 
 __device__ __forceinline__ float softplus(float t) { return fmaxf(t, 0.f) + log1pf(expf(-fabsf(t))); }
 __device__ __forceinline__ float sigmoid(float t) { return 1.f / (1.f + expf(-t)); }
@@ -62,11 +51,7 @@ __global__ void layer1_kernel(const float *__restrict__ x, long n, const uint16_
 }
 
 // C[M][N] (+)= op(A) op(B): A float32 (row-major [M][K], or [K][M] when TA),
-// B bfloat16 or float32 ([N][K] when TB, else [K][N]).  Epilogues:
-//   EPI_BIAS_GELU: pre = C + bias[n] -> out0 = pre, out1 = gelu(pre)
-//   EPI_GELU_GRAD: out0 = C * gelu'(aux[m][n])
-//   EPI_STORE:     out0 = C
-enum { EPI_BIAS_GELU = 0, EPI_GELU_GRAD = 1, EPI_STORE = 2 };
+// B bfloat16 or float32 ([N][K] when TB, else [K][N]); epilogues EPI_*.
 constexpr int TM = 64, TN = 64, TK = 16;
 
 template <bool TA, bool TB, bool BBF, int EPI>
@@ -194,23 +179,6 @@ layer3_kernel(const float *__restrict__ h2, long n, const uint16_t *__restrict__
 // B-fragment loads of a warp hit 32 banks) and loop over 64-sample tiles.
 // ---------------------------------------------------------------------------
 constexpr int kW2P = H + 8;   // padded row of the staged W2 (bfloat16)
-
-// two float32 values rounded to bfloat16 (nearest, ties to even: the same
-// rounding as f_to_bf16) in one register, the first in the low half
-__device__ __forceinline__ unsigned cvt_bf16x2(float first, float second) {
-    const __nv_bfloat162 v = __floats2bfloat162_rn(first, second);
-    return *reinterpret_cast<const unsigned *>(&v);
-}
-__device__ __forceinline__ float bf16_lo(unsigned v) { return __uint_as_float(v << 16); }
-__device__ __forceinline__ float bf16_hi(unsigned v) { return __uint_as_float(v & 0xffff0000u); }
-
-// (hi, mid, lo) bfloat16 pairs of two float32 values
-__device__ __forceinline__ void split3_bf16x2(float a, float b, unsigned &hi, unsigned &mid, unsigned &lo) {
-    hi = cvt_bf16x2(a, b);
-    const float ra = a - bf16_lo(hi), rb = b - bf16_hi(hi);
-    mid = cvt_bf16x2(ra, rb);
-    lo = cvt_bf16x2(ra - bf16_lo(mid), rb - bf16_hi(mid));
-}
 
 __device__ __forceinline__ void mma_bf16(float (&c)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
     asm volatile(
@@ -391,6 +359,7 @@ constexpr int OFF_W1 = 0, OFF_B1 = OFF_W1 + H * 4, OFF_W2 = OFF_B1 + H, OFF_B2 =
 constexpr int OFF_W3 = OFF_B2 + H, OFF_B3 = OFF_W3 + NOUT * H, NPAR = OFF_B3 + NOUT;
 static_assert(NPAR == RX_MLP_PARAMS, "parameter count");
 constexpr long kRows = 256;          // batch rows per partial-sum block
+constexpr long kSliceTc = 256;       // batch rows per dW2 slice of the tensor-core GEMM
 }  // namespace
 
 static cudaError_t mlp_ensure(MlpDev &d, long n) {
@@ -407,8 +376,8 @@ static cudaError_t mlp_ensure(MlpDev &d, long n) {
     const long nb = (n + kRows - 1) / kRows;
     // column-sum partials: the widest is dW1 (H x 4) / biases (H) / dW3 (6 x H)
     if ((e = cudaMalloc(&d.part, sizeof(float) * (size_t)nb * H * 8)) != cudaSuccess) return e;
-    // dW2 over batch slices of kRows * 8 samples
-    const long ns = (n + kRows * 8 - 1) / (kRows * 8);
+    // dW2 over batch slices of kRows * 8 samples (float32 GEMM) or kSliceTc
+    const long ns = std::max((n + kRows * 8 - 1) / (kRows * 8), (n + kSliceTc - 1) / kSliceTc);
     if ((e = cudaMalloc(&d.wpart, sizeof(float) * (size_t)ns * H * H)) != cudaSuccess) return e;
     d.cap = n;
     return cudaSuccess;
@@ -457,9 +426,16 @@ static cudaError_t mlp_forward(MlpDev &d, const float *x, const float *s2, const
     cudaError_t e = mlp_ensure(d, n);
     if (e != cudaSuccess) return e;
     layer1_kernel<<<(unsigned)((n * H + 255) / 256), 256, 0, st>>>(x, n, d.W1q, d.theta + OFF_B1, d.a1, d.h1);
-    dim3 g2(H / TN, (unsigned)((n + TM - 1) / TM), 1);
-    gemm_kernel<false, true, true, EPI_BIAS_GELU><<<g2, 256, 0, st>>>(
-        (int)n, H, H, d.h1, H, d.W2q, H, d.theta + OFF_B2, nullptr, 0, d.a2, d.h2, H, H, 0);
+    if (d.train_tc) {
+        // a2[s][j] = sum_i h1[s][i] W2[j][i] + b2[j]
+        e = launch_gemm_tc(EPI_BIAS_GELU, true, (int)n, H, H, d.h1, H, 1, d.W2q, H, 1, d.theta + OFF_B2, nullptr,
+                           0, d.a2, d.h2, H, H, 0, 1, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        dim3 g2(H / TN, (unsigned)((n + TM - 1) / TM), 1);
+        gemm_kernel<false, true, true, EPI_BIAS_GELU><<<g2, 256, 0, st>>>(
+            (int)n, H, H, d.h1, H, d.W2q, H, d.theta + OFF_B2, nullptr, 0, d.a2, d.h2, H, H, 0);
+    }
     layer3_kernel<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(d.h2, n, d.W3q, d.theta + OFF_B3, s2, bits, d.dO,
                                                               d.loss_s, llr);
     return cudaGetLastError();
@@ -476,17 +452,31 @@ cudaError_t mlp_grad(MlpDev &d, const float *x, const float *s2, const uint8_t *
     if ((e = colsum(d, d.dO, NOUT, nullptr, 0, NOUT, 1, n, g + OFF_B3, st)) != cudaSuccess) return e;
     back3_kernel<<<(unsigned)((n * H + 255) / 256), 256, 0, st>>>(d.dO, n, d.W3q, d.a2, d.da2);
     // layer 2: dW2 = da2^T h1 (batch slices, then an ordered sum), db2
-    const long slice = kRows * 8;
+    const long slice = d.train_tc ? kSliceTc : kRows * 8;
     const long ns = (n + slice - 1) / slice;
-    dim3 gw(H / TN, H / TM, (unsigned)ns);
-    gemm_kernel<true, false, false, EPI_STORE><<<gw, 256, 0, st>>>(
-        H, H, (int)n, d.da2, H, d.h1, H, nullptr, nullptr, 0, d.wpart, nullptr, H, slice, (long)H * H);
+    if (d.train_tc) {
+        // dW2[j][i] = sum_s da2[s][j] h1[s][i]: both operands float32 (six term products)
+        e = launch_gemm_tc(EPI_STORE, false, H, H, n, d.da2, 1, H, d.h1, 1, H, nullptr, nullptr, 0, d.wpart,
+                           nullptr, H, slice, (long)H * H, (int)ns, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        dim3 gw(H / TN, H / TM, (unsigned)ns);
+        gemm_kernel<true, false, false, EPI_STORE><<<gw, 256, 0, st>>>(
+            H, H, (int)n, d.da2, H, d.h1, H, nullptr, nullptr, 0, d.wpart, nullptr, H, slice, (long)H * H);
+    }
     colsum_final_kernel<<<(H * H + 255) / 256, 256, 0, st>>>(d.wpart, (int)ns, H * H, g + OFF_W2);
     if ((e = colsum(d, d.da2, H, nullptr, 0, H, 1, n, g + OFF_B2, st)) != cudaSuccess) return e;
     // layer 1: da1 = (da2 W2) gelu'(a1); dW1 = da1^T x; db1
-    dim3 g1(H / TN, (unsigned)((n + TM - 1) / TM), 1);
-    gemm_kernel<false, false, true, EPI_GELU_GRAD><<<g1, 256, 0, st>>>(
-        (int)n, H, H, d.da2, H, d.W2q, H, nullptr, d.a1, H, d.da1, nullptr, H, H, 0);
+    if (d.train_tc) {
+        // dh1[s][i] = sum_j da2[s][j] W2[j][i]
+        e = launch_gemm_tc(EPI_GELU_GRAD, true, (int)n, H, H, d.da2, H, 1, d.W2q, 1, H, nullptr, d.a1, H, d.da1,
+                           nullptr, H, H, 0, 1, st);
+        if (e != cudaSuccess) return e;
+    } else {
+        dim3 g1(H / TN, (unsigned)((n + TM - 1) / TM), 1);
+        gemm_kernel<false, false, true, EPI_GELU_GRAD><<<g1, 256, 0, st>>>(
+            (int)n, H, H, d.da2, H, d.W2q, H, nullptr, d.a1, H, d.da1, nullptr, H, H, 0);
+    }
     if ((e = colsum(d, d.da1, H, x, 4, H, 4, n, g + OFF_W1, st)) != cudaSuccess) return e;
     if ((e = colsum(d, d.da1, H, nullptr, 0, H, 1, n, g + OFF_B1, st)) != cudaSuccess) return e;
     if (loss) {
@@ -504,6 +494,9 @@ cudaError_t mlp_adam(MlpDev &d, int t, float lr, cudaStream_t st) {
 
 cudaError_t mlp_infer(MlpDev &d, const float *x, const float *s2, long n, float *llr, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
+    if (d.infer == 2)
+        return launch_infer_umma(x, s2, n, d.W1q, d.theta + OFF_B1, d.W2q, d.theta + OFF_B2, d.W3q,
+                                 d.theta + OFF_B3, llr, st);
     const long tiles = (n + 63) / 64;
     const int grid = (int)std::min<long>(tiles, 4L * sm_count());
     infer_tc_kernel<<<grid, 128, 0, st>>>(x, s2, n, d.W1q, d.theta + OFF_B1, d.W2q, d.theta + OFF_B2, d.W3q,

@@ -874,6 +874,11 @@ int fill_stats(rx_handle *h, rx_stats *out) {
         CK(bps_tc_status(&gave_up));
         if (gave_up) return fail(RX_ETIMEDOUT, "a bounded wait of the tensor-core phase search gave up");
     }
+    if (h->mlp) {
+        unsigned int gave_up = 0;
+        CK(mlp_tc_status(&gave_up));
+        if (gave_up) return fail(RX_ETIMEDOUT, "a bounded wait of the MLP's tensor-core kernels gave up");
+    }
     // before the first block of a handle there are no device counters yet
     if (h->sd) CK(cudaMemcpy(sd.data(), h->sd, sizeof(StreamDev) * S, cudaMemcpyDeviceToHost));
     else std::memset(sd.data(), 0, sizeof(StreamDev) * S);
@@ -1383,6 +1388,9 @@ int rx_mlp_set_stream(rx_mlp *m, void *cuda_stream) {
 int rx_mlp_get_params(rx_mlp *m, float *params) {
     if (!m || !params) return fail(RX_EINVAL, "NULL argument");
     CK(cudaStreamSynchronize(m->st));
+    unsigned int gave_up = 0;
+    CK(mlp_tc_status(&gave_up));
+    if (gave_up) return fail(RX_ETIMEDOUT, "a bounded wait of the MLP's tensor-core kernels gave up");
     CK(cudaMemcpy(params, m->d.theta, sizeof(float) * RX_MLP_PARAMS, cudaMemcpyDeviceToHost));
     return RX_OK;
 }
@@ -1396,6 +1404,30 @@ int rx_mlp_set_params(rx_mlp *m, const float *params) {
     m->t = 0;
     CK(mlp_quantize(m->d, m->st));
     CK(cudaStreamSynchronize(m->st));
+    return RX_OK;
+}
+
+int rx_mlp_set_param(rx_mlp *m, const char *key, double value) {
+    if (!m || !key) return fail(RX_EINVAL, "NULL argument");
+    const std::string k(key);
+    if (k == "train_tc") {
+        if (value != 0.0 && value != 1.0) return fail(RX_EINVAL, "train_tc must be 0 or 1");
+        m->d.train_tc = (int)value;
+    } else if (k == "infer") {
+        if (value != 1.0 && value != 2.0) return fail(RX_EINVAL, "infer must be 1 or 2");
+        m->d.infer = (int)value;
+    } else {
+        return fail(RX_EINVAL, "unknown MLP parameter '%s'", key);
+    }
+    return RX_OK;
+}
+
+int rx_mlp_get_param(const rx_mlp *m, const char *key, double *value) {
+    if (!m || !key || !value) return fail(RX_EINVAL, "NULL argument");
+    const std::string k(key);
+    if (k == "train_tc") *value = m->d.train_tc;
+    else if (k == "infer") *value = m->d.infer;
+    else return fail(RX_EINVAL, "unknown MLP parameter '%s'", key);
     return RX_OK;
 }
 

@@ -284,6 +284,9 @@ struct MlpDev {
     float *a1 = nullptr, *h1 = nullptr, *a2 = nullptr, *h2 = nullptr, *dO = nullptr, *da2 = nullptr,
           *da1 = nullptr, *loss_s = nullptr, *part = nullptr, *wpart = nullptr;
     long part_cap = 0;
+    // kernel paths: training GEMMs (0: float32 SIMT, 1: tcgen05 with split
+    // bfloat16 operands), inference (1: mma.sync, 2: tcgen05)
+    int train_tc = 1, infer = 2;
 };
 
 
@@ -294,6 +297,17 @@ cudaError_t mlp_grad(MlpDev &d, const float *x, const float *s2, const uint8_t *
                      cudaStream_t st);
 cudaError_t mlp_adam(MlpDev &d, int t, float lr, cudaStream_t st);
 cudaError_t mlp_infer(MlpDev &d, const float *x, const float *s2, long n, float *llr, cudaStream_t st);
+// k_mlp_tc.cu: tcgen05 GEMM of the training steps (C = A B^T over K slices,
+// strided float32 A, float32 or bfloat16 B, epilogue epi of mlp_dev.h), the
+// fused tcgen05 inference, and the flag of their bounded waits
+cudaError_t launch_gemm_tc(int epi, bool b_bf16, int M, int N, long K, const float *A, long sam, long sak,
+                           const void *B, long sbn, long sbk, const float *bias, const float *aux, int ldaux,
+                           float *out0, float *out1, int ldo, long k_slice, long out_slice_stride, int n_slices,
+                           cudaStream_t st);
+cudaError_t launch_infer_umma(const float *x, const float *s2, long n, const uint16_t *W1q, const float *b1,
+                              const uint16_t *W2q, const float *b2, const uint16_t *W3q, const float *b3, float *llr,
+                              cudaStream_t st);
+cudaError_t mlp_tc_status(unsigned int *flag);
 
 cudaError_t launch_demap(const float2 *z, long z_stride, long z_off, long a, long e,
                          const double *sigma2, int sigma2_stride, float *llr,

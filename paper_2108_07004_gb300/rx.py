@@ -103,6 +103,8 @@ _PROTOS = {
     "rx_mlp_grad": (_I, [_VP, _VP, _VP, _VP, _SZ, _VP, _VP]),
     "rx_mlp_train_step": (_I, [_VP, _VP, _VP, _VP, _SZ, C.c_float, _VP]),
     "rx_mlp_infer": (_I, [_VP, _VP, _VP, _SZ, _VP]),
+    "rx_mlp_set_param": (_I, [_VP, C.c_char_p, _D]),
+    "rx_mlp_get_param": (_I, [_VP, C.c_char_p, C.POINTER(_D)]),
     "rx_format_info": (_I, [_VP, C.POINTER(_I), C.POINTER(_I), C.POINTER(_I)]),
     "rx_last_error": (C.c_char_p, []),
     "rx_cdc": (_I, [_VP, _VP, _VP, _SZ]),
@@ -574,6 +576,16 @@ class Mlp:
     def set_params(self, params: np.ndarray):
         buf = np.ascontiguousarray(params, dtype=np.float32)
         _ck(lib().rx_mlp_set_params(self.h, buf.ctypes.data))
+
+    def set_param(self, key: str, value: float):
+        """Kernel path: "train_tc" (1 tcgen05 GEMMs, 0 float32 SIMT) or
+        "infer" (2 tcgen05, 1 mma.sync)."""
+        _ck(lib().rx_mlp_set_param(self.h, key.encode(), float(value)))
+
+    def get_param(self, key: str) -> float:
+        v = C.c_double()
+        _ck(lib().rx_mlp_get_param(self.h, key.encode(), C.byref(v)))
+        return v.value
 
     def grad(self, x, sigma2, bits):
         g = torch.empty(MLP_PARAMS, dtype=torch.float32, device=x.device)

@@ -46,12 +46,18 @@ def _params(seed):
     return th
 
 
+@pytest.mark.parametrize("train_tc", [1, 0])
 @pytest.mark.parametrize("n", [777, 4096])
-def test_gradient_matches_oracle(n):
+def test_gradient_matches_oracle(n, train_tc):
+    """Both GEMM paths: tcgen05 with three-term bfloat16 operands (ragged
+    batch 777: a partial 128-row tile and a partial 256-sample dW2 slice)
+    and the float32 SIMT GEMMs."""
     rx = _rx()
     th = _params(3)
     x, s2, bits, _ = _awgn(n, 10.0, 4)
     m = rx.Mlp(th)
+    m.set_param("train_tc", train_tc)
+    assert m.get_param("train_tc") == train_tc
     g, loss = m.grad(_dev(x, np.float32), _dev(s2, np.float32), _dev(bits, np.uint8))
     torch.cuda.synchronize()
     w = mlp.compute_weights(th)
@@ -83,12 +89,17 @@ def test_adam_step_matches_oracle():
     assert np.all(step <= 1e-3 * (1 + 1e-6))
 
 
-def test_inference_matches_oracle():
+@pytest.mark.parametrize("path", [2, 1])
+@pytest.mark.parametrize("n", [5000, 200_003])
+def test_inference_matches_oracle(n, path):
+    """tcgen05 (2) and mma.sync (1) inference; 5000 samples end in a partial
+    128-sample tile, 200 003 give the persistent blocks several tiles each."""
     rx = _rx()
     th = _params(7)
-    x, s2, bits, _ = _awgn(5000, 12.0, 8)
+    x, s2, bits, _ = _awgn(n, 12.0, 8)
     s2 = s2 * np.linspace(0.5, 2.0, s2.size)                  # per-symbol sigma^2
     m = rx.Mlp(th)
+    m.set_param("infer", path)
     llr = m.infer(_dev(x, np.float32), _dev(s2, np.float32)).cpu().numpy().astype(np.float64)
     ref = mlp.llr(mlp.compute_weights(th), x.astype(np.float32).astype(np.float64),
                   s2.astype(np.float32).astype(np.float64))
