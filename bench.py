@@ -1134,7 +1134,7 @@ def run_precision(args):
 # ---- serving (config 5): 64 streams, Poisson arrivals, mixed formats and lengths ----
 SERVE = dict(n_req=64, len_log2=(14, 20), km=(80.0, 2000.0), budget=8 << 30, slots=64, load=0.8,
              esn0={"dp_qpsk": 12.0, "dp_16qam": 18.0, "gs4d64": 14.0},
-             bps={"dp_qpsk": 32, "dp_16qam": 32, "gs4d64": 64}, m={"dp_qpsk": 4, "dp_16qam": 8, "gs4d64": 6})
+             bps={"dp_qpsk": 32, "dp_16qam": 32, "gs4d64": 64}, m={"dp_qpsk": 4, "dp_16qam": 8, "gs4d64": 6}, issue=1)
 
 
 def serving_requests(seed: int):
@@ -1196,7 +1196,17 @@ def run_serving(args):
         ids_last.update(ids)
         return wall, lat, states, info
 
-    # capacity: every request present at once
+    # capacity (every request present at once) in each issue mode of the
+    # handles: 0 stages on their own streams with events, 1 one stream per
+    # request, 2 one stream and the blocks after the first as CUDA graphs
+    cap_by_issue = {}
+    for mode in (0, 1, 2):
+        srv.set_param("issue", mode)
+        for _ in range(max(1, args.warmup)):
+            serve(np.zeros(len(reqs)))
+        w_, _, _, _ = serve(np.zeros(len(reqs)))
+        cap_by_issue[str(mode)] = total_bits / w_ / 1e9
+    srv.set_param("issue", SERVE["issue"])
     for _ in range(max(1, args.warmup)):
         serve(np.zeros(len(reqs)))
     wall0, lat0, states0, info0 = serve(np.zeros(len(reqs)))
@@ -1222,6 +1232,7 @@ def run_serving(args):
                    "symbols": int(sum(n for _, n, _, _ in reqs)), "budget_bytes": SERVE["budget"],
                    "slots": SERVE["slots"], "load": SERVE["load"], "block": 1 << 16, "fft": 4096, "taps": 31},
         "capacity_gbps_all_at_once": cap_bits / 1e9,
+        "capacity_gbps_by_issue_mode": cap_by_issue, "issue_mode": SERVE["issue"],
         "request_latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "request_latency_ms_all_at_once": {"p50": 1e3 * lat0[len(lat0) // 2], "p99": 1e3 * lat0[-1]},
         "max_running": info["max_active"], "all_done": ok, "not_done": failed[:8],

@@ -154,7 +154,17 @@ void rx_destroy(rx_handle *h);                      /* NULL-safe */
  *   "sm_reserve" [0]: SMs the handle leaves to other work on the GPU (e.g.
  *   another handle's frame in flight) when it sizes the phase search and
  *   FIR grids to one wave; the phase search's range split, and with it the
- *   summation order of the block's sigma^2, follows the grid.
+ *   summation order of the block's sigma^2, follows the grid,
+ *   "issue" [0]: how rx_process / rx_process_blocks issue their work: 0
+ *   each stage group on its own stream (start-up and LMS chains, demap)
+ *   with events between them, so a handle alone overlaps its own stages; 1
+ *   every launch on the handle's stream, no event operations (for handles
+ *   that run beside many others, whose work fills the device: the host
+ *   issues about a third of the operations); 2 as 1, and a call that
+ *   continues a stream (b0 > 0) is captured as a CUDA graph and launched
+ *   as one, the handle's instantiated graph updated in place when only
+ *   kernel arguments changed.  Results are the same in every mode; the
+ *   host entry (rx_process_host) and the streaming entry always use 0.
  * Changing a parameter resets the stream state (rx_reset). */
 int rx_set_param(rx_handle *h, const char *key, double value);
 int rx_get_param(const rx_handle *h, const char *key, double *value);
@@ -446,7 +456,8 @@ typedef struct {
  * request's blocks always from one thread) one
  * block of every running request, so requests that arrived at different
  * times overlap on the device (the paper's multiple processing streams,
- * Sec. 2).  A finished request frees its slot and memory at the next step.
+ * Sec. 2); by default a request's launches all go on its own stream
+ * without event operations (issue mode 1, rx_server_set_param).  A finished request frees its slot and memory at the next step.
  * Results of a request equal those of a handle processing it alone.  Not
  * thread-safe; errors: rx_server_last_error(). */
 typedef struct rx_server rx_server;
@@ -465,6 +476,10 @@ int rx_server_step(rx_server *s, int *n_left);
 int rx_server_run(rx_server *s);
 /* State (RX_REQ_*) of a request and, once done, its statistics. */
 int rx_server_poll(rx_server *s, uint64_t id, int *state, rx_stats *stats);
+/* Server settings: "issue" [1], the issue mode of the requests' handles
+ * (rx_set_param "issue"); "issue_threads" [hardware threads, at most 8],
+ * the host threads that issue a step's blocks.  RX_EINVAL otherwise. */
+int rx_server_set_param(rx_server *s, const char *key, double value);
 /* Memory in use, the most requests ever running at once, steps taken. */
 int rx_server_info(rx_server *s, size_t *mem_used, int *max_active, long *steps);
 const char *rx_server_last_error(void);

@@ -134,6 +134,16 @@ struct rx_handle {
     bool cdc_side = false;
     cudaStream_t cst = nullptr;
     cudaEvent_t ev_cdcg = nullptr;
+    // issue mode of the device entry points (parameter "issue"): 0 the
+    // stages on their own streams with events between them; 1 every stage
+    // on the main stream, no event operations (handles that run beside many
+    // others: the other handles fill the device); 2 as 1, and the blocks of
+    // a call after the stream's first are captured as a CUDA graph and
+    // launched as one, the instantiated graph updated in place per block
+    int issue = 0;
+    cudaGraphExec_t gexec = nullptr;
+    cudaStream_t gst = nullptr;   // capture stream (the handle's own stream may be a default stream)
+    bool in_host = false;     // inside rx_process_host (multi-stream always)
     // reference bits left in host memory (rx_set_reference_host): copied in
     // with the next host-entry call, group by group, into ref_bits
     const uint8_t *ref_host = nullptr;
@@ -666,6 +676,12 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     if ((rc = upload_tables(h)) != RX_OK) return rc;
     if ((rc = ensure_buffers(h, N)) != RX_OK) return rc;
     if ((rc = ensure_streams(h)) != RX_OK) return rc;
+    // one-stream issue: every stage on the main stream, where stream order
+    // gives every dependency the events below would (skipped)
+    const bool one = h->issue != 0 && !win && !h->in_host;
+    auto rec = [one](cudaEvent_t e, cudaStream_t s) { return one ? cudaSuccess : cudaEventRecord(e, s); };
+    auto wt = [one](cudaStream_t s, cudaEvent_t e) { return one ? cudaSuccess : cudaStreamWaitEvent(s, e, 0); };
+    const cudaStream_t side = one ? st : h->side;
     const FmtDev &f = h->fmt;
     const int D = (T - 1) / 2;
 
@@ -685,8 +701,8 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         if (fs > f0) {
             STAGE(ST_CDC, st, 1, launch_cdc(in, h->x, ns, 2 * S, h->n_fft, h->n_ov, h->H, h->tw, st, f0, fs,
                                             h->prec));
-            CK(cudaEventRecord(h->ev_cdc0, st));
-            CK(cudaStreamWaitEvent(h->side, h->ev_cdc0, 0));
+            CK(rec(h->ev_cdc0, st));
+            CK(wt(side, h->ev_cdc0));
         }
         if (h->wait_rest) {
             CK(cudaStreamWaitEvent(st, h->ev_in_rest, 0));
@@ -706,7 +722,7 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         }
     }
     if (b0 == 0 && G == 0) {
-        const cudaStream_t ss = h->side;     // start-up stream
+        const cudaStream_t ss = side;        // start-up stream
         // the identity butterfly and the stream state are written by kernels:
         // a copy from pageable host memory would synchronise its stream first
         float2 *w0 = slot(h, 0);
@@ -725,8 +741,8 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         }
         // W_0 into the slots of U_{-lag} .. U_{-1}
         for (int i = 1; i <= L; ++i) CK(cudaMemcpyAsync(slot(h, -i), w0, tapsz, cudaMemcpyDeviceToDevice, ss));
-        CK(cudaEventRecord(h->ev_start, ss));
-        CK(cudaStreamWaitEvent(st, h->ev_start, 0));
+        CK(rec(h->ev_start, ss));
+        CK(wt(st, h->ev_start));
         h->u = 0;
         h->blocks_done = 0;
         h->started = true;
@@ -772,14 +788,14 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
     }
     cnt.sd = h->sd;
     cnt.partial = h->part_d;
-    const cudaStream_t ds = h->dst;
+    const cudaStream_t ds = one ? st : h->dst;
     // the demap stream starts after this call's set-up on the main stream
-    CK(cudaEventRecord(h->ev_setup, st));
-    CK(cudaStreamWaitEvent(ds, h->ev_setup, 0));
+    CK(rec(h->ev_setup, st));
+    CK(wt(ds, h->ev_setup));
     for (long n = b0; n < b1; ++n) {
         const long g = n + G;                 // global block number
         const long k0 = n * Nb, k1 = std::min(k0 + Nb, N);
-        if (L >= 2 && g >= L) CK(cudaStreamWaitEvent(st, h->ev_lms[(g - L) % R], 0));
+        if (L >= 2 && g >= L) CK(wt(st, h->ev_lms[(g - L) % R]));
         // W_g = U_{g-lag}; for g < lag the slot read has not been written since start-up (W_0)
         const float2 *wn = slot(h, g - L);
         cudaEvent_t blk0 = nullptr;
@@ -795,15 +811,15 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         // the partial sums of this parity were read by the demap of block n - 2
         // (possibly of an earlier call: the demap stream is not joined between
         // the host entry's groups)
-        if (g >= 2) CK(cudaStreamWaitEvent(st, h->ev_dm[par], 0));
+        if (g >= 2) CK(wt(st, h->ev_dm[par]));
         if (tc)
             STAGE(ST_BPS, st, 1, launch_bps_tc(h->y, N, a, e, k1, h->W, h->bidx, N, a, dsum_n, mdsum_n, chunks, S,
                                                h->bps_w, f, st, h->prec));
         else
             STAGE(ST_BPS, st, 1, launch_bps(h->y, N, a, e, k1, h->W, h->bidx, N, a, dsum_n, mdsum_n, chunks, S,
                                             f, st, h->prec));
-        CK(cudaEventRecord(h->ev_bps[par], st));
-        CK(cudaStreamWaitEvent(ds, h->ev_bps[par], 0));
+        CK(rec(h->ev_bps[par], st));
+        CK(wt(ds, h->ev_bps[par]));
         const int cin = (int)(g & 1), cout = 1 - cin;
         if (g == 0 && h->trained) {
             // the training phases fix the start quadrant of the unwrap
@@ -828,21 +844,21 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
             STAGE(ST_DEMAP, ds, 1,
                   launch_count_llr(llr + (size_t)a * m, N * m, sym.x4, N, a, e, h->sig, 1, cnt, S, f, ds));
         }
-        CK(cudaEventRecord(h->ev_dm[par], ds));
+        CK(rec(h->ev_dm[par], ds));
         if (blk0) {
             cudaEvent_t blk1 = prof_event(h);
             if (blk1) { CK(cudaEventRecord(blk1, ds)); h->blk.push_back({blk0, blk1}); }
         }
         const long span = std::max(0L, std::min((long)h->n_upd, N - k0));
         // the LMS of block n reads the phase codes its demap wrote
-        CK(cudaEventRecord(h->ev_unwrap, ds));
+        CK(rec(h->ev_unwrap, ds));
         cudaStream_t ls = st;
-        if (L >= 2) {
+        if (L >= 2 && !one) {
             const int r = (int)(g % chains);
-            ls = r == 0 ? h->side : h->side_x[r - 1];
-            CK(cudaStreamWaitEvent(ls, h->ev_unwrap, 0));
+            ls = r == 0 ? side : h->side_x[r - 1];
+            CK(wt(ls, h->ev_unwrap));
         } else {
-            CK(cudaStreamWaitEvent(st, h->ev_unwrap, 0));
+            CK(wt(st, h->ev_unwrap));
         }
         // the update starts from U_{n-1} (one chain) or from W_n = U_{n-lag}
         const float2 *u_in = slot(h, chains > 1 ? g - L : g - 1);
@@ -854,14 +870,14 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
             STAGE(ST_LMS, ls, span > 0 ? 1 : 0,
                   launch_lms(h->x, ns, u_in, slot(h, g), k0, (int)span, h->pcode, N, 2, 1,
                              h->u, (int)h->n_cma, (float)h->mu, nullptr, 0, S, T, f, ls, h->prec, lms_opts(h)));
-        if (L >= 2) CK(cudaEventRecord(h->ev_lms[g % R], ls));
+        if (L >= 2) CK(rec(h->ev_lms[g % R], ls));
         h->u += span;
         h->blocks_done = g + 1;
     }
     // the caller's stream sees the demaps (LLRs, counters, carries) done
-    if (join && b1 > b0) CK(cudaStreamWaitEvent(st, h->ev_dm[(int)((b1 - 1 + G) & 1)], 0));
+    if (join && b1 > b0) CK(wt(st, h->ev_dm[(int)((b1 - 1 + G) & 1)]));
     if (join && L >= 2)
-        for (long n = std::max(b0, b1 - chains); n < b1; ++n) CK(cudaStreamWaitEvent(st, h->ev_lms[(n + G) % R], 0));
+        for (long n = std::max(b0, b1 - chains); n < b1; ++n) CK(wt(st, h->ev_lms[(n + G) % R]));
     return RX_OK;
 }
 
@@ -1161,6 +1177,11 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     else if (k == "bps_tc") { rc = as_int(0, 1, t); h->bps_tc = (int)t; }
     else if (k == "lms_exact") { rc = as_int(0, 1, t); h->lms_exact = (int)t; }
     else if (k == "sm_reserve") { rc = as_int(0, 1024, t); h->sm_reserve = (int)t; }
+    else if (k == "issue") {
+        rc = as_int(0, 2, t);
+        h->issue = (int)t;
+        if (h->gexec) { cudaGraphExecDestroy(h->gexec); h->gexec = nullptr; }
+    }
     else return fail(RX_EINVAL, "unknown parameter '%s'", k.c_str());
     if (rc != RX_OK) return rc;
     if (k == "overlap") h->tables_dirty = true;
@@ -1262,6 +1283,8 @@ rx_handle *rx_create(const rx_format *format, double symbol_rate, int sps, doubl
 void rx_destroy(rx_handle *h) {
     if (!h) return;
     if (h->st) cudaStreamSynchronize(h->st);
+    if (h->gexec) cudaGraphExecDestroy(h->gexec);
+    if (h->gst) cudaStreamDestroy(h->gst);
     if (h->side) { cudaStreamSynchronize(h->side); cudaStreamDestroy(h->side); }
     for (auto &x : h->side_x)
         if (x) { cudaStreamSynchronize(x); cudaStreamDestroy(x); }
@@ -1335,6 +1358,7 @@ int rx_get_param(const rx_handle *h, const char *key, double *value) {
     else if (k == "bps_tc") *value = use_bps_tc(h) ? 1.0 : 0.0;
     else if (k == "lms_exact") *value = h->lms_exact;
     else if (k == "sm_reserve") *value = h->sm_reserve;
+    else if (k == "issue") *value = h->issue;
     else if (k == "cd_ps_per_nm") *value = h->cd;
     else if (k == "profile") *value = h->profile;
     else if (k == "precision") *value = h->prec;
@@ -1732,7 +1756,9 @@ int rx_process_host(rx_handle *h, const void *samples, size_t n_samples, float *
         // CDC waits for theirs on its own stream (run_blocks)
         if (g0 == 0) CK(cudaStreamWaitEvent(h->st, h->ev_in, 0));
         h->cdc_side = g0 > 0;
+        h->in_host = true;
         rc = run_blocks(h, h->d_in, N, g0, g1, h->d_out, g0 == 0, g1 == nblk);
+        h->in_host = false;
         h->cdc_side = false;
         h->wait_rest = false;
         if (rc != RX_OK) return rc;
@@ -1808,8 +1834,41 @@ int rx_process_blocks(rx_handle *h, const void *samples, size_t n_samples, size_
     if (b0 > 0 && !(h->started && h->cur_n == N && h->blocks_done == (long)b0))
         return fail(RX_ESTATE, "block %zu does not continue the handle's stream (at block %ld of a %ld-symbol "
                     "stream%s)", b0, h->blocks_done, h->cur_n, h->started ? "" : ", not started");
-    int rc = run_blocks(h, (const float2 *)samples, N, (long)b0, (long)b1, llr_out);
-    if (rc != RX_OK) return rc;
+    int rc;
+    if (h->issue == 2 && b0 > 0 && !h->profile && !h->ref_host) {
+        // the blocks as one CUDA graph: captured on a private stream (a
+        // default stream cannot be captured), the instantiated graph of the
+        // previous call updated in place (same topology: new kernel
+        // arguments only) or instantiated anew, launched on the handle's stream
+        if (!h->gst) CK(cudaStreamCreateWithFlags(&h->gst, cudaStreamNonBlocking));
+        cudaGraph_t gr = nullptr;
+        const cudaStream_t user = h->st;
+        CK(cudaStreamBeginCapture(h->gst, cudaStreamCaptureModeThreadLocal));
+        h->st = h->gst;
+        rc = run_blocks(h, (const float2 *)samples, N, (long)b0, (long)b1, llr_out);
+        h->st = user;
+        const cudaError_t ce = cudaStreamEndCapture(h->gst, &gr);
+        if (rc != RX_OK) {
+            if (gr) cudaGraphDestroy(gr);
+            return rc;
+        }
+        CK(ce);
+        if (h->gexec) {
+            cudaGraphExecUpdateResultInfo info;
+            if (cudaGraphExecUpdate(h->gexec, gr, &info) != cudaSuccess) {
+                cudaGetLastError();
+                cudaGraphExecDestroy(h->gexec);
+                h->gexec = nullptr;
+            }
+        }
+        const cudaError_t ie = h->gexec ? cudaSuccess : cudaGraphInstantiate(&h->gexec, gr, 0);
+        cudaGraphDestroy(gr);
+        CK(ie);
+        CK(cudaGraphLaunch(h->gexec, h->st));
+    } else {
+        rc = run_blocks(h, (const float2 *)samples, N, (long)b0, (long)b1, llr_out);
+        if (rc != RX_OK) return rc;
+    }
     CK(cudaGetLastError());
     if (stats) return fill_stats(h, stats);
     return RX_OK;

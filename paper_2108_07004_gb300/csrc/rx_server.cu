@@ -13,6 +13,11 @@
 // handle processing the stream alone (the library's kernels are
 // deterministic), so its results do not depend on the mix.
 //
+// A request's handle issues in one-stream mode by default (rx_set_param
+// "issue" 1: every launch on the request's stream, no event operations): the
+// other requests fill the device, and the host issues about a third of the
+// operations of the multi-stream mode.
+//
 // Host code only; everything on the device goes through the public entry
 // points (rx_create, rx_process_blocks, rx_get_stats, ...).
 #include <algorithm>
@@ -104,6 +109,7 @@ struct rx_server {
     size_t issue_threads = 1;           // host threads that issue a step's blocks
     size_t pooled = 0;                  // their memory estimates
     int max_active_seen = 0;
+    int issue = 1;                      // the handles' issue mode (rx_set_param "issue")
 };
 
 namespace {
@@ -213,6 +219,9 @@ bool admit(rx_server *s, Req *q) {
         if (rc == RX_OK && cudaEventCreateWithFlags(&q->done, cudaEventDisableTiming) != cudaSuccess) rc = RX_ECUDA;
     }
     if (rc == RX_OK) rc = rx_set_stream(q->h, q->st);
+    double issue = -1;
+    if (rc == RX_OK) rc = rx_get_param(q->h, "issue", &issue);
+    if (rc == RX_OK && issue != s->issue) rc = rx_set_param(q->h, "issue", s->issue);
     // a request without reference bits clears what a reused handle still
     // holds from its previous request (no training stage, no counting)
     if (rc == RX_OK) rc = q->r.ref_bits ? rx_set_reference(q->h, q->r.ref_bits, q->N)
@@ -382,6 +391,22 @@ int rx_server_poll(rx_server *s, uint64_t id, int *state, rx_stats *stats) {
     *state = q->state;
     if (stats && q->state == Q_DONE) *stats = q->stats;
     if (q->state == Q_FAILED) g_srv_err = q->err;
+    return RX_OK;
+}
+
+int rx_server_set_param(rx_server *s, const char *key, double value) {
+    if (!s || !key) return srv_fail(RX_EINVAL, "NULL argument");
+    const std::string k(key);
+    if (k == "issue") {
+        if (value != 0 && value != 1 && value != 2) return srv_fail(RX_EINVAL, "issue must be 0, 1 or 2");
+        s->issue = (int)value;
+    } else if (k == "issue_threads") {
+        if (!(value >= 1 && value <= 64) || value != (double)(long)value)
+            return srv_fail(RX_EINVAL, "issue_threads must be 1 .. 64");
+        s->issue_threads = (size_t)value;
+    } else {
+        return srv_fail(RX_EINVAL, "unknown server parameter '" + k + "'");
+    }
     return RX_OK;
 }
 

@@ -36,9 +36,11 @@ def _submit(srv, i, samples, bits):
     return rid, llr
 
 
-def _serve(idx, streams, budget=1 << 33, slots=16):
+def _serve(idx, streams, budget=1 << 33, slots=16, issue=None):
     from paper_2108_07004_gb300 import rx
     srv = rx.Server(budget, slots)
+    if issue is not None:
+        srv.set_param("issue", issue)
     got = {i: _submit(srv, i, *streams[i]) for i in idx}
     srv.run()
     torch.cuda.synchronize()
@@ -61,6 +63,45 @@ def test_each_result_is_the_same_alone_and_in_the_mix(streams):
         assert not np.isnan(mix[i][0]).any()
         for k in ("bit_errors", "n_sym", "gmi_sum"):
             assert alone[i][1][k] == mix[i][1][k], (i, k)
+
+
+@pytest.mark.parametrize("issue", [0, 1, 2])
+def test_issue_modes_give_the_results_of_the_multi_stream_handle(streams, issue):
+    """The handles' issue modes (0: stages on their own streams with events;
+    1: every launch on the request's stream; 2: blocks after the first as
+    CUDA graphs updated in place) serve every request of the mix with the
+    LLRs and counts of the request alone in mode 0."""
+    alone = {i: _serve([i], streams, issue=0)[0][i] for i in range(len(REQS))}
+    mix, info = _serve(range(len(REQS)), streams, issue=issue)
+    assert info["max_active"] == len(REQS)
+    for i in range(len(REQS)):
+        assert np.array_equal(alone[i][0], mix[i][0]), (issue, i)
+        for k in ("bit_errors", "n_sym", "gmi_sum"):
+            assert alone[i][1][k] == mix[i][1][k], (issue, i, k)
+
+
+def test_graph_issue_block_by_block_equals_one_call(streams):
+    """A handle in issue mode 2 fed block by block (the first call direct,
+    the others as one instantiated graph updated per block) gives the LLRs
+    and counts of one rx_process call in mode 0."""
+    from paper_2108_07004_gb300 import rx
+    i = 3
+    fmt, n, km, esn0, T, B = REQS[i]
+    samples, bits = streams[i]
+    kw = dict(cd_ps_per_nm=17.0 * km, taps=T, bps_phases=B, fft=4096, overlap=1024, block=8192, n_pre=2048)
+    r0 = rx.Receiver(fmt, **kw)
+    r0.set_reference(bits[None].contiguous())
+    ref, st0 = r0.process(samples[None].contiguous())
+    r2 = rx.Receiver(fmt, **kw)
+    r2.set("issue", 2)
+    r2.set_reference(bits[None].contiguous())
+    nblk = (n + 8191) // 8192
+    llr = torch.full_like(ref, float("nan"))
+    for b in range(nblk):
+        _, st2 = r2.process_blocks(samples[None].contiguous(), b, b + 1, llr, stats=b == nblk - 1)
+    torch.cuda.synchronize()
+    assert np.array_equal(llr.cpu().numpy(), ref.cpu().numpy())
+    assert st2[0]["bit_errors"] == st0[0]["bit_errors"] and st2[0]["gmi_sum"] == st0[0]["gmi_sum"]
 
 
 def test_served_request_equals_a_handle(streams):
