@@ -492,10 +492,23 @@ cudaError_t mlp_adam(MlpDev &d, int t, float lr, cudaStream_t st) {
     return mlp_quantize(d, st);
 }
 
+cudaError_t mlp_infer_seg(MlpDev &d, const float *x, const float *s2, long n, int n_seg, long x_stride,
+                          float *llr, long llr_stride, cudaStream_t st) {
+    if (d.infer == 2)
+        return launch_infer_umma(x, s2, n, n_seg, x_stride, llr_stride, d.W1q, d.theta + OFF_B1, d.W2q,
+                                 d.theta + OFF_B2, d.W3q, d.theta + OFF_B3, llr, st);
+    for (int g = 0; g < n_seg; ++g) {
+        const cudaError_t e = mlp_infer(d, x + (size_t)g * x_stride * 4, s2 + (size_t)g * x_stride, n,
+                                        llr + (size_t)g * llr_stride * NOUT, st);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t mlp_infer(MlpDev &d, const float *x, const float *s2, long n, float *llr, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     if (d.infer == 2)
-        return launch_infer_umma(x, s2, n, d.W1q, d.theta + OFF_B1, d.W2q, d.theta + OFF_B2, d.W3q,
+        return launch_infer_umma(x, s2, n, 1, n, n, d.W1q, d.theta + OFF_B1, d.W2q, d.theta + OFF_B2, d.W3q,
                                  d.theta + OFF_B3, llr, st);
     const long tiles = (n + 63) / 64;
     const int grid = (int)std::min<long>(tiles, 4L * sm_count());

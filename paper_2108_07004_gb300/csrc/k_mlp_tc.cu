@@ -54,31 +54,84 @@ __device__ __forceinline__ void put_row(unsigned char *tile, int row, const unsi
 }
 
 // ---------------------------------------------------------------------------
+// GELU of a pair of values for the inference kernel: a Phi(a) with the
+// normal distribution function from erfc by Abramowitz and Stegun's rational
+// approximation 7.1.26 (Handbook of Mathematical Functions, after Hastings;
+// |error| <= 1.5e-7 on erf):
+//   erfc(z) ~ t (a1 + t (a2 + t (a3 + t (a4 + t a5)))) e^{-z^2},
+//   t = 1 / (1 + p z),  z = |a| / sqrt(2) >= 0,
+//   Phi(a) = 1/2 + copysign(1/2 - erfc(z) / 2, a),
+// with e^{-a^2/2} = 2^{-a^2 log2(e) / 2}.  The reciprocal and the power of
+// two are one hardware instruction each; the rest runs on packed f32x2
+// pairs.  (The training kernels keep the exact-erf GELU of mlp_dev.h; the
+// two agree to a few 1e-7 of |a|.)
+// ---------------------------------------------------------------------------
+constexpr float kAsP = 0.3275911f * 0.70710678118654752f;     // p / sqrt(2): t from |a|
+// a1 .. a5 halved (the erfc / 2 of Phi)
+constexpr float kAs1 = 0.5f * 0.254829592f, kAs2 = 0.5f * -0.284496736f, kAs3 = 0.5f * 1.421413741f,
+                kAs4 = 0.5f * -1.453152027f, kAs5 = 0.5f * 1.061405429f;
+constexpr float kNegHalfLog2e = -0.72134752044448170f;          // -log2(e) / 2
+
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float r;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ f32x2 gelu2(f32x2 a2) {
+    float a0, a1;
+    upk2(a2, a0, a1);
+    const f32x2 t = pk2(rcp_approx(fmaf(fabsf(a0), kAsP, 1.f)), rcp_approx(fmaf(fabsf(a1), kAsP, 1.f)));
+    f32x2 P = fma2(t, pk2(kAs5, kAs5), pk2(kAs4, kAs4));
+    P = fma2(t, P, pk2(kAs3, kAs3));
+    P = fma2(t, P, pk2(kAs2, kAs2));
+    P = fma2(t, P, pk2(kAs1, kAs1));
+    P = mul2(t, P);                                         // erfc(z) / 2 without e^{-z^2}
+    const f32x2 u = mul2(mul2(a2, a2), pk2(kNegHalfLog2e, kNegHalfLog2e));
+    float u0, u1;
+    upk2(u, u0, u1);
+    const f32x2 q = mul2(P, pk2(ex2_approx(u0), ex2_approx(u1)));   // erfc(z) / 2
+    float q0, q1;
+    upk2(sub2(pk2(0.5f, 0.5f), q), q0, q1);
+    const f32x2 phi = add2(pk2(copysignf(q0, a0), copysignf(q1, a1)), pk2(0.5f, 0.5f));
+    return mul2(a2, phi);
+}
+
+// ---------------------------------------------------------------------------
 // Inference: x [n][4] -> LLR [n][6].  A block loops over tiles of 128
 // samples (thread = sample = accumulator row).  Per K-step the threads make
-// 16 columns of layer 1 (bias, GELU) and write their three bfloat16 terms;
-// one thread issues the three MMAs against the K-step's tile of W2 (staged
-// once per block) while the threads make the next K-step's columns.  After
-// the eighth K-step each thread reads its row of layer 2 from TMEM, adds the
-// bias, applies GELU and forms layer 3 and the LLRs.
+// 16 columns of layer 1 (bias, GELU; pairs of columns as packed f32x2) and
+// write their three bfloat16 terms; one thread issues the three MMAs against
+// the K-step's tile of W2 (staged once per block) while the threads make the
+// next K-step's columns.  After the eighth K-step each thread reads its row
+// of layer 2 from TMEM, adds the bias, applies GELU and forms layer 3 (each
+// output as a packed pair of even- and odd-column partial sums) and the LLRs.
 // ---------------------------------------------------------------------------
 struct InferSmem {
     unsigned char w2[kKsteps][kTileB];     // B operand: W2 [n][k], one tile per K-step
     unsigned char a[3][kTileB];            // A operand of the current K-step: hi, mid, lo
-    float4 w1[H];                          // W1 rows (bfloat16 values)
-    float b1[H], b2[H];
-    float4 w3[H][2];                       // W3 column j: outputs 0..5, padded to 8
+    f32x2 w1p[H / 2][4];                   // (W1[2i][c], W1[2i+1][c]) (bfloat16 values)
+    f32x2 b1p[H / 2], b2p[H / 2];          // bias pairs
+    f32x2 w3p[H / 2][NOUT];                // (W3[k][2i], W3[k][2i+1])
     float b3[8];
     unsigned long long bar;
     uint32_t tmem_slot;
     int fail;
 };
 
+// Segments: n_seg runs of n samples each, segment g's samples at rows
+// g x_stride .. of x (and sigma2) and its LLRs at rows g llr_stride .. (the
+// chain's streams of one block); tiles never straddle two segments.
 __global__ void __launch_bounds__(kThr, 4)
-infer_umma_kernel(const float *__restrict__ x, const float *__restrict__ sigma2, long n,
-                  const uint16_t *__restrict__ W1q, const float *__restrict__ b1, const uint16_t *__restrict__ W2q,
-                  const float *__restrict__ b2, const uint16_t *__restrict__ W3q, const float *__restrict__ b3,
-                  float *__restrict__ llr) {
+infer_umma_kernel(const float *__restrict__ x, const float *__restrict__ sigma2, long n, int n_seg, long x_stride,
+                  long llr_stride, const uint16_t *__restrict__ W1q, const float *__restrict__ b1,
+                  const uint16_t *__restrict__ W2q, const float *__restrict__ b2, const uint16_t *__restrict__ W3q,
+                  const float *__restrict__ b3, float *__restrict__ llr) {
     extern __shared__ __align__(128) unsigned char sm_raw[];
     InferSmem &sm = *reinterpret_cast<InferSmem *>(sm_raw);
     const int tid = threadIdx.x, warp = tid >> 5;
@@ -88,16 +141,14 @@ infer_umma_kernel(const float *__restrict__ x, const float *__restrict__ sigma2,
         const uint4 v = reinterpret_cast<const uint4 *>(W2q)[i];
         *reinterpret_cast<uint4 *>(sm.w2[k / kKstep] + tc::kstep_off_bf16(row, k % kKstep)) = v;
     }
-    for (int j = tid; j < H; j += kThr) {
-        sm.w1[j] = make_float4(bf16_to_f(W1q[4 * j]), bf16_to_f(W1q[4 * j + 1]), bf16_to_f(W1q[4 * j + 2]),
-                               bf16_to_f(W1q[4 * j + 3]));
-        sm.b1[j] = b1[j];
-        sm.b2[j] = b2[j];
-        float w[8];
+    for (int i = tid; i < H / 2; i += kThr) {
+        const int j = 2 * i;
 #pragma unroll
-        for (int k = 0; k < 8; ++k) w[k] = k < NOUT ? bf16_to_f(W3q[k * H + j]) : 0.f;
-        sm.w3[j][0] = make_float4(w[0], w[1], w[2], w[3]);
-        sm.w3[j][1] = make_float4(w[4], w[5], w[6], w[7]);
+        for (int c = 0; c < 4; ++c) sm.w1p[i][c] = pk2(bf16_to_f(W1q[4 * j + c]), bf16_to_f(W1q[4 * j + 4 + c]));
+        sm.b1p[i] = pk2(b1[j], b1[j + 1]);
+        sm.b2p[i] = pk2(b2[j], b2[j + 1]);
+#pragma unroll
+        for (int k = 0; k < NOUT; ++k) sm.w3p[i][k] = pk2(bf16_to_f(W3q[k * H + j]), bf16_to_f(W3q[k * H + j + 1]));
     }
     if (tid < 8) sm.b3[tid] = tid < NOUT ? b3[tid] : 0.f;
     if (warp == 0) tc::tmem_alloc(&sm.tmem_slot, 128);
@@ -114,27 +165,30 @@ infer_umma_kernel(const float *__restrict__ x, const float *__restrict__ sigma2,
     const uint32_t t_row = tmem + ((uint32_t)(32 * warp) << 16);   // this warp's 32 lanes
     uint32_t issued = 0;                                          // K-steps committed
     bool stop = false;
-    const long n_tiles = (n + 127) / 128;
+    const long tps = (n + 127) / 128, n_tiles = tps * n_seg;
     for (long tile = blockIdx.x; tile < n_tiles && !stop; tile += gridDim.x) {
-        const long r = tile * 128 + tid;
-        float xv[4] = {0.f, 0.f, 0.f, 0.f};
-        if (r < n) {
+        const long seg = tile / tps;
+        const long rl = (tile - seg * tps) * 128 + tid;           // sample within the segment
+        const bool ok = rl < n;
+        const long rx = seg * x_stride + rl, ro = seg * llr_stride + rl;
+        f32x2 X[4];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) xv[c] = x[r * 4 + c];
+        for (int c = 0; c < 4; ++c) {
+            const float v = ok ? x[rx * 4 + c] : 0.f;
+            X[c] = pk2(v, v);
         }
 #pragma unroll 1
         for (int kk = 0; kk < kKsteps; ++kk) {
             unsigned th[8], tm[8], tl[8];
 #pragma unroll
             for (int p = 0; p < 8; ++p) {
-                const int j = kk * kKstep + 2 * p;
-                const float4 wa = sm.w1[j], wb = sm.w1[j + 1];
-                float a0 = sm.b1[j], a1 = sm.b1[j + 1];
-                a0 = fmaf(xv[0], wa.x, a0); a0 = fmaf(xv[1], wa.y, a0);
-                a0 = fmaf(xv[2], wa.z, a0); a0 = fmaf(xv[3], wa.w, a0);
-                a1 = fmaf(xv[0], wb.x, a1); a1 = fmaf(xv[1], wb.y, a1);
-                a1 = fmaf(xv[2], wb.z, a1); a1 = fmaf(xv[3], wb.w, a1);
-                split3_bf16x2(gelu(a0), gelu(a1), th[p], tm[p], tl[p]);
+                const int i = kk * (kKstep / 2) + p;            // column pair 2i, 2i + 1
+                f32x2 A = sm.b1p[i];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) A = fma2(X[c], sm.w1p[i][c], A);
+                float g0, g1;
+                upk2(gelu2(A), g0, g1);
+                split3_bf16x2(g0, g1, th[p], tm[p], tl[p]);
             }
             // the A tiles are free once the previous K-step's MMAs are done
             if (issued > 0 && !tc::mbar_wait(bar, (issued - 1) & 1)) sm.fail = 1;
@@ -160,28 +214,30 @@ infer_umma_kernel(const float *__restrict__ x, const float *__restrict__ sigma2,
         // layer 2 of this tile is in TMEM
         if (!tc::mbar_wait(bar, (issued - 1) & 1)) sm.fail = 1;
         tc::fence_after();
-        float o[8];
+        f32x2 o[NOUT];
 #pragma unroll
-        for (int k = 0; k < 8; ++k) o[k] = 0.f;
+        for (int k = 0; k < NOUT; ++k) o[k] = pk2(0.f, 0.f);
 #pragma unroll 1
         for (int q = 0; q < H / 32; ++q) {
             float v[32];
             tc::tmem_ld32(t_row + (uint32_t)(32 * q), v);
 #pragma unroll
-            for (int i = 0; i < 32; ++i) {
-                const int j = 32 * q + i;
-                const float h = gelu(v[i] + sm.b2[j]);
-                const float4 wa = sm.w3[j][0], wb = sm.w3[j][1];
-                o[0] = fmaf(h, wa.x, o[0]); o[1] = fmaf(h, wa.y, o[1]);
-                o[2] = fmaf(h, wa.z, o[2]); o[3] = fmaf(h, wa.w, o[3]);
-                o[4] = fmaf(h, wb.x, o[4]); o[5] = fmaf(h, wb.y, o[5]);
+            for (int p = 0; p < 16; ++p) {
+                const int i = 16 * q + p;                        // column pair 2i, 2i + 1
+                const f32x2 h = gelu2(add2(pk2(v[2 * p], v[2 * p + 1]), sm.b2p[i]));
+#pragma unroll
+                for (int k = 0; k < NOUT; ++k) o[k] = fma2(h, sm.w3p[i][k], o[k]);
             }
         }
         tc::fence_before();     // the TMEM reads come before the next tile's first MMA
-        if (r < n) {
-            const float inv = 1.f / sigma2[r];
+        if (ok) {
+            const float inv = 1.f / sigma2[rx];
 #pragma unroll
-            for (int k = 0; k < NOUT; ++k) llr[r * NOUT + k] = (o[k] + sm.b3[k]) * inv;
+            for (int k = 0; k < NOUT; ++k) {
+                float e0, e1;
+                upk2(o[k], e0, e1);
+                llr[ro * NOUT + k] = ((e0 + e1) + sm.b3[k]) * inv;
+            }
         }
     }
     // a block that stopped early may still have MMAs in flight: wait for them
@@ -433,20 +489,22 @@ cudaError_t launch_gemm_tc(int epi, bool b_bf16, int M, int N, long K, const flo
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_infer_umma(const float *x, const float *s2, long n, const uint16_t *W1q, const float *b1,
-                              const uint16_t *W2q, const float *b2, const uint16_t *W3q, const float *b3, float *llr,
-                              cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
+cudaError_t launch_infer_umma(const float *x, const float *s2, long n, int n_seg, long x_stride, long llr_stride,
+                              const uint16_t *W1q, const float *b1, const uint16_t *W2q, const float *b2,
+                              const uint16_t *W3q, const float *b3, float *llr, cudaStream_t st) {
+    if (n <= 0 || n_seg <= 0) return cudaSuccess;
+    if (n_seg > 1 && (x_stride < n || llr_stride < n)) return cudaErrorInvalidValue;
     if ((reinterpret_cast<uintptr_t>(W2q) & 15) != 0) return cudaErrorInvalidValue;
     static std::atomic<unsigned long long> set_on{0};
     const int smem = (int)sizeof(InferSmem);
     cudaError_t e = smem_opt_in(infer_umma_kernel, smem, set_on);
     if (e != cudaSuccess) return e;
-    const long tiles = (n + 127) / 128;
+    const long tiles = (n + 127) / 128 * n_seg;
     // four blocks per SM hold all 512 TMEM columns (128 each); the shared
     // memory request keeps a fifth off the SM
     const int grid = (int)std::min<long>(tiles, 4L * sm_count());
-    infer_umma_kernel<<<grid, kThr, smem, st>>>(x, s2, n, W1q, b1, W2q, b2, W3q, b3, llr);
+    infer_umma_kernel<<<grid, kThr, smem, st>>>(x, s2, n, n_seg, x_stride, llr_stride, W1q, b1, W2q, b2, W3q, b3,
+                                                llr);
     return cudaGetLastError();
 }
 

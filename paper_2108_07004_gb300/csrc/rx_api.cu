@@ -837,10 +837,10 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
                                  h->mlp ? nullptr : llr + (size_t)a * m, N * m, cnt, sym, S, f, ds, h->prec,
                                  avail));
         if (h->mlp) {
-            for (int s = 0; s < S; ++s)
-                STAGE(ST_DEMAP, ds, 3,
-                      mlp_infer(h->mlp->d, sym.x4 + ((size_t)s * N + a) * 4, sym.s2 + (size_t)s * N + a, e - a,
-                                llr + ((size_t)s * N + a) * m, ds));
+            // every stream's symbols of the block in one launch (tcgen05 path)
+            STAGE(ST_DEMAP, ds, h->mlp->d.infer == 2 ? 1 : S,
+                  mlp_infer_seg(h->mlp->d, sym.x4 + (size_t)a * 4, sym.s2 + a, e - a, S, N, llr + (size_t)a * m, N,
+                                ds));
             STAGE(ST_DEMAP, ds, 1,
                   launch_count_llr(llr + (size_t)a * m, N * m, sym.x4, N, a, e, h->sig, 1, cnt, S, f, ds));
         }

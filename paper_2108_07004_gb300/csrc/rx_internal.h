@@ -304,9 +304,14 @@ cudaError_t launch_gemm_tc(int epi, bool b_bf16, int M, int N, long K, const flo
                            const void *B, long sbn, long sbk, const float *bias, const float *aux, int ldaux,
                            float *out0, float *out1, int ldo, long k_slice, long out_slice_stride, int n_slices,
                            cudaStream_t st);
-cudaError_t launch_infer_umma(const float *x, const float *s2, long n, const uint16_t *W1q, const float *b1,
-                              const uint16_t *W2q, const float *b2, const uint16_t *W3q, const float *b3, float *llr,
-                              cudaStream_t st);
+cudaError_t launch_infer_umma(const float *x, const float *s2, long n, int n_seg, long x_stride, long llr_stride,
+                              const uint16_t *W1q, const float *b1, const uint16_t *W2q, const float *b2,
+                              const uint16_t *W3q, const float *b3, float *llr, cudaStream_t st);
+// inference of n_seg segments of n samples (segment g at rows g x_stride of
+// x and sigma2, its LLRs at rows g llr_stride): one launch on the tcgen05
+// path, one per segment on the mma.sync path
+cudaError_t mlp_infer_seg(MlpDev &d, const float *x, const float *s2, long n, int n_seg, long x_stride,
+                          float *llr, long llr_stride, cudaStream_t st);
 cudaError_t mlp_tc_status(unsigned int *flag);
 
 cudaError_t launch_demap(const float2 *z, long z_stride, long z_off, long a, long e,

@@ -138,39 +138,43 @@ def test_training_on_the_gpu_gains_over_the_untrained_network():
     assert b0 < 0.0 and exact - 0.3 < a0 < exact + 0.01
 
 
-def test_chain_with_learned_demapper_and_symbol_output():
+@pytest.mark.parametrize("S", [1, 3])
+def test_chain_with_learned_demapper_and_symbol_output(S):
     """The chain's symbol output does not change its LLRs; with the learned
-    demapper the chain's LLRs are the MLP's on those symbols and its bit
-    counts are those of its own hard decisions."""
+    demapper the chain's LLRs are the MLP's on those symbols (one inference
+    launch per block over the S streams) and its bit counts are those of its
+    own hard decisions."""
     rx = _rx()
     from paper_2108_07004_gb300 import synth
     n = 20000
-    st = synth.make_stream("gs4d64", n, seed=synth.stream_seed(4, 1), esn0_db=13.0,
-                           cd_ps_per_nm=17000.0, linewidth_ts=2e-5)
-    samples = _dev(st.rx[None], np.complex64)
-    bits = _dev(st.bits[None], np.uint8)
+    sts = [synth.make_stream("gs4d64", n, seed=synth.stream_seed(4, 1 + s), esn0_db=13.0 - s,
+                             cd_ps_per_nm=17000.0, linewidth_ts=2e-5) for s in range(S)]
+    samples = _dev(np.stack([st.rx for st in sts]), np.complex64)
+    bits = _dev(np.stack([st.bits for st in sts]), np.uint8)
 
     def receiver():
         r = rx.Receiver("gs4d64", cd_ps_per_nm=17000.0, taps=31, bps_phases=64)
-        for k, v in (("fft", 4096), ("overlap", 1024), ("block", 4096), ("n_pre", 4096)):
+        for k, v in (("fft", 4096), ("overlap", 1024), ("block", 4096), ("n_pre", 4096), ("streams", S)):
             r.set(k, v)
         r.set_reference(bits)
         return r
 
     ref, st_ref = receiver().process(samples)
     r = receiver()
-    x4 = torch.zeros((1, n, 4), dtype=torch.float32, device="cuda")
-    s2 = torch.zeros((1, n), dtype=torch.float32, device="cuda")
+    x4 = torch.zeros((S, n, 4), dtype=torch.float32, device="cuda")
+    s2 = torch.zeros((S, n), dtype=torch.float32, device="cuda")
     r.set_symbol_output(x4, s2)
     got, st_got = r.process(samples)
-    assert torch.equal(got, ref) and st_got[0]["bit_errors"] == st_ref[0]["bit_errors"]
+    assert torch.equal(got, ref)
+    assert all(st_got[s]["bit_errors"] == st_ref[s]["bit_errors"] for s in range(S))
     assert torch.all(s2 > 0) and torch.all(torch.isfinite(x4))
     m = rx.Mlp(_params(13))
     r2 = receiver()
     r2.set_demapper(m)
     learned, st_l = r2.process(samples)
-    want = m.infer(x4[0].contiguous(), s2[0].contiguous())
-    assert torch.equal(learned[0], want)
     c0, c1 = 4096, n - 512
-    hard = (learned[0, c0:c1].cpu().numpy() < 0).astype(np.uint8)
-    assert st_l[0]["bit_errors"] == int(np.sum(hard != st.bits[c0:c1]))
+    for s in range(S):
+        want = m.infer(x4[s].contiguous(), s2[s].contiguous())
+        assert torch.equal(learned[s], want), s
+        hard = (learned[s, c0:c1].cpu().numpy() < 0).astype(np.uint8)
+        assert st_l[s]["bit_errors"] == int(np.sum(hard != sts[s].bits[c0:c1])), s
