@@ -1040,7 +1040,7 @@ def run_mlp_infer(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "bf16 weights / f32",
         "data": "synthetic",
         "config": {"workload": f"mlp_4x128x128x6_infer_{n}", "symbols": n, "esn0_db": 12.0,
-                   "l2": "inputs 256 MiB, outputs 384 MiB > L2, no flush"},
+                   "l2": f"inputs {n * 20 / 2**20:.0f} MiB, outputs {n * 24 / 2**20:.0f} MiB; no flush"},
         "roofline": {"bound": "tensor", "kernel": "infer_umma_kernel", "achieved": tf, "peak": peak, "unit": "TFLOP/s",
                      "frac": tf / peak, "traffic": None, "peak_kind": pk_kind,
                      "note": "algorithmic flops; the kernel issues 3 products per layer-2 term (bfloat16 split)"},
