@@ -164,7 +164,13 @@ void rx_destroy(rx_handle *h);                      /* NULL-safe */
  *   continues a stream (b0 > 0) is captured as a CUDA graph and launched
  *   as one, the handle's instantiated graph updated in place when only
  *   kernel arguments changed.  Results are the same in every mode; the
- *   host entry (rx_process_host) and the streaming entry always use 0.
+ *   host entry (rx_process_host) and the streaming entry always use 0,
+ *   "fir_tma" [1]: the FIR stages each tile's input window with the tensor
+ *   memory accelerator (3D tensor copies of the [2S][n_samples] rows in
+ *   64-byte groups, zero-filled outside them) where the rows are 16-byte
+ *   aligned whole groups (N a multiple of 4 for float32 storage, of 8 for
+ *   16-bit storage), else, and with 0, with cp.async; the outputs are the
+ *   same bits.
  * Changing a parameter resets the stream state (rx_reset). */
 int rx_set_param(rx_handle *h, const char *key, double value);
 int rx_get_param(const rx_handle *h, const char *key, double *value);

@@ -19,6 +19,7 @@
 #include <thread>
 #include <vector>
 
+#include "k_fir.h"
 #include "rx_internal.h"
 #include "gs4d64_table.inc"   // kGs4d64Points, kGs4d64Labels (written by build.py)
 #include "k_kk.h"
@@ -141,6 +142,9 @@ struct rx_handle {
     // a call after the stream's first are captured as a CUDA graph and
     // launched as one, the instantiated graph updated in place per block
     int issue = 0;
+    // the FIR's input windows staged by TMA where the rows allow (parameter
+    // "fir_tma"; 0: the cp.async form, the same bits)
+    int fir_tma = 1;
     cudaGraphExec_t gexec = nullptr;
     cudaStream_t gst = nullptr;   // capture stream (the handle's own stream may be a default stream)
     bool in_host = false;     // inside rx_process_host (multi-stream always)
@@ -614,9 +618,9 @@ int train_stage(rx_handle *h, const void *x, long ns, float2 *taps, long ntr, ui
         CK(cudaMalloc(&h->ytr, need));
         h->ytr_cap = need;
     }
-    STAGE(ST_STARTUP, st, 1, launch_fir(x, ns, taps, 0, ntr, h->ytr, ntr, 0, S, T, st, sk, 0, h->wl));
+    STAGE(ST_STARTUP, st, 1, launch_fir_ex(x, ns, taps, 0, ntr, h->ytr, ntr, 0, S, T, st, sk, 0, h->wl, h->fir_tma));
     STAGE(ST_STARTUP, st, 1, launch_align(h->ytr, ntr, taps, h->ref, h->ref_n, (int)ntr, S, tl(h), h->fmt, st, sk));
-    STAGE(ST_STARTUP, st, 1, launch_fir(x, ns, taps, 0, ntr, h->ytr, ntr, 0, S, T, st, sk, 0, h->wl));
+    STAGE(ST_STARTUP, st, 1, launch_fir_ex(x, ns, taps, 0, ntr, h->ytr, ntr, 0, S, T, st, sk, 0, h->wl, h->fir_tma));
     STAGE(ST_STARTUP, st, 1, launch_train_phase(h->ytr, ntr, h->ref, h->ref_n, (int)ntr, h->W, pcode,
                                                 pcode_stride, carry, carry_stride, S, h->fmt, st, sk));
     if (h->train_passes > 0)
@@ -800,7 +804,8 @@ int run_blocks(rx_handle *h, const float2 *in, long N, long b0, long b1, float *
         const float2 *wn = slot(h, g - L);
         cudaEvent_t blk0 = nullptr;
         if (h->profile == 1 && (blk0 = prof_event(h))) CK(cudaEventRecord(blk0, st));
-        STAGE(ST_FIR, st, 1, launch_fir(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st, h->prec, avail, h->wl));
+        STAGE(ST_FIR, st, 1,
+              launch_fir_ex(h->x, ns, wn, k0, k1, h->y, N, k0, S, T, st, h->prec, avail, h->wl, h->fir_tma));
         const long a = std::max(0L, k0 - h->W / 2);
         const long e = (n == nblk - 1) ? N : k1 - h->W / 2;
         const bool tc = use_bps_tc(h);
@@ -889,6 +894,11 @@ int fill_stats(rx_handle *h, rx_stats *out) {
         unsigned int gave_up = 0;
         CK(bps_tc_status(&gave_up));
         if (gave_up) return fail(RX_ETIMEDOUT, "a bounded wait of the tensor-core phase search gave up");
+    }
+    if (h->fir_tma) {
+        unsigned int gave_up = 0;
+        CK(fir_tma_status(&gave_up));
+        if (gave_up) return fail(RX_ETIMEDOUT, "a bounded wait of the TMA-staged FIR gave up");
     }
     if (h->mlp) {
         unsigned int gave_up = 0;
@@ -1177,6 +1187,7 @@ int set_param_impl(rx_handle *h, const std::string &k, double v) {
     else if (k == "bps_tc") { rc = as_int(0, 1, t); h->bps_tc = (int)t; }
     else if (k == "lms_exact") { rc = as_int(0, 1, t); h->lms_exact = (int)t; }
     else if (k == "sm_reserve") { rc = as_int(0, 1024, t); h->sm_reserve = (int)t; }
+    else if (k == "fir_tma") { rc = as_int(0, 1, t); h->fir_tma = (int)t; }
     else if (k == "issue") {
         rc = as_int(0, 2, t);
         h->issue = (int)t;
@@ -1359,6 +1370,7 @@ int rx_get_param(const rx_handle *h, const char *key, double *value) {
     else if (k == "lms_exact") *value = h->lms_exact;
     else if (k == "sm_reserve") *value = h->sm_reserve;
     else if (k == "issue") *value = h->issue;
+    else if (k == "fir_tma") *value = h->fir_tma;
     else if (k == "cd_ps_per_nm") *value = h->cd;
     else if (k == "profile") *value = h->profile;
     else if (k == "precision") *value = h->prec;
@@ -2000,8 +2012,8 @@ int rx_cdc(rx_handle *h, const void *in, void *out, size_t n_samples) {
 int rx_fir(rx_handle *h, const void *x, size_t n_samples, const void *taps, size_t k0, size_t k1, void *y) {
     if (!h || !x || !taps || !y) return fail(RX_EINVAL, "NULL argument");
     if (k1 < k0) return fail(RX_EINVAL, "k1 < k0");
-    CK(launch_fir(x, (long)n_samples, (const float2 *)taps, (long)k0, (long)k1,
-                  y, (long)(k1 - k0), 0, h->streams, h->T, h->st, h->prec, 0, h->wl));
+    CK(launch_fir_ex(x, (long)n_samples, (const float2 *)taps, (long)k0, (long)k1,
+                     y, (long)(k1 - k0), 0, h->streams, h->T, h->st, h->prec, 0, h->wl, h->fir_tma));
     return RX_OK;
 }
 
