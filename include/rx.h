@@ -63,10 +63,11 @@ typedef struct rx_handle rx_handle;
  *   kind      RX_FMT_*; for built-ins the other fields are ignored.
  *   dims      2: one 2D table used on each polarisation (m_bits per pol);
  *             4: one joint 4D table over both polarisations.
- *   m_bits    bits per table entry (table size 2^m_bits; dims 2: 2 .. 6,
- *             i.e. 4 to 64 points per polarisation, the paper's 4- to
- *             64-QAM and GS-8; dims 4: 6), with at most 16 orbits under
- *             the rotation by 2 pi / sym_order.
+ *   m_bits    bits per table entry (table size 2^m_bits; dims 2: 2 .. 7,
+ *             i.e. 4 to 128 points per polarisation, the paper's 4- to
+ *             64-QAM, GS-8 and GS-128 (Sec. 5); dims 4: 6), with at most
+ *             32 (dims 2) / 16 (dims 4) orbits under the rotation by
+ *             2 pi / sym_order.
  *   points    host, [2^m_bits][dims] float32 (re, im [, re_y, im_y]),
  *             copied at creation.
  *   labels    host, [2^m_bits] bit label of each row, a permutation of

@@ -109,7 +109,10 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
             // per orbit o (and polarisation for 2D tables): CR = (Re c, Im c) and
             // CI = (Im c, -Re c), c = sum_p y_p conj(rep_p); then for a test phase,
             // (P, Q) = cos(phi) CR + sin(phi) CI is one packed multiply and one packed FMA
-            f32x2 CR[2][NORB], CI[2][NORB];
+            // 2D tables of more than 16 orbits (GS-128: 32) form the
+            // correlations per pass over the test phases instead (registers)
+            constexpr bool kBig = DIMS == 2 && NORB > 16;
+            f32x2 CR[2][kBig ? 1 : NORB], CI[2][kBig ? 1 : NORB];
             float yn0, yn1;
             if (DIMS == 4) {
                 yn0 = cnorm(ya) + cnorm(yb);
@@ -124,11 +127,11 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
                         CI[0][o] = pk2(ci, -cr);
                     }
                 }
-            } else {
+            } else if (!kBig) {
                 yn0 = cnorm(ya);
                 yn1 = cnorm(yb);
     #pragma unroll
-                for (int o = 0; o < NORB; ++o) {
+                for (int o = 0; o < (kBig ? 1 : NORB); ++o) {
                     if (o < f.n_orb) {
                         const float r0 = f.orb[o][0], r1 = f.orb[o][1];
                         const float cr0 = ya.x * r0 + ya.y * r1, ci0 = ya.y * r0 - ya.x * r1;
@@ -139,9 +142,59 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
                         CI[1][o] = pk2(ci1, -cr1);
                     }
                 }
+            } else {
+                yn0 = cnorm(ya);
+                yn1 = cnorm(yb);
             }
             const int slot = (jc + 1) % RX_NCHUNK;
             const int hb = B >> 1;
+            if constexpr (kBig) {
+                // passes of eight phase pairs; per orbit the correlations of
+                // both polarisations, then the pairs' minima (the same
+                // operations and minima as the loop below, in another order
+                // of the exact min)
+                constexpr int kCh = 8;
+                for (int b0 = 0; b0 < hb; b0 += kCh) {
+                    float x0[kCh], x1[kCh], w0[kCh], w1[kCh];
+#pragma unroll
+                    for (int i = 0; i < kCh; ++i) x0[i] = x1[i] = w0[i] = w1[i] = 3.0e38f;
+#pragma unroll 2
+                    for (int o = 0; o < NORB; ++o) {
+                        if (o < f.n_orb) {
+                            const float r0 = f.orb[o][0], r1 = f.orb[o][1], eo = f.orbe[o];
+                            const float cr0 = ya.x * r0 + ya.y * r1, ci0 = ya.y * r0 - ya.x * r1;
+                            const float cr1 = yb.x * r0 + yb.y * r1, ci1 = yb.y * r0 - yb.x * r1;
+                            const f32x2 CR0 = pk2(cr0, ci0), CI0 = pk2(ci0, -cr0);
+                            const f32x2 CR1 = pk2(cr1, ci1), CI1 = pk2(ci1, -cr1);
+#pragma unroll
+                            for (int i = 0; i < kCh; ++i) {
+                                if (b0 + i < hb) {
+                                    const f32x2 *cp1 = reinterpret_cast<const f32x2 *>(f.csp[b0 + i]);
+                                    const f32x2 C1 = cp1[0], S1 = cp1[1];
+                                    float P0, Q0, P1, Q1;
+                                    upk2(fma2(S1, CI0, mul2(C1, CR0)), P0, Q0);
+                                    upk2(fma2(S1, CI1, mul2(C1, CR1)), P1, Q1);
+                                    x0[i] = fminf(x0[i], fmaf(-2.f, orbit_v(P0, Q0, SS), eo));
+                                    x1[i] = fminf(x1[i], fmaf(-2.f, orbit_v(P1, Q1, SS), eo));
+                                    w0[i] = fminf(w0[i], half_turn_d(P0, Q0, SS, eo));
+                                    w1[i] = fminf(w1[i], half_turn_d(P1, Q1, SS, eo));
+                                }
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int i = 0; i < kCh; ++i) {
+                        const int b = b0 + i;
+                        if (b < hb) {
+                            float md = (yn0 + x0[i]) + (yn1 + x1[i]);
+                            float md2 = (yn0 + w0[i]) + (yn1 + w1[i]);
+                            if (!valid) { md = 0.f; md2 = 0.f; }
+                            Eb[(slot * B + b) * kRow + lane] = md;
+                            Eb[(slot * B + b + hb) * kRow + lane] = md2;
+                        }
+                    }
+                }
+            } else {
             // test phases b and b + B/2 together: phi_{b+B/2} = phi_b + pi/S, a
             // rotation of P + jQ that half_turn_d applies without another multiply
             // two phase pairs per trip: independent min chains for the scheduler
@@ -180,7 +233,7 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
                 } else {
                     float x0 = 3.0e38f, x1 = 3.0e38f, w0 = 3.0e38f, w1 = 3.0e38f;
     #pragma unroll
-                    for (int o = 0; o < NORB; ++o) {
+                    for (int o = 0; o < (kBig ? 1 : NORB); ++o) {
                         float P0, Q0, P1, Q1;
                         upk2(fma2(S1, CI[0][o], mul2(C1, CR[0][o])), P0, Q0);
                         upk2(fma2(S1, CI[1][o], mul2(C1, CR[1][o])), P1, Q1);
@@ -195,6 +248,7 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
                 if (!valid) { md = 0.f; md2 = 0.f; }
                 Eb[(slot * B + b) * kRow + lane] = md;
                 Eb[(slot * B + b + hb) * kRow + lane] = md2;
+            }
             }
             __syncwarp();
             // exclusive prefix of every test phase's row over the chunk's 32
@@ -657,6 +711,7 @@ cudaError_t launch_bps(const void *y, long y_stride, long a, long e, long n_vali
         case 4: RX_BPS(2, 4);
         case 8: RX_BPS(2, 8);
         case 16: RX_BPS(2, 16);
+        case 32: RX_BPS(2, 32);
         default: return cudaErrorInvalidValue;
     }
 #undef RX_BPS
@@ -682,11 +737,19 @@ cudaError_t launch_unwrap(const float2 *y, long y_stride, const uint8_t *b, long
                                                     z + z_off, z_stride, pcode + pcode_off, pcode_stride,
                                                     partial, sigma2_out, sigma2_stride, ticket, ticket_stride, kR, mdsum, f);
     } else {
-        // NORB bounds the orbit loop (predicated on f.n_orb): 16 covers every 2D table
-        unwrap_kernel<2, 16><<<grid, 256, 0, st>>>(y, y_stride, b + b_off, b_stride, a, e, dsum, n_cta,
-                                                    carry_in, carry_in_stride, carry_out, carry_out_stride,
-                                                    z + z_off, z_stride, pcode + pcode_off, pcode_stride,
-                                                    partial, sigma2_out, sigma2_stride, ticket, ticket_stride, kR, mdsum, f);
+        // NORB bounds the orbit loop (predicated on f.n_orb): 16, or 32 for larger 2D tables
+        if (f.n_orb > 16)
+            unwrap_kernel<2, 32><<<grid, 256, 0, st>>>(y, y_stride, b + b_off, b_stride, a, e, dsum, n_cta,
+                                                        carry_in, carry_in_stride, carry_out, carry_out_stride,
+                                                        z + z_off, z_stride, pcode + pcode_off, pcode_stride,
+                                                        partial, sigma2_out, sigma2_stride, ticket, ticket_stride, kR,
+                                                        mdsum, f);
+        else
+            unwrap_kernel<2, 16><<<grid, 256, 0, st>>>(y, y_stride, b + b_off, b_stride, a, e, dsum, n_cta,
+                                                        carry_in, carry_in_stride, carry_out, carry_out_stride,
+                                                        z + z_off, z_stride, pcode + pcode_off, pcode_stride,
+                                                        partial, sigma2_out, sigma2_stride, ticket, ticket_stride, kR,
+                                                        mdsum, f);
     }
     return cudaGetLastError();
 }

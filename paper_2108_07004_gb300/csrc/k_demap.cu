@@ -706,6 +706,7 @@ cudaError_t launch_derot_demap(const void *y, long y_stride, const uint8_t *b, l
     if (f.dims == 2 && f.M == 16) RX_DD(2, 16, 4);
     if (f.dims == 2 && f.M == 32) RX_DD(2, 32, 5);
     if (f.dims == 2 && f.M == 64) RX_DD(2, 64, 6);
+    if (f.dims == 2 && f.M == 128) RX_DD(2, 128, 7);
 #undef RX_DD
     return cudaErrorInvalidValue;
 }
@@ -729,6 +730,8 @@ cudaError_t launch_count_llr(const float *llr, long llr_stride, const float *x4,
         count_llr_kernel<2, 5><<<grid, 256, 0, st>>>(llr, llr_stride, xv, x_stride, a, e, sigma2, s2_stride, cnt, f);
     else if (f.dims == 2 && f.m_pol == 6)
         count_llr_kernel<2, 6><<<grid, 256, 0, st>>>(llr, llr_stride, xv, x_stride, a, e, sigma2, s2_stride, cnt, f);
+    else if (f.dims == 2 && f.m_pol == 7)
+        count_llr_kernel<2, 7><<<grid, 256, 0, st>>>(llr, llr_stride, xv, x_stride, a, e, sigma2, s2_stride, cnt, f);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -751,5 +754,7 @@ cudaError_t launch_demap(const float2 *z, long z_stride, long z_off, long a, lon
         return demap_t<2, 32, 5>(zz, z_stride, a, e, sigma2, sigma2_stride, llr, llr_stride, cnt, n_streams, f, st);
     if (f.dims == 2 && f.M == 64)
         return demap_t<2, 64, 6>(zz, z_stride, a, e, sigma2, sigma2_stride, llr, llr_stride, cnt, n_streams, f, st);
+    if (f.dims == 2 && f.M == 128)
+        return demap_t<2, 128, 7>(zz, z_stride, a, e, sigma2, sigma2_stride, llr, llr_stride, cnt, n_streams, f, st);
     return cudaErrorInvalidValue;
 }

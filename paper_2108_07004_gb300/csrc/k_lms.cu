@@ -517,7 +517,9 @@ lms_kernel(const void *__restrict__ x, long ns, const float2 *__restrict__ taps_
 
             // decision warp state: partial y of update 16 s + lane, both outputs
             float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
-            const int o = lane & 15;
+            // lane o holds orbit o: 16 orbits twice over (4D and up to 16 2D
+            // orbits), or 32 for 2D tables of more than 16 orbits
+            const int o = (DIMS == 2 && f.n_orb > 16) ? lane : (lane & 15);
             const bool valid = o < f.n_orb;
             const float4 r = tb.orb[valid ? o : 0];
             const float eo = valid ? tb.orbe[o] : __int_as_float(0x7f800000);   // +inf: never the minimum

@@ -303,7 +303,7 @@ int build_format(const rx_format *f, FmtDev &d) {
         const uint32_t *fl = gs ? kGs4d64Labels : f->labels;
         if (dims != 2 && dims != 4) return fail(RX_EINVAL, "format dims must be 2 or 4");
         if (!fp || !fl) return fail(RX_EINVAL, "custom format needs points and labels");
-        if (mb < 1 || mb > 6) return fail(RX_EINVAL, "m_bits %d out of range", mb);
+        if (mb < 1 || mb > (dims == 2 ? 7 : 6)) return fail(RX_EINVAL, "m_bits %d out of range", mb);
         const int M = 1 << mb;
         pts.assign((size_t)M * dims, 0.f);
         std::vector<int> seen(M, 0);
@@ -318,7 +318,7 @@ int build_format(const rx_format *f, FmtDev &d) {
     }
     const int M = 1 << mb;
     if (S != 1 && S != 2 && S != 4) return fail(RX_EINVAL, "sym_order must be 1, 2 or 4");
-    if (dims == 2 && (M < 4 || M > 64)) return fail(RX_EINVAL, "2D tables of 4 to 64 points are supported");
+    if (dims == 2 && (M < 4 || M > 128)) return fail(RX_EINVAL, "2D tables of 4 to 128 points are supported");
     if (dims == 4 && M != 64) return fail(RX_EINVAL, "4D tables of 64 points are supported");
     std::memset(&d, 0, sizeof d);
     d.dims = dims;
@@ -371,7 +371,9 @@ int build_format(const rx_format *f, FmtDev &d) {
         for (int c = 0; c < 4; ++c) d.orbT[c][o] = o < no ? d.orb[o][c] : 0.f;
         d.orbeP[o] = o < no ? d.orbe[o] : std::numeric_limits<float>::infinity();
     }
-    if (no > 16) return fail(RX_EINVAL, "%d orbits under the rotation by 2pi/%d; at most 16 are supported", no, S);
+    if (no > (dims == 2 ? 32 : 16))
+        return fail(RX_EINVAL, "%d orbits under the rotation by 2pi/%d; at most %d are supported", no, S,
+                    dims == 2 ? 32 : 16);
     return RX_OK;
 }
 
@@ -1277,8 +1279,8 @@ rx_handle *rx_create(const rx_format *format, double symbol_rate, int sps, doubl
     h->B = bps_phases;
     if (check_config(h) != RX_OK) { delete h; return nullptr; }
     set_phases(h->fmt, bps_phases);
-    if (h->fmt.n_orb > 16) {
-        fail(RX_EINVAL, "phase search needs at most 16 orbits (use sym_order 4)");
+    if (h->fmt.n_orb > (h->fmt.dims == 2 ? 32 : 16)) {
+        fail(RX_EINVAL, "phase search needs at most 16 (4D) / 32 (2D) orbits (use sym_order 4)");
         delete h;
         return nullptr;
     }

@@ -9,8 +9,8 @@
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
-#define RX_MAXM 64        // largest table (4D: 64 points; 2D: 16 points per polarisation)
-// reference label of one 4D symbol (m bits, MSB first): up to 12 bits (DP-64QAM)
+#define RX_MAXM 128       // largest table (4D: 64 points; 2D: 128 points per polarisation)
+// reference label of one 4D symbol (m bits, MSB first): up to 14 bits (two 2D labels of 7)
 typedef uint16_t reflab_t;
 #define RX_MAXB 64        // largest number of BPS test phases
 #define RX_NCHUNK 10      // BPS ring of 32-symbol chunks

@@ -65,7 +65,10 @@ def test_ahead_equals_exact_search_bench_shape():
 
 
 @pytest.mark.parametrize("fmt,esn0", [("dp_qpsk", [9.0, 12.0]), ("dp_16qam", [15.0, 18.0]),
-                                      ("dp_64qam", [21.0, 24.0])])
+                                      ("dp_64qam", [21.0, 24.0]), ("gs128", [18.0, 20.0])])
 def test_ahead_equals_exact_search_2d(fmt, esn0):
-    phases = 64 if fmt == "dp_64qam" else 32
+    """GS-128 (32 orbits per polarisation): the exact search spreads the
+    orbits over all 32 lanes, the decisions taken ahead search 16 then the
+    rest serially."""
+    phases = 64 if fmt in ("dp_64qam", "gs128") else 32
     _same(fmt, esn0, 1360.0, 15, phases, 1 << 17, 20, fft=1024, overlap=256, **KEYS)

@@ -50,6 +50,12 @@ CASES = {
     "qam16": ("dp_16qam", 12000, 2000.0, 1024, 256, 15, 32, 4096, 18.0, 1e-5),
     "qam64": ("dp_64qam", 12000, 1000.0, 1024, 256, 15, 64, 4096, 24.0, 1e-6),
     "gs8": ("gs8", 12000, 500.0, 1024, 256, 15, 32, 4096, 14.0, 1e-5),
+    # the paper's 128-point 2D GS format (Sec. 5): 32 orbits per polarisation
+    # under the quarter-turn symmetry; at 30 dB the oracle's DD span has no
+    # near-tie decision (the DD stage test needs none), and at the format's
+    # 20 dB design point (BER ~4e-2) every test but the DD stage test runs
+    "gs128": ("gs128", 12000, 500.0, 1024, 256, 15, 64, 4096, 30.0, 1e-6),
+    "gs128_20db": ("gs128", 12000, 500.0, 1024, 256, 15, 64, 4096, 20.0, 1e-6),
     # the paper's receiver order: two single-polarisation KK signals (CSPR
     # 14 dB) through the KK front-end and the trained static equaliser
     # (oracle), then the chain as X and Y with the CDC reduced to the
@@ -57,6 +63,7 @@ CASES = {
     "kk16": ("dp_16qam", 12000, 0.0, 1024, 256, 15, 32, 4096, 20.0, 0.0),
 }
 KK_CASES = {"kk16"}
+DD_NEAR_TIE_CASES = {"gs128_20db"}
 
 
 def _kk_input(n_sym, seed, esn0):
@@ -181,6 +188,8 @@ def test_lms_cma_parity(case):
 @pytest.mark.parametrize("case", list(CASES))
 def test_lms_dd_parity(case):
     """DD-LMS of one block span with the oracle's taps and phases."""
+    if case in DD_NEAR_TIE_CASES:
+        pytest.skip("the oracle's DD span holds near-tie decisions at this operating point")
     st, p, res = _oracle_run(case)
     r = _receiver(case)
     fmt = oracle_format(CASES[case][0])
@@ -285,7 +294,7 @@ def test_demap_parity(case):
     assert np.all(err <= LLR_RTOL * np.maximum(1.0, np.abs(ref)))
 
 
-@pytest.mark.parametrize("name", ["gs4d64", "dp_16qam", "dp_qpsk", "dp_64qam", "gs8"])
+@pytest.mark.parametrize("name", ["gs4d64", "dp_16qam", "dp_qpsk", "dp_64qam", "gs8", "gs128"])
 def test_demap_extreme_llrs(name):
     """Subset sums beyond the float range of the common shift use their own
     shift: every symbol extreme (small sigma^2), and a ragged length with
