@@ -741,6 +741,66 @@ def run_widely_linear(args):
     print(json.dumps(line), flush=True)
 
 
+# ---- GS-128 (Sec. 5's 128-point 2D format) through the chain ----
+WGS128 = dict(workload="gs128_500km_24dB_9x2p20", fmt="gs128", n_sym=1 << 20, streams=9, esn0_db=24.0,
+              cd_ps_per_nm=8500.0, linewidth_ts=1e-6, symbol_rate=28e9, sps=2, fft=1024, overlap=256,
+              taps=15, bps_phases=64, bps_window=64, block=1 << 16, n_upd=1024, lag=3, lms_start=1,
+              mu=1e-3, n_pre=2048, cma_passes=1, n_cma=0, n_train=1024, train_passes=3, skip_head=16384,
+              skip_tail=512)
+
+
+def run_gs128(args):
+    """Nine streams of the 2D 128-point GS format at 24 dB (500 km, lag 3 with
+    independent LMS chains): Gbit/s of LLRs (14 bits per 4D symbol), the
+    bit-error rate, and the oracle on one stream.  At the format's 20 dB
+    design point the blind phase search (64 test phases, 64-symbol window)
+    slips quadrants within 2^18 symbols, in the oracle as on the GPU; at 22
+    and 24 dB the oracle holds the quadrant over 2^18 symbols."""
+    import torch
+    from paper_2108_07004_gb300 import rx as rx_mod
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    wl = WGS128
+    S = wl["streams"]
+    n = args.n_sym if args.n_sym != WL["n_sym"] else wl["n_sym"]
+    m = 14
+    rxs, bits = [], []
+    for p_ in range(S):
+        st = synth.make_stream(wl["fmt"], n, seed=synth.stream_seed(16, p_), esn0_db=wl["esn0_db"],
+                               cd_ps_per_nm=wl["cd_ps_per_nm"], linewidth_ts=wl["linewidth_ts"])
+        rxs.append(st.rx)
+        bits.append(st.bits)
+    samples = torch.from_numpy(np.stack(rxs)).cuda()
+    bits_d = torch.from_numpy(np.stack(bits)).cuda()
+    del rxs
+    r = rx_mod.Receiver(wl["fmt"], cd_ps_per_nm=wl["cd_ps_per_nm"], taps=wl["taps"], bps_phases=wl["bps_phases"],
+                        streams=S, **rx_params(wl))
+    r.set_reference(bits_d)
+    llr = torch.empty((S, n, m), dtype=torch.float32, device="cuda")
+    ms, stg, st_ = timed_steps(r, samples, llr, args.steps, args.warmup)
+    nb = sum(x["n_bits"] for x in st_)
+    line = {
+        "metric": METRIC, "value": S * n * m / (ms * 1e-3) / 1e9, "unit": "Gbit/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": wl["workload"], "streams": S, "symbols_per_stream": n, "format": wl["fmt"],
+                   "fft": wl["fft"], "overlap": wl["overlap"], "taps": wl["taps"],
+                   "bps_phases": wl["bps_phases"], "block": wl["block"], "lag": wl["lag"], "lms_start": 1,
+                   "esn0_db": wl["esn0_db"]},
+        "stages_ms": stg,
+        "ber": sum(x["bit_errors"] for x in st_) / max(1, nb),
+        "gmi_per_4d_symbol": float(np.mean([x["gmi"] for x in st_])),
+        "gpu_launches": None,
+    }
+    if not args.no_cpu_baseline:
+        v, dt, st_o, res_o = cpu_baseline(1 << 14, wl, wl["esn0_db"], synth.stream_seed(16, 99))
+        line["cpu_baseline"] = {"value": v, "unit": "Gbit/s", "cores": 1, "kind": "oracle",
+                                "sample": f"one stream of 16384 GS-128 symbols, {dt:.1f} s"}
+        if not args.no_parity:
+            line["parity"] = parity_on(rx_mod, torch, st_o, res_o, wl)
+    r.close()
+    print(json.dumps(line), flush=True)
+
+
 # ---- Kramers-Kronig receiver front-end (Sec. 2): 32 streams of 2^22 ADC samples ----
 KKW = dict(workload="kk_frontend_fde_32x2p22", streams=32, n=1 << 22, distinct=4, fmt="dp_16qam", cspr_db=14.0,
            esn0_db=25.0, n_ov=512, floor=1e-3, fde_taps=203, fde_ov=256, n_train=4096)
@@ -1418,7 +1478,7 @@ def main():
                     help="handles whose consecutive frames overlap (1: one frame at a time)")
     ap.add_argument("--no-parity", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision", "serving", "block_lms", "widely_linear", "kk", "kk_chain", "mlp_infer", "bps_paths"],
+    ap.add_argument("--variant", default="plain", choices=["plain", "learned", "precision", "serving", "block_lms", "widely_linear", "kk", "kk_chain", "mlp_infer", "bps_paths", "gs128"],
                     help="learned: train the MLP demapper on chain output, compare with the exact one; "
                          "precision: DP-QPSK chain with CDC/FIR data in float32, half and bfloat16; "
                          "serving: 64 mixed streams with Poisson arrivals through the continuous-batching server")
@@ -1447,6 +1507,8 @@ def main():
         run_bps_paths(args)
     elif args.variant == "serving":
         run_serving(args)
+    elif args.variant == "gs128":
+        run_gs128(args)
     else:
         run_ours(args)
 

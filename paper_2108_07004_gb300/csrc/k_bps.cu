@@ -149,35 +149,64 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
             const int slot = (jc + 1) % RX_NCHUNK;
             const int hb = B >> 1;
             if constexpr (kBig) {
-                // passes of eight phase pairs; per orbit the correlations of
-                // both polarisations, then the pairs' minima (the same
-                // operations and minima as the loop below, in another order
-                // of the exact min)
+                // passes of eight phase pairs; per orbit pair the
+                // correlations of both polarisations, then the phase pairs'
+                // minima (the same roundings as the loop below; the minima
+                // are exact in any order)
                 constexpr int kCh = 8;
                 for (int b0 = 0; b0 < hb; b0 += kCh) {
                     float x0[kCh], x1[kCh], w0[kCh], w1[kCh];
+                    f32x2 Cp[kCh], Sp[kCh];          // (cos, cos), (sin, sin) of the pass's phases
 #pragma unroll
-                    for (int i = 0; i < kCh; ++i) x0[i] = x1[i] = w0[i] = w1[i] = 3.0e38f;
-#pragma unroll 2
-                    for (int o = 0; o < NORB; ++o) {
+                    for (int i = 0; i < kCh; ++i) {
+                        x0[i] = x1[i] = w0[i] = w1[i] = 3.0e38f;
+                        const f32x2 *cp1 = reinterpret_cast<const f32x2 *>(f.csp[min(b0 + i, hb - 1)]);
+                        Cp[i] = cp1[0];
+                        Sp[i] = cp1[1];
+                    }
+                    const f32x2 CV = pk2(OrbitCoef<SS>::cv, OrbitCoef<SS>::cv);
+                    const f32x2 CU = pk2(OrbitCoef<SS>::cu, OrbitCoef<SS>::cu);
+                    // two orbits at a time (as the 4D loop): their distances
+                    // as packed FMAs, then three-input minima
+#pragma unroll 1
+                    for (int o = 0; o < NORB; o += 2) {
                         if (o < f.n_orb) {
-                            const float r0 = f.orb[o][0], r1 = f.orb[o][1], eo = f.orbe[o];
-                            const float cr0 = ya.x * r0 + ya.y * r1, ci0 = ya.y * r0 - ya.x * r1;
-                            const float cr1 = yb.x * r0 + yb.y * r1, ci1 = yb.y * r0 - yb.x * r1;
-                            const f32x2 CR0 = pk2(cr0, ci0), CI0 = pk2(ci0, -cr0);
-                            const f32x2 CR1 = pk2(cr1, ci1), CI1 = pk2(ci1, -cr1);
+                            const bool two = o + 1 < f.n_orb;
+                            const float ra0 = f.orb[o][0], ra1 = f.orb[o][1];
+                            const float rb0 = two ? f.orb[o + 1][0] : 0.f, rb1 = two ? f.orb[o + 1][1] : 0.f;
+                            const f32x2 EO = pk2(f.orbe[o], two ? f.orbe[o + 1] : __int_as_float(0x7f800000));
+                            f32x2 CRa[2], CIa[2], CRb[2], CIb[2];
+#pragma unroll
+                            for (int q = 0; q < 2; ++q) {
+                                const float2 yq = q ? yb : ya;
+                                const float cra = yq.x * ra0 + yq.y * ra1, cia = yq.y * ra0 - yq.x * ra1;
+                                const float crb = yq.x * rb0 + yq.y * rb1, cib = yq.y * rb0 - yq.x * rb1;
+                                CRa[q] = pk2(cra, cia);
+                                CIa[q] = pk2(cia, -cra);
+                                CRb[q] = pk2(crb, cib);
+                                CIb[q] = pk2(cib, -crb);
+                            }
 #pragma unroll
                             for (int i = 0; i < kCh; ++i) {
                                 if (b0 + i < hb) {
-                                    const f32x2 *cp1 = reinterpret_cast<const f32x2 *>(f.csp[b0 + i]);
-                                    const f32x2 C1 = cp1[0], S1 = cp1[1];
-                                    float P0, Q0, P1, Q1;
-                                    upk2(fma2(S1, CI0, mul2(C1, CR0)), P0, Q0);
-                                    upk2(fma2(S1, CI1, mul2(C1, CR1)), P1, Q1);
-                                    x0[i] = fminf(x0[i], fmaf(-2.f, orbit_v(P0, Q0, SS), eo));
-                                    x1[i] = fminf(x1[i], fmaf(-2.f, orbit_v(P1, Q1, SS), eo));
-                                    w0[i] = fminf(w0[i], half_turn_d(P0, Q0, SS, eo));
-                                    w1[i] = fminf(w1[i], half_turn_d(P1, Q1, SS, eo));
+                                    const f32x2 C1 = Cp[i], S1 = Sp[i];
+#pragma unroll
+                                    for (int q = 0; q < 2; ++q) {
+                                        float P, Q, R, U, v0, u0, v1, u1, d0, d1, h0, h1;
+                                        upk2(fma2(S1, CIa[q], mul2(C1, CRa[q])), P, Q);
+                                        upk2(fma2(S1, CIb[q], mul2(C1, CRb[q])), R, U);
+                                        orbit_vu<SS>(P, Q, v0, u0);
+                                        orbit_vu<SS>(R, U, v1, u1);
+                                        upk2(fma2(CV, pk2(v0, v1), EO), d0, d1);
+                                        upk2(fma2(CU, pk2(u0, u1), EO), h0, h1);
+                                        if (q == 0) {
+                                            x0[i] = fmin3(x0[i], d0, d1);
+                                            w0[i] = fmin3(w0[i], h0, h1);
+                                        } else {
+                                            x1[i] = fmin3(x1[i], d0, d1);
+                                            w1[i] = fmin3(w1[i], h0, h1);
+                                        }
+                                    }
                                 }
                             }
                         }

@@ -286,6 +286,114 @@ __device__ __forceinline__ bool llr_4d_stream(float2 z0, float2 z1, const FmtDev
     return low;
 }
 
+// 2D table of MT points (128: GS-128) with MB label bits, every bit's two
+// subsets with their own shift: a first pass finds the nearest label (lowest
+// on ties) and each subset's minimum distance m_{b,v}; the second
+// recomputes every distance |z - s_j|^2 (differences, two labels per packed
+// pair) and adds 2^{(m_{b,v} - d_j) c2} to the subset sum of each of its
+// label bits, so every sum is at least 1 (its nearest point) and at most MT:
+//   LLR_b = ln 2 (log2 S_{b,0} - m_{b,0} c2 - log2 S_{b,1} + m_{b,1} c2).
+// (With one common shift, at high SNR most symbols of a large table have a
+// subset below the float range and would take the warp-wide rare path.)
+template <int MT, int MB>
+__device__ __forceinline__ bool llr_2d_subsets(float2 z, const FmtDev &f, float c2, float *out, float &g,
+                                               int &jmin, int ref, int &ne, float &g2) {
+    const f32x2 ZX = pk2(z.x, z.x), ZY = pk2(z.y, z.y);
+    const f32x2 *T0 = reinterpret_cast<const f32x2 *>(f.ptsT[0]);
+    const f32x2 *T1 = reinterpret_cast<const f32x2 *>(f.ptsT[1]);
+    float m0[MB], m1[MB];
+#pragma unroll
+    for (int b = 0; b < MB; ++b) { m0[b] = 3.0e38f; m1[b] = 3.0e38f; }
+    float best = 3.0e38f;
+    int bj = 0;
+    // groups of eight labels: the low three label bits known at compile time
+#pragma unroll 1
+    for (int g8 = 0; g8 < MT; g8 += 8) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int jp = g8 / 2 + v;
+            const f32x2 u0 = sub2(ZX, T0[jp]), u1 = sub2(ZY, T1[jp]);
+            float d[2];
+            upk2(fma2(u1, u1, mul2(u0, u0)), d[0], d[1]);
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int jl = 2 * v + h;                 // label g8 + jl
+                if (d[h] < best) { best = d[h]; bj = g8 + jl; }
+#pragma unroll
+                for (int b = 0; b < 3; ++b) {
+                    if ((jl >> b) & 1) m1[b] = fminf(m1[b], d[h]);
+                    else m0[b] = fminf(m0[b], d[h]);
+                }
+            }
+            const float dm = fminf(d[0], d[1]);
+#pragma unroll
+            for (int b = 3; b < MB; ++b) {
+                const bool set = (g8 >> b) & 1;
+                m1[b] = set ? fminf(m1[b], dm) : m1[b];
+                m0[b] = set ? m0[b] : fminf(m0[b], dm);
+            }
+        }
+    }
+    // subset sums as packed pairs: S[0] = (S_{0,0}, S_{0,1}) (bit 0 splits
+    // the two labels of a pair); for b >= 1 S[b] and S1[b] the bit-clear and
+    // bit-set subsets, each as even / odd label partial sums
+    f32x2 S[MB], S1[MB];
+#pragma unroll
+    for (int b = 0; b < MB; ++b) { S[b] = 0ull; S1[b] = 0ull; }
+    const f32x2 NC = pk2(-c2, -c2), O0 = pk2(m0[0] * c2, m1[0] * c2);
+    float o0[MB], o1[MB];
+#pragma unroll
+    for (int b = 0; b < MB; ++b) { o0[b] = m0[b] * c2; o1[b] = m1[b] * c2; }
+#pragma unroll 1
+    for (int g8 = 0; g8 < MT; g8 += 8) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int jp = g8 / 2 + v;
+            const f32x2 u0 = sub2(ZX, T0[jp]), u1 = sub2(ZY, T1[jp]);
+            const f32x2 d = fma2(u1, u1, mul2(u0, u0));
+            float a0, a1;
+            // bit 0: label 2 jp in subset (0, 0), label 2 jp + 1 in subset (0, 1)
+            upk2(fma2(d, NC, O0), a0, a1);
+            S[0] = add2(S[0], pk2(ex2_ftz(a0), ex2_ftz(a1)));
+#pragma unroll
+            for (int b = 1; b < MB; ++b) {
+                // both labels of the pair share bit b
+                const bool set = b < 3 ? (((2 * v) >> b) & 1) : ((g8 >> b) & 1);
+                const float ob = set ? o1[b] : o0[b];
+                upk2(fma2(d, NC, pk2(ob, ob)), a0, a1);
+                const f32x2 e2 = pk2(ex2_ftz(a0), ex2_ftz(a1));
+                if (set) S1[b] = add2(S1[b], e2);
+                else S[b] = add2(S[b], e2);
+            }
+        }
+    }
+    g = fmaxf(best, 0.f);
+    jmin = bj;
+    ne = 0;
+    g2 = 0.f;
+#pragma unroll
+    for (int bp = 0; bp < MB; ++bp) {
+        float s0, s1;
+        if (bp == 0) {
+            upk2(S[0], s0, s1);
+        } else {
+            float x, y;
+            upk2(S[bp], x, y);
+            s0 = x + y;
+            upk2(S1[bp], x, y);
+            s1 = x + y;
+        }
+        const float L = ((__log2f(s0) - o0[bp]) - (__log2f(s1) - o1[bp])) * kLn2;
+        out[MB - 1 - bp] = L;
+        if (ref >= 0) {
+            const int bit = (ref >> bp) & 1;
+            ne += (int)((L < 0.f) != (bit != 0));
+            g2 += softplus_bits(bit ? L : -L);
+        }
+    }
+    return false;
+}
+
 // Per-thread counting terms of the symbols one thread demapped.
 struct CountAcc {
     int nerr = 0, ncnt = 0;
@@ -319,7 +427,9 @@ __device__ __forceinline__ void demap_symbol(float2 z0, float2 z1, float c2, con
             const int rp = ref < 0 ? -1 : (p ? (ref & ((1 << MB) - 1)) : (ref >> MB));
             float g, g2;
             int jm, nep;
-            const bool low = llr_table<2, MT, MB>(zp, zp, f, c2, L + p * MB, g, jm, rp, nep, g2);
+            bool low;
+            if constexpr (MT > 64) low = llr_2d_subsets<MT, MB>(zp, f, c2, L + p * MB, g, jm, rp, nep, g2);
+            else low = llr_table<2, MT, MB>(zp, zp, f, c2, L + p * MB, g, jm, rp, nep, g2);
             const unsigned need = __ballot_sync(0xffffffffu, low && active);
             if (need) llr_fixup_warp<2, MT, MB>(need, zp, zp, f, c2, L + p * MB, rp, nep, g2);
             ne += nep;
