@@ -1225,7 +1225,10 @@ def run_serving(args):
     srv = rx_mod.Server(SERVE["budget"], SERVE["slots"])
     ids_last = {}
 
+    host_ms = [0.0]       # host time inside rx_server_step (issue of the blocks)
+
     def serve(arrivals):
+        host_ms[0] = 0.0
         llrs, ids, t_arr, t_done = {}, {}, {}, {}
         order = np.argsort(arrivals)
         torch.cuda.synchronize()
@@ -1241,7 +1244,9 @@ def run_serving(args):
                                     bps_phases=SERVE["bps"][fmt], fft=4096, overlap=1024, block=1 << 16)
                 t_arr[i] = now
                 k += 1
+            th0 = time.perf_counter()
             srv.step()
+            host_ms[0] += (time.perf_counter() - th0) * 1e3
             for i, rid in ids.items():
                 if i not in t_done and srv.poll(rid)[0] in (rx_mod.REQ_DONE, rx_mod.REQ_FAILED):
                     t_done[i] = time.perf_counter() - t0
@@ -1259,13 +1264,23 @@ def run_serving(args):
     # capacity (every request present at once) in each issue mode of the
     # handles: 0 stages on their own streams with events, 1 one stream per
     # request, 2 one stream and the blocks after the first as CUDA graphs
-    cap_by_issue = {}
+    cap_by_issue, host_by_issue = {}, {}
     for mode in (0, 1, 2):
         srv.set_param("issue", mode)
         for _ in range(max(1, args.warmup)):
             serve(np.zeros(len(reqs)))
         w_, _, _, _ = serve(np.zeros(len(reqs)))
         cap_by_issue[str(mode)] = total_bits / w_ / 1e9
+        host_by_issue[str(mode)] = {"wall_ms": w_ * 1e3, "host_ms_in_step": host_ms[0]}
+    # the same in mode 1 with 1 / 2 / 4 host issue threads
+    cap_by_threads = {}
+    srv.set_param("issue", 1)
+    for nt in (1, 2, 4):
+        srv.set_param("issue_threads", nt)
+        serve(np.zeros(len(reqs)))
+        w_, _, _, _ = serve(np.zeros(len(reqs)))
+        cap_by_threads[str(nt)] = total_bits / w_ / 1e9
+    srv.set_param("issue_threads", min(8, os.cpu_count() or 1))
     srv.set_param("issue", SERVE["issue"])
     for _ in range(max(1, args.warmup)):
         serve(np.zeros(len(reqs)))
@@ -1293,6 +1308,7 @@ def run_serving(args):
                    "slots": SERVE["slots"], "load": SERVE["load"], "block": 1 << 16, "fft": 4096, "taps": 31},
         "capacity_gbps_all_at_once": cap_bits / 1e9,
         "capacity_gbps_by_issue_mode": cap_by_issue, "issue_mode": SERVE["issue"],
+        "host_by_issue_mode": host_by_issue, "capacity_gbps_by_issue_threads_mode1": cap_by_threads,
         "request_latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "request_latency_ms_all_at_once": {"p50": 1e3 * lat0[len(lat0) // 2], "p99": 1e3 * lat0[-1]},
         "max_running": info["max_active"], "all_done": ok, "not_done": failed[:8],
