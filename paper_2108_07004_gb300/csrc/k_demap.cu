@@ -678,11 +678,28 @@ derot_demap_kernel(const void *__restrict__ y, long y_stride, const uint8_t *__r
     const long yoff = (long)s * 2 * y_stride;      // y of stream s: [2][y_stride], storage kind sk
     uint16_t *pc = pcode + (long)s * pc_stride;
     CountAcc acc;
+    // the samples (and reference label) of the next symbol are loaded while
+    // this one is demapped
+    auto sym_k = [&](int u) { const int t = u * 256 + tid; return t0 + (t < nloc ? t : nloc - 1); };
+    auto ref_of = [&](long k) {
+        return (llr && cnt.ref_lab && k >= cnt.c0 && k < cnt.c1) ? (int)cnt.ref_lab[(long)s * cnt.ref_stride + k] : -1;
+    };
+    long k_n = sym_k(0);
+    float2 ya_n = ld_sample(y, yoff + k_n, sk), yb_n = ld_sample(y, yoff + y_stride + k_n, sk);
+    int ref_n = ref_of(k_n);
     for (int u = 0; u < PT; ++u) {
         const int t = u * 256 + tid;
         const bool active = t < nloc;
         const int tt = active ? t : nloc - 1;
         const long k = t0 + tt;
+        const float2 ya = ya_n, yb = yb_n;
+        const int ref_k = ref_n;
+        if (u + 1 < PT) {
+            k_n = sym_k(u + 1);
+            ya_n = ld_sample(y, yoff + k_n, sk);
+            yb_n = ld_sample(y, yoff + y_stride + k_n, sk);
+            ref_n = ref_of(k_n);
+        }
         const int b = bl[tt], mq = mql[tt];
         // exp(-j phi) = conj(cs_b) (-j)^mq
         float2 rot = rot_sh[b];
@@ -692,7 +709,7 @@ derot_demap_kernel(const void *__restrict__ y, long y_stride, const uint8_t *__r
         } else if (S == 2) {
             if (mq) rot = make_float2(-rot.x, -rot.y);
         }
-        const float2 z0 = cmul(ld_sample(y, yoff + k, sk), rot), z1 = cmul(ld_sample(y, yoff + y_stride + k, sk), rot);
+        const float2 z0 = cmul(ya, rot), z1 = cmul(yb, rot);
         if (active) {
             pc[k - a] = (uint16_t)(b | (mq << 8));
             if (sym.x4)
@@ -701,7 +718,7 @@ derot_demap_kernel(const void *__restrict__ y, long y_stride, const uint8_t *__r
         }
         if (!llr) continue;                   // symbols only (another demapper follows)
         const bool counted = active && cnt.ref_lab && k >= cnt.c0 && k < cnt.c1;
-        const int ref = counted ? (int)cnt.ref_lab[(long)s * cnt.ref_stride + k] : -1;
+        const int ref = counted ? ref_k : -1;
         demap_symbol<DIMS, MT, MB>(z0, z1, c2, f, en_sh, active, ref, counted,
                                    llr + (long)s * llr_stride + (k - a) * M_OUT, acc);
     }
