@@ -444,9 +444,12 @@ fir_tma_kernel(const __grid_constant__ CUtensorMap tmap, const float2 *__restric
         __syncthreads();   // buffer `buf`, its taps and hA / hB are rewritten from the next tile on
     }
     // a block that stopped on a failed wait leaves no copy in flight behind
-    // (bounded): the other buffer's copy, if one was issued
+    // (bounded waits): the copy it gave up on, and the other buffer's if one
+    // was issued for the next tile
     if (fail_sh) {
-        fir_mbar_wait(smem_addr(&sm.bar[buf ^ 1]), (phases >> (buf ^ 1)) & 1u);
+        fir_mbar_wait(smem_addr(&sm.bar[buf]), ((phases >> buf) & 1u) ^ 1u);
+        if (tile + (int)gridDim.x < n_tiles)
+            fir_mbar_wait(smem_addr(&sm.bar[buf ^ 1]), (phases >> (buf ^ 1)) & 1u);
         if (tid == 0) atomicOr(&g_fir_err, 1u);
     }
 }
