@@ -1321,8 +1321,8 @@ def run_serving(args):
 # ---- learned demapper (MLP 4 -> 128 -> 128 -> 6) on the same chain ------------
 # Adam at lr 1e-3; the last `decay_epochs` epochs run at lr_final (a step
 # schedule that lets the network settle; 0 keeps the rate constant)
-LEARN = dict(train_streams=16, train_sym=(1 << 18) + (1 << 14), skip=1 << 14, epochs=40, batch=8192,
-             lr=1e-3, lr_final=1e-4, decay_epochs=10, infer_streams=16, infer_sym=1 << 20, esn0=(8.0, 16.0),
+LEARN = dict(train_streams=16, train_sym=(1 << 18) + (1 << 14), skip=1 << 14, epochs=80, batch=8192,
+             lr=1e-3, lr_final=1e-4, decay_epochs=20, infer_streams=16, infer_sym=1 << 20, esn0=(8.0, 16.0),
              init_seed=2108070044)
 
 
@@ -1424,6 +1424,7 @@ def run_learned(args):
         "gmi_gap_mean": float(np.mean(ge - gl)), "gmi_gap_max": float(np.max(ge - gl)),
         "ber_delta_rel_max": float(np.max(np.abs(bl - be) / np.maximum(be, 1e-12))),
         "gmi_exact": [round(float(v), 5) for v in ge], "gmi_learned": [round(float(v), 5) for v in gl],
+        "ber_exact": [float(f"{v:.4g}") for v in be], "ber_learned": [float(f"{v:.4g}") for v in bl],
         "train_seconds": train_s, "train_loss_per_epoch": [round(float(v), 6) for v in losses],
     }
     print(json.dumps(line), flush=True)
