@@ -517,7 +517,9 @@ cudaError_t launch_fir_ex(const void *x, long ns, const float2 *taps, long k0, l
                                    const_cast<void *>(x), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
                                    CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    // a map the driver refuses leaves the cp.async form (the same results)
+    if (r != CUDA_SUCCESS)
+        return launch_fir(x, ns, taps, k0, k1, y, y_stride, y_off, n_streams, T, st, sk, sm_avail, wl);
     if (wl) {
         switch (sk) {
             case SK_F32: return fir_tma_t<SK_F32, true>(tm, taps, k0, k1, y, y_stride, y_off, T, grid, tps, n_tiles, st);
