@@ -148,6 +148,7 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
             }
             const int slot = (jc + 1) % RX_NCHUNK;
             const int hb = B >> 1;
+            const float yq1 = (yn0 + yn1) + 2.f * f.orbe[0];      // one-orbit tables
             if constexpr (kBig) {
                 // passes of eight phase pairs; per orbit pair the
                 // correlations of both polarisations, then the phase pairs'
@@ -259,6 +260,17 @@ bps_kernel(const void *__restrict__ y, long y_stride, long a, long e, long n_val
                     }
                     md = yn0 + a0;
                     md2 = yn0 + a1;
+                } else if (NORB == 1) {
+                    // one orbit (QPSK): no minimum over orbits, so both
+                    // polarisations' distances share one sum, |y_X|^2 +
+                    // |y_Y|^2 + 2 e - 2 (v_X + v_Y)
+                    float P0, Q0, P1, Q1, v0, u0, v1, u1;
+                    upk2(fma2(S1, CI[0][0], mul2(C1, CR[0][0])), P0, Q0);
+                    upk2(fma2(S1, CI[1][0], mul2(C1, CR[1][0])), P1, Q1);
+                    orbit_vu<SS>(P0, Q0, v0, u0);
+                    orbit_vu<SS>(P1, Q1, v1, u1);
+                    md = fmaf(OrbitCoef<SS>::cv, v0 + v1, yq1);
+                    md2 = fmaf(OrbitCoef<SS>::cu, u0 + u1, yq1);
                 } else {
                     float x0 = 3.0e38f, x1 = 3.0e38f, w0 = 3.0e38f, w1 = 3.0e38f;
     #pragma unroll
