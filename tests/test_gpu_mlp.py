@@ -178,3 +178,17 @@ def test_chain_with_learned_demapper_and_symbol_output(S):
         assert torch.equal(learned[s], want), s
         hard = (learned[s, c0:c1].cpu().numpy() < 0).astype(np.uint8)
         assert st_l[s]["bit_errors"] == int(np.sum(hard != sts[s].bits[c0:c1])), s
+
+
+def test_mlp_kernel_path_parameters_are_validated():
+    """rx_mlp_set_param takes "train_tc" in {0, 1} and "infer" in {1, 2};
+    other keys and values are refused and leave the setting unchanged."""
+    rx = _rx()
+    m = rx.Mlp(_params(21))
+    assert m.get_param("train_tc") == 1 and m.get_param("infer") == 2
+    for key, value in (("train_tc", 2), ("infer", 0), ("infer", 3), ("unknown", 1)):
+        with pytest.raises(rx.RxError):
+            m.set_param(key, value)
+    assert m.get_param("train_tc") == 1 and m.get_param("infer") == 2
+    m.set_param("infer", 1)
+    assert m.get_param("infer") == 1

@@ -191,3 +191,25 @@ def test_reused_handle_without_reference_forgets_the_previous_one(streams):
     assert state == rx.REQ_DONE
     assert stats_a["n_sym"] == 0 and stats["n_sym"] == 0 and stats["bit_errors"] == 0
     assert np.array_equal(llr.cpu().numpy(), llr_a.cpu().numpy())
+
+
+def test_issue_settings_are_validated(streams):
+    """The handle's "issue" takes 0, 1 or 2 and "fir_tma" 0 or 1; the
+    server's "issue" the same and "issue_threads" 1 .. 64; anything else is
+    refused."""
+    from paper_2108_07004_gb300 import rx
+    r = rx.Receiver("dp_qpsk", cd_ps_per_nm=1360.0, taps=15, bps_phases=32)
+    for key, good, bad in (("issue", (0, 1, 2), (3, -1, 0.5)), ("fir_tma", (0, 1), (2,))):
+        for v in good:
+            r.set(key, v)
+            assert r.get(key) == v
+        for v in bad:
+            with pytest.raises(rx.RxError):
+                r.set(key, v)
+    srv = rx.Server(1 << 30, 4)
+    srv.set_param("issue", 2)
+    srv.set_param("issue_threads", 3)
+    for key, v in (("issue", 5), ("issue_threads", 0), ("issue_threads", 65), ("nothing", 1)):
+        with pytest.raises(rx.RxError):
+            srv.set_param(key, v)
+    srv.close()
