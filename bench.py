@@ -1272,15 +1272,15 @@ def run_serving(args):
         w_, _, _, _ = serve(np.zeros(len(reqs)))
         cap_by_issue[str(mode)] = total_bits / w_ / 1e9
         host_by_issue[str(mode)] = {"wall_ms": w_ * 1e3, "host_ms_in_step": host_ms[0]}
-    # the same in mode 1 with 1 / 2 / 4 host issue threads
+    # the same in mode 1 with 1 / 2 / 4 / 8 host issue threads
     cap_by_threads = {}
     srv.set_param("issue", 1)
-    for nt in (1, 2, 4):
+    for nt in (1, 2, 4, 8):
         srv.set_param("issue_threads", nt)
         serve(np.zeros(len(reqs)))
         w_, _, _, _ = serve(np.zeros(len(reqs)))
         cap_by_threads[str(nt)] = total_bits / w_ / 1e9
-    srv.set_param("issue_threads", min(8, os.cpu_count() or 1))
+    srv.set_param("issue_threads", min(2, os.cpu_count() or 1))
     srv.set_param("issue", SERVE["issue"])
     for _ in range(max(1, args.warmup)):
         serve(np.zeros(len(reqs)))

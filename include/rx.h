@@ -459,8 +459,8 @@ typedef struct {
  * the next request with the same format, symbol rate, sps, taps and test
  * phases, so that no device memory is freed while others run; idle handles
  * count against the budget and are destroyed when room is needed), and
- * every step issues (from up to eight host threads of the library, one
- * request's blocks always from one thread) one
+ * every step issues (from up to "issue_threads" host threads of the library,
+ * one request's blocks always from one thread) one
  * block of every running request, so requests that arrived at different
  * times overlap on the device (the paper's multiple processing streams,
  * Sec. 2); by default a request's launches all go on its own stream
@@ -484,7 +484,7 @@ int rx_server_run(rx_server *s);
 /* State (RX_REQ_*) of a request and, once done, its statistics. */
 int rx_server_poll(rx_server *s, uint64_t id, int *state, rx_stats *stats);
 /* Server settings: "issue" [1], the issue mode of the requests' handles
- * (rx_set_param "issue"); "issue_threads" [hardware threads, at most 8],
+ * (rx_set_param "issue"); "issue_threads" [2, or 1 on a one-core host],
  * the host threads that issue a step's blocks.  RX_EINVAL otherwise. */
 int rx_server_set_param(rx_server *s, const char *key, double value);
 /* Memory in use, the most requests ever running at once, steps taken. */

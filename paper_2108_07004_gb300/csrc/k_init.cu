@@ -20,7 +20,29 @@ __global__ void stream_init_kernel(StreamDev *__restrict__ sd, int S, int B) {
     sd[s] = v;
 }
 
+constexpr double kPiD = 3.14159265358979323846;
+constexpr double kCD = 299792458.0;
+
+__global__ void cd_response_kernel(float2 *__restrict__ H, const double *__restrict__ mag, int n, double fs,
+                                   double dl, double wl) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const double f = (k < n / 2 ? k : k - n) * fs / n;
+    const double w = 2 * kPiD * f;
+    const double ph = -dl * wl * wl * w * w / (4 * kPiD * kCD);
+    double sn, cs;
+    sincos(ph, &sn, &cs);
+    H[k] = make_float2((float)(mag[k] * cs), (float)(mag[k] * sn));
+}
+
 }  // namespace
+
+cudaError_t launch_cd_response(float2 *H, const double *mag, int n, double fs, double dl, double wavelength,
+                               cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    cd_response_kernel<<<(n + 255) / 256, 256, 0, st>>>(H, mag, n, fs, dl, wavelength);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_center_spike(float2 *taps, int S, int L, int D, cudaStream_t st) {
     const int n = S * 4 * L;

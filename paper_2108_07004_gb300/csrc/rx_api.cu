@@ -160,8 +160,13 @@ struct rx_handle {
     // side (r = 0) or side_x[r - 1]
     int lms_start = 0;
     cudaStream_t side_x[3] = {nullptr, nullptr, nullptr};
-    // device tables
+    // device tables: the CDC response H (per dispersion, formed on the
+    // device), the twiddles tw (per FFT size) and the matched filter's
+    // magnitude with 1/n_fft (per FFT size, sample rate and roll-off)
     float2 *H = nullptr, *tw = nullptr;
+    double *Hmag = nullptr;
+    double mag_key[5] = {0, 0, 0, 0, -1};
+    cudaEvent_t ev_tab = nullptr;
     // the tensor-core phase search (parameter "bps_tc", default on where the
     // format allows): its B operand, built for the table and B test phases
     int bps_tc = 0;
@@ -407,27 +412,42 @@ int upload_tables(rx_handle *h) {
     }
     if (!h->tables_dirty && h->tab_fft == h->n_fft) return RX_OK;
     const int n = h->n_fft;
-    std::vector<float2> H(n), tw(n);
     const double fs = h->sps * h->symbol_rate;
-    const double dl = h->cd * 1e-3;   // ps/nm -> s/m
-    for (int k = 0; k < n; ++k) {
-        const double f = (k < n / 2 ? k : k - n) * fs / n;
-        const double w = 2 * kPi * f;
-        const double ph = -dl * h->wavelength * h->wavelength * w * w / (4 * kPi * kC);   // conj(H_CD)
-        const double mag = (h->matched_filter ? std::sqrt(h->sps * raised_cosine(f, h->symbol_rate, h->rolloff)) : 1.0) / n;
-        H[k] = make_float2((float)(mag * std::cos(ph)), (float)(mag * std::sin(ph)));
-        tw[k] = make_float2((float)std::cos(2 * kPi * k / n), (float)(-std::sin(2 * kPi * k / n)));
-    }
     if (h->tab_fft != n) {
         cudaFree(h->H);
         cudaFree(h->tw);
+        cudaFree(h->Hmag);
         h->H = h->tw = nullptr;
+        h->Hmag = nullptr;
         CK(cudaMalloc(&h->H, sizeof(float2) * n));
         CK(cudaMalloc(&h->tw, sizeof(float2) * n));
+        CK(cudaMalloc(&h->Hmag, sizeof(double) * n));
+        std::vector<float2> tw(n);
+        for (int k = 0; k < n; ++k)
+            tw[k] = make_float2((float)std::cos(2 * kPi * k / n), (float)(-std::sin(2 * kPi * k / n)));
+        CK(cudaMemcpy(h->tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
         h->tab_fft = n;
+        h->mag_key[4] = -1;
     }
-    CK(cudaMemcpy(h->H, H.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(h->tw, tw.data(), sizeof(float2) * n, cudaMemcpyHostToDevice));
+    const double key[5] = {fs, h->symbol_rate, h->rolloff, h->matched_filter ? 1.0 : 0.0, (double)n};
+    if (std::memcmp(key, h->mag_key, sizeof key) != 0) {
+        std::vector<double> mag(n);
+        for (int k = 0; k < n; ++k) {
+            const double f = (k < n / 2 ? k : k - n) * fs / n;
+            mag[k] = (h->matched_filter ? std::sqrt(h->sps * raised_cosine(f, h->symbol_rate, h->rolloff)) : 1.0) / n;
+        }
+        CK(cudaMemcpy(h->Hmag, mag.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+        std::memcpy(h->mag_key, key, sizeof key);
+    }
+    // the dispersion phase on the device (a request's new link costs one
+    // small kernel, not a host loop and a synchronous copy)
+    CK(launch_cd_response(h->H, h->Hmag, n, fs, h->cd * 1e-3, h->wavelength, h->st));
+    if (h->cst) {
+        // the host entry's CDC of later groups runs on its own stream
+        if (!h->ev_tab) CK(cudaEventCreateWithFlags(&h->ev_tab, cudaEventDisableTiming));
+        CK(cudaEventRecord(h->ev_tab, h->st));
+        CK(cudaStreamWaitEvent(h->cst, h->ev_tab, 0));
+    }
     h->tables_dirty = false;
     return RX_OK;
 }
@@ -1325,6 +1345,8 @@ void rx_destroy(rx_handle *h) {
     cudaFree(h->s2sym);
     cudaFree(h->H);
     cudaFree(h->tw);
+    cudaFree(h->Hmag);
+    if (h->ev_tab) cudaEventDestroy(h->ev_tab);
     cudaFree(h->bps_w);
     cudaFree(h->ref);
     cudaFree(h->d_in);
