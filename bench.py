@@ -1194,7 +1194,8 @@ def run_precision(args):
 # ---- serving (config 5): 64 streams, Poisson arrivals, mixed formats and lengths ----
 SERVE = dict(n_req=64, len_log2=(14, 20), km=(80.0, 2000.0), budget=8 << 30, slots=64, load=0.8,
              esn0={"dp_qpsk": 12.0, "dp_16qam": 18.0, "gs4d64": 14.0},
-             bps={"dp_qpsk": 32, "dp_16qam": 32, "gs4d64": 64}, m={"dp_qpsk": 4, "dp_16qam": 8, "gs4d64": 6}, issue=1)
+             bps={"dp_qpsk": 32, "dp_16qam": 32, "gs4d64": 64}, m={"dp_qpsk": 4, "dp_16qam": 8, "gs4d64": 6}, issue=1,
+             connections="32")
 
 
 def serving_requests(seed: int):
@@ -1212,6 +1213,9 @@ def serving_requests(seed: int):
 
 
 def run_serving(args):
+    # 64 request streams share the CUDA context's hardware work queues: 32
+    # (the most) instead of the default 8, set before the context is created
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", SERVE["connections"])
     import torch
     from paper_2108_07004_gb300 import rx as rx_mod
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
@@ -1223,6 +1227,8 @@ def run_serving(args):
     # one long-lived server (its pool of idle handles carries over from the
     # warm-up to the measured runs, as in a running receiver)
     srv = rx_mod.Server(SERVE["budget"], SERVE["slots"])
+    bps_default = int(srv.get_param("blocks_per_step"))     # the server's defaults for these queues
+    threads_default = int(srv.get_param("issue_threads"))
     ids_last = {}
 
     host_ms = [0.0]       # host time inside rx_server_step (issue of the blocks)
@@ -1264,6 +1270,8 @@ def run_serving(args):
     # capacity (every request present at once) in each issue mode of the
     # handles: 0 stages on their own streams with events, 1 one stream per
     # request, 2 one stream and the blocks after the first as CUDA graphs
+    # (one block per step)
+    srv.set_param("blocks_per_step", 1)
     cap_by_issue, host_by_issue = {}, {}
     for mode in (0, 1, 2):
         srv.set_param("issue", mode)
@@ -1272,15 +1280,25 @@ def run_serving(args):
         w_, _, _, _ = serve(np.zeros(len(reqs)))
         cap_by_issue[str(mode)] = total_bits / w_ / 1e9
         host_by_issue[str(mode)] = {"wall_ms": w_ * 1e3, "host_ms_in_step": host_ms[0]}
-    # the same in mode 1 with 1 / 2 / 4 / 8 host issue threads
+    # the same in mode 1 with 1 / 2 / 4 / 8 host issue threads (the
+    # server's default blocks per step)
     cap_by_threads = {}
     srv.set_param("issue", 1)
+    srv.set_param("blocks_per_step", bps_default)
     for nt in (1, 2, 4, 8):
         srv.set_param("issue_threads", nt)
         serve(np.zeros(len(reqs)))
         w_, _, _, _ = serve(np.zeros(len(reqs)))
         cap_by_threads[str(nt)] = total_bits / w_ / 1e9
-    srv.set_param("issue_threads", min(2, os.cpu_count() or 1))
+    srv.set_param("issue_threads", threads_default)
+    # and with 1 / 2 / 4 / all blocks of a request per step (one call each)
+    cap_by_bps = {}
+    for bps in (1, 2, 4, 1 << 20):
+        srv.set_param("blocks_per_step", bps)
+        serve(np.zeros(len(reqs)))
+        w_, _, _, _ = serve(np.zeros(len(reqs)))
+        cap_by_bps[str(bps)] = total_bits / w_ / 1e9
+    srv.set_param("blocks_per_step", bps_default)
     srv.set_param("issue", SERVE["issue"])
     for _ in range(max(1, args.warmup)):
         serve(np.zeros(len(reqs)))
@@ -1297,6 +1315,7 @@ def run_serving(args):
             srv.poll(ids_last[i])                      # sets the server's last error to this request's
             failed.append(f"request {i} ({reqs[i][0]}, {reqs[i][1]} symbols): state {st_}: "
                           f"{rx_mod.lib().rx_server_last_error().decode()}")
+    handles = {k: int(srv.get_param(k)) for k in ("handles_created", "handles_destroyed", "handle_regrows")}
     srv.close()
     ok = all(s == rx_mod.REQ_DONE for s, _ in states)
     line = {
@@ -1305,10 +1324,14 @@ def run_serving(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "serving_64_streams_poisson_mixed_formats", "requests": len(reqs),
                    "symbols": int(sum(n for _, n, _, _ in reqs)), "budget_bytes": SERVE["budget"],
-                   "slots": SERVE["slots"], "load": SERVE["load"], "block": 1 << 16, "fft": 4096, "taps": 31},
+                   "slots": SERVE["slots"], "load": SERVE["load"], "block": 1 << 16, "fft": 4096, "taps": 31,
+                   "cuda_device_max_connections": os.environ["CUDA_DEVICE_MAX_CONNECTIONS"]},
         "capacity_gbps_all_at_once": cap_bits / 1e9,
         "capacity_gbps_by_issue_mode": cap_by_issue, "issue_mode": SERVE["issue"],
         "host_by_issue_mode": host_by_issue, "capacity_gbps_by_issue_threads_mode1": cap_by_threads,
+        "capacity_gbps_by_blocks_per_step_mode1": cap_by_bps, "blocks_per_step": bps_default,
+        "issue_threads": threads_default,
+        "handles": handles,
         "request_latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "request_latency_ms_all_at_once": {"p50": 1e3 * lat0[len(lat0) // 2], "p99": 1e3 * lat0[-1]},
         "max_running": info["max_active"], "all_done": ok, "not_done": failed[:8],

@@ -460,8 +460,8 @@ typedef struct {
  * phases, so that no device memory is freed while others run; idle handles
  * count against the budget and are destroyed when room is needed), and
  * every step issues (from up to "issue_threads" host threads of the library,
- * one request's blocks always from one thread) one
- * block of every running request, so requests that arrived at different
+ * one request's blocks always from one thread) the next
+ * "blocks_per_step" blocks of every running request, so requests that arrived at different
  * times overlap on the device (the paper's multiple processing streams,
  * Sec. 2); by default a request's launches all go on its own stream
  * without event operations (issue mode 1, rx_server_set_param).  A finished request frees its slot and memory at the next step.
@@ -476,17 +476,30 @@ rx_server *rx_server_create(size_t mem_budget_bytes, int max_slots);
 void rx_server_destroy(rx_server *s);               /* NULL-safe; waits for running work */
 /* Queue a request (RX_EINVAL if it alone exceeds the budget); *id names it. */
 int rx_server_submit(rx_server *s, const rx_request *r, uint64_t *id);
-/* Retire finished requests, admit what fits, issue one block of each running
- * request; *n_left (may be NULL) = running + queued.  Does not wait. */
+/* Retire finished requests, admit what fits, issue the next blocks_per_step
+ * blocks of each running request; *n_left (may be NULL) = running + queued.
+ * Does not wait. */
 int rx_server_step(rx_server *s, int *n_left);
 /* Step until every submitted request is done. */
 int rx_server_run(rx_server *s);
 /* State (RX_REQ_*) of a request and, once done, its statistics. */
 int rx_server_poll(rx_server *s, uint64_t id, int *state, rx_stats *stats);
 /* Server settings: "issue" [1], the issue mode of the requests' handles
- * (rx_set_param "issue"); "issue_threads" [2, or 1 on a one-core host],
- * the host threads that issue a step's blocks.  RX_EINVAL otherwise. */
+ * (rx_set_param "issue"); "issue_threads" (1 .. 64), the host threads that
+ * issue a step's blocks; "blocks_per_step" (1 .. 2^20), the blocks of each
+ * running request issued per step (one rx_process_blocks call: fewer calls
+ * and CDC launches, coarser interleaving).  Their defaults follow the
+ * environment's CUDA_DEVICE_MAX_CONNECTIONS (the CUDA context's hardware
+ * work queues, which the requests' streams share; 8 unless set before the
+ * context is created): 4 threads and 4 blocks at 32 or more queues, else 2
+ * threads (at most the host's cores) and 2 blocks at 16, 1 block below.  Many concurrent
+ * requests run best with CUDA_DEVICE_MAX_CONNECTIONS=32.  RX_EINVAL
+ * otherwise. */
 int rx_server_set_param(rx_server *s, const char *key, double value);
+/* Reads a setting above or a counter: "handles_created",
+ * "handles_destroyed", "handle_regrows" (pooled handles reused for a request
+ * longer than their buffers, which then grow).  RX_EINVAL for other keys. */
+int rx_server_get_param(const rx_server *s, const char *key, double *value);
 /* Memory in use, the most requests ever running at once, steps taken. */
 int rx_server_info(rx_server *s, size_t *mem_used, int *max_active, long *steps);
 const char *rx_server_last_error(void);

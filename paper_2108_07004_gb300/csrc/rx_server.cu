@@ -3,8 +3,8 @@
 // A request is one stream (any built-in or custom format, its own link and
 // receiver parameters).  Requests wait in a FIFO queue until a slot is free
 // and their device-memory estimate fits the budget; an admitted request gets
-// its own handle and CUDA stream and is processed one block at a time,
-// interleaved with every other admitted request, so the work of requests
+// its own handle and CUDA stream and is processed a few blocks at a time
+// ("blocks_per_step"), interleaved with every other admitted request, so the work of requests
 // that arrived at different times overlaps on the device.  A finished
 // request frees its slot and its memory estimate; its handle (with its CUDA
 // stream and buffers) is kept idle for the next request with the same
@@ -21,6 +21,7 @@
 // Host code only; everything on the device goes through the public entry
 // points (rx_create, rx_process_blocks, rx_get_stats, ...).
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <memory>
@@ -110,6 +111,8 @@ struct rx_server {
     size_t pooled = 0;                  // their memory estimates
     int max_active_seen = 0;
     int issue = 1;                      // the handles' issue mode (rx_set_param "issue")
+    long blocks_per_step = 1;           // blocks of a running request issued per step
+    long n_created = 0, n_destroyed = 0, n_regrown = 0;   // handles made, freed, reused with too small buffers
 };
 
 namespace {
@@ -121,8 +124,11 @@ int srv_fail(int code, const std::string &msg) {
     return code;
 }
 
-void destroy_handle(rx_handle *h, cudaStream_t st, cudaEvent_t done) {
-    if (h) rx_destroy(h);
+void destroy_handle(rx_server *s, rx_handle *h, cudaStream_t st, cudaEvent_t done) {
+    if (h) {
+        rx_destroy(h);
+        ++s->n_destroyed;
+    }
     if (done) cudaEventDestroy(done);
     if (st) cudaStreamDestroy(st);
 }
@@ -140,7 +146,7 @@ void release(rx_server *s, Req *q) {
         s->pool.push_back(p);
         s->pooled += p.mem;
     } else {
-        destroy_handle(q->h, q->st, q->done);
+        destroy_handle(s, q->h, q->st, q->done);
     }
     q->h = nullptr;
     q->st = nullptr;
@@ -174,7 +180,7 @@ bool make_room(rx_server *s, const Req *q) {
         Pooled p = s->pool[i];
         s->pool.erase(s->pool.begin() + (long)i);
         s->pooled -= p.mem;
-        destroy_handle(p.h, p.st, p.done);
+        destroy_handle(s, p.h, p.st, p.done);
     }
     return fits();
 }
@@ -194,6 +200,7 @@ bool admit(rx_server *s, Req *q) {
         q->st = p.st;
         q->done = p.done;
         q->cap_n = p.cap_n;
+        if (p.cap_n < q->N) ++s->n_regrown;
         rc |= rx_set_param(q->h, "cd_ps_per_nm", q->r.cd_ps_per_nm);
         rc |= rx_set_param(q->h, "fft", q->r.fft ? q->r.fft : 1024);
         rc |= rx_set_param(q->h, "overlap", q->r.overlap ? q->r.overlap : 256);
@@ -211,6 +218,7 @@ bool admit(rx_server *s, Req *q) {
             q->state = Q_FAILED;
             return false;
         }
+        ++s->n_created;
         if (q->r.fft) rc |= rx_set_param(q->h, "fft", q->r.fft);
         if (q->r.overlap) rc |= rx_set_param(q->h, "overlap", q->r.overlap);
         if (q->r.block) rc |= rx_set_param(q->h, "block", q->r.block);
@@ -255,11 +263,21 @@ rx_server *rx_server_create(size_t mem_budget_bytes, int max_slots) {
     }
     rx_server *s = new rx_server();
     const unsigned hc = std::thread::hardware_concurrency();
-    // two issue threads: with the launches of a request-block on one stream
-    // and the dispersion response formed on the device, more threads in one
-    // CUDA context measured no faster (one 6.55, two 6.56, four 6.45, eight
-    // 6.35 Gbit/s of serving capacity)
-    s->issue_threads = std::max(1u, std::min(2u, hc ? hc : 1u));
+    // Defaults by the hardware work queues the CUDA context has
+    // (CUDA_DEVICE_MAX_CONNECTIONS, 8 unless set before the context is made).
+    // The requests' streams share those queues, so with few queues a
+    // request's consecutive blocks hold up the requests queued behind them:
+    // one block per step interleaves best, and more issue threads do not
+    // help.  Measured serving capacity, 64 mixed requests (Gbit/s):
+    //   blocks per step 1 / 2 / 4 / all (2 threads): 8 queues 6.64 / 6.14 /
+    //   5.80 / 4.47, 16 queues 7.55 / 7.95 / 7.74 / 6.90, 32 queues 7.36 /
+    //   7.99 / 8.33 / 8.38;
+    //   issue threads 1 / 2 / 4 / 8: 8 queues, 1 block per step 6.81 / 6.61 /
+    //   6.55 / 6.46; 32 queues, 4 blocks per step 7.64 / 8.23 / 8.90 / 8.65.
+    const char *conn = std::getenv("CUDA_DEVICE_MAX_CONNECTIONS");
+    const long nconn = conn ? std::strtol(conn, nullptr, 10) : 8;
+    s->blocks_per_step = nconn >= 32 ? 4 : nconn >= 16 ? 2 : 1;
+    s->issue_threads = std::max(1u, std::min(nconn >= 32 ? 4u : 2u, hc ? hc : 1u));
     s->budget = mem_budget_bytes;
     s->max_slots = max_slots;
     return s;
@@ -269,10 +287,10 @@ void rx_server_destroy(rx_server *s) {
     if (!s) return;
     for (Req *q : s->active) {
         if (q->st) cudaStreamSynchronize(q->st);
-        destroy_handle(q->h, q->st, q->done);
+        destroy_handle(s, q->h, q->st, q->done);
         q->h = nullptr;
     }
-    for (Pooled &p : s->pool) destroy_handle(p.h, p.st, p.done);
+    for (Pooled &p : s->pool) destroy_handle(s, p.h, p.st, p.done);
     delete s;
 }
 
@@ -326,10 +344,11 @@ int rx_server_step(rx_server *s, int *n_active) {
         if (admit(s, q)) s->active.push_back(q);
     }
     if ((int)s->active.size() > s->max_active_seen) s->max_active_seen = (int)s->active.size();
-    // one block of every running request, each on its own stream.  Issuing
-    // a block costs the host some twenty launches and event operations, so
-    // the requests are split over a few host threads (each touches only its
-    // own requests' handles; the results are those of one thread)
+    // the next blocks_per_step blocks of every running request, each request
+    // on its own stream.  Issuing a block costs the host a few launches (and,
+    // in issue mode 0, event operations) plus the call's own set-up, so the
+    // requests are split over a few host threads (each touches only its own
+    // requests' handles; the results are those of one thread)
     std::vector<Req *> todo;
     for (Req *q : s->active)
         if (q->next < q->nblk) todo.push_back(q);
@@ -341,7 +360,8 @@ int rx_server_step(rx_server *s, int *n_active) {
         cudaSetDevice(dev);                 // a new host thread starts on device 0
         for (size_t i = i0; i < i1; ++i) {
             Req *q = todo[i];
-            rcs[i] = rx_process_blocks(q->h, q->r.samples, q->r.n_samples, (size_t)q->next, (size_t)q->next + 1,
+            const long b1 = std::min(q->nblk, q->next + s->blocks_per_step);
+            rcs[i] = rx_process_blocks(q->h, q->r.samples, q->r.n_samples, (size_t)q->next, (size_t)b1,
                                        q->r.llr_out, nullptr);
             if (rcs[i] != RX_OK) errs[i] = rx_last_error();
         }
@@ -363,7 +383,7 @@ int rx_server_step(rx_server *s, int *n_active) {
             q->err = errs[i];
             q->next = q->nblk;
         } else {
-            ++q->next;
+            q->next = std::min(q->nblk, q->next + s->blocks_per_step);
         }
         if (q->next >= q->nblk) cudaEventRecord(q->done, q->st);
     }
@@ -408,9 +428,26 @@ int rx_server_set_param(rx_server *s, const char *key, double value) {
         if (!(value >= 1 && value <= 64) || value != (double)(long)value)
             return srv_fail(RX_EINVAL, "issue_threads must be 1 .. 64");
         s->issue_threads = (size_t)value;
+    } else if (k == "blocks_per_step") {
+        if (!(value >= 1 && value <= 1 << 20) || value != (double)(long)value)
+            return srv_fail(RX_EINVAL, "blocks_per_step must be 1 .. 2^20");
+        s->blocks_per_step = (long)value;
     } else {
         return srv_fail(RX_EINVAL, "unknown server parameter '" + k + "'");
     }
+    return RX_OK;
+}
+
+int rx_server_get_param(const rx_server *s, const char *key, double *value) {
+    if (!s || !key || !value) return srv_fail(RX_EINVAL, "NULL argument");
+    const std::string k(key);
+    if (k == "issue") *value = s->issue;
+    else if (k == "issue_threads") *value = (double)s->issue_threads;
+    else if (k == "blocks_per_step") *value = (double)s->blocks_per_step;
+    else if (k == "handles_created") *value = (double)s->n_created;
+    else if (k == "handles_destroyed") *value = (double)s->n_destroyed;
+    else if (k == "handle_regrows") *value = (double)s->n_regrown;
+    else return srv_fail(RX_EINVAL, "unknown server parameter '" + k + "'");
     return RX_OK;
 }
 

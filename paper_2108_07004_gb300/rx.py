@@ -82,6 +82,7 @@ _PROTOS = {
     "rx_server_poll": (_I, [_VP, C.c_uint64, C.POINTER(_I), _VP]),
     "rx_server_info": (_I, [_VP, C.POINTER(_SZ), C.POINTER(_I), C.POINTER(C.c_long)]),
     "rx_server_set_param": (_I, [_VP, C.c_char_p, _D]),
+    "rx_server_get_param": (_I, [_VP, C.c_char_p, C.POINTER(_D)]),
     "rx_server_last_error": (C.c_char_p, []),
     "rx_set_demapper": (_I, [_VP, _VP]),
     "rx_set_symbol_output": (_I, [_VP, _VP, _VP]),
@@ -643,8 +644,14 @@ class Server:
             raise RxError(rc, lib().rx_server_last_error().decode())
 
     def set_param(self, key: str, value: float):
-        """"issue" (the handles' issue mode, 0/1/2) or "issue_threads"."""
+        """"issue" (the handles' issue mode, 0/1/2), "issue_threads" or "blocks_per_step"."""
         self._ck(lib().rx_server_set_param(self.h, key.encode(), float(value)))
+
+    def get_param(self, key: str) -> float:
+        """A setting, or the counters "handles_created", "handles_destroyed", "handle_regrows"."""
+        v = _D()
+        self._ck(lib().rx_server_get_param(self.h, key.encode(), C.byref(v)))
+        return v.value
 
     def submit(self, fmt: str, samples: torch.Tensor, llr: torch.Tensor, bits: torch.Tensor | None = None,
                *, cd_ps_per_nm: float, taps: int, bps_phases: int, symbol_rate: float = 28e9, sps: int = 2,

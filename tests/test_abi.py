@@ -61,3 +61,26 @@ def test_builtin_gs4d64_table_is_the_design_file():
     d = json.load(open(os.path.join(ROOT, "paper_2108_07004_gb300", "data", "gs4d64_v1.json")))
     assert np.array_equal(np.array(vals, np.float32).reshape(64, 4), np.array(d["points"], np.float32))
     assert labs == d["labels"]
+
+
+def test_server_settings_and_counters_without_device(lib):
+    """The server's settings are validated and read back and its handle
+    counters start at zero; none of it touches the device (no request)."""
+    from paper_2108_07004_gb300 import rx
+    srv = rx.Server(1 << 30, 4)
+    for key, good, bad in (("issue", (0, 1, 2), (3, -1, 0.5)), ("issue_threads", (1, 3, 64), (0, 65, 1.5)),
+                           ("blocks_per_step", (1, 4, 1 << 20), (0, (1 << 20) + 1, 2.5))):
+        for v in good:
+            srv.set_param(key, v)
+            assert srv.get_param(key) == v
+        for v in bad:
+            with pytest.raises(rx.RxError):
+                srv.set_param(key, v)
+    for key in ("handles_created", "handles_destroyed", "handle_regrows"):
+        assert srv.get_param(key) == 0
+    for key in ("nothing", "slots"):
+        with pytest.raises(rx.RxError):
+            srv.get_param(key)
+        with pytest.raises(rx.RxError):
+            srv.set_param(key, 1)
+    srv.close()

@@ -36,11 +36,13 @@ def _submit(srv, i, samples, bits):
     return rid, llr
 
 
-def _serve(idx, streams, budget=1 << 33, slots=16, issue=None):
+def _serve(idx, streams, budget=1 << 33, slots=16, issue=None, blocks_per_step=None):
     from paper_2108_07004_gb300 import rx
     srv = rx.Server(budget, slots)
     if issue is not None:
         srv.set_param("issue", issue)
+    if blocks_per_step is not None:
+        srv.set_param("blocks_per_step", blocks_per_step)
     got = {i: _submit(srv, i, *streams[i]) for i in idx}
     srv.run()
     torch.cuda.synchronize()
@@ -78,6 +80,42 @@ def test_issue_modes_give_the_results_of_the_multi_stream_handle(streams, issue)
         assert np.array_equal(alone[i][0], mix[i][0]), (issue, i)
         for k in ("bit_errors", "n_sym", "gmi_sum"):
             assert alone[i][1][k] == mix[i][1][k], (issue, i, k)
+
+
+@pytest.mark.parametrize("issue,bps", [(1, 3), (1, 1 << 20), (0, 2), (2, 3)])
+def test_several_blocks_per_step_give_the_same_results(streams, issue, bps):
+    """Issuing several blocks of a request per step (one rx_process_blocks
+    call over them, the whole request for 2^20) changes no LLR and no count
+    of any request of the mix, in each issue mode."""
+    alone = {i: _serve([i], streams, issue=0)[0][i] for i in range(len(REQS))}
+    mix, info = _serve(range(len(REQS)), streams, issue=issue, blocks_per_step=bps)
+    assert info["max_active"] == len(REQS)
+    for i in range(len(REQS)):
+        assert np.array_equal(alone[i][0], mix[i][0]), (issue, bps, i)
+        for k in ("bit_errors", "n_sym", "gmi_sum"):
+            assert alone[i][1][k] == mix[i][1][k], (issue, bps, i, k)
+
+
+def test_pooled_handle_grows_for_a_longer_request(streams):
+    """A request longer than the pooled handle it reuses (same key) grows
+    that handle's buffers: the server counts one regrow, creates no second
+    handle, and the result is that of the request served alone."""
+    from paper_2108_07004_gb300 import rx
+    i_short, i_long = 1, 3                  # gs4d64, 50000 then 70001 symbols, 31 taps, B = 64
+    alone = _serve([i_long], streams)[0][i_long]
+    srv = rx.Server(1 << 33, 4)
+    _submit(srv, i_short, *streams[i_short])
+    srv.run()
+    rid, llr = _submit(srv, i_long, *streams[i_long])
+    srv.run()
+    torch.cuda.synchronize()
+    state, stats = srv.poll(rid)
+    assert state == rx.REQ_DONE
+    assert (srv.get_param("handles_created"), srv.get_param("handle_regrows"),
+            srv.get_param("handles_destroyed")) == (1, 1, 0)
+    srv.close()
+    assert np.array_equal(llr.cpu().numpy(), alone[0])
+    assert stats["bit_errors"] == alone[1]["bit_errors"]
 
 
 def test_graph_issue_block_by_block_equals_one_call(streams):
