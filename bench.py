@@ -1315,6 +1315,12 @@ def run_serving(args):
             srv.poll(ids_last[i])                      # sets the server's last error to this request's
             failed.append(f"request {i} ({reqs[i][0]}, {reqs[i][1]} symbols): state {st_}: "
                           f"{rx_mod.lib().rx_server_last_error().decode()}")
+    # the same arrivals again with every issue call timed on the device (an
+    # event pair per call of blocks_per_step blocks): the block latency
+    srv.set_param("block_latency", 1)
+    serve(arrivals)
+    blat = sorted(srv.block_latency())
+    srv.set_param("block_latency", 0)
     handles = {k: int(srv.get_param(k)) for k in ("handles_created", "handles_destroyed", "handle_regrows")}
     srv.close()
     ok = all(s == rx_mod.REQ_DONE for s, _ in states)
@@ -1334,6 +1340,8 @@ def run_serving(args):
         "handles": handles,
         "request_latency_ms": {"p50": 1e3 * lat[len(lat) // 2], "p99": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]},
         "request_latency_ms_all_at_once": {"p50": 1e3 * lat0[len(lat0) // 2], "p99": 1e3 * lat0[-1]},
+        "block_latency_ms": {"p50": blat[len(blat) // 2], "p99": blat[min(len(blat) - 1, int(0.99 * len(blat)))],
+                             "calls": len(blat), "blocks_per_call": bps_default},
         "max_running": info["max_active"], "all_done": ok, "not_done": failed[:8],
         "ber_by_format": {f: float(np.mean([st["ber"] for (s_, st), (fm, _, _, _) in zip(states, reqs) if fm == f and st]))
                           for f in ("dp_qpsk", "dp_16qam", "gs4d64")},

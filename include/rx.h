@@ -492,7 +492,10 @@ int rx_server_poll(rx_server *s, uint64_t id, int *state, rx_stats *stats);
  * environment's CUDA_DEVICE_MAX_CONNECTIONS (the CUDA context's hardware
  * work queues, which the requests' streams share; 8 unless set before the
  * context is created): 4 threads and 4 blocks at 32 or more queues, else 2
- * threads (at most the host's cores) and 2 blocks at 16, 1 block below.  Many concurrent
+ * threads (at most the host's cores) and 2 blocks at 16, 1 block below.
+ * "block_latency" [0]: 1 times every issue call of every request (an event
+ * pair on the request's stream around the call's launches; turning it on
+ * clears the times kept), read by rx_server_get_block_latency.  Many concurrent
  * requests run best with CUDA_DEVICE_MAX_CONNECTIONS=32.  RX_EINVAL
  * otherwise. */
 int rx_server_set_param(rx_server *s, const char *key, double value);
@@ -500,6 +503,13 @@ int rx_server_set_param(rx_server *s, const char *key, double value);
  * "handles_destroyed", "handle_regrows" (pooled handles reused for a request
  * longer than their buffers, which then grow).  RX_EINVAL for other keys. */
 int rx_server_get_param(const rx_server *s, const char *key, double *value);
+/* With "block_latency" on: the device time (ms) from the start of each issue
+ * call's first launch to the end of its last (one call covers
+ * blocks_per_step blocks of a request, and includes the time other requests'
+ * work held the device), for the requests retired since it was turned on, in
+ * retirement order.  *n = how many are kept; the first min(cap, *n) go to ms
+ * (may be NULL when cap = 0). */
+int rx_server_get_block_latency(const rx_server *s, double *ms, size_t cap, size_t *n);
 /* Memory in use, the most requests ever running at once, steps taken. */
 int rx_server_info(rx_server *s, size_t *mem_used, int *max_active, long *steps);
 const char *rx_server_last_error(void);

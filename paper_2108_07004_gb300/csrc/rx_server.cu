@@ -54,6 +54,7 @@ struct Req {
     std::string key;                    // handle_key of the request
     long cap_n = 0;                     // symbols the handle's buffers hold (reused handles: >= N)
     double t_submit = 0, t_admit = 0, t_done = 0;   // server step counters
+    std::vector<cudaEvent_t> lat_ev;    // "block_latency": start / end event of each issue call
 };
 
 size_t estimate_bytes_n(size_t N) {
@@ -113,6 +114,8 @@ struct rx_server {
     int issue = 1;                      // the handles' issue mode (rx_set_param "issue")
     long blocks_per_step = 1;           // blocks of a running request issued per step
     long n_created = 0, n_destroyed = 0, n_regrown = 0;   // handles made, freed, reused with too small buffers
+    bool block_latency = false;         // time each issue call of a request (events on its stream)
+    std::vector<double> blk_ms;         // those times of retired requests, in retirement order
 };
 
 namespace {
@@ -131,6 +134,17 @@ void destroy_handle(rx_server *s, rx_handle *h, cudaStream_t st, cudaEvent_t don
     }
     if (done) cudaEventDestroy(done);
     if (st) cudaStreamDestroy(st);
+}
+
+// elapsed times of q's issue calls (from the start of the call's first
+// launch on q's stream to the end of its last), then the events are freed
+void collect_latency(rx_server *s, Req *q) {
+    for (size_t i = 0; i + 1 < q->lat_ev.size(); i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, q->lat_ev[i], q->lat_ev[i + 1]) == cudaSuccess) s->blk_ms.push_back(ms);
+    }
+    for (cudaEvent_t e : q->lat_ev) cudaEventDestroy(e);
+    q->lat_ev.clear();
 }
 
 void release(rx_server *s, Req *q) {
@@ -287,6 +301,7 @@ void rx_server_destroy(rx_server *s) {
     if (!s) return;
     for (Req *q : s->active) {
         if (q->st) cudaStreamSynchronize(q->st);
+        for (cudaEvent_t e : q->lat_ev) cudaEventDestroy(e);
         destroy_handle(s, q->h, q->st, q->done);
         q->h = nullptr;
     }
@@ -329,6 +344,7 @@ int rx_server_step(rx_server *s, int *n_active) {
         Req *q = s->active[i];
         if (q->next >= q->nblk && cudaEventQuery(q->done) == cudaSuccess) {
             if (rx_get_stats(q->h, &q->stats) != RX_OK) q->err = rx_last_error();
+            collect_latency(s, q);
             q->state = q->err.empty() ? Q_DONE : Q_FAILED;
             q->t_done = (double)s->steps;
             release(s, q);
@@ -356,14 +372,26 @@ int rx_server_step(rx_server *s, int *n_active) {
     std::vector<std::string> errs(todo.size());
     int dev = 0;
     cudaGetDevice(&dev);
+    const bool timed = s->block_latency;
     auto issue = [&](size_t i0, size_t i1) {
         cudaSetDevice(dev);                 // a new host thread starts on device 0
         for (size_t i = i0; i < i1; ++i) {
             Req *q = todo[i];
             const long b1 = std::min(q->nblk, q->next + s->blocks_per_step);
+            cudaEvent_t ev[2] = {nullptr, nullptr};
+            if (timed && cudaEventCreate(&ev[0]) == cudaSuccess && cudaEventCreate(&ev[1]) == cudaSuccess &&
+                cudaEventRecord(ev[0], q->st) == cudaSuccess) {
+                q->lat_ev.push_back(ev[0]);
+                q->lat_ev.push_back(ev[1]);
+            } else if (timed) {
+                if (ev[0]) cudaEventDestroy(ev[0]);
+                if (ev[1]) cudaEventDestroy(ev[1]);
+                ev[1] = nullptr;
+            }
             rcs[i] = rx_process_blocks(q->h, q->r.samples, q->r.n_samples, (size_t)q->next, (size_t)b1,
                                        q->r.llr_out, nullptr);
             if (rcs[i] != RX_OK) errs[i] = rx_last_error();
+            if (ev[1]) cudaEventRecord(ev[1], q->st);
         }
     };
     const size_t nt = std::min<size_t>(s->issue_threads, todo.size() / 4 + 1);
@@ -428,6 +456,10 @@ int rx_server_set_param(rx_server *s, const char *key, double value) {
         if (!(value >= 1 && value <= 64) || value != (double)(long)value)
             return srv_fail(RX_EINVAL, "issue_threads must be 1 .. 64");
         s->issue_threads = (size_t)value;
+    } else if (k == "block_latency") {
+        if (value != 0 && value != 1) return srv_fail(RX_EINVAL, "block_latency must be 0 or 1");
+        s->block_latency = value != 0;
+        if (s->block_latency) s->blk_ms.clear();
     } else if (k == "blocks_per_step") {
         if (!(value >= 1 && value <= 1 << 20) || value != (double)(long)value)
             return srv_fail(RX_EINVAL, "blocks_per_step must be 1 .. 2^20");
@@ -444,10 +476,18 @@ int rx_server_get_param(const rx_server *s, const char *key, double *value) {
     if (k == "issue") *value = s->issue;
     else if (k == "issue_threads") *value = (double)s->issue_threads;
     else if (k == "blocks_per_step") *value = (double)s->blocks_per_step;
+    else if (k == "block_latency") *value = s->block_latency ? 1 : 0;
     else if (k == "handles_created") *value = (double)s->n_created;
     else if (k == "handles_destroyed") *value = (double)s->n_destroyed;
     else if (k == "handle_regrows") *value = (double)s->n_regrown;
     else return srv_fail(RX_EINVAL, "unknown server parameter '" + k + "'");
+    return RX_OK;
+}
+
+int rx_server_get_block_latency(const rx_server *s, double *ms, size_t cap, size_t *n) {
+    if (!s || !n || (cap && !ms)) return srv_fail(RX_EINVAL, "NULL argument");
+    *n = s->blk_ms.size();
+    std::copy(s->blk_ms.begin(), s->blk_ms.begin() + (long)std::min(cap, s->blk_ms.size()), ms);
     return RX_OK;
 }
 

@@ -83,6 +83,7 @@ _PROTOS = {
     "rx_server_info": (_I, [_VP, C.POINTER(_SZ), C.POINTER(_I), C.POINTER(C.c_long)]),
     "rx_server_set_param": (_I, [_VP, C.c_char_p, _D]),
     "rx_server_get_param": (_I, [_VP, C.c_char_p, C.POINTER(_D)]),
+    "rx_server_get_block_latency": (_I, [_VP, C.POINTER(_D), _SZ, C.POINTER(_SZ)]),
     "rx_server_last_error": (C.c_char_p, []),
     "rx_set_demapper": (_I, [_VP, _VP]),
     "rx_set_symbol_output": (_I, [_VP, _VP, _VP]),
@@ -644,7 +645,7 @@ class Server:
             raise RxError(rc, lib().rx_server_last_error().decode())
 
     def set_param(self, key: str, value: float):
-        """"issue" (the handles' issue mode, 0/1/2), "issue_threads" or "blocks_per_step"."""
+        """"issue" (the handles' issue mode, 0/1/2), "issue_threads", "blocks_per_step" or "block_latency"."""
         self._ck(lib().rx_server_set_param(self.h, key.encode(), float(value)))
 
     def get_param(self, key: str) -> float:
@@ -652,6 +653,14 @@ class Server:
         v = _D()
         self._ck(lib().rx_server_get_param(self.h, key.encode(), C.byref(v)))
         return v.value
+
+    def block_latency(self) -> list[float]:
+        """Device ms of each timed issue call ("block_latency" on), retired requests only."""
+        n = _SZ()
+        self._ck(lib().rx_server_get_block_latency(self.h, None, 0, C.byref(n)))
+        buf = (_D * max(1, n.value))()
+        self._ck(lib().rx_server_get_block_latency(self.h, buf, n.value, C.byref(n)))
+        return list(buf[:n.value])
 
     def submit(self, fmt: str, samples: torch.Tensor, llr: torch.Tensor, bits: torch.Tensor | None = None,
                *, cd_ps_per_nm: float, taps: int, bps_phases: int, symbol_rate: float = 28e9, sps: int = 2,

@@ -69,7 +69,8 @@ def test_server_settings_and_counters_without_device(lib):
     from paper_2108_07004_gb300 import rx
     srv = rx.Server(1 << 30, 4)
     for key, good, bad in (("issue", (0, 1, 2), (3, -1, 0.5)), ("issue_threads", (1, 3, 64), (0, 65, 1.5)),
-                           ("blocks_per_step", (1, 4, 1 << 20), (0, (1 << 20) + 1, 2.5))):
+                           ("blocks_per_step", (1, 4, 1 << 20), (0, (1 << 20) + 1, 2.5)),
+                           ("block_latency", (1, 0), (2, -1, 0.5))):
         for v in good:
             srv.set_param(key, v)
             assert srv.get_param(key) == v
@@ -78,6 +79,7 @@ def test_server_settings_and_counters_without_device(lib):
                 srv.set_param(key, v)
     for key in ("handles_created", "handles_destroyed", "handle_regrows"):
         assert srv.get_param(key) == 0
+    assert srv.block_latency() == []
     for key in ("nothing", "slots"):
         with pytest.raises(rx.RxError):
             srv.get_param(key)

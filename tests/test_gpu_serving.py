@@ -96,6 +96,31 @@ def test_several_blocks_per_step_give_the_same_results(streams, issue, bps):
             assert alone[i][1][k] == mix[i][1][k], (issue, bps, i, k)
 
 
+def test_block_latency_times_every_issue_call(streams):
+    """With "block_latency" on, every issue call of every request is timed
+    (one time per call of blocks_per_step blocks, all positive) and the
+    results are those of the requests alone."""
+    from paper_2108_07004_gb300 import rx
+    alone = {i: _serve([i], streams)[0][i] for i in range(len(REQS))}
+    srv = rx.Server(1 << 33, 16)
+    srv.set_param("blocks_per_step", 2)
+    srv.set_param("block_latency", 1)
+    got = {i: _submit(srv, i, *streams[i]) for i in range(len(REQS))}
+    srv.run()
+    torch.cuda.synchronize()
+    srv.step()                               # retires what the last step left running
+    for i, (rid, llr) in got.items():
+        state, stats = srv.poll(rid)
+        assert state == rx.REQ_DONE
+        assert np.array_equal(llr.cpu().numpy(), alone[i][0]), i
+    lat = srv.block_latency()
+    calls = sum(-(-(-(-n // 16384)) // 2) for _, n, *_ in REQS)    # ceil(ceil(n / block) / 2)
+    assert len(lat) == calls and min(lat) > 0.0, (len(lat), calls)
+    srv.set_param("block_latency", 1)        # turning it on again clears the times
+    assert srv.block_latency() == []
+    srv.close()
+
+
 def test_pooled_handle_grows_for_a_longer_request(streams):
     """A request longer than the pooled handle it reuses (same key) grows
     that handle's buffers: the server counts one regrow, creates no second
