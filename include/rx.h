@@ -465,8 +465,11 @@ typedef struct {
  * times overlap on the device (the paper's multiple processing streams,
  * Sec. 2); by default a request's launches all go on its own stream
  * without event operations (issue mode 1, rx_server_set_param).  A finished request frees its slot and memory at the next step.
- * Results of a request equal those of a handle processing it alone.  Not
- * thread-safe; errors: rx_server_last_error(). */
+ * Results of a request equal those of a handle processing it alone.  Every
+ * entry point takes the server's lock, so submit / poll / info and the
+ * settings may be called from any thread; steps come from one place at a
+ * time (the caller's rx_server_step / rx_server_run, or the server's own loop
+ * of rx_server_start).  Errors: rx_server_last_error() (per thread). */
 typedef struct rx_server rx_server;
 #define RX_REQ_QUEUED  0
 #define RX_REQ_RUNNING 1
@@ -482,6 +485,16 @@ int rx_server_submit(rx_server *s, const rx_request *r, uint64_t *id);
 int rx_server_step(rx_server *s, int *n_left);
 /* Step until every submitted request is done. */
 int rx_server_run(rx_server *s);
+/* The server's own loop: a host thread of the library, on the device current
+ * at the call, that steps while requests run or wait (waiting up to 100 us
+ * between steps that issue nothing, and sleeping while none are submitted),
+ * so requests submitted from any thread are admitted and issued without the
+ * caller stepping; rx_server_step and rx_server_run return RX_ESTATE while it
+ * runs.  rx_server_stop ends it after its current step (requests still
+ * running then finish by rx_server_step / rx_server_run); rx_server_destroy
+ * stops it first.  RX_ESTATE if already running / not running. */
+int rx_server_start(rx_server *s);
+int rx_server_stop(rx_server *s);
 /* State (RX_REQ_*) of a request and, once done, its statistics. */
 int rx_server_poll(rx_server *s, uint64_t id, int *state, rx_stats *stats);
 /* Server settings: "issue" [1], the issue mode of the requests' handles
@@ -499,7 +512,8 @@ int rx_server_poll(rx_server *s, uint64_t id, int *state, rx_stats *stats);
  * requests run best with CUDA_DEVICE_MAX_CONNECTIONS=32.  RX_EINVAL
  * otherwise. */
 int rx_server_set_param(rx_server *s, const char *key, double value);
-/* Reads a setting above or a counter: "handles_created",
+/* Reads a setting above, "running" (1 while the server's loop runs) or a
+ * counter: "handles_created",
  * "handles_destroyed", "handle_regrows" (pooled handles reused for a request
  * longer than their buffers, which then grow).  RX_EINVAL for other keys. */
 int rx_server_get_param(const rx_server *s, const char *key, double *value);

@@ -21,9 +21,13 @@
 // Host code only; everything on the device goes through the public entry
 // points (rx_create, rx_process_blocks, rx_get_stats, ...).
 #include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <mutex>
 #include <memory>
 #include <string>
 #include <thread>
@@ -116,6 +120,13 @@ struct rx_server {
     long n_created = 0, n_destroyed = 0, n_regrown = 0;   // handles made, freed, reused with too small buffers
     bool block_latency = false;         // time each issue call of a request (events on its stream)
     std::vector<double> blk_ms;         // those times of retired requests, in retirement order
+    // the server's own loop (rx_server_start): the host thread that steps,
+    // the lock every entry point takes around the server's state, and the
+    // condition it waits on while idle
+    mutable std::mutex mu;
+    std::condition_variable cv;
+    std::thread loop;
+    std::atomic<bool> running{false};
 };
 
 namespace {
@@ -266,6 +277,129 @@ bool admit(rx_server *s, Req *q) {
 
 }  // namespace
 
+namespace {
+
+// One step: retire finished requests, admit from the queue, then issue the
+// next blocks_per_step blocks of every running request.  The server's lock
+// is held around the bookkeeping and released while blocks are issued (the
+// requests being issued are touched by this step alone; submit and poll may
+// run meanwhile).  Returns how many requests had blocks issued.
+size_t step_impl(rx_server *s, int *n_active) {
+    std::vector<Req *> todo;
+    long per_step = 1;
+    size_t threads = 1;
+    bool timed = false;
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        ++s->steps;
+        // retire requests whose last block has finished
+        for (size_t i = 0; i < s->active.size();) {
+            Req *q = s->active[i];
+            if (q->next >= q->nblk && cudaEventQuery(q->done) == cudaSuccess) {
+                if (rx_get_stats(q->h, &q->stats) != RX_OK) q->err = rx_last_error();
+                collect_latency(s, q);
+                q->state = q->err.empty() ? Q_DONE : Q_FAILED;
+                q->t_done = (double)s->steps;
+                release(s, q);
+                s->active.erase(s->active.begin() + (long)i);
+            } else {
+                ++i;
+            }
+        }
+        // admit from the head of the queue while a slot and memory are free
+        while (!s->queue.empty() && (int)s->active.size() < s->max_slots && make_room(s, s->queue.front())) {
+            Req *q = s->queue.front();
+            s->queue.pop_front();
+            if (admit(s, q)) s->active.push_back(q);
+        }
+        if ((int)s->active.size() > s->max_active_seen) s->max_active_seen = (int)s->active.size();
+        for (Req *q : s->active)
+            if (q->next < q->nblk) todo.push_back(q);
+        per_step = s->blocks_per_step;
+        threads = s->issue_threads;
+        timed = s->block_latency;
+    }
+    // the next blocks_per_step blocks of every running request, each request
+    // on its own stream.  Issuing a block costs the host a few launches (and,
+    // in issue mode 0, event operations) plus the call's own set-up, so the
+    // requests are split over a few host threads (each touches only its own
+    // requests' handles; the results are those of one thread)
+    std::vector<int> rcs(todo.size(), RX_OK);
+    std::vector<std::string> errs(todo.size());
+    int dev = 0;
+    cudaGetDevice(&dev);
+    auto issue = [&](size_t i0, size_t i1) {
+        cudaSetDevice(dev);                 // a new host thread starts on device 0
+        for (size_t i = i0; i < i1; ++i) {
+            Req *q = todo[i];
+            const long b1 = std::min(q->nblk, q->next + per_step);
+            cudaEvent_t ev[2] = {nullptr, nullptr};
+            if (timed && cudaEventCreate(&ev[0]) == cudaSuccess && cudaEventCreate(&ev[1]) == cudaSuccess &&
+                cudaEventRecord(ev[0], q->st) == cudaSuccess) {
+                q->lat_ev.push_back(ev[0]);
+                q->lat_ev.push_back(ev[1]);
+            } else if (timed) {
+                if (ev[0]) cudaEventDestroy(ev[0]);
+                if (ev[1]) cudaEventDestroy(ev[1]);
+                ev[1] = nullptr;
+            }
+            rcs[i] = rx_process_blocks(q->h, q->r.samples, q->r.n_samples, (size_t)q->next, (size_t)b1,
+                                       q->r.llr_out, nullptr);
+            if (rcs[i] != RX_OK) errs[i] = rx_last_error();
+            if (ev[1]) cudaEventRecord(ev[1], q->st);
+        }
+    };
+    const size_t nt = std::min<size_t>(threads, todo.size() / 4 + 1);
+    if (nt <= 1) {
+        issue(0, todo.size());
+    } else {
+        std::vector<std::thread> pool;
+        const size_t per = (todo.size() + nt - 1) / nt;
+        for (size_t t = 1; t < nt; ++t)
+            pool.emplace_back(issue, std::min(todo.size(), t * per), std::min(todo.size(), (t + 1) * per));
+        issue(0, std::min(todo.size(), per));
+        for (auto &th : pool) th.join();
+    }
+    std::lock_guard<std::mutex> lock(s->mu);
+    for (size_t i = 0; i < todo.size(); ++i) {
+        Req *q = todo[i];
+        if (rcs[i] != RX_OK) {
+            q->err = errs[i];
+            q->next = q->nblk;
+        } else {
+            q->next = std::min(q->nblk, q->next + per_step);
+        }
+        if (q->next >= q->nblk) cudaEventRecord(q->done, q->st);
+    }
+    if (n_active) *n_active = (int)(s->active.size() + s->queue.size());
+    return todo.size();
+}
+
+// The server's own loop (rx_server_start): steps while requests run or wait;
+// when a step issued nothing (every running request's blocks are in flight,
+// or nothing can be admitted yet) it waits up to 100 us for a submission or
+// for the device to finish some; with nothing submitted it sleeps until a
+// submission or rx_server_stop.
+void loop_main(rx_server *s, int dev) {
+    cudaSetDevice(dev);
+    while (s->running) {
+        {
+            std::unique_lock<std::mutex> lock(s->mu);
+            s->cv.wait(lock, [s] { return !s->running || !s->queue.empty() || !s->active.empty(); });
+            if (!s->running) break;
+        }
+        const size_t issued = step_impl(s, nullptr);
+        if (issued == 0) {
+            std::unique_lock<std::mutex> lock(s->mu);
+            const size_t queued = s->queue.size();
+            s->cv.wait_for(lock, std::chrono::microseconds(100),
+                           [s, queued] { return !s->running || s->queue.size() != queued; });
+        }
+    }
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *rx_server_last_error(void) { return g_srv_err.c_str(); }
@@ -299,6 +433,7 @@ rx_server *rx_server_create(size_t mem_budget_bytes, int max_slots) {
 
 void rx_server_destroy(rx_server *s) {
     if (!s) return;
+    if (s->running) rx_server_stop(s);
     for (Req *q : s->active) {
         if (q->st) cudaStreamSynchronize(q->st);
         for (cudaEvent_t e : q->lat_ev) cudaEventDestroy(e);
@@ -314,7 +449,6 @@ int rx_server_submit(rx_server *s, const rx_request *r, uint64_t *id) {
     if (!r->samples || !r->llr_out || r->n_samples < 2 || (r->n_samples & 1))
         return srv_fail(RX_EINVAL, "request needs device samples, an even n_samples and an LLR buffer");
     auto q = std::make_unique<Req>();
-    q->id = s->next_id++;
     q->r = *r;
     if (r->format.kind == RX_FMT_CUSTOM) {
         const int M = 1 << r->format.m_bits;
@@ -329,114 +463,71 @@ int rx_server_submit(rx_server *s, const rx_request *r, uint64_t *id) {
     if (q->mem > s->budget)
         return srv_fail(RX_EINVAL, "request needs about " + std::to_string(q->mem) +
                                        " bytes, more than the whole budget");
-    q->t_submit = (double)s->steps;
-    *id = q->id;
-    s->queue.push_back(q.get());
-    s->all[q->id] = std::move(q);
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        q->id = s->next_id++;
+        q->t_submit = (double)s->steps;
+        *id = q->id;
+        s->queue.push_back(q.get());
+        s->all[q->id] = std::move(q);
+    }
+    s->cv.notify_one();
     return RX_OK;
 }
 
 int rx_server_step(rx_server *s, int *n_active) {
     if (!s) return srv_fail(RX_EINVAL, "NULL server");
-    ++s->steps;
-    // retire requests whose last block has finished
-    for (size_t i = 0; i < s->active.size();) {
-        Req *q = s->active[i];
-        if (q->next >= q->nblk && cudaEventQuery(q->done) == cudaSuccess) {
-            if (rx_get_stats(q->h, &q->stats) != RX_OK) q->err = rx_last_error();
-            collect_latency(s, q);
-            q->state = q->err.empty() ? Q_DONE : Q_FAILED;
-            q->t_done = (double)s->steps;
-            release(s, q);
-            s->active.erase(s->active.begin() + (long)i);
-        } else {
-            ++i;
-        }
-    }
-    // admit from the head of the queue while a slot and memory are free
-    while (!s->queue.empty() && (int)s->active.size() < s->max_slots && make_room(s, s->queue.front())) {
-        Req *q = s->queue.front();
-        s->queue.pop_front();
-        if (admit(s, q)) s->active.push_back(q);
-    }
-    if ((int)s->active.size() > s->max_active_seen) s->max_active_seen = (int)s->active.size();
-    // the next blocks_per_step blocks of every running request, each request
-    // on its own stream.  Issuing a block costs the host a few launches (and,
-    // in issue mode 0, event operations) plus the call's own set-up, so the
-    // requests are split over a few host threads (each touches only its own
-    // requests' handles; the results are those of one thread)
-    std::vector<Req *> todo;
-    for (Req *q : s->active)
-        if (q->next < q->nblk) todo.push_back(q);
-    std::vector<int> rcs(todo.size(), RX_OK);
-    std::vector<std::string> errs(todo.size());
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const bool timed = s->block_latency;
-    auto issue = [&](size_t i0, size_t i1) {
-        cudaSetDevice(dev);                 // a new host thread starts on device 0
-        for (size_t i = i0; i < i1; ++i) {
-            Req *q = todo[i];
-            const long b1 = std::min(q->nblk, q->next + s->blocks_per_step);
-            cudaEvent_t ev[2] = {nullptr, nullptr};
-            if (timed && cudaEventCreate(&ev[0]) == cudaSuccess && cudaEventCreate(&ev[1]) == cudaSuccess &&
-                cudaEventRecord(ev[0], q->st) == cudaSuccess) {
-                q->lat_ev.push_back(ev[0]);
-                q->lat_ev.push_back(ev[1]);
-            } else if (timed) {
-                if (ev[0]) cudaEventDestroy(ev[0]);
-                if (ev[1]) cudaEventDestroy(ev[1]);
-                ev[1] = nullptr;
-            }
-            rcs[i] = rx_process_blocks(q->h, q->r.samples, q->r.n_samples, (size_t)q->next, (size_t)b1,
-                                       q->r.llr_out, nullptr);
-            if (rcs[i] != RX_OK) errs[i] = rx_last_error();
-            if (ev[1]) cudaEventRecord(ev[1], q->st);
-        }
-    };
-    const size_t nt = std::min<size_t>(s->issue_threads, todo.size() / 4 + 1);
-    if (nt <= 1) {
-        issue(0, todo.size());
-    } else {
-        std::vector<std::thread> pool;
-        const size_t per = (todo.size() + nt - 1) / nt;
-        for (size_t t = 1; t < nt; ++t)
-            pool.emplace_back(issue, std::min(todo.size(), t * per), std::min(todo.size(), (t + 1) * per));
-        issue(0, std::min(todo.size(), per));
-        for (auto &th : pool) th.join();
-    }
-    for (size_t i = 0; i < todo.size(); ++i) {
-        Req *q = todo[i];
-        if (rcs[i] != RX_OK) {
-            q->err = errs[i];
-            q->next = q->nblk;
-        } else {
-            q->next = std::min(q->nblk, q->next + s->blocks_per_step);
-        }
-        if (q->next >= q->nblk) cudaEventRecord(q->done, q->st);
-    }
-    if (n_active) *n_active = (int)(s->active.size() + s->queue.size());
+    if (s->running) return srv_fail(RX_ESTATE, "the server's own loop is running (rx_server_stop first)");
+    step_impl(s, n_active);
     return RX_OK;
 }
 
 int rx_server_run(rx_server *s) {
     if (!s) return srv_fail(RX_EINVAL, "NULL server");
+    if (s->running) return srv_fail(RX_ESTATE, "the server's own loop is running (rx_server_stop first)");
     int left = 1;
     while (left > 0) {
-        const int rc = rx_server_step(s, &left);
-        if (rc != RX_OK) return rc;
-        if (left > 0 && !s->active.empty()) {
-            // all blocks issued: wait for the oldest running request
-            bool issued = true;
-            for (Req *q : s->active) issued &= q->next >= q->nblk;
-            if (issued) cudaEventSynchronize(s->active.front()->done);
+        step_impl(s, &left);
+        cudaEvent_t oldest = nullptr;
+        {
+            std::lock_guard<std::mutex> lock(s->mu);
+            if (left > 0 && !s->active.empty()) {
+                // all blocks issued: wait for the oldest running request
+                bool issued = true;
+                for (Req *q : s->active) issued &= q->next >= q->nblk;
+                if (issued) oldest = s->active.front()->done;
+            }
         }
+        if (oldest) cudaEventSynchronize(oldest);
     }
+    return RX_OK;
+}
+
+int rx_server_start(rx_server *s) {
+    if (!s) return srv_fail(RX_EINVAL, "NULL server");
+    if (s->running) return srv_fail(RX_ESTATE, "the server's loop is already running");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return srv_fail(RX_ECUDA, "no CUDA device");
+    s->running = true;
+    s->loop = std::thread(loop_main, s, dev);
+    return RX_OK;
+}
+
+int rx_server_stop(rx_server *s) {
+    if (!s) return srv_fail(RX_EINVAL, "NULL server");
+    if (!s->running) return srv_fail(RX_ESTATE, "the server's loop is not running");
+    {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->running = false;
+    }
+    s->cv.notify_all();
+    s->loop.join();
     return RX_OK;
 }
 
 int rx_server_poll(rx_server *s, uint64_t id, int *state, rx_stats *stats) {
     if (!s || !state) return srv_fail(RX_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lock(s->mu);
     auto it = s->all.find(id);
     if (it == s->all.end()) return srv_fail(RX_EINVAL, "unknown request id");
     Req *q = it->second.get();
@@ -449,6 +540,7 @@ int rx_server_poll(rx_server *s, uint64_t id, int *state, rx_stats *stats) {
 int rx_server_set_param(rx_server *s, const char *key, double value) {
     if (!s || !key) return srv_fail(RX_EINVAL, "NULL argument");
     const std::string k(key);
+    std::lock_guard<std::mutex> lock(s->mu);
     if (k == "issue") {
         if (value != 0 && value != 1 && value != 2) return srv_fail(RX_EINVAL, "issue must be 0, 1 or 2");
         s->issue = (int)value;
@@ -473,7 +565,9 @@ int rx_server_set_param(rx_server *s, const char *key, double value) {
 int rx_server_get_param(const rx_server *s, const char *key, double *value) {
     if (!s || !key || !value) return srv_fail(RX_EINVAL, "NULL argument");
     const std::string k(key);
+    std::lock_guard<std::mutex> lock(s->mu);
     if (k == "issue") *value = s->issue;
+    else if (k == "running") *value = s->running ? 1 : 0;
     else if (k == "issue_threads") *value = (double)s->issue_threads;
     else if (k == "blocks_per_step") *value = (double)s->blocks_per_step;
     else if (k == "block_latency") *value = s->block_latency ? 1 : 0;
@@ -486,6 +580,7 @@ int rx_server_get_param(const rx_server *s, const char *key, double *value) {
 
 int rx_server_get_block_latency(const rx_server *s, double *ms, size_t cap, size_t *n) {
     if (!s || !n || (cap && !ms)) return srv_fail(RX_EINVAL, "NULL argument");
+    std::lock_guard<std::mutex> lock(s->mu);
     *n = s->blk_ms.size();
     std::copy(s->blk_ms.begin(), s->blk_ms.begin() + (long)std::min(cap, s->blk_ms.size()), ms);
     return RX_OK;
@@ -493,6 +588,7 @@ int rx_server_get_block_latency(const rx_server *s, double *ms, size_t cap, size
 
 int rx_server_info(rx_server *s, size_t *mem_used, int *max_active, long *steps) {
     if (!s) return srv_fail(RX_EINVAL, "NULL server");
+    std::lock_guard<std::mutex> lock(s->mu);
     if (mem_used) *mem_used = s->used;
     if (max_active) *max_active = s->max_active_seen;
     if (steps) *steps = s->steps;

@@ -79,6 +79,8 @@ _PROTOS = {
     "rx_server_submit": (_I, [_VP, _VP, C.POINTER(C.c_uint64)]),
     "rx_server_step": (_I, [_VP, C.POINTER(_I)]),
     "rx_server_run": (_I, [_VP]),
+    "rx_server_start": (_I, [_VP]),
+    "rx_server_stop": (_I, [_VP]),
     "rx_server_poll": (_I, [_VP, C.c_uint64, C.POINTER(_I), _VP]),
     "rx_server_info": (_I, [_VP, C.POINTER(_SZ), C.POINTER(_I), C.POINTER(C.c_long)]),
     "rx_server_set_param": (_I, [_VP, C.c_char_p, _D]),
@@ -683,6 +685,13 @@ class Server:
 
     def run(self):
         self._ck(lib().rx_server_run(self.h))
+
+    def start(self):
+        """The server's own loop: admits and issues without step() calls."""
+        self._ck(lib().rx_server_start(self.h))
+
+    def stop(self):
+        self._ck(lib().rx_server_stop(self.h))
 
     def poll(self, rid: int):
         st = C.c_int()

@@ -80,6 +80,9 @@ def test_server_settings_and_counters_without_device(lib):
     for key in ("handles_created", "handles_destroyed", "handle_regrows"):
         assert srv.get_param(key) == 0
     assert srv.block_latency() == []
+    assert srv.get_param("running") == 0
+    with pytest.raises(rx.RxError):
+        srv.stop()                           # no loop to stop
     for key in ("nothing", "slots"):
         with pytest.raises(rx.RxError):
             srv.get_param(key)

@@ -31,6 +31,7 @@ def streams():
 def _submit(srv, i, samples, bits):
     fmt, n, km, esn0, T, B = REQS[i]
     llr = torch.full((n, M[fmt]), float("nan"), dtype=torch.float32, device="cuda")
+    torch.cuda.synchronize()                 # the fill is done before the request's stream writes
     rid = srv.submit(fmt, samples, llr, bits, cd_ps_per_nm=17.0 * km, taps=T, bps_phases=B,
                      fft=4096, overlap=1024, block=16384, n_pre=2048)
     return rid, llr
@@ -118,6 +119,45 @@ def test_block_latency_times_every_issue_call(streams):
     assert len(lat) == calls and min(lat) > 0.0, (len(lat), calls)
     srv.set_param("block_latency", 1)        # turning it on again clears the times
     assert srv.block_latency() == []
+    srv.close()
+
+
+def test_server_loop_admits_requests_submitted_while_it_runs(streams):
+    """The server's own loop (rx_server_start): requests submitted one by one
+    while it runs are admitted and issued without step() calls, each with
+    the result of the request alone; step() is refused while the loop runs,
+    and after stop() the caller steps again."""
+    import time
+    from paper_2108_07004_gb300 import rx
+    alone = {i: _serve([i], streams)[0][i] for i in range(len(REQS))}
+    srv = rx.Server(1 << 33, 16)
+    srv.start()
+    assert srv.get_param("running") == 1
+    with pytest.raises(rx.RxError):
+        srv.step()
+    with pytest.raises(rx.RxError):
+        srv.start()
+    got = {}
+    for i in range(len(REQS)):
+        got[i] = _submit(srv, i, *streams[i])
+        time.sleep(0.002)
+    t0 = time.time()
+    while any(srv.poll(rid)[0] not in (rx.REQ_DONE, rx.REQ_FAILED) for rid, _ in got.values()):
+        assert time.time() - t0 < 60.0, "requests not finished by the server's loop"
+        time.sleep(0.001)
+    torch.cuda.synchronize()
+    for i, (rid, llr) in got.items():
+        state, stats = srv.poll(rid)
+        assert state == rx.REQ_DONE
+        assert np.array_equal(llr.cpu().numpy(), alone[i][0]), i
+        assert stats["bit_errors"] == alone[i][1]["bit_errors"]
+    srv.stop()
+    assert srv.get_param("running") == 0
+    rid, llr = _submit(srv, 0, *streams[0])  # stepped by the caller again
+    srv.run()
+    torch.cuda.synchronize()
+    assert srv.poll(rid)[0] == rx.REQ_DONE
+    assert np.array_equal(llr.cpu().numpy(), alone[0][0])
     srv.close()
 
 
