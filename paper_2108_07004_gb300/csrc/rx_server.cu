@@ -18,6 +18,11 @@
 // other requests fill the device, and the host issues about a third of the
 // operations of the multi-stream mode.
 //
+// The steps come from the caller (rx_server_step / rx_server_run) or from the
+// server's own host thread (rx_server_start), which steps while requests run
+// or wait; every entry point takes the server's lock, which a step releases
+// while it issues blocks.
+//
 // Host code only; everything on the device goes through the public entry
 // points (rx_create, rx_process_blocks, rx_get_stats, ...).
 #include <algorithm>
