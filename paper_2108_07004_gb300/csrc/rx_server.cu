@@ -32,6 +32,7 @@
 #include <cstdlib>
 #include <cstring>
 #include <deque>
+#include <exception>
 #include <mutex>
 #include <memory>
 #include <string>
@@ -514,7 +515,12 @@ int rx_server_start(rx_server *s) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return srv_fail(RX_ECUDA, "no CUDA device");
     s->running = true;
-    s->loop = std::thread(loop_main, s, dev);
+    try {
+        s->loop = std::thread(loop_main, s, dev);
+    } catch (const std::exception &e) {
+        s->running = false;
+        return srv_fail(RX_ENOMEM, std::string("cannot start the server's thread: ") + e.what());
+    }
     return RX_OK;
 }
 
