@@ -110,6 +110,26 @@ def peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
 
 
+def rank_env():
+    """(rank, world size, local rank) of this process under torchrun; (0, 1, 0) alone."""
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def max_over_ranks(v: float, device=None) -> float:
+    """The largest v over the ranks of the process group (v itself with no
+    group): every rank's timed region must have ended for the job's step to
+    have, so the job's time per step is the slowest rank's.  The tensor sits
+    on `device` (the rank's GPU under NCCL; None: the host, as gloo wants)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(v)
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def make_inputs(rank: int, n_sym: int, n_streams: int):
     rxs, bits = [], []
     for p in range(n_streams):
@@ -316,7 +336,7 @@ def stage_errors(rx_mod, torch, st, res, wl: dict, precision: int) -> dict:
 
 
 def run_reference(args):
-    rank = int(os.environ.get("RANK", "0"))
+    rank, _, _ = rank_env()
     if rank != 0:
         return
     n = args.ref_sym
@@ -344,9 +364,7 @@ def run_ours(args):
     import torch.distributed as dist
     from paper_2108_07004_gb300 import rx as rx_mod
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = rank_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
@@ -437,10 +455,7 @@ def run_ours(args):
     stage = {s: r.profile(s) for s in ("cdc", "fir", "bps", "unwrap", "demap", "lms", "startup")}
     lat = sorted(r.block_latency())
     r.set("profile", 0)
-    if world > 1:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+    ms = max_over_ranks(ms, device="cuda")
     bits_per_step = S * n_sym * 6 * world
     value = bits_per_step / (ms * 1e-3) / 1e9
 
@@ -479,10 +494,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         dt = (time.perf_counter() - t0) / (ke * F)
         l_h = l_hs[0]
-        if world > 1:
-            t = torch.tensor([dt], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            dt = t.item()
+        dt = max_over_ranks(dt, device="cuda")
         e2e = {"value": bits_per_step / dt / 1e9, "unit": "Gbit/s",
                "h2d_bytes_per_step": int(rx_h.nbytes + bits_h.nbytes),
                "d2h_bytes_per_step": int(l_h.numel() * 4), "ms_per_step": dt * 1e3}
