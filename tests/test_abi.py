@@ -89,3 +89,22 @@ def test_server_settings_and_counters_without_device(lib):
         with pytest.raises(rx.RxError):
             srv.set_param(key, 1)
     srv.close()
+
+
+def test_server_loop_start_and_stop_without_requests(lib):
+    """rx_server_start either starts the server's loop (a device is present:
+    it idles with nothing submitted, and rx_server_stop ends it) or, with no
+    device, fails with an error and leaves no loop running."""
+    from paper_2108_07004_gb300 import rx
+    srv = rx.Server(1 << 30, 4)
+    try:
+        srv.start()
+    except rx.RxError:
+        assert srv.get_param("running") == 0
+    else:
+        assert srv.get_param("running") == 1
+        with pytest.raises(rx.RxError):
+            srv.step()                       # steps come from the loop while it runs
+        srv.stop()
+        assert srv.get_param("running") == 0
+    srv.close()
