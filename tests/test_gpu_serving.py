@@ -1,7 +1,9 @@
 """Serving with continuous batching (rx_server_*): every request's LLRs and
 counts are the same alone and in a mix of requests of different formats,
-lengths and links, and a small device-memory budget makes requests queue
-without changing any result."""
+lengths and links — in every issue mode, with several blocks per step, with
+block latency timed, from several host threads and through the server's own
+loop — and a small device-memory budget makes requests queue without
+changing any result."""
 import numpy as np
 import pytest
 
